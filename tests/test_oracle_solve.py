@@ -1,0 +1,199 @@
+"""Pins of the oracle's reduced system and solves.
+
+Closed forms (linear patch test, potential flow past a cylinder), invariants
+(antisymmetry, the symmetry the paper's Table 1 shows, flux balance, linearity)
+and agreement of three independent solution routes (dense Cholesky, sparse LU,
+the element-by-element CG of Appendix A), plus Schur form == MPC form."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import mesh as M, post as P, solve as SV, system as S
+from paper_2512_12232_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def distorted_mesh_without_bodies(nx=20, ny=14, seed=0, amp=0.3):
+    m = M.build_mesh((0.0, 2.0, -1.0, 0.4, nx, ny), np.zeros((0, 3)), 0)
+    rng = np.random.default_rng(seed)
+    hx, hy = 2.0 / nx, 1.4 / ny
+    m.x[1:-1, 1:-1] += rng.uniform(-amp, amp, (ny - 1, nx - 1)) * hx
+    m.y[1:-1, 1:-1] += rng.uniform(-amp, amp, (ny - 1, nx - 1)) * hy
+    return m
+
+
+def test_linear_patch_test_on_distorted_mesh():
+    """Bilinear isoparametric elements reproduce any linear field exactly."""
+    m = distorted_mesh_without_bodies()
+    g = (0.7 * m.x - 1.9 * m.y + 0.3).ravel()
+    sysm = S.assemble(m, g=g)
+    _, psi = SV.solve_direct(sysm)
+    np.testing.assert_allclose(psi, g, rtol=0, atol=1e-13)
+
+
+def test_three_solution_routes_agree_on_a_tiny_mesh():
+    c = W.Case(-3.0, 3.0, -2.0, 2.0, 30, 20, np.array([[0.2, 0.1, 0.8], [-1.6, -0.3, 0.4]]), 9)
+    m = M.build_mesh(c.grid, c.bodies, c.sweeps, c.bc)
+    sysm = S.assemble(m, 1.3)
+    u1, psi1 = SV.solve_direct(sysm, dense=True)
+    u2, psi2 = SV.solve_direct(sysm)
+    np.testing.assert_allclose(psi1, psi2, rtol=0, atol=1e-12)
+    x, psik, it, _ = SV.cg_paper(sysm, m.kind.ravel(), m.body.ravel(), tol=1e-14, criterion="relative")
+    assert it > 10
+    np.testing.assert_allclose(x, psi2, rtol=0, atol=1e-11)
+    np.testing.assert_allclose(psik, u2[sysm.n_free:], rtol=0, atol=1e-11)
+    # the paper's absolute stopping rule on sum r^2 also stops
+    _, _, it2, rn = SV.cg_paper(sysm, m.kind.ravel(), m.body.ravel(), tol=1e-24, criterion="paper")
+    assert rn <= 1e-24 and it2 > 10
+
+
+def test_single_cylinder_body_value_is_zero_by_antisymmetry():
+    c = W.single_cylinder()
+    m = M.build_mesh(c.grid, c.bodies, c.sweeps, c.bc)
+    sysm = S.assemble(m, 1.0)
+    u, psi = SV.solve_direct(sysm)
+    assert abs(u[-1]) < 1e-12
+    P_ = psi.reshape(m.ny + 1, m.nx + 1)
+    np.testing.assert_allclose(P_, -P_[::-1, :], atol=1e-12)
+
+
+def exact_cylinder_psi(x, y, a, U=1.0):
+    r2 = np.maximum(x * x + y * y, 1e-300)
+    return U * y * (1.0 - a * a / r2)
+
+
+def test_closed_form_cylinder_second_order_convergence():
+    """Dirichlet data from psi = U y (1 - a^2/r^2) on the outer ring: C = 0 and the
+    nodal error falls with order ~2 under refinement."""
+    errs, hs = [], []
+    for nx in (64, 128, 256):
+        c = W.Case(-4.0, 4.0, -2.0, 2.0, nx, nx // 2, np.array([[0.0, 0.0, 0.5]]), 3 * nx // 8)
+        m = M.build_mesh(c.grid, c.bodies, c.sweeps, c.bc)
+        g = exact_cylinder_psi(m.x, m.y, 0.5).ravel()
+        sysm = S.assemble(m, g=g)
+        u, psi = SV.solve_direct(sysm)
+        assert abs(u[-1]) < 1e-11
+        live = (m.kind != M.INACTIVE).ravel()
+        ex = np.where(m.kind == M.BODY, 0.0, exact_cylinder_psi(m.x, m.y, 0.5)).ravel()
+        errs.append(np.abs(psi - ex)[live].max())
+        hs.append(8.0 / nx)
+    order = np.log(errs[1] / errs[2]) / np.log(hs[1] / hs[2])
+    assert order > 1.7, (errs, order)
+
+
+def test_surface_velocity_approaches_two_u_sin_theta():
+    """Tangential speed on an isolated cylinder is 2U|sin theta|; the boundary-edge
+    estimate converges to it (first order in h, pointwise)."""
+    err = []
+    for nx in (128, 256):
+        c = W.Case(-4.0, 4.0, -2.0, 2.0, nx, nx // 2, np.array([[0.0, 0.0, 0.5]]), 3 * nx // 8)
+        m = M.build_mesh(c.grid, c.bodies, c.sweeps, c.bc)
+        g = exact_cylinder_psi(m.x, m.y, 0.5).ravel()
+        sysm = S.assemble(m, g=g)
+        u, psi = SV.solve_direct(sysm)
+        th, ut = P.surface_velocity(m, psi, u[sysm.n_free:], 0)
+        assert th.size > 20 and np.all((th >= 0) & (th < 360))
+        err.append(np.mean(np.abs(np.abs(ut) - 2 * np.abs(np.sin(np.radians(th))))))
+    assert err[1] < 0.75 * err[0] and err[1] < 0.3
+
+
+def test_paper_validation_channel_body_value_is_one_half():
+    """Validation section: walls psi = 0 (bottom) and psi = 1 (top), natural inlet and
+    outlet, a centred cylinder; the paper reports 0.50001959 against the exact 0.5."""
+    gold = json.load(open(os.path.join(GOLDEN, "paper_values.json")))
+    # radius 0.21 (8.4 h): no grid node lies on the circle, so rounding of the
+    # mirrored node positions cannot classify the two halves differently
+    c = W.Case(-2.0, 2.0, 0.0, 1.0, 160, 40, np.array([[0.0, 0.5, 0.21]]), 40,
+               bc=(W.BC_NATURAL, W.BC_NATURAL, W.BC_DIRICHLET_UY, W.BC_DIRICHLET_UY))
+    m = M.build_mesh(c.grid, c.bodies, c.sweeps, c.bc)
+    sysm = S.assemble(m, 1.0)
+    u, _ = SV.solve_direct(sysm)
+    C = u[sysm.n_free]
+    assert abs(C - 0.5) < 1e-10
+    assert abs(C - gold["validation_body_psi"]["value"]) < 3e-5
+
+
+def paper_like_channel(delta, nx=403, ny=201, S_=60):
+    """Five cylinders in the channel [0,1]x[0,0.5] (walls psi = 0 / 1, natural inlet
+    and outlet): 1, 2, 3 of D = 0.2 on the axis, 4 and 5 of D = 0.1 transverse with
+    centre distance h_c = delta * h_d.  The x positions are an assumption; the grid
+    is chosen so that no node lies exactly on a circle (no rounding-decided ties)."""
+    hd = 0.5
+    yc = 0.25
+    hc = delta * hd
+    bodies = np.array([[0.15, yc, 0.1], [0.55, yc, 0.1], [0.85, yc, 0.1],
+                       [0.35, yc - hc / 2, 0.05], [0.35, yc + hc / 2, 0.05]])
+    return W.Case(0.0, 1.0, 0.0, 0.5, nx, ny, bodies, S_,
+                  bc=(W.BC_NATURAL, W.BC_NATURAL, W.BC_DIRICHLET_UY, W.BC_DIRICHLET_UY))
+
+
+def test_table1_structure_symmetry_and_trend():
+    """Table 1 shows psi_1 = 0.5, psi_4 + psi_5 = 1 and CoPFI < 1 rising with delta.
+    The same layout family (positions assumed) must show the same structure;
+    the printed values themselves are parity-unpinned (geometry in figures only)."""
+    gold = json.load(open(os.path.join(GOLDEN, "paper_values.json")))
+    rows = gold["table1"]["rows"]
+    for r in rows:   # the table is internally consistent
+        assert abs((r["psi5"] - r["psi4"]) - r["Q54"]) < 2e-5
+        assert abs(r["Q54"] / r["delta"] - r["CoPFI"]) < 2e-5
+    prev = -1
+    for r in rows:
+        c = paper_like_channel(r["delta"])
+        m = M.build_mesh(c.grid, c.bodies, c.sweeps, c.bc)
+        sysm = S.assemble(m, 2.0)
+        u, _ = SV.solve_direct(sysm)
+        C = u[sysm.n_free:]
+        assert abs(C[0] - 0.5) < 1e-10 and abs(C[1] - 0.5) < 1e-10 and abs(C[2] - 0.5) < 1e-10
+        assert abs(C[3] + C[4] - 1.0) < 1e-10
+        cp, q = P.copfi(C, c.bodies, 3, 4, 2.0)
+        assert abs(cp - q / r["delta"]) < 1e-12
+        assert 0 < cp < 1 and cp > prev
+        prev = cp
+
+
+def test_five_cylinder_symmetry_invariants():
+    c = W.five_cylinder_case(0.5, 320, 160, 40)
+    m = M.build_mesh(c.grid, c.bodies, c.sweeps, c.bc)
+    sysm = S.assemble(m, 1.0)
+    u, psi = SV.solve_direct(sysm)
+    C = u[sysm.n_free:]
+    assert np.abs(C[:3]).max() < 1e-12
+    assert abs(C[3] + C[4]) < 1e-12 and C[4] > 0
+
+
+def test_flux_balance_and_zero_body_circulation():
+    c = W.five_cylinder_case(1.0, 200, 100, 30)
+    m = M.build_mesh(c.grid, c.bodies, c.sweeps, c.bc)
+    sysm = S.assemble(m, 1.0)
+    u, psi = SV.solve_direct(sysm)
+    y = S.full_operator_apply(sysm, psi)
+    kind = m.kind.ravel()
+    scale = np.abs(y[kind == M.DIRICHLET]).max()
+    assert abs(y[kind == M.DIRICHLET].sum()) < 1e-11 * scale * 10   # 1^T K = 0
+    assert np.abs(y[kind == M.FREE]).max() < 1e-11 * scale
+    for k in range(5):
+        sel = (kind == M.BODY) & (m.body.ravel() == k)
+        assert abs(y[sel].sum()) < 1e-11 * scale                    # collapsed body row
+
+
+def test_linearity_in_u():
+    c = W.five_cylinder_case(0.25, 160, 80, 20)
+    m = M.build_mesh(c.grid, c.bodies, c.sweeps, c.bc)
+    _, p1 = SV.solve_direct(S.assemble(m, 1.0))
+    _, p3 = SV.solve_direct(S.assemble(m, 3.5))
+    np.testing.assert_allclose(p3, 3.5 * p1, rtol=0, atol=1e-12 * np.abs(p3).max())
+
+
+def test_schur_form_equals_mpc_form():
+    c = W.five_cylinder_case(0.25, 200, 100, 30)
+    m = M.build_mesh(c.grid, c.bodies, c.sweeps, c.bc)
+    sysm = S.assemble(m, 1.0)
+    u, psi = SV.solve_direct(sysm)
+    u2, psi2, Smat = SV.solve_schur(sysm, m.kind.ravel(), m.body.ravel())
+    np.testing.assert_allclose(u2[sysm.n_free:], u[sysm.n_free:], rtol=0, atol=1e-12)
+    np.testing.assert_allclose(psi2, psi, rtol=0, atol=1e-11)
+    np.testing.assert_allclose(Smat, Smat.T, atol=1e-10)
+    assert np.all(np.linalg.eigvalsh(Smat) > 0)
