@@ -1,0 +1,207 @@
+/*
+ * pfq4.h - C ABI of the GB300 matrix-free Q4 stream-function solver.
+ *
+ * Method: Sadasivan & Yadav, "A Computational Approach for Multi-Body Potential-Flow
+ * Interaction Effects Using Matrix-Free FEM and Body-Conforming Grids".
+ *   - mesh: section "Body-Conforming Grid Generation" (background Cartesian grid,
+ *     near-boundary nodes moved onto the bodies, Laplacian propagation of the
+ *     displacement, x_new = x_old + d);
+ *   - operator: section "Weak formulation", K_e = int (grad N)^T grad N over bilinear
+ *     quadrilaterals, never assembled (section "Matrix-Free Conjugate Gradient with
+ *     Multiple Constraint Enforcement");
+ *   - unknowns: N_dof = N_int + N_N + N_b, one multi-point-constraint value C_i per
+ *     body (section "Boundary Conditions": psi = C_i on body i);
+ *   - solve: Conjugate Gradient of Appendix A (Algorithm);
+ *   - outputs: surface tangential velocity (section "Velocity Field and Surface
+ *     Tangential Velocity"), Q and CoPFI (section "Effect of Gap Ratio").
+ *
+ * Conventions for every function:
+ *   - The return value is a pf_status; 0 (PF_OK) means success.  Nothing throws
+ *     across the ABI.  pf_last_error() returns a message for the calling thread's
+ *     last failure (valid until that thread's next call).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Calls are ordered on that stream; functions that return host values
+ *     synchronise the stream before returning.
+ *   - Pointers named dev_* are device pointers owned by the caller (for example
+ *     torch tensors' data_ptr()); all other pointers are host memory owned by the
+ *     caller.  Opaque handles (pf_batch) own their device memory, which is
+ *     allocated through the allocator installed with pf_set_allocator (default:
+ *     cudaMallocAsync on the call's stream) and released by pf_batch_destroy.
+ *   - Nodes are numbered logically per variant: node (i, j), 0 <= i <= nx,
+ *     0 <= j <= ny, has index j*(nx+1) + i.  Node-valued outputs of a batch are the
+ *     variants' logical arrays concatenated in variant order.
+ *   - Every call must be made with the device that built the handle current.
+ */
+#ifndef PFQ4_H
+#define PFQ4_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int pf_status;
+enum {
+    PF_OK = 0,
+    PF_EINVAL = 1,          /* bad argument: sizes, NULL pointers, bodies overlapping / too close to the box */
+    PF_EMESH_INVALID = 2,   /* generated mesh unusable: det J <= 0 at a Gauss point of an active cell */
+    PF_ENOT_CONVERGED = 3,  /* k_max reached before the tolerance; outputs hold the last iterate */
+    PF_EBREAKDOWN = 4,      /* p^T A p <= 0 or not finite in CG */
+    PF_ETIMEOUT = 5,        /* a bounded device-side wait gave up */
+    PF_ECUDA = 6,           /* a CUDA runtime call failed (message in pf_last_error) */
+    PF_ENOMEM = 7           /* device allocation failed */
+};
+
+/* Side order for boundary conditions: left (x = x0), right (x = x1), bottom (y = y0), top (y = y1). */
+enum { PF_BC_DIRICHLET_UY = 0,  /* psi = U*y on the side (the uniform stream; a reference streamline) */
+       PF_BC_NATURAL = 1 };     /* zero normal derivative (inlet / outlet, section "Validation") */
+
+enum { PF_FP64 = 0,             /* FP64 vectors, operator and reductions */
+       PF_MIXED = 1 };          /* FP32 operator + vectors, FP64 reductions / scalars / true residual,
+                                   iterative refinement in FP64 */
+
+enum { PF_OBJ_COPFI = 0,        /* J = (C_hi - C_lo) / (U (cy_hi - cy_lo)) */
+       PF_OBJ_GAP_FLOW = 1 };   /* J = C_hi - C_lo */
+
+/* Node kinds reported by pf_mesh_tags. */
+enum { PF_NODE_FREE = 0, PF_NODE_DIRICHLET = 1, PF_NODE_BODY = 2, PF_NODE_INACTIVE = 3 };
+
+typedef struct pf_grid { double x0, x1, y0, y1; int nx, ny; } pf_grid;   /* background grid, nx x ny cells */
+typedef struct pf_body { double cx, cy, r; } pf_body;                     /* circular body Gamma_i */
+
+typedef struct pf_mesh_stats {
+    long long n_nodes;          /* (nx+1)(ny+1) */
+    long long n_free;           /* N_int + N_N */
+    long long n_dof;            /* n_free + n_bodies */
+    long long n_body_nodes;     /* nodes carrying a body value */
+    long long n_inactive;
+    long long n_active_cells;
+    long long n_general_cells;  /* active cells with a displaced corner (stored K_e used) */
+    int n_bodies;
+    int n_boundary_edges;       /* over all bodies of the variant */
+    double min_detJ;            /* minimum det J over the Gauss points of active cells */
+    double h;                   /* max(hx, hy) */
+} pf_mesh_stats;
+
+typedef struct pf_solve_opts {
+    double tol;            /* stop when ||b - A u||_2 / ||b||_2 <= tol (true residual, FP64) */
+    long long k_max;       /* cap on the total CG iterations per variant */
+    int precision;         /* PF_FP64 or PF_MIXED */
+    double inner_tol;      /* PF_MIXED: relative residual reduction of each inner FP32 solve */
+    int chunk;             /* CG iterations per captured graph launch (0 = automatic) */
+    int warm_start;        /* 1: start from the previous solution held by the handle */
+} pf_solve_opts;
+
+typedef struct pf_solve_info {
+    long long iters;             /* CG iterations (all inner solves) */
+    int refinements;             /* true-residual evaluations after the first */
+    int status;                  /* per-variant pf_status */
+    double rel_true_residual;    /* ||b - A u|| / ||b||, FP64 */
+    long long n_dof;
+} pf_solve_info;
+
+typedef struct pf_timing {
+    double cg_kernel_ms;         /* summed device time of the fused CG-iteration launches (CUDA events) */
+    long long cg_launches;       /* number of such launches */
+    double residual_kernel_ms;   /* summed device time of the FP64 true-residual launches */
+    long long residual_launches;
+    double solve_ms;             /* device time of the whole solve, events on the call's stream */
+    double cg_bytes_per_launch;  /* algorithmic HBM bytes of one fused CG launch over all variants */
+} pf_timing;
+
+typedef struct pf_batch pf_batch;   /* opaque: one or more mesh variants and their solver state */
+
+/* Optional allocator hook (e.g. PyTorch's caching allocator).  alloc(bytes, stream, ctx) returns
+   a device pointer or NULL; free(ptr, stream, ctx) releases it.  Pass NULLs to restore the default.
+   Affects handles built afterwards. */
+typedef void* (*pf_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*pf_free_fn)(void* ptr, void* stream, void* ctx);
+pf_status pf_set_allocator(pf_alloc_fn alloc, pf_free_fn free_fn, void* ctx);
+
+/* Build the body-conforming mesh of n_variants independent problems
+   (section "Body-Conforming Grid Generation").
+   grids[v]: background grid of variant v (nx, ny >= 2).
+   body_offsets[v] .. body_offsets[v+1]-1: rows of `bodies` belonging to variant v
+     (0 <= bodies per variant <= 64).  Bodies must be disjoint, have r > 0, and lie at
+     least 2h inside the box, else PF_EINVAL.
+   sweeps: Jacobi smoothing sweeps S >= 0 of the displacement.
+   bc[4]: PF_BC_* for left, right, bottom, top (at least one side must be Dirichlet).
+   On success *out receives a handle; on PF_EMESH_INVALID the handle is still returned
+   (so pf_mesh_stats can report min_detJ) but solves on it are refused. */
+pf_status pf_batch_build(const pf_grid* grids, const int* body_offsets, const pf_body* bodies,
+                         int n_variants, int sweeps, const int bc[4], void* stream, pf_batch** out);
+
+/* Single-variant convenience form of pf_batch_build. */
+pf_status pf_mesh_build(const pf_grid* grid, const pf_body* bodies, int n_bodies, int sweeps,
+                        const int bc[4], void* stream, pf_batch** out);
+
+void pf_batch_destroy(pf_batch* b);
+
+pf_status pf_batch_size(const pf_batch* b, int* n_variants, long long* total_nodes, int* total_bodies);
+pf_status pf_mesh_stats_get(const pf_batch* b, int variant, pf_mesh_stats* out);
+
+/* Final node coordinates of variant v: dev_xy[n][2] (x, y), logical order, FP64. */
+pf_status pf_mesh_coords(const pf_batch* b, int variant, double* dev_xy, void* stream);
+
+/* Node classification of variant v: dev_kind[n] = PF_NODE_*, dev_body[n] = body index
+   (local to the variant) for BODY nodes, else -1.  Either pointer may be NULL. */
+pf_status pf_mesh_tags(const pf_batch* b, int variant, int8_t* dev_kind, int32_t* dev_body, void* stream);
+
+/* Matrix-free operator of the reduced system on nodal vectors (Appendix A, "Compute Ap"):
+   y_n = sum over active cells e containing n of (K_e p_e)_n for FREE and BODY nodes,
+   0 for DIRICHLET and INACTIVE nodes, where p is used as given at every node (so a
+   DIRICHLET value enters as lifting).  body_sums[k] (host, optional) receives the
+   collapsed body rows sum_{n in body k} y_n for the variant's bodies.
+   precision PF_FP64 uses the FP64 element matrices; PF_MIXED rounds p to FP32 and
+   applies the FP32 element matrices (FP32 result widened to FP64).  All variants'
+   logical vectors concatenated; body_sums over all bodies. */
+pf_status pf_apply(pf_batch* b, int precision, const double* dev_p, double* dev_y,
+                   double* body_sums, void* stream);
+
+/* Solve for psi on every variant (sections "Boundary Conditions" to Appendix A):
+   Dirichlet sides carry psi = U*y, each body one unknown constant.
+   dev_psi: optional device output [total nodes] (logical order, INACTIVE nodes = 0).
+   body_psi: optional host output [total bodies], the C_i.
+   info: optional host output [n_variants].
+   Returns PF_OK if every variant reached tol, else the first failing variant's status. */
+pf_status pf_psi_solve(pf_batch* b, double U, const pf_solve_opts* opts, double* dev_psi,
+                       double* body_psi, pf_solve_info* info, void* stream);
+
+/* Device-event timing of the last pf_psi_solve on this handle. */
+pf_status pf_last_timing(const pf_batch* b, pf_timing* out);
+
+/* Surface tangential velocity on body `body` of variant v after a solve
+   (section "Velocity Field and Surface Tangential Velocity"): for every boundary edge
+   (edge of an active cell whose end nodes are distinct BODY nodes of this body),
+   u_t = (psi_c - C) / d_nc with psi_c the mean nodal psi of the cell and d_nc the
+   distance from the cell's vertex centroid to the edge line; theta_deg is the polar
+   angle of the edge midpoint about the body centre in [0, 360).  Edges in cell order
+   (row-major), then by the edge's first corner.  Host outputs of capacity `cap`;
+   *count receives the number of edges (outputs truncated to cap). */
+pf_status pf_surface_velocity(pf_batch* b, int variant, int body, double* theta_deg, double* ut,
+                              int cap, int* count, void* stream);
+
+/* Q = C_hi - C_lo and CoPFI = Q / (U (cy_hi - cy_lo)) after a solve (section "Effect of Gap Ratio"). */
+pf_status pf_copfi(const pf_batch* b, int variant, int body_lo, int body_hi, double U,
+                   double* copfi, double* q);
+
+/* Adjoint shape gradient of J (PF_OBJ_*) for body pair (lo, hi) of every variant after a
+   solve with the same U.  dev_dJdX: optional device output [total nodes][2], the gradient
+   with respect to the final node coordinates (topology held fixed); dJdc: optional host
+   output [total bodies][2], with respect to the body centres through the projection and the
+   S smoothing sweeps; J: optional host output [n_variants].  The adjoint system is solved
+   in FP64 to `tol`. */
+pf_status pf_grad(pf_batch* b, int objective, int body_lo, int body_hi, double U, double tol,
+                  double* dev_dJdX, double* dJdc, double* J, void* stream);
+
+/* Bytes of device memory held by the handle. */
+size_t pf_workspace_bytes(const pf_batch* b);
+
+const char* pf_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PFQ4_H */

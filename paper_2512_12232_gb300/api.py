@@ -1,0 +1,198 @@
+"""Python binding of the GB300 matrix-free Q4 stream-function solver.
+
+Thin layer over the C ABI (include/pfq4.h): it marshals arguments, allocates the
+caller-owned outputs as torch CUDA tensors and passes torch's current stream.
+Every step of the computation runs in the library's CUDA kernels; there is no CPU
+fallback, and loading fails loudly when the library has not been built.
+
+    mesh = mesh_build(grid, bodies, sweeps)          # section "Body-Conforming Grid Generation"
+    res = psi_solve(mesh, U=1.0, tol=1e-8)           # Appendix A, Algorithm
+    theta, ut = surface_velocity(mesh, 0, body=0)    # section "Velocity Field and ..."
+    copfi, q = copfi(mesh, 0, lo=3, hi=4, U=1.0)     # section "Effect of Gap Ratio"
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _lib as L
+from ._lib import PF_FP64, PF_MIXED, PF_OBJ_COPFI, PF_OBJ_GAP_FLOW, check
+
+__all__ = ["Mesh", "SolveResult", "mesh_build", "batch_build", "psi_solve", "apply", "surface_velocity",
+           "copfi", "grad", "PF_FP64", "PF_MIXED", "PF_OBJ_COPFI", "PF_OBJ_GAP_FLOW"]
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+@dataclass
+class SolveResult:
+    psi: torch.Tensor            # (total nodes,) float64 on the GPU, logical order per variant
+    body_psi: np.ndarray         # (total bodies,) C_i
+    info: list                   # per-variant dicts: iters, refinements, status, rel_true_residual, n_dof
+    status: int
+
+
+class Mesh:
+    """A pf_batch handle: one or more body-conforming mesh variants on the GPU."""
+
+    def __init__(self, grids, body_lists, sweeps, bc=(0, 0, 0, 0)):
+        lib = L.load()
+        nv = len(grids)
+        g = (L.pf_grid * nv)()
+        for v, gr in enumerate(grids):
+            x0, x1, y0, y1, nx, ny = gr
+            g[v] = L.pf_grid(float(x0), float(x1), float(y0), float(y1), int(nx), int(ny))
+        offs = [0]
+        flat = []
+        for bl in body_lists:
+            bl = np.asarray(bl, dtype=np.float64).reshape(-1, 3)
+            flat.extend(bl.tolist())
+            offs.append(len(flat))
+        off = (C.c_int * (nv + 1))(*offs)
+        bodies = (L.pf_body * max(1, len(flat)))(*[L.pf_body(*row) for row in flat])
+        bcs = (C.c_int * 4)(*[int(s) for s in bc])
+        h = C.c_void_p()
+        self._h = None
+        code = lib.pf_batch_build(g, off, bodies, nv, int(sweeps), bcs, _stream(), C.byref(h))
+        if code == L.PF_EMESH_INVALID:
+            self._h = h
+            self.valid = False
+        else:
+            check(code)
+            self._h = h
+            self.valid = True
+        self.n_variants = nv
+        self.grids = [tuple(gr) for gr in grids]
+        self.bodies = [np.asarray(bl, dtype=np.float64).reshape(-1, 3) for bl in body_lists]
+        self.body_offsets = offs
+        self.n_nodes = [(gr[4] + 1) * (gr[5] + 1) for gr in grids]
+        self.node_offsets = np.concatenate([[0], np.cumsum(self.n_nodes)]).astype(np.int64)
+        self.sweeps = sweeps
+        self.bc = tuple(bc)
+
+    # ------------------------------------------------------------------ handle
+    @property
+    def handle(self):
+        if self._h is None:
+            raise RuntimeError("mesh handle is closed")
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            L.load().pf_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ------------------------------------------------------------------ queries
+    def stats(self, v=0) -> dict:
+        s = L.pf_mesh_stats()
+        check(L.load().pf_mesh_stats_get(self.handle, v, C.byref(s)))
+        return {k: getattr(s, k) for k, _ in L.pf_mesh_stats._fields_}
+
+    def workspace_bytes(self) -> int:
+        return int(L.load().pf_workspace_bytes(self.handle))
+
+    def coords(self, v=0) -> torch.Tensor:
+        out = torch.empty((self.n_nodes[v], 2), dtype=torch.float64, device="cuda")
+        check(L.load().pf_mesh_coords(self.handle, v, _ptr(out), _stream()))
+        return out
+
+    def tags(self, v=0):
+        kind = torch.empty(self.n_nodes[v], dtype=torch.int8, device="cuda")
+        body = torch.empty(self.n_nodes[v], dtype=torch.int32, device="cuda")
+        check(L.load().pf_mesh_tags(self.handle, v, _ptr(kind), _ptr(body), _stream()))
+        return kind, body
+
+    def timing(self) -> dict:
+        t = L.pf_timing()
+        check(L.load().pf_last_timing(self.handle, C.byref(t)))
+        return {k: getattr(t, k) for k, _ in L.pf_timing._fields_}
+
+
+def mesh_build(grid, bodies, sweeps, bc=(0, 0, 0, 0)) -> Mesh:
+    """One variant: grid = (x0, x1, y0, y1, nx, ny), bodies = rows of (cx, cy, r)."""
+    return Mesh([grid], [bodies], sweeps, bc)
+
+
+def batch_build(cases, sweeps=None, bc=None) -> Mesh:
+    """Many variants (objects with .grid, .bodies, .sweeps, .bc) in one handle."""
+    sweeps = cases[0].sweeps if sweeps is None else sweeps
+    bc = cases[0].bc if bc is None else bc
+    return Mesh([c.grid for c in cases], [c.bodies for c in cases], sweeps, bc)
+
+
+def apply(mesh: Mesh, p: torch.Tensor, precision=PF_FP64):
+    """y = A p on nodal vectors (FREE and BODY rows), plus the collapsed body rows."""
+    p = p.to(device="cuda", dtype=torch.float64).contiguous()
+    y = torch.empty_like(p)
+    nb = mesh.body_offsets[-1]
+    sums = (C.c_double * max(1, nb))()
+    check(L.load().pf_apply(mesh.handle, int(precision), _ptr(p), _ptr(y), sums, _stream()))
+    return y, np.array(sums[:nb])
+
+
+def psi_solve(mesh: Mesh, U=1.0, tol=1e-8, precision=PF_MIXED, k_max=10_000_000, inner_tol=1e-4,
+              chunk=0, warm_start=False, want_psi=True, raise_on_failure=True) -> SolveResult:
+    opts = L.pf_solve_opts(float(tol), int(k_max), int(precision), float(inner_tol), int(chunk),
+                           int(bool(warm_start)))
+    total = int(mesh.node_offsets[-1])
+    psi = torch.empty(total, dtype=torch.float64, device="cuda") if want_psi else None
+    nb = mesh.body_offsets[-1]
+    bpsi = (C.c_double * max(1, nb))()
+    info = (L.pf_solve_info * mesh.n_variants)()
+    code = L.load().pf_psi_solve(mesh.handle, float(U), C.byref(opts), _ptr(psi), bpsi, info, _stream())
+    if raise_on_failure:
+        check(code)
+    infos = [{k: getattr(i, k) for k, _ in L.pf_solve_info._fields_} for i in info]
+    return SolveResult(psi, np.array(bpsi[:nb]), infos, code)
+
+
+def surface_velocity(mesh: Mesh, v=0, body=0):
+    """(theta_deg, u_t) on the boundary edges of one body after a solve."""
+    cnt = C.c_int()
+    check(L.load().pf_surface_velocity(mesh.handle, v, body, None, None, 0, C.byref(cnt), _stream()))
+    n = cnt.value
+    th = (C.c_double * max(1, n))()
+    ut = (C.c_double * max(1, n))()
+    check(L.load().pf_surface_velocity(mesh.handle, v, body, th, ut, n, C.byref(cnt), _stream()))
+    return np.array(th[:n]), np.array(ut[:n])
+
+
+def copfi(mesh: Mesh, v=0, lo=3, hi=4, U=1.0):
+    """(CoPFI, Q) = ((C_hi - C_lo) / (U (cy_hi - cy_lo)), C_hi - C_lo) after a solve."""
+    c = C.c_double()
+    q = C.c_double()
+    check(L.load().pf_copfi(mesh.handle, v, lo, hi, float(U), C.byref(c), C.byref(q)))
+    return c.value, q.value
+
+
+def grad(mesh: Mesh, objective=PF_OBJ_COPFI, lo=3, hi=4, U=1.0, tol=1e-12, want_dX=True):
+    """Adjoint shape gradient after a solve: (dJ/dX (nodes, 2) tensor, dJ/dc (bodies, 2), J per variant)."""
+    total = int(mesh.node_offsets[-1])
+    dX = torch.empty((total, 2), dtype=torch.float64, device="cuda") if want_dX else None
+    nb = mesh.body_offsets[-1]
+    dc = (C.c_double * max(1, 2 * nb))()
+    J = (C.c_double * mesh.n_variants)()
+    check(L.load().pf_grad(mesh.handle, int(objective), int(lo), int(hi), float(U), float(tol), _ptr(dX), dc, J,
+                           _stream()))
+    return dX, np.array(dc[:2 * nb]).reshape(nb, 2), np.array(J[:])

@@ -1,0 +1,129 @@
+// Host-side state of a pf_batch handle (one or more mesh variants) and the
+// internal entry points that the C ABI in capi.cu calls.
+#pragma once
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace pfq4 {
+
+struct HostVariant {
+  pf_grid g;
+  double hx, hy;
+  int P;
+  long long base, V;
+  int nb, body0;
+  int tiles_x, tiles_y;
+  long long tile0;             // first tile of the variant in the tile list
+  pf_mesh_stats stats;
+};
+
+struct Error {                 // thrown inside the library, converted to pf_status at the ABI
+  pf_status code;
+  std::string msg;
+};
+
+struct Batch;
+void* dev_alloc(Batch& b, size_t bytes);
+void dev_free_all(Batch& b);
+
+struct Batch {
+  int device = 0;
+  cudaStream_t stream = nullptr;     // stream of the current call
+  int nv = 0, B = 0, sweeps = 0;
+  int bc[4] = {0, 0, 0, 0};
+  long long Vtot = 0;
+  std::vector<HostVariant> hv;
+  std::vector<pf_body> bodies;
+  std::vector<int> body_off;         // [nv+1]
+  std::vector<int> h_body_ptr;       // [B+1]
+  std::vector<int> h_edge_ptr;       // [B+1]
+  bool valid = false;                // det J > 0 everywhere
+
+  // device mesh
+  DevVariant* d_var = nullptr;
+  pf_body* d_bodies = nullptr;
+  int* d_body_var = nullptr;         // [B] variant of each global body
+  int4* d_bbox = nullptr;            // [B] node box (i_lo, i_hi, j_lo, j_hi)
+  uint8_t* tag = nullptr;
+  int* bid = nullptr;                // inside-body index (local) or -1
+  double* X = nullptr;               // [2][Vtot] final coordinates
+  double* K64 = nullptr;             // [6][Vtot]
+  float* K32 = nullptr;              // [6][Vtot]
+  int* body_ptr = nullptr;           // [B+1]
+  long long* body_nodes = nullptr;
+  int* edge_ptr = nullptr;           // [B+1]
+  long long* edge_rec = nullptr;     // (cell padded index << 2) | first corner
+  long long* d_stats_i = nullptr;    // [nv][6] integer counts
+  double* d_detmin = nullptr;        // [nv]
+  long long* d_lbase = nullptr;      // [nv+1] logical node offsets of the variants
+  double* d_bsum = nullptr;          // [B] scratch for collapsed body rows
+
+  // tiles and persistent schedule
+  long long T = 0;
+  int2* tile_ij = nullptr;           // [T]
+  int* tile_var = nullptr;           // [T]
+  int G = 0, S = 0;
+  int *cta_seg = nullptr, *seg_var = nullptr, *seg_t0 = nullptr, *seg_t1 = nullptr;
+  int *var_seg0 = nullptr, *var_seg1 = nullptr, *counter = nullptr;
+  double* partial = nullptr;
+  Sched sched{};
+
+  // solver state
+  VarState* state = nullptr;         // [nv]
+  SolveParams* params = nullptr;
+  int* n_done = nullptr;             // device counter of finished variants
+  double* x64 = nullptr;             // [Vtot] solution (Dirichlet values in place)
+  double* w64 = nullptr;             // [Vtot] FP64 scratch (body-node rows of the true residual)
+  double *r64 = nullptr, *p64 = nullptr, *q64 = nullptr;                 // FP64-mode CG vectors
+  float *x32 = nullptr, *r32 = nullptr, *p32 = nullptr, *q32 = nullptr;  // mixed-mode inner vectors
+  double* sb64 = nullptr;            // [4][B] FP64 body values x, r, p, q (x = the solution C_k)
+  float* sb32 = nullptr;             // [4][B] FP32 inner body values x, r, p, q
+  double* sbr64 = nullptr;           // [B] FP64 true-residual body rows
+  bool solved = false;
+  double lastU = 0.0;
+  int last_precision = -1;
+  std::vector<double> bnorm2_unit;   // ||b||^2 at U = 1, per variant (filled by the first solve)
+
+  // graphs (one per precision) and timing events
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  cudaStream_t graph_stream[2] = {nullptr, nullptr};
+  int graph_chunk[2] = {0, 0};
+  cudaEvent_t ev[6] = {};
+  pf_timing timing{};
+  double cg_bytes_per_node[2] = {0, 0};
+
+  std::vector<std::pair<void*, size_t>> allocs;
+  size_t bytes = 0;
+  void* alloc_ctx = nullptr;
+  pf_alloc_fn alloc_fn = nullptr;
+  pf_free_fn free_fn = nullptr;
+};
+
+void check_cuda(cudaError_t e, const char* what);
+#define PF_CUDA(call) ::pfq4::check_cuda((call), #call)
+
+// mesh.cu
+void build_batch(Batch& b, const pf_grid* grids, const int* body_offsets, const pf_body* bodies,
+                 int nv, int sweeps, const int bc[4]);
+void export_coords(Batch& b, int v, double* dev_xy);
+void export_tags(Batch& b, int v, int8_t* kind, int32_t* body);
+
+// solver.cu
+void make_schedule(Batch& b);
+void ensure_solver_memory(Batch& b, int precision);
+void apply_operator(Batch& b, int precision, const double* dev_p, double* dev_y, double* body_sums);
+pf_status psi_solve(Batch& b, double U, const pf_solve_opts& o, double* dev_psi, double* body_psi,
+                    pf_solve_info* info);
+void export_psi(Batch& b, double* dev_psi);
+void body_values(Batch& b, std::vector<double>& C);
+
+// post.cu
+int surface_velocity(Batch& b, int v, int body, double* theta, double* ut, int cap);
+
+// grad.cu
+pf_status shape_gradient(Batch& b, int obj, int lo, int hi, double U, double tol, double* dev_dJdX,
+                         double* dJdc, double* J);
+
+}  // namespace pfq4

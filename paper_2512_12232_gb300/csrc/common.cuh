@@ -1,0 +1,241 @@
+// Shared definitions of the GB300 matrix-free Q4 solver library.
+//
+// Data layout (HBM): every variant's nodes live in padded row-major planes,
+// node (i, j) at base + j*P + i with the row pitch P = round_up(nx+1, 32) so that
+// every row starts on a 128-byte boundary.  Cells are stored at the index of their
+// corner 0 (i, j).  Columns nx+1 .. P-1 are padding (tag INACTIVE, values 0) and are
+// never read as neighbours: tile loaders bounds-check against (nx, ny).
+//
+// One tile = 32 x 8 nodes = one 256-thread CTA pass.  Tiles of all variants form one
+// list (variant-major, row-major inside a variant).  Solver kernels run a persistent
+// grid: CTA b owns a contiguous range of the tile list, cut into "segments" at
+// variant boundaries; per-segment partial reductions are summed in a fixed order by
+// the last CTA to finish a variant, so every reduction is deterministic.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/pfq4.h"
+
+namespace pfq4 {
+
+constexpr int TX = 32;
+constexpr int TY = 8;
+constexpr int NT = TX * TY;          // threads per CTA
+constexpr int SW = TX + 2;           // shared tile row width with halo
+constexpr int NHALO = 2 * SW + 2 * TY;
+constexpr int MAXB = 64;             // bodies per variant
+
+// node tag byte
+constexpr uint8_t KIND_MASK = 3;
+constexpr uint8_t K_FREE = PF_NODE_FREE, K_DIR = PF_NODE_DIRICHLET, K_BODY = PF_NODE_BODY,
+                  K_INACT = PF_NODE_INACTIVE;
+constexpr uint8_t CELL_ACTIVE = 4;   // cell (i, j) whose corner 0 is this node is active
+constexpr uint8_t CELL_GENERAL = 8;  // ... and has a displaced corner: stored K_e is used
+constexpr uint8_t DISPLACED = 16;    // node moved by the mesh generator (d != 0)
+constexpr uint8_t RING = 32;         // node on the outer boundary of the box
+
+// solver phases (per variant)
+constexpr int PH_CG = 0, PH_RESID = 1, PH_DONE = 2;
+
+struct DevVariant {
+  double x0, y0, hx, hy;
+  long long base;      // first padded node index of the variant
+  int nx, ny, P, nb;   // grid, pitch, bodies
+  int body0;           // first global body index
+  int tiles_x, tiles_y;
+  int pad_;
+  double kr64[6];      // K_e of an undisplaced hx-by-hy cell: K01 K02 K03 K12 K13 K23
+  float kr32[6];
+};
+
+struct VarState {
+  double alpha, beta;          // scalars of the next fused CG launch
+  double gamma, pi, rho, mu;   // last dots  r.r, p.Ap, r.Ap, Ap.Ap
+  double gamma_start;          // r.r at the start of the current inner solve
+  double bnorm2;               // ||b||^2 (at U of the solve)
+  double rr64;                 // last true residual ||b - A u||^2 (FP64)
+  double thr_abs2;             // inner stop: gamma <= max(thr_rel * gamma_start, thr_abs2)
+  double thr_rel;
+  long long iters;             // all CG iterations of the solve
+  long long inner_iters;       // iterations of the current inner solve
+  int phase;                   // PH_CG / PH_RESID / PH_DONE
+  int status;                  // pf_status
+  int n_resid;                 // true-residual evaluations
+  int capped;                  // k_max reached
+};
+
+struct SolveParams {
+  double tol2;                 // tol^2
+  double inner_rel2;           // inner_tol^2 (mixed) or 0
+  long long k_max;
+  int mixed;
+  int pad_;
+};
+
+struct Sched {                 // persistent tile schedule
+  const int* cta_seg;          // [G+1] first segment of each CTA
+  const int* seg_var;          // [S]
+  const int* seg_t0;           // [S] first tile (global tile list)
+  const int* seg_t1;           // [S] one past last tile
+  const int2* tile_ij;         // [T] (i0, j0)
+  const int* var_seg0;         // [nv] first segment of the variant
+  const int* var_seg1;         // [nv]
+  double* partial;             // [S][4]
+  int* counter;                // [nv] finished segments in the current launch
+  int n_cta;
+};
+
+struct MeshDev {
+  const DevVariant* var;
+  const uint8_t* tag;
+  const int* bid;              // body index local to the variant (BODY nodes), else -1
+  const int* body_ptr;         // [B+1] into body_nodes
+  const long long* body_nodes; // padded node indices, per body in row-major order
+  const double* K64;           // [6][Vtot]
+  const float* K32;            // [6][Vtot]
+  long long Vtot;
+};
+
+// ---------------------------------------------------------------- reductions
+// Compensated two-float accumulation (Knuth TwoSum + exact FMA products): the
+// FP32 path accumulates dot products with ~2^-44 relative error per operation and
+// converts to FP64 once per warp, so no FP64 instruction is issued per node.
+struct FF { float hi, lo; };
+
+__device__ __forceinline__ void ff_add_prod(FF& a, float x, float y) {
+  float p = x * y;
+  float e = fmaf(x, y, -p);           // p + e == x*y exactly
+  float s = a.hi + p;
+  float bb = s - a.hi;
+  float err = (a.hi - (s - bb)) + (p - bb);
+  a.hi = s;
+  a.lo += err + e;
+}
+
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+  float s = a.hi + b.hi;
+  float bb = s - a.hi;
+  float err = (a.hi - (s - bb)) + (b.hi - bb);
+  err += a.lo + b.lo;
+  float h = s + err;
+  return FF{h, err - (h - s)};
+}
+
+template <typename T> struct Acc;
+template <> struct Acc<double> {
+  double v[4];
+  __device__ void zero() { v[0] = v[1] = v[2] = v[3] = 0.0; }
+  __device__ void add(int k, double x, double y) { v[k] = fma(x, y, v[k]); }
+  // warp-reduce, lane 0 returns the sums
+  __device__ void warp_reduce(double out[4]) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      double s = v[k];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      out[k] = s;
+    }
+  }
+};
+template <> struct Acc<float> {
+  FF v[4];
+  __device__ void zero() {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = FF{0.f, 0.f};
+  }
+  __device__ void add(int k, float x, float y) { ff_add_prod(v[k], x, y); }
+  __device__ void warp_reduce(double out[4]) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      FF s = v[k];
+      s = ff_add(s, FF{0.f, 0.f});   // renormalise
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        FF t{__shfl_xor_sync(0xffffffffu, s.hi, o), __shfl_xor_sync(0xffffffffu, s.lo, o)};
+        s = ff_add(s, t);
+      }
+      out[k] = (double)s.hi + (double)s.lo;
+    }
+  }
+};
+
+// Block-wide fixed-order sum of a double; all threads get the result.
+__device__ __forceinline__ double block_sum(double x, double* scratch /* >= NT/32 */) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  __syncthreads();
+  if (lane == 0) scratch[w] = x;
+  __syncthreads();
+  double s = 0.0;
+  for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += scratch[k];
+  __syncthreads();
+  return s;
+}
+
+__device__ __forceinline__ int linear_tid() { return threadIdx.y * TX + threadIdx.x; }
+
+// Halo position h in [0, NHALO) -> shared-tile coordinates (li, lj).
+__device__ __forceinline__ void halo_pos(int h, int& li, int& lj) {
+  if (h < SW) { li = h; lj = 0; }
+  else if (h < 2 * SW) { li = h - SW; lj = TY + 1; }
+  else if (h < 2 * SW + TY) { li = 0; lj = 1 + (h - 2 * SW); }
+  else { li = TX + 1; lj = 1 + (h - 2 * SW - TY); }
+}
+
+// Row of the matrix-free Q4 operator at the node in the centre of shared tile
+// position (li, lj): y = sum over the four cells around the node of
+// sum_{b != a} K_e[a,b] (p_b - p_a), which equals (K_e p_e)_a because every row of
+// K_e sums to zero.  Inactive cells contribute nothing.  Cell coefficients come
+// from the stored planes for displaced cells and from `kr` (closed-form rectangle)
+// otherwise.  n: padded node index, P: pitch, K: [6][plane].
+template <typename T>
+__device__ __forceinline__ T q4_row(const T (*ps)[SW], const uint8_t (*ts)[SW], int li, int lj,
+                                    long long n, int P, const T* __restrict__ K, long long plane,
+                                    const T* kr) {
+  const T pc = ps[lj][li];
+  const T dE = ps[lj][li + 1] - pc, dW = ps[lj][li - 1] - pc;
+  const T dN = ps[lj + 1][li] - pc, dS = ps[lj - 1][li] - pc;
+  const T dNE = ps[lj + 1][li + 1] - pc, dNW = ps[lj + 1][li - 1] - pc;
+  const T dSE = ps[lj - 1][li + 1] - pc, dSW = ps[lj - 1][li - 1] - pc;
+  T y = T(0);
+  uint8_t t = ts[lj][li];                      // cell (i, j): node is corner 0
+  if (t & CELL_ACTIVE) {
+    T k01 = kr[0], k02 = kr[1], k03 = kr[2];
+    if (t & CELL_GENERAL) {
+      k01 = __ldg(K + n); k02 = __ldg(K + plane + n); k03 = __ldg(K + 2 * plane + n);
+    }
+    y += k01 * dE + k02 * dNE + k03 * dN;
+  }
+  t = ts[lj][li - 1];                          // cell (i-1, j): corner 1
+  if (t & CELL_ACTIVE) {
+    T k01 = kr[0], k12 = kr[3], k13 = kr[4];
+    if (t & CELL_GENERAL) {
+      const long long c = n - 1;
+      k01 = __ldg(K + c); k12 = __ldg(K + 3 * plane + c); k13 = __ldg(K + 4 * plane + c);
+    }
+    y += k01 * dW + k12 * dN + k13 * dNW;
+  }
+  t = ts[lj - 1][li - 1];                      // cell (i-1, j-1): corner 2
+  if (t & CELL_ACTIVE) {
+    T k02 = kr[1], k12 = kr[3], k23 = kr[5];
+    if (t & CELL_GENERAL) {
+      const long long c = n - P - 1;
+      k02 = __ldg(K + plane + c); k12 = __ldg(K + 3 * plane + c); k23 = __ldg(K + 5 * plane + c);
+    }
+    y += k02 * dSW + k12 * dS + k23 * dW;
+  }
+  t = ts[lj - 1][li];                          // cell (i, j-1): corner 3
+  if (t & CELL_ACTIVE) {
+    T k03 = kr[2], k13 = kr[4], k23 = kr[5];
+    if (t & CELL_GENERAL) {
+      const long long c = n - P;
+      k03 = __ldg(K + 2 * plane + c); k13 = __ldg(K + 4 * plane + c); k23 = __ldg(K + 5 * plane + c);
+    }
+    y += k03 * dS + k13 * dSE + k23 * dE;
+  }
+  return y;
+}
+
+}  // namespace pfq4

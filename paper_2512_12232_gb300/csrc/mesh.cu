@@ -1,0 +1,582 @@
+// Body-conforming mesh generation on the GPU (section "Body-Conforming Grid
+// Generation"): background grid, inside test, radial projection of the nodes just
+// inside each body, S Jacobi sweeps of the displacement, x = x_grid + d; then the
+// Q4 element matrices (section "Weak formulation", 2x2 Gauss) and the per-body node
+// and boundary-edge lists used by the constraint collapse and the post-processing.
+//
+// The mesh rules are evaluated with explicitly rounded FP64 intrinsics
+// (__dadd_rn, __dmul_rn, __ddiv_rn, __dsqrt_rn), never contracted into FMAs, so the
+// classification and the coordinates are reproducible bit for bit by any IEEE FP64
+// implementation of the same operation sequence.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "batch.h"
+
+namespace pfq4 {
+
+namespace {
+
+__device__ __forceinline__ double grid_x(const DevVariant& V, int i) {
+  return __dadd_rn(V.x0, __dmul_rn((double)i, V.hx));
+}
+__device__ __forceinline__ double grid_y(const DevVariant& V, int j) {
+  return __dadd_rn(V.y0, __dmul_rn((double)j, V.hy));
+}
+
+struct TileCtx {
+  int v, i, j;
+  long long n;
+  bool in;
+};
+
+__device__ __forceinline__ TileCtx tile_ctx(const DevVariant* var, const int* tile_var, const int2* tile_ij) {
+  TileCtx c;
+  const long long t = blockIdx.x;
+  c.v = tile_var[t];
+  const int2 ij = tile_ij[t];
+  const DevVariant& V = var[c.v];
+  c.i = ij.x + threadIdx.x;
+  c.j = ij.y + threadIdx.y;
+  c.in = (c.i <= V.nx) && (c.j <= V.ny);
+  c.n = V.base + (long long)c.j * V.P + c.i;
+  return c;
+}
+
+// 1. inside test: bid[n] = body k (local) if (x-cx)^2 + (y-cy)^2 <= r^2, else -1.
+__global__ void k_classify(const DevVariant* var, const int* tile_var, const int2* tile_ij,
+                           const pf_body* bodies, int* bid, int* err) {
+  TileCtx c = tile_ctx(var, tile_var, tile_ij);
+  const DevVariant& V = var[c.v];
+  if (!c.in) return;
+  const double x = grid_x(V, c.i), y = grid_y(V, c.j);
+  int ib = -1;
+  for (int k = 0; k < V.nb; ++k) {
+    const pf_body B = bodies[V.body0 + k];
+    const double dx = __dsub_rn(x, B.cx), dy = __dsub_rn(y, B.cy);
+    const double d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+    if (d2 <= __dmul_rn(B.r, B.r)) {
+      if (ib >= 0) atomicOr(err, 1);
+      ib = k;
+    }
+  }
+  bid[c.n] = ib;
+}
+
+// 2. node kinds, cell activity, ring flag, projection displacement d0.
+__global__ void k_kinds(const DevVariant* var, const int* tile_var, const int2* tile_ij,
+                        const pf_body* bodies, const int* bid, uint8_t* tag, double2* d0,
+                        int bc0, int bc1, int bc2, int bc3, int* err) {
+  TileCtx c = tile_ctx(var, tile_var, tile_ij);
+  const DevVariant& V = var[c.v];
+  if (!c.in) return;
+  const int i = c.i, j = c.j, nx = V.nx, ny = V.ny, P = V.P;
+  const long long n = c.n;
+  auto outside = [&](int ii, int jj) -> bool { return bid[V.base + (long long)jj * P + ii] < 0; };
+  auto cell_active = [&](int ci, int cj) -> bool {
+    if (ci < 0 || cj < 0 || ci >= nx || cj >= ny) return false;
+    return outside(ci, cj) || outside(ci + 1, cj) || outside(ci, cj + 1) || outside(ci + 1, cj + 1);
+  };
+  uint8_t t = 0;
+  const int ib = bid[n];
+  const bool ring = (i == 0) || (i == nx) || (j == 0) || (j == ny);
+  if (ring) t |= RING;
+  if (cell_active(i, j)) t |= CELL_ACTIVE;
+  double2 d = make_double2(0.0, 0.0);
+  if (ib < 0) {
+    const bool dir = (i == 0 && bc0 == PF_BC_DIRICHLET_UY) || (i == nx && bc1 == PF_BC_DIRICHLET_UY) ||
+                     (j == 0 && bc2 == PF_BC_DIRICHLET_UY) || (j == ny && bc3 == PF_BC_DIRICHLET_UY);
+    t |= dir ? K_DIR : K_FREE;
+  } else {
+    const bool touch = cell_active(i - 1, j - 1) || cell_active(i, j - 1) || cell_active(i - 1, j) ||
+                       cell_active(i, j);
+    if (touch) {
+      t |= K_BODY;
+      const pf_body B = bodies[V.body0 + ib];
+      const double xg = grid_x(V, i), yg = grid_y(V, j);
+      const double ex = __dsub_rn(xg, B.cx), ey = __dsub_rn(yg, B.cy);
+      const double rho = __dsqrt_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)));
+      if (rho == 0.0) atomicOr(err, 2);
+      const double xb = __dadd_rn(B.cx, __ddiv_rn(__dmul_rn(B.r, ex), rho));
+      const double yb = __dadd_rn(B.cy, __ddiv_rn(__dmul_rn(B.r, ey), rho));
+      d = make_double2(__dsub_rn(xb, xg), __dsub_rn(yb, yg));
+    } else {
+      t |= K_INACT;
+    }
+  }
+  tag[n] = t;
+  d0[n] = d;
+}
+
+// 3. one Jacobi sweep: nodes outside every body and off the outer ring take the
+//    average of their four neighbours, summed W, E, S, N, divided by 4.
+__global__ void k_jacobi(const DevVariant* var, const int* tile_var, const int2* tile_ij,
+                         const int* bid, const uint8_t* tag, const double2* __restrict__ src,
+                         double2* __restrict__ dst) {
+  TileCtx c = tile_ctx(var, tile_var, tile_ij);
+  const DevVariant& V = var[c.v];
+  if (!c.in) return;
+  const long long n = c.n;
+  double2 out = src[n];
+  if (bid[n] < 0 && !(tag[n] & RING)) {
+    const double2 w = src[n - 1], e = src[n + 1], s = src[n - V.P], nn = src[n + V.P];
+    const double sx = __dadd_rn(__dadd_rn(__dadd_rn(w.x, e.x), s.x), nn.x);
+    const double sy = __dadd_rn(__dadd_rn(__dadd_rn(w.y, e.y), s.y), nn.y);
+    out = make_double2(__ddiv_rn(sx, 4.0), __ddiv_rn(sy, 4.0));
+  }
+  dst[n] = out;
+}
+
+// 4. final coordinates x = x_grid + d and the DISPLACED flag.
+__global__ void k_finalize(const DevVariant* var, const int* tile_var, const int2* tile_ij,
+                           const double2* d, uint8_t* tag, double* X, long long Vtot) {
+  TileCtx c = tile_ctx(var, tile_var, tile_ij);
+  const DevVariant& V = var[c.v];
+  if (!c.in) return;
+  const double2 dd = d[c.n];
+  X[c.n] = __dadd_rn(grid_x(V, c.i), dd.x);
+  X[Vtot + c.n] = __dadd_rn(grid_y(V, c.j), dd.y);
+  if (dd.x != 0.0 || dd.y != 0.0) tag[c.n] |= DISPLACED;
+}
+
+__device__ void atomic_min_double(double* addr, double val) {
+  unsigned long long* a = (unsigned long long*)addr;
+  unsigned long long old = *a, assumed;
+  while (val < __longlong_as_double((long long)old)) {
+    assumed = old;
+    old = atomicCAS(a, assumed, (unsigned long long)__double_as_longlong(val));
+    if (old == assumed) break;
+  }
+}
+
+// 5. Q4 element matrices of the active cells (2x2 Gauss), FP64 and FP32 copies,
+//    CELL_GENERAL flag, per-variant counts and min det J.
+__global__ void k_stiffness(const DevVariant* var, const int* tile_var, const int2* tile_ij,
+                            uint8_t* tag, const double* X, long long Vtot, double* K64, float* K32,
+                            long long* stats_i, double* detmin) {
+  TileCtx c = tile_ctx(var, tile_var, tile_ij);
+  const DevVariant& V = var[c.v];
+  __shared__ long long cnt[5];
+  __shared__ double dmin;
+  const int tid = linear_tid();
+  if (tid < 5) cnt[tid] = 0;
+  if (tid == 0) dmin = 1e300;
+  __syncthreads();
+  if (c.in) {
+    const long long n = c.n;
+    const uint8_t t = tag[n];
+    const uint8_t kind = t & KIND_MASK;
+    if (kind == K_FREE) atomicAdd((unsigned long long*)&cnt[0], 1ull);
+    if (kind == K_BODY) atomicAdd((unsigned long long*)&cnt[1], 1ull);
+    if (kind == K_INACT) atomicAdd((unsigned long long*)&cnt[2], 1ull);
+    if (t & CELL_ACTIVE) {
+      atomicAdd((unsigned long long*)&cnt[3], 1ull);
+      const long long idx[4] = {n, n + 1, n + 1 + V.P, n + V.P};
+      double x[4], y[4];
+      bool disp = false;
+      for (int a = 0; a < 4; ++a) {
+        x[a] = X[idx[a]];
+        y[a] = X[Vtot + idx[a]];
+        disp |= (tag[idx[a]] & DISPLACED) != 0;
+      }
+      const double g = 0.57735026918962576451;   // 1/sqrt(3)
+      const double xi_a[4] = {-1, 1, 1, -1}, eta_a[4] = {-1, -1, 1, 1};
+      const double gx[4] = {-g, g, g, -g}, gy[4] = {-g, -g, g, g};
+      double K[4][4] = {};
+      double dm = 1e300;
+      for (int q = 0; q < 4; ++q) {
+        double dxi[4], deta[4];
+        for (int a = 0; a < 4; ++a) {
+          dxi[a] = 0.25 * xi_a[a] * (1.0 + eta_a[a] * gy[q]);
+          deta[a] = 0.25 * eta_a[a] * (1.0 + xi_a[a] * gx[q]);
+        }
+        double j00 = 0, j01 = 0, j10 = 0, j11 = 0;
+        for (int a = 0; a < 4; ++a) {
+          j00 += dxi[a] * x[a]; j01 += dxi[a] * y[a];
+          j10 += deta[a] * x[a]; j11 += deta[a] * y[a];
+        }
+        const double det = j00 * j11 - j01 * j10;
+        dm = fmin(dm, det);
+        const double inv = 1.0 / det;
+        double bx[4], by[4];
+        for (int a = 0; a < 4; ++a) {
+          bx[a] = (j11 * dxi[a] - j01 * deta[a]) * inv;
+          by[a] = (-j10 * dxi[a] + j00 * deta[a]) * inv;
+        }
+        for (int a = 0; a < 4; ++a)
+          for (int b2 = a + 1; b2 < 4; ++b2) K[a][b2] += det * (bx[a] * bx[b2] + by[a] * by[b2]);
+      }
+      const double k6[6] = {K[0][1], K[0][2], K[0][3], K[1][2], K[1][3], K[2][3]};
+      for (int m = 0; m < 6; ++m) {
+        K64[m * Vtot + n] = k6[m];
+        K32[m * Vtot + n] = (float)k6[m];
+      }
+      if (disp) {
+        tag[n] = t | CELL_GENERAL;
+        atomicAdd((unsigned long long*)&cnt[4], 1ull);
+      }
+      atomic_min_double(&dmin, dm);
+    }
+  }
+  __syncthreads();
+  if (tid < 5 && cnt[tid]) atomicAdd((unsigned long long*)&stats_i[c.v * 6 + tid], (unsigned long long)cnt[tid]);
+  if (tid == 0 && dmin < 1e300) atomic_min_double(&detmin[c.v], dmin);
+}
+
+// Block-wide exclusive scan of one int per thread (256 threads, 1-D linear id).
+__device__ int block_exscan(int x, int* total, int* sh /* >= 9 */) {
+  const int tid = linear_tid(), lane = tid & 31, w = tid >> 5;
+  int incl = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  __syncthreads();
+  if (lane == 31) sh[w] = incl;
+  __syncthreads();
+  if (tid == 0) {
+    int s = 0;
+    for (int k = 0; k < NT / 32; ++k) { int t = sh[k]; sh[k] = s; s += t; }
+    sh[NT / 32] = s;
+  }
+  __syncthreads();
+  const int r = sh[w] + incl - x;
+  *total = sh[NT / 32];
+  __syncthreads();
+  return r;
+}
+
+// 6. per-body node lists (row-major inside the body's node box).  pass 0 counts,
+//    pass 1 writes.  One CTA per global body.
+__global__ void k_body_nodes(const DevVariant* var, const int* body_var, const int4* bbox,
+                             const uint8_t* tag, const int* bid, int* count, const int* ptr,
+                             long long* out, int pass) {
+  __shared__ int sh[NT / 32 + 1];
+  const int gb = blockIdx.x;
+  const int v = body_var[gb];
+  const DevVariant& V = var[v];
+  const int k = gb - V.body0;
+  const int4 bx = bbox[gb];
+  const int w = bx.y - bx.x + 1, h = bx.w - bx.z + 1;
+  const long long total = (long long)w * h;
+  int run = 0;
+  for (long long s = 0; s < total; s += NT) {
+    const long long q = s + linear_tid();
+    int flag = 0;
+    long long n = 0;
+    if (q < total) {
+      const int i = bx.x + (int)(q % w), j = bx.z + (int)(q / w);
+      n = V.base + (long long)j * V.P + i;
+      flag = ((tag[n] & KIND_MASK) == K_BODY) && bid[n] == k;
+    }
+    int tot;
+    const int pos = block_exscan(flag, &tot, sh);
+    if (pass == 1 && flag) out[ptr[gb] + run + pos] = n;
+    run += tot;
+  }
+  if (pass == 0 && linear_tid() == 0) count[gb] = run;
+}
+
+// 7. per-body boundary edges: edges (corner a -> a+1) of active cells whose two end
+//    nodes are BODY nodes of this body at distinct positions.  Cells row-major in the
+//    body's box, edges by first corner.  pass 0 counts, pass 1 writes.
+__global__ void k_body_edges(const DevVariant* var, const int* body_var, const int4* bbox,
+                             const uint8_t* tag, const int* bid, const double* X, long long Vtot,
+                             int* count, const int* ptr, long long* out, int pass) {
+  __shared__ int sh[NT / 32 + 1];
+  const int gb = blockIdx.x;
+  const int v = body_var[gb];
+  const DevVariant& V = var[v];
+  const int k = gb - V.body0;
+  const int4 bx = bbox[gb];
+  const int ci0 = bx.x, ci1 = min(bx.y, V.nx - 1), cj0 = bx.z, cj1 = min(bx.w, V.ny - 1);
+  const int w = ci1 - ci0 + 1, h = cj1 - cj0 + 1;
+  const long long total = (w > 0 && h > 0) ? (long long)w * h : 0;
+  int run = 0;
+  for (long long s = 0; s < total; s += NT) {
+    const long long q = s + linear_tid();
+    int cnt = 0;
+    unsigned mask = 0;
+    long long n = 0;
+    if (q < total) {
+      const int i = ci0 + (int)(q % w), j = cj0 + (int)(q / w);
+      n = V.base + (long long)j * V.P + i;
+      if (tag[n] & CELL_ACTIVE) {
+        const long long idx[4] = {n, n + 1, n + 1 + V.P, n + V.P};
+        bool isb[4];
+        for (int a = 0; a < 4; ++a) isb[a] = ((tag[idx[a]] & KIND_MASK) == K_BODY) && bid[idx[a]] == k;
+        for (int a = 0; a < 4; ++a) {
+          const int b2 = (a + 1) & 3;
+          if (isb[a] && isb[b2] &&
+              (X[idx[a]] != X[idx[b2]] || X[Vtot + idx[a]] != X[Vtot + idx[b2]])) {
+            mask |= 1u << a;
+            ++cnt;
+          }
+        }
+      }
+    }
+    int tot;
+    const int pos = block_exscan(cnt, &tot, sh);
+    if (pass == 1 && cnt) {
+      int o = ptr[gb] + run + pos;
+      for (int a = 0; a < 4; ++a)
+        if (mask & (1u << a)) out[o++] = (n << 2) | a;
+    }
+    run += tot;
+  }
+  if (pass == 0 && linear_tid() == 0) count[gb] = run;
+}
+
+// export kernels: padded -> logical order
+__global__ void k_export_coords(const DevVariant* var, int v, const double* X, long long Vtot,
+                                double* xy) {
+  const DevVariant& V = var[v];
+  const long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long N = (long long)(V.nx + 1) * (V.ny + 1);
+  if (m >= N) return;
+  const int i = (int)(m % (V.nx + 1)), j = (int)(m / (V.nx + 1));
+  const long long n = V.base + (long long)j * V.P + i;
+  xy[2 * m] = X[n];
+  xy[2 * m + 1] = X[Vtot + n];
+}
+
+__global__ void k_export_tags(const DevVariant* var, int v, const uint8_t* tag, const int* bid,
+                              int8_t* kind, int32_t* body) {
+  const DevVariant& V = var[v];
+  const long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long N = (long long)(V.nx + 1) * (V.ny + 1);
+  if (m >= N) return;
+  const int i = (int)(m % (V.nx + 1)), j = (int)(m / (V.nx + 1));
+  const long long n = V.base + (long long)j * V.P + i;
+  if (kind) kind[m] = (int8_t)(tag[n] & KIND_MASK);
+  if (body) body[m] = bid[n];
+}
+
+}  // namespace
+
+static void rect_stiffness(double hx, double hy, double k[6]) {
+  // closed form of K_e for an axis-aligned hx x hy rectangle, off-diagonals
+  const double b = hy / hx, a = hx / hy;
+  k[0] = (-2.0 * b + a) / 6.0;   // K01
+  k[1] = (-b - a) / 6.0;         // K02
+  k[2] = (b - 2.0 * a) / 6.0;    // K03
+  k[3] = (b - 2.0 * a) / 6.0;    // K12
+  k[4] = (-b - a) / 6.0;         // K13
+  k[5] = (-2.0 * b + a) / 6.0;   // K23
+}
+
+template <typename T>
+static T* upload(Batch& b, const std::vector<T>& h) {
+  T* d = (T*)dev_alloc(b, std::max<size_t>(1, h.size()) * sizeof(T));
+  if (!h.empty()) PF_CUDA(cudaMemcpyAsync(d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, b.stream));
+  return d;
+}
+
+void build_batch(Batch& b, const pf_grid* grids, const int* body_offsets, const pf_body* bodies,
+                 int nv, int sweeps, const int bc[4]) {
+  if (nv < 1 || !grids || !body_offsets || sweeps < 0 || !bc) throw Error{PF_EINVAL, "invalid arguments"};
+  bool any_dir = false;
+  for (int s = 0; s < 4; ++s) {
+    if (bc[s] != PF_BC_DIRICHLET_UY && bc[s] != PF_BC_NATURAL) throw Error{PF_EINVAL, "invalid boundary kind"};
+    any_dir |= bc[s] == PF_BC_DIRICHLET_UY;
+    b.bc[s] = bc[s];
+  }
+  if (!any_dir) throw Error{PF_EINVAL, "at least one side must carry Dirichlet data"};
+  b.nv = nv;
+  b.sweeps = sweeps;
+  if (body_offsets[0] != 0) throw Error{PF_EINVAL, "body_offsets[0] must be 0"};
+  b.body_off.assign(body_offsets, body_offsets + nv + 1);
+  b.B = body_offsets[nv];
+  if (b.B > 0 && !bodies) throw Error{PF_EINVAL, "bodies is NULL"};
+  b.bodies.assign(bodies, bodies + b.B);
+
+  // ---- host validation and layout
+  std::vector<DevVariant> dv(nv);
+  std::vector<int2> tij;
+  std::vector<int> tvar;
+  std::vector<int4> bbox(b.B);
+  std::vector<int> body_var(b.B);
+  long long base = 0;
+  b.hv.resize(nv);
+  for (int v = 0; v < nv; ++v) {
+    const pf_grid& g = grids[v];
+    const int nb = body_offsets[v + 1] - body_offsets[v];
+    if (g.nx < 2 || g.ny < 2 || !(g.x1 > g.x0) || !(g.y1 > g.y0) || nb < 0 || nb > MAXB)
+      throw Error{PF_EINVAL, "variant " + std::to_string(v) + ": invalid grid or body count"};
+    if ((long long)(g.nx + 1) * (g.ny + 1) > (1LL << 40)) throw Error{PF_EINVAL, "grid too large"};
+    HostVariant& H = b.hv[v];
+    H.g = g;
+    H.hx = (g.x1 - g.x0) / g.nx;
+    H.hy = (g.y1 - g.y0) / g.ny;
+    H.P = ((g.nx + 1 + 31) / 32) * 32;
+    H.V = (long long)(g.ny + 1) * H.P;
+    H.base = base;
+    base += H.V;
+    H.nb = nb;
+    H.body0 = body_offsets[v];
+    H.tiles_x = (g.nx + 1 + TX - 1) / TX;
+    H.tiles_y = (g.ny + 1 + TY - 1) / TY;
+    H.tile0 = (long long)tij.size();
+    for (int ty = 0; ty < H.tiles_y; ++ty)
+      for (int tx = 0; tx < H.tiles_x; ++tx) {
+        tij.push_back(make_int2(tx * TX, ty * TY));
+        tvar.push_back(v);
+      }
+    for (int k = 0; k < nb; ++k) {
+      const pf_body& B = b.bodies[H.body0 + k];
+      if (!(B.r > 0)) throw Error{PF_EINVAL, "variant " + std::to_string(v) + ": body radius must be positive"};
+      if (B.cx - B.r < g.x0 + 2 * H.hx || B.cx + B.r > g.x1 - 2 * H.hx || B.cy - B.r < g.y0 + 2 * H.hy ||
+          B.cy + B.r > g.y1 - 2 * H.hy)
+        throw Error{PF_EINVAL, "variant " + std::to_string(v) + ": body within 2h of the outer boundary"};
+      for (int k2 = 0; k2 < k; ++k2) {
+        const pf_body& C = b.bodies[H.body0 + k2];
+        const double ddx = B.cx - C.cx, ddy = B.cy - C.cy;
+        if (ddx * ddx + ddy * ddy <= (B.r + C.r) * (B.r + C.r))
+          throw Error{PF_EINVAL, "variant " + std::to_string(v) + ": bodies overlap or touch"};
+      }
+      int4 bb;
+      bb.x = std::max(0, (int)std::floor((B.cx - B.r - g.x0) / H.hx) - 1);
+      bb.y = std::min(g.nx, (int)std::ceil((B.cx + B.r - g.x0) / H.hx) + 1);
+      bb.z = std::max(0, (int)std::floor((B.cy - B.r - g.y0) / H.hy) - 1);
+      bb.w = std::min(g.ny, (int)std::ceil((B.cy + B.r - g.y0) / H.hy) + 1);
+      bbox[H.body0 + k] = bb;
+      body_var[H.body0 + k] = v;
+    }
+    DevVariant& D = dv[v];
+    memset(&D, 0, sizeof(D));
+    D.x0 = g.x0; D.y0 = g.y0; D.hx = H.hx; D.hy = H.hy;
+    D.base = H.base; D.nx = g.nx; D.ny = g.ny; D.P = H.P; D.nb = nb; D.body0 = H.body0;
+    D.tiles_x = H.tiles_x; D.tiles_y = H.tiles_y;
+    rect_stiffness(H.hx, H.hy, D.kr64);
+    for (int m = 0; m < 6; ++m) D.kr32[m] = (float)D.kr64[m];
+  }
+  b.Vtot = base;
+  b.T = (long long)tij.size();
+  const long long Vt = b.Vtot;
+
+  // ---- device arrays
+  b.d_var = upload(b, dv);
+  std::vector<pf_body> hb(b.bodies);
+  b.d_bodies = upload(b, hb);
+  b.d_body_var = upload(b, body_var);
+  b.d_bbox = upload(b, bbox);
+  b.tile_ij = upload(b, tij);
+  b.tile_var = upload(b, tvar);
+  b.tag = (uint8_t*)dev_alloc(b, Vt);
+  b.bid = (int*)dev_alloc(b, Vt * sizeof(int));
+  b.X = (double*)dev_alloc(b, 2 * Vt * sizeof(double));
+  b.K64 = (double*)dev_alloc(b, 6 * Vt * sizeof(double));
+  b.K32 = (float*)dev_alloc(b, 6 * Vt * sizeof(float));
+  double2* dA = (double2*)dev_alloc(b, Vt * sizeof(double2));
+  double2* dB = (double2*)dev_alloc(b, Vt * sizeof(double2));
+  int* err = (int*)dev_alloc(b, sizeof(int));
+  b.d_stats_i = (long long*)dev_alloc(b, nv * 6 * sizeof(long long));
+  b.d_detmin = (double*)dev_alloc(b, nv * sizeof(double));
+  cudaStream_t s = b.stream;
+  PF_CUDA(cudaMemsetAsync(b.tag, K_INACT, Vt, s));
+  PF_CUDA(cudaMemsetAsync(b.bid, 0xff, Vt * sizeof(int), s));
+  PF_CUDA(cudaMemsetAsync(b.X, 0, 2 * Vt * sizeof(double), s));
+  PF_CUDA(cudaMemsetAsync(b.K64, 0, 6 * Vt * sizeof(double), s));
+  PF_CUDA(cudaMemsetAsync(b.K32, 0, 6 * Vt * sizeof(float), s));
+  PF_CUDA(cudaMemsetAsync(dA, 0, Vt * sizeof(double2), s));
+  PF_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+  PF_CUDA(cudaMemsetAsync(b.d_stats_i, 0, nv * 6 * sizeof(long long), s));
+  {
+    std::vector<double> big(nv, 1e300);
+    PF_CUDA(cudaMemcpyAsync(b.d_detmin, big.data(), nv * sizeof(double), cudaMemcpyHostToDevice, s));
+    PF_CUDA(cudaStreamSynchronize(s));
+  }
+
+  const dim3 blk(TX, TY);
+  const unsigned grid = (unsigned)b.T;
+  k_classify<<<grid, blk, 0, s>>>(b.d_var, b.tile_var, b.tile_ij, b.d_bodies, b.bid, err);
+  k_kinds<<<grid, blk, 0, s>>>(b.d_var, b.tile_var, b.tile_ij, b.d_bodies, b.bid, b.tag, dA, bc[0], bc[1],
+                               bc[2], bc[3], err);
+  PF_CUDA(cudaMemcpyAsync(dB, dA, Vt * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+  for (int it = 0; it < sweeps; ++it) {
+    k_jacobi<<<grid, blk, 0, s>>>(b.d_var, b.tile_var, b.tile_ij, b.bid, b.tag, dA, dB);
+    std::swap(dA, dB);
+  }
+  k_finalize<<<grid, blk, 0, s>>>(b.d_var, b.tile_var, b.tile_ij, dA, b.tag, b.X, Vt);
+  k_stiffness<<<grid, blk, 0, s>>>(b.d_var, b.tile_var, b.tile_ij, b.tag, b.X, Vt, b.K64, b.K32, b.d_stats_i,
+                                   b.d_detmin);
+  PF_CUDA(cudaGetLastError());
+
+  // ---- body node and edge lists
+  b.body_ptr = (int*)dev_alloc(b, (b.B + 1) * sizeof(int));
+  b.edge_ptr = (int*)dev_alloc(b, (b.B + 1) * sizeof(int));
+  int* cnt = (int*)dev_alloc(b, std::max(1, 2 * b.B) * sizeof(int));
+  std::vector<int> hcnt(2 * b.B);
+  if (b.B > 0) {
+    k_body_nodes<<<b.B, blk, 0, s>>>(b.d_var, b.d_body_var, b.d_bbox, b.tag, b.bid, cnt, nullptr, nullptr, 0);
+    k_body_edges<<<b.B, blk, 0, s>>>(b.d_var, b.d_body_var, b.d_bbox, b.tag, b.bid, b.X, Vt, cnt + b.B, nullptr,
+                                     nullptr, 0);
+    PF_CUDA(cudaMemcpyAsync(hcnt.data(), cnt, 2 * b.B * sizeof(int), cudaMemcpyDeviceToHost, s));
+  }
+  int herr = 0;
+  PF_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  PF_CUDA(cudaStreamSynchronize(s));
+  if (herr & 1) throw Error{PF_EINVAL, "a grid node lies inside two bodies"};
+  if (herr & 2) throw Error{PF_EINVAL, "a grid node lies at a body centre"};
+  b.h_body_ptr.assign(b.B + 1, 0);
+  b.h_edge_ptr.assign(b.B + 1, 0);
+  for (int k = 0; k < b.B; ++k) {
+    b.h_body_ptr[k + 1] = b.h_body_ptr[k] + hcnt[k];
+    b.h_edge_ptr[k + 1] = b.h_edge_ptr[k] + hcnt[b.B + k];
+  }
+  PF_CUDA(cudaMemcpyAsync(b.body_ptr, b.h_body_ptr.data(), (b.B + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
+  PF_CUDA(cudaMemcpyAsync(b.edge_ptr, b.h_edge_ptr.data(), (b.B + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
+  b.body_nodes = (long long*)dev_alloc(b, std::max(1, b.h_body_ptr[b.B]) * sizeof(long long));
+  b.edge_rec = (long long*)dev_alloc(b, std::max(1, b.h_edge_ptr[b.B]) * sizeof(long long));
+  if (b.B > 0) {
+    k_body_nodes<<<b.B, blk, 0, s>>>(b.d_var, b.d_body_var, b.d_bbox, b.tag, b.bid, nullptr, b.body_ptr,
+                                     b.body_nodes, 1);
+    k_body_edges<<<b.B, blk, 0, s>>>(b.d_var, b.d_body_var, b.d_bbox, b.tag, b.bid, b.X, Vt, nullptr, b.edge_ptr,
+                                     b.edge_rec, 1);
+  }
+  PF_CUDA(cudaGetLastError());
+
+  // ---- stats
+  std::vector<long long> st(nv * 6);
+  std::vector<double> dmin(nv);
+  PF_CUDA(cudaMemcpyAsync(st.data(), b.d_stats_i, nv * 6 * sizeof(long long), cudaMemcpyDeviceToHost, s));
+  PF_CUDA(cudaMemcpyAsync(dmin.data(), b.d_detmin, nv * sizeof(double), cudaMemcpyDeviceToHost, s));
+  PF_CUDA(cudaStreamSynchronize(s));
+  b.valid = true;
+  for (int v = 0; v < nv; ++v) {
+    HostVariant& H = b.hv[v];
+    pf_mesh_stats& S = H.stats;
+    S.n_nodes = (long long)(H.g.nx + 1) * (H.g.ny + 1);
+    S.n_free = st[v * 6 + 0];
+    S.n_body_nodes = st[v * 6 + 1];
+    S.n_inactive = st[v * 6 + 2];
+    S.n_active_cells = st[v * 6 + 3];
+    S.n_general_cells = st[v * 6 + 4];
+    S.n_bodies = H.nb;
+    S.n_dof = S.n_free + H.nb;
+    S.n_boundary_edges = b.h_edge_ptr[H.body0 + H.nb] - b.h_edge_ptr[H.body0];
+    S.min_detJ = dmin[v];
+    S.h = std::max(H.hx, H.hy);
+    if (!(dmin[v] > 0.0)) b.valid = false;
+  }
+  // dA/dB/err/cnt stay allocated until destroy (simple arena ownership)
+  make_schedule(b);
+}
+
+void export_coords(Batch& b, int v, double* dev_xy) {
+  const HostVariant& H = b.hv[v];
+  const long long N = (long long)(H.g.nx + 1) * (H.g.ny + 1);
+  k_export_coords<<<(unsigned)((N + 255) / 256), 256, 0, b.stream>>>(b.d_var, v, b.X, b.Vtot, dev_xy);
+  PF_CUDA(cudaGetLastError());
+}
+
+void export_tags(Batch& b, int v, int8_t* kind, int32_t* body) {
+  const HostVariant& H = b.hv[v];
+  const long long N = (long long)(H.g.nx + 1) * (H.g.ny + 1);
+  k_export_tags<<<(unsigned)((N + 255) / 256), 256, 0, b.stream>>>(b.d_var, v, b.tag, b.bid, kind, body);
+  PF_CUDA(cudaGetLastError());
+}
+
+}  // namespace pfq4

@@ -1,0 +1,885 @@
+// Matrix-free multi-point-constraint Conjugate Gradient (Appendix A, Algorithm) on
+// GB300, for one or many mesh variants at once.
+//
+// Per CG iteration one fused, persistent kernel (k_cg) does, for every tile of every
+// unconverged variant:
+//     r_k = r_{k-1} - alpha_{k-1} q_{k-1}        (residual update)
+//     x_k = x_{k-1} + alpha_{k-1} p_{k-1}        (solution update)
+//     p_k = r_k + beta_{k-1} p_{k-1}             (search direction, also on the halo)
+//     q_k = A p_k                                (matrix-free Q4 apply, "Compute Ap")
+// plus the four dot products r.r, p.q, r.q, q.q.  The body unknowns follow the
+// paper's collapse / expand: q at the nodes of body k is summed into one body row
+// (collapse) and the body's single search-direction value is used at all of its
+// nodes (expand).  The last CTA to finish a variant reduces the per-segment partial
+// sums in a fixed order and forms alpha_k = r.r / p.q and
+// beta_k = |r_{k+1}|^2 / |r_k|^2 with |r_{k+1}|^2 = r.r - 2 alpha r.q + alpha^2 q.q, so a
+// single grid-wide reduction per iteration suffices.  Dirichlet and inactive nodes
+// keep zero search directions (constraint enforcement after every update).
+//
+// A second kernel (k_resid) forms the true FP64 residual b - A u from the FP64
+// solution (the Dirichlet values sit in place, so the lifting is part of the same
+// apply), folds in the FP32 correction in mixed precision (iterative refinement),
+// and restarts the inner CG from that residual.  Both kernels read their per-variant
+// phase from device memory, so the host launches a captured graph of
+// [k_cg x chunk, k_resid] until every variant is done.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "batch.h"
+
+namespace pfq4 {
+
+template <typename T>
+struct CGArgs {
+  MeshDev m;
+  Sched sc;
+  VarState* st;
+  const SolveParams* prm;
+  T *x, *r, *p, *q;         // node vectors of the CG (FP64 mode: x is the solution)
+  T* sb;                    // [4][B] body x, r, p, q of the CG
+  int B;
+  int* n_done;
+};
+
+template <typename T>
+struct ResidArgs {
+  MeshDev m;
+  Sched sc;
+  VarState* st;
+  const SolveParams* prm;
+  double* x64;              // solution, Dirichlet values in place
+  double* w64;              // body-node rows of A u
+  T *x, *r, *p, *q;         // CG vectors to restart (mixed: x is the correction)
+  double* sb64;             // [4][B]: [0] = body solution values
+  T* sb;                    // [4][B] CG body values
+  double* sbr;              // [B] true residual body rows
+  int B;
+  int mixed;
+  int* n_done;
+};
+
+template <typename T> __device__ __forceinline__ const T* kplane(const MeshDev& m);
+template <> __device__ __forceinline__ const double* kplane<double>(const MeshDev& m) { return m.K64; }
+template <> __device__ __forceinline__ const float* kplane<float>(const MeshDev& m) { return m.K32; }
+template <typename T> __device__ __forceinline__ const T* krect(const DevVariant& V);
+template <> __device__ __forceinline__ const double* krect<double>(const DevVariant& V) { return V.kr64; }
+template <> __device__ __forceinline__ const float* krect<float>(const DevVariant& V) { return V.kr32; }
+
+// The CG vector recurrences, shared by tile owners, halo readers and the body
+// finaliser so that every copy of a value is bit-identical.
+template <typename T>
+__device__ __forceinline__ T next_r(T r, T q, T alpha) { return r - alpha * q; }
+template <typename T>
+__device__ __forceinline__ T next_p(T rn, T p, T beta) { return rn + beta * p; }
+template <typename T>
+__device__ __forceinline__ T next_x(T x, T p, T alpha) { return x + alpha * p; }
+
+__device__ __forceinline__ int seg_count(const Sched& sc, int v) { return sc.var_seg1[v] - sc.var_seg0[v]; }
+
+// Sum of the per-segment partials of variant v (fixed order); all threads get sums.
+__device__ void reduce_partials(const Sched& sc, int v, int nk, double* out, double* scratch) {
+  double s[4] = {0, 0, 0, 0};
+  const int tid = linear_tid();
+  for (int sg = sc.var_seg0[v] + tid; sg < sc.var_seg1[v]; sg += NT)
+    for (int k = 0; k < nk; ++k) s[k] += __ldcg(&sc.partial[sg * 4 + k]);
+  for (int k = 0; k < nk; ++k) out[k] = block_sum(s[k], scratch);
+}
+
+// Sum of a node vector over the nodes of one body (fixed order), all threads get it.
+template <typename T>
+__device__ double body_gather(const MeshDev& m, int gb, const T* vec, double* scratch) {
+  double s = 0.0;
+  const int e1 = m.body_ptr[gb + 1];
+  for (int e = m.body_ptr[gb] + linear_tid(); e < e1; e += NT) s += (double)__ldcg(vec + m.body_nodes[e]);
+  return block_sum(s, scratch);
+}
+
+// ---------------------------------------------------------------- fused CG step
+template <typename T>
+__device__ void finalize_cg(const CGArgs<T>& a, int v, double* scratch, double* sh_qb) {
+  const DevVariant& V = a.m.var[v];
+  VarState* S = &a.st[v];
+  double d[4];
+  reduce_partials(a.sc, v, 4, d, scratch);
+  for (int k = 0; k < V.nb; ++k) {
+    const double s = body_gather<T>(a.m, V.body0 + k, a.q, scratch);
+    if (linear_tid() == 0) sh_qb[k] = s;
+  }
+  __syncthreads();
+  if (linear_tid() == 0) {
+    const T alpha = (T)S->alpha, beta = (T)S->beta;
+    const int B = a.B;
+    for (int k = 0; k < V.nb; ++k) {
+      const int gb = V.body0 + k;
+      const T xb = a.sb[gb], rb = a.sb[B + gb], pb = a.sb[2 * B + gb], qb = a.sb[3 * B + gb];
+      const T rn = next_r(rb, qb, alpha);
+      const T pn = next_p(rn, pb, beta);
+      const T xn = next_x(xb, pb, alpha);
+      const T qn = (T)sh_qb[k];
+      a.sb[gb] = xn;
+      a.sb[B + gb] = rn;
+      a.sb[2 * B + gb] = pn;
+      a.sb[3 * B + gb] = qn;
+      d[0] += (double)rn * (double)rn;
+      d[1] += (double)pn * (double)qn;
+      d[2] += (double)rn * (double)qn;
+      d[3] += (double)qn * (double)qn;
+    }
+    const double g = d[0], pi = d[1], rho = d[2], mu = d[3];
+    S->iters += 1;
+    S->inner_iters += 1;
+    if (S->inner_iters == 1) S->gamma_start = g;
+    S->gamma = g; S->pi = pi; S->rho = rho; S->mu = mu;
+    if (!isfinite(g) || !isfinite(pi) || !(pi > 0.0)) {
+      if (g == 0.0) {
+        S->phase = PH_RESID;
+      } else {
+        S->status = PF_EBREAKDOWN;
+        S->phase = PH_DONE;
+        atomicAdd(a.n_done, 1);
+      }
+    } else if (g <= fmax(S->thr_rel * S->gamma_start, S->thr_abs2)) {
+      S->phase = PH_RESID;
+    } else if (S->iters >= a.prm->k_max) {
+      S->capped = 1;
+      S->phase = PH_RESID;
+    } else {
+      const double al = g / pi;
+      const double gn = g - 2.0 * al * rho + al * al * mu;
+      S->alpha = al;
+      S->beta = gn > 0.0 ? gn / g : 0.0;
+    }
+    a.sc.counter[v] = 0;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT) k_cg(CGArgs<T> a) {
+  __shared__ T ps[TY + 2][SW];
+  __shared__ uint8_t ts[TY + 2][SW];
+  __shared__ T s_pb[MAXB];
+  __shared__ double red[NT / 32][4];
+  __shared__ double scratch[NT / 32 + 1];
+  __shared__ double sh_qb[MAXB];
+  __shared__ int s_last;
+  const int tid = linear_tid(), lane = tid & 31, warp = tid >> 5;
+  const int B = a.B;
+  const T* K = kplane<T>(a.m);
+  const long long plane = a.m.Vtot;
+  for (int sg = a.sc.cta_seg[blockIdx.x]; sg < a.sc.cta_seg[blockIdx.x + 1]; ++sg) {
+    const int v = a.sc.seg_var[sg];
+    if (a.st[v].phase != PH_CG) continue;
+    const DevVariant& V = a.m.var[v];
+    const T alpha = (T)a.st[v].alpha, beta = (T)a.st[v].beta;
+    const T* kr = krect<T>(V);
+    if (tid < V.nb) {
+      const int gb = V.body0 + tid;
+      const T rn = next_r(a.sb[B + gb], a.sb[3 * B + gb], alpha);
+      s_pb[tid] = next_p(rn, a.sb[2 * B + gb], beta);
+    }
+    __syncthreads();
+    Acc<T> acc;
+    acc.zero();
+    for (int t = a.sc.seg_t0[sg]; t < a.sc.seg_t1[sg]; ++t) {
+      const int2 ij = a.sc.tile_ij[t];
+      const int i = ij.x + threadIdx.x, j = ij.y + threadIdx.y;
+      const bool in = (i <= V.nx) && (j <= V.ny);
+      const long long n = V.base + (long long)j * V.P + i;
+      const uint8_t tg = in ? a.m.tag[n] : K_INACT;
+      const int kind = tg & KIND_MASK;
+      T rn = T(0), pn = T(0), xn = T(0);
+      if (kind == K_FREE) {
+        const T po = a.p[n];
+        rn = next_r(a.r[n], a.q[n], alpha);
+        xn = next_x(a.x[n], po, alpha);
+        pn = next_p(rn, po, beta);
+      } else if (kind == K_BODY) {
+        pn = s_pb[a.m.bid[n]];
+      }
+      ps[threadIdx.y + 1][threadIdx.x + 1] = pn;
+      ts[threadIdx.y + 1][threadIdx.x + 1] = tg;
+      if (tid < NHALO) {
+        int li, lj;
+        halo_pos(tid, li, lj);
+        const int hi = ij.x - 1 + li, hj = ij.y - 1 + lj;
+        uint8_t ht = K_INACT;
+        T hp = T(0);
+        if (hi >= 0 && hj >= 0 && hi <= V.nx && hj <= V.ny) {
+          const long long hn = V.base + (long long)hj * V.P + hi;
+          ht = a.m.tag[hn];
+          const int hk = ht & KIND_MASK;
+          if (hk == K_FREE) hp = next_p(next_r(a.r[hn], a.q[hn], alpha), a.p[hn], beta);
+          else if (hk == K_BODY) hp = s_pb[a.m.bid[hn]];
+        }
+        ps[lj][li] = hp;
+        ts[lj][li] = ht;
+      }
+      __syncthreads();
+      if (kind == K_FREE || kind == K_BODY) {
+        const T y = q4_row<T>(ps, ts, threadIdx.x + 1, threadIdx.y + 1, n, V.P, K, plane, kr);
+        a.q[n] = y;
+        if (kind == K_FREE) {
+          a.x[n] = xn;
+          a.r[n] = rn;
+          a.p[n] = pn;
+          acc.add(0, rn, rn);
+          acc.add(1, pn, y);
+          acc.add(2, rn, y);
+          acc.add(3, y, y);
+        }
+      }
+      __syncthreads();
+    }
+    double w4[4];
+    acc.warp_reduce(w4);
+    if (lane == 0)
+      for (int k = 0; k < 4; ++k) red[warp][k] = w4[k];
+    __syncthreads();
+    if (tid == 0) {
+      for (int k = 0; k < 4; ++k) {
+        double s = 0.0;
+        for (int w = 0; w < NT / 32; ++w) s += red[w][k];
+        a.sc.partial[sg * 4 + k] = s;
+      }
+      __threadfence();
+      const int done = atomicAdd(&a.sc.counter[v], 1);
+      s_last = (done == seg_count(a.sc, v) - 1);
+    }
+    __syncthreads();
+    if (s_last) {
+      __threadfence();
+      finalize_cg<T>(a, v, scratch, sh_qb);
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- true residual
+template <typename T>
+__device__ void finalize_resid(const ResidArgs<T>& a, int v, double* scratch, double* sh_rb) {
+  const DevVariant& V = a.m.var[v];
+  VarState* S = &a.st[v];
+  double d[1];
+  reduce_partials(a.sc, v, 1, d, scratch);
+  for (int k = 0; k < V.nb; ++k) {
+    const double s = body_gather<double>(a.m, V.body0 + k, a.w64, scratch);
+    if (linear_tid() == 0) sh_rb[k] = -s;
+  }
+  __syncthreads();
+  if (linear_tid() == 0) {
+    const int B = a.B;
+    double g = d[0];
+    for (int k = 0; k < V.nb; ++k) {
+      const int gb = V.body0 + k;
+      const double rb = sh_rb[k];
+      g += rb * rb;
+      a.sbr[gb] = rb;
+      if (a.mixed) {
+        a.sb64[gb] = a.sb64[gb] + (double)a.sb[gb];
+        a.sb[gb] = T(0);
+      }
+      a.sb[B + gb] = (T)rb;
+      a.sb[2 * B + gb] = T(0);
+      a.sb[3 * B + gb] = T(0);
+    }
+    S->rr64 = g;
+    S->n_resid += 1;
+    if (S->bnorm2 < 0.0) S->bnorm2 = g;
+    const double tol2 = a.prm->tol2;
+    bool fin = false;
+    if (S->bnorm2 == 0.0 || g <= tol2 * S->bnorm2) {
+      S->status = PF_OK;
+      fin = true;
+    } else if (S->capped || !isfinite(g)) {
+      S->status = isfinite(g) ? PF_ENOT_CONVERGED : PF_EBREAKDOWN;
+      fin = true;
+    }
+    if (fin) {
+      S->phase = PH_DONE;
+      atomicAdd(a.n_done, 1);
+    } else {
+      S->phase = PH_CG;
+      S->alpha = 0.0;
+      S->beta = 0.0;
+      S->inner_iters = 0;
+      S->thr_rel = a.mixed ? a.prm->inner_rel2 : 0.0;
+      S->thr_abs2 = (a.mixed ? 0.25 : 1.0) * tol2 * S->bnorm2;
+    }
+    a.sc.counter[v] = 0;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT) k_resid(ResidArgs<T> a) {
+  __shared__ double ps[TY + 2][SW];
+  __shared__ uint8_t ts[TY + 2][SW];
+  __shared__ double s_xb[MAXB];
+  __shared__ double red[NT / 32];
+  __shared__ double scratch[NT / 32 + 1];
+  __shared__ double sh_rb[MAXB];
+  __shared__ int s_last;
+  const int tid = linear_tid(), lane = tid & 31, warp = tid >> 5;
+  const long long plane = a.m.Vtot;
+  for (int sg = a.sc.cta_seg[blockIdx.x]; sg < a.sc.cta_seg[blockIdx.x + 1]; ++sg) {
+    const int v = a.sc.seg_var[sg];
+    if (a.st[v].phase != PH_RESID) continue;
+    const DevVariant& V = a.m.var[v];
+    if (tid < V.nb) {
+      const int gb = V.body0 + tid;
+      s_xb[tid] = a.mixed ? a.sb64[gb] + (double)a.sb[gb] : a.sb64[gb];
+    }
+    __syncthreads();
+    double acc = 0.0;
+    for (int t = a.sc.seg_t0[sg]; t < a.sc.seg_t1[sg]; ++t) {
+      const int2 ij = a.sc.tile_ij[t];
+      const int i = ij.x + threadIdx.x, j = ij.y + threadIdx.y;
+      const bool in = (i <= V.nx) && (j <= V.ny);
+      const long long n = V.base + (long long)j * V.P + i;
+      const uint8_t tg = in ? a.m.tag[n] : K_INACT;
+      const int kind = tg & KIND_MASK;
+      double u = 0.0;
+      if (kind == K_FREE) u = a.mixed ? a.x64[n] + (double)a.x[n] : a.x64[n];
+      else if (kind == K_DIR) u = a.x64[n];
+      else if (kind == K_BODY) u = s_xb[a.m.bid[n]];
+      ps[threadIdx.y + 1][threadIdx.x + 1] = u;
+      ts[threadIdx.y + 1][threadIdx.x + 1] = tg;
+      if (tid < NHALO) {
+        int li, lj;
+        halo_pos(tid, li, lj);
+        const int hi = ij.x - 1 + li, hj = ij.y - 1 + lj;
+        uint8_t ht = K_INACT;
+        double hu = 0.0;
+        if (hi >= 0 && hj >= 0 && hi <= V.nx && hj <= V.ny) {
+          const long long hn = V.base + (long long)hj * V.P + hi;
+          ht = a.m.tag[hn];
+          const int hk = ht & KIND_MASK;
+          if (hk == K_FREE) hu = a.mixed ? a.x64[hn] + (double)a.x[hn] : a.x64[hn];
+          else if (hk == K_DIR) hu = a.x64[hn];
+          else if (hk == K_BODY) hu = s_xb[a.m.bid[hn]];
+        }
+        ps[lj][li] = hu;
+        ts[lj][li] = ht;
+      }
+      __syncthreads();
+      if (kind == K_FREE || kind == K_BODY) {
+        const double y = q4_row<double>(ps, ts, threadIdx.x + 1, threadIdx.y + 1, n, V.P, a.m.K64, plane, V.kr64);
+        if (kind == K_FREE) {
+          const double r = -y;
+          if (a.mixed) {
+            a.x64[n] = u;
+            a.x[n] = T(0);
+          }
+          a.r[n] = (T)r;
+          a.p[n] = T(0);
+          a.q[n] = T(0);
+          acc = fma(r, r, acc);
+        } else {
+          a.w64[n] = y;
+        }
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) red[warp] = acc;
+    __syncthreads();
+    if (tid == 0) {
+      double s = 0.0;
+      for (int w = 0; w < NT / 32; ++w) s += red[w];
+      a.sc.partial[sg * 4] = s;
+      __threadfence();
+      const int done = atomicAdd(&a.sc.counter[v], 1);
+      s_last = (done == seg_count(a.sc, v) - 1);
+    }
+    __syncthreads();
+    if (s_last) {
+      __threadfence();
+      finalize_resid<T>(a, v, scratch, sh_rb);
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- init / export
+__global__ void k_init(const DevVariant* var, const int* tile_var, const int2* tile_ij, const uint8_t* tag,
+                       const double* X, long long Vtot, double U, int warm, double* x64, double* w64,
+                       void* v0, void* v1, void* v2, void* v3, int vbytes) {
+  const long long t = blockIdx.x;
+  const int v = tile_var[t];
+  const DevVariant& V = var[v];
+  const int2 ij = tile_ij[t];
+  const int i = ij.x + threadIdx.x, j = ij.y + threadIdx.y;
+  if (i >= V.P || j > V.ny) return;
+  const long long n = V.base + (long long)j * V.P + i;
+  const int kind = (i <= V.nx) ? (tag[n] & KIND_MASK) : K_INACT;
+  double u = 0.0;
+  if (kind == K_DIR) u = __dmul_rn(U, X[Vtot + n]);
+  else if (kind == K_FREE && warm) u = x64[n];
+  x64[n] = u;
+  w64[n] = 0.0;
+  if (vbytes == 8) {
+    ((double*)v0)[n] = 0.0; ((double*)v1)[n] = 0.0; ((double*)v2)[n] = 0.0;
+    if (v3) ((double*)v3)[n] = 0.0;
+  } else {
+    ((float*)v0)[n] = 0.f; ((float*)v1)[n] = 0.f; ((float*)v2)[n] = 0.f;
+    if (v3) ((float*)v3)[n] = 0.f;
+  }
+}
+
+__global__ void k_export_psi(const DevVariant* var, int nv, const long long* lbase, const uint8_t* tag,
+                             const int* bid, const double* x64, const double* xb, double* psi) {
+  // one grid over all variants' logical nodes: blockIdx.y = variant
+  const int v = blockIdx.y;
+  const DevVariant& V = var[v];
+  const long long N = (long long)(V.nx + 1) * (V.ny + 1);
+  for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < N; m += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(m % (V.nx + 1)), j = (int)(m / (V.nx + 1));
+    const long long n = V.base + (long long)j * V.P + i;
+    const int kind = tag[n] & KIND_MASK;
+    double u = 0.0;
+    if (kind == K_FREE || kind == K_DIR) u = x64[n];
+    else if (kind == K_BODY) u = xb[V.body0 + bid[n]];
+    psi[lbase[v] + m] = u;
+  }
+}
+
+// logical <-> padded copies used by pf_apply
+template <typename T>
+__global__ void k_to_padded(const DevVariant* var, const long long* lbase, const double* src, T* dst) {
+  const int v = blockIdx.y;
+  const DevVariant& V = var[v];
+  const long long N = (long long)(V.nx + 1) * (V.ny + 1);
+  for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < N; m += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(m % (V.nx + 1)), j = (int)(m / (V.nx + 1));
+    dst[V.base + (long long)j * V.P + i] = (T)src[lbase[v] + m];
+  }
+}
+
+template <typename T>
+__global__ void k_from_padded(const DevVariant* var, const long long* lbase, const T* src, double* dst) {
+  const int v = blockIdx.y;
+  const DevVariant& V = var[v];
+  const long long N = (long long)(V.nx + 1) * (V.ny + 1);
+  for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < N; m += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(m % (V.nx + 1)), j = (int)(m / (V.nx + 1));
+    dst[lbase[v] + m] = (double)src[V.base + (long long)j * V.P + i];
+  }
+}
+
+// one tile per CTA: y = A p at FREE and BODY nodes (p used as given everywhere)
+template <typename T>
+__global__ void __launch_bounds__(NT) k_apply(MeshDev m, const int* tile_var, const int2* tile_ij, const T* p, T* y) {
+  __shared__ T ps[TY + 2][SW];
+  __shared__ uint8_t ts[TY + 2][SW];
+  const long long t = blockIdx.x;
+  const int v = tile_var[t];
+  const DevVariant& V = m.var[v];
+  const int2 ij = tile_ij[t];
+  const int tid = linear_tid();
+  const int i = ij.x + threadIdx.x, j = ij.y + threadIdx.y;
+  const bool in = (i <= V.nx) && (j <= V.ny);
+  const long long n = V.base + (long long)j * V.P + i;
+  const uint8_t tg = in ? m.tag[n] : K_INACT;
+  ps[threadIdx.y + 1][threadIdx.x + 1] = in ? p[n] : T(0);
+  ts[threadIdx.y + 1][threadIdx.x + 1] = tg;
+  if (tid < NHALO) {
+    int li, lj;
+    halo_pos(tid, li, lj);
+    const int hi = ij.x - 1 + li, hj = ij.y - 1 + lj;
+    uint8_t ht = K_INACT;
+    T hp = T(0);
+    if (hi >= 0 && hj >= 0 && hi <= V.nx && hj <= V.ny) {
+      const long long hn = V.base + (long long)hj * V.P + hi;
+      ht = m.tag[hn];
+      hp = p[hn];
+    }
+    ps[lj][li] = hp;
+    ts[lj][li] = ht;
+  }
+  __syncthreads();
+  if (!in) return;
+  const int kind = tg & KIND_MASK;
+  T out = T(0);
+  if (kind == K_FREE || kind == K_BODY)
+    out = q4_row<T>(ps, ts, threadIdx.x + 1, threadIdx.y + 1, n, V.P, kplane<T>(m), m.Vtot, krect<T>(V));
+  y[n] = out;
+}
+
+// collapsed body rows: one CTA per global body, fixed-order sum
+template <typename T>
+__global__ void __launch_bounds__(NT) k_body_sums(MeshDev m, const T* y, double* out) {
+  __shared__ double scratch[NT / 32 + 1];
+  const double s = body_gather<T>(m, blockIdx.x, y, scratch);
+  if (linear_tid() == 0) out[blockIdx.x] = s;
+}
+
+// ---------------------------------------------------------------- host side
+static MeshDev mesh_dev(const Batch& b) {
+  MeshDev m;
+  m.var = b.d_var;
+  m.tag = b.tag;
+  m.bid = b.bid;
+  m.body_ptr = b.body_ptr;
+  m.body_nodes = b.body_nodes;
+  m.K64 = b.K64;
+  m.K32 = b.K32;
+  m.Vtot = b.Vtot;
+  return m;
+}
+
+void make_schedule(Batch& b) {
+  int dev = 0, nsm = 0;
+  PF_CUDA(cudaGetDevice(&dev));
+  PF_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  int o32 = 0, o64 = 0, oR = 0;
+  PF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o32, k_cg<float>, NT, 0));
+  PF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o64, k_cg<double>, NT, 0));
+  PF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&oR, k_resid<float>, NT, 0));
+  const int occ = std::max(1, std::min(o32, std::min(o64, oR)));
+  long long G = std::min<long long>((long long)nsm * occ, b.T);
+  b.G = (int)G;
+  std::vector<int> cta_seg(G + 1), seg_var, seg_t0, seg_t1;
+  std::vector<int> tv(b.T);
+  for (int v = 0; v < b.nv; ++v)
+    for (long long t = b.hv[v].tile0; t < b.hv[v].tile0 + (long long)b.hv[v].tiles_x * b.hv[v].tiles_y; ++t) tv[t] = v;
+  for (long long c = 0; c < G; ++c) {
+    const long long t0 = c * b.T / G, t1 = (c + 1) * b.T / G;
+    cta_seg[c] = (int)seg_var.size();
+    long long s0 = t0;
+    for (long long t = t0; t < t1; ++t) {
+      if (t + 1 == t1 || tv[t + 1] != tv[t]) {
+        seg_var.push_back(tv[t]);
+        seg_t0.push_back((int)s0);
+        seg_t1.push_back((int)(t + 1));
+        s0 = t + 1;
+      }
+    }
+  }
+  cta_seg[G] = (int)seg_var.size();
+  b.S = (int)seg_var.size();
+  std::vector<int> vs0(b.nv, -1), vs1(b.nv, -1);
+  for (int sgi = 0; sgi < b.S; ++sgi) {
+    const int v = seg_var[sgi];
+    if (vs0[v] < 0) vs0[v] = sgi;
+    vs1[v] = sgi + 1;
+  }
+  auto up = [&](const std::vector<int>& h) {
+    int* d = (int*)dev_alloc(b, std::max<size_t>(1, h.size()) * sizeof(int));
+    PF_CUDA(cudaMemcpyAsync(d, h.data(), h.size() * sizeof(int), cudaMemcpyHostToDevice, b.stream));
+    return d;
+  };
+  b.cta_seg = up(cta_seg);
+  b.seg_var = up(seg_var);
+  b.seg_t0 = up(seg_t0);
+  b.seg_t1 = up(seg_t1);
+  b.var_seg0 = up(vs0);
+  b.var_seg1 = up(vs1);
+  b.counter = (int*)dev_alloc(b, b.nv * sizeof(int));
+  PF_CUDA(cudaMemsetAsync(b.counter, 0, b.nv * sizeof(int), b.stream));
+  b.partial = (double*)dev_alloc(b, (size_t)b.S * 4 * sizeof(double));
+  b.sched.cta_seg = b.cta_seg;
+  b.sched.seg_var = b.seg_var;
+  b.sched.seg_t0 = b.seg_t0;
+  b.sched.seg_t1 = b.seg_t1;
+  b.sched.tile_ij = b.tile_ij;
+  b.sched.var_seg0 = b.var_seg0;
+  b.sched.var_seg1 = b.var_seg1;
+  b.sched.partial = b.partial;
+  b.sched.counter = b.counter;
+  b.sched.n_cta = b.G;
+  PF_CUDA(cudaStreamSynchronize(b.stream));
+}
+
+void ensure_solver_memory(Batch& b, int precision) {
+  const size_t V = (size_t)b.Vtot;
+  const int B = std::max(1, b.B);
+  if (!b.x64) {
+    b.x64 = (double*)dev_alloc(b, V * sizeof(double));
+    b.w64 = (double*)dev_alloc(b, V * sizeof(double));
+    b.sb64 = (double*)dev_alloc(b, 4 * B * sizeof(double));
+    b.sb32 = (float*)dev_alloc(b, 4 * B * sizeof(float));
+    b.sbr64 = (double*)dev_alloc(b, B * sizeof(double));
+    b.state = (VarState*)dev_alloc(b, b.nv * sizeof(VarState));
+    b.params = (SolveParams*)dev_alloc(b, sizeof(SolveParams));
+    b.n_done = (int*)dev_alloc(b, sizeof(int));
+    PF_CUDA(cudaMemsetAsync(b.x64, 0, V * sizeof(double), b.stream));
+    PF_CUDA(cudaMemsetAsync(b.sb64, 0, 4 * B * sizeof(double), b.stream));
+    PF_CUDA(cudaMemsetAsync(b.sb32, 0, 4 * B * sizeof(float), b.stream));
+    b.bnorm2_unit.assign(b.nv, -1.0);
+    for (int k = 0; k < 6; ++k) PF_CUDA(cudaEventCreate(&b.ev[k]));
+  }
+  if (precision == PF_FP64 && !b.r64) {
+    b.r64 = (double*)dev_alloc(b, V * sizeof(double));
+    b.p64 = (double*)dev_alloc(b, V * sizeof(double));
+    b.q64 = (double*)dev_alloc(b, V * sizeof(double));
+  }
+  if (precision == PF_MIXED && !b.r32) {
+    b.x32 = (float*)dev_alloc(b, V * sizeof(float));
+    b.r32 = (float*)dev_alloc(b, V * sizeof(float));
+    b.p32 = (float*)dev_alloc(b, V * sizeof(float));
+    b.q32 = (float*)dev_alloc(b, V * sizeof(float));
+  }
+}
+
+static std::vector<long long> logical_bases(const Batch& b) {
+  std::vector<long long> lb(b.nv + 1, 0);
+  for (int v = 0; v < b.nv; ++v) lb[v + 1] = lb[v] + (long long)(b.hv[v].g.nx + 1) * (b.hv[v].g.ny + 1);
+  return lb;
+}
+
+static long long* lbase_cached(Batch& b) {
+  if (!b.d_lbase) {
+    const std::vector<long long> h = logical_bases(b);
+    b.d_lbase = (long long*)dev_alloc(b, h.size() * sizeof(long long));
+    PF_CUDA(cudaMemcpyAsync(b.d_lbase, h.data(), h.size() * sizeof(long long), cudaMemcpyHostToDevice, b.stream));
+  }
+  return b.d_lbase;
+}
+
+static double* body_sum_scratch(Batch& b) {
+  if (!b.d_bsum) b.d_bsum = (double*)dev_alloc(b, std::max(1, b.B) * sizeof(double));
+  return b.d_bsum;
+}
+
+void apply_operator(Batch& b, int precision, const double* dev_p, double* dev_y, double* body_sums) {
+  ensure_solver_memory(b, PF_FP64);
+  ensure_solver_memory(b, PF_MIXED);
+  long long* lb = lbase_cached(b);
+  const MeshDev m = mesh_dev(b);
+  const dim3 g2(512, b.nv);
+  double* sums = body_sum_scratch(b);
+  if (precision == PF_FP64) {
+    k_to_padded<double><<<g2, 256, 0, b.stream>>>(b.d_var, lb, dev_p, b.r64);
+    PF_CUDA(cudaMemsetAsync(b.q64, 0, b.Vtot * sizeof(double), b.stream));
+    k_apply<double><<<(unsigned)b.T, dim3(TX, TY), 0, b.stream>>>(m, b.tile_var, b.tile_ij, b.r64, b.q64);
+    k_from_padded<double><<<g2, 256, 0, b.stream>>>(b.d_var, lb, b.q64, dev_y);
+    if (b.B) k_body_sums<double><<<b.B, dim3(TX, TY), 0, b.stream>>>(m, b.q64, sums);
+  } else {
+    k_to_padded<float><<<g2, 256, 0, b.stream>>>(b.d_var, lb, dev_p, b.r32);
+    PF_CUDA(cudaMemsetAsync(b.q32, 0, b.Vtot * sizeof(float), b.stream));
+    k_apply<float><<<(unsigned)b.T, dim3(TX, TY), 0, b.stream>>>(m, b.tile_var, b.tile_ij, b.r32, b.q32);
+    k_from_padded<float><<<g2, 256, 0, b.stream>>>(b.d_var, lb, b.q32, dev_y);
+    if (b.B) k_body_sums<float><<<b.B, dim3(TX, TY), 0, b.stream>>>(m, b.q32, sums);
+  }
+  PF_CUDA(cudaGetLastError());
+  if (body_sums && b.B) {
+    PF_CUDA(cudaMemcpyAsync(body_sums, sums, b.B * sizeof(double), cudaMemcpyDeviceToHost, b.stream));
+  }
+  PF_CUDA(cudaStreamSynchronize(b.stream));
+}
+
+template <typename T>
+static void fill_cg_args(Batch& b, CGArgs<T>& a, T* x, T* r, T* p, T* q, T* sb) {
+  a.m = mesh_dev(b);
+  a.sc = b.sched;
+  a.st = b.state;
+  a.prm = b.params;
+  a.x = x; a.r = r; a.p = p; a.q = q;
+  a.sb = sb;
+  a.B = std::max(1, b.B);
+  a.n_done = b.n_done;
+}
+
+template <typename T>
+static void fill_resid_args(Batch& b, ResidArgs<T>& a, T* x, T* r, T* p, T* q, T* sb, int mixed) {
+  a.m = mesh_dev(b);
+  a.sc = b.sched;
+  a.st = b.state;
+  a.prm = b.params;
+  a.x64 = b.x64;
+  a.w64 = b.w64;
+  a.x = x; a.r = r; a.p = p; a.q = q;
+  a.sb64 = b.sb64;
+  a.sb = sb;
+  a.sbr = b.sbr64;
+  a.B = std::max(1, b.B);
+  a.mixed = mixed;
+  a.n_done = b.n_done;
+}
+
+// launch sequence of one graph chunk: [ev0] k_cg x chunk [ev1] k_resid [ev2]
+static void launch_chunk(Batch& b, int precision, int chunk, cudaStream_t s, bool with_events) {
+  const dim3 blk(TX, TY);
+  if (with_events) PF_CUDA(cudaEventRecord(b.ev[0], s));
+  if (precision == PF_FP64) {
+    CGArgs<double> a;
+    fill_cg_args<double>(b, a, b.x64, b.r64, b.p64, b.q64, b.sb64);
+    for (int k = 0; k < chunk; ++k) k_cg<double><<<b.G, blk, 0, s>>>(a);
+    if (with_events) PF_CUDA(cudaEventRecord(b.ev[1], s));
+    ResidArgs<double> ra;
+    fill_resid_args<double>(b, ra, b.x64, b.r64, b.p64, b.q64, b.sb64, 0);
+    k_resid<double><<<b.G, blk, 0, s>>>(ra);
+  } else {
+    CGArgs<float> a;
+    fill_cg_args<float>(b, a, b.x32, b.r32, b.p32, b.q32, b.sb32);
+    for (int k = 0; k < chunk; ++k) k_cg<float><<<b.G, blk, 0, s>>>(a);
+    if (with_events) PF_CUDA(cudaEventRecord(b.ev[1], s));
+    ResidArgs<float> ra;
+    fill_resid_args<float>(b, ra, b.x32, b.r32, b.p32, b.q32, b.sb32, 1);
+    k_resid<float><<<b.G, blk, 0, s>>>(ra);
+  }
+  if (with_events) PF_CUDA(cudaEventRecord(b.ev[2], s));
+  PF_CUDA(cudaGetLastError());
+}
+
+static void launch_resid_only(Batch& b, int precision, cudaStream_t s) {
+  const dim3 blk(TX, TY);
+  if (precision == PF_FP64) {
+    ResidArgs<double> ra;
+    fill_resid_args<double>(b, ra, b.x64, b.r64, b.p64, b.q64, b.sb64, 0);
+    k_resid<double><<<b.G, blk, 0, s>>>(ra);
+  } else {
+    ResidArgs<float> ra;
+    fill_resid_args<float>(b, ra, b.x32, b.r32, b.p32, b.q32, b.sb32, 1);
+    k_resid<float><<<b.G, blk, 0, s>>>(ra);
+  }
+  PF_CUDA(cudaGetLastError());
+}
+
+static cudaGraphExec_t get_graph(Batch& b, int precision, int chunk) {
+  if (b.graph[precision] && b.graph_chunk[precision] == chunk) return b.graph[precision];
+  if (b.graph[precision]) {
+    cudaGraphExecDestroy(b.graph[precision]);
+    b.graph[precision] = nullptr;
+  }
+  cudaStream_t cs;
+  PF_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaGraph_t g;
+  PF_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  launch_chunk(b, precision, chunk, cs, true);
+  PF_CUDA(cudaStreamEndCapture(cs, &g));
+  cudaGraphExec_t ex;
+  PF_CUDA(cudaGraphInstantiate(&ex, g, 0));
+  PF_CUDA(cudaGraphDestroy(g));
+  PF_CUDA(cudaStreamDestroy(cs));
+  b.graph[precision] = ex;
+  b.graph_chunk[precision] = chunk;
+  return ex;
+}
+
+pf_status psi_solve(Batch& b, double U, const pf_solve_opts& o, double* dev_psi, double* body_psi,
+                    pf_solve_info* info) {
+  if (!b.valid) throw Error{PF_EMESH_INVALID, "mesh has det J <= 0 at a Gauss point; solve refused"};
+  if (o.precision != PF_FP64 && o.precision != PF_MIXED) throw Error{PF_EINVAL, "invalid precision"};
+  if (!(o.tol > 0) || o.k_max < 1 || !std::isfinite(U)) throw Error{PF_EINVAL, "invalid tol, k_max or U"};
+  const int prec = o.precision;
+  ensure_solver_memory(b, prec);
+  cudaStream_t s = b.stream;
+  SolveParams sp{};
+  sp.tol2 = o.tol * o.tol;
+  const double itol = o.inner_tol > 0 ? o.inner_tol : 1e-4;
+  sp.inner_rel2 = itol * itol;
+  sp.k_max = o.k_max;
+  sp.mixed = prec == PF_MIXED;
+  PF_CUDA(cudaMemcpyAsync(b.params, &sp, sizeof(sp), cudaMemcpyHostToDevice, s));
+  const bool warm = o.warm_start && b.solved;
+  std::vector<VarState> st(b.nv);
+  for (int v = 0; v < b.nv; ++v) {
+    VarState& S = st[v];
+    memset(&S, 0, sizeof(S));
+    S.phase = PH_RESID;
+    S.status = PF_OK;
+    S.bnorm2 = (b.bnorm2_unit[v] >= 0.0) ? b.bnorm2_unit[v] * U * U : -1.0;
+    if (warm && S.bnorm2 < 0) S.bnorm2 = -1.0;
+  }
+  PF_CUDA(cudaMemcpyAsync(b.state, st.data(), b.nv * sizeof(VarState), cudaMemcpyHostToDevice, s));
+  PF_CUDA(cudaMemsetAsync(b.n_done, 0, sizeof(int), s));
+  const int B = std::max(1, b.B);
+  if (!warm) PF_CUDA(cudaMemsetAsync(b.sb64, 0, 4 * B * sizeof(double), s));
+  else PF_CUDA(cudaMemsetAsync(b.sb64 + B, 0, 3 * B * sizeof(double), s));
+  PF_CUDA(cudaMemsetAsync(b.sb32, 0, 4 * B * sizeof(float), s));
+  if (prec == PF_FP64)
+    k_init<<<(unsigned)b.T, dim3(TX, TY), 0, s>>>(b.d_var, b.tile_var, b.tile_ij, b.tag, b.X, b.Vtot, U, warm, b.x64,
+                                                  b.w64, b.r64, b.p64, b.q64, nullptr, 8);
+  else
+    k_init<<<(unsigned)b.T, dim3(TX, TY), 0, s>>>(b.d_var, b.tile_var, b.tile_ij, b.tag, b.X, b.Vtot, U, warm, b.x64,
+                                                  b.w64, b.r32, b.p32, b.q32, b.x32, 4);
+  PF_CUDA(cudaGetLastError());
+  PF_CUDA(cudaEventRecord(b.ev[3], s));
+  launch_resid_only(b, prec, s);
+  int chunk = o.chunk > 0 ? o.chunk : 0;
+  if (chunk == 0) {
+    long long nodes = 0;
+    for (auto& H : b.hv) nodes += H.stats.n_nodes;
+    chunk = nodes > (8LL << 20) ? 16 : (nodes > (1LL << 20) ? 64 : 256);
+  }
+  cudaGraphExec_t ex = get_graph(b, prec, chunk);
+  int* hdone = nullptr;
+  PF_CUDA(cudaMallocHost(&hdone, sizeof(int)));
+  double cg_ms = 0, res_ms = 0;
+  long long launches = 0, rlaunches = 1;
+  const long long max_chunks = o.k_max / chunk + 1000;
+  for (long long c = 0; c < max_chunks; ++c) {
+    PF_CUDA(cudaGraphLaunch(ex, s));
+    PF_CUDA(cudaMemcpyAsync(hdone, b.n_done, sizeof(int), cudaMemcpyDeviceToHost, s));
+    PF_CUDA(cudaStreamSynchronize(s));
+    float ms1 = 0, ms2 = 0;
+    PF_CUDA(cudaEventElapsedTime(&ms1, b.ev[0], b.ev[1]));
+    PF_CUDA(cudaEventElapsedTime(&ms2, b.ev[1], b.ev[2]));
+    cg_ms += ms1;
+    res_ms += ms2;
+    launches += chunk;
+    rlaunches += 1;
+    if (*hdone >= b.nv) break;
+  }
+  PF_CUDA(cudaEventRecord(b.ev[4], s));
+  PF_CUDA(cudaFreeHost(hdone));
+  std::vector<VarState> fin(b.nv);
+  PF_CUDA(cudaMemcpyAsync(fin.data(), b.state, b.nv * sizeof(VarState), cudaMemcpyDeviceToHost, s));
+  PF_CUDA(cudaStreamSynchronize(s));
+  float tot = 0;
+  PF_CUDA(cudaEventElapsedTime(&tot, b.ev[3], b.ev[4]));
+  b.solved = true;
+  b.lastU = U;
+  b.last_precision = prec;
+  pf_status ret = PF_OK;
+  double bytes_done = 0.0;
+  for (int v = 0; v < b.nv; ++v) {
+    const VarState& S = fin[v];
+    const pf_mesh_stats& M = b.hv[v].stats;
+    if (S.phase != PH_DONE && ret == PF_OK) ret = PF_ENOT_CONVERGED;
+    if (S.status != PF_OK && ret == PF_OK) ret = S.status;
+    if (b.bnorm2_unit[v] < 0 && S.bnorm2 >= 0 && U != 0) b.bnorm2_unit[v] = S.bnorm2 / (U * U);
+    const double per_node_free = prec == PF_MIXED ? 32.0 : 64.0;
+    const double per_body = prec == PF_MIXED ? 8.0 : 12.0;
+    const double per_gen = prec == PF_MIXED ? 24.0 : 48.0;
+    const double bv = per_node_free * M.n_free + per_body * M.n_body_nodes + 1.0 * M.n_nodes +
+                      per_gen * M.n_general_cells;
+    bytes_done += bv * (double)S.iters;
+    if (info) {
+      info[v].iters = S.iters;
+      info[v].refinements = std::max(0, S.n_resid - 1);
+      info[v].status = S.phase == PH_DONE ? S.status : PF_ENOT_CONVERGED;
+      info[v].rel_true_residual = S.bnorm2 > 0 ? std::sqrt(S.rr64 / S.bnorm2) : 0.0;
+      info[v].n_dof = M.n_dof;
+    }
+  }
+  b.timing.cg_kernel_ms = cg_ms;
+  b.timing.cg_launches = launches;
+  b.timing.residual_kernel_ms = res_ms;
+  b.timing.residual_launches = rlaunches;
+  b.timing.solve_ms = tot;
+  b.timing.cg_bytes_per_launch = launches > 0 ? bytes_done / (double)launches : 0.0;
+  if (dev_psi) export_psi(b, dev_psi);
+  if (body_psi && b.B) {
+    PF_CUDA(cudaMemcpyAsync(body_psi, b.sb64, b.B * sizeof(double), cudaMemcpyDeviceToHost, s));
+    PF_CUDA(cudaStreamSynchronize(s));
+  }
+  return ret;
+}
+
+void export_psi(Batch& b, double* dev_psi) {
+  long long* lb = lbase_cached(b);
+  k_export_psi<<<dim3(256, b.nv), 256, 0, b.stream>>>(b.d_var, b.nv, lb, b.tag, b.bid, b.x64, b.sb64, dev_psi);
+  PF_CUDA(cudaGetLastError());
+}
+
+void body_values(Batch& b, std::vector<double>& C) {
+  C.assign(b.B, 0.0);
+  if (!b.B || !b.sb64) return;
+  PF_CUDA(cudaMemcpyAsync(C.data(), b.sb64, b.B * sizeof(double), cudaMemcpyDeviceToHost, b.stream));
+  PF_CUDA(cudaStreamSynchronize(b.stream));
+}
+
+}  // namespace pfq4

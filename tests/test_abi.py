@@ -1,0 +1,58 @@
+"""CPU checks of the C-ABI library: it builds, loads, and exports every entry point
+declared in include/pfq4.h (no compute calls: no GPU here)."""
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "pfq4.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(pf_[a-z_]+)\s*\(", src)) - {"pf_alloc_fn", "pf_free_fn"})
+
+
+@pytest.fixture(scope="module")
+def lib_path():
+    from paper_2512_12232_gb300 import build
+    return build.build()
+
+
+def test_library_exports_every_declared_symbol(lib_path):
+    out = subprocess.run(["nm", "-D", "--defined-only", lib_path], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (pf_[a-z_]+)", out))
+    missing = [f for f in declared_functions() if f not in exported]
+    assert not missing, missing
+
+
+def test_ctypes_binding_covers_the_header(lib_path):
+    from paper_2512_12232_gb300 import _lib
+    lib = _lib.load(lib_path)
+    assert sorted(_lib.EXPORTED) == declared_functions()
+    for name in _lib.EXPORTED:
+        assert hasattr(lib, name)
+
+
+def test_error_path_without_gpu(lib_path):
+    """Argument validation happens before any device work and reports PF_EINVAL."""
+    import ctypes as C
+    from paper_2512_12232_gb300 import _lib
+    lib = _lib.load(lib_path)
+    assert lib.pf_batch_build(None, None, None, 0, 0, None, None, None) == _lib.PF_EINVAL
+    assert b"NULL" in lib.pf_last_error() or len(lib.pf_last_error()) > 0
+    assert lib.pf_set_allocator(_lib.ALLOC_FN(), _lib.FREE_FN(), None) == _lib.PF_OK
+    assert lib.pf_workspace_bytes(None) == 0
+
+
+def test_product_path_fails_loudly_without_library(tmp_path):
+    from paper_2512_12232_gb300 import _lib
+    saved = _lib._lib
+    _lib._lib = None
+    try:
+        with pytest.raises(RuntimeError, match="missing"):
+            _lib.load(str(tmp_path / "nope.so"))
+    finally:
+        _lib._lib = saved

@@ -1,0 +1,118 @@
+"""GPU parity of the solve against the oracle's direct solution of the reduced
+system, in FP64 (rel L2 <= 1e-10, body values to 1e-8) and in mixed precision
+(rel L2 <= 1e-6 after refinement), for single meshes and batches, plus the
+post-processing outputs."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import mesh as OM, post as OP
+from paper_2512_12232_gb300 import workloads as W
+from tests.gpu_util import oracle_solution, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-10
+MIXED_TOL = 1e-6
+BODY_TOL = 1e-8
+
+CASES = [
+    W.single_cylinder(),
+    W.Case(-3.0, 3.0, -2.0, 2.0, 24, 16, np.array([[0.1, 0.05, 0.9]]), 7),
+    W.Case(-4.0, 4.0, -2.0, 2.0, 29, 17, np.array([[-1.6, 0.2, 0.7], [1.3, -0.4, 0.55]]), 11, bc=(1, 1, 0, 0)),
+    W.five_cylinder_case(0.25, 256, 128, 40),
+    W.five_cylinder_case(1.0, 200, 100, 30),
+]
+IDS = [c.name or f"{c.nx}x{c.ny}" for c in CASES]
+
+
+@pytest.fixture(scope="module")
+def api():
+    from paper_2512_12232_gb300 import api
+    return api
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_solve_matches_oracle(api, case, prec):
+    U = 1.3
+    m, s, u, psi_ref = oracle_solution(case, U)
+    C_ref = u[s.n_free:]
+    p = api.PF_FP64 if prec == "fp64" else api.PF_MIXED
+    with api.mesh_build(case.grid, case.bodies, case.sweeps, case.bc) as g:
+        res = api.psi_solve(g, U=U, tol=1e-13 if prec == "fp64" else 1e-12, precision=p)
+    psi = res.psi.cpu().numpy()
+    err = rel_l2(psi, psi_ref)
+    assert err <= (FP64_TOL if prec == "fp64" else MIXED_TOL), err
+    np.testing.assert_allclose(res.body_psi, C_ref, rtol=0, atol=BODY_TOL)
+    assert res.info[0]["status"] == 0
+    assert res.info[0]["rel_true_residual"] <= (1e-13 if prec == "fp64" else 1e-12)
+    assert res.info[0]["n_dof"] == s.n_dof
+
+
+def test_batched_solve_equals_single_solves(api):
+    cases = W.parametric_sweep(5, seed=4, nx_choices=(128, 160, 192, 224))
+    with api.batch_build(cases) as g:
+        res = api.psi_solve(g, U=1.0, tol=1e-13, precision=api.PF_FP64)
+        psi_b = res.psi.cpu().numpy()
+        offs = g.node_offsets
+    for v, c in enumerate(cases):
+        m, s, u, psi_ref = oracle_solution(c, 1.0)
+        assert rel_l2(psi_b[offs[v]:offs[v + 1]], psi_ref) <= FP64_TOL
+        np.testing.assert_allclose(res.body_psi[5 * v:5 * v + 5], u[s.n_free:], rtol=0, atol=BODY_TOL)
+        with api.mesh_build(c.grid, c.bodies, c.sweeps, c.bc) as g1:
+            r1 = api.psi_solve(g1, U=1.0, tol=1e-13, precision=api.PF_FP64)
+        assert rel_l2(psi_b[offs[v]:offs[v + 1]], r1.psi.cpu().numpy()) <= 1e-12
+
+
+def test_mixed_batch_reaches_tolerance_and_matches(api):
+    cases = W.parametric_sweep(4, seed=5, nx_choices=(128, 192, 256))
+    with api.batch_build(cases) as g:
+        res = api.psi_solve(g, U=1.0, tol=1e-8, precision=api.PF_MIXED)
+        psi_b = res.psi.cpu().numpy()
+        offs = g.node_offsets
+    for v, c in enumerate(cases):
+        assert res.info[v]["status"] == 0 and res.info[v]["rel_true_residual"] <= 1e-8
+        m, s, u, psi_ref = oracle_solution(c, 1.0)
+        assert rel_l2(psi_b[offs[v]:offs[v + 1]], psi_ref) <= 1e-4
+
+
+def test_solve_is_deterministic(api):
+    c = W.five_cylinder_case(0.5, 160, 80, 20)
+    outs = []
+    for _ in range(2):
+        with api.mesh_build(c.grid, c.bodies, c.sweeps, c.bc) as g:
+            outs.append(api.psi_solve(g, U=1.0, tol=1e-10, precision=api.PF_MIXED).psi.cpu().numpy())
+    assert np.array_equal(outs[0], outs[1])
+
+
+def test_surface_velocity_and_copfi_match_oracle(api):
+    c = W.five_cylinder_case(0.25, 256, 128, 40)
+    m, s, u, psi_ref = oracle_solution(c, 1.0)
+    C_ref = u[s.n_free:]
+    with api.mesh_build(c.grid, c.bodies, c.sweeps, c.bc) as g:
+        api.psi_solve(g, U=1.0, tol=1e-13, precision=api.PF_FP64)
+        for k in range(5):
+            th, ut = api.surface_velocity(g, 0, k)
+            th_ref, ut_ref = OP.surface_velocity(m, psi_ref, C_ref, k)
+            assert th.size == th_ref.size > 10
+            np.testing.assert_allclose(th, th_ref, rtol=0, atol=1e-9)
+            np.testing.assert_allclose(ut, ut_ref, rtol=1e-8, atol=1e-9)
+        cp, q = api.copfi(g, 0, 3, 4, 1.0)
+    cp_ref, q_ref = OP.copfi(C_ref, c.bodies, 3, 4, 1.0)
+    assert abs(q - q_ref) <= 2 * BODY_TOL and abs(cp - cp_ref) <= 2 * BODY_TOL
+
+
+def test_k_max_reports_not_converged(api):
+    c = W.five_cylinder_case(0.5, 160, 80, 20)
+    with api.mesh_build(c.grid, c.bodies, c.sweeps, c.bc) as g:
+        res = api.psi_solve(g, U=1.0, tol=1e-12, precision=api.PF_FP64, k_max=5, raise_on_failure=False)
+    assert res.status == 3 and res.info[0]["status"] == 3 and res.info[0]["iters"] <= 5 + 256
+
+
+def test_linearity_in_U(api):
+    c = W.five_cylinder_case(0.25, 160, 80, 20)
+    with api.mesh_build(c.grid, c.bodies, c.sweeps, c.bc) as g:
+        a = api.psi_solve(g, U=1.0, tol=1e-13, precision=api.PF_FP64).psi.cpu().numpy()
+        b = api.psi_solve(g, U=-2.5, tol=1e-13, precision=api.PF_FP64).psi.cpu().numpy()
+    assert rel_l2(b, -2.5 * a) <= 1e-11
