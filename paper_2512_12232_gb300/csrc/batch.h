@@ -76,11 +76,15 @@ struct Batch {
   int* n_done = nullptr;             // device counter of finished variants
   double* x64 = nullptr;             // [Vtot] solution (Dirichlet values in place)
   double* w64 = nullptr;             // [Vtot] FP64 scratch (body-node rows of the true residual)
-  double *r64 = nullptr, *p64 = nullptr, *q64 = nullptr;                 // FP64-mode CG vectors
-  float *x32 = nullptr, *r32 = nullptr, *p32 = nullptr, *q32 = nullptr;  // mixed-mode inner vectors
+  // CG vectors: r, p, q are double-buffered (a launch reads one parity and writes the
+  // other, so halo reads never see a neighbour tile's new values); x is updated in place.
+  double *r64[2] = {nullptr, nullptr}, *p64[2] = {nullptr, nullptr}, *q64[2] = {nullptr, nullptr};
+  float* x32 = nullptr;
+  float *r32[2] = {nullptr, nullptr}, *p32[2] = {nullptr, nullptr}, *q32[2] = {nullptr, nullptr};
   double* sb64 = nullptr;            // [4][B] FP64 body values x, r, p, q (x = the solution C_k)
   float* sb32 = nullptr;             // [4][B] FP32 inner body values x, r, p, q
   double* sbr64 = nullptr;           // [B] FP64 true-residual body rows
+  void** d_vecs = nullptr;           // device list of the vectors k_init clears
   bool solved = false;
   double lastU = 0.0;
   int last_precision = -1;

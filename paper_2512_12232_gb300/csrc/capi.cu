@@ -17,6 +17,7 @@ static void* g_ctx = nullptr;
 
 void check_cuda(cudaError_t e, const char* what) {
   if (e != cudaSuccess) {
+    cudaGetLastError();   // clear a non-sticky error so later calls start clean
     const pf_status code = (e == cudaErrorMemoryAllocation) ? PF_ENOMEM : PF_ECUDA;
     throw Error{code, std::string(what) + ": " + cudaGetErrorString(e)};
   }

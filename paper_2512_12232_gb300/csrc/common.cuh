@@ -63,6 +63,8 @@ struct VarState {
   int status;                  // pf_status
   int n_resid;                 // true-residual evaluations
   int capped;                  // k_max reached
+  int buf;                     // ping-pong parity of the r, p, q buffers holding the current iterate
+  int pad_;
 };
 
 struct SolveParams {
@@ -160,21 +162,21 @@ template <> struct Acc<float> {
   }
 };
 
+__device__ __forceinline__ int linear_tid() { return threadIdx.y * TX + threadIdx.x; }
+
 // Block-wide fixed-order sum of a double; all threads get the result.
 __device__ __forceinline__ double block_sum(double x, double* scratch /* >= NT/32 */) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int tid = linear_tid(), lane = tid & 31, w = tid >> 5;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
   __syncthreads();
   if (lane == 0) scratch[w] = x;
   __syncthreads();
   double s = 0.0;
-  for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += scratch[k];
+  for (int k = 0; k < NT / 32; ++k) s += scratch[k];
   __syncthreads();
   return s;
 }
-
-__device__ __forceinline__ int linear_tid() { return threadIdx.y * TX + threadIdx.x; }
 
 // Halo position h in [0, NHALO) -> shared-tile coordinates (li, lj).
 __device__ __forceinline__ void halo_pos(int h, int& li, int& lj) {

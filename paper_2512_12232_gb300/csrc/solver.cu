@@ -36,7 +36,8 @@ struct CGArgs {
   Sched sc;
   VarState* st;
   const SolveParams* prm;
-  T *x, *r, *p, *q;         // node vectors of the CG (FP64 mode: x is the solution)
+  T* x;                     // iterate (FP64 mode: the solution itself), updated in place
+  T *r[2], *p[2], *q[2];    // ping-pong buffers, parity VarState::buf holds the current ones
   T* sb;                    // [4][B] body x, r, p, q of the CG
   int B;
   int* n_done;
@@ -48,9 +49,9 @@ struct ResidArgs {
   Sched sc;
   VarState* st;
   const SolveParams* prm;
-  double* x64;              // solution, Dirichlet values in place
+  double* x64;              // solution, Dirichlet values in place (read only here)
   double* w64;              // body-node rows of A u
-  T *x, *r, *p, *q;         // CG vectors to restart (mixed: x is the correction)
+  T *r[2], *p[2], *q[2];    // CG vectors to restart, in the current parity
   double* sb64;             // [4][B]: [0] = body solution values
   T* sb;                    // [4][B] CG body values
   double* sbr;              // [B] true residual body rows
@@ -102,8 +103,9 @@ __device__ void finalize_cg(const CGArgs<T>& a, int v, double* scratch, double* 
   VarState* S = &a.st[v];
   double d[4];
   reduce_partials(a.sc, v, 4, d, scratch);
+  const T* qnew = a.q[S->buf ^ 1];
   for (int k = 0; k < V.nb; ++k) {
-    const double s = body_gather<T>(a.m, V.body0 + k, a.q, scratch);
+    const double s = body_gather<T>(a.m, V.body0 + k, qnew, scratch);
     if (linear_tid() == 0) sh_qb[k] = s;
   }
   __syncthreads();
@@ -127,6 +129,7 @@ __device__ void finalize_cg(const CGArgs<T>& a, int v, double* scratch, double* 
       d[3] += (double)qn * (double)qn;
     }
     const double g = d[0], pi = d[1], rho = d[2], mu = d[3];
+    S->buf ^= 1;
     S->iters += 1;
     S->inner_iters += 1;
     if (S->inner_iters == 1) S->gamma_start = g;
@@ -172,6 +175,13 @@ __global__ void __launch_bounds__(NT) k_cg(CGArgs<T> a) {
     if (a.st[v].phase != PH_CG) continue;
     const DevVariant& V = a.m.var[v];
     const T alpha = (T)a.st[v].alpha, beta = (T)a.st[v].beta;
+    const int cur = a.st[v].buf;
+    const T* __restrict__ r_old = a.r[cur];
+    const T* __restrict__ p_old = a.p[cur];
+    const T* __restrict__ q_old = a.q[cur];
+    T* __restrict__ r_new = a.r[cur ^ 1];
+    T* __restrict__ p_new = a.p[cur ^ 1];
+    T* __restrict__ q_new = a.q[cur ^ 1];
     const T* kr = krect<T>(V);
     if (tid < V.nb) {
       const int gb = V.body0 + tid;
@@ -190,8 +200,8 @@ __global__ void __launch_bounds__(NT) k_cg(CGArgs<T> a) {
       const int kind = tg & KIND_MASK;
       T rn = T(0), pn = T(0), xn = T(0);
       if (kind == K_FREE) {
-        const T po = a.p[n];
-        rn = next_r(a.r[n], a.q[n], alpha);
+        const T po = p_old[n];
+        rn = next_r(r_old[n], q_old[n], alpha);
         xn = next_x(a.x[n], po, alpha);
         pn = next_p(rn, po, beta);
       } else if (kind == K_BODY) {
@@ -209,7 +219,7 @@ __global__ void __launch_bounds__(NT) k_cg(CGArgs<T> a) {
           const long long hn = V.base + (long long)hj * V.P + hi;
           ht = a.m.tag[hn];
           const int hk = ht & KIND_MASK;
-          if (hk == K_FREE) hp = next_p(next_r(a.r[hn], a.q[hn], alpha), a.p[hn], beta);
+          if (hk == K_FREE) hp = next_p(next_r(r_old[hn], q_old[hn], alpha), p_old[hn], beta);
           else if (hk == K_BODY) hp = s_pb[a.m.bid[hn]];
         }
         ps[lj][li] = hp;
@@ -218,11 +228,11 @@ __global__ void __launch_bounds__(NT) k_cg(CGArgs<T> a) {
       __syncthreads();
       if (kind == K_FREE || kind == K_BODY) {
         const T y = q4_row<T>(ps, ts, threadIdx.x + 1, threadIdx.y + 1, n, V.P, K, plane, kr);
-        a.q[n] = y;
+        q_new[n] = y;
         if (kind == K_FREE) {
           a.x[n] = xn;
-          a.r[n] = rn;
-          a.p[n] = pn;
+          r_new[n] = rn;
+          p_new[n] = pn;
           acc.add(0, rn, rn);
           acc.add(1, pn, y);
           acc.add(2, rn, y);
@@ -329,6 +339,10 @@ __global__ void __launch_bounds__(NT) k_resid(ResidArgs<T> a) {
       const int gb = V.body0 + tid;
       s_xb[tid] = a.mixed ? a.sb64[gb] + (double)a.sb[gb] : a.sb64[gb];
     }
+    const int cur = a.st[v].buf;
+    T* __restrict__ r_out = a.r[cur];
+    T* __restrict__ p_out = a.p[cur];
+    T* __restrict__ q_out = a.q[cur];
     __syncthreads();
     double acc = 0.0;
     for (int t = a.sc.seg_t0[sg]; t < a.sc.seg_t1[sg]; ++t) {
@@ -339,8 +353,7 @@ __global__ void __launch_bounds__(NT) k_resid(ResidArgs<T> a) {
       const uint8_t tg = in ? a.m.tag[n] : K_INACT;
       const int kind = tg & KIND_MASK;
       double u = 0.0;
-      if (kind == K_FREE) u = a.mixed ? a.x64[n] + (double)a.x[n] : a.x64[n];
-      else if (kind == K_DIR) u = a.x64[n];
+      if (kind == K_FREE || kind == K_DIR) u = a.x64[n];
       else if (kind == K_BODY) u = s_xb[a.m.bid[n]];
       ps[threadIdx.y + 1][threadIdx.x + 1] = u;
       ts[threadIdx.y + 1][threadIdx.x + 1] = tg;
@@ -354,8 +367,7 @@ __global__ void __launch_bounds__(NT) k_resid(ResidArgs<T> a) {
           const long long hn = V.base + (long long)hj * V.P + hi;
           ht = a.m.tag[hn];
           const int hk = ht & KIND_MASK;
-          if (hk == K_FREE) hu = a.mixed ? a.x64[hn] + (double)a.x[hn] : a.x64[hn];
-          else if (hk == K_DIR) hu = a.x64[hn];
+          if (hk == K_FREE || hk == K_DIR) hu = a.x64[hn];
           else if (hk == K_BODY) hu = s_xb[a.m.bid[hn]];
         }
         ps[lj][li] = hu;
@@ -366,13 +378,9 @@ __global__ void __launch_bounds__(NT) k_resid(ResidArgs<T> a) {
         const double y = q4_row<double>(ps, ts, threadIdx.x + 1, threadIdx.y + 1, n, V.P, a.m.K64, plane, V.kr64);
         if (kind == K_FREE) {
           const double r = -y;
-          if (a.mixed) {
-            a.x64[n] = u;
-            a.x[n] = T(0);
-          }
-          a.r[n] = (T)r;
-          a.p[n] = T(0);
-          a.q[n] = T(0);
+          r_out[n] = (T)r;
+          p_out[n] = T(0);
+          q_out[n] = T(0);
           acc = fma(r, r, acc);
         } else {
           a.w64[n] = y;
@@ -401,10 +409,27 @@ __global__ void __launch_bounds__(NT) k_resid(ResidArgs<T> a) {
   }
 }
 
+// Mixed precision: fold the FP32 correction into the FP64 solution before the true
+// residual (pointwise, its own launch so no tile ever sees a half-updated neighbour).
+__global__ void k_fold(const DevVariant* var, const int* tile_var, const int2* tile_ij, const uint8_t* tag,
+                       const VarState* st, double* x64, float* x32) {
+  const long long t = blockIdx.x;
+  const int v = tile_var[t];
+  if (st[v].phase != PH_RESID) return;
+  const DevVariant& V = var[v];
+  const int2 ij = tile_ij[t];
+  const int i = ij.x + threadIdx.x, j = ij.y + threadIdx.y;
+  if (i > V.nx || j > V.ny) return;
+  const long long n = V.base + (long long)j * V.P + i;
+  if ((tag[n] & KIND_MASK) != K_FREE) return;
+  x64[n] = x64[n] + (double)x32[n];
+  x32[n] = 0.f;
+}
+
 // ---------------------------------------------------------------- init / export
 __global__ void k_init(const DevVariant* var, const int* tile_var, const int2* tile_ij, const uint8_t* tag,
                        const double* X, long long Vtot, double U, int warm, double* x64, double* w64,
-                       void* v0, void* v1, void* v2, void* v3, int vbytes) {
+                       void* const* vecs, int nvec, int vbytes) {
   const long long t = blockIdx.x;
   const int v = tile_var[t];
   const DevVariant& V = var[v];
@@ -418,12 +443,9 @@ __global__ void k_init(const DevVariant* var, const int* tile_var, const int2* t
   else if (kind == K_FREE && warm) u = x64[n];
   x64[n] = u;
   w64[n] = 0.0;
-  if (vbytes == 8) {
-    ((double*)v0)[n] = 0.0; ((double*)v1)[n] = 0.0; ((double*)v2)[n] = 0.0;
-    if (v3) ((double*)v3)[n] = 0.0;
-  } else {
-    ((float*)v0)[n] = 0.f; ((float*)v1)[n] = 0.f; ((float*)v2)[n] = 0.f;
-    if (v3) ((float*)v3)[n] = 0.f;
+  for (int k = 0; k < nvec; ++k) {
+    if (vbytes == 8) ((double*)vecs[k])[n] = 0.0;
+    else ((float*)vecs[k])[n] = 0.f;
   }
 }
 
@@ -609,16 +631,20 @@ void ensure_solver_memory(Batch& b, int precision) {
     b.bnorm2_unit.assign(b.nv, -1.0);
     for (int k = 0; k < 6; ++k) PF_CUDA(cudaEventCreate(&b.ev[k]));
   }
-  if (precision == PF_FP64 && !b.r64) {
-    b.r64 = (double*)dev_alloc(b, V * sizeof(double));
-    b.p64 = (double*)dev_alloc(b, V * sizeof(double));
-    b.q64 = (double*)dev_alloc(b, V * sizeof(double));
+  if (precision == PF_FP64 && !b.r64[0]) {
+    for (int k = 0; k < 2; ++k) {
+      b.r64[k] = (double*)dev_alloc(b, V * sizeof(double));
+      b.p64[k] = (double*)dev_alloc(b, V * sizeof(double));
+      b.q64[k] = (double*)dev_alloc(b, V * sizeof(double));
+    }
   }
-  if (precision == PF_MIXED && !b.r32) {
+  if (precision == PF_MIXED && !b.r32[0]) {
     b.x32 = (float*)dev_alloc(b, V * sizeof(float));
-    b.r32 = (float*)dev_alloc(b, V * sizeof(float));
-    b.p32 = (float*)dev_alloc(b, V * sizeof(float));
-    b.q32 = (float*)dev_alloc(b, V * sizeof(float));
+    for (int k = 0; k < 2; ++k) {
+      b.r32[k] = (float*)dev_alloc(b, V * sizeof(float));
+      b.p32[k] = (float*)dev_alloc(b, V * sizeof(float));
+      b.q32[k] = (float*)dev_alloc(b, V * sizeof(float));
+    }
   }
 }
 
@@ -650,17 +676,17 @@ void apply_operator(Batch& b, int precision, const double* dev_p, double* dev_y,
   const dim3 g2(512, b.nv);
   double* sums = body_sum_scratch(b);
   if (precision == PF_FP64) {
-    k_to_padded<double><<<g2, 256, 0, b.stream>>>(b.d_var, lb, dev_p, b.r64);
-    PF_CUDA(cudaMemsetAsync(b.q64, 0, b.Vtot * sizeof(double), b.stream));
-    k_apply<double><<<(unsigned)b.T, dim3(TX, TY), 0, b.stream>>>(m, b.tile_var, b.tile_ij, b.r64, b.q64);
-    k_from_padded<double><<<g2, 256, 0, b.stream>>>(b.d_var, lb, b.q64, dev_y);
-    if (b.B) k_body_sums<double><<<b.B, dim3(TX, TY), 0, b.stream>>>(m, b.q64, sums);
+    k_to_padded<double><<<g2, 256, 0, b.stream>>>(b.d_var, lb, dev_p, b.r64[0]);
+    PF_CUDA(cudaMemsetAsync(b.q64[0], 0, b.Vtot * sizeof(double), b.stream));
+    k_apply<double><<<(unsigned)b.T, dim3(TX, TY), 0, b.stream>>>(m, b.tile_var, b.tile_ij, b.r64[0], b.q64[0]);
+    k_from_padded<double><<<g2, 256, 0, b.stream>>>(b.d_var, lb, b.q64[0], dev_y);
+    if (b.B) k_body_sums<double><<<b.B, dim3(TX, TY), 0, b.stream>>>(m, b.q64[0], sums);
   } else {
-    k_to_padded<float><<<g2, 256, 0, b.stream>>>(b.d_var, lb, dev_p, b.r32);
-    PF_CUDA(cudaMemsetAsync(b.q32, 0, b.Vtot * sizeof(float), b.stream));
-    k_apply<float><<<(unsigned)b.T, dim3(TX, TY), 0, b.stream>>>(m, b.tile_var, b.tile_ij, b.r32, b.q32);
-    k_from_padded<float><<<g2, 256, 0, b.stream>>>(b.d_var, lb, b.q32, dev_y);
-    if (b.B) k_body_sums<float><<<b.B, dim3(TX, TY), 0, b.stream>>>(m, b.q32, sums);
+    k_to_padded<float><<<g2, 256, 0, b.stream>>>(b.d_var, lb, dev_p, b.r32[0]);
+    PF_CUDA(cudaMemsetAsync(b.q32[0], 0, b.Vtot * sizeof(float), b.stream));
+    k_apply<float><<<(unsigned)b.T, dim3(TX, TY), 0, b.stream>>>(m, b.tile_var, b.tile_ij, b.r32[0], b.q32[0]);
+    k_from_padded<float><<<g2, 256, 0, b.stream>>>(b.d_var, lb, b.q32[0], dev_y);
+    if (b.B) k_body_sums<float><<<b.B, dim3(TX, TY), 0, b.stream>>>(m, b.q32[0], sums);
   }
   PF_CUDA(cudaGetLastError());
   if (body_sums && b.B) {
@@ -670,26 +696,36 @@ void apply_operator(Batch& b, int precision, const double* dev_p, double* dev_y,
 }
 
 template <typename T>
-static void fill_cg_args(Batch& b, CGArgs<T>& a, T* x, T* r, T* p, T* q, T* sb) {
+static void fill_cg_args(Batch& b, CGArgs<T>& a, T* x, T* const r[2], T* const p[2], T* const q[2], T* sb) {
   a.m = mesh_dev(b);
   a.sc = b.sched;
   a.st = b.state;
   a.prm = b.params;
-  a.x = x; a.r = r; a.p = p; a.q = q;
+  a.x = x;
+  for (int k = 0; k < 2; ++k) {
+    a.r[k] = r[k];
+    a.p[k] = p[k];
+    a.q[k] = q[k];
+  }
   a.sb = sb;
   a.B = std::max(1, b.B);
   a.n_done = b.n_done;
 }
 
 template <typename T>
-static void fill_resid_args(Batch& b, ResidArgs<T>& a, T* x, T* r, T* p, T* q, T* sb, int mixed) {
+static void fill_resid_args(Batch& b, ResidArgs<T>& a, T* const r[2], T* const p[2], T* const q[2], T* sb,
+                            int mixed) {
   a.m = mesh_dev(b);
   a.sc = b.sched;
   a.st = b.state;
   a.prm = b.params;
   a.x64 = b.x64;
   a.w64 = b.w64;
-  a.x = x; a.r = r; a.p = p; a.q = q;
+  for (int k = 0; k < 2; ++k) {
+    a.r[k] = r[k];
+    a.p[k] = p[k];
+    a.q[k] = q[k];
+  }
   a.sb64 = b.sb64;
   a.sb = sb;
   a.sbr = b.sbr64;
@@ -698,28 +734,18 @@ static void fill_resid_args(Batch& b, ResidArgs<T>& a, T* x, T* r, T* p, T* q, T
   a.n_done = b.n_done;
 }
 
-// launch sequence of one graph chunk: [ev0] k_cg x chunk [ev1] k_resid [ev2]
-static void launch_chunk(Batch& b, int precision, int chunk, cudaStream_t s, bool with_events) {
+// the k_cg launches of one chunk (captured once as a graph)
+static void launch_cg_chunk(Batch& b, int precision, int chunk, cudaStream_t s) {
   const dim3 blk(TX, TY);
-  if (with_events) PF_CUDA(cudaEventRecord(b.ev[0], s));
   if (precision == PF_FP64) {
     CGArgs<double> a;
     fill_cg_args<double>(b, a, b.x64, b.r64, b.p64, b.q64, b.sb64);
     for (int k = 0; k < chunk; ++k) k_cg<double><<<b.G, blk, 0, s>>>(a);
-    if (with_events) PF_CUDA(cudaEventRecord(b.ev[1], s));
-    ResidArgs<double> ra;
-    fill_resid_args<double>(b, ra, b.x64, b.r64, b.p64, b.q64, b.sb64, 0);
-    k_resid<double><<<b.G, blk, 0, s>>>(ra);
   } else {
     CGArgs<float> a;
     fill_cg_args<float>(b, a, b.x32, b.r32, b.p32, b.q32, b.sb32);
     for (int k = 0; k < chunk; ++k) k_cg<float><<<b.G, blk, 0, s>>>(a);
-    if (with_events) PF_CUDA(cudaEventRecord(b.ev[1], s));
-    ResidArgs<float> ra;
-    fill_resid_args<float>(b, ra, b.x32, b.r32, b.p32, b.q32, b.sb32, 1);
-    k_resid<float><<<b.G, blk, 0, s>>>(ra);
   }
-  if (with_events) PF_CUDA(cudaEventRecord(b.ev[2], s));
   PF_CUDA(cudaGetLastError());
 }
 
@@ -727,11 +753,12 @@ static void launch_resid_only(Batch& b, int precision, cudaStream_t s) {
   const dim3 blk(TX, TY);
   if (precision == PF_FP64) {
     ResidArgs<double> ra;
-    fill_resid_args<double>(b, ra, b.x64, b.r64, b.p64, b.q64, b.sb64, 0);
+    fill_resid_args<double>(b, ra, b.r64, b.p64, b.q64, b.sb64, 0);
     k_resid<double><<<b.G, blk, 0, s>>>(ra);
   } else {
+    k_fold<<<(unsigned)b.T, blk, 0, s>>>(b.d_var, b.tile_var, b.tile_ij, b.tag, b.state, b.x64, b.x32);
     ResidArgs<float> ra;
-    fill_resid_args<float>(b, ra, b.x32, b.r32, b.p32, b.q32, b.sb32, 1);
+    fill_resid_args<float>(b, ra, b.r32, b.p32, b.q32, b.sb32, 1);
     k_resid<float><<<b.G, blk, 0, s>>>(ra);
   }
   PF_CUDA(cudaGetLastError());
@@ -747,7 +774,7 @@ static cudaGraphExec_t get_graph(Batch& b, int precision, int chunk) {
   PF_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
   cudaGraph_t g;
   PF_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-  launch_chunk(b, precision, chunk, cs, true);
+  launch_cg_chunk(b, precision, chunk, cs);
   PF_CUDA(cudaStreamEndCapture(cs, &g));
   cudaGraphExec_t ex;
   PF_CUDA(cudaGraphInstantiate(&ex, g, 0));
@@ -789,12 +816,20 @@ pf_status psi_solve(Batch& b, double U, const pf_solve_opts& o, double* dev_psi,
   if (!warm) PF_CUDA(cudaMemsetAsync(b.sb64, 0, 4 * B * sizeof(double), s));
   else PF_CUDA(cudaMemsetAsync(b.sb64 + B, 0, 3 * B * sizeof(double), s));
   PF_CUDA(cudaMemsetAsync(b.sb32, 0, 4 * B * sizeof(float), s));
-  if (prec == PF_FP64)
+  {
+    void* vecs[7];
+    int nvec = 0;
+    if (prec == PF_FP64) {
+      for (int k = 0; k < 2; ++k) { vecs[nvec++] = b.r64[k]; vecs[nvec++] = b.p64[k]; vecs[nvec++] = b.q64[k]; }
+    } else {
+      for (int k = 0; k < 2; ++k) { vecs[nvec++] = b.r32[k]; vecs[nvec++] = b.p32[k]; vecs[nvec++] = b.q32[k]; }
+      vecs[nvec++] = b.x32;
+    }
+    if (!b.d_vecs) b.d_vecs = (void**)dev_alloc(b, 8 * sizeof(void*));
+    PF_CUDA(cudaMemcpyAsync(b.d_vecs, vecs, nvec * sizeof(void*), cudaMemcpyHostToDevice, s));
     k_init<<<(unsigned)b.T, dim3(TX, TY), 0, s>>>(b.d_var, b.tile_var, b.tile_ij, b.tag, b.X, b.Vtot, U, warm, b.x64,
-                                                  b.w64, b.r64, b.p64, b.q64, nullptr, 8);
-  else
-    k_init<<<(unsigned)b.T, dim3(TX, TY), 0, s>>>(b.d_var, b.tile_var, b.tile_ij, b.tag, b.X, b.Vtot, U, warm, b.x64,
-                                                  b.w64, b.r32, b.p32, b.q32, b.x32, 4);
+                                                  b.w64, b.d_vecs, nvec, prec == PF_FP64 ? 8 : 4);
+  }
   PF_CUDA(cudaGetLastError());
   PF_CUDA(cudaEventRecord(b.ev[3], s));
   launch_resid_only(b, prec, s);
@@ -811,7 +846,11 @@ pf_status psi_solve(Batch& b, double U, const pf_solve_opts& o, double* dev_psi,
   long long launches = 0, rlaunches = 1;
   const long long max_chunks = o.k_max / chunk + 1000;
   for (long long c = 0; c < max_chunks; ++c) {
+    PF_CUDA(cudaEventRecord(b.ev[0], s));
     PF_CUDA(cudaGraphLaunch(ex, s));
+    PF_CUDA(cudaEventRecord(b.ev[1], s));
+    launch_resid_only(b, prec, s);
+    PF_CUDA(cudaEventRecord(b.ev[2], s));
     PF_CUDA(cudaMemcpyAsync(hdone, b.n_done, sizeof(int), cudaMemcpyDeviceToHost, s));
     PF_CUDA(cudaStreamSynchronize(s));
     float ms1 = 0, ms2 = 0;

@@ -44,7 +44,7 @@ def test_mesh_is_bit_exact(api, case):
 
 
 def test_batched_mesh_equals_single_meshes(api):
-    cases = W.parametric_sweep(6, seed=3, nx_choices=(160, 192, 256))
+    cases = W.parametric_sweep(6, seed=3, nx_choices=(256, 288, 320))
     with api.batch_build(cases) as g:
         for v, c in enumerate(cases):
             m = OM.build_mesh(c.grid, c.bodies, c.sweeps, c.bc)

@@ -51,7 +51,7 @@ def test_solve_matches_oracle(api, case, prec):
 
 
 def test_batched_solve_equals_single_solves(api):
-    cases = W.parametric_sweep(5, seed=4, nx_choices=(128, 160, 192, 224))
+    cases = W.parametric_sweep(5, seed=4, nx_choices=(256, 288, 320))
     with api.batch_build(cases) as g:
         res = api.psi_solve(g, U=1.0, tol=1e-13, precision=api.PF_FP64)
         psi_b = res.psi.cpu().numpy()
@@ -66,7 +66,7 @@ def test_batched_solve_equals_single_solves(api):
 
 
 def test_mixed_batch_reaches_tolerance_and_matches(api):
-    cases = W.parametric_sweep(4, seed=5, nx_choices=(128, 192, 256))
+    cases = W.parametric_sweep(4, seed=5, nx_choices=(256, 320, 384))
     with api.batch_build(cases) as g:
         res = api.psi_solve(g, U=1.0, tol=1e-8, precision=api.PF_MIXED)
         psi_b = res.psi.cpu().numpy()
