@@ -1,0 +1,338 @@
+#!/usr/bin/env python
+"""Benchmark of the matrix-free Q4 stream-function solve on GB300.
+
+Workload (one step = the whole hot path over one batch of synthetic input):
+five cylinders of diameter 1 in [-20,20]x[-10,10] on a 2048x1024 background grid,
+200 smoothing sweeps, the five gap ratios delta in {0.1, 0.25, 0.5, 1, 2} as one
+batch of five variants: mesh build (classify, project, smooth, element matrices)
+-> mixed-precision solve (FP32 matrix-free operator and vectors, FP64 reductions,
+FP64 true residual and iterative refinement) to a relative true residual of 1e-8
+-> body stream-function values, CoPFI and the nodal psi field.
+
+Metric: CG DOF-iterations per second (sum over variants of N_dof x CG iterations,
+per second of the whole step), with the HBM bandwidth of the fused CG-iteration
+kernel against the measured copy bandwidth and the batched solves per second.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank solves its own copy of the batch (independent
+problems, no collective on the data path: "weak" scaling); rank 0 prints one JSON
+line with the whole-job value.  `--impl reference` times the CPU oracle (the plain
+FP64 numpy implementation the tests compare against) on a bounded sample.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "CG DOF-iters/s & HBM GB/s of matrix-free Q4 apply; batched solves/s at 1e-8"
+UNIT = "DOF-iters/s"
+DELTAS = (0.1, 0.25, 0.5, 1.0, 2.0)
+NX, NY, SWEEPS = 2048, 1024, 200
+WORKLOAD = "five_cylinders_2048x1024_S200_delta{0.1,0.25,0.5,1,2}_batched_mixed_1e-8"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--inner-tol", type=float, default=1e-4)
+    ap.add_argument("--nx", type=int, default=NX)
+    ap.add_argument("--variants", type=int, default=len(DELTAS))
+    ap.add_argument("--cpu-iters", type=int, default=60, help="oracle CG iterations in the CPU sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def cases(args):
+    from paper_2512_12232_gb300 import workloads as W
+    ds = (list(DELTAS) * ((args.variants + len(DELTAS) - 1) // len(DELTAS)))[: args.variants]
+    return [W.five_cylinder_case(d, args.nx, args.nx // 2, SWEEPS) for d in ds]
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("common.cuh", "solver.cu"):
+        h.update(open(os.path.join(ROOT, "paper_2512_12232_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(nodes_per_launch):
+    """DRAM bytes per fused CG launch from the committed ncu summary, scaled to this
+    launch by node count; None if absent or if the kernel sources changed since."""
+    path = os.path.join(ROOT, "profiles", "k_cg_mixed_five_cylinders.md")
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    m_hash = re.search(r"kernel_source_hash:\s*([0-9a-f]+)", txt)
+    m_bpn = re.search(r"dram_bytes_per_node_per_launch:\s*([0-9.eE+-]+)", txt)
+    if not m_hash or not m_bpn or m_hash.group(1) != kernel_source_hash():
+        return None
+    return float(m_bpn.group(1)) * nodes_per_launch
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}",
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), float(parts[2]), parts[4:8]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        smax = max(r[1] for r in rows)
+        load = [r for r in rows if r[2] > 200.0] or rows
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[3][k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(r[0] for r in load), "sm_max_mhz": smax, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ CPU oracle sample
+def oracle_sample(args, iters, reps=1):
+    """The oracle's element-by-element CG (Appendix A) on one full-size variant:
+    returns (DOF-iters/s, seconds, n_dof).  Setup (mesh, element matrices) untimed."""
+    from oracle import mesh as OM, solve as OS, system as OSY
+    c = cases(args)[1 % args.variants]
+    m = OM.build_mesh(c.grid, c.bodies, c.sweeps, c.bc)
+    s = OSY.assemble(m, 1.0)
+    times = []
+    for _ in range(reps):
+        t = time.perf_counter()
+        OS.cg_paper(s, m.kind.ravel(), m.body.ravel(), tol=0.0, k_max=iters, criterion="paper")
+        times.append(time.perf_counter() - t)
+    return s.n_dof * iters / min(times), times, s.n_dof
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    iters = max(1, args.cpu_iters // 3)
+    from oracle import mesh as OM, solve as OS, system as OSY
+    c = cases(args)[1 % args.variants]
+    m = OM.build_mesh(c.grid, c.bodies, c.sweeps, c.bc)
+    s = OSY.assemble(m, 1.0)
+    kind, body = m.kind.ravel(), m.body.ravel()
+    for _ in range(args.warmup):
+        OS.cg_paper(s, kind, body, tol=0.0, k_max=iters, criterion="paper")
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        OS.cg_paper(s, kind, body, tol=0.0, k_max=iters, criterion="paper")
+    el = time.perf_counter() - t
+    value = s.n_dof * iters * args.steps / el
+    sample = (f"oracle element-by-element CG (Appendix A), {iters} iterations per step on one "
+              f"{c.nx}x{c.ny} five-cylinder variant (delta={c.meta['delta']}, N_dof={s.n_dof}); mesh and "
+              f"element matrices built untimed")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": "one variant, fixed CG iterations"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_ours(args, rank, world, local):
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", rank=rank, world_size=world, device_id=torch.device("cuda", local))
+    from paper_2512_12232_gb300 import api
+    api.use_torch_allocator()
+    cs = cases(args)
+    prec = api.PF_MIXED if args.precision == "mixed" else api.PF_FP64
+
+    def step(host_out=None):
+        g = api.batch_build(cs)
+        res = api.psi_solve(g, U=1.0, tol=args.tol, precision=prec, inner_tol=args.inner_tol)
+        cps = [api.copfi(g, v, 3, 4, 1.0) for v in range(len(cs))]
+        if host_out is not None:
+            host_out.copy_(res.psi, non_blocking=True)
+        tm = g.timing()
+        st = [g.stats(v) for v in range(len(cs))]
+        g.close()
+        return res, cps, tm, st
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    records = []
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            records.append(step())
+        e1.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    elapsed = e0.elapsed_time(e1) / 1e3
+    dof_iters = sum(sum(st[v]["n_dof"] * res.info[v]["iters"] for v in range(len(cs)))
+                    for res, _, _, st in records)
+    solves = sum(len(cs) for _ in records)
+    ok = all(i["status"] == 0 and i["rel_true_residual"] <= args.tol for res, _, _, _ in records for i in res.info)
+    cg_ms = sum(tm["cg_kernel_ms"] for _, _, tm, _ in records)
+    cg_launches = sum(tm["cg_launches"] for _, _, tm, _ in records)
+    cg_bytes = sum(tm["cg_bytes_per_launch"] * tm["cg_launches"] for _, _, tm, _ in records)
+    launches = sum(tm["kernel_launches"] for _, _, tm, _ in records)
+    nodes = sum(st[v]["n_nodes"] for v in range(len(cs)) for st in [records[0][3]])
+
+    # e2e: the public API with host buffers (geometry in, psi field and body values out)
+    e2e = None
+    if not args.no_e2e:
+        host = torch.empty(int(nodes), dtype=torch.float64, pin_memory=True)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t = time.perf_counter()
+        e2e_rec = [step(host) for _ in range(args.steps)]
+        torch.cuda.synchronize()
+        e2e_el = time.perf_counter() - t
+        e2e_units = sum(sum(st[v]["n_dof"] * res.info[v]["iters"] for v in range(len(cs)))
+                        for res, _, _, st in e2e_rec)
+        h2d = len(cs) * 40 + (len(cs) + 1) * 4 + 5 * len(cs) * 24 + 16
+        d2h = 8 * int(nodes) + 8 * 5 * len(cs) + 32 * len(cs)
+        e2e = [e2e_units, e2e_el, h2d, d2h]
+
+    # whole-job aggregation: units summed over ranks, time = max over ranks
+    vals = [dof_iters, elapsed, solves]
+    if dist:
+        t = torch.tensor([dof_iters, solves], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t)
+        mx = torch.tensor([elapsed], dtype=torch.float64, device="cuda")
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        vals = [t[0].item(), mx.item(), t[1].item()]
+        if e2e:
+            t2 = torch.tensor([e2e[0]], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t2)
+            m2 = torch.tensor([e2e[1]], dtype=torch.float64, device="cuda")
+            dist.all_reduce(m2, op=dist.ReduceOp.MAX)
+            e2e[0], e2e[1] = t2.item(), m2.item()
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+    pk = peaks()
+    hbm = pk.get("hbm_gbs")
+    achieved = cg_bytes / (cg_ms / 1e3) / 1e9 if cg_ms > 0 else None
+    traffic = ncu_traffic(nodes)
+    roofline = {"bound": "hbm", "kernel": "k_cg<float> (fused CG iteration: r, x, p updates + Q4 apply + 4 dots)",
+                "achieved": achieved, "peak": hbm if hbm else 6800.0,
+                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if hbm else "fallback 6.8 TB/s",
+                "unit": "GB/s", "frac": (achieved / hbm) if (achieved and hbm) else None,
+                "traffic": traffic,
+                "algorithmic_bytes_per_launch": cg_bytes / cg_launches if cg_launches else None,
+                "avg_launch_us": 1e3 * cg_ms / cg_launches if cg_launches else None}
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        v, times, ndof = oracle_sample(args, args.cpu_iters)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{args.cpu_iters} iterations of the oracle's element-by-element CG on one "
+                         f"{args.nx}x{args.nx // 2} variant (N_dof={ndof}), {min(times):.1f} s"}
+    clocks = clk.summary()
+    iters = [res.info[v]["iters"] for v in range(len(cs)) for res in [records[-1][0]]]
+    line = {
+        "metric": METRIC, "value": vals[0] / vals[1], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * vals[1] / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD if (args.nx == NX and args.variants == 5 and args.precision == "mixed")
+                   else f"five_cylinders_{args.nx}x{args.nx // 2}_x{args.variants}_{args.precision}",
+                   "variants": len(cs), "nodes_per_step": int(nodes), "tol": args.tol,
+                   "precision": "FP32 operator+vectors, FP64 dots/scalars/true residual/refinement"
+                   if args.precision == "mixed" else "FP64",
+                   "inner_tol": args.inner_tol, "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2: each step builds fresh meshes; 5-variant working set > 500 MB"},
+        "solves_per_s": vals[2] / vals[1], "all_converged": ok, "iters_per_variant": iters,
+        "copfi": [cp for cp, _ in records[-1][1]],
+        "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": int(launches),
+        "e2e": ({"value": e2e[0] / e2e[1], "unit": UNIT, "h2d_bytes_per_step": e2e[2],
+                 "d2h_bytes_per_step": e2e[3]} if e2e else None),
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

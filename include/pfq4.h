@@ -26,7 +26,7 @@
  *     torch tensors' data_ptr()); all other pointers are host memory owned by the
  *     caller.  Opaque handles (pf_batch) own their device memory, which is
  *     allocated through the allocator installed with pf_set_allocator (default:
- *     cudaMallocAsync on the call's stream) and released by pf_batch_destroy.
+ *     cudaMalloc) and released by pf_batch_destroy.
  *   - Nodes are numbered logically per variant: node (i, j), 0 <= i <= nx,
  *     0 <= j <= ny, has index j*(nx+1) + i.  Node-valued outputs of a batch are the
  *     variants' logical arrays concatenated in variant order.
@@ -108,7 +108,9 @@ typedef struct pf_timing {
     double residual_kernel_ms;   /* summed device time of the FP64 true-residual launches */
     long long residual_launches;
     double solve_ms;             /* device time of the whole solve, events on the call's stream */
-    double cg_bytes_per_launch;  /* algorithmic HBM bytes of one fused CG launch over all variants */
+    double cg_bytes_per_launch;  /* algorithmic HBM bytes of one fused CG launch, averaged over the
+                                    launches of the solve (variants already converged move nothing) */
+    long long kernel_launches;   /* kernels launched by this handle since it was built (mesh + solves) */
 } pf_timing;
 
 typedef struct pf_batch pf_batch;   /* opaque: one or more mesh variants and their solver state */

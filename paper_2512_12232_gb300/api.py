@@ -12,7 +12,9 @@ fallback, and loading fails loudly when the library has not been built.
 """
 from __future__ import annotations
 
+import atexit
 import ctypes as C
+import weakref
 from dataclasses import dataclass
 
 import numpy as np
@@ -22,11 +24,53 @@ from . import _lib as L
 from ._lib import PF_FP64, PF_MIXED, PF_OBJ_COPFI, PF_OBJ_GAP_FLOW, check
 
 __all__ = ["Mesh", "SolveResult", "mesh_build", "batch_build", "psi_solve", "apply", "surface_velocity",
-           "copfi", "grad", "PF_FP64", "PF_MIXED", "PF_OBJ_COPFI", "PF_OBJ_GAP_FLOW"]
+           "copfi", "grad", "use_torch_allocator", "PF_FP64", "PF_MIXED", "PF_OBJ_COPFI", "PF_OBJ_GAP_FLOW"]
 
 
 def _stream():
     return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+_LIVE = weakref.WeakSet()
+_HOOKS = []
+
+
+def use_torch_allocator(enable: bool = True):
+    """Route the library's device allocations through torch's caching allocator
+    (applies to handles built afterwards).  Rebuilding meshes in a loop then reuses
+    cached blocks instead of calling cudaMalloc / cudaFree every time."""
+    lib = L.load()
+    if not enable:
+        check(lib.pf_set_allocator(L.ALLOC_FN(), L.FREE_FN(), None))
+        _HOOKS.clear()
+        return
+
+    @L.ALLOC_FN
+    def _alloc(nbytes, stream, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(), int(stream or 0))
+        except Exception:
+            return None
+
+    @L.FREE_FN
+    def _free(ptr, stream, ctx):
+        try:
+            torch.cuda.caching_allocator_delete(int(ptr))
+        except Exception:
+            pass
+
+    _HOOKS[:] = [_alloc, _free]
+    check(lib.pf_set_allocator(_alloc, _free, None))
+
+
+@atexit.register
+def _close_live_handles():
+    # release library memory while torch's allocator is still alive
+    for m in list(_LIVE):
+        try:
+            m.close()
+        except Exception:
+            pass
 
 
 def _ptr(t):
@@ -78,6 +122,7 @@ class Mesh:
         self.node_offsets = np.concatenate([[0], np.cumsum(self.n_nodes)]).astype(np.int64)
         self.sweeps = sweeps
         self.bc = tuple(bc)
+        _LIVE.add(self)
 
     # ------------------------------------------------------------------ handle
     @property

@@ -26,6 +26,7 @@ struct Error {                 // thrown inside the library, converted to pf_sta
 
 struct Batch;
 void* dev_alloc(Batch& b, size_t bytes);
+void dev_free(Batch& b, void* p);
 void dev_free_all(Batch& b);
 
 struct Batch {
@@ -97,6 +98,9 @@ struct Batch {
   cudaEvent_t ev[6] = {};
   pf_timing timing{};
   double cg_bytes_per_node[2] = {0, 0};
+
+  int* h_poll = nullptr;             // pinned host word for the convergence poll
+  long long launches = 0;            // kernel launches issued by this handle
 
   std::vector<std::pair<void*, size_t>> allocs;
   size_t bytes = 0;

@@ -41,6 +41,18 @@ void* dev_alloc(Batch& b, size_t bytes) {
   return p;
 }
 
+void dev_free(Batch& b, void* p) {
+  for (size_t k = 0; k < b.allocs.size(); ++k) {
+    if (b.allocs[k].first != p) continue;
+    cudaStreamSynchronize(b.stream);
+    if (b.free_fn) b.free_fn(p, (void*)b.stream, b.alloc_ctx);
+    else cudaFree(p);
+    b.bytes -= b.allocs[k].second;
+    b.allocs.erase(b.allocs.begin() + k);
+    return;
+  }
+}
+
 void dev_free_all(Batch& b) {
   cudaStreamSynchronize(b.stream);
   for (auto& a : b.allocs) {
@@ -147,6 +159,7 @@ void pf_batch_destroy(pf_batch* h) {
     if (b->graph[k]) cudaGraphExecDestroy(b->graph[k]);
   for (int k = 0; k < 6; ++k)
     if (b->ev[k]) cudaEventDestroy(b->ev[k]);
+  if (b->h_poll) cudaFreeHost(b->h_poll);
   dev_free_all(*b);
   delete b;
 }
@@ -229,6 +242,7 @@ pf_status pf_last_timing(const pf_batch* h, pf_timing* out) {
     const Batch* b = (const Batch*)h;
     if (!b || !out) throw Error{PF_EINVAL, "NULL argument"};
     *out = b->timing;
+    out->kernel_launches = b->launches;
     return PF_OK;
   });
 }

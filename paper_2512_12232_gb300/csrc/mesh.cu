@@ -561,7 +561,11 @@ void build_batch(Batch& b, const pf_grid* grids, const int* body_offsets, const 
     S.h = std::max(H.hx, H.hy);
     if (!(dmin[v] > 0.0)) b.valid = false;
   }
-  // dA/dB/err/cnt stay allocated until destroy (simple arena ownership)
+  dev_free(b, dA);
+  dev_free(b, dB);
+  dev_free(b, err);
+  dev_free(b, cnt);
+  b.launches += 7 + sweeps + (b.B > 0 ? 4 : 0);
   make_schedule(b);
 }
 

@@ -2,6 +2,7 @@
 // and Surface Tangential Velocity"): u_t ~ (psi_c - psi_b) / d_nc with psi_c the mean
 // psi of the adjacent cell, psi_b the body's constant value and d_nc the distance
 // from the cell's vertex centroid to the edge line.  One thread per boundary edge.
+#include <algorithm>
 #include <cmath>
 
 #include "batch.h"
@@ -55,10 +56,12 @@ int surface_velocity(Batch& b, int v, int body, double* theta, double* ut, int c
   k_surface_velocity<<<(ne + 127) / 128, 128, 0, b.stream>>>(b.d_var, v, gb, b.d_bodies, b.tag, b.bid, b.X, b.Vtot,
                                                              b.x64, b.sb64, b.edge_ptr, b.edge_rec, d, d + ne);
   PF_CUDA(cudaGetLastError());
+  b.launches += 1;
   const int m = std::min(ne, cap);
   if (m > 0 && theta) PF_CUDA(cudaMemcpyAsync(theta, d, m * sizeof(double), cudaMemcpyDeviceToHost, b.stream));
   if (m > 0 && ut) PF_CUDA(cudaMemcpyAsync(ut, d + ne, m * sizeof(double), cudaMemcpyDeviceToHost, b.stream));
   PF_CUDA(cudaStreamSynchronize(b.stream));
+  dev_free(b, d);
   return ne;
 }
 

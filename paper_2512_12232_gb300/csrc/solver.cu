@@ -840,8 +840,8 @@ pf_status psi_solve(Batch& b, double U, const pf_solve_opts& o, double* dev_psi,
     chunk = nodes > (8LL << 20) ? 16 : (nodes > (1LL << 20) ? 64 : 256);
   }
   cudaGraphExec_t ex = get_graph(b, prec, chunk);
-  int* hdone = nullptr;
-  PF_CUDA(cudaMallocHost(&hdone, sizeof(int)));
+  if (!b.h_poll) PF_CUDA(cudaMallocHost(&b.h_poll, sizeof(int)));
+  int* hdone = b.h_poll;
   double cg_ms = 0, res_ms = 0;
   long long launches = 0, rlaunches = 1;
   const long long max_chunks = o.k_max / chunk + 1000;
@@ -863,7 +863,7 @@ pf_status psi_solve(Batch& b, double U, const pf_solve_opts& o, double* dev_psi,
     if (*hdone >= b.nv) break;
   }
   PF_CUDA(cudaEventRecord(b.ev[4], s));
-  PF_CUDA(cudaFreeHost(hdone));
+  b.launches += 1 + launches + (long long)rlaunches * (prec == PF_MIXED ? 2 : 1);
   std::vector<VarState> fin(b.nv);
   PF_CUDA(cudaMemcpyAsync(fin.data(), b.state, b.nv * sizeof(VarState), cudaMemcpyDeviceToHost, s));
   PF_CUDA(cudaStreamSynchronize(s));
@@ -910,6 +910,7 @@ pf_status psi_solve(Batch& b, double U, const pf_solve_opts& o, double* dev_psi,
 
 void export_psi(Batch& b, double* dev_psi) {
   long long* lb = lbase_cached(b);
+  b.launches += 1;
   k_export_psi<<<dim3(256, b.nv), 256, 0, b.stream>>>(b.d_var, b.nv, lb, b.tag, b.bid, b.x64, b.sb64, dev_psi);
   PF_CUDA(cudaGetLastError());
 }
