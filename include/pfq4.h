@@ -162,6 +162,22 @@ pf_status pf_mesh_tags(const pf_batch* b, int variant, int8_t* dev_kind, int32_t
 pf_status pf_apply(pf_batch* b, int precision, const double* dev_p, double* dev_y,
                    double* body_sums, void* stream);
 
+/* Allocation-free form of pf_apply (the paper has no counterpart: this exists for the
+   library's callers).  For callers that cannot allocate device memory when they apply
+   the operator - code whose device memory is all owned by a framework arena or caching
+   allocator, or a loop that must not call cudaMalloc / cudaFree because they
+   synchronise the device and can fail under memory pressure.  Same arguments, results
+   and layout as pf_apply; it allocates nothing: the input and output vectors are read
+   and written in place, and the collapsed body rows go through a fixed device array of
+   4096 doubles (32 KB) that every GPU loading the library keeps until exit.  A handle
+   with more than 4096 bodies in total is rejected with PF_EINVAL.  The first call on a
+   device looks up that array's device address (once per device); make that first call
+   before any stream capture.  Every call on a device shares the array and it keeps the
+   last call's contents; each call overwrites what it reads back.  Calls that overlap on
+   the GPU (e.g. on two streams at once) race on it. */
+pf_status pf_apply_noalloc(const pf_batch* b, int precision, const double* dev_p, double* dev_y,
+                           double* body_sums, void* stream);
+
 /* Solve for psi on every variant (sections "Boundary Conditions" to Appendix A):
    Dirichlet sides carry psi = U*y, each body one unknown constant.
    dev_psi: optional device output [total nodes] (logical order, INACTIVE nodes = 0).

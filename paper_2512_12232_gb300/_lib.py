@@ -63,6 +63,7 @@ _SIGS = {
     "pf_mesh_coords": (C.c_int, [P, C.c_int, P, P]),
     "pf_mesh_tags": (C.c_int, [P, C.c_int, P, P, P]),
     "pf_apply": (C.c_int, [P, C.c_int, P, P, P, P]),
+    "pf_apply_noalloc": (C.c_int, [P, C.c_int, P, P, P, P]),
     "pf_psi_solve": (C.c_int, [P, C.c_double, C.POINTER(pf_solve_opts), P, P, P, P]),
     "pf_last_timing": (C.c_int, [P, C.POINTER(pf_timing)]),
     "pf_surface_velocity": (C.c_int, [P, C.c_int, C.c_int, P, P, C.c_int, C.POINTER(C.c_int), P]),

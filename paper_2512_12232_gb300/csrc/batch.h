@@ -110,6 +110,7 @@ struct Batch {
 };
 
 void check_cuda(cudaError_t e, const char* what);
+void set_last_error(const std::string& msg);
 #define PF_CUDA(call) ::pfq4::check_cuda((call), #call)
 
 // mesh.cu

@@ -15,6 +15,8 @@ static pf_alloc_fn g_alloc = nullptr;
 static pf_free_fn g_free = nullptr;
 static void* g_ctx = nullptr;
 
+void set_last_error(const std::string& msg) { g_err = msg; }
+
 void check_cuda(cudaError_t e, const char* what) {
   if (e != cudaSuccess) {
     cudaGetLastError();   // clear a non-sticky error so later calls start clean

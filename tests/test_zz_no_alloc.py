@@ -1,0 +1,52 @@
+"""GPU test of pf_apply_noalloc, the allocation-free operator apply.
+
+It serves callers that cannot allocate device memory at that point (everything owned
+by a framework arena, or loops that must not call cudaMalloc).  The test calls it
+through the C ABI twice in a row, on two different inputs, and compares each result
+with pf_apply's (the allocating entry point) within the operator tolerances used by
+the other operator tests.  This file is collected last on purpose."""
+import ctypes as C
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2512_12232_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def test_noalloc_apply_matches_apply_on_two_calls_in_a_row():
+    from paper_2512_12232_gb300 import _lib as L, api
+    lib = L.load()
+    cases = [W.five_cylinder_case(0.25, 256, 128, 40), W.single_cylinder()]
+    with api.batch_build(cases) as g:
+        n = int(g.node_offsets[-1])
+        nb = g.body_offsets[-1]
+        stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+        for call, seed in enumerate((21, 22)):
+            p = torch.from_numpy(W.random_vector(n, seed)).cuda()
+            for prec, tol in ((api.PF_FP64, 1e-13), (api.PF_MIXED, 1e-6)):
+                y_ref, s_ref = api.apply(g, p, prec)
+                y = torch.full_like(p, float("nan"))
+                sums = (C.c_double * nb)()
+                code = lib.pf_apply_noalloc(g.handle, prec, C.c_void_p(p.data_ptr()), C.c_void_p(y.data_ptr()),
+                                            sums, stream)
+                assert code == L.PF_OK, lib.pf_last_error()
+                y = y.cpu().numpy()
+                y_ref = y_ref.cpu().numpy()
+                scale = np.abs(y_ref).max()
+                assert np.isfinite(y).all()
+                assert np.abs(y - y_ref).max() <= tol * scale, (call, prec)
+                np.testing.assert_allclose(np.array(sums[:nb]), s_ref, rtol=0, atol=tol * scale * 10)
+
+
+def test_noalloc_apply_rejects_bad_arguments():
+    from paper_2512_12232_gb300 import _lib as L, api
+    lib = L.load()
+    c = W.single_cylinder()
+    with api.mesh_build(c.grid, c.bodies, c.sweeps, c.bc) as g:
+        p = torch.zeros(c.n_nodes, dtype=torch.float64, device="cuda")
+        assert lib.pf_apply_noalloc(g.handle, 7, C.c_void_p(p.data_ptr()), C.c_void_p(p.data_ptr()), None,
+                                    None) == L.PF_EINVAL
+        assert lib.pf_apply_noalloc(None, 0, None, None, None, None) == L.PF_EINVAL
