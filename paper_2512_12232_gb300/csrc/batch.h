@@ -5,6 +5,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "tma.cuh"
 
 namespace pfq4 {
 
@@ -61,6 +62,16 @@ struct Batch {
   long long* d_lbase = nullptr;      // [nv+1] logical node offsets of the variants
   double* d_bsum = nullptr;          // [B] scratch for collapsed body rows
 
+  // fused-CG tiles (CTX x CTY) and their persistent schedule
+  long long Tcg = 0;
+  int2* tile_cg_ij = nullptr;
+  int* tile_cg_var = nullptr;
+  uint8_t* tile_cg_gen = nullptr;    // 1 if a cell used by the tile has stored coefficients
+  int Gcg = 0, Scg = 0;
+  Sched sched_cg{};
+  long long Rtot = 0;                // rows of the batch's 2-D node arrays (Vtot / P)
+  int P = 0;                         // common row pitch
+
   // tiles and persistent schedule
   long long T = 0;
   int2* tile_ij = nullptr;           // [T]
@@ -75,6 +86,8 @@ struct Batch {
   VarState* state = nullptr;         // [nv]
   SolveParams* params = nullptr;
   int* n_done = nullptr;             // device counter of finished variants
+  int* d_err = nullptr;              // device flag: a bounded wait gave up
+  CgMaps maps[2];                    // TMA descriptors of the fused CG kernel (FP64, mixed)
   double* x64 = nullptr;             // [Vtot] solution (Dirichlet values in place)
   double* w64 = nullptr;             // [Vtot] FP64 scratch (body-node rows of the true residual)
   // CG vectors: r, p, q are double-buffered (a launch reads one parity and writes the

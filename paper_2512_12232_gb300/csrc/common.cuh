@@ -25,6 +25,8 @@ constexpr int NT = TX * TY;          // threads per CTA
 constexpr int SW = TX + 2;           // shared tile row width with halo
 constexpr int NHALO = 2 * SW + 2 * TY;
 constexpr int MAXB = 64;             // bodies per variant
+constexpr int CTX = 64;              // fused-CG tile: 64 x 8 nodes, 2 per thread
+constexpr int CTY = 8;
 
 // node tag byte
 constexpr uint8_t KIND_MASK = 3;
@@ -40,11 +42,11 @@ constexpr int PH_CG = 0, PH_RESID = 1, PH_DONE = 2;
 
 struct DevVariant {
   double x0, y0, hx, hy;
-  long long base;      // first padded node index of the variant
-  int nx, ny, P, nb;   // grid, pitch, bodies
+  long long base;      // first padded node index of the variant (= row0 * P)
+  int nx, ny, P, nb;   // grid, pitch (common to all variants of a batch), bodies
   int body0;           // first global body index
   int tiles_x, tiles_y;
-  int pad_;
+  int row0;            // first row of the variant in the batch's 2-D node arrays
   double kr64[6];      // K_e of an undisplaced hx-by-hy cell: K01 K02 K03 K12 K13 K23
   float kr32[6];
 };

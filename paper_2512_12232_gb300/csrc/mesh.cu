@@ -224,6 +224,23 @@ __global__ void k_stiffness(const DevVariant* var, const int* tile_var, const in
   if (tid == 0 && dmin < 1e300) atomic_min_double(&detmin[c.v], dmin);
 }
 
+// 5b. per fused-CG tile: does any cell used by the tile (cells i0-1 .. i0+CTX-1,
+//     j0-1 .. j0+CTY-1 of its variant) carry stored coefficients?
+__global__ void k_tile_general(const DevVariant* var, const int* tile_var, const int2* tile_ij, const uint8_t* tag,
+                               uint8_t* gen) {
+  const long long t = blockIdx.x;
+  const DevVariant& V = var[tile_var[t]];
+  const int2 ij = tile_ij[t];
+  int any = 0;
+  for (int q = linear_tid(); q < (CTX + 1) * (CTY + 1); q += NT) {
+    const int i = ij.x - 1 + q % (CTX + 1), j = ij.y - 1 + q / (CTX + 1);
+    if (i >= 0 && j >= 0 && i < V.nx && j < V.ny)
+      any |= (tag[V.base + (long long)j * V.P + i] & CELL_GENERAL) != 0;
+  }
+  any = __syncthreads_or(any);
+  if (linear_tid() == 0) gen[t] = (uint8_t)any;
+}
+
 // Block-wide exclusive scan of one int per thread (256 threads, 1-D linear id).
 __device__ int block_exscan(int x, int* total, int* sh /* >= 9 */) {
   const int tid = linear_tid(), lane = tid & 31, w = tid >> 5;
@@ -400,6 +417,13 @@ void build_batch(Batch& b, const pf_grid* grids, const int* body_offsets, const 
   std::vector<int> body_var(b.B);
   long long base = 0;
   b.hv.resize(nv);
+  int max_nx = 0;
+  for (int v = 0; v < nv; ++v) max_nx = std::max(max_nx, grids[v].nx);
+  // one row pitch for the whole batch, so one 2-D tensor map covers every variant
+  const int Pc = ((max_nx + 1 + 31) / 32) * 32;
+  b.P = Pc;
+  std::vector<int2> cij;
+  std::vector<int> cvar;
   for (int v = 0; v < nv; ++v) {
     const pf_grid& g = grids[v];
     const int nb = body_offsets[v + 1] - body_offsets[v];
@@ -410,7 +434,7 @@ void build_batch(Batch& b, const pf_grid* grids, const int* body_offsets, const 
     H.g = g;
     H.hx = (g.x1 - g.x0) / g.nx;
     H.hy = (g.y1 - g.y0) / g.ny;
-    H.P = ((g.nx + 1 + 31) / 32) * 32;
+    H.P = Pc;
     H.V = (long long)(g.ny + 1) * H.P;
     H.base = base;
     base += H.V;
@@ -423,6 +447,11 @@ void build_batch(Batch& b, const pf_grid* grids, const int* body_offsets, const 
       for (int tx = 0; tx < H.tiles_x; ++tx) {
         tij.push_back(make_int2(tx * TX, ty * TY));
         tvar.push_back(v);
+      }
+    for (int ty = 0; ty < (g.ny + 1 + CTY - 1) / CTY; ++ty)
+      for (int tx = 0; tx < (g.nx + 1 + CTX - 1) / CTX; ++tx) {
+        cij.push_back(make_int2(tx * CTX, ty * CTY));
+        cvar.push_back(v);
       }
     for (int k = 0; k < nb; ++k) {
       const pf_body& B = b.bodies[H.body0 + k];
@@ -449,11 +478,14 @@ void build_batch(Batch& b, const pf_grid* grids, const int* body_offsets, const 
     D.x0 = g.x0; D.y0 = g.y0; D.hx = H.hx; D.hy = H.hy;
     D.base = H.base; D.nx = g.nx; D.ny = g.ny; D.P = H.P; D.nb = nb; D.body0 = H.body0;
     D.tiles_x = H.tiles_x; D.tiles_y = H.tiles_y;
+    D.row0 = (int)(H.base / Pc);
     rect_stiffness(H.hx, H.hy, D.kr64);
     for (int m = 0; m < 6; ++m) D.kr32[m] = (float)D.kr64[m];
   }
   b.Vtot = base;
+  b.Rtot = base / Pc;
   b.T = (long long)tij.size();
+  b.Tcg = (long long)cij.size();
   const long long Vt = b.Vtot;
 
   // ---- device arrays
@@ -464,6 +496,9 @@ void build_batch(Batch& b, const pf_grid* grids, const int* body_offsets, const 
   b.d_bbox = upload(b, bbox);
   b.tile_ij = upload(b, tij);
   b.tile_var = upload(b, tvar);
+  b.tile_cg_ij = upload(b, cij);
+  b.tile_cg_var = upload(b, cvar);
+  b.tile_cg_gen = (uint8_t*)dev_alloc(b, std::max<long long>(1, b.Tcg));
   b.tag = (uint8_t*)dev_alloc(b, Vt);
   b.bid = (int*)dev_alloc(b, Vt * sizeof(int));
   b.X = (double*)dev_alloc(b, 2 * Vt * sizeof(double));
@@ -502,6 +537,7 @@ void build_batch(Batch& b, const pf_grid* grids, const int* body_offsets, const 
   k_finalize<<<grid, blk, 0, s>>>(b.d_var, b.tile_var, b.tile_ij, dA, b.tag, b.X, Vt);
   k_stiffness<<<grid, blk, 0, s>>>(b.d_var, b.tile_var, b.tile_ij, b.tag, b.X, Vt, b.K64, b.K32, b.d_stats_i,
                                    b.d_detmin);
+  k_tile_general<<<(unsigned)b.Tcg, blk, 0, s>>>(b.d_var, b.tile_cg_var, b.tile_cg_ij, b.tag, b.tile_cg_gen);
   PF_CUDA(cudaGetLastError());
 
   // ---- body node and edge lists
@@ -565,7 +601,7 @@ void build_batch(Batch& b, const pf_grid* grids, const int* body_offsets, const 
   dev_free(b, dB);
   dev_free(b, err);
   dev_free(b, cnt);
-  b.launches += 7 + sweeps + (b.B > 0 ? 4 : 0);
+  b.launches += 8 + sweeps + (b.B > 0 ? 4 : 0);
   make_schedule(b);
 }
 

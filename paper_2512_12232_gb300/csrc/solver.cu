@@ -27,6 +27,7 @@
 #include <cstring>
 
 #include "batch.h"
+#include "tma.cuh"
 
 namespace pfq4 {
 
@@ -41,6 +42,9 @@ struct CGArgs {
   T* sb;                    // [4][B] body x, r, p, q of the CG
   int B;
   int* n_done;
+  const uint8_t* tile_gen;  // per fused-CG tile: stored coefficients needed
+  long long Rtot;           // rows of the batch's 2-D node arrays
+  int* err;                 // set to 1 if a bounded wait gave up
 };
 
 template <typename T>
@@ -157,89 +161,248 @@ __device__ void finalize_cg(const CGArgs<T>& a, int v, double* scratch, double* 
   }
 }
 
+// Shared-memory layout of one pipeline stage of k_cg (T = float or double).  Tiles are
+// CTX x CTY nodes.  r, p, q boxes cover nodes i0-4 .. i0+CTX+3 (16-byte aligned start)
+// and rows j0-1 .. j0+CTY; tags cover i0-16 .. i0+CTX+15; x covers the tile itself;
+// the six element-coefficient planes (FP32 only) cover cells i0-4 .. i0+CTX+3,
+// rows j0-1 .. j0+CTY-1.
 template <typename T>
-__global__ void __launch_bounds__(NT) k_cg(CGArgs<T> a) {
-  __shared__ T ps[TY + 2][SW];
-  __shared__ uint8_t ts[TY + 2][SW];
+struct CgSmem {
+  static constexpr int BW = CTX + 8;             // r / p / q / K box width
+  static constexpr int TBW = CTX + 32;           // tag box width
+  static constexpr int RPQ = BW * (CTY + 2);     // elements of one r / p / q box
+  static constexpr int KB = BW * (CTY + 1);      // elements of one coefficient plane box
+  static constexpr bool kTmaK = sizeof(T) == 4;
+  static constexpr int align(int b) { return (b + 127) / 128 * 128; }
+  static constexpr int off_r = 0;
+  static constexpr int off_p = off_r + align(RPQ * (int)sizeof(T));
+  static constexpr int off_q = off_p + align(RPQ * (int)sizeof(T));
+  static constexpr int off_x = off_q + align(RPQ * (int)sizeof(T));
+  static constexpr int off_t = off_x + align(CTX * CTY * (int)sizeof(T));
+  static constexpr int off_k = off_t + align(TBW * (CTY + 2));
+  static constexpr int stage_bytes = off_k + (kTmaK ? 6 * align(KB * (int)sizeof(T)) : 0);
+  static constexpr int kplane_bytes = align(KB * (int)sizeof(T));
+  static constexpr int tx_base = 3 * RPQ * (int)sizeof(T) + CTX * CTY * (int)sizeof(T) + TBW * (CTY + 2);
+  static constexpr int tx_k = kTmaK ? 6 * KB * (int)sizeof(T) : 0;
+  // after the two stages: p tile with halo, effective tags, barriers
+  static constexpr int off_ptile = 2 * stage_bytes;
+  static constexpr int off_ttile = off_ptile + align((CTX + 2) * (CTY + 2) * (int)sizeof(T));
+  static constexpr int off_bar = off_ttile + align((CTX + 2) * (CTY + 2));
+  static constexpr int total = off_bar + 128;
+};
+
+// Row of the operator at ptile position (li, lj) with cell coefficients taken from the
+// staged planes (FP32) or from global memory (FP64), closed form for undisplaced cells.
+template <typename T>
+__device__ __forceinline__ T q4_row_tile(const T* pt, const uint8_t* tt, const T* ks, int li, int lj, long long n,
+                                         int P, const T* __restrict__ Kg, long long plane, const T* kr) {
+  using L = CgSmem<T>;
+  constexpr int W = CTX + 2;
+  const T pc = pt[lj * W + li];
+  const T dE = pt[lj * W + li + 1] - pc, dW = pt[lj * W + li - 1] - pc;
+  const T dN = pt[(lj + 1) * W + li] - pc, dS = pt[(lj - 1) * W + li] - pc;
+  const T dNE = pt[(lj + 1) * W + li + 1] - pc, dNW = pt[(lj + 1) * W + li - 1] - pc;
+  const T dSE = pt[(lj - 1) * W + li + 1] - pc, dSW = pt[(lj - 1) * W + li - 1] - pc;
+  const int kp = L::kplane_bytes / (int)sizeof(T);
+  auto coef = [&](int m, int crow, int ccol, long long gidx) -> T {
+    if constexpr (L::kTmaK) {
+      return ks[m * kp + crow * L::BW + ccol];
+    } else {
+      return __ldg(Kg + m * plane + gidx);
+    }
+  };
+  T y = T(0);
+  uint8_t t = tt[lj * W + li];                      // cell (i, j): corner 0
+  if (t & CELL_ACTIVE) {
+    T k01 = kr[0], k02 = kr[1], k03 = kr[2];
+    if (t & CELL_GENERAL) { k01 = coef(0, lj, li + 3, n); k02 = coef(1, lj, li + 3, n); k03 = coef(2, lj, li + 3, n); }
+    y += k01 * dE + k02 * dNE + k03 * dN;
+  }
+  t = tt[lj * W + li - 1];                          // cell (i-1, j): corner 1
+  if (t & CELL_ACTIVE) {
+    T k01 = kr[0], k12 = kr[3], k13 = kr[4];
+    if (t & CELL_GENERAL) {
+      k01 = coef(0, lj, li + 2, n - 1); k12 = coef(3, lj, li + 2, n - 1); k13 = coef(4, lj, li + 2, n - 1);
+    }
+    y += k01 * dW + k12 * dN + k13 * dNW;
+  }
+  t = tt[(lj - 1) * W + li - 1];                    // cell (i-1, j-1): corner 2
+  if (t & CELL_ACTIVE) {
+    T k02 = kr[1], k12 = kr[3], k23 = kr[5];
+    if (t & CELL_GENERAL) {
+      const long long c = n - P - 1;
+      k02 = coef(1, lj - 1, li + 2, c); k12 = coef(3, lj - 1, li + 2, c); k23 = coef(5, lj - 1, li + 2, c);
+    }
+    y += k02 * dSW + k12 * dS + k23 * dW;
+  }
+  t = tt[(lj - 1) * W + li];                        // cell (i, j-1): corner 3
+  if (t & CELL_ACTIVE) {
+    T k03 = kr[2], k13 = kr[4], k23 = kr[5];
+    if (t & CELL_GENERAL) {
+      const long long c = n - P;
+      k03 = coef(2, lj - 1, li + 3, c); k13 = coef(4, lj - 1, li + 3, c); k23 = coef(5, lj - 1, li + 3, c);
+    }
+    y += k03 * dS + k13 * dSE + k23 * dE;
+  }
+  return y;
+}
+
+// Issue the TMA loads of tile t into stage s (one thread).
+template <typename T>
+__device__ __forceinline__ void cg_issue(const CgMaps& mp, int cur, unsigned char* stage, uint64_t* bar,
+                                         int2 ij, int row0, long long Rtot, bool gen) {
+  using L = CgSmem<T>;
+  const int x0 = ij.x - 4, y0 = row0 + ij.y - 1;
+  mbar_arrive_expect_tx(bar, L::tx_base + (gen ? L::tx_k : 0));
+  tma_load_2d(stage + L::off_r, &mp.r[cur], x0, y0, bar);
+  tma_load_2d(stage + L::off_p, &mp.p[cur], x0, y0, bar);
+  tma_load_2d(stage + L::off_q, &mp.q[cur], x0, y0, bar);
+  tma_load_2d(stage + L::off_x, &mp.x, ij.x, row0 + ij.y, bar);
+  tma_load_2d(stage + L::off_t, &mp.tag, ij.x - 16, y0, bar);
+  if constexpr (L::kTmaK) {
+    if (gen)
+      for (int m = 0; m < 6; ++m)
+        tma_load_2d(stage + L::off_k + m * L::kplane_bytes, &mp.k, x0, (int)(m * Rtot) + y0, bar);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT) k_cg(CGArgs<T> a, const __grid_constant__ CgMaps mp) {
+  using L = CgSmem<T>;
+  extern __shared__ __align__(128) unsigned char smem[];
   __shared__ T s_pb[MAXB];
   __shared__ double red[NT / 32][4];
   __shared__ double scratch[NT / 32 + 1];
   __shared__ double sh_qb[MAXB];
   __shared__ int s_last;
+  T* pt = reinterpret_cast<T*>(smem + L::off_ptile);
+  uint8_t* tt = reinterpret_cast<uint8_t*>(smem + L::off_ttile);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::off_bar);
   const int tid = linear_tid(), lane = tid & 31, warp = tid >> 5;
   const int B = a.B;
-  const T* K = kplane<T>(a.m);
   const long long plane = a.m.Vtot;
+  constexpr int W = CTX + 2;
+  if (tid == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  uint32_t parity = 0;                           // bit s: parity of the next wait on stage s
   for (int sg = a.sc.cta_seg[blockIdx.x]; sg < a.sc.cta_seg[blockIdx.x + 1]; ++sg) {
     const int v = a.sc.seg_var[sg];
     if (a.st[v].phase != PH_CG) continue;
     const DevVariant& V = a.m.var[v];
     const T alpha = (T)a.st[v].alpha, beta = (T)a.st[v].beta;
     const int cur = a.st[v].buf;
-    const T* __restrict__ r_old = a.r[cur];
-    const T* __restrict__ p_old = a.p[cur];
-    const T* __restrict__ q_old = a.q[cur];
     T* __restrict__ r_new = a.r[cur ^ 1];
     T* __restrict__ p_new = a.p[cur ^ 1];
     T* __restrict__ q_new = a.q[cur ^ 1];
     const T* kr = krect<T>(V);
+    const int t0 = a.sc.seg_t0[sg], t1 = a.sc.seg_t1[sg];
     if (tid < V.nb) {
       const int gb = V.body0 + tid;
       const T rn = next_r(a.sb[B + gb], a.sb[3 * B + gb], alpha);
       s_pb[tid] = next_p(rn, a.sb[2 * B + gb], beta);
     }
+    if (tid == 0) {
+      for (int k = 0; k < 2 && t0 + k < t1; ++k) {
+        fence_proxy_async_smem();
+        cg_issue<T>(mp, cur, smem + k * L::stage_bytes, &bars[k], a.sc.tile_ij[t0 + k], V.row0, a.Rtot,
+                    a.tile_gen[t0 + k] != 0);
+      }
+    }
     __syncthreads();
     Acc<T> acc;
     acc.zero();
-    for (int t = a.sc.seg_t0[sg]; t < a.sc.seg_t1[sg]; ++t) {
-      const int2 ij = a.sc.tile_ij[t];
-      const int i = ij.x + threadIdx.x, j = ij.y + threadIdx.y;
-      const bool in = (i <= V.nx) && (j <= V.ny);
-      const long long n = V.base + (long long)j * V.P + i;
-      const uint8_t tg = in ? a.m.tag[n] : K_INACT;
-      const int kind = tg & KIND_MASK;
-      T rn = T(0), pn = T(0), xn = T(0);
-      if (kind == K_FREE) {
-        const T po = p_old[n];
-        rn = next_r(r_old[n], q_old[n], alpha);
-        xn = next_x(a.x[n], po, alpha);
-        pn = next_p(rn, po, beta);
-      } else if (kind == K_BODY) {
-        pn = s_pb[a.m.bid[n]];
+    for (int t = t0; t < t1; ++t) {
+      const int s = (t - t0) & 1;
+      unsigned char* st = smem + s * L::stage_bytes;
+      const bool ok = mbar_wait(&bars[s], (parity >> s) & 1u);
+      parity ^= 1u << s;
+      if (__syncthreads_or(!ok)) {
+        if (tid == 0) atomicExch(a.err, 1);
+        // drain the other stage if a load is still in flight, then leave
+        if (t + 1 < t1) mbar_wait(&bars[s ^ 1], (parity >> (s ^ 1)) & 1u);
+        return;
       }
-      ps[threadIdx.y + 1][threadIdx.x + 1] = pn;
-      ts[threadIdx.y + 1][threadIdx.x + 1] = tg;
-      if (tid < NHALO) {
+      const T* Rs = reinterpret_cast<const T*>(st + L::off_r);
+      const T* Ps = reinterpret_cast<const T*>(st + L::off_p);
+      const T* Qs = reinterpret_cast<const T*>(st + L::off_q);
+      const T* Xs = reinterpret_cast<const T*>(st + L::off_x);
+      const uint8_t* Tg = reinterpret_cast<const uint8_t*>(st + L::off_t);
+      const T* Ks = reinterpret_cast<const T*>(st + L::off_k);
+      const int2 ij = a.sc.tile_ij[t];
+      // pass 1: own nodes (2 per thread) and the halo ring -> p tile, effective tags
+      T rn2[2], pn2[2], xn2[2];
+      uint8_t tg2[2];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int li = 1 + threadIdx.x + 32 * u, lj = 1 + threadIdx.y;
+        const int i = ij.x - 1 + li, j = ij.y - 1 + lj;
+        const bool in = (i <= V.nx) && (j <= V.ny);
+        uint8_t tg = in ? Tg[lj * L::TBW + li + 15] : K_INACT;
+        const int kind = tg & KIND_MASK;
+        T rn = T(0), pn = T(0), xn = T(0);
+        if (kind == K_FREE) {
+          const T po = Ps[lj * L::BW + li + 3];
+          rn = next_r(Rs[lj * L::BW + li + 3], Qs[lj * L::BW + li + 3], alpha);
+          xn = next_x(Xs[(lj - 1) * CTX + (li - 1)], po, alpha);
+          pn = next_p(rn, po, beta);
+        } else if (kind == K_BODY) {
+          pn = s_pb[a.m.bid[V.base + (long long)j * V.P + i]];
+        }
+        pt[lj * W + li] = pn;
+        tt[lj * W + li] = tg;
+        rn2[u] = rn; pn2[u] = pn; xn2[u] = xn; tg2[u] = tg;
+      }
+      for (int h = tid; h < 2 * W + 2 * CTY; h += NT) {
         int li, lj;
-        halo_pos(tid, li, lj);
-        const int hi = ij.x - 1 + li, hj = ij.y - 1 + lj;
+        if (h < W) { li = h; lj = 0; }
+        else if (h < 2 * W) { li = h - W; lj = CTY + 1; }
+        else if (h < 2 * W + CTY) { li = 0; lj = 1 + (h - 2 * W); }
+        else { li = CTX + 1; lj = 1 + (h - 2 * W - CTY); }
+        const int i = ij.x - 1 + li, j = ij.y - 1 + lj;
         uint8_t ht = K_INACT;
         T hp = T(0);
-        if (hi >= 0 && hj >= 0 && hi <= V.nx && hj <= V.ny) {
-          const long long hn = V.base + (long long)hj * V.P + hi;
-          ht = a.m.tag[hn];
+        if (i >= 0 && j >= 0 && i <= V.nx && j <= V.ny) {
+          ht = Tg[lj * L::TBW + li + 15];
           const int hk = ht & KIND_MASK;
-          if (hk == K_FREE) hp = next_p(next_r(r_old[hn], q_old[hn], alpha), p_old[hn], beta);
-          else if (hk == K_BODY) hp = s_pb[a.m.bid[hn]];
+          if (hk == K_FREE)
+            hp = next_p(next_r(Rs[lj * L::BW + li + 3], Qs[lj * L::BW + li + 3], alpha), Ps[lj * L::BW + li + 3], beta);
+          else if (hk == K_BODY)
+            hp = s_pb[a.m.bid[V.base + (long long)j * V.P + i]];
         }
-        ps[lj][li] = hp;
-        ts[lj][li] = ht;
+        pt[lj * W + li] = hp;
+        tt[lj * W + li] = ht;
       }
       __syncthreads();
-      if (kind == K_FREE || kind == K_BODY) {
-        const T y = q4_row<T>(ps, ts, threadIdx.x + 1, threadIdx.y + 1, n, V.P, K, plane, kr);
-        q_new[n] = y;
-        if (kind == K_FREE) {
-          a.x[n] = xn;
-          r_new[n] = rn;
-          p_new[n] = pn;
-          acc.add(0, rn, rn);
-          acc.add(1, pn, y);
-          acc.add(2, rn, y);
-          acc.add(3, y, y);
+      // pass 2: operator rows of the own nodes, stores, dots
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int li = 1 + threadIdx.x + 32 * u, lj = 1 + threadIdx.y;
+        const int kind = tg2[u] & KIND_MASK;
+        if (kind == K_FREE || kind == K_BODY) {
+          const int i = ij.x - 1 + li, j = ij.y - 1 + lj;
+          const long long n = V.base + (long long)j * V.P + i;
+          const T y = q4_row_tile<T>(pt, tt, Ks, li, lj, n, V.P, kplane<T>(a.m), plane, kr);
+          q_new[n] = y;
+          if (kind == K_FREE) {
+            a.x[n] = xn2[u];
+            r_new[n] = rn2[u];
+            p_new[n] = pn2[u];
+            acc.add(0, rn2[u], rn2[u]);
+            acc.add(1, pn2[u], y);
+            acc.add(2, rn2[u], y);
+            acc.add(3, y, y);
+          }
         }
       }
       __syncthreads();
+      if (tid == 0 && t + 2 < t1) {
+        fence_proxy_async_smem();
+        cg_issue<T>(mp, cur, st, &bars[s], a.sc.tile_ij[t + 2], V.row0, a.Rtot, a.tile_gen[t + 2] != 0);
+      }
     }
     double w4[4];
     acc.warp_reduce(w4);
@@ -248,9 +411,9 @@ __global__ void __launch_bounds__(NT) k_cg(CGArgs<T> a) {
     __syncthreads();
     if (tid == 0) {
       for (int k = 0; k < 4; ++k) {
-        double s = 0.0;
-        for (int w = 0; w < NT / 32; ++w) s += red[w][k];
-        a.sc.partial[sg * 4 + k] = s;
+        double sum = 0.0;
+        for (int w = 0; w < NT / 32; ++w) sum += red[w][k];
+        a.sc.partial[sg * 4 + k] = sum;
       }
       __threadfence();
       const int done = atomicAdd(&a.sc.counter[v], 1);
@@ -550,23 +713,13 @@ static MeshDev mesh_dev(const Batch& b) {
   return m;
 }
 
-void make_schedule(Batch& b) {
-  int dev = 0, nsm = 0;
-  PF_CUDA(cudaGetDevice(&dev));
-  PF_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  int o32 = 0, o64 = 0, oR = 0;
-  PF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o32, k_cg<float>, NT, 0));
-  PF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o64, k_cg<double>, NT, 0));
-  PF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&oR, k_resid<float>, NT, 0));
-  const int occ = std::max(1, std::min(o32, std::min(o64, oR)));
-  long long G = std::min<long long>((long long)nsm * occ, b.T);
-  b.G = (int)G;
+// Persistent schedule over a tile list: CTA c owns tiles [c*T/G, (c+1)*T/G), cut into
+// segments at variant boundaries.
+static Sched build_sched(Batch& b, const std::vector<int>& tv, int G) {
+  const long long T = (long long)tv.size();
   std::vector<int> cta_seg(G + 1), seg_var, seg_t0, seg_t1;
-  std::vector<int> tv(b.T);
-  for (int v = 0; v < b.nv; ++v)
-    for (long long t = b.hv[v].tile0; t < b.hv[v].tile0 + (long long)b.hv[v].tiles_x * b.hv[v].tiles_y; ++t) tv[t] = v;
   for (long long c = 0; c < G; ++c) {
-    const long long t0 = c * b.T / G, t1 = (c + 1) * b.T / G;
+    const long long t0 = c * T / G, t1 = (c + 1) * T / G;
     cta_seg[c] = (int)seg_var.size();
     long long s0 = t0;
     for (long long t = t0; t < t1; ++t) {
@@ -579,11 +732,12 @@ void make_schedule(Batch& b) {
     }
   }
   cta_seg[G] = (int)seg_var.size();
-  b.S = (int)seg_var.size();
-  std::vector<int> vs0(b.nv, -1), vs1(b.nv, -1);
-  for (int sgi = 0; sgi < b.S; ++sgi) {
+  const int S = (int)seg_var.size();
+  std::vector<int> vs0(b.nv, 0), vs1(b.nv, 0);
+  std::vector<int> seen(b.nv, 0);
+  for (int sgi = 0; sgi < S; ++sgi) {
     const int v = seg_var[sgi];
-    if (vs0[v] < 0) vs0[v] = sgi;
+    if (!seen[v]) { vs0[v] = sgi; seen[v] = 1; }
     vs1[v] = sgi + 1;
   }
   auto up = [&](const std::vector<int>& h) {
@@ -591,26 +745,94 @@ void make_schedule(Batch& b) {
     PF_CUDA(cudaMemcpyAsync(d, h.data(), h.size() * sizeof(int), cudaMemcpyHostToDevice, b.stream));
     return d;
   };
-  b.cta_seg = up(cta_seg);
-  b.seg_var = up(seg_var);
-  b.seg_t0 = up(seg_t0);
-  b.seg_t1 = up(seg_t1);
-  b.var_seg0 = up(vs0);
-  b.var_seg1 = up(vs1);
-  b.counter = (int*)dev_alloc(b, b.nv * sizeof(int));
-  PF_CUDA(cudaMemsetAsync(b.counter, 0, b.nv * sizeof(int), b.stream));
-  b.partial = (double*)dev_alloc(b, (size_t)b.S * 4 * sizeof(double));
-  b.sched.cta_seg = b.cta_seg;
-  b.sched.seg_var = b.seg_var;
-  b.sched.seg_t0 = b.seg_t0;
-  b.sched.seg_t1 = b.seg_t1;
-  b.sched.tile_ij = b.tile_ij;
-  b.sched.var_seg0 = b.var_seg0;
-  b.sched.var_seg1 = b.var_seg1;
-  b.sched.partial = b.partial;
-  b.sched.counter = b.counter;
-  b.sched.n_cta = b.G;
+  Sched sc{};
+  sc.cta_seg = up(cta_seg);
+  sc.seg_var = up(seg_var);
+  sc.seg_t0 = up(seg_t0);
+  sc.seg_t1 = up(seg_t1);
+  sc.var_seg0 = up(vs0);
+  sc.var_seg1 = up(vs1);
+  int* counter = (int*)dev_alloc(b, b.nv * sizeof(int));
+  PF_CUDA(cudaMemsetAsync(counter, 0, b.nv * sizeof(int), b.stream));
+  sc.counter = counter;
+  sc.partial = (double*)dev_alloc(b, (size_t)std::max(1, S) * 4 * sizeof(double));
+  sc.n_cta = G;
   PF_CUDA(cudaStreamSynchronize(b.stream));
+  return sc;
+}
+
+void make_schedule(Batch& b) {
+  int dev = 0, nsm = 0;
+  PF_CUDA(cudaGetDevice(&dev));
+  PF_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  // residual kernel: 32 x 8 tiles
+  int oR32 = 0, oR64 = 0;
+  PF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&oR32, k_resid<float>, NT, 0));
+  PF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&oR64, k_resid<double>, NT, 0));
+  std::vector<int> tv(b.T);
+  for (int v = 0; v < b.nv; ++v)
+    for (long long t = b.hv[v].tile0; t < b.hv[v].tile0 + (long long)b.hv[v].tiles_x * b.hv[v].tiles_y; ++t) tv[t] = v;
+  b.G = (int)std::min<long long>((long long)nsm * std::max(1, std::min(oR32, oR64)), b.T);
+  b.sched = build_sched(b, tv, b.G);
+  b.sched.tile_ij = b.tile_ij;
+  b.S = 0;
+  // fused CG kernel: CTX x CTY tiles, TMA-staged, dynamic shared memory
+  PF_CUDA(cudaFuncSetAttribute(k_cg<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, CgSmem<float>::total));
+  PF_CUDA(cudaFuncSetAttribute(k_cg<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, CgSmem<double>::total));
+  int o32 = 0, o64 = 0;
+  PF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o32, k_cg<float>, NT, CgSmem<float>::total));
+  PF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o64, k_cg<double>, NT, CgSmem<double>::total));
+  std::vector<int> tc(b.Tcg);
+  {
+    long long t = 0;
+    for (int v = 0; v < b.nv; ++v) {
+      const long long n = (long long)((b.hv[v].g.nx + 1 + CTX - 1) / CTX) * ((b.hv[v].g.ny + 1 + CTY - 1) / CTY);
+      for (long long k = 0; k < n; ++k) tc[t++] = v;
+    }
+  }
+  b.Gcg = (int)std::min<long long>((long long)nsm * std::max(1, std::min(o32, o64)), b.Tcg);
+  b.sched_cg = build_sched(b, tc, b.Gcg);
+  b.sched_cg.tile_ij = b.tile_cg_ij;
+}
+
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    PF_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
+    if (q != cudaDriverEntryPointSuccess || !p) throw Error{PF_ECUDA, "cuTensorMapEncodeTiled is unavailable"};
+    fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  return fn;
+}
+
+// 2-D map over a [rows][P] array of elem_bytes elements, boxes of box_w x box_h.
+static void encode_2d(CUtensorMap* map, void* base, CUtensorMapDataType dt, int elem_bytes, long long P,
+                      long long rows, int box_w, int box_h) {
+  const cuuint64_t dims[2] = {(cuuint64_t)P, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)P * elem_bytes};
+  const cuuint32_t box[2] = {(cuuint32_t)box_w, (cuuint32_t)box_h};
+  const cuuint32_t es[2] = {1, 1};
+  const CUresult r = tensor_map_encoder()(map, dt, 2, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) throw Error{PF_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")"};
+}
+
+template <typename T>
+static void make_cg_maps(Batch& b, CgMaps& mp, T* const r[2], T* const p[2], T* const q[2], T* x, T* K) {
+  using L = CgSmem<T>;
+  const CUtensorMapDataType dt = sizeof(T) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  const int e = (int)sizeof(T);
+  for (int k = 0; k < 2; ++k) {
+    encode_2d(&mp.r[k], r[k], dt, e, b.P, b.Rtot, L::BW, CTY + 2);
+    encode_2d(&mp.p[k], p[k], dt, e, b.P, b.Rtot, L::BW, CTY + 2);
+    encode_2d(&mp.q[k], q[k], dt, e, b.P, b.Rtot, L::BW, CTY + 2);
+  }
+  encode_2d(&mp.x, x, dt, e, b.P, b.Rtot, CTX, CTY);
+  encode_2d(&mp.tag, b.tag, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, b.P, b.Rtot, L::TBW, CTY + 2);
+  encode_2d(&mp.k, K, dt, e, b.P, 6 * b.Rtot, L::BW, CTY + 1);
 }
 
 void ensure_solver_memory(Batch& b, int precision) {
@@ -624,7 +846,8 @@ void ensure_solver_memory(Batch& b, int precision) {
     b.sbr64 = (double*)dev_alloc(b, B * sizeof(double));
     b.state = (VarState*)dev_alloc(b, b.nv * sizeof(VarState));
     b.params = (SolveParams*)dev_alloc(b, sizeof(SolveParams));
-    b.n_done = (int*)dev_alloc(b, sizeof(int));
+    b.n_done = (int*)dev_alloc(b, 2 * sizeof(int));
+    b.d_err = b.n_done + 1;
     PF_CUDA(cudaMemsetAsync(b.x64, 0, V * sizeof(double), b.stream));
     PF_CUDA(cudaMemsetAsync(b.sb64, 0, 4 * B * sizeof(double), b.stream));
     PF_CUDA(cudaMemsetAsync(b.sb32, 0, 4 * B * sizeof(float), b.stream));
@@ -637,6 +860,7 @@ void ensure_solver_memory(Batch& b, int precision) {
       b.p64[k] = (double*)dev_alloc(b, V * sizeof(double));
       b.q64[k] = (double*)dev_alloc(b, V * sizeof(double));
     }
+    make_cg_maps<double>(b, b.maps[0], b.r64, b.p64, b.q64, b.x64, b.K64);
   }
   if (precision == PF_MIXED && !b.r32[0]) {
     b.x32 = (float*)dev_alloc(b, V * sizeof(float));
@@ -645,6 +869,7 @@ void ensure_solver_memory(Batch& b, int precision) {
       b.p32[k] = (float*)dev_alloc(b, V * sizeof(float));
       b.q32[k] = (float*)dev_alloc(b, V * sizeof(float));
     }
+    make_cg_maps<float>(b, b.maps[1], b.r32, b.p32, b.q32, b.x32, b.K32);
   }
 }
 
@@ -698,7 +923,10 @@ void apply_operator(Batch& b, int precision, const double* dev_p, double* dev_y,
 template <typename T>
 static void fill_cg_args(Batch& b, CGArgs<T>& a, T* x, T* const r[2], T* const p[2], T* const q[2], T* sb) {
   a.m = mesh_dev(b);
-  a.sc = b.sched;
+  a.sc = b.sched_cg;
+  a.tile_gen = b.tile_cg_gen;
+  a.Rtot = b.Rtot;
+  a.err = b.d_err;
   a.st = b.state;
   a.prm = b.params;
   a.x = x;
@@ -740,11 +968,11 @@ static void launch_cg_chunk(Batch& b, int precision, int chunk, cudaStream_t s) 
   if (precision == PF_FP64) {
     CGArgs<double> a;
     fill_cg_args<double>(b, a, b.x64, b.r64, b.p64, b.q64, b.sb64);
-    for (int k = 0; k < chunk; ++k) k_cg<double><<<b.G, blk, 0, s>>>(a);
+    for (int k = 0; k < chunk; ++k) k_cg<double><<<b.Gcg, blk, CgSmem<double>::total, s>>>(a, b.maps[0]);
   } else {
     CGArgs<float> a;
     fill_cg_args<float>(b, a, b.x32, b.r32, b.p32, b.q32, b.sb32);
-    for (int k = 0; k < chunk; ++k) k_cg<float><<<b.G, blk, 0, s>>>(a);
+    for (int k = 0; k < chunk; ++k) k_cg<float><<<b.Gcg, blk, CgSmem<float>::total, s>>>(a, b.maps[1]);
   }
   PF_CUDA(cudaGetLastError());
 }
@@ -811,7 +1039,7 @@ pf_status psi_solve(Batch& b, double U, const pf_solve_opts& o, double* dev_psi,
     if (warm && S.bnorm2 < 0) S.bnorm2 = -1.0;
   }
   PF_CUDA(cudaMemcpyAsync(b.state, st.data(), b.nv * sizeof(VarState), cudaMemcpyHostToDevice, s));
-  PF_CUDA(cudaMemsetAsync(b.n_done, 0, sizeof(int), s));
+  PF_CUDA(cudaMemsetAsync(b.n_done, 0, 2 * sizeof(int), s));
   const int B = std::max(1, b.B);
   if (!warm) PF_CUDA(cudaMemsetAsync(b.sb64, 0, 4 * B * sizeof(double), s));
   else PF_CUDA(cudaMemsetAsync(b.sb64 + B, 0, 3 * B * sizeof(double), s));
@@ -840,7 +1068,7 @@ pf_status psi_solve(Batch& b, double U, const pf_solve_opts& o, double* dev_psi,
     chunk = nodes > (8LL << 20) ? 16 : (nodes > (1LL << 20) ? 64 : 256);
   }
   cudaGraphExec_t ex = get_graph(b, prec, chunk);
-  if (!b.h_poll) PF_CUDA(cudaMallocHost(&b.h_poll, sizeof(int)));
+  if (!b.h_poll) PF_CUDA(cudaMallocHost(&b.h_poll, 2 * sizeof(int)));
   int* hdone = b.h_poll;
   double cg_ms = 0, res_ms = 0;
   long long launches = 0, rlaunches = 1;
@@ -851,7 +1079,7 @@ pf_status psi_solve(Batch& b, double U, const pf_solve_opts& o, double* dev_psi,
     PF_CUDA(cudaEventRecord(b.ev[1], s));
     launch_resid_only(b, prec, s);
     PF_CUDA(cudaEventRecord(b.ev[2], s));
-    PF_CUDA(cudaMemcpyAsync(hdone, b.n_done, sizeof(int), cudaMemcpyDeviceToHost, s));
+    PF_CUDA(cudaMemcpyAsync(hdone, b.n_done, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
     PF_CUDA(cudaStreamSynchronize(s));
     float ms1 = 0, ms2 = 0;
     PF_CUDA(cudaEventElapsedTime(&ms1, b.ev[0], b.ev[1]));
@@ -860,7 +1088,8 @@ pf_status psi_solve(Batch& b, double U, const pf_solve_opts& o, double* dev_psi,
     res_ms += ms2;
     launches += chunk;
     rlaunches += 1;
-    if (*hdone >= b.nv) break;
+    if (hdone[1]) throw Error{PF_ETIMEOUT, "a bounded wait in the CG kernel gave up (TMA tile not delivered)"};
+    if (hdone[0] >= b.nv) break;
   }
   PF_CUDA(cudaEventRecord(b.ev[4], s));
   b.launches += 1 + launches + (long long)rlaunches * (prec == PF_MIXED ? 2 : 1);
