@@ -25,6 +25,13 @@ struct Error {                 // thrown inside the library, converted to pf_sta
   std::string msg;
 };
 
+struct CgConfig {                  // persistent grid + schedule of one fused-CG kernel instance
+  bool ready = false;
+  int G = 0;
+  int smem = 0;
+  Sched sc{};
+};
+
 struct Batch;
 void* dev_alloc(Batch& b, size_t bytes);
 void dev_free(Batch& b, void* p);
@@ -67,8 +74,9 @@ struct Batch {
   int2* tile_cg_ij = nullptr;
   int* tile_cg_var = nullptr;
   uint8_t* tile_cg_gen = nullptr;    // 1 if a cell used by the tile has stored coefficients
-  int Gcg = 0, Scg = 0;
-  Sched sched_cg{};
+  CgConfig cg_cfg[2][2];             // [precision][stages - 2]
+  int cg_stages = 2;
+  int nsm = 0;
   long long Rtot = 0;                // rows of the batch's 2-D node arrays (Vtot / P)
   int P = 0;                         // common row pitch
 
@@ -108,6 +116,7 @@ struct Batch {
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   cudaStream_t graph_stream[2] = {nullptr, nullptr};
   int graph_chunk[2] = {0, 0};
+  int graph_stages[2] = {0, 0};
   cudaEvent_t ev[6] = {};
   pf_timing timing{};
   double cg_bytes_per_node[2] = {0, 0};

@@ -117,6 +117,15 @@ __device__ __forceinline__ void ff_add_prod(FF& a, float x, float y) {
   a.lo += err + e;
 }
 
+// Add one FP32 value into the two-float accumulator (TwoSum, error kept in lo).
+__device__ __forceinline__ void ff_add_value(FF& a, float p) {
+  float s = a.hi + p;
+  float bb = s - a.hi;
+  float err = (a.hi - (s - bb)) + (p - bb);
+  a.hi = s;
+  a.lo += err;
+}
+
 __device__ __forceinline__ FF ff_add(FF a, FF b) {
   float s = a.hi + b.hi;
   float bb = s - a.hi;
@@ -131,6 +140,7 @@ template <> struct Acc<double> {
   double v[4];
   __device__ void zero() { v[0] = v[1] = v[2] = v[3] = 0.0; }
   __device__ void add(int k, double x, double y) { v[k] = fma(x, y, v[k]); }
+  __device__ void add2(int k, double x1, double y1, double x2, double y2) { v[k] = fma(x2, y2, fma(x1, y1, v[k])); }
   // warp-reduce, lane 0 returns the sums
   __device__ void warp_reduce(double out[4]) {
 #pragma unroll
@@ -149,6 +159,10 @@ template <> struct Acc<float> {
     for (int k = 0; k < 4; ++k) v[k] = FF{0.f, 0.f};
   }
   __device__ void add(int k, float x, float y) { ff_add_prod(v[k], x, y); }
+  // a thread's two products of one tile: each rounded to FP32 and summed in FP32, the
+  // pair sum accumulated with compensation (error <= 2^-23 (|x1 y1| + |x2 y2|) per pair,
+  // no growth with the number of pairs beyond the two-float accumulation error)
+  __device__ void add2(int k, float x1, float y1, float x2, float y2) { ff_add_value(v[k], fmaf(x1, y1, x2 * y2)); }
   __device__ void warp_reduce(double out[4]) {
 #pragma unroll
     for (int k = 0; k < 4; ++k) {

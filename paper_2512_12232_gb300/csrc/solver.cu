@@ -24,6 +24,7 @@
 // [k_cg x chunk, k_resid] until every variant is done.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 
 #include "batch.h"
@@ -163,29 +164,29 @@ __device__ void finalize_cg(const CGArgs<T>& a, int v, double* scratch, double* 
 
 // Shared-memory layout of one pipeline stage of k_cg (T = float or double).  Tiles are
 // CTX x CTY nodes.  r, p, q boxes cover nodes i0-4 .. i0+CTX+3 (16-byte aligned start)
-// and rows j0-1 .. j0+CTY; tags cover i0-16 .. i0+CTX+15; x covers the tile itself;
-// the six element-coefficient planes (FP32 only) cover cells i0-4 .. i0+CTX+3,
-// rows j0-1 .. j0+CTY-1.
-template <typename T>
+// and rows j0-1 .. j0+CTY; tags cover i0-16 .. i0+CTX+15; the six element-coefficient
+// planes (FP32 only) cover cells i0-4 .. i0+CTX-1, rows j0-1 .. j0+CTY-1.  x is read
+// straight from global memory (own nodes only), which keeps four CTAs per SM.
+template <typename T, int NS = 2>
 struct CgSmem {
-  static constexpr int BW = CTX + 8;             // r / p / q / K box width
+  static constexpr int BW = CTX + 8;             // r / p / q box width
+  static constexpr int KBW = CTX + 4;            // coefficient box width (cells i0-4 .. i0+CTX-1)
   static constexpr int TBW = CTX + 32;           // tag box width
   static constexpr int RPQ = BW * (CTY + 2);     // elements of one r / p / q box
-  static constexpr int KB = BW * (CTY + 1);      // elements of one coefficient plane box
+  static constexpr int KB = KBW * (CTY + 1);     // elements of one coefficient plane box
   static constexpr bool kTmaK = sizeof(T) == 4;
   static constexpr int align(int b) { return (b + 127) / 128 * 128; }
   static constexpr int off_r = 0;
   static constexpr int off_p = off_r + align(RPQ * (int)sizeof(T));
   static constexpr int off_q = off_p + align(RPQ * (int)sizeof(T));
-  static constexpr int off_x = off_q + align(RPQ * (int)sizeof(T));
-  static constexpr int off_t = off_x + align(CTX * CTY * (int)sizeof(T));
+  static constexpr int off_t = off_q + align(RPQ * (int)sizeof(T));
   static constexpr int off_k = off_t + align(TBW * (CTY + 2));
   static constexpr int stage_bytes = off_k + (kTmaK ? 6 * align(KB * (int)sizeof(T)) : 0);
   static constexpr int kplane_bytes = align(KB * (int)sizeof(T));
-  static constexpr int tx_base = 3 * RPQ * (int)sizeof(T) + CTX * CTY * (int)sizeof(T) + TBW * (CTY + 2);
+  static constexpr int tx_base = 3 * RPQ * (int)sizeof(T) + TBW * (CTY + 2);
   static constexpr int tx_k = kTmaK ? 6 * KB * (int)sizeof(T) : 0;
-  // after the two stages: p tile with halo, effective tags, barriers
-  static constexpr int off_ptile = 2 * stage_bytes;
+  // after the NS stages: p tile with halo, effective tags, barriers
+  static constexpr int off_ptile = NS * stage_bytes;
   static constexpr int off_ttile = off_ptile + align((CTX + 2) * (CTY + 2) * (int)sizeof(T));
   static constexpr int off_bar = off_ttile + align((CTX + 2) * (CTY + 2));
   static constexpr int total = off_bar + 128;
@@ -206,19 +207,28 @@ __device__ __forceinline__ T q4_row_tile(const T* pt, const uint8_t* tt, const T
   const int kp = L::kplane_bytes / (int)sizeof(T);
   auto coef = [&](int m, int crow, int ccol, long long gidx) -> T {
     if constexpr (L::kTmaK) {
-      return ks[m * kp + crow * L::BW + ccol];
+      return ks[m * kp + crow * L::KBW + ccol];
     } else {
       return __ldg(Kg + m * plane + gidx);
     }
   };
+  const uint8_t c0 = tt[lj * W + li], c1 = tt[lj * W + li - 1], c2 = tt[(lj - 1) * W + li - 1],
+                c3 = tt[(lj - 1) * W + li];
+  constexpr uint8_t FLAGS = CELL_ACTIVE | CELL_GENERAL;
+  if ((c0 & FLAGS) == CELL_ACTIVE && (c1 & FLAGS) == CELL_ACTIVE && (c2 & FLAGS) == CELL_ACTIVE &&
+      (c3 & FLAGS) == CELL_ACTIVE) {
+    // all four cells are undisplaced rectangles: K23 = K01, K12 = K03, K13 = K02, so the
+    // row collapses to 2 K01 (dE + dW) + 2 K03 (dN + dS) + K02 (sum of diagonals)
+    return T(2) * kr[0] * (dE + dW) + T(2) * kr[2] * (dN + dS) + kr[1] * ((dNE + dSW) + (dNW + dSE));
+  }
   T y = T(0);
-  uint8_t t = tt[lj * W + li];                      // cell (i, j): corner 0
+  uint8_t t = c0;                                   // cell (i, j): corner 0
   if (t & CELL_ACTIVE) {
     T k01 = kr[0], k02 = kr[1], k03 = kr[2];
     if (t & CELL_GENERAL) { k01 = coef(0, lj, li + 3, n); k02 = coef(1, lj, li + 3, n); k03 = coef(2, lj, li + 3, n); }
     y += k01 * dE + k02 * dNE + k03 * dN;
   }
-  t = tt[lj * W + li - 1];                          // cell (i-1, j): corner 1
+  t = c1;                                           // cell (i-1, j): corner 1
   if (t & CELL_ACTIVE) {
     T k01 = kr[0], k12 = kr[3], k13 = kr[4];
     if (t & CELL_GENERAL) {
@@ -226,7 +236,7 @@ __device__ __forceinline__ T q4_row_tile(const T* pt, const uint8_t* tt, const T
     }
     y += k01 * dW + k12 * dN + k13 * dNW;
   }
-  t = tt[(lj - 1) * W + li - 1];                    // cell (i-1, j-1): corner 2
+  t = c2;                                           // cell (i-1, j-1): corner 2
   if (t & CELL_ACTIVE) {
     T k02 = kr[1], k12 = kr[3], k23 = kr[5];
     if (t & CELL_GENERAL) {
@@ -235,7 +245,7 @@ __device__ __forceinline__ T q4_row_tile(const T* pt, const uint8_t* tt, const T
     }
     y += k02 * dSW + k12 * dS + k23 * dW;
   }
-  t = tt[(lj - 1) * W + li];                        // cell (i, j-1): corner 3
+  t = c3;                                           // cell (i, j-1): corner 3
   if (t & CELL_ACTIVE) {
     T k03 = kr[2], k13 = kr[4], k23 = kr[5];
     if (t & CELL_GENERAL) {
@@ -251,13 +261,12 @@ __device__ __forceinline__ T q4_row_tile(const T* pt, const uint8_t* tt, const T
 template <typename T>
 __device__ __forceinline__ void cg_issue(const CgMaps& mp, int cur, unsigned char* stage, uint64_t* bar,
                                          int2 ij, int row0, long long Rtot, bool gen) {
-  using L = CgSmem<T>;
+  using L = CgSmem<T, 2>;   // stage layout does not depend on the stage count
   const int x0 = ij.x - 4, y0 = row0 + ij.y - 1;
   mbar_arrive_expect_tx(bar, L::tx_base + (gen ? L::tx_k : 0));
   tma_load_2d(stage + L::off_r, &mp.r[cur], x0, y0, bar);
   tma_load_2d(stage + L::off_p, &mp.p[cur], x0, y0, bar);
   tma_load_2d(stage + L::off_q, &mp.q[cur], x0, y0, bar);
-  tma_load_2d(stage + L::off_x, &mp.x, ij.x, row0 + ij.y, bar);
   tma_load_2d(stage + L::off_t, &mp.tag, ij.x - 16, y0, bar);
   if constexpr (L::kTmaK) {
     if (gen)
@@ -266,9 +275,9 @@ __device__ __forceinline__ void cg_issue(const CgMaps& mp, int cur, unsigned cha
   }
 }
 
-template <typename T>
+template <typename T, int NS>
 __global__ void __launch_bounds__(NT) k_cg(CGArgs<T> a, const __grid_constant__ CgMaps mp) {
-  using L = CgSmem<T>;
+  using L = CgSmem<T, NS>;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ T s_pb[MAXB];
   __shared__ double red[NT / 32][4];
@@ -283,8 +292,7 @@ __global__ void __launch_bounds__(NT) k_cg(CGArgs<T> a, const __grid_constant__ 
   const long long plane = a.m.Vtot;
   constexpr int W = CTX + 2;
   if (tid == 0) {
-    mbar_init(&bars[0], 1);
-    mbar_init(&bars[1], 1);
+    for (int k = 0; k < NS; ++k) mbar_init(&bars[k], 1);
     fence_mbar_init();
   }
   __syncthreads();
@@ -306,7 +314,7 @@ __global__ void __launch_bounds__(NT) k_cg(CGArgs<T> a, const __grid_constant__ 
       s_pb[tid] = next_p(rn, a.sb[2 * B + gb], beta);
     }
     if (tid == 0) {
-      for (int k = 0; k < 2 && t0 + k < t1; ++k) {
+      for (int k = 0; k < NS && t0 + k < t1; ++k) {
         fence_proxy_async_smem();
         cg_issue<T>(mp, cur, smem + k * L::stage_bytes, &bars[k], a.sc.tile_ij[t0 + k], V.row0, a.Rtot,
                     a.tile_gen[t0 + k] != 0);
@@ -316,26 +324,36 @@ __global__ void __launch_bounds__(NT) k_cg(CGArgs<T> a, const __grid_constant__ 
     Acc<T> acc;
     acc.zero();
     for (int t = t0; t < t1; ++t) {
-      const int s = (t - t0) & 1;
+      const int s = (t - t0) % NS;
       unsigned char* st = smem + s * L::stage_bytes;
       const bool ok = mbar_wait(&bars[s], (parity >> s) & 1u);
       parity ^= 1u << s;
       if (__syncthreads_or(!ok)) {
         if (tid == 0) atomicExch(a.err, 1);
-        // drain the other stage if a load is still in flight, then leave
-        if (t + 1 < t1) mbar_wait(&bars[s ^ 1], (parity >> (s ^ 1)) & 1u);
+        // drain the stages whose loads may still be in flight (bounded), then leave
+        for (int k = 1; k < NS && t + k < t1; ++k) {
+          const int s2 = (t + k - t0) % NS;
+          mbar_wait(&bars[s2], (parity >> s2) & 1u);
+        }
         return;
       }
       const T* Rs = reinterpret_cast<const T*>(st + L::off_r);
       const T* Ps = reinterpret_cast<const T*>(st + L::off_p);
       const T* Qs = reinterpret_cast<const T*>(st + L::off_q);
-      const T* Xs = reinterpret_cast<const T*>(st + L::off_x);
       const uint8_t* Tg = reinterpret_cast<const uint8_t*>(st + L::off_t);
       const T* Ks = reinterpret_cast<const T*>(st + L::off_k);
       const int2 ij = a.sc.tile_ij[t];
+      // global index of the tile's node (i0, j0); own node (li, lj) is at tb + (lj-1)*P + li-1
+      const long long tb = V.base + (long long)ij.y * V.P + ij.x;
       // pass 1: own nodes (2 per thread) and the halo ring -> p tile, effective tags
       T rn2[2], pn2[2], xn2[2];
       uint8_t tg2[2];
+      T xo[2];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int i = ij.x + threadIdx.x + 32 * u, j = ij.y + threadIdx.y;
+        xo[u] = (i <= V.nx && j <= V.ny) ? a.x[tb + threadIdx.y * V.P + threadIdx.x + 32 * u] : T(0);
+      }
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
         const int li = 1 + threadIdx.x + 32 * u, lj = 1 + threadIdx.y;
@@ -347,10 +365,10 @@ __global__ void __launch_bounds__(NT) k_cg(CGArgs<T> a, const __grid_constant__ 
         if (kind == K_FREE) {
           const T po = Ps[lj * L::BW + li + 3];
           rn = next_r(Rs[lj * L::BW + li + 3], Qs[lj * L::BW + li + 3], alpha);
-          xn = next_x(Xs[(lj - 1) * CTX + (li - 1)], po, alpha);
+          xn = next_x(xo[u], po, alpha);
           pn = next_p(rn, po, beta);
         } else if (kind == K_BODY) {
-          pn = s_pb[a.m.bid[V.base + (long long)j * V.P + i]];
+          pn = s_pb[a.m.bid[tb + (lj - 1) * V.P + (li - 1)]];
         }
         pt[lj * W + li] = pn;
         tt[lj * W + li] = tg;
@@ -371,37 +389,44 @@ __global__ void __launch_bounds__(NT) k_cg(CGArgs<T> a, const __grid_constant__ 
           if (hk == K_FREE)
             hp = next_p(next_r(Rs[lj * L::BW + li + 3], Qs[lj * L::BW + li + 3], alpha), Ps[lj * L::BW + li + 3], beta);
           else if (hk == K_BODY)
-            hp = s_pb[a.m.bid[V.base + (long long)j * V.P + i]];
+            hp = s_pb[a.m.bid[tb + (long long)(lj - 1) * V.P + (li - 1)]];
         }
         pt[lj * W + li] = hp;
         tt[lj * W + li] = ht;
       }
       __syncthreads();
       // pass 2: operator rows of the own nodes, stores, dots
+      T yq[2], rr[2], pp[2];
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
         const int li = 1 + threadIdx.x + 32 * u, lj = 1 + threadIdx.y;
         const int kind = tg2[u] & KIND_MASK;
+        yq[u] = T(0);
+        rr[u] = T(0);
+        pp[u] = T(0);
         if (kind == K_FREE || kind == K_BODY) {
-          const int i = ij.x - 1 + li, j = ij.y - 1 + lj;
-          const long long n = V.base + (long long)j * V.P + i;
+          const long long n = tb + (lj - 1) * V.P + (li - 1);
           const T y = q4_row_tile<T>(pt, tt, Ks, li, lj, n, V.P, kplane<T>(a.m), plane, kr);
           q_new[n] = y;
           if (kind == K_FREE) {
             a.x[n] = xn2[u];
             r_new[n] = rn2[u];
             p_new[n] = pn2[u];
-            acc.add(0, rn2[u], rn2[u]);
-            acc.add(1, pn2[u], y);
-            acc.add(2, rn2[u], y);
-            acc.add(3, y, y);
+            yq[u] = y;
+            rr[u] = rn2[u];
+            pp[u] = pn2[u];
           }
         }
       }
+      // dots over the FREE nodes (others contribute exact zeros)
+      acc.add2(0, rr[0], rr[0], rr[1], rr[1]);
+      acc.add2(1, pp[0], yq[0], pp[1], yq[1]);
+      acc.add2(2, rr[0], yq[0], rr[1], yq[1]);
+      acc.add2(3, yq[0], yq[0], yq[1], yq[1]);
       __syncthreads();
-      if (tid == 0 && t + 2 < t1) {
+      if (tid == 0 && t + NS < t1) {
         fence_proxy_async_smem();
-        cg_issue<T>(mp, cur, st, &bars[s], a.sc.tile_ij[t + 2], V.row0, a.Rtot, a.tile_gen[t + 2] != 0);
+        cg_issue<T>(mp, cur, st, &bars[s], a.sc.tile_ij[t + NS], V.row0, a.Rtot, a.tile_gen[t + NS] != 0);
       }
     }
     double w4[4];
@@ -776,23 +801,44 @@ void make_schedule(Batch& b) {
   b.sched = build_sched(b, tv, b.G);
   b.sched.tile_ij = b.tile_ij;
   b.S = 0;
-  // fused CG kernel: CTX x CTY tiles, TMA-staged, dynamic shared memory
-  PF_CUDA(cudaFuncSetAttribute(k_cg<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, CgSmem<float>::total));
-  PF_CUDA(cudaFuncSetAttribute(k_cg<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, CgSmem<double>::total));
-  int o32 = 0, o64 = 0;
-  PF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o32, k_cg<float>, NT, CgSmem<float>::total));
-  PF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o64, k_cg<double>, NT, CgSmem<double>::total));
+  b.nsm = nsm;
+}
+
+// Kernel instance of the fused CG step for a (precision, stages) configuration.
+template <typename T, int NS>
+static const void* cg_kernel() { return (const void*)k_cg<T, NS>; }
+
+static int cg_smem(int precision, int ns) {
+  if (precision == PF_FP64) return ns == 3 ? CgSmem<double, 3>::total : CgSmem<double, 2>::total;
+  return ns == 3 ? CgSmem<float, 3>::total : CgSmem<float, 2>::total;
+}
+
+static const void* cg_func(int precision, int ns) {
+  if (precision == PF_FP64) return ns == 3 ? cg_kernel<double, 3>() : cg_kernel<double, 2>();
+  return ns == 3 ? cg_kernel<float, 3>() : cg_kernel<float, 2>();
+}
+
+// Persistent grid (occupancy x SMs) and tile schedule of one CG configuration, built once.
+static CgConfig& cg_config(Batch& b, int precision, int ns) {
+  CgConfig& c = b.cg_cfg[precision][ns - 2];
+  if (c.ready) return c;
+  const void* f = cg_func(precision, ns);
+  const int smem = cg_smem(precision, ns);
+  PF_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  int occ = 0;
+  PF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, f, NT, smem));
   std::vector<int> tc(b.Tcg);
-  {
-    long long t = 0;
-    for (int v = 0; v < b.nv; ++v) {
-      const long long n = (long long)((b.hv[v].g.nx + 1 + CTX - 1) / CTX) * ((b.hv[v].g.ny + 1 + CTY - 1) / CTY);
-      for (long long k = 0; k < n; ++k) tc[t++] = v;
-    }
+  long long t = 0;
+  for (int v = 0; v < b.nv; ++v) {
+    const long long n = (long long)((b.hv[v].g.nx + 1 + CTX - 1) / CTX) * ((b.hv[v].g.ny + 1 + CTY - 1) / CTY);
+    for (long long k = 0; k < n; ++k) tc[t++] = v;
   }
-  b.Gcg = (int)std::min<long long>((long long)nsm * std::max(1, std::min(o32, o64)), b.Tcg);
-  b.sched_cg = build_sched(b, tc, b.Gcg);
-  b.sched_cg.tile_ij = b.tile_cg_ij;
+  c.G = (int)std::min<long long>((long long)b.nsm * std::max(1, occ), b.Tcg);
+  c.sc = build_sched(b, tc, c.G);
+  c.sc.tile_ij = b.tile_cg_ij;
+  c.smem = smem;
+  c.ready = true;
+  return c;
 }
 
 static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
@@ -821,7 +867,7 @@ static void encode_2d(CUtensorMap* map, void* base, CUtensorMapDataType dt, int 
 }
 
 template <typename T>
-static void make_cg_maps(Batch& b, CgMaps& mp, T* const r[2], T* const p[2], T* const q[2], T* x, T* K) {
+static void make_cg_maps(Batch& b, CgMaps& mp, T* const r[2], T* const p[2], T* const q[2], T* K) {
   using L = CgSmem<T>;
   const CUtensorMapDataType dt = sizeof(T) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
   const int e = (int)sizeof(T);
@@ -830,9 +876,8 @@ static void make_cg_maps(Batch& b, CgMaps& mp, T* const r[2], T* const p[2], T* 
     encode_2d(&mp.p[k], p[k], dt, e, b.P, b.Rtot, L::BW, CTY + 2);
     encode_2d(&mp.q[k], q[k], dt, e, b.P, b.Rtot, L::BW, CTY + 2);
   }
-  encode_2d(&mp.x, x, dt, e, b.P, b.Rtot, CTX, CTY);
   encode_2d(&mp.tag, b.tag, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, b.P, b.Rtot, L::TBW, CTY + 2);
-  encode_2d(&mp.k, K, dt, e, b.P, 6 * b.Rtot, L::BW, CTY + 1);
+  encode_2d(&mp.k, K, dt, e, b.P, 6 * b.Rtot, L::KBW, CTY + 1);
 }
 
 void ensure_solver_memory(Batch& b, int precision) {
@@ -860,7 +905,7 @@ void ensure_solver_memory(Batch& b, int precision) {
       b.p64[k] = (double*)dev_alloc(b, V * sizeof(double));
       b.q64[k] = (double*)dev_alloc(b, V * sizeof(double));
     }
-    make_cg_maps<double>(b, b.maps[0], b.r64, b.p64, b.q64, b.x64, b.K64);
+    make_cg_maps<double>(b, b.maps[0], b.r64, b.p64, b.q64, b.K64);
   }
   if (precision == PF_MIXED && !b.r32[0]) {
     b.x32 = (float*)dev_alloc(b, V * sizeof(float));
@@ -869,7 +914,7 @@ void ensure_solver_memory(Batch& b, int precision) {
       b.p32[k] = (float*)dev_alloc(b, V * sizeof(float));
       b.q32[k] = (float*)dev_alloc(b, V * sizeof(float));
     }
-    make_cg_maps<float>(b, b.maps[1], b.r32, b.p32, b.q32, b.x32, b.K32);
+    make_cg_maps<float>(b, b.maps[1], b.r32, b.p32, b.q32, b.K32);
   }
 }
 
@@ -921,9 +966,10 @@ void apply_operator(Batch& b, int precision, const double* dev_p, double* dev_y,
 }
 
 template <typename T>
-static void fill_cg_args(Batch& b, CGArgs<T>& a, T* x, T* const r[2], T* const p[2], T* const q[2], T* sb) {
+static void fill_cg_args(Batch& b, CGArgs<T>& a, T* x, T* const r[2], T* const p[2], T* const q[2], T* sb,
+                         const Sched& sc) {
   a.m = mesh_dev(b);
-  a.sc = b.sched_cg;
+  a.sc = sc;
   a.tile_gen = b.tile_cg_gen;
   a.Rtot = b.Rtot;
   a.err = b.d_err;
@@ -965,14 +1011,22 @@ static void fill_resid_args(Batch& b, ResidArgs<T>& a, T* const r[2], T* const p
 // the k_cg launches of one chunk (captured once as a graph)
 static void launch_cg_chunk(Batch& b, int precision, int chunk, cudaStream_t s) {
   const dim3 blk(TX, TY);
+  const int ns = b.cg_stages;
+  CgConfig& c = cg_config(b, precision, ns);
   if (precision == PF_FP64) {
     CGArgs<double> a;
-    fill_cg_args<double>(b, a, b.x64, b.r64, b.p64, b.q64, b.sb64);
-    for (int k = 0; k < chunk; ++k) k_cg<double><<<b.Gcg, blk, CgSmem<double>::total, s>>>(a, b.maps[0]);
+    fill_cg_args<double>(b, a, b.x64, b.r64, b.p64, b.q64, b.sb64, c.sc);
+    for (int k = 0; k < chunk; ++k) {
+      if (ns == 3) k_cg<double, 3><<<c.G, blk, c.smem, s>>>(a, b.maps[0]);
+      else k_cg<double, 2><<<c.G, blk, c.smem, s>>>(a, b.maps[0]);
+    }
   } else {
     CGArgs<float> a;
-    fill_cg_args<float>(b, a, b.x32, b.r32, b.p32, b.q32, b.sb32);
-    for (int k = 0; k < chunk; ++k) k_cg<float><<<b.Gcg, blk, CgSmem<float>::total, s>>>(a, b.maps[1]);
+    fill_cg_args<float>(b, a, b.x32, b.r32, b.p32, b.q32, b.sb32, c.sc);
+    for (int k = 0; k < chunk; ++k) {
+      if (ns == 3) k_cg<float, 3><<<c.G, blk, c.smem, s>>>(a, b.maps[1]);
+      else k_cg<float, 2><<<c.G, blk, c.smem, s>>>(a, b.maps[1]);
+    }
   }
   PF_CUDA(cudaGetLastError());
 }
@@ -993,7 +1047,10 @@ static void launch_resid_only(Batch& b, int precision, cudaStream_t s) {
 }
 
 static cudaGraphExec_t get_graph(Batch& b, int precision, int chunk) {
-  if (b.graph[precision] && b.graph_chunk[precision] == chunk) return b.graph[precision];
+  if (b.graph[precision] && b.graph_chunk[precision] == chunk && b.graph_stages[precision] == b.cg_stages)
+    return b.graph[precision];
+  b.graph_stages[precision] = b.cg_stages;
+  cg_config(b, precision, b.cg_stages);   // schedule set-up synchronises: do it before capturing
   if (b.graph[precision]) {
     cudaGraphExecDestroy(b.graph[precision]);
     b.graph[precision] = nullptr;
@@ -1020,6 +1077,10 @@ pf_status psi_solve(Batch& b, double U, const pf_solve_opts& o, double* dev_psi,
   if (!(o.tol > 0) || o.k_max < 1 || !std::isfinite(U)) throw Error{PF_EINVAL, "invalid tol, k_max or U"};
   const int prec = o.precision;
   ensure_solver_memory(b, prec);
+  {
+    const char* e = getenv("PFQ4_CG_STAGES");
+    b.cg_stages = (e && atoi(e) == 3) ? 3 : 2;
+  }
   cudaStream_t s = b.stream;
   SolveParams sp{};
   sp.tol2 = o.tol * o.tol;

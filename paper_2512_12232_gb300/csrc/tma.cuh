@@ -11,7 +11,7 @@ namespace pfq4 {
 constexpr int MBAR_POLL_LIMIT = 1 << 22;
 
 struct CgMaps {                 // TMA descriptors of the fused CG kernel (__grid_constant__ parameter)
-  CUtensorMap r[2], p[2], q[2], x, tag, k;
+  CUtensorMap r[2], p[2], q[2], tag, k;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
