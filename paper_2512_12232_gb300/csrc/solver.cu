@@ -276,7 +276,7 @@ __device__ __forceinline__ void cg_issue(const CgMaps& mp, int cur, unsigned cha
 }
 
 template <typename T, int NS>
-__global__ void __launch_bounds__(NT) k_cg(CGArgs<T> a, const __grid_constant__ CgMaps mp) {
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 4 : 2) k_cg(CGArgs<T> a, const __grid_constant__ CgMaps mp) {
   using L = CgSmem<T, NS>;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ T s_pb[MAXB];
@@ -300,25 +300,39 @@ __global__ void __launch_bounds__(NT) k_cg(CGArgs<T> a, const __grid_constant__ 
   for (int sg = a.sc.cta_seg[blockIdx.x]; sg < a.sc.cta_seg[blockIdx.x + 1]; ++sg) {
     const int v = a.sc.seg_var[sg];
     if (a.st[v].phase != PH_CG) continue;
-    const DevVariant& V = a.m.var[v];
+    // variant constants in registers (the kernel's stores could alias them otherwise)
+    const DevVariant& Vg = a.m.var[v];
+    const int nx = Vg.nx, ny = Vg.ny, P = Vg.P, row0 = Vg.row0, nb = Vg.nb, body0 = Vg.body0;
+    const long long base = Vg.base;
+    T kr[6];
+#pragma unroll
+    for (int m = 0; m < 6; ++m) kr[m] = krect<T>(Vg)[m];
     const T alpha = (T)a.st[v].alpha, beta = (T)a.st[v].beta;
     const int cur = a.st[v].buf;
     T* __restrict__ r_new = a.r[cur ^ 1];
     T* __restrict__ p_new = a.p[cur ^ 1];
     T* __restrict__ q_new = a.q[cur ^ 1];
-    const T* kr = krect<T>(V);
+    const T* __restrict__ xg = a.x;
     const int t0 = a.sc.seg_t0[sg], t1 = a.sc.seg_t1[sg];
-    if (tid < V.nb) {
-      const int gb = V.body0 + tid;
+    if (tid < nb) {
+      const int gb = body0 + tid;
       const T rn = next_r(a.sb[B + gb], a.sb[3 * B + gb], alpha);
       s_pb[tid] = next_p(rn, a.sb[2 * B + gb], beta);
     }
     if (tid == 0) {
       for (int k = 0; k < NS && t0 + k < t1; ++k) {
         fence_proxy_async_smem();
-        cg_issue<T>(mp, cur, smem + k * L::stage_bytes, &bars[k], a.sc.tile_ij[t0 + k], V.row0, a.Rtot,
+        cg_issue<T>(mp, cur, smem + k * L::stage_bytes, &bars[k], a.sc.tile_ij[t0 + k], row0, a.Rtot,
                     a.tile_gen[t0 + k] != 0);
       }
+    }
+    // own-node x of the first tile (later tiles are prefetched one tile ahead)
+    int2 ij_next = a.sc.tile_ij[t0];
+    T xo_next[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int i = ij_next.x + threadIdx.x + 32 * u, j = ij_next.y + threadIdx.y;
+      xo_next[u] = (i <= nx && j <= ny) ? xg[base + (long long)j * P + i] : T(0);
     }
     __syncthreads();
     Acc<T> acc;
@@ -326,6 +340,16 @@ __global__ void __launch_bounds__(NT) k_cg(CGArgs<T> a, const __grid_constant__ 
     for (int t = t0; t < t1; ++t) {
       const int s = (t - t0) % NS;
       unsigned char* st = smem + s * L::stage_bytes;
+      const int2 ij = ij_next;
+      T xo[2] = {xo_next[0], xo_next[1]};
+      if (t + 1 < t1) {
+        ij_next = a.sc.tile_ij[t + 1];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int i = ij_next.x + threadIdx.x + 32 * u, j = ij_next.y + threadIdx.y;
+          xo_next[u] = (i <= nx && j <= ny) ? xg[base + (long long)j * P + i] : T(0);
+        }
+      }
       const bool ok = mbar_wait(&bars[s], (parity >> s) & 1u);
       parity ^= 1u << s;
       if (__syncthreads_or(!ok)) {
@@ -342,23 +366,16 @@ __global__ void __launch_bounds__(NT) k_cg(CGArgs<T> a, const __grid_constant__ 
       const T* Qs = reinterpret_cast<const T*>(st + L::off_q);
       const uint8_t* Tg = reinterpret_cast<const uint8_t*>(st + L::off_t);
       const T* Ks = reinterpret_cast<const T*>(st + L::off_k);
-      const int2 ij = a.sc.tile_ij[t];
       // global index of the tile's node (i0, j0); own node (li, lj) is at tb + (lj-1)*P + li-1
-      const long long tb = V.base + (long long)ij.y * V.P + ij.x;
+      const long long tb = base + (long long)ij.y * P + ij.x;
       // pass 1: own nodes (2 per thread) and the halo ring -> p tile, effective tags
       T rn2[2], pn2[2], xn2[2];
       uint8_t tg2[2];
-      T xo[2];
-#pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        const int i = ij.x + threadIdx.x + 32 * u, j = ij.y + threadIdx.y;
-        xo[u] = (i <= V.nx && j <= V.ny) ? a.x[tb + threadIdx.y * V.P + threadIdx.x + 32 * u] : T(0);
-      }
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
         const int li = 1 + threadIdx.x + 32 * u, lj = 1 + threadIdx.y;
         const int i = ij.x - 1 + li, j = ij.y - 1 + lj;
-        const bool in = (i <= V.nx) && (j <= V.ny);
+        const bool in = (i <= nx) && (j <= ny);
         uint8_t tg = in ? Tg[lj * L::TBW + li + 15] : K_INACT;
         const int kind = tg & KIND_MASK;
         T rn = T(0), pn = T(0), xn = T(0);
@@ -368,31 +385,35 @@ __global__ void __launch_bounds__(NT) k_cg(CGArgs<T> a, const __grid_constant__ 
           xn = next_x(xo[u], po, alpha);
           pn = next_p(rn, po, beta);
         } else if (kind == K_BODY) {
-          pn = s_pb[a.m.bid[tb + (lj - 1) * V.P + (li - 1)]];
+          pn = s_pb[a.m.bid[tb + (lj - 1) * P + (li - 1)]];
         }
         pt[lj * W + li] = pn;
         tt[lj * W + li] = tg;
         rn2[u] = rn; pn2[u] = pn; xn2[u] = xn; tg2[u] = tg;
       }
-      for (int h = tid; h < 2 * W + 2 * CTY; h += NT) {
-        int li, lj;
-        if (h < W) { li = h; lj = 0; }
-        else if (h < 2 * W) { li = h - W; lj = CTY + 1; }
-        else if (h < 2 * W + CTY) { li = 0; lj = 1 + (h - 2 * W); }
-        else { li = CTX + 1; lj = 1 + (h - 2 * W - CTY); }
-        const int i = ij.x - 1 + li, j = ij.y - 1 + lj;
-        uint8_t ht = K_INACT;
-        T hp = T(0);
-        if (i >= 0 && j >= 0 && i <= V.nx && j <= V.ny) {
-          ht = Tg[lj * L::TBW + li + 15];
-          const int hk = ht & KIND_MASK;
-          if (hk == K_FREE)
-            hp = next_p(next_r(Rs[lj * L::BW + li + 3], Qs[lj * L::BW + li + 3], alpha), Ps[lj * L::BW + li + 3], beta);
-          else if (hk == K_BODY)
-            hp = s_pb[a.m.bid[tb + (long long)(lj - 1) * V.P + (li - 1)]];
+      {
+        // halo ring positions spread over all eight warps (lanes 0..18 of each)
+        const int h = warp + (NT / 32) * lane;
+        if (h < 2 * W + 2 * CTY) {
+          int li, lj;
+          if (h < W) { li = h; lj = 0; }
+          else if (h < 2 * W) { li = h - W; lj = CTY + 1; }
+          else if (h < 2 * W + CTY) { li = 0; lj = 1 + (h - 2 * W); }
+          else { li = CTX + 1; lj = 1 + (h - 2 * W - CTY); }
+          const int i = ij.x - 1 + li, j = ij.y - 1 + lj;
+          uint8_t ht = K_INACT;
+          T hp = T(0);
+          if (i >= 0 && j >= 0 && i <= nx && j <= ny) {
+            ht = Tg[lj * L::TBW + li + 15];
+            const int hk = ht & KIND_MASK;
+            if (hk == K_FREE)
+              hp = next_p(next_r(Rs[lj * L::BW + li + 3], Qs[lj * L::BW + li + 3], alpha), Ps[lj * L::BW + li + 3], beta);
+            else if (hk == K_BODY)
+              hp = s_pb[a.m.bid[tb + (long long)(lj - 1) * P + (li - 1)]];
+          }
+          pt[lj * W + li] = hp;
+          tt[lj * W + li] = ht;
         }
-        pt[lj * W + li] = hp;
-        tt[lj * W + li] = ht;
       }
       __syncthreads();
       // pass 2: operator rows of the own nodes, stores, dots
@@ -405,8 +426,8 @@ __global__ void __launch_bounds__(NT) k_cg(CGArgs<T> a, const __grid_constant__ 
         rr[u] = T(0);
         pp[u] = T(0);
         if (kind == K_FREE || kind == K_BODY) {
-          const long long n = tb + (lj - 1) * V.P + (li - 1);
-          const T y = q4_row_tile<T>(pt, tt, Ks, li, lj, n, V.P, kplane<T>(a.m), plane, kr);
+          const long long n = tb + (lj - 1) * P + (li - 1);
+          const T y = q4_row_tile<T>(pt, tt, Ks, li, lj, n, P, kplane<T>(a.m), plane, kr);
           q_new[n] = y;
           if (kind == K_FREE) {
             a.x[n] = xn2[u];
@@ -426,7 +447,7 @@ __global__ void __launch_bounds__(NT) k_cg(CGArgs<T> a, const __grid_constant__ 
       __syncthreads();
       if (tid == 0 && t + NS < t1) {
         fence_proxy_async_smem();
-        cg_issue<T>(mp, cur, st, &bars[s], a.sc.tile_ij[t + NS], V.row0, a.Rtot, a.tile_gen[t + NS] != 0);
+        cg_issue<T>(mp, cur, st, &bars[s], a.sc.tile_ij[t + NS], row0, a.Rtot, a.tile_gen[t + NS] != 0);
       }
     }
     double w4[4];
