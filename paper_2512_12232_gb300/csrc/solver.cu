@@ -759,13 +759,28 @@ static MeshDev mesh_dev(const Batch& b) {
   return m;
 }
 
-// Persistent schedule over a tile list: CTA c owns tiles [c*T/G, (c+1)*T/G), cut into
-// segments at variant boundaries.
-static Sched build_sched(Batch& b, const std::vector<int>& tv, int G) {
+// Persistent schedule over a tile list: CTA c owns a contiguous range of tiles, cut into
+// segments at variant boundaries.  With per-tile costs the ranges hold equal cost
+// (tiles with stored coefficients move and compute more), else equal tile counts.
+static Sched build_sched(Batch& b, const std::vector<int>& tv, int G, const std::vector<double>* cost = nullptr) {
   const long long T = (long long)tv.size();
+  std::vector<long long> cut(G + 1, 0);
+  if (cost) {
+    double total = 0.0;
+    for (double c : *cost) total += c;
+    long long t = 0;
+    double run = 0.0;
+    for (int c = 0; c <= G; ++c) {
+      const double target = total * c / G;
+      while (t < T && run + 0.5 * (*cost)[t] < target) run += (*cost)[t++];
+      cut[c] = (c == G) ? T : t;
+    }
+  } else {
+    for (int c = 0; c <= G; ++c) cut[c] = (long long)c * T / G;
+  }
   std::vector<int> cta_seg(G + 1), seg_var, seg_t0, seg_t1;
   for (long long c = 0; c < G; ++c) {
-    const long long t0 = c * T / G, t1 = (c + 1) * T / G;
+    const long long t0 = cut[c], t1 = cut[c + 1];
     cta_seg[c] = (int)seg_var.size();
     long long s0 = t0;
     for (long long t = t0; t < t1; ++t) {
@@ -855,7 +870,13 @@ static CgConfig& cg_config(Batch& b, int precision, int ns) {
     for (long long k = 0; k < n; ++k) tc[t++] = v;
   }
   c.G = (int)std::min<long long>((long long)b.nsm * std::max(1, occ), b.Tcg);
-  c.sc = build_sched(b, tc, c.G);
+  // relative cost of a tile with stored coefficients (extra TMA planes + general rows)
+  std::vector<uint8_t> gen(b.Tcg);
+  PF_CUDA(cudaMemcpy(gen.data(), b.tile_cg_gen, b.Tcg, cudaMemcpyDeviceToHost));
+  std::vector<double> cost(b.Tcg);
+  const double gw = precision == PF_FP64 ? 1.4 : 1.6;
+  for (long long k = 0; k < b.Tcg; ++k) cost[k] = gen[k] ? gw : 1.0;
+  c.sc = build_sched(b, tc, c.G, &cost);
   c.sc.tile_ij = b.tile_cg_ij;
   c.smem = smem;
   c.ready = true;
