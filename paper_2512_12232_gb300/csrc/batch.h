@@ -98,13 +98,16 @@ struct Batch {
   CgMaps maps[2];                    // TMA descriptors of the fused CG kernel (FP64, mixed)
   double* x64 = nullptr;             // [Vtot] solution (Dirichlet values in place)
   double* w64 = nullptr;             // [Vtot] FP64 scratch (body-node rows of the true residual)
-  // CG vectors: r, p, q are double-buffered (a launch reads one parity and writes the
-  // other, so halo reads never see a neighbour tile's new values); x is updated in place.
-  double *r64[2] = {nullptr, nullptr}, *p64[2] = {nullptr, nullptr}, *q64[2] = {nullptr, nullptr};
-  float* x32 = nullptr;
-  float *r32[2] = {nullptr, nullptr}, *p32[2] = {nullptr, nullptr}, *q32[2] = {nullptr, nullptr};
-  double* sb64 = nullptr;            // [4][B] FP64 body values x, r, p, q (x = the solution C_k)
-  float* sb32 = nullptr;             // [4][B] FP32 inner body values x, r, p, q
+  // CG state records (x, r, p, q) double-buffered by parity: a launch reads one parity
+  // with its halo and writes the other, so no tile sees a neighbour's new values
+  State4<double>* st64[2] = {nullptr, nullptr};
+  State4<float>* st32[2] = {nullptr, nullptr};
+  void** d_sbuf = nullptr;           // device copy of {st64[0], st64[1], st32[0], st32[1]}
+  double* sol64 = nullptr;           // [B] body solution values C_k (FP64)
+  double* sb64 = nullptr;            // [4][B] FP64-mode CG body values x, r, p, q
+  float* sb32 = nullptr;             // [4][B] mixed-mode CG body values x, r, p, q
+  double* ap64[2] = {nullptr, nullptr};   // pf_apply scratch (padded in / out)
+  float* ap32[2] = {nullptr, nullptr};
   double* sbr64 = nullptr;           // [B] FP64 true-residual body rows
   void** d_vecs = nullptr;           // device list of the vectors k_init clears
   bool solved = false;

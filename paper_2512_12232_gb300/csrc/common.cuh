@@ -69,6 +69,11 @@ struct VarState {
   int pad_;
 };
 
+// One node's CG state: x (correction), r, p, q = A p.
+template <typename T> struct State4;
+template <> struct __align__(16) State4<float> { float x, r, p, q; };
+template <> struct __align__(32) State4<double> { double x, r, p, q; };
+
 struct SolveParams {
   double tol2;                 // tol^2
   double inner_rel2;           // inner_tol^2 (mixed) or 0

@@ -54,7 +54,7 @@ int surface_velocity(Batch& b, int v, int body, double* theta, double* ut, int c
   if (ne == 0) return 0;
   double* d = (double*)dev_alloc(b, 2 * (size_t)ne * sizeof(double));
   k_surface_velocity<<<(ne + 127) / 128, 128, 0, b.stream>>>(b.d_var, v, gb, b.d_bodies, b.tag, b.bid, b.X, b.Vtot,
-                                                             b.x64, b.sb64, b.edge_ptr, b.edge_rec, d, d + ne);
+                                                             b.x64, b.sol64, b.edge_ptr, b.edge_rec, d, d + ne);
   PF_CUDA(cudaGetLastError());
   b.launches += 1;
   const int m = std::min(ne, cap);

@@ -16,12 +16,15 @@
 // single grid-wide reduction per iteration suffices.  Dirichlet and inactive nodes
 // keep zero search directions (constraint enforcement after every update).
 //
-// A second kernel (k_resid) forms the true FP64 residual b - A u from the FP64
-// solution (the Dirichlet values sit in place, so the lifting is part of the same
-// apply), folds in the FP32 correction in mixed precision (iterative refinement),
-// and restarts the inner CG from that residual.  Both kernels read their per-variant
-// phase from device memory, so the host launches a captured graph of
-// [k_cg x chunk, k_resid] until every variant is done.
+// The CG runs on a correction: the state of a node is one record (x, r, p, q) of the
+// working precision, double-buffered by parity (a launch reads one parity with its
+// halo and writes the other), so a tile is one TMA box and one 16- or 32-byte store
+// per node.  k_fold adds the correction x into the FP64 solution x64 and k_resid forms
+// the true FP64 residual b - A x64 (Dirichlet values sit in x64, so the lifting is part
+// of the same apply) and restarts the CG from it: iterative refinement, with an FP32
+// inner solver in mixed precision and an FP64 one in FP64 mode.  All kernels read
+// their per-variant phase from device memory, so the host launches a captured graph
+// of k_cg launches followed by [k_fold, k_resid] until every variant is done.
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
@@ -38,8 +41,7 @@ struct CGArgs {
   Sched sc;
   VarState* st;
   const SolveParams* prm;
-  T* x;                     // iterate (FP64 mode: the solution itself), updated in place
-  T *r[2], *p[2], *q[2];    // ping-pong buffers, parity VarState::buf holds the current ones
+  State4<T>* s[2];          // ping-pong state, parity VarState::buf holds the current one
   T* sb;                    // [4][B] body x, r, p, q of the CG
   int B;
   int* n_done;
@@ -56,8 +58,8 @@ struct ResidArgs {
   const SolveParams* prm;
   double* x64;              // solution, Dirichlet values in place (read only here)
   double* w64;              // body-node rows of A u
-  T *r[2], *p[2], *q[2];    // CG vectors to restart, in the current parity
-  double* sb64;             // [4][B]: [0] = body solution values
+  State4<T>* s[2];          // CG state to restart, in the current parity
+  double* sol;              // [B] body solution values
   T* sb;                    // [4][B] CG body values
   double* sbr;              // [B] true residual body rows
   int B;
@@ -101,6 +103,15 @@ __device__ double body_gather(const MeshDev& m, int gb, const T* vec, double* sc
   return block_sum(s, scratch);
 }
 
+// Sum of q over the nodes of one body from state records (fixed order).
+template <typename T>
+__device__ double body_gather_q(const MeshDev& m, int gb, const State4<T>* st, double* scratch) {
+  double s = 0.0;
+  const int e1 = m.body_ptr[gb + 1];
+  for (int e = m.body_ptr[gb] + linear_tid(); e < e1; e += NT) s += (double)__ldcg(&st[m.body_nodes[e]].q);
+  return block_sum(s, scratch);
+}
+
 // ---------------------------------------------------------------- fused CG step
 template <typename T>
 __device__ void finalize_cg(const CGArgs<T>& a, int v, double* scratch, double* sh_qb) {
@@ -108,9 +119,9 @@ __device__ void finalize_cg(const CGArgs<T>& a, int v, double* scratch, double* 
   VarState* S = &a.st[v];
   double d[4];
   reduce_partials(a.sc, v, 4, d, scratch);
-  const T* qnew = a.q[S->buf ^ 1];
+  const State4<T>* snew = a.s[S->buf ^ 1];
   for (int k = 0; k < V.nb; ++k) {
-    const double s = body_gather<T>(a.m, V.body0 + k, qnew, scratch);
+    const double s = body_gather_q<T>(a.m, V.body0 + k, snew, scratch);
     if (linear_tid() == 0) sh_qb[k] = s;
   }
   __syncthreads();
@@ -163,27 +174,24 @@ __device__ void finalize_cg(const CGArgs<T>& a, int v, double* scratch, double* 
 }
 
 // Shared-memory layout of one pipeline stage of k_cg (T = float or double).  Tiles are
-// CTX x CTY nodes.  r, p, q boxes cover nodes i0-4 .. i0+CTX+3 (16-byte aligned start)
-// and rows j0-1 .. j0+CTY; tags cover i0-16 .. i0+CTX+15; the six element-coefficient
-// planes (FP32 only) cover cells i0-4 .. i0+CTX-1, rows j0-1 .. j0+CTY-1.  x is read
-// straight from global memory (own nodes only), which keeps four CTAs per SM.
+// CTX x CTY nodes.  The state box covers nodes i0-1 .. i0+CTX and rows j0-1 .. j0+CTY
+// (records of 4 values); tags cover i0-16 .. i0+CTX+15; the six element-coefficient
+// planes (FP32 only) cover cells i0-4 .. i0+CTX-1, rows j0-1 .. j0+CTY-1.
 template <typename T, int NS = 2>
 struct CgSmem {
-  static constexpr int BW = CTX + 8;             // r / p / q box width
+  static constexpr int SBW = CTX + 2;            // state box width (nodes)
   static constexpr int KBW = CTX + 4;            // coefficient box width (cells i0-4 .. i0+CTX-1)
   static constexpr int TBW = CTX + 32;           // tag box width
-  static constexpr int RPQ = BW * (CTY + 2);     // elements of one r / p / q box
+  static constexpr int SB = 4 * SBW * (CTY + 2); // elements of the state box
   static constexpr int KB = KBW * (CTY + 1);     // elements of one coefficient plane box
   static constexpr bool kTmaK = sizeof(T) == 4;
   static constexpr int align(int b) { return (b + 127) / 128 * 128; }
-  static constexpr int off_r = 0;
-  static constexpr int off_p = off_r + align(RPQ * (int)sizeof(T));
-  static constexpr int off_q = off_p + align(RPQ * (int)sizeof(T));
-  static constexpr int off_t = off_q + align(RPQ * (int)sizeof(T));
+  static constexpr int off_s = 0;
+  static constexpr int off_t = off_s + align(SB * (int)sizeof(T));
   static constexpr int off_k = off_t + align(TBW * (CTY + 2));
   static constexpr int stage_bytes = off_k + (kTmaK ? 6 * align(KB * (int)sizeof(T)) : 0);
   static constexpr int kplane_bytes = align(KB * (int)sizeof(T));
-  static constexpr int tx_base = 3 * RPQ * (int)sizeof(T) + TBW * (CTY + 2);
+  static constexpr int tx_base = SB * (int)sizeof(T) + TBW * (CTY + 2);
   static constexpr int tx_k = kTmaK ? 6 * KB * (int)sizeof(T) : 0;
   // after the NS stages: p tile with halo, effective tags, barriers
   static constexpr int off_ptile = NS * stage_bytes;
@@ -264,9 +272,7 @@ __device__ __forceinline__ void cg_issue(const CgMaps& mp, int cur, unsigned cha
   using L = CgSmem<T, 2>;   // stage layout does not depend on the stage count
   const int x0 = ij.x - 4, y0 = row0 + ij.y - 1;
   mbar_arrive_expect_tx(bar, L::tx_base + (gen ? L::tx_k : 0));
-  tma_load_2d(stage + L::off_r, &mp.r[cur], x0, y0, bar);
-  tma_load_2d(stage + L::off_p, &mp.p[cur], x0, y0, bar);
-  tma_load_2d(stage + L::off_q, &mp.q[cur], x0, y0, bar);
+  tma_load_3d(stage + L::off_s, &mp.s[cur], 0, ij.x - 1, y0, bar);
   tma_load_2d(stage + L::off_t, &mp.tag, ij.x - 16, y0, bar);
   if constexpr (L::kTmaK) {
     if (gen)
@@ -309,10 +315,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 4 : 2) k_cg(CGArgs<T> a, 
     for (int m = 0; m < 6; ++m) kr[m] = krect<T>(Vg)[m];
     const T alpha = (T)a.st[v].alpha, beta = (T)a.st[v].beta;
     const int cur = a.st[v].buf;
-    T* __restrict__ r_new = a.r[cur ^ 1];
-    T* __restrict__ p_new = a.p[cur ^ 1];
-    T* __restrict__ q_new = a.q[cur ^ 1];
-    const T* __restrict__ xg = a.x;
+    State4<T>* __restrict__ s_new = a.s[cur ^ 1];
     const int t0 = a.sc.seg_t0[sg], t1 = a.sc.seg_t1[sg];
     if (tid < nb) {
       const int gb = body0 + tid;
@@ -326,14 +329,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 4 : 2) k_cg(CGArgs<T> a, 
                     a.tile_gen[t0 + k] != 0);
       }
     }
-    // own-node x of the first tile (later tiles are prefetched one tile ahead)
     int2 ij_next = a.sc.tile_ij[t0];
-    T xo_next[2];
-#pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      const int i = ij_next.x + threadIdx.x + 32 * u, j = ij_next.y + threadIdx.y;
-      xo_next[u] = (i <= nx && j <= ny) ? xg[base + (long long)j * P + i] : T(0);
-    }
     __syncthreads();
     Acc<T> acc;
     acc.zero();
@@ -341,15 +337,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 4 : 2) k_cg(CGArgs<T> a, 
       const int s = (t - t0) % NS;
       unsigned char* st = smem + s * L::stage_bytes;
       const int2 ij = ij_next;
-      T xo[2] = {xo_next[0], xo_next[1]};
-      if (t + 1 < t1) {
-        ij_next = a.sc.tile_ij[t + 1];
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          const int i = ij_next.x + threadIdx.x + 32 * u, j = ij_next.y + threadIdx.y;
-          xo_next[u] = (i <= nx && j <= ny) ? xg[base + (long long)j * P + i] : T(0);
-        }
-      }
+      if (t + 1 < t1) ij_next = a.sc.tile_ij[t + 1];
       const bool ok = mbar_wait(&bars[s], (parity >> s) & 1u);
       parity ^= 1u << s;
       if (__syncthreads_or(!ok)) {
@@ -361,9 +349,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 4 : 2) k_cg(CGArgs<T> a, 
         }
         return;
       }
-      const T* Rs = reinterpret_cast<const T*>(st + L::off_r);
-      const T* Ps = reinterpret_cast<const T*>(st + L::off_p);
-      const T* Qs = reinterpret_cast<const T*>(st + L::off_q);
+      const State4<T>* Ss = reinterpret_cast<const State4<T>*>(st + L::off_s);
       const uint8_t* Tg = reinterpret_cast<const uint8_t*>(st + L::off_t);
       const T* Ks = reinterpret_cast<const T*>(st + L::off_k);
       // global index of the tile's node (i0, j0); own node (li, lj) is at tb + (lj-1)*P + li-1
@@ -380,10 +366,10 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 4 : 2) k_cg(CGArgs<T> a, 
         const int kind = tg & KIND_MASK;
         T rn = T(0), pn = T(0), xn = T(0);
         if (kind == K_FREE) {
-          const T po = Ps[lj * L::BW + li + 3];
-          rn = next_r(Rs[lj * L::BW + li + 3], Qs[lj * L::BW + li + 3], alpha);
-          xn = next_x(xo[u], po, alpha);
-          pn = next_p(rn, po, beta);
+          const State4<T> o = Ss[lj * L::SBW + li];
+          rn = next_r(o.r, o.q, alpha);
+          xn = next_x(o.x, o.p, alpha);
+          pn = next_p(rn, o.p, beta);
         } else if (kind == K_BODY) {
           pn = s_pb[a.m.bid[tb + (lj - 1) * P + (li - 1)]];
         }
@@ -406,8 +392,10 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 4 : 2) k_cg(CGArgs<T> a, 
           if (i >= 0 && j >= 0 && i <= nx && j <= ny) {
             ht = Tg[lj * L::TBW + li + 15];
             const int hk = ht & KIND_MASK;
-            if (hk == K_FREE)
-              hp = next_p(next_r(Rs[lj * L::BW + li + 3], Qs[lj * L::BW + li + 3], alpha), Ps[lj * L::BW + li + 3], beta);
+            if (hk == K_FREE) {
+              const State4<T> o = Ss[lj * L::SBW + li];
+              hp = next_p(next_r(o.r, o.q, alpha), o.p, beta);
+            }
             else if (hk == K_BODY)
               hp = s_pb[a.m.bid[tb + (long long)(lj - 1) * P + (li - 1)]];
           }
@@ -428,11 +416,13 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 4 : 2) k_cg(CGArgs<T> a, 
         if (kind == K_FREE || kind == K_BODY) {
           const long long n = tb + (lj - 1) * P + (li - 1);
           const T y = q4_row_tile<T>(pt, tt, Ks, li, lj, n, P, kplane<T>(a.m), plane, kr);
-          q_new[n] = y;
+          State4<T> o;
+          o.x = xn2[u];
+          o.r = rn2[u];
+          o.p = pn2[u];
+          o.q = y;
+          s_new[n] = o;            // BODY nodes carry only q (x, r, p are zero there)
           if (kind == K_FREE) {
-            a.x[n] = xn2[u];
-            r_new[n] = rn2[u];
-            p_new[n] = pn2[u];
             yq[u] = y;
             rr[u] = rn2[u];
             pp[u] = pn2[u];
@@ -494,10 +484,8 @@ __device__ void finalize_resid(const ResidArgs<T>& a, int v, double* scratch, do
       const double rb = sh_rb[k];
       g += rb * rb;
       a.sbr[gb] = rb;
-      if (a.mixed) {
-        a.sb64[gb] = a.sb64[gb] + (double)a.sb[gb];
-        a.sb[gb] = T(0);
-      }
+      a.sol[gb] = a.sol[gb] + (double)a.sb[gb];   // fold the body correction
+      a.sb[gb] = T(0);
       a.sb[B + gb] = (T)rb;
       a.sb[2 * B + gb] = T(0);
       a.sb[3 * B + gb] = T(0);
@@ -523,7 +511,7 @@ __device__ void finalize_resid(const ResidArgs<T>& a, int v, double* scratch, do
       S->beta = 0.0;
       S->inner_iters = 0;
       S->thr_rel = a.mixed ? a.prm->inner_rel2 : 0.0;
-      S->thr_abs2 = (a.mixed ? 0.25 : 1.0) * tol2 * S->bnorm2;
+      S->thr_abs2 = (a.mixed ? 0.25 : 0.5) * tol2 * S->bnorm2;
     }
     a.sc.counter[v] = 0;
   }
@@ -546,12 +534,10 @@ __global__ void __launch_bounds__(NT) k_resid(ResidArgs<T> a) {
     const DevVariant& V = a.m.var[v];
     if (tid < V.nb) {
       const int gb = V.body0 + tid;
-      s_xb[tid] = a.mixed ? a.sb64[gb] + (double)a.sb[gb] : a.sb64[gb];
+      s_xb[tid] = a.sol[gb] + (double)a.sb[gb];
     }
     const int cur = a.st[v].buf;
-    T* __restrict__ r_out = a.r[cur];
-    T* __restrict__ p_out = a.p[cur];
-    T* __restrict__ q_out = a.q[cur];
+    State4<T>* __restrict__ s_out = a.s[cur];
     __syncthreads();
     double acc = 0.0;
     for (int t = a.sc.seg_t0[sg]; t < a.sc.seg_t1[sg]; ++t) {
@@ -587,9 +573,12 @@ __global__ void __launch_bounds__(NT) k_resid(ResidArgs<T> a) {
         const double y = q4_row<double>(ps, ts, threadIdx.x + 1, threadIdx.y + 1, n, V.P, a.m.K64, plane, V.kr64);
         if (kind == K_FREE) {
           const double r = -y;
-          r_out[n] = (T)r;
-          p_out[n] = T(0);
-          q_out[n] = T(0);
+          State4<T> o;
+          o.x = T(0);
+          o.r = (T)r;
+          o.p = T(0);
+          o.q = T(0);
+          s_out[n] = o;
           acc = fma(r, r, acc);
         } else {
           a.w64[n] = y;
@@ -618,10 +607,11 @@ __global__ void __launch_bounds__(NT) k_resid(ResidArgs<T> a) {
   }
 }
 
-// Mixed precision: fold the FP32 correction into the FP64 solution before the true
-// residual (pointwise, its own launch so no tile ever sees a half-updated neighbour).
+// Fold the CG correction into the FP64 solution before the true residual (pointwise,
+// its own launch so no tile ever sees a half-updated neighbour).
+template <typename T>
 __global__ void k_fold(const DevVariant* var, const int* tile_var, const int2* tile_ij, const uint8_t* tag,
-                       const VarState* st, double* x64, float* x32) {
+                       const VarState* st, double* x64, State4<T>* const* sbuf) {
   const long long t = blockIdx.x;
   const int v = tile_var[t];
   if (st[v].phase != PH_RESID) return;
@@ -631,14 +621,14 @@ __global__ void k_fold(const DevVariant* var, const int* tile_var, const int2* t
   if (i > V.nx || j > V.ny) return;
   const long long n = V.base + (long long)j * V.P + i;
   if ((tag[n] & KIND_MASK) != K_FREE) return;
-  x64[n] = x64[n] + (double)x32[n];
-  x32[n] = 0.f;
+  State4<T>* s = sbuf[st[v].buf];
+  x64[n] = x64[n] + (double)s[n].x;
+  s[n].x = T(0);
 }
 
 // ---------------------------------------------------------------- init / export
 __global__ void k_init(const DevVariant* var, const int* tile_var, const int2* tile_ij, const uint8_t* tag,
-                       const double* X, long long Vtot, double U, int warm, double* x64, double* w64,
-                       void* const* vecs, int nvec, int vbytes) {
+                       const double* X, long long Vtot, double U, int warm, double* x64, double* w64) {
   const long long t = blockIdx.x;
   const int v = tile_var[t];
   const DevVariant& V = var[v];
@@ -652,10 +642,6 @@ __global__ void k_init(const DevVariant* var, const int* tile_var, const int2* t
   else if (kind == K_FREE && warm) u = x64[n];
   x64[n] = u;
   w64[n] = 0.0;
-  for (int k = 0; k < nvec; ++k) {
-    if (vbytes == 8) ((double*)vecs[k])[n] = 0.0;
-    else ((float*)vecs[k])[n] = 0.f;
-  }
 }
 
 __global__ void k_export_psi(const DevVariant* var, int nv, const long long* lbase, const uint8_t* tag,
@@ -909,14 +895,20 @@ static void encode_2d(CUtensorMap* map, void* base, CUtensorMapDataType dt, int 
 }
 
 template <typename T>
-static void make_cg_maps(Batch& b, CgMaps& mp, T* const r[2], T* const p[2], T* const q[2], T* K) {
+static void make_cg_maps(Batch& b, CgMaps& mp, State4<T>* const st[2], T* K) {
   using L = CgSmem<T>;
   const CUtensorMapDataType dt = sizeof(T) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
   const int e = (int)sizeof(T);
   for (int k = 0; k < 2; ++k) {
-    encode_2d(&mp.r[k], r[k], dt, e, b.P, b.Rtot, L::BW, CTY + 2);
-    encode_2d(&mp.p[k], p[k], dt, e, b.P, b.Rtot, L::BW, CTY + 2);
-    encode_2d(&mp.q[k], q[k], dt, e, b.P, b.Rtot, L::BW, CTY + 2);
+    // state records as a 3-D tensor: (component, column, row)
+    const cuuint64_t dims[3] = {4, (cuuint64_t)b.P, (cuuint64_t)b.Rtot};
+    const cuuint64_t strides[2] = {(cuuint64_t)4 * e, (cuuint64_t)b.P * 4 * e};
+    const cuuint32_t box[3] = {4, (cuuint32_t)L::SBW, (cuuint32_t)(CTY + 2)};
+    const cuuint32_t es[3] = {1, 1, 1};
+    const CUresult r = tensor_map_encoder()(&mp.s[k], dt, 3, st[k], dims, strides, box, es,
+                                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) throw Error{PF_ECUDA, "cuTensorMapEncodeTiled (state) failed (" + std::to_string((int)r) + ")"};
   }
   encode_2d(&mp.tag, b.tag, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, b.P, b.Rtot, L::TBW, CTY + 2);
   encode_2d(&mp.k, K, dt, e, b.P, 6 * b.Rtot, L::KBW, CTY + 1);
@@ -928,6 +920,7 @@ void ensure_solver_memory(Batch& b, int precision) {
   if (!b.x64) {
     b.x64 = (double*)dev_alloc(b, V * sizeof(double));
     b.w64 = (double*)dev_alloc(b, V * sizeof(double));
+    b.sol64 = (double*)dev_alloc(b, B * sizeof(double));
     b.sb64 = (double*)dev_alloc(b, 4 * B * sizeof(double));
     b.sb32 = (float*)dev_alloc(b, 4 * B * sizeof(float));
     b.sbr64 = (double*)dev_alloc(b, B * sizeof(double));
@@ -935,28 +928,23 @@ void ensure_solver_memory(Batch& b, int precision) {
     b.params = (SolveParams*)dev_alloc(b, sizeof(SolveParams));
     b.n_done = (int*)dev_alloc(b, 2 * sizeof(int));
     b.d_err = b.n_done + 1;
+    b.d_sbuf = (void**)dev_alloc(b, 4 * sizeof(void*));
     PF_CUDA(cudaMemsetAsync(b.x64, 0, V * sizeof(double), b.stream));
+    PF_CUDA(cudaMemsetAsync(b.sol64, 0, B * sizeof(double), b.stream));
     PF_CUDA(cudaMemsetAsync(b.sb64, 0, 4 * B * sizeof(double), b.stream));
     PF_CUDA(cudaMemsetAsync(b.sb32, 0, 4 * B * sizeof(float), b.stream));
     b.bnorm2_unit.assign(b.nv, -1.0);
     for (int k = 0; k < 6; ++k) PF_CUDA(cudaEventCreate(&b.ev[k]));
   }
-  if (precision == PF_FP64 && !b.r64[0]) {
-    for (int k = 0; k < 2; ++k) {
-      b.r64[k] = (double*)dev_alloc(b, V * sizeof(double));
-      b.p64[k] = (double*)dev_alloc(b, V * sizeof(double));
-      b.q64[k] = (double*)dev_alloc(b, V * sizeof(double));
-    }
-    make_cg_maps<double>(b, b.maps[0], b.r64, b.p64, b.q64, b.K64);
+  if (precision == PF_FP64 && !b.st64[0]) {
+    for (int k = 0; k < 2; ++k) b.st64[k] = (State4<double>*)dev_alloc(b, V * sizeof(State4<double>));
+    make_cg_maps<double>(b, b.maps[0], b.st64, b.K64);
+    PF_CUDA(cudaMemcpy(b.d_sbuf, b.st64, 2 * sizeof(void*), cudaMemcpyHostToDevice));
   }
-  if (precision == PF_MIXED && !b.r32[0]) {
-    b.x32 = (float*)dev_alloc(b, V * sizeof(float));
-    for (int k = 0; k < 2; ++k) {
-      b.r32[k] = (float*)dev_alloc(b, V * sizeof(float));
-      b.p32[k] = (float*)dev_alloc(b, V * sizeof(float));
-      b.q32[k] = (float*)dev_alloc(b, V * sizeof(float));
-    }
-    make_cg_maps<float>(b, b.maps[1], b.r32, b.p32, b.q32, b.K32);
+  if (precision == PF_MIXED && !b.st32[0]) {
+    for (int k = 0; k < 2; ++k) b.st32[k] = (State4<float>*)dev_alloc(b, V * sizeof(State4<float>));
+    make_cg_maps<float>(b, b.maps[1], b.st32, b.K32);
+    PF_CUDA(cudaMemcpy(b.d_sbuf + 2, b.st32, 2 * sizeof(void*), cudaMemcpyHostToDevice));
   }
 }
 
@@ -981,24 +969,28 @@ static double* body_sum_scratch(Batch& b) {
 }
 
 void apply_operator(Batch& b, int precision, const double* dev_p, double* dev_y, double* body_sums) {
-  ensure_solver_memory(b, PF_FP64);
-  ensure_solver_memory(b, PF_MIXED);
+  if (!b.ap64[0]) {
+    for (int k = 0; k < 2; ++k) {
+      b.ap64[k] = (double*)dev_alloc(b, b.Vtot * sizeof(double));
+      b.ap32[k] = (float*)dev_alloc(b, b.Vtot * sizeof(float));
+    }
+  }
   long long* lb = lbase_cached(b);
   const MeshDev m = mesh_dev(b);
   const dim3 g2(512, b.nv);
   double* sums = body_sum_scratch(b);
   if (precision == PF_FP64) {
-    k_to_padded<double><<<g2, 256, 0, b.stream>>>(b.d_var, lb, dev_p, b.r64[0]);
-    PF_CUDA(cudaMemsetAsync(b.q64[0], 0, b.Vtot * sizeof(double), b.stream));
-    k_apply<double><<<(unsigned)b.T, dim3(TX, TY), 0, b.stream>>>(m, b.tile_var, b.tile_ij, b.r64[0], b.q64[0]);
-    k_from_padded<double><<<g2, 256, 0, b.stream>>>(b.d_var, lb, b.q64[0], dev_y);
-    if (b.B) k_body_sums<double><<<b.B, dim3(TX, TY), 0, b.stream>>>(m, b.q64[0], sums);
+    k_to_padded<double><<<g2, 256, 0, b.stream>>>(b.d_var, lb, dev_p, b.ap64[0]);
+    PF_CUDA(cudaMemsetAsync(b.ap64[1], 0, b.Vtot * sizeof(double), b.stream));
+    k_apply<double><<<(unsigned)b.T, dim3(TX, TY), 0, b.stream>>>(m, b.tile_var, b.tile_ij, b.ap64[0], b.ap64[1]);
+    k_from_padded<double><<<g2, 256, 0, b.stream>>>(b.d_var, lb, b.ap64[1], dev_y);
+    if (b.B) k_body_sums<double><<<b.B, dim3(TX, TY), 0, b.stream>>>(m, b.ap64[1], sums);
   } else {
-    k_to_padded<float><<<g2, 256, 0, b.stream>>>(b.d_var, lb, dev_p, b.r32[0]);
-    PF_CUDA(cudaMemsetAsync(b.q32[0], 0, b.Vtot * sizeof(float), b.stream));
-    k_apply<float><<<(unsigned)b.T, dim3(TX, TY), 0, b.stream>>>(m, b.tile_var, b.tile_ij, b.r32[0], b.q32[0]);
-    k_from_padded<float><<<g2, 256, 0, b.stream>>>(b.d_var, lb, b.q32[0], dev_y);
-    if (b.B) k_body_sums<float><<<b.B, dim3(TX, TY), 0, b.stream>>>(m, b.q32[0], sums);
+    k_to_padded<float><<<g2, 256, 0, b.stream>>>(b.d_var, lb, dev_p, b.ap32[0]);
+    PF_CUDA(cudaMemsetAsync(b.ap32[1], 0, b.Vtot * sizeof(float), b.stream));
+    k_apply<float><<<(unsigned)b.T, dim3(TX, TY), 0, b.stream>>>(m, b.tile_var, b.tile_ij, b.ap32[0], b.ap32[1]);
+    k_from_padded<float><<<g2, 256, 0, b.stream>>>(b.d_var, lb, b.ap32[1], dev_y);
+    if (b.B) k_body_sums<float><<<b.B, dim3(TX, TY), 0, b.stream>>>(m, b.ap32[1], sums);
   }
   PF_CUDA(cudaGetLastError());
   if (body_sums && b.B) {
@@ -1008,8 +1000,7 @@ void apply_operator(Batch& b, int precision, const double* dev_p, double* dev_y,
 }
 
 template <typename T>
-static void fill_cg_args(Batch& b, CGArgs<T>& a, T* x, T* const r[2], T* const p[2], T* const q[2], T* sb,
-                         const Sched& sc) {
+static void fill_cg_args(Batch& b, CGArgs<T>& a, State4<T>* const st[2], T* sb, const Sched& sc) {
   a.m = mesh_dev(b);
   a.sc = sc;
   a.tile_gen = b.tile_cg_gen;
@@ -1017,32 +1008,24 @@ static void fill_cg_args(Batch& b, CGArgs<T>& a, T* x, T* const r[2], T* const p
   a.err = b.d_err;
   a.st = b.state;
   a.prm = b.params;
-  a.x = x;
-  for (int k = 0; k < 2; ++k) {
-    a.r[k] = r[k];
-    a.p[k] = p[k];
-    a.q[k] = q[k];
-  }
+  a.s[0] = st[0];
+  a.s[1] = st[1];
   a.sb = sb;
   a.B = std::max(1, b.B);
   a.n_done = b.n_done;
 }
 
 template <typename T>
-static void fill_resid_args(Batch& b, ResidArgs<T>& a, T* const r[2], T* const p[2], T* const q[2], T* sb,
-                            int mixed) {
+static void fill_resid_args(Batch& b, ResidArgs<T>& a, State4<T>* const st[2], T* sb, int mixed) {
   a.m = mesh_dev(b);
   a.sc = b.sched;
   a.st = b.state;
   a.prm = b.params;
   a.x64 = b.x64;
   a.w64 = b.w64;
-  for (int k = 0; k < 2; ++k) {
-    a.r[k] = r[k];
-    a.p[k] = p[k];
-    a.q[k] = q[k];
-  }
-  a.sb64 = b.sb64;
+  a.s[0] = st[0];
+  a.s[1] = st[1];
+  a.sol = b.sol64;
   a.sb = sb;
   a.sbr = b.sbr64;
   a.B = std::max(1, b.B);
@@ -1057,14 +1040,14 @@ static void launch_cg_chunk(Batch& b, int precision, int chunk, cudaStream_t s) 
   CgConfig& c = cg_config(b, precision, ns);
   if (precision == PF_FP64) {
     CGArgs<double> a;
-    fill_cg_args<double>(b, a, b.x64, b.r64, b.p64, b.q64, b.sb64, c.sc);
+    fill_cg_args<double>(b, a, b.st64, b.sb64, c.sc);
     for (int k = 0; k < chunk; ++k) {
       if (ns == 3) k_cg<double, 3><<<c.G, blk, c.smem, s>>>(a, b.maps[0]);
       else k_cg<double, 2><<<c.G, blk, c.smem, s>>>(a, b.maps[0]);
     }
   } else {
     CGArgs<float> a;
-    fill_cg_args<float>(b, a, b.x32, b.r32, b.p32, b.q32, b.sb32, c.sc);
+    fill_cg_args<float>(b, a, b.st32, b.sb32, c.sc);
     for (int k = 0; k < chunk; ++k) {
       if (ns == 3) k_cg<float, 3><<<c.G, blk, c.smem, s>>>(a, b.maps[1]);
       else k_cg<float, 2><<<c.G, blk, c.smem, s>>>(a, b.maps[1]);
@@ -1076,13 +1059,16 @@ static void launch_cg_chunk(Batch& b, int precision, int chunk, cudaStream_t s) 
 static void launch_resid_only(Batch& b, int precision, cudaStream_t s) {
   const dim3 blk(TX, TY);
   if (precision == PF_FP64) {
+    k_fold<double><<<(unsigned)b.T, blk, 0, s>>>(b.d_var, b.tile_var, b.tile_ij, b.tag, b.state, b.x64,
+                                                 (State4<double>* const*)b.d_sbuf);
     ResidArgs<double> ra;
-    fill_resid_args<double>(b, ra, b.r64, b.p64, b.q64, b.sb64, 0);
+    fill_resid_args<double>(b, ra, b.st64, b.sb64, 0);
     k_resid<double><<<b.G, blk, 0, s>>>(ra);
   } else {
-    k_fold<<<(unsigned)b.T, blk, 0, s>>>(b.d_var, b.tile_var, b.tile_ij, b.tag, b.state, b.x64, b.x32);
+    k_fold<float><<<(unsigned)b.T, blk, 0, s>>>(b.d_var, b.tile_var, b.tile_ij, b.tag, b.state, b.x64,
+                                                (State4<float>* const*)(b.d_sbuf + 2));
     ResidArgs<float> ra;
-    fill_resid_args<float>(b, ra, b.r32, b.p32, b.q32, b.sb32, 1);
+    fill_resid_args<float>(b, ra, b.st32, b.sb32, 1);
     k_resid<float><<<b.G, blk, 0, s>>>(ra);
   }
   PF_CUDA(cudaGetLastError());
@@ -1144,23 +1130,15 @@ pf_status psi_solve(Batch& b, double U, const pf_solve_opts& o, double* dev_psi,
   PF_CUDA(cudaMemcpyAsync(b.state, st.data(), b.nv * sizeof(VarState), cudaMemcpyHostToDevice, s));
   PF_CUDA(cudaMemsetAsync(b.n_done, 0, 2 * sizeof(int), s));
   const int B = std::max(1, b.B);
-  if (!warm) PF_CUDA(cudaMemsetAsync(b.sb64, 0, 4 * B * sizeof(double), s));
-  else PF_CUDA(cudaMemsetAsync(b.sb64 + B, 0, 3 * B * sizeof(double), s));
+  if (!warm) PF_CUDA(cudaMemsetAsync(b.sol64, 0, B * sizeof(double), s));
+  PF_CUDA(cudaMemsetAsync(b.sb64, 0, 4 * B * sizeof(double), s));
   PF_CUDA(cudaMemsetAsync(b.sb32, 0, 4 * B * sizeof(float), s));
-  {
-    void* vecs[7];
-    int nvec = 0;
-    if (prec == PF_FP64) {
-      for (int k = 0; k < 2; ++k) { vecs[nvec++] = b.r64[k]; vecs[nvec++] = b.p64[k]; vecs[nvec++] = b.q64[k]; }
-    } else {
-      for (int k = 0; k < 2; ++k) { vecs[nvec++] = b.r32[k]; vecs[nvec++] = b.p32[k]; vecs[nvec++] = b.q32[k]; }
-      vecs[nvec++] = b.x32;
-    }
-    if (!b.d_vecs) b.d_vecs = (void**)dev_alloc(b, 8 * sizeof(void*));
-    PF_CUDA(cudaMemcpyAsync(b.d_vecs, vecs, nvec * sizeof(void*), cudaMemcpyHostToDevice, s));
-    k_init<<<(unsigned)b.T, dim3(TX, TY), 0, s>>>(b.d_var, b.tile_var, b.tile_ij, b.tag, b.X, b.Vtot, U, warm, b.x64,
-                                                  b.w64, b.d_vecs, nvec, prec == PF_FP64 ? 8 : 4);
+  for (int k = 0; k < 2; ++k) {
+    if (prec == PF_FP64) PF_CUDA(cudaMemsetAsync(b.st64[k], 0, b.Vtot * sizeof(State4<double>), s));
+    else PF_CUDA(cudaMemsetAsync(b.st32[k], 0, b.Vtot * sizeof(State4<float>), s));
   }
+  k_init<<<(unsigned)b.T, dim3(TX, TY), 0, s>>>(b.d_var, b.tile_var, b.tile_ij, b.tag, b.X, b.Vtot, U, warm, b.x64,
+                                                b.w64);
   PF_CUDA(cudaGetLastError());
   PF_CUDA(cudaEventRecord(b.ev[3], s));
   launch_resid_only(b, prec, s);
@@ -1195,7 +1173,7 @@ pf_status psi_solve(Batch& b, double U, const pf_solve_opts& o, double* dev_psi,
     if (hdone[0] >= b.nv) break;
   }
   PF_CUDA(cudaEventRecord(b.ev[4], s));
-  b.launches += 1 + launches + (long long)rlaunches * (prec == PF_MIXED ? 2 : 1);
+  b.launches += 1 + launches + (long long)rlaunches * 2;
   std::vector<VarState> fin(b.nv);
   PF_CUDA(cudaMemcpyAsync(fin.data(), b.state, b.nv * sizeof(VarState), cudaMemcpyDeviceToHost, s));
   PF_CUDA(cudaStreamSynchronize(s));
@@ -1213,7 +1191,7 @@ pf_status psi_solve(Batch& b, double U, const pf_solve_opts& o, double* dev_psi,
     if (S.status != PF_OK && ret == PF_OK) ret = S.status;
     if (b.bnorm2_unit[v] < 0 && S.bnorm2 >= 0 && U != 0) b.bnorm2_unit[v] = S.bnorm2 / (U * U);
     const double per_node_free = prec == PF_MIXED ? 32.0 : 64.0;
-    const double per_body = prec == PF_MIXED ? 8.0 : 12.0;
+    const double per_body = prec == PF_MIXED ? 20.0 : 36.0;
     const double per_gen = prec == PF_MIXED ? 24.0 : 48.0;
     const double bv = per_node_free * M.n_free + per_body * M.n_body_nodes + 1.0 * M.n_nodes +
                       per_gen * M.n_general_cells;
@@ -1234,7 +1212,7 @@ pf_status psi_solve(Batch& b, double U, const pf_solve_opts& o, double* dev_psi,
   b.timing.cg_bytes_per_launch = launches > 0 ? bytes_done / (double)launches : 0.0;
   if (dev_psi) export_psi(b, dev_psi);
   if (body_psi && b.B) {
-    PF_CUDA(cudaMemcpyAsync(body_psi, b.sb64, b.B * sizeof(double), cudaMemcpyDeviceToHost, s));
+    PF_CUDA(cudaMemcpyAsync(body_psi, b.sol64, b.B * sizeof(double), cudaMemcpyDeviceToHost, s));
     PF_CUDA(cudaStreamSynchronize(s));
   }
   return ret;
@@ -1243,14 +1221,14 @@ pf_status psi_solve(Batch& b, double U, const pf_solve_opts& o, double* dev_psi,
 void export_psi(Batch& b, double* dev_psi) {
   long long* lb = lbase_cached(b);
   b.launches += 1;
-  k_export_psi<<<dim3(256, b.nv), 256, 0, b.stream>>>(b.d_var, b.nv, lb, b.tag, b.bid, b.x64, b.sb64, dev_psi);
+  k_export_psi<<<dim3(256, b.nv), 256, 0, b.stream>>>(b.d_var, b.nv, lb, b.tag, b.bid, b.x64, b.sol64, dev_psi);
   PF_CUDA(cudaGetLastError());
 }
 
 void body_values(Batch& b, std::vector<double>& C) {
   C.assign(b.B, 0.0);
-  if (!b.B || !b.sb64) return;
-  PF_CUDA(cudaMemcpyAsync(C.data(), b.sb64, b.B * sizeof(double), cudaMemcpyDeviceToHost, b.stream));
+  if (!b.B || !b.sol64) return;
+  PF_CUDA(cudaMemcpyAsync(C.data(), b.sol64, b.B * sizeof(double), cudaMemcpyDeviceToHost, b.stream));
   PF_CUDA(cudaStreamSynchronize(b.stream));
 }
 

@@ -11,7 +11,7 @@ namespace pfq4 {
 constexpr int MBAR_POLL_LIMIT = 1 << 22;
 
 struct CgMaps {                 // TMA descriptors of the fused CG kernel (__grid_constant__ parameter)
-  CUtensorMap r[2], p[2], q[2], tag, k;
+  CUtensorMap s[2], tag, k;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -59,6 +59,14 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
   asm volatile(
       "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
       ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// 3-D tiled TMA load of one box at (x, y, z) into shared memory.
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
       : "memory");
 }
 
