@@ -25,8 +25,8 @@ constexpr int NT = TX * TY;          // threads per CTA
 constexpr int SW = TX + 2;           // shared tile row width with halo
 constexpr int NHALO = 2 * SW + 2 * TY;
 constexpr int MAXB = 64;             // bodies per variant
-constexpr int CTX = 64;              // fused-CG tile: 64 x 8 nodes, 2 per thread
-constexpr int CTY = 8;
+constexpr int CTX = 64;              // fused-CG tile: 64 x 16 nodes, a 4-node vertical strip per thread
+constexpr int CTY = 16;
 
 // node tag byte
 constexpr uint8_t KIND_MASK = 3;
@@ -146,6 +146,11 @@ template <> struct Acc<double> {
   __device__ void zero() { v[0] = v[1] = v[2] = v[3] = 0.0; }
   __device__ void add(int k, double x, double y) { v[k] = fma(x, y, v[k]); }
   __device__ void add2(int k, double x1, double y1, double x2, double y2) { v[k] = fma(x2, y2, fma(x1, y1, v[k])); }
+  template <int N>
+  __device__ void add4(int k, const double (&x)[N], const double (&y)[N]) {
+#pragma unroll
+    for (int u = 0; u < N; ++u) v[k] = fma(x[u], y[u], v[k]);
+  }
   // warp-reduce, lane 0 returns the sums
   __device__ void warp_reduce(double out[4]) {
 #pragma unroll
@@ -168,6 +173,15 @@ template <> struct Acc<float> {
   // pair sum accumulated with compensation (error <= 2^-23 (|x1 y1| + |x2 y2|) per pair,
   // no growth with the number of pairs beyond the two-float accumulation error)
   __device__ void add2(int k, float x1, float y1, float x2, float y2) { ff_add_value(v[k], fmaf(x1, y1, x2 * y2)); }
+  // a thread's N products of one tile strip: each rounded to FP32, summed in FP32, the
+  // group sum accumulated with compensation (error <= N 2^-24 sum |x_u y_u| per group)
+  template <int N>
+  __device__ void add4(int k, const float (&x)[N], const float (&y)[N]) {
+    float g = x[0] * y[0];
+#pragma unroll
+    for (int u = 1; u < N; ++u) g = fmaf(x[u], y[u], g);
+    ff_add_value(v[k], g);
+  }
   __device__ void warp_reduce(double out[4]) {
 #pragma unroll
     for (int k = 0; k < 4; ++k) {

@@ -200,65 +200,61 @@ struct CgSmem {
   static constexpr int total = off_bar + 128;
 };
 
-// Row of the operator at ptile position (li, lj) with cell coefficients taken from the
-// staged planes (FP32) or from global memory (FP64), closed form for undisplaced cells.
+// Row of the operator at one node from its 3x3 neighbourhood p[3][3] (p[1][1] = the
+// node, first index = row j-1, j, j+1, second = column i-1, i, i+1) and the tags of its
+// four cells: c0 = (i, j), c1 = (i-1, j), c2 = (i-1, j-1), c3 = (i, j-1).  Displaced
+// cells read their six coefficients from the staged planes (FP32) or global memory
+// (FP64); undisplaced cells use the closed-form rectangle constants kr.
 template <typename T>
-__device__ __forceinline__ T q4_row_tile(const T* pt, const uint8_t* tt, const T* ks, int li, int lj, long long n,
-                                         int P, const T* __restrict__ Kg, long long plane, const T* kr) {
+__device__ __forceinline__ T q4_row_nb(const T (&p)[3][3], uint8_t c0, uint8_t c1, uint8_t c2, uint8_t c3,
+                                       const T* ks, int kcol, int krow, long long n, int P,
+                                       const T* __restrict__ Kg, long long plane, const T* kr) {
   using L = CgSmem<T>;
-  constexpr int W = CTX + 2;
-  const T pc = pt[lj * W + li];
-  const T dE = pt[lj * W + li + 1] - pc, dW = pt[lj * W + li - 1] - pc;
-  const T dN = pt[(lj + 1) * W + li] - pc, dS = pt[(lj - 1) * W + li] - pc;
-  const T dNE = pt[(lj + 1) * W + li + 1] - pc, dNW = pt[(lj + 1) * W + li - 1] - pc;
-  const T dSE = pt[(lj - 1) * W + li + 1] - pc, dSW = pt[(lj - 1) * W + li - 1] - pc;
-  const int kp = L::kplane_bytes / (int)sizeof(T);
-  auto coef = [&](int m, int crow, int ccol, long long gidx) -> T {
-    if constexpr (L::kTmaK) {
-      return ks[m * kp + crow * L::KBW + ccol];
-    } else {
-      return __ldg(Kg + m * plane + gidx);
-    }
-  };
-  const uint8_t c0 = tt[lj * W + li], c1 = tt[lj * W + li - 1], c2 = tt[(lj - 1) * W + li - 1],
-                c3 = tt[(lj - 1) * W + li];
+  const T pc = p[1][1];
+  const T dE = p[1][2] - pc, dW = p[1][0] - pc, dN = p[2][1] - pc, dS = p[0][1] - pc;
+  const T dNE = p[2][2] - pc, dNW = p[2][0] - pc, dSE = p[0][2] - pc, dSW = p[0][0] - pc;
   constexpr uint8_t FLAGS = CELL_ACTIVE | CELL_GENERAL;
   if ((c0 & FLAGS) == CELL_ACTIVE && (c1 & FLAGS) == CELL_ACTIVE && (c2 & FLAGS) == CELL_ACTIVE &&
       (c3 & FLAGS) == CELL_ACTIVE) {
-    // all four cells are undisplaced rectangles: K23 = K01, K12 = K03, K13 = K02, so the
-    // row collapses to 2 K01 (dE + dW) + 2 K03 (dN + dS) + K02 (sum of diagonals)
+    // four undisplaced rectangles: K23 = K01, K12 = K03, K13 = K02, so the row is
+    // 2 K01 (dE + dW) + 2 K03 (dN + dS) + K02 (sum of the diagonal differences)
     return T(2) * kr[0] * (dE + dW) + T(2) * kr[2] * (dN + dS) + kr[1] * ((dNE + dSW) + (dNW + dSE));
   }
+  constexpr int kp = L::kplane_bytes / (int)sizeof(T);
+  // coefficient m of the cell whose corner 0 is at box column kc, box row kr_, global index g
+  auto coef = [&](int m, int kr_, int kc, long long g) -> T {
+    if constexpr (L::kTmaK) {
+      return ks[m * kp + kr_ * L::KBW + kc];
+    } else {
+      return __ldg(Kg + m * plane + g);
+    }
+  };
   T y = T(0);
-  uint8_t t = c0;                                   // cell (i, j): corner 0
-  if (t & CELL_ACTIVE) {
+  if (c0 & CELL_ACTIVE) {                         // node is corner 0 of cell (i, j)
     T k01 = kr[0], k02 = kr[1], k03 = kr[2];
-    if (t & CELL_GENERAL) { k01 = coef(0, lj, li + 3, n); k02 = coef(1, lj, li + 3, n); k03 = coef(2, lj, li + 3, n); }
+    if (c0 & CELL_GENERAL) { k01 = coef(0, krow, kcol, n); k02 = coef(1, krow, kcol, n); k03 = coef(2, krow, kcol, n); }
     y += k01 * dE + k02 * dNE + k03 * dN;
   }
-  t = c1;                                           // cell (i-1, j): corner 1
-  if (t & CELL_ACTIVE) {
+  if (c1 & CELL_ACTIVE) {                         // corner 1 of cell (i-1, j)
     T k01 = kr[0], k12 = kr[3], k13 = kr[4];
-    if (t & CELL_GENERAL) {
-      k01 = coef(0, lj, li + 2, n - 1); k12 = coef(3, lj, li + 2, n - 1); k13 = coef(4, lj, li + 2, n - 1);
+    if (c1 & CELL_GENERAL) {
+      k01 = coef(0, krow, kcol - 1, n - 1); k12 = coef(3, krow, kcol - 1, n - 1); k13 = coef(4, krow, kcol - 1, n - 1);
     }
     y += k01 * dW + k12 * dN + k13 * dNW;
   }
-  t = c2;                                           // cell (i-1, j-1): corner 2
-  if (t & CELL_ACTIVE) {
+  if (c2 & CELL_ACTIVE) {                         // corner 2 of cell (i-1, j-1)
     T k02 = kr[1], k12 = kr[3], k23 = kr[5];
-    if (t & CELL_GENERAL) {
+    if (c2 & CELL_GENERAL) {
       const long long c = n - P - 1;
-      k02 = coef(1, lj - 1, li + 2, c); k12 = coef(3, lj - 1, li + 2, c); k23 = coef(5, lj - 1, li + 2, c);
+      k02 = coef(1, krow - 1, kcol - 1, c); k12 = coef(3, krow - 1, kcol - 1, c); k23 = coef(5, krow - 1, kcol - 1, c);
     }
     y += k02 * dSW + k12 * dS + k23 * dW;
   }
-  t = c3;                                           // cell (i, j-1): corner 3
-  if (t & CELL_ACTIVE) {
+  if (c3 & CELL_ACTIVE) {                         // corner 3 of cell (i, j-1)
     T k03 = kr[2], k13 = kr[4], k23 = kr[5];
-    if (t & CELL_GENERAL) {
+    if (c3 & CELL_GENERAL) {
       const long long c = n - P;
-      k03 = coef(2, lj - 1, li + 3, c); k13 = coef(4, lj - 1, li + 3, c); k23 = coef(5, lj - 1, li + 3, c);
+      k03 = coef(2, krow - 1, kcol, c); k13 = coef(4, krow - 1, kcol, c); k23 = coef(5, krow - 1, kcol, c);
     }
     y += k03 * dS + k13 * dSE + k23 * dE;
   }
@@ -281,8 +277,12 @@ __device__ __forceinline__ void cg_issue(const CgMaps& mp, int cur, unsigned cha
   }
 }
 
+// Nodes per thread (a vertical strip) and the thread -> strip mapping of a tile.
+constexpr int STRIP = CTY * CTX / NT;             // 4
+static_assert(STRIP * NT == CTX * CTY, "tile must split into strips");
+
 template <typename T, int NS>
-__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 4 : 2) k_cg(CGArgs<T> a, const __grid_constant__ CgMaps mp) {
+__global__ void __launch_bounds__(NT, 2) k_cg(CGArgs<T> a, const __grid_constant__ CgMaps mp) {
   using L = CgSmem<T, NS>;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ T s_pb[MAXB];
@@ -294,9 +294,12 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 4 : 2) k_cg(CGArgs<T> a, 
   uint8_t* tt = reinterpret_cast<uint8_t*>(smem + L::off_ttile);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::off_bar);
   const int tid = linear_tid(), lane = tid & 31, warp = tid >> 5;
+  const int col = tid % CTX;                      // strip column inside the tile
+  const int row_lo = (tid / CTX) * STRIP;         // first strip row inside the tile
   const int B = a.B;
   const long long plane = a.m.Vtot;
   constexpr int W = CTX + 2;
+  constexpr int NH = 2 * W + 2 * CTY;             // halo ring positions
   if (tid == 0) {
     for (int k = 0; k < NS; ++k) mbar_init(&bars[k], 1);
     fence_mbar_init();
@@ -340,47 +343,37 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 4 : 2) k_cg(CGArgs<T> a, 
       if (t + 1 < t1) ij_next = a.sc.tile_ij[t + 1];
       const bool ok = mbar_wait(&bars[s], (parity >> s) & 1u);
       parity ^= 1u << s;
-      if (__syncthreads_or(!ok)) {
-        if (tid == 0) atomicExch(a.err, 1);
-        // drain the stages whose loads may still be in flight (bounded), then leave
-        for (int k = 1; k < NS && t + k < t1; ++k) {
-          const int s2 = (t + k - t0) % NS;
-          mbar_wait(&bars[s2], (parity >> s2) & 1u);
-        }
-        return;
-      }
       const State4<T>* Ss = reinterpret_cast<const State4<T>*>(st + L::off_s);
       const uint8_t* Tg = reinterpret_cast<const uint8_t*>(st + L::off_t);
       const T* Ks = reinterpret_cast<const T*>(st + L::off_k);
-      // global index of the tile's node (i0, j0); own node (li, lj) is at tb + (lj-1)*P + li-1
+      // global index of the tile's node (i0, j0)
       const long long tb = base + (long long)ij.y * P + ij.x;
-      // pass 1: own nodes (2 per thread) and the halo ring -> p tile, effective tags
-      T rn2[2], pn2[2], xn2[2];
-      uint8_t tg2[2];
+      // pass 1: own strip and the halo ring -> p tile, effective tags
+      T rn4[STRIP], pn4[STRIP], xn4[STRIP];
+      uint8_t tg4[STRIP];
+      if (ok) {
 #pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        const int li = 1 + threadIdx.x + 32 * u, lj = 1 + threadIdx.y;
-        const int i = ij.x - 1 + li, j = ij.y - 1 + lj;
-        const bool in = (i <= nx) && (j <= ny);
-        uint8_t tg = in ? Tg[lj * L::TBW + li + 15] : K_INACT;
-        const int kind = tg & KIND_MASK;
-        T rn = T(0), pn = T(0), xn = T(0);
-        if (kind == K_FREE) {
-          const State4<T> o = Ss[lj * L::SBW + li];
-          rn = next_r(o.r, o.q, alpha);
-          xn = next_x(o.x, o.p, alpha);
-          pn = next_p(rn, o.p, beta);
-        } else if (kind == K_BODY) {
-          pn = s_pb[a.m.bid[tb + (lj - 1) * P + (li - 1)]];
+        for (int u = 0; u < STRIP; ++u) {
+          const int li = 1 + col, lj = 1 + row_lo + u;
+          const int i = ij.x + col, j = ij.y + row_lo + u;
+          const bool in = (i <= nx) && (j <= ny);
+          const uint8_t tg = in ? Tg[lj * L::TBW + li + 15] : K_INACT;
+          const int kind = tg & KIND_MASK;
+          T rn = T(0), pn = T(0), xn = T(0);
+          if (kind == K_FREE) {
+            const State4<T> o = Ss[lj * L::SBW + li];
+            rn = next_r(o.r, o.q, alpha);
+            xn = next_x(o.x, o.p, alpha);
+            pn = next_p(rn, o.p, beta);
+          } else if (kind == K_BODY) {
+            pn = s_pb[a.m.bid[tb + (long long)(row_lo + u) * P + col]];
+          }
+          pt[lj * W + li] = pn;
+          tt[lj * W + li] = tg;
+          rn4[u] = rn; pn4[u] = pn; xn4[u] = xn; tg4[u] = tg;
         }
-        pt[lj * W + li] = pn;
-        tt[lj * W + li] = tg;
-        rn2[u] = rn; pn2[u] = pn; xn2[u] = xn; tg2[u] = tg;
-      }
-      {
-        // halo ring positions spread over all eight warps (lanes 0..18 of each)
-        const int h = warp + (NT / 32) * lane;
-        if (h < 2 * W + 2 * CTY) {
+        // halo ring positions spread over all eight warps
+        for (int h = warp + (NT / 32) * lane; h < NH; h += NT) {
           int li, lj;
           if (h < W) { li = h; lj = 0; }
           else if (h < 2 * W) { li = h - W; lj = CTY + 1; }
@@ -395,45 +388,74 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 4 : 2) k_cg(CGArgs<T> a, 
             if (hk == K_FREE) {
               const State4<T> o = Ss[lj * L::SBW + li];
               hp = next_p(next_r(o.r, o.q, alpha), o.p, beta);
-            }
-            else if (hk == K_BODY)
+            } else if (hk == K_BODY) {
               hp = s_pb[a.m.bid[tb + (long long)(lj - 1) * P + (li - 1)]];
+            }
           }
           pt[lj * W + li] = hp;
           tt[lj * W + li] = ht;
         }
       }
-      __syncthreads();
-      // pass 2: operator rows of the own nodes, stores, dots
-      T yq[2], rr[2], pp[2];
+      if (__syncthreads_or(!ok)) {
+        if (tid == 0) atomicExch(a.err, 1);
+        // drain the stages whose loads may still be in flight (bounded), then leave
+        for (int k = 1; k < NS && t + k < t1; ++k) {
+          const int s2 = (t + k - t0) % NS;
+          mbar_wait(&bars[s2], (parity >> s2) & 1u);
+        }
+        return;
+      }
+      // pass 2: operator rows of the strip from a register window of the p tile
+      {
+        const int li = 1 + col;
+        T win[STRIP + 2][3];
+        uint8_t cl[STRIP + 1], cr[STRIP + 1];     // cells (i-1, j) and (i, j) for rows j0-1 .. j0+3
 #pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        const int li = 1 + threadIdx.x + 32 * u, lj = 1 + threadIdx.y;
-        const int kind = tg2[u] & KIND_MASK;
-        yq[u] = T(0);
-        rr[u] = T(0);
-        pp[u] = T(0);
-        if (kind == K_FREE || kind == K_BODY) {
-          const long long n = tb + (lj - 1) * P + (li - 1);
-          const T y = q4_row_tile<T>(pt, tt, Ks, li, lj, n, P, kplane<T>(a.m), plane, kr);
-          State4<T> o;
-          o.x = xn2[u];
-          o.r = rn2[u];
-          o.p = pn2[u];
-          o.q = y;
-          s_new[n] = o;            // BODY nodes carry only q (x, r, p are zero there)
-          if (kind == K_FREE) {
-            yq[u] = y;
-            rr[u] = rn2[u];
-            pp[u] = pn2[u];
+        for (int r = 0; r < STRIP + 2; ++r) {
+          const int lj = row_lo + r;              // p tile rows row_lo .. row_lo + STRIP + 1
+          win[r][0] = pt[lj * W + li - 1];
+          win[r][1] = pt[lj * W + li];
+          win[r][2] = pt[lj * W + li + 1];
+        }
+#pragma unroll
+        for (int r = 0; r < STRIP + 1; ++r) {
+          const int lj = row_lo + r;
+          cl[r] = tt[lj * W + li - 1];
+          cr[r] = tt[lj * W + li];
+        }
+        T yq[STRIP], rr[STRIP], pp[STRIP];
+#pragma unroll
+        for (int u = 0; u < STRIP; ++u) {
+          const int kind = tg4[u] & KIND_MASK;
+          yq[u] = T(0);
+          rr[u] = T(0);
+          pp[u] = T(0);
+          if (kind == K_FREE || kind == K_BODY) {
+            const long long n = tb + (long long)(row_lo + u) * P + col;
+            const T nbh[3][3] = {{win[u][0], win[u][1], win[u][2]},
+                                 {win[u + 1][0], win[u + 1][1], win[u + 1][2]},
+                                 {win[u + 2][0], win[u + 2][1], win[u + 2][2]}};
+            const T y = q4_row_nb<T>(nbh, cr[u + 1], cl[u + 1], cl[u], cr[u], Ks, col + 4, row_lo + u + 1, n, P,
+                                     kplane<T>(a.m), plane, kr);
+            State4<T> o;
+            o.x = xn4[u];
+            o.r = rn4[u];
+            o.p = pn4[u];
+            o.q = y;
+            s_new[n] = o;          // BODY nodes carry only q (x, r, p are zero there)
+            if (kind == K_FREE) {
+              yq[u] = y;
+              rr[u] = rn4[u];
+              pp[u] = pn4[u];
+            }
           }
         }
+        // dots over the FREE nodes (others contribute exact zeros)
+        acc.add4(0, rr, rr);
+        acc.add4(1, pp, yq);
+        acc.add4(2, rr, yq);
+        acc.add4(3, yq, yq);
       }
-      // dots over the FREE nodes (others contribute exact zeros)
-      acc.add2(0, rr[0], rr[0], rr[1], rr[1]);
-      acc.add2(1, pp[0], yq[0], pp[1], yq[1]);
-      acc.add2(2, rr[0], yq[0], rr[1], yq[1]);
-      acc.add2(3, yq[0], yq[0], yq[1], yq[1]);
       __syncthreads();
       if (tid == 0 && t + NS < t1) {
         fence_proxy_async_smem();
