@@ -113,20 +113,40 @@ __device__ double body_gather_q(const MeshDev& m, int gb, const State4<T>* st, d
 }
 
 // ---------------------------------------------------------------- fused CG step
+__device__ __forceinline__ double warp_sum(double x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
 template <typename T>
 __device__ void finalize_cg(const CGArgs<T>& a, int v, double* scratch, double* sh_qb) {
   const DevVariant& V = a.m.var[v];
   VarState* S = &a.st[v];
-  double d[4];
-  reduce_partials(a.sc, v, 4, d, scratch);
+  const int tid = linear_tid(), warp = tid >> 5, lane = tid & 31;
+  double* d = scratch;                       // d[0..3]: the four dots over FREE nodes
+  // warps 0-3: dot k = warp over the variant's segment partials (fixed order)
+  if (warp < 4) {
+    double s = 0.0;
+    for (int sg = a.sc.var_seg0[v] + lane; sg < a.sc.var_seg1[v]; sg += 32) s += __ldcg(&a.sc.partial[sg * 4 + warp]);
+    s = warp_sum(s);
+    if (lane == 0) d[warp] = s;
+  }
+  // warps 4-7: collapsed body rows of q (the new parity), one warp per body
   const State4<T>* snew = a.s[S->buf ^ 1];
-  for (int k = 0; k < V.nb; ++k) {
-    const double s = body_gather_q<T>(a.m, V.body0 + k, snew, scratch);
-    if (linear_tid() == 0) sh_qb[k] = s;
+  for (int k = warp - 4; k < V.nb; k += NT / 32 - 4) {
+    if (k < 0) continue;
+    const int gb = V.body0 + k;
+    double s = 0.0;
+    for (int e = a.m.body_ptr[gb] + lane; e < a.m.body_ptr[gb + 1]; e += 32)
+      s += (double)__ldcg(&snew[a.m.body_nodes[e]].q);
+    s = warp_sum(s);
+    if (lane == 0) sh_qb[k] = s;
   }
   __syncthreads();
   if (linear_tid() == 0) {
     const T alpha = (T)S->alpha, beta = (T)S->beta;
+    double dd[4] = {d[0], d[1], d[2], d[3]};
     const int B = a.B;
     for (int k = 0; k < V.nb; ++k) {
       const int gb = V.body0 + k;
@@ -139,12 +159,12 @@ __device__ void finalize_cg(const CGArgs<T>& a, int v, double* scratch, double* 
       a.sb[B + gb] = rn;
       a.sb[2 * B + gb] = pn;
       a.sb[3 * B + gb] = qn;
-      d[0] += (double)rn * (double)rn;
-      d[1] += (double)pn * (double)qn;
-      d[2] += (double)rn * (double)qn;
-      d[3] += (double)qn * (double)qn;
+      dd[0] += (double)rn * (double)rn;
+      dd[1] += (double)pn * (double)qn;
+      dd[2] += (double)rn * (double)qn;
+      dd[3] += (double)qn * (double)qn;
     }
-    const double g = d[0], pi = d[1], rho = d[2], mu = d[3];
+    const double g = dd[0], pi = dd[1], rho = dd[2], mu = dd[3];
     S->buf ^= 1;
     S->iters += 1;
     S->inner_iters += 1;
