@@ -109,6 +109,13 @@ struct Batch {
   double* ap64[2] = {nullptr, nullptr};   // pf_apply scratch (padded in / out)
   float* ap32[2] = {nullptr, nullptr};
   double* sbr64 = nullptr;           // [B] FP64 true-residual body rows
+  double* d_rhsb = nullptr;          // [B] body-row right-hand side of the adjoint solve
+  bool rhs_active = false;
+  double* psi_save = nullptr;        // [Vtot] forward solution kept during the adjoint solve
+  double* sol_save = nullptr;        // [B]
+  double* gradX = nullptr;           // [2][Vtot] dJ/dX (padded), then the transposed sweeps
+  double* gradT = nullptr;           // [2][Vtot] ping-pong partner of gradX
+  double* cellG = nullptr;           // [8][Vtot] per-cell shape derivatives
   void** d_vecs = nullptr;           // device list of the vectors k_init clears
   bool solved = false;
   double lastU = 0.0;
@@ -150,6 +157,9 @@ void ensure_solver_memory(Batch& b, int precision);
 void apply_operator(Batch& b, int precision, const double* dev_p, double* dev_y, double* body_sums);
 pf_status psi_solve(Batch& b, double U, const pf_solve_opts& o, double* dev_psi, double* body_psi,
                     pf_solve_info* info);
+pf_status solve_core(Batch& b, double U, const pf_solve_opts& o, double* dev_psi, double* body_psi,
+                     pf_solve_info* info, bool record_bnorm);
+long long* lbase_cached(Batch& b);
 void export_psi(Batch& b, double* dev_psi);
 void body_values(Batch& b, std::vector<double>& C);
 

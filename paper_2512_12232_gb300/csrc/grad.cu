@@ -1,12 +1,333 @@
-// Adjoint shape gradients (placeholder until the adjoint kernels land).
+// Adjoint shape gradients of J = C_hi - C_lo (transverse-gap flow) or
+// J = (C_hi - C_lo) / (U (cy_hi - cy_lo)) (CoPFI, section "Effect of Gap Ratio") with
+// respect to the smoothed node coordinates X and the body centres c.  The paper has
+// no gradient; its conclusions name shape optimisation and sensitivity analysis.
+//
+// With the reduced residual R(u, X) = P^T K(X) psi(u, X) (P collapses body rows, psi
+// carries the Dirichlet data g = U y) and the adjoint A lambda = dJ/du,
+//   dJ/dX = - sum_e Lambda_e^T (dK_e/dX) psi_e - U (K Lambda)_n  [y of Dirichlet nodes]
+// The element term is the shape derivative of the 2x2-Gauss form: for a corner a and
+// a component c, d/dx_{a,c} [det J grad(lambda).grad(psi)] at a Gauss point equals
+//   det J [ (grad lambda . grad psi) dN_a/dx_c - d_c lambda (grad N_a . grad psi)
+//                                             - d_c psi (grad N_a . grad lambda) ],
+// exact for the quadrature sum because the Gauss points move with the element.
+// The mesh is linear in the projection displacement d0 (X = X_grid + M^S d0), so
+// dJ/dd0 = (M^T)^S dJ/dX, and d0 of a body node depends on the centre through the
+// radial projection: dx_b/dc = I - (r/rho)(I - u u^T).  Topology is held fixed.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
 #include "batch.h"
 
 namespace pfq4 {
 
+namespace {
+
+__device__ __forceinline__ double node_value(int kind, long long n, int bidn, int body0, const double* nodal,
+                                             const double* bodyv) {
+  if (kind == K_BODY) return bodyv[body0 + bidn];
+  if (kind == K_INACT) return 0.0;
+  return nodal[n];
+}
+
+// Per active cell: G[a][c] = Lambda_e^T (dK_e/dx_{a,c}) psi_e for its four corners.
+__global__ void k_shape_cells(const DevVariant* var, const int* tile_var, const int2* tile_ij, const uint8_t* tag,
+                              const int* bid, const double* X, long long Vtot, const double* psi,
+                              const double* psib, const double* lam, const double* lamb, double* G) {
+  const long long t = blockIdx.x;
+  const int v = tile_var[t];
+  const DevVariant& V = var[v];
+  const int2 ij = tile_ij[t];
+  const int i = ij.x + threadIdx.x, j = ij.y + threadIdx.y;
+  if (i >= V.nx || j >= V.ny) return;
+  const long long n = V.base + (long long)j * V.P + i;
+  if (!(tag[n] & CELL_ACTIVE)) return;
+  const long long idx[4] = {n, n + 1, n + 1 + V.P, n + V.P};
+  double x[4], y[4], ps[4], lm[4];
+  for (int a = 0; a < 4; ++a) {
+    const int kind = tag[idx[a]] & KIND_MASK;
+    const int bn = bid[idx[a]];
+    x[a] = X[idx[a]];
+    y[a] = X[Vtot + idx[a]];
+    ps[a] = node_value(kind, idx[a], bn, V.body0, psi, psib);
+    lm[a] = node_value(kind, idx[a], bn, V.body0, lam, lamb);
+  }
+  const double g = 0.57735026918962576451;   // 1/sqrt(3)
+  const double xi_a[4] = {-1, 1, 1, -1}, eta_a[4] = {-1, -1, 1, 1};
+  const double gx[4] = {-g, g, g, -g}, gy[4] = {-g, -g, g, g};
+  double out[4][2] = {};
+  for (int q = 0; q < 4; ++q) {
+    double dxi[4], deta[4];
+    for (int a = 0; a < 4; ++a) {
+      dxi[a] = 0.25 * xi_a[a] * (1.0 + eta_a[a] * gy[q]);
+      deta[a] = 0.25 * eta_a[a] * (1.0 + xi_a[a] * gx[q]);
+    }
+    double j00 = 0, j01 = 0, j10 = 0, j11 = 0;
+    for (int a = 0; a < 4; ++a) {
+      j00 += dxi[a] * x[a]; j01 += dxi[a] * y[a];
+      j10 += deta[a] * x[a]; j11 += deta[a] * y[a];
+    }
+    const double det = j00 * j11 - j01 * j10;
+    const double inv = 1.0 / det;
+    double bx[4], by[4];
+    double gl[2] = {0, 0}, gp[2] = {0, 0};
+    for (int a = 0; a < 4; ++a) {
+      bx[a] = (j11 * dxi[a] - j01 * deta[a]) * inv;
+      by[a] = (-j10 * dxi[a] + j00 * deta[a]) * inv;
+      gl[0] += bx[a] * lm[a]; gl[1] += by[a] * lm[a];
+      gp[0] += bx[a] * ps[a]; gp[1] += by[a] * ps[a];
+    }
+    const double lp = gl[0] * gp[0] + gl[1] * gp[1];
+    for (int a = 0; a < 4; ++a) {
+      const double na_p = bx[a] * gp[0] + by[a] * gp[1];
+      const double na_l = bx[a] * gl[0] + by[a] * gl[1];
+      const double b2[2] = {bx[a], by[a]};
+      for (int c = 0; c < 2; ++c) out[a][c] += det * (lp * b2[c] - gl[c] * na_p - gp[c] * na_l);
+    }
+  }
+  for (int a = 0; a < 4; ++a)
+    for (int c = 0; c < 2; ++c) G[(a * 2 + c) * Vtot + n] = out[a][c];
+}
+
+// Per node: dJ/dX_n = - sum of the corner entries of its active cells, and for Dirichlet
+// nodes the data term - U (K Lambda)_n on the y component.
+__global__ void k_shape_nodes(const DevVariant* var, const int* tile_var, const int2* tile_ij, const uint8_t* tag,
+                              const int* bid, long long Vtot, const double* G, const double* K64,
+                              const double* lam, const double* lamb, double U, double* dX) {
+  const long long t = blockIdx.x;
+  const int v = tile_var[t];
+  const DevVariant& V = var[v];
+  const int2 ij = tile_ij[t];
+  const int i = ij.x + threadIdx.x, j = ij.y + threadIdx.y;
+  if (i > V.nx || j > V.ny) return;
+  const long long n = V.base + (long long)j * V.P + i;
+  double gx = 0.0, gy = 0.0;
+  // cells around the node and the node's corner number in each
+  const int ci[4] = {i, i - 1, i - 1, i};
+  const int cj[4] = {j, j, j - 1, j - 1};
+  const int corner[4] = {0, 1, 2, 3};
+  for (int k = 0; k < 4; ++k) {
+    if (ci[k] < 0 || cj[k] < 0 || ci[k] >= V.nx || cj[k] >= V.ny) continue;
+    const long long c = V.base + (long long)cj[k] * V.P + ci[k];
+    if (!(tag[c] & CELL_ACTIVE)) continue;
+    gx += G[(corner[k] * 2 + 0) * Vtot + c];
+    gy += G[(corner[k] * 2 + 1) * Vtot + c];
+  }
+  gx = -gx;
+  gy = -gy;
+  if ((tag[n] & KIND_MASK) == K_DIR && U != 0.0) {
+    // (K Lambda)_n = sum over cells of sum_{b != a} K_ab (Lambda_b - Lambda_a), Lambda_a = 0 here
+    auto lv = [&](long long m) -> double {
+      const int kind = tag[m] & KIND_MASK;
+      return node_value(kind, m, bid[m], V.body0, lam, lamb);
+    };
+    auto kc = [&](int m, long long c, bool gen) -> double { return gen ? K64[m * Vtot + c] : V.kr64[m]; };
+    double kl = 0.0;
+    const long long P = V.P;
+    // cell (i, j), corner 0: K01 E, K02 NE, K03 N
+    if (i < V.nx && j < V.ny && (tag[n] & CELL_ACTIVE)) {
+      const bool gen = tag[n] & CELL_GENERAL;
+      kl += kc(0, n, gen) * lv(n + 1) + kc(1, n, gen) * lv(n + 1 + P) + kc(2, n, gen) * lv(n + P);
+    }
+    // cell (i-1, j), corner 1: K01 W, K12 N, K13 NW
+    if (i > 0 && j < V.ny && (tag[n - 1] & CELL_ACTIVE)) {
+      const long long c = n - 1;
+      const bool gen = tag[c] & CELL_GENERAL;
+      kl += kc(0, c, gen) * lv(n - 1) + kc(3, c, gen) * lv(n + P) + kc(4, c, gen) * lv(n - 1 + P);
+    }
+    // cell (i-1, j-1), corner 2: K02 SW, K12 S, K23 W
+    if (i > 0 && j > 0 && (tag[n - P - 1] & CELL_ACTIVE)) {
+      const long long c = n - P - 1;
+      const bool gen = tag[c] & CELL_GENERAL;
+      kl += kc(1, c, gen) * lv(n - P - 1) + kc(3, c, gen) * lv(n - P) + kc(5, c, gen) * lv(n - 1);
+    }
+    // cell (i, j-1), corner 3: K03 S, K13 SE, K23 E
+    if (j > 0 && i < V.nx && (tag[n - P] & CELL_ACTIVE)) {
+      const long long c = n - P;
+      const bool gen = tag[c] & CELL_GENERAL;
+      kl += kc(2, c, gen) * lv(n - P) + kc(4, c, gen) * lv(n - P + 1) + kc(5, c, gen) * lv(n + 1);
+    }
+    gy -= U * kl;
+  }
+  dX[n] = gx;
+  dX[Vtot + n] = gy;
+}
+
+// One transposed Jacobi sweep: out_m = [m fixed] in_m + sum over updated neighbours n of in_n / 4.
+__global__ void k_jacobi_T(const DevVariant* var, const int* tile_var, const int2* tile_ij, const uint8_t* tag,
+                           const int* bid, long long Vtot, const double* in, double* out) {
+  const long long t = blockIdx.x;
+  const int v = tile_var[t];
+  const DevVariant& V = var[v];
+  const int2 ij = tile_ij[t];
+  const int i = ij.x + threadIdx.x, j = ij.y + threadIdx.y;
+  if (i > V.nx || j > V.ny) return;
+  const long long n = V.base + (long long)j * V.P + i;
+  auto updated = [&](long long m) -> bool { return bid[m] < 0 && !(tag[m] & RING); };
+  double ox = 0.0, oy = 0.0;
+  if (!updated(n)) {
+    ox = in[n];
+    oy = in[Vtot + n];
+  }
+  const int ni[4] = {i - 1, i + 1, i, i};
+  const int nj[4] = {j, j, j - 1, j + 1};
+  for (int k = 0; k < 4; ++k) {
+    if (ni[k] < 0 || nj[k] < 0 || ni[k] > V.nx || nj[k] > V.ny) continue;
+    const long long m = V.base + (long long)nj[k] * V.P + ni[k];
+    if (updated(m)) {
+      ox += 0.25 * in[m];
+      oy += 0.25 * in[Vtot + m];
+    }
+  }
+  out[n] = ox;
+  out[Vtot + n] = oy;
+}
+
+// dJ/dc_k = sum over the body's nodes of Jp^T (dJ/dd0)_n, Jp = I - (r/rho)(I - u u^T) at
+// the node's background-grid position.  One CTA per global body, fixed-order sum.
+__global__ void k_centre_grad(const DevVariant* var, const int* body_var, const pf_body* bodies, const int* body_ptr,
+                              const long long* body_nodes, long long Vtot, const double* gd, double* out) {
+  __shared__ double scratch[NT / 32 + 1];
+  const int gb = blockIdx.x;
+  const DevVariant& V = var[body_var[gb]];
+  const pf_body Bd = bodies[gb];
+  double sx = 0.0, sy = 0.0;
+  for (int e = body_ptr[gb] + linear_tid(); e < body_ptr[gb + 1]; e += NT) {
+    const long long n = body_nodes[e];
+    const long long rem = n - V.base;
+    const int i = (int)(rem % V.P), j = (int)(rem / V.P);
+    const double xg = V.x0 + (double)i * V.hx, yg = V.y0 + (double)j * V.hy;
+    const double ex = xg - Bd.cx, ey = yg - Bd.cy;
+    const double rho = sqrt(ex * ex + ey * ey);
+    const double ux = ex / rho, uy = ey / rho, s = Bd.r / rho;
+    const double j00 = 1.0 - s * (1.0 - ux * ux), j01 = s * ux * uy, j11 = 1.0 - s * (1.0 - uy * uy);
+    const double gx = gd[n], gy = gd[Vtot + n];
+    sx += j00 * gx + j01 * gy;
+    sy += j01 * gx + j11 * gy;
+  }
+  sx = block_sum(sx, scratch);
+  sy = block_sum(sy, scratch);
+  if (linear_tid() == 0) {
+    out[2 * gb] = sx;
+    out[2 * gb + 1] = sy;
+  }
+}
+
+__global__ void k_export_grad(const DevVariant* var, const long long* lbase, long long Vtot, const double* dX,
+                              double* out) {
+  const int v = blockIdx.y;
+  const DevVariant& V = var[v];
+  const long long N = (long long)(V.nx + 1) * (V.ny + 1);
+  for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < N; m += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(m % (V.nx + 1)), j = (int)(m / (V.nx + 1));
+    const long long n = V.base + (long long)j * V.P + i;
+    out[2 * (lbase[v] + m)] = dX[n];
+    out[2 * (lbase[v] + m) + 1] = dX[Vtot + n];
+  }
+}
+
+}  // namespace
+
 pf_status shape_gradient(Batch& b, int obj, int lo, int hi, double U, double tol, double* dev_dJdX, double* dJdc,
                          double* J) {
-  (void)b; (void)obj; (void)lo; (void)hi; (void)U; (void)tol; (void)dev_dJdX; (void)dJdc; (void)J;
-  throw Error{PF_EINVAL, "pf_grad: not available in this build"};
+  if (!b.solved) throw Error{PF_EINVAL, "pf_grad needs a solve on this handle first"};
+  if (U != b.lastU) throw Error{PF_EINVAL, "pf_grad must use the U of the last solve"};
+  if (!(tol > 0)) throw Error{PF_EINVAL, "invalid tol"};
+  cudaStream_t s = b.stream;
+  const long long Vt = b.Vtot;
+  const int B = std::max(1, b.B);
+  // objective values and adjoint right-hand sides (host)
+  std::vector<double> C;
+  body_values(b, C);
+  std::vector<double> Jv(b.nv), w(b.nv), dy(b.nv), rhs(B, 0.0);
+  for (int v = 0; v < b.nv; ++v) {
+    const int g0 = b.hv[v].body0;
+    const double q = C[g0 + hi] - C[g0 + lo];
+    dy[v] = b.bodies[g0 + hi].cy - b.bodies[g0 + lo].cy;
+    if (obj == PF_OBJ_COPFI) {
+      if (U == 0.0 || dy[v] == 0.0) throw Error{PF_EINVAL, "CoPFI needs U != 0 and distinct body heights"};
+      Jv[v] = q / (U * dy[v]);
+      w[v] = 1.0 / (U * dy[v]);
+    } else {
+      Jv[v] = q;
+      w[v] = 1.0;
+    }
+    rhs[g0 + hi] += w[v];
+    rhs[g0 + lo] -= w[v];
+  }
+  if (!b.psi_save) {
+    b.psi_save = (double*)dev_alloc(b, Vt * sizeof(double));
+    b.sol_save = (double*)dev_alloc(b, B * sizeof(double));
+    b.d_rhsb = (double*)dev_alloc(b, B * sizeof(double));
+    b.gradX = (double*)dev_alloc(b, 2 * Vt * sizeof(double));
+    b.gradT = (double*)dev_alloc(b, 2 * Vt * sizeof(double));
+    b.cellG = (double*)dev_alloc(b, 8 * Vt * sizeof(double));
+  }
+  PF_CUDA(cudaMemcpyAsync(b.psi_save, b.x64, Vt * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  PF_CUDA(cudaMemcpyAsync(b.sol_save, b.sol64, B * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  PF_CUDA(cudaMemcpyAsync(b.d_rhsb, rhs.data(), B * sizeof(double), cudaMemcpyHostToDevice, s));
+  // adjoint solve: same operator (self-adjoint), no Dirichlet data, body-row right-hand side
+  pf_solve_opts o{};
+  o.tol = tol;
+  o.k_max = 100000000;
+  o.precision = PF_MIXED;
+  o.inner_tol = 1e-4;
+  b.rhs_active = true;
+  pf_status st = PF_OK;
+  try {
+    st = solve_core(b, 0.0, o, nullptr, nullptr, nullptr, false);
+  } catch (...) {
+    b.rhs_active = false;
+    throw;
+  }
+  b.rhs_active = false;
+  // element shape derivatives and node gradient
+  const dim3 blk(TX, TY);
+  PF_CUDA(cudaMemsetAsync(b.cellG, 0, 8 * Vt * sizeof(double), s));
+  k_shape_cells<<<(unsigned)b.T, blk, 0, s>>>(b.d_var, b.tile_var, b.tile_ij, b.tag, b.bid, b.X, Vt, b.psi_save,
+                                              b.sol_save, b.x64, b.sol64, b.cellG);
+  PF_CUDA(cudaMemsetAsync(b.gradX, 0, 2 * Vt * sizeof(double), s));
+  k_shape_nodes<<<(unsigned)b.T, blk, 0, s>>>(b.d_var, b.tile_var, b.tile_ij, b.tag, b.bid, Vt, b.cellG, b.K64,
+                                              b.x64, b.sol64, U, b.gradX);
+  PF_CUDA(cudaGetLastError());
+  if (dev_dJdX) {
+    k_export_grad<<<dim3(256, b.nv), 256, 0, s>>>(b.d_var, lbase_cached(b), Vt, b.gradX, dev_dJdX);
+    PF_CUDA(cudaGetLastError());
+  }
+  if (dJdc) {
+    double* a = b.gradX;
+    double* c = b.gradT;
+    PF_CUDA(cudaMemsetAsync(c, 0, 2 * Vt * sizeof(double), s));
+    for (int k = 0; k < b.sweeps; ++k) {
+      k_jacobi_T<<<(unsigned)b.T, blk, 0, s>>>(b.d_var, b.tile_var, b.tile_ij, b.tag, b.bid, Vt, a, c);
+      std::swap(a, c);
+    }
+    PF_CUDA(cudaGetLastError());
+    double* out = b.cellG;   // reuse as a [B][2] result buffer
+    if (b.B > 0) {
+      k_centre_grad<<<b.B, blk, 0, s>>>(b.d_var, b.d_body_var, b.d_bodies, b.body_ptr, b.body_nodes, Vt, a, out);
+      PF_CUDA(cudaGetLastError());
+      PF_CUDA(cudaMemcpyAsync(dJdc, out, 2 * b.B * sizeof(double), cudaMemcpyDeviceToHost, s));
+    }
+    PF_CUDA(cudaStreamSynchronize(s));
+    if (obj == PF_OBJ_COPFI) {
+      for (int v = 0; v < b.nv; ++v) {
+        const int g0 = b.hv[v].body0;
+        dJdc[2 * (g0 + hi) + 1] += -Jv[v] / dy[v];
+        dJdc[2 * (g0 + lo) + 1] += Jv[v] / dy[v];
+      }
+    }
+  }
+  // restore the forward solution
+  PF_CUDA(cudaMemcpyAsync(b.x64, b.psi_save, Vt * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  PF_CUDA(cudaMemcpyAsync(b.sol64, b.sol_save, B * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  PF_CUDA(cudaStreamSynchronize(s));
+  b.lastU = U;
+  b.launches += 2 + (dev_dJdX ? 1 : 0) + (dJdc ? b.sweeps + 1 : 0);
+  if (J)
+    for (int v = 0; v < b.nv; ++v) J[v] = Jv[v];
+  return st;
 }
 
 }  // namespace pfq4

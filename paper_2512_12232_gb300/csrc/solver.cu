@@ -62,6 +62,7 @@ struct ResidArgs {
   double* sol;              // [B] body solution values
   T* sb;                    // [4][B] CG body values
   double* sbr;              // [B] true residual body rows
+  const double* rhsb;       // [B] extra right-hand side on the body rows (adjoint), or NULL
   int B;
   int mixed;
   int* n_done;
@@ -515,7 +516,7 @@ __device__ void finalize_resid(const ResidArgs<T>& a, int v, double* scratch, do
   reduce_partials(a.sc, v, 1, d, scratch);
   for (int k = 0; k < V.nb; ++k) {
     const double s = body_gather<double>(a.m, V.body0 + k, a.w64, scratch);
-    if (linear_tid() == 0) sh_rb[k] = -s;
+    if (linear_tid() == 0) sh_rb[k] = (a.rhsb ? a.rhsb[V.body0 + k] : 0.0) - s;
   }
   __syncthreads();
   if (linear_tid() == 0) {
@@ -996,7 +997,7 @@ static std::vector<long long> logical_bases(const Batch& b) {
   return lb;
 }
 
-static long long* lbase_cached(Batch& b) {
+long long* lbase_cached(Batch& b) {
   if (!b.d_lbase) {
     const std::vector<long long> h = logical_bases(b);
     b.d_lbase = (long long*)dev_alloc(b, h.size() * sizeof(long long));
@@ -1070,6 +1071,7 @@ static void fill_resid_args(Batch& b, ResidArgs<T>& a, State4<T>* const st[2], T
   a.sol = b.sol64;
   a.sb = sb;
   a.sbr = b.sbr64;
+  a.rhsb = b.rhs_active ? b.d_rhsb : nullptr;
   a.B = std::max(1, b.B);
   a.mixed = mixed;
   a.n_done = b.n_done;
@@ -1142,6 +1144,14 @@ static cudaGraphExec_t get_graph(Batch& b, int precision, int chunk) {
 
 pf_status psi_solve(Batch& b, double U, const pf_solve_opts& o, double* dev_psi, double* body_psi,
                     pf_solve_info* info) {
+  b.rhs_active = false;
+  return solve_core(b, U, o, dev_psi, body_psi, info, true);
+}
+
+// The solve proper.  With b.rhs_active the body rows carry the extra right-hand side
+// b.d_rhsb (used by the adjoint); record_bnorm stores ||b||^2 at U = 1 for later warm starts.
+pf_status solve_core(Batch& b, double U, const pf_solve_opts& o, double* dev_psi, double* body_psi,
+                     pf_solve_info* info, bool record_bnorm) {
   if (!b.valid) throw Error{PF_EMESH_INVALID, "mesh has det J <= 0 at a Gauss point; solve refused"};
   if (o.precision != PF_FP64 && o.precision != PF_MIXED) throw Error{PF_EINVAL, "invalid precision"};
   if (!(o.tol > 0) || o.k_max < 1 || !std::isfinite(U)) throw Error{PF_EINVAL, "invalid tol, k_max or U"};
@@ -1166,8 +1176,7 @@ pf_status psi_solve(Batch& b, double U, const pf_solve_opts& o, double* dev_psi,
     memset(&S, 0, sizeof(S));
     S.phase = PH_RESID;
     S.status = PF_OK;
-    S.bnorm2 = (b.bnorm2_unit[v] >= 0.0) ? b.bnorm2_unit[v] * U * U : -1.0;
-    if (warm && S.bnorm2 < 0) S.bnorm2 = -1.0;
+    S.bnorm2 = (record_bnorm && b.bnorm2_unit[v] >= 0.0) ? b.bnorm2_unit[v] * U * U : -1.0;
   }
   PF_CUDA(cudaMemcpyAsync(b.state, st.data(), b.nv * sizeof(VarState), cudaMemcpyHostToDevice, s));
   PF_CUDA(cudaMemsetAsync(b.n_done, 0, 2 * sizeof(int), s));
@@ -1231,7 +1240,7 @@ pf_status psi_solve(Batch& b, double U, const pf_solve_opts& o, double* dev_psi,
     const pf_mesh_stats& M = b.hv[v].stats;
     if (S.phase != PH_DONE && ret == PF_OK) ret = PF_ENOT_CONVERGED;
     if (S.status != PF_OK && ret == PF_OK) ret = S.status;
-    if (b.bnorm2_unit[v] < 0 && S.bnorm2 >= 0 && U != 0) b.bnorm2_unit[v] = S.bnorm2 / (U * U);
+    if (record_bnorm && b.bnorm2_unit[v] < 0 && S.bnorm2 >= 0 && U != 0 && !warm) b.bnorm2_unit[v] = S.bnorm2 / (U * U);
     const double per_node_free = prec == PF_MIXED ? 32.0 : 64.0;
     const double per_body = prec == PF_MIXED ? 20.0 : 36.0;
     const double per_gen = prec == PF_MIXED ? 24.0 : 48.0;
