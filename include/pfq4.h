@@ -187,6 +187,17 @@ pf_status pf_apply_noalloc(const pf_batch* b, int precision, const double* dev_p
 pf_status pf_psi_solve(pf_batch* b, double U, const pf_solve_opts* opts, double* dev_psi,
                        double* body_psi, pf_solve_info* info, void* stream);
 
+/* The same solve through the Schur complement of the body unknowns (algebraically equal
+   to the multi-point-constraint system of section "Matrix-Free Conjugate Gradient with
+   Multiple Constraint Enforcement"): per variant, N_b + 1 solves with the body values held
+   as data (psi_0 with the Dirichlet data, phi_k with C_k = 1) run as one internal batch;
+   the body rows of K phi_k form the N_b x N_b FP64 Schur matrix, S C = -(body rows of
+   K psi_0) is solved by Cholesky, and psi = psi_0 + sum_k C_k phi_k.  A warm-started MPC
+   solve then reports the true residual (and iterates only if tol is not yet met).
+   Arguments and outputs as pf_psi_solve; info[v].iters includes the sub-solves. */
+pf_status pf_psi_solve_schur(pf_batch* b, double U, const pf_solve_opts* opts, double* dev_psi,
+                             double* body_psi, pf_solve_info* info, void* stream);
+
 /* Device-event timing of the last pf_psi_solve on this handle. */
 pf_status pf_last_timing(const pf_batch* b, pf_timing* out);
 

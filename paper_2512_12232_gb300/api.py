@@ -197,7 +197,9 @@ def apply(mesh: Mesh, p: torch.Tensor, precision=PF_FP64):
 
 
 def psi_solve(mesh: Mesh, U=1.0, tol=1e-8, precision=PF_MIXED, k_max=10_000_000, inner_tol=1e-4,
-              chunk=0, warm_start=False, want_psi=True, raise_on_failure=True) -> SolveResult:
+              chunk=0, warm_start=False, want_psi=True, raise_on_failure=True, method="mpc") -> SolveResult:
+    """Solve for psi.  method="mpc": CG on the multi-point-constraint system;
+    method="schur": body values through the Schur complement (N_b + 1 fixed-body solves)."""
     opts = L.pf_solve_opts(float(tol), int(k_max), int(precision), float(inner_tol), int(chunk),
                            int(bool(warm_start)))
     total = int(mesh.node_offsets[-1])
@@ -205,7 +207,8 @@ def psi_solve(mesh: Mesh, U=1.0, tol=1e-8, precision=PF_MIXED, k_max=10_000_000,
     nb = mesh.body_offsets[-1]
     bpsi = (C.c_double * max(1, nb))()
     info = (L.pf_solve_info * mesh.n_variants)()
-    code = L.load().pf_psi_solve(mesh.handle, float(U), C.byref(opts), _ptr(psi), bpsi, info, _stream())
+    fn = L.load().pf_psi_solve_schur if method == "schur" else L.load().pf_psi_solve
+    code = fn(mesh.handle, float(U), C.byref(opts), _ptr(psi), bpsi, info, _stream())
     if raise_on_failure:
         check(code)
     infos = [{k: getattr(i, k) for k, _ in L.pf_solve_info._fields_} for i in info]

@@ -111,6 +111,9 @@ struct Batch {
   double* sbr64 = nullptr;           // [B] FP64 true-residual body rows
   double* d_rhsb = nullptr;          // [B] body-row right-hand side of the adjoint solve
   bool rhs_active = false;
+  bool fixed_bodies = false;         // Schur sub-solves: body values are data (sol64 preset)
+  double* d_Uv = nullptr;            // [nv] per-variant U of the Dirichlet data
+  bool Uv_active = false;
   double* psi_save = nullptr;        // [Vtot] forward solution kept during the adjoint solve
   double* sol_save = nullptr;        // [B]
   double* gradX = nullptr;           // [2][Vtot] dJ/dX (padded), then the transposed sweeps
@@ -162,6 +165,10 @@ pf_status solve_core(Batch& b, double U, const pf_solve_opts& o, double* dev_psi
 long long* lbase_cached(Batch& b);
 void export_psi(Batch& b, double* dev_psi);
 void body_values(Batch& b, std::vector<double>& C);
+
+// schur.cu
+pf_status schur_solve(Batch& b, double U, const pf_solve_opts& o, double* dev_psi, double* body_psi,
+                      pf_solve_info* info);
 
 // post.cu
 int surface_velocity(Batch& b, int v, int body, double* theta, double* ut, int cap);

@@ -239,6 +239,21 @@ pf_status pf_psi_solve(pf_batch* h, double U, const pf_solve_opts* opts, double*
   });
 }
 
+pf_status pf_psi_solve_schur(pf_batch* h, double U, const pf_solve_opts* opts, double* dev_psi, double* body_psi,
+                             pf_solve_info* info, void* stream) {
+  return guarded([&]() -> pf_status {
+    Batch* b = (Batch*)h;
+    bind(b, stream);
+    pf_solve_opts o{};
+    o.tol = 1e-8;
+    o.k_max = 10000000;
+    o.precision = PF_MIXED;
+    o.inner_tol = 1e-4;
+    if (opts) o = *opts;
+    return schur_solve(*b, U, o, dev_psi, body_psi, info);
+  });
+}
+
 pf_status pf_last_timing(const pf_batch* h, pf_timing* out) {
   return guarded([&]() -> pf_status {
     const Batch* b = (const Batch*)h;

@@ -79,7 +79,7 @@ struct SolveParams {
   double inner_rel2;           // inner_tol^2 (mixed) or 0
   long long k_max;
   int mixed;
-  int pad_;
+  int fixed_bodies;            // body values are given data (Schur sub-solves), not unknowns
 };
 
 struct Sched {                 // persistent tile schedule

@@ -149,7 +149,7 @@ __device__ void finalize_cg(const CGArgs<T>& a, int v, double* scratch, double* 
     const T alpha = (T)S->alpha, beta = (T)S->beta;
     double dd[4] = {d[0], d[1], d[2], d[3]};
     const int B = a.B;
-    for (int k = 0; k < V.nb; ++k) {
+    for (int k = 0; k < (a.prm->fixed_bodies ? 0 : V.nb); ++k) {
       const int gb = V.body0 + k;
       const T xb = a.sb[gb], rb = a.sb[B + gb], pb = a.sb[2 * B + gb], qb = a.sb[3 * B + gb];
       const T rn = next_r(rb, qb, alpha);
@@ -344,7 +344,7 @@ __global__ void __launch_bounds__(NT, 2) k_cg(CGArgs<T> a, const __grid_constant
     if (tid < nb) {
       const int gb = body0 + tid;
       const T rn = next_r(a.sb[B + gb], a.sb[3 * B + gb], alpha);
-      s_pb[tid] = next_p(rn, a.sb[2 * B + gb], beta);
+      s_pb[tid] = a.prm->fixed_bodies ? T(0) : next_p(rn, a.sb[2 * B + gb], beta);
     }
     if (tid == 0) {
       for (int k = 0; k < NS && t0 + k < t1; ++k) {
@@ -522,11 +522,16 @@ __device__ void finalize_resid(const ResidArgs<T>& a, int v, double* scratch, do
   if (linear_tid() == 0) {
     const int B = a.B;
     double g = d[0];
+    const bool fixed = a.prm->fixed_bodies != 0;
     for (int k = 0; k < V.nb; ++k) {
       const int gb = V.body0 + k;
       const double rb = sh_rb[k];
-      g += rb * rb;
       a.sbr[gb] = rb;
+      if (fixed) {                 // given body value: its row is an output, not an equation
+        a.sb[B + gb] = T(0);
+        continue;
+      }
+      g += rb * rb;
       a.sol[gb] = a.sol[gb] + (double)a.sb[gb];   // fold the body correction
       a.sb[gb] = T(0);
       a.sb[B + gb] = (T)rb;
@@ -671,9 +676,11 @@ __global__ void k_fold(const DevVariant* var, const int* tile_var, const int2* t
 
 // ---------------------------------------------------------------- init / export
 __global__ void k_init(const DevVariant* var, const int* tile_var, const int2* tile_ij, const uint8_t* tag,
-                       const double* X, long long Vtot, double U, int warm, double* x64, double* w64) {
+                       const double* X, long long Vtot, double U0, const double* Uv, int warm, double* x64,
+                       double* w64) {
   const long long t = blockIdx.x;
   const int v = tile_var[t];
+  const double U = Uv ? Uv[v] : U0;
   const DevVariant& V = var[v];
   const int2 ij = tile_ij[t];
   const int i = ij.x + threadIdx.x, j = ij.y + threadIdx.y;
@@ -1144,7 +1151,10 @@ static cudaGraphExec_t get_graph(Batch& b, int precision, int chunk) {
 
 pf_status psi_solve(Batch& b, double U, const pf_solve_opts& o, double* dev_psi, double* body_psi,
                     pf_solve_info* info) {
+  if (o.k_max < 1) throw Error{PF_EINVAL, "k_max must be >= 1"};
   b.rhs_active = false;
+  b.fixed_bodies = false;
+  b.Uv_active = false;
   return solve_core(b, U, o, dev_psi, body_psi, info, true);
 }
 
@@ -1154,7 +1164,7 @@ pf_status solve_core(Batch& b, double U, const pf_solve_opts& o, double* dev_psi
                      pf_solve_info* info, bool record_bnorm) {
   if (!b.valid) throw Error{PF_EMESH_INVALID, "mesh has det J <= 0 at a Gauss point; solve refused"};
   if (o.precision != PF_FP64 && o.precision != PF_MIXED) throw Error{PF_EINVAL, "invalid precision"};
-  if (!(o.tol > 0) || o.k_max < 1 || !std::isfinite(U)) throw Error{PF_EINVAL, "invalid tol, k_max or U"};
+  if (!(o.tol > 0) || o.k_max < 0 || !std::isfinite(U)) throw Error{PF_EINVAL, "invalid tol, k_max or U"};
   const int prec = o.precision;
   ensure_solver_memory(b, prec);
   {
@@ -1168,6 +1178,7 @@ pf_status solve_core(Batch& b, double U, const pf_solve_opts& o, double* dev_psi
   sp.inner_rel2 = itol * itol;
   sp.k_max = o.k_max;
   sp.mixed = prec == PF_MIXED;
+  sp.fixed_bodies = b.fixed_bodies ? 1 : 0;
   PF_CUDA(cudaMemcpyAsync(b.params, &sp, sizeof(sp), cudaMemcpyHostToDevice, s));
   const bool warm = o.warm_start && b.solved;
   std::vector<VarState> st(b.nv);
@@ -1181,15 +1192,15 @@ pf_status solve_core(Batch& b, double U, const pf_solve_opts& o, double* dev_psi
   PF_CUDA(cudaMemcpyAsync(b.state, st.data(), b.nv * sizeof(VarState), cudaMemcpyHostToDevice, s));
   PF_CUDA(cudaMemsetAsync(b.n_done, 0, 2 * sizeof(int), s));
   const int B = std::max(1, b.B);
-  if (!warm) PF_CUDA(cudaMemsetAsync(b.sol64, 0, B * sizeof(double), s));
+  if (!warm && !b.fixed_bodies) PF_CUDA(cudaMemsetAsync(b.sol64, 0, B * sizeof(double), s));
   PF_CUDA(cudaMemsetAsync(b.sb64, 0, 4 * B * sizeof(double), s));
   PF_CUDA(cudaMemsetAsync(b.sb32, 0, 4 * B * sizeof(float), s));
   for (int k = 0; k < 2; ++k) {
     if (prec == PF_FP64) PF_CUDA(cudaMemsetAsync(b.st64[k], 0, b.Vtot * sizeof(State4<double>), s));
     else PF_CUDA(cudaMemsetAsync(b.st32[k], 0, b.Vtot * sizeof(State4<float>), s));
   }
-  k_init<<<(unsigned)b.T, dim3(TX, TY), 0, s>>>(b.d_var, b.tile_var, b.tile_ij, b.tag, b.X, b.Vtot, U, warm, b.x64,
-                                                b.w64);
+  k_init<<<(unsigned)b.T, dim3(TX, TY), 0, s>>>(b.d_var, b.tile_var, b.tile_ij, b.tag, b.X, b.Vtot, U,
+                                                b.Uv_active ? b.d_Uv : nullptr, warm, b.x64, b.w64);
   PF_CUDA(cudaGetLastError());
   PF_CUDA(cudaEventRecord(b.ev[3], s));
   launch_resid_only(b, prec, s);
@@ -1204,7 +1215,8 @@ pf_status solve_core(Batch& b, double U, const pf_solve_opts& o, double* dev_psi
   int* hdone = b.h_poll;
   double cg_ms = 0, res_ms = 0;
   long long launches = 0, rlaunches = 1;
-  const long long max_chunks = o.k_max / chunk + 1000;
+  // k_max == 0 (internal use): only the initial residual, which measures ||b||
+  const long long max_chunks = o.k_max == 0 ? 0 : o.k_max / chunk + 1000;
   for (long long c = 0; c < max_chunks; ++c) {
     PF_CUDA(cudaEventRecord(b.ev[0], s));
     PF_CUDA(cudaGraphLaunch(ex, s));

@@ -116,3 +116,27 @@ def test_linearity_in_U(api):
         a = api.psi_solve(g, U=1.0, tol=1e-13, precision=api.PF_FP64).psi.cpu().numpy()
         b = api.psi_solve(g, U=-2.5, tol=1e-13, precision=api.PF_FP64).psi.cpu().numpy()
     assert rel_l2(b, -2.5 * a) <= 1e-11
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_schur_form_matches_oracle_and_mpc(api, prec):
+    c = W.five_cylinder_case(0.25, 256, 128, 40)
+    m, s, u, psi_ref = oracle_solution(c, 1.0)
+    p = api.PF_FP64 if prec == "fp64" else api.PF_MIXED
+    with api.mesh_build(c.grid, c.bodies, c.sweeps, c.bc) as g:
+        rs = api.psi_solve(g, U=1.0, tol=1e-12, precision=p, method="schur")
+        rm = api.psi_solve(g, U=1.0, tol=1e-12, precision=p)
+    assert rs.info[0]["status"] == 0 and rs.info[0]["rel_true_residual"] <= 1e-12
+    np.testing.assert_allclose(rs.body_psi, u[s.n_free:], rtol=0, atol=BODY_TOL)
+    assert rel_l2(rs.psi.cpu().numpy(), psi_ref) <= (FP64_TOL if prec == "fp64" else MIXED_TOL)
+    np.testing.assert_allclose(rs.body_psi, rm.body_psi, rtol=0, atol=1e-9)
+
+
+def test_schur_form_on_a_batch(api):
+    cases = W.parametric_sweep(3, seed=6, nx_choices=(256, 320))
+    with api.batch_build(cases) as g:
+        r = api.psi_solve(g, U=1.0, tol=1e-10, precision=api.PF_MIXED, method="schur")
+    for v, c in enumerate(cases):
+        m, s, u, psi_ref = oracle_solution(c, 1.0)
+        np.testing.assert_allclose(r.body_psi[5 * v:5 * v + 5], u[s.n_free:], rtol=0, atol=1e-7)
+        assert r.info[v]["status"] == 0
