@@ -60,6 +60,7 @@ struct Batch {
   double* X = nullptr;               // [2][Vtot] final coordinates
   double* K64 = nullptr;             // [6][Vtot]
   float* K32 = nullptr;              // [6][Vtot]
+  float* K32i = nullptr;             // [Vtot][6] the same coefficients interleaved per cell (TMA-friendly)
   int* body_ptr = nullptr;           // [B+1]
   long long* body_nodes = nullptr;
   int* edge_ptr = nullptr;           // [B+1]

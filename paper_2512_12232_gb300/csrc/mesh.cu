@@ -153,7 +153,7 @@ __device__ void atomic_min_double(double* addr, double val) {
 // 5. Q4 element matrices of the active cells (2x2 Gauss), FP64 and FP32 copies,
 //    CELL_GENERAL flag, per-variant counts and min det J.
 __global__ void k_stiffness(const DevVariant* var, const int* tile_var, const int2* tile_ij,
-                            uint8_t* tag, const double* X, long long Vtot, double* K64, float* K32,
+                            uint8_t* tag, const double* X, long long Vtot, double* K64, float* K32, float* K32i,
                             long long* stats_i, double* detmin) {
   TileCtx c = tile_ctx(var, tile_var, tile_ij);
   const DevVariant& V = var[c.v];
@@ -211,6 +211,7 @@ __global__ void k_stiffness(const DevVariant* var, const int* tile_var, const in
       for (int m = 0; m < 6; ++m) {
         K64[m * Vtot + n] = k6[m];
         K32[m * Vtot + n] = (float)k6[m];
+        K32i[6 * n + m] = (float)k6[m];
       }
       if (disp) {
         tag[n] = t | CELL_GENERAL;
@@ -504,6 +505,7 @@ void build_batch(Batch& b, const pf_grid* grids, const int* body_offsets, const 
   b.X = (double*)dev_alloc(b, 2 * Vt * sizeof(double));
   b.K64 = (double*)dev_alloc(b, 6 * Vt * sizeof(double));
   b.K32 = (float*)dev_alloc(b, 6 * Vt * sizeof(float));
+  b.K32i = (float*)dev_alloc(b, 6 * Vt * sizeof(float));
   double2* dA = (double2*)dev_alloc(b, Vt * sizeof(double2));
   double2* dB = (double2*)dev_alloc(b, Vt * sizeof(double2));
   int* err = (int*)dev_alloc(b, sizeof(int));
@@ -515,6 +517,7 @@ void build_batch(Batch& b, const pf_grid* grids, const int* body_offsets, const 
   PF_CUDA(cudaMemsetAsync(b.X, 0, 2 * Vt * sizeof(double), s));
   PF_CUDA(cudaMemsetAsync(b.K64, 0, 6 * Vt * sizeof(double), s));
   PF_CUDA(cudaMemsetAsync(b.K32, 0, 6 * Vt * sizeof(float), s));
+  PF_CUDA(cudaMemsetAsync(b.K32i, 0, 6 * Vt * sizeof(float), s));
   PF_CUDA(cudaMemsetAsync(dA, 0, Vt * sizeof(double2), s));
   PF_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
   PF_CUDA(cudaMemsetAsync(b.d_stats_i, 0, nv * 6 * sizeof(long long), s));
@@ -535,7 +538,7 @@ void build_batch(Batch& b, const pf_grid* grids, const int* body_offsets, const 
     std::swap(dA, dB);
   }
   k_finalize<<<grid, blk, 0, s>>>(b.d_var, b.tile_var, b.tile_ij, dA, b.tag, b.X, Vt);
-  k_stiffness<<<grid, blk, 0, s>>>(b.d_var, b.tile_var, b.tile_ij, b.tag, b.X, Vt, b.K64, b.K32, b.d_stats_i,
+  k_stiffness<<<grid, blk, 0, s>>>(b.d_var, b.tile_var, b.tile_ij, b.tag, b.X, Vt, b.K64, b.K32, b.K32i, b.d_stats_i,
                                    b.d_detmin);
   k_tile_general<<<(unsigned)b.Tcg, blk, 0, s>>>(b.d_var, b.tile_cg_var, b.tile_cg_ij, b.tag, b.tile_cg_gen);
   PF_CUDA(cudaGetLastError());

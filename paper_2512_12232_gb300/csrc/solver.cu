@@ -135,7 +135,7 @@ __device__ void finalize_cg(const CGArgs<T>& a, int v, double* scratch, double* 
   }
   // warps 4-7: collapsed body rows of q (the new parity), one warp per body
   const State4<T>* snew = a.s[S->buf ^ 1];
-  for (int k = warp - 4; k < V.nb; k += NT / 32 - 4) {
+  for (int k = warp - 4; k < V.nb && warp < NT / 32; k += NT / 32 - 4) {
     if (k < 0) continue;
     const int gb = V.body0 + k;
     double s = 0.0;
@@ -202,6 +202,7 @@ template <typename T, int NS = 2>
 struct CgSmem {
   static constexpr int SBW = CTX + 2;            // state box width (nodes)
   static constexpr int KBW = CTX + 4;            // coefficient box width (cells i0-4 .. i0+CTX-1)
+  static constexpr int KHALF = KBW / 2;          // cells per coefficient box (two boxes of 6*KHALF floats)
   static constexpr int TBW = CTX + 32;           // tag box width
   static constexpr int SB = 4 * SBW * (CTY + 2); // elements of the state box
   static constexpr int KB = KBW * (CTY + 1);     // elements of one coefficient plane box
@@ -210,15 +211,22 @@ struct CgSmem {
   static constexpr int off_s = 0;
   static constexpr int off_t = off_s + align(SB * (int)sizeof(T));
   static constexpr int off_k = off_t + align(TBW * (CTY + 2));
-  static constexpr int stage_bytes = off_k + (kTmaK ? 6 * align(KB * (int)sizeof(T)) : 0);
+  // two coefficient boxes, each starting on a 128-byte boundary (TMA destination alignment)
+  static constexpr int kbox_bytes = align((CTY + 1) * 6 * KHALF * (int)sizeof(T));
+  static constexpr int stage_bytes = off_k + (kTmaK ? 2 * kbox_bytes : 0);
   static constexpr int kplane_bytes = align(KB * (int)sizeof(T));
   static constexpr int tx_base = SB * (int)sizeof(T) + TBW * (CTY + 2);
   static constexpr int tx_k = kTmaK ? 6 * KB * (int)sizeof(T) : 0;
-  // after the NS stages: p tile with halo, effective tags, barriers
+  // after the NS stages: two p tiles with halo, two effective-tag tiles, barriers
+  static constexpr int ptile_bytes = align((CTX + 2) * (CTY + 2) * (int)sizeof(T));
+  static constexpr int ttile_bytes = align((CTX + 2) * (CTY + 2));
   static constexpr int off_ptile = NS * stage_bytes;
-  static constexpr int off_ttile = off_ptile + align((CTX + 2) * (CTY + 2) * (int)sizeof(T));
-  static constexpr int off_bar = off_ttile + align((CTX + 2) * (CTY + 2));
-  static constexpr int total = off_bar + 128;
+  static constexpr int off_ttile = off_ptile + 2 * ptile_bytes;
+  static constexpr int off_bar = off_ttile + 2 * ttile_bytes;
+  static constexpr int total = off_bar + 2 * NS * 8;
+  static_assert(off_s % 128 == 0 && off_t % 128 == 0 && off_k % 128 == 0 && kbox_bytes % 128 == 0 &&
+                    stage_bytes % 128 == 0,
+                "TMA destinations must start on 128-byte boundaries");
 };
 
 // Row of the operator at one node from its 3x3 neighbourhood p[3][3] (p[1][1] = the
@@ -241,11 +249,12 @@ __device__ __forceinline__ T q4_row_nb(const T (&p)[3][3], uint8_t c0, uint8_t c
     // 2 K01 (dE + dW) + 2 K03 (dN + dS) + K02 (sum of the diagonal differences)
     return T(2) * kr[0] * (dE + dW) + T(2) * kr[2] * (dN + dS) + kr[1] * ((dNE + dSW) + (dNW + dSE));
   }
-  constexpr int kp = L::kplane_bytes / (int)sizeof(T);
   // coefficient m of the cell whose corner 0 is at box column kc, box row kr_, global index g
   auto coef = [&](int m, int kr_, int kc, long long g) -> T {
     if constexpr (L::kTmaK) {
-      return ks[m * kp + kr_ * L::KBW + kc];
+      // two boxes of [CTY+1][6*KHALF], cells interleaved (6 coefficients per cell)
+      const int half = kc >= L::KHALF;
+      return ks[half * (L::kbox_bytes / (int)sizeof(T)) + kr_ * (6 * L::KHALF) + (kc - half * L::KHALF) * 6 + m];
     } else {
       return __ldg(Kg + m * plane + g);
     }
@@ -292,29 +301,33 @@ __device__ __forceinline__ void cg_issue(const CgMaps& mp, int cur, unsigned cha
   tma_load_3d(stage + L::off_s, &mp.s[cur], 0, ij.x - 1, y0, bar);
   tma_load_2d(stage + L::off_t, &mp.tag, ij.x - 16, y0, bar);
   if constexpr (L::kTmaK) {
-    if (gen)
-      for (int m = 0; m < 6; ++m)
-        tma_load_2d(stage + L::off_k + m * L::kplane_bytes, &mp.k, x0, (int)(m * Rtot) + y0, bar);
+    if (gen) {
+      // interleaved coefficients as a [rows][6 P] array: two boxes of KHALF cells
+      tma_load_2d(stage + L::off_k, &mp.k, 6 * x0, y0, bar);
+      tma_load_2d(stage + L::off_k + L::kbox_bytes, &mp.k, 6 * (x0 + L::KHALF), y0, bar);
+    }
   }
 }
 
 // Nodes per thread (a vertical strip) and the thread -> strip mapping of a tile.
 constexpr int STRIP = CTY * CTX / NT;             // 4
 static_assert(STRIP * NT == CTX * CTY, "tile must split into strips");
+constexpr int NTC = NT + 32;                      // 8 consumer warps + 1 TMA producer warp
+constexpr int CONSUMER_BAR = 1;                   // named barrier of the consumer warps
 
 template <typename T, int NS>
-__global__ void __launch_bounds__(NT, 2) k_cg(CGArgs<T> a, const __grid_constant__ CgMaps mp) {
+__global__ void __launch_bounds__(NTC, sizeof(T) == 4 ? 2 : 1) k_cg(CGArgs<T> a, const __grid_constant__ CgMaps mp) {
   using L = CgSmem<T, NS>;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ T s_pb[MAXB];
   __shared__ double red[NT / 32][4];
   __shared__ double scratch[NT / 32 + 1];
   __shared__ double sh_qb[MAXB];
-  __shared__ int s_last;
-  T* pt = reinterpret_cast<T*>(smem + L::off_ptile);
-  uint8_t* tt = reinterpret_cast<uint8_t*>(smem + L::off_ttile);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::off_bar);
-  const int tid = linear_tid(), lane = tid & 31, warp = tid >> 5;
+  __shared__ int s_last, s_abort, s_issued;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + L::off_bar);
+  uint64_t* empty = full + NS;
+  const int tid = threadIdx.y * TX + threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const bool producer = warp == NT / 32;
   const int col = tid % CTX;                      // strip column inside the tile
   const int row_lo = (tid / CTX) * STRIP;         // first strip row inside the tile
   const int B = a.B;
@@ -322,170 +335,189 @@ __global__ void __launch_bounds__(NT, 2) k_cg(CGArgs<T> a, const __grid_constant
   constexpr int W = CTX + 2;
   constexpr int NH = 2 * W + 2 * CTY;             // halo ring positions
   if (tid == 0) {
-    for (int k = 0; k < NS; ++k) mbar_init(&bars[k], 1);
+    for (int k = 0; k < NS; ++k) {
+      mbar_init(&full[k], 1);
+      mbar_init(&empty[k], NT / 32);
+    }
     fence_mbar_init();
+    s_abort = 0;
+    s_issued = 0;
   }
   __syncthreads();
-  uint32_t parity = 0;                           // bit s: parity of the next wait on stage s
+  int q = 0;                                      // tiles consumed (consumers) / issued (producer) so far
   for (int sg = a.sc.cta_seg[blockIdx.x]; sg < a.sc.cta_seg[blockIdx.x + 1]; ++sg) {
     const int v = a.sc.seg_var[sg];
     if (a.st[v].phase != PH_CG) continue;
-    // variant constants in registers (the kernel's stores could alias them otherwise)
     const DevVariant& Vg = a.m.var[v];
     const int nx = Vg.nx, ny = Vg.ny, P = Vg.P, row0 = Vg.row0, nb = Vg.nb, body0 = Vg.body0;
     const long long base = Vg.base;
-    T kr[6];
-#pragma unroll
-    for (int m = 0; m < 6; ++m) kr[m] = krect<T>(Vg)[m];
-    const T alpha = (T)a.st[v].alpha, beta = (T)a.st[v].beta;
     const int cur = a.st[v].buf;
-    State4<T>* __restrict__ s_new = a.s[cur ^ 1];
     const int t0 = a.sc.seg_t0[sg], t1 = a.sc.seg_t1[sg];
-    if (tid < nb) {
-      const int gb = body0 + tid;
-      const T rn = next_r(a.sb[B + gb], a.sb[3 * B + gb], alpha);
-      s_pb[tid] = a.prm->fixed_bodies ? T(0) : next_p(rn, a.sb[2 * B + gb], beta);
-    }
-    if (tid == 0) {
-      for (int k = 0; k < NS && t0 + k < t1; ++k) {
-        fence_proxy_async_smem();
-        cg_issue<T>(mp, cur, smem + k * L::stage_bytes, &bars[k], a.sc.tile_ij[t0 + k], row0, a.Rtot,
-                    a.tile_gen[t0 + k] != 0);
-      }
-    }
-    int2 ij_next = a.sc.tile_ij[t0];
-    __syncthreads();
     Acc<T> acc;
     acc.zero();
-    for (int t = t0; t < t1; ++t) {
-      const int s = (t - t0) % NS;
-      unsigned char* st = smem + s * L::stage_bytes;
-      const int2 ij = ij_next;
-      if (t + 1 < t1) ij_next = a.sc.tile_ij[t + 1];
-      const bool ok = mbar_wait(&bars[s], (parity >> s) & 1u);
-      parity ^= 1u << s;
-      const State4<T>* Ss = reinterpret_cast<const State4<T>*>(st + L::off_s);
-      const uint8_t* Tg = reinterpret_cast<const uint8_t*>(st + L::off_t);
-      const T* Ks = reinterpret_cast<const T*>(st + L::off_k);
-      // global index of the tile's node (i0, j0)
-      const long long tb = base + (long long)ij.y * P + ij.x;
-      // pass 1: own strip and the halo ring -> p tile, effective tags
-      T rn4[STRIP], pn4[STRIP], xn4[STRIP];
-      uint8_t tg4[STRIP];
-      if (ok) {
-#pragma unroll
-        for (int u = 0; u < STRIP; ++u) {
-          const int li = 1 + col, lj = 1 + row_lo + u;
-          const int i = ij.x + col, j = ij.y + row_lo + u;
-          const bool in = (i <= nx) && (j <= ny);
-          const uint8_t tg = in ? Tg[lj * L::TBW + li + 15] : K_INACT;
-          const int kind = tg & KIND_MASK;
-          T rn = T(0), pn = T(0), xn = T(0);
-          if (kind == K_FREE) {
-            const State4<T> o = Ss[lj * L::SBW + li];
-            rn = next_r(o.r, o.q, alpha);
-            xn = next_x(o.x, o.p, alpha);
-            pn = next_p(rn, o.p, beta);
-          } else if (kind == K_BODY) {
-            pn = s_pb[a.m.bid[tb + (long long)(row_lo + u) * P + col]];
+    if (producer) {
+      // ---- TMA producer: stage s is reused once its previous tile has been released
+      if (lane == 0) {
+        for (int t = t0; t < t1; ++t, ++q) {
+          const int s = q % NS, use = q / NS;
+          if (use > 0 && !mbar_wait(&empty[s], (use - 1) & 1)) {
+            atomicExch(a.err, 1);
+            s_abort = 1;
+            break;
           }
-          pt[lj * W + li] = pn;
-          tt[lj * W + li] = tg;
-          rn4[u] = rn; pn4[u] = pn; xn4[u] = xn; tg4[u] = tg;
-        }
-        // halo ring positions spread over all eight warps
-        for (int h = warp + (NT / 32) * lane; h < NH; h += NT) {
-          int li, lj;
-          if (h < W) { li = h; lj = 0; }
-          else if (h < 2 * W) { li = h - W; lj = CTY + 1; }
-          else if (h < 2 * W + CTY) { li = 0; lj = 1 + (h - 2 * W); }
-          else { li = CTX + 1; lj = 1 + (h - 2 * W - CTY); }
-          const int i = ij.x - 1 + li, j = ij.y - 1 + lj;
-          uint8_t ht = K_INACT;
-          T hp = T(0);
-          if (i >= 0 && j >= 0 && i <= nx && j <= ny) {
-            ht = Tg[lj * L::TBW + li + 15];
-            const int hk = ht & KIND_MASK;
-            if (hk == K_FREE) {
-              const State4<T> o = Ss[lj * L::SBW + li];
-              hp = next_p(next_r(o.r, o.q, alpha), o.p, beta);
-            } else if (hk == K_BODY) {
-              hp = s_pb[a.m.bid[tb + (long long)(lj - 1) * P + (li - 1)]];
-            }
-          }
-          pt[lj * W + li] = hp;
-          tt[lj * W + li] = ht;
+          if (*(volatile int*)&s_abort) break;
+          fence_proxy_async_smem();
+          cg_issue<T>(mp, cur, smem + s * L::stage_bytes, &full[s], a.sc.tile_ij[t], row0, a.Rtot,
+                      a.tile_gen[t] != 0);
+          s_issued = q + 1;
         }
       }
-      if (__syncthreads_or(!ok)) {
-        if (tid == 0) atomicExch(a.err, 1);
-        // drain the stages whose loads may still be in flight (bounded), then leave
-        for (int k = 1; k < NS && t + k < t1; ++k) {
-          const int s2 = (t + k - t0) % NS;
-          mbar_wait(&bars[s2], (parity >> s2) & 1u);
-        }
-        return;
+      q = __shfl_sync(0xffffffffu, q, 0);
+    } else {
+      // ---- consumers
+      T kr[6];
+#pragma unroll
+      for (int m = 0; m < 6; ++m) kr[m] = krect<T>(Vg)[m];
+      const T alpha = (T)a.st[v].alpha, beta = (T)a.st[v].beta;
+      State4<T>* __restrict__ s_new = a.s[cur ^ 1];
+      if (tid < nb) {
+        const int gb = body0 + tid;
+        const T rn = next_r(a.sb[B + gb], a.sb[3 * B + gb], alpha);
+        s_pb[tid] = a.prm->fixed_bodies ? T(0) : next_p(rn, a.sb[2 * B + gb], beta);
       }
-      // pass 2: operator rows of the strip from a register window of the p tile
-      {
-        const int li = 1 + col;
-        T win[STRIP + 2][3];
-        uint8_t cl[STRIP + 1], cr[STRIP + 1];     // cells (i-1, j) and (i, j) for rows j0-1 .. j0+3
+      named_bar_sync(CONSUMER_BAR, NT);
+      for (int t = t0; t < t1; ++t, ++q) {
+        const int s = q % NS;
+        unsigned char* st = smem + s * L::stage_bytes;
+        T* pt = reinterpret_cast<T*>(smem + L::off_ptile + (q & 1) * L::ptile_bytes);
+        uint8_t* tt = reinterpret_cast<uint8_t*>(smem + L::off_ttile + (q & 1) * L::ttile_bytes);
+        const int2 ij = a.sc.tile_ij[t];
+        const bool ok = mbar_wait(&full[s], (q / NS) & 1);
+        const State4<T>* Ss = reinterpret_cast<const State4<T>*>(st + L::off_s);
+        const uint8_t* Tg = reinterpret_cast<const uint8_t*>(st + L::off_t);
+        const T* Ks = reinterpret_cast<const T*>(st + L::off_k);
+        const long long tb = base + (long long)ij.y * P + ij.x;
+        // pass 1: own strip and the halo ring -> p tile, effective tags
+        T rn4[STRIP], pn4[STRIP], xn4[STRIP];
+        uint8_t tg4[STRIP];
+        if (ok) {
 #pragma unroll
-        for (int r = 0; r < STRIP + 2; ++r) {
-          const int lj = row_lo + r;              // p tile rows row_lo .. row_lo + STRIP + 1
-          win[r][0] = pt[lj * W + li - 1];
-          win[r][1] = pt[lj * W + li];
-          win[r][2] = pt[lj * W + li + 1];
-        }
-#pragma unroll
-        for (int r = 0; r < STRIP + 1; ++r) {
-          const int lj = row_lo + r;
-          cl[r] = tt[lj * W + li - 1];
-          cr[r] = tt[lj * W + li];
-        }
-        T yq[STRIP], rr[STRIP], pp[STRIP];
-#pragma unroll
-        for (int u = 0; u < STRIP; ++u) {
-          const int kind = tg4[u] & KIND_MASK;
-          yq[u] = T(0);
-          rr[u] = T(0);
-          pp[u] = T(0);
-          if (kind == K_FREE || kind == K_BODY) {
-            const long long n = tb + (long long)(row_lo + u) * P + col;
-            const T nbh[3][3] = {{win[u][0], win[u][1], win[u][2]},
-                                 {win[u + 1][0], win[u + 1][1], win[u + 1][2]},
-                                 {win[u + 2][0], win[u + 2][1], win[u + 2][2]}};
-            const T y = q4_row_nb<T>(nbh, cr[u + 1], cl[u + 1], cl[u], cr[u], Ks, col + 4, row_lo + u + 1, n, P,
-                                     kplane<T>(a.m), plane, kr);
-            State4<T> o;
-            o.x = xn4[u];
-            o.r = rn4[u];
-            o.p = pn4[u];
-            o.q = y;
-            s_new[n] = o;          // BODY nodes carry only q (x, r, p are zero there)
+          for (int u = 0; u < STRIP; ++u) {
+            const int li = 1 + col, lj = 1 + row_lo + u;
+            const int i = ij.x + col, j = ij.y + row_lo + u;
+            const bool in = (i <= nx) && (j <= ny);
+            const uint8_t tg = in ? Tg[lj * L::TBW + li + 15] : K_INACT;
+            const int kind = tg & KIND_MASK;
+            T rn = T(0), pn = T(0), xn = T(0);
             if (kind == K_FREE) {
-              yq[u] = y;
-              rr[u] = rn4[u];
-              pp[u] = pn4[u];
+              const State4<T> o = Ss[lj * L::SBW + li];
+              rn = next_r(o.r, o.q, alpha);
+              xn = next_x(o.x, o.p, alpha);
+              pn = next_p(rn, o.p, beta);
+            } else if (kind == K_BODY) {
+              pn = s_pb[a.m.bid[tb + (long long)(row_lo + u) * P + col]];
             }
+            pt[lj * W + li] = pn;
+            tt[lj * W + li] = tg;
+            rn4[u] = rn; pn4[u] = pn; xn4[u] = xn; tg4[u] = tg;
+          }
+          for (int h = warp + (NT / 32) * lane; h < NH; h += NT) {
+            int li, lj;
+            if (h < W) { li = h; lj = 0; }
+            else if (h < 2 * W) { li = h - W; lj = CTY + 1; }
+            else if (h < 2 * W + CTY) { li = 0; lj = 1 + (h - 2 * W); }
+            else { li = CTX + 1; lj = 1 + (h - 2 * W - CTY); }
+            const int i = ij.x - 1 + li, j = ij.y - 1 + lj;
+            uint8_t ht = K_INACT;
+            T hp = T(0);
+            if (i >= 0 && j >= 0 && i <= nx && j <= ny) {
+              ht = Tg[lj * L::TBW + li + 15];
+              const int hk = ht & KIND_MASK;
+              if (hk == K_FREE) {
+                const State4<T> o = Ss[lj * L::SBW + li];
+                hp = next_p(next_r(o.r, o.q, alpha), o.p, beta);
+              } else if (hk == K_BODY) {
+                hp = s_pb[a.m.bid[tb + (long long)(lj - 1) * P + (li - 1)]];
+              }
+            }
+            pt[lj * W + li] = hp;
+            tt[lj * W + li] = ht;
           }
         }
-        // dots over the FREE nodes (others contribute exact zeros)
-        acc.add4(0, rr, rr);
-        acc.add4(1, pp, yq);
-        acc.add4(2, rr, yq);
-        acc.add4(3, yq, yq);
+        if (named_bar_or(CONSUMER_BAR, NT, !ok)) {
+          if (tid == 0) {
+            atomicExch(a.err, 1);
+            s_abort = 1;
+          }
+          break;
+        }
+        // pass 2: operator rows of the strip from a register window of the p tile
+        {
+          const int li = 1 + col;
+          T win[STRIP + 2][3];
+          uint8_t cl[STRIP + 1], cr[STRIP + 1];     // cells (i-1, j) and (i, j) for rows j0-1 .. j0+3
+#pragma unroll
+          for (int r = 0; r < STRIP + 2; ++r) {
+            const int lj = row_lo + r;
+            win[r][0] = pt[lj * W + li - 1];
+            win[r][1] = pt[lj * W + li];
+            win[r][2] = pt[lj * W + li + 1];
+          }
+#pragma unroll
+          for (int r = 0; r < STRIP + 1; ++r) {
+            const int lj = row_lo + r;
+            cl[r] = tt[lj * W + li - 1];
+            cr[r] = tt[lj * W + li];
+          }
+          T yq[STRIP], rr[STRIP], pp[STRIP];
+#pragma unroll
+          for (int u = 0; u < STRIP; ++u) {
+            const int kind = tg4[u] & KIND_MASK;
+            yq[u] = T(0);
+            rr[u] = T(0);
+            pp[u] = T(0);
+            if (kind == K_FREE || kind == K_BODY) {
+              const long long n = tb + (long long)(row_lo + u) * P + col;
+              const T nbh[3][3] = {{win[u][0], win[u][1], win[u][2]},
+                                   {win[u + 1][0], win[u + 1][1], win[u + 1][2]},
+                                   {win[u + 2][0], win[u + 2][1], win[u + 2][2]}};
+              const T y = q4_row_nb<T>(nbh, cr[u + 1], cl[u + 1], cl[u], cr[u], Ks, col + 4, row_lo + u + 1, n, P,
+                                       kplane<T>(a.m), plane, kr);
+              State4<T> o;
+              o.x = xn4[u];
+              o.r = rn4[u];
+              o.p = pn4[u];
+              o.q = y;
+              s_new[n] = o;          // BODY nodes carry only q (x, r, p are zero there)
+              if (kind == K_FREE) {
+                yq[u] = y;
+                rr[u] = rn4[u];
+                pp[u] = pn4[u];
+              }
+            }
+          }
+          acc.add4(0, rr, rr);
+          acc.add4(1, pp, yq);
+          acc.add4(2, rr, yq);
+          acc.add4(3, yq, yq);
+        }
+        // release the stage to the producer (one arrival per consumer warp)
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
       }
+    }
+    // ---- segment end: partial sums, last-CTA reduction (all warps)
+    __syncthreads();
+    if (s_abort) {
+      // drain loads issued but not consumed (bounded), then leave
+      if (tid == 0)
+        for (int k = q; k < s_issued; ++k) mbar_wait(&full[k % NS], (k / NS) & 1);
       __syncthreads();
-      if (tid == 0 && t + NS < t1) {
-        fence_proxy_async_smem();
-        cg_issue<T>(mp, cur, st, &bars[s], a.sc.tile_ij[t + NS], row0, a.Rtot, a.tile_gen[t + NS] != 0);
-      }
+      return;
     }
     double w4[4];
     acc.warp_reduce(w4);
-    if (lane == 0)
+    if (lane == 0 && !producer)
       for (int k = 0; k < 4; ++k) red[warp][k] = w4[k];
     __syncthreads();
     if (tid == 0) {
@@ -898,7 +930,7 @@ static CgConfig& cg_config(Batch& b, int precision, int ns) {
   const int smem = cg_smem(precision, ns);
   PF_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   int occ = 0;
-  PF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, f, NT, smem));
+  PF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, f, NTC, smem));
   std::vector<int> tc(b.Tcg);
   long long t = 0;
   for (int v = 0; v < b.nv; ++v) {
@@ -961,7 +993,8 @@ static void make_cg_maps(Batch& b, CgMaps& mp, State4<T>* const st[2], T* K) {
     if (r != CUDA_SUCCESS) throw Error{PF_ECUDA, "cuTensorMapEncodeTiled (state) failed (" + std::to_string((int)r) + ")"};
   }
   encode_2d(&mp.tag, b.tag, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, b.P, b.Rtot, L::TBW, CTY + 2);
-  encode_2d(&mp.k, K, dt, e, b.P, 6 * b.Rtot, L::KBW, CTY + 1);
+  if (sizeof(T) == 4) encode_2d(&mp.k, K, dt, e, 6 * b.P, b.Rtot, 6 * L::KHALF, CTY + 1);   // interleaved
+  else encode_2d(&mp.k, K, dt, e, b.P, 6 * b.Rtot, L::KBW, CTY + 1);
 }
 
 void ensure_solver_memory(Batch& b, int precision) {
@@ -993,7 +1026,7 @@ void ensure_solver_memory(Batch& b, int precision) {
   }
   if (precision == PF_MIXED && !b.st32[0]) {
     for (int k = 0; k < 2; ++k) b.st32[k] = (State4<float>*)dev_alloc(b, V * sizeof(State4<float>));
-    make_cg_maps<float>(b, b.maps[1], b.st32, b.K32);
+    make_cg_maps<float>(b, b.maps[1], b.st32, b.K32i);
     PF_CUDA(cudaMemcpy(b.d_sbuf + 2, b.st32, 2 * sizeof(void*), cudaMemcpyHostToDevice));
   }
 }
@@ -1086,7 +1119,7 @@ static void fill_resid_args(Batch& b, ResidArgs<T>& a, State4<T>* const st[2], T
 
 // the k_cg launches of one chunk (captured once as a graph)
 static void launch_cg_chunk(Batch& b, int precision, int chunk, cudaStream_t s) {
-  const dim3 blk(TX, TY);
+  const dim3 blk(TX, NTC / TX);
   const int ns = b.cg_stages;
   CgConfig& c = cg_config(b, precision, ns);
   if (precision == PF_FP64) {
