@@ -75,7 +75,7 @@ struct Batch {
   int2* tile_cg_ij = nullptr;
   int* tile_cg_var = nullptr;
   uint8_t* tile_cg_gen = nullptr;    // 1 if a cell used by the tile has stored coefficients
-  CgConfig cg_cfg[2][2];             // [precision][stages - 2]
+  CgConfig cg_cfg[2][3];             // [precision][stages - 2]
   int cg_stages = 2;
   int nsm = 0;
   long long Rtot = 0;                // rows of the batch's 2-D node arrays (Vtot / P)

@@ -205,11 +205,14 @@ struct CgSmem {
   static constexpr int KHALF = KBW / 2;          // cells per coefficient box (two boxes of 6*KHALF floats)
   static constexpr int TBW = CTX + 32;           // tag box width
   static constexpr int SB = 4 * SBW * (CTY + 2); // elements of the state box
+  static constexpr int SHALF = SBW / 2;          // nodes per state box (two boxes of 4*SHALF values per row)
+  static constexpr int sbox_bytes = ((CTY + 2) * 4 * SHALF * (int)sizeof(T) + 127) / 128 * 128;
+  static constexpr int sbox_recs = sbox_bytes / (4 * (int)sizeof(T));
   static constexpr int KB = KBW * (CTY + 1);     // elements of one coefficient plane box
   static constexpr bool kTmaK = sizeof(T) == 4;
   static constexpr int align(int b) { return (b + 127) / 128 * 128; }
   static constexpr int off_s = 0;
-  static constexpr int off_t = off_s + align(SB * (int)sizeof(T));
+  static constexpr int off_t = off_s + 2 * sbox_bytes;
   static constexpr int off_k = off_t + align(TBW * (CTY + 2));
   // two coefficient boxes, each starting on a 128-byte boundary (TMA destination alignment)
   static constexpr int kbox_bytes = align((CTY + 1) * 6 * KHALF * (int)sizeof(T));
@@ -225,6 +228,7 @@ struct CgSmem {
   static constexpr int off_bar = off_ttile + 2 * ttile_bytes;
   static constexpr int total = off_bar + 2 * NS * 8;
   static_assert(off_s % 128 == 0 && off_t % 128 == 0 && off_k % 128 == 0 && kbox_bytes % 128 == 0 &&
+                    sbox_bytes % 128 == 0 && SBW % 2 == 0 &&
                     stage_bytes % 128 == 0,
                 "TMA destinations must start on 128-byte boundaries");
 };
@@ -298,7 +302,9 @@ __device__ __forceinline__ void cg_issue(const CgMaps& mp, int cur, unsigned cha
   using L = CgSmem<T, 2>;   // stage layout does not depend on the stage count
   const int x0 = ij.x - 4, y0 = row0 + ij.y - 1;
   mbar_arrive_expect_tx(bar, L::tx_base + (gen ? L::tx_k : 0));
-  tma_load_3d(stage + L::off_s, &mp.s[cur], 0, ij.x - 1, y0, bar);
+  // state records viewed as a [rows][4 P] array: two boxes of SHALF nodes (long rows)
+  tma_load_2d(stage + L::off_s, &mp.s[cur], 4 * (ij.x - 1), y0, bar);
+  tma_load_2d(stage + L::off_s + L::sbox_bytes, &mp.s[cur], 4 * (ij.x - 1 + L::SHALF), y0, bar);
   tma_load_2d(stage + L::off_t, &mp.tag, ij.x - 16, y0, bar);
   if constexpr (L::kTmaK) {
     if (gen) {
@@ -314,6 +320,14 @@ constexpr int STRIP = CTY * CTX / NT;             // 4
 static_assert(STRIP * NT == CTX * CTY, "tile must split into strips");
 constexpr int NTC = NT + 32;                      // 8 consumer warps + 1 TMA producer warp
 constexpr int CONSUMER_BAR = 1;                   // named barrier of the consumer warps
+
+// State record of p-tile position (li, lj) inside the two staged state boxes.
+template <typename T>
+__device__ __forceinline__ State4<T> staged_state(const State4<T>* Ss, int li, int lj) {
+  using L = CgSmem<T>;
+  const int half = li >= L::SHALF;
+  return Ss[half * L::sbox_recs + lj * L::SHALF + (li - half * L::SHALF)];
+}
 
 template <typename T, int NS>
 __global__ void __launch_bounds__(NTC, sizeof(T) == 4 ? 2 : 1) k_cg(CGArgs<T> a, const __grid_constant__ CgMaps mp) {
@@ -410,7 +424,7 @@ __global__ void __launch_bounds__(NTC, sizeof(T) == 4 ? 2 : 1) k_cg(CGArgs<T> a,
             const int kind = tg & KIND_MASK;
             T rn = T(0), pn = T(0), xn = T(0);
             if (kind == K_FREE) {
-              const State4<T> o = Ss[lj * L::SBW + li];
+              const State4<T> o = staged_state<T>(Ss, li, lj);
               rn = next_r(o.r, o.q, alpha);
               xn = next_x(o.x, o.p, alpha);
               pn = next_p(rn, o.p, beta);
@@ -434,7 +448,7 @@ __global__ void __launch_bounds__(NTC, sizeof(T) == 4 ? 2 : 1) k_cg(CGArgs<T> a,
               ht = Tg[lj * L::TBW + li + 15];
               const int hk = ht & KIND_MASK;
               if (hk == K_FREE) {
-                const State4<T> o = Ss[lj * L::SBW + li];
+                const State4<T> o = staged_state<T>(Ss, li, lj);
                 hp = next_p(next_r(o.r, o.q, alpha), o.p, beta);
               } else if (hk == K_BODY) {
                 hp = s_pb[a.m.bid[tb + (long long)(lj - 1) * P + (li - 1)]];
@@ -913,13 +927,15 @@ template <typename T, int NS>
 static const void* cg_kernel() { return (const void*)k_cg<T, NS>; }
 
 static int cg_smem(int precision, int ns) {
-  if (precision == PF_FP64) return ns == 3 ? CgSmem<double, 3>::total : CgSmem<double, 2>::total;
-  return ns == 3 ? CgSmem<float, 3>::total : CgSmem<float, 2>::total;
+  if (precision == PF_FP64)
+    return ns == 4 ? CgSmem<double, 4>::total : ns == 3 ? CgSmem<double, 3>::total : CgSmem<double, 2>::total;
+  return ns == 4 ? CgSmem<float, 4>::total : ns == 3 ? CgSmem<float, 3>::total : CgSmem<float, 2>::total;
 }
 
 static const void* cg_func(int precision, int ns) {
-  if (precision == PF_FP64) return ns == 3 ? cg_kernel<double, 3>() : cg_kernel<double, 2>();
-  return ns == 3 ? cg_kernel<float, 3>() : cg_kernel<float, 2>();
+  if (precision == PF_FP64)
+    return ns == 4 ? cg_kernel<double, 4>() : ns == 3 ? cg_kernel<double, 3>() : cg_kernel<double, 2>();
+  return ns == 4 ? cg_kernel<float, 4>() : ns == 3 ? cg_kernel<float, 3>() : cg_kernel<float, 2>();
 }
 
 // Persistent grid (occupancy x SMs) and tile schedule of one CG configuration, built once.
@@ -981,17 +997,8 @@ static void make_cg_maps(Batch& b, CgMaps& mp, State4<T>* const st[2], T* K) {
   using L = CgSmem<T>;
   const CUtensorMapDataType dt = sizeof(T) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
   const int e = (int)sizeof(T);
-  for (int k = 0; k < 2; ++k) {
-    // state records as a 3-D tensor: (component, column, row)
-    const cuuint64_t dims[3] = {4, (cuuint64_t)b.P, (cuuint64_t)b.Rtot};
-    const cuuint64_t strides[2] = {(cuuint64_t)4 * e, (cuuint64_t)b.P * 4 * e};
-    const cuuint32_t box[3] = {4, (cuuint32_t)L::SBW, (cuuint32_t)(CTY + 2)};
-    const cuuint32_t es[3] = {1, 1, 1};
-    const CUresult r = tensor_map_encoder()(&mp.s[k], dt, 3, st[k], dims, strides, box, es,
-                                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) throw Error{PF_ECUDA, "cuTensorMapEncodeTiled (state) failed (" + std::to_string((int)r) + ")"};
-  }
+  for (int k = 0; k < 2; ++k)   // state records as a [rows][4 P] array, boxes of SHALF records
+    encode_2d(&mp.s[k], st[k], dt, e, 4 * b.P, b.Rtot, 4 * L::SHALF, CTY + 2);
   encode_2d(&mp.tag, b.tag, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, b.P, b.Rtot, L::TBW, CTY + 2);
   if (sizeof(T) == 4) encode_2d(&mp.k, K, dt, e, 6 * b.P, b.Rtot, 6 * L::KHALF, CTY + 1);   // interleaved
   else encode_2d(&mp.k, K, dt, e, b.P, 6 * b.Rtot, L::KBW, CTY + 1);
@@ -1126,14 +1133,16 @@ static void launch_cg_chunk(Batch& b, int precision, int chunk, cudaStream_t s) 
     CGArgs<double> a;
     fill_cg_args<double>(b, a, b.st64, b.sb64, c.sc);
     for (int k = 0; k < chunk; ++k) {
-      if (ns == 3) k_cg<double, 3><<<c.G, blk, c.smem, s>>>(a, b.maps[0]);
+      if (ns == 4) k_cg<double, 4><<<c.G, blk, c.smem, s>>>(a, b.maps[0]);
+      else if (ns == 3) k_cg<double, 3><<<c.G, blk, c.smem, s>>>(a, b.maps[0]);
       else k_cg<double, 2><<<c.G, blk, c.smem, s>>>(a, b.maps[0]);
     }
   } else {
     CGArgs<float> a;
     fill_cg_args<float>(b, a, b.st32, b.sb32, c.sc);
     for (int k = 0; k < chunk; ++k) {
-      if (ns == 3) k_cg<float, 3><<<c.G, blk, c.smem, s>>>(a, b.maps[1]);
+      if (ns == 4) k_cg<float, 4><<<c.G, blk, c.smem, s>>>(a, b.maps[1]);
+      else if (ns == 3) k_cg<float, 3><<<c.G, blk, c.smem, s>>>(a, b.maps[1]);
       else k_cg<float, 2><<<c.G, blk, c.smem, s>>>(a, b.maps[1]);
     }
   }
@@ -1202,7 +1211,8 @@ pf_status solve_core(Batch& b, double U, const pf_solve_opts& o, double* dev_psi
   ensure_solver_memory(b, prec);
   {
     const char* e = getenv("PFQ4_CG_STAGES");
-    b.cg_stages = (e && atoi(e) == 3) ? 3 : 2;
+    const int ns = e ? atoi(e) : 2;
+    b.cg_stages = (ns >= 2 && ns <= 4) ? ns : 2;
   }
   cudaStream_t s = b.stream;
   SolveParams sp{};
