@@ -110,12 +110,26 @@ __global__ void k_kinds(const DevVariant* var, const int* tile_var, const int2* 
 }
 
 // 3. one Jacobi sweep: nodes outside every body and off the outer ring take the
-//    average of their four neighbours, summed W, E, S, N, divided by 4.
+//    average of their four neighbours, summed W, E, S, N, divided by 4.  Before sweep s
+//    (0-based) the displacement is exactly zero farther than s cells from every body
+//    node, so a tile farther than s + 1 cells from every body's node box is all zeros
+//    in both ping-pong buffers and is skipped (bit-identical result, less traffic).
 __global__ void k_jacobi(const DevVariant* var, const int* tile_var, const int2* tile_ij,
-                         const int* bid, const uint8_t* tag, const double2* __restrict__ src,
-                         double2* __restrict__ dst) {
+                         const int* bid, const uint8_t* tag, const int4* bbox, int sweep,
+                         const double2* __restrict__ src, double2* __restrict__ dst) {
   TileCtx c = tile_ctx(var, tile_var, tile_ij);
   const DevVariant& V = var[c.v];
+  {
+    const int2 ij = tile_ij[blockIdx.x];
+    const int reach = sweep + 1;
+    bool near = false;
+    for (int k = 0; k < V.nb && !near; ++k) {
+      const int4 bx = bbox[V.body0 + k];
+      near = ij.x <= bx.y + reach && ij.x + TX - 1 >= bx.x - reach && ij.y <= bx.w + reach &&
+             ij.y + TY - 1 >= bx.z - reach;
+    }
+    if (!near) return;
+  }
   if (!c.in) return;
   const long long n = c.n;
   double2 out = src[n];
@@ -534,7 +548,7 @@ void build_batch(Batch& b, const pf_grid* grids, const int* body_offsets, const 
                                bc[2], bc[3], err);
   PF_CUDA(cudaMemcpyAsync(dB, dA, Vt * sizeof(double2), cudaMemcpyDeviceToDevice, s));
   for (int it = 0; it < sweeps; ++it) {
-    k_jacobi<<<grid, blk, 0, s>>>(b.d_var, b.tile_var, b.tile_ij, b.bid, b.tag, dA, dB);
+    k_jacobi<<<grid, blk, 0, s>>>(b.d_var, b.tile_var, b.tile_ij, b.bid, b.tag, b.d_bbox, it, dA, dB);
     std::swap(dA, dB);
   }
   k_finalize<<<grid, blk, 0, s>>>(b.d_var, b.tile_var, b.tile_ij, dA, b.tag, b.X, Vt);
