@@ -63,6 +63,7 @@ struct Batch {
   float* K32i = nullptr;             // [Vtot][6] the same coefficients interleaved per cell (TMA-friendly)
   int* body_ptr = nullptr;           // [B+1]
   long long* body_nodes = nullptr;
+  double* bq = nullptr;              // [body nodes] q of the last fused CG iteration, per BODY node
   int* edge_ptr = nullptr;           // [B+1]
   long long* edge_rec = nullptr;     // (cell padded index << 2) | first corner
   long long* d_stats_i = nullptr;    // [nv][6] integer counts

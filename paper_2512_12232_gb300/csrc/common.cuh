@@ -199,6 +199,16 @@ template <> struct Acc<float> {
 
 __device__ __forceinline__ int linear_tid() { return threadIdx.y * TX + threadIdx.x; }
 
+// Atomic add with acquire-release semantics at GPU scope; returns the old value.  Used
+// as the arrival of a CTA at a per-variant counter: it publishes the CTA's stores
+// (ordered before it by a block barrier) and, in the last CTA, makes the other CTAs'
+// stores visible to the threads that synchronise with it through a block barrier.
+__device__ __forceinline__ int atom_add_acq_rel_gpu(int* p, int v) {
+  int old;
+  asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+
 // Block-wide fixed-order sum of a double; all threads get the result.
 __device__ __forceinline__ double block_sum(double x, double* scratch /* >= NT/32 */) {
   const int tid = linear_tid(), lane = tid & 31, w = tid >> 5;

@@ -43,6 +43,7 @@ struct CGArgs {
   const SolveParams* prm;
   State4<T>* s[2];          // ping-pong state, parity VarState::buf holds the current one
   T* sb;                    // [4][B] body x, r, p, q of the CG
+  double* bq;               // [body nodes] q at each BODY node (slot order of body_nodes)
   int B;
   int* n_done;
   const uint8_t* tile_gen;  // per fused-CG tile: stored coefficients needed
@@ -104,15 +105,6 @@ __device__ double body_gather(const MeshDev& m, int gb, const T* vec, double* sc
   return block_sum(s, scratch);
 }
 
-// Sum of q over the nodes of one body from state records (fixed order).
-template <typename T>
-__device__ double body_gather_q(const MeshDev& m, int gb, const State4<T>* st, double* scratch) {
-  double s = 0.0;
-  const int e1 = m.body_ptr[gb + 1];
-  for (int e = m.body_ptr[gb] + linear_tid(); e < e1; e += NT) s += (double)__ldcg(&st[m.body_nodes[e]].q);
-  return block_sum(s, scratch);
-}
-
 // ---------------------------------------------------------------- fused CG step
 __device__ __forceinline__ double warp_sum(double x) {
 #pragma unroll
@@ -120,56 +112,117 @@ __device__ __forceinline__ double warp_sum(double x) {
   return x;
 }
 
+// What the end of an iteration needs from global memory, loaded by the consumer warps
+// at the start of each segment so that the serial finaliser issues no dependent loads.
 template <typename T>
-__device__ void finalize_cg(const CGArgs<T>& a, int v, double* scratch, double* sh_qb) {
-  const DevVariant& V = a.m.var[v];
+struct FinCache {
+  T sb[4][MAXB];             // body x, r, p, q before this iteration
+  int bptr[MAXB + 1];        // body_ptr of the variant's bodies (global slots)
+  double alpha, beta, gamma_start, thr_rel, thr_abs2;
+  long long iters, inner_iters, k_max;
+  int seg0, seg1, buf, fixed;
+};
+
+// A BODY node has no x, r or p of its own (its value is the body's unknown), so the x
+// field of its state record carries the node's position in body_nodes (its slot), as
+// raw bits: the fused CG step then finds the node's body and stores its row of A p by
+// slot with no extra memory access.
+__device__ __forceinline__ float slot_bits(int e, float) { return __int_as_float(e); }
+__device__ __forceinline__ double slot_bits(int e, double) { return __longlong_as_double((long long)e); }
+__device__ __forceinline__ int slot_of(float x) { return __float_as_int(x); }
+__device__ __forceinline__ int slot_of(double x) { return (int)__double_as_longlong(x); }
+
+// Local index of the body whose slot range [bptr[k], bptr[k+1]) holds slot e.
+__device__ __forceinline__ int body_of_slot(const int* bptr, int nb, int e) {
+  int lo = 0, hi = nb;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (bptr[mid] <= e) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// Runs in the last CTA of variant v to finish an iteration (all NTHR threads of the
+// CTA); gbuf is shared memory of gcap >= 4 * MAXB doubles that no copy is writing.
+template <typename T, int NTHR>
+__device__ __noinline__ void finalize_cg(const CGArgs<T>& a, int v, int nb, int body0, const FinCache<T>& fc, double* scratch,
+                            double* sh_qb, double* gbuf, int gcap) {
   VarState* S = &a.st[v];
   const int tid = linear_tid(), warp = tid >> 5, lane = tid & 31;
+  constexpr int NW = NTHR / 32;
+  constexpr int GB = 8;                      // independent loads in flight per thread
   double* d = scratch;                       // d[0..3]: the four dots over FREE nodes
   // warps 0-3: dot k = warp over the variant's segment partials (fixed order)
   if (warp < 4) {
     double s = 0.0;
-    for (int sg = a.sc.var_seg0[v] + lane; sg < a.sc.var_seg1[v]; sg += 32) s += __ldcg(&a.sc.partial[sg * 4 + warp]);
+    for (int sg = fc.seg0 + lane; sg < fc.seg1; sg += 32) s += __ldcg(&a.sc.partial[sg * 4 + warp]);
     s = warp_sum(s);
     if (lane == 0) d[warp] = s;
   }
-  // warps 4-7: collapsed body rows of q (the new parity), one warp per body
-  const State4<T>* snew = a.s[S->buf ^ 1];
-  for (int k = warp - 4; k < V.nb && warp < NT / 32; k += NT / 32 - 4) {
-    if (k < 0) continue;
-    const int gb = V.body0 + k;
-    double s = 0.0;
-    for (int e = a.m.body_ptr[gb] + lane; e < a.m.body_ptr[gb + 1]; e += 32)
-      s += (double)__ldcg(&snew[a.m.body_nodes[e]].q);
-    s = warp_sum(s);
-    if (lane == 0) sh_qb[k] = s;
+  // collapsed body rows of q: every thread fetches body-node q values (stored by slot
+  // during the iteration) into shared memory, then one warp per body sums its entries
+  // in a fixed order, chunk by chunk
+  for (int k = tid; k < nb; k += NTHR) sh_qb[k] = 0.0;
+  const int e0 = fc.bptr[0], e1 = fc.bptr[nb];
+  for (int c0 = e0; c0 < e1; c0 += gcap) {
+    const int c1 = min(e1, c0 + gcap);
+    for (int b = c0; b < c1; b += GB * NTHR) {
+      double val[GB];
+#pragma unroll
+      for (int u = 0; u < GB; ++u) {
+        const int e = b + u * NTHR + tid;
+        val[u] = e < c1 ? __ldcg(&a.bq[e]) : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < GB; ++u) {
+        const int e = b + u * NTHR + tid;
+        if (e < c1) gbuf[e - c0] = val[u];
+      }
+    }
+    __syncthreads();
+    for (int k = warp; k < nb; k += NW) {
+      const int b0 = max(c0, fc.bptr[k]), b1 = min(c1, fc.bptr[k + 1]);
+      double s = 0.0;
+      for (int e = b0 + lane; e < b1; e += 32) s += gbuf[e - c0];
+      s = warp_sum(s);
+      if (lane == 0) sh_qb[k] += s;
+    }
+    __syncthreads();
+  }
+  // body unknowns, one thread per body; their dot contributions are added in body order
+  double* contrib = gbuf;                    // [4][MAXB]
+  const T alpha = (T)fc.alpha, beta = (T)fc.beta;
+  const int nbu = fc.fixed ? 0 : nb;
+  const int B = a.B;
+  for (int k = tid; k < nbu; k += NTHR) {
+    const int gb = body0 + k;
+    const T pb = fc.sb[2][k];
+    const T rn = next_r(fc.sb[1][k], fc.sb[3][k], alpha);
+    const T pn = next_p(rn, pb, beta);
+    const T xn = next_x(fc.sb[0][k], pb, alpha);
+    const T qn = (T)sh_qb[k];
+    a.sb[gb] = xn;
+    a.sb[B + gb] = rn;
+    a.sb[2 * B + gb] = pn;
+    a.sb[3 * B + gb] = qn;
+    contrib[k] = (double)rn * (double)rn;
+    contrib[MAXB + k] = (double)pn * (double)qn;
+    contrib[2 * MAXB + k] = (double)rn * (double)qn;
+    contrib[3 * MAXB + k] = (double)qn * (double)qn;
   }
   __syncthreads();
-  if (linear_tid() == 0) {
-    const T alpha = (T)S->alpha, beta = (T)S->beta;
+  if (tid == 0) {
     double dd[4] = {d[0], d[1], d[2], d[3]};
-    const int B = a.B;
-    for (int k = 0; k < (a.prm->fixed_bodies ? 0 : V.nb); ++k) {
-      const int gb = V.body0 + k;
-      const T xb = a.sb[gb], rb = a.sb[B + gb], pb = a.sb[2 * B + gb], qb = a.sb[3 * B + gb];
-      const T rn = next_r(rb, qb, alpha);
-      const T pn = next_p(rn, pb, beta);
-      const T xn = next_x(xb, pb, alpha);
-      const T qn = (T)sh_qb[k];
-      a.sb[gb] = xn;
-      a.sb[B + gb] = rn;
-      a.sb[2 * B + gb] = pn;
-      a.sb[3 * B + gb] = qn;
-      dd[0] += (double)rn * (double)rn;
-      dd[1] += (double)pn * (double)qn;
-      dd[2] += (double)rn * (double)qn;
-      dd[3] += (double)qn * (double)qn;
-    }
+    for (int k = 0; k < nbu; ++k)
+      for (int j = 0; j < 4; ++j) dd[j] += contrib[j * MAXB + k];
     const double g = dd[0], pi = dd[1], rho = dd[2], mu = dd[3];
-    S->buf ^= 1;
-    S->iters += 1;
-    S->inner_iters += 1;
-    if (S->inner_iters == 1) S->gamma_start = g;
+    const long long iters = fc.iters + 1, inner = fc.inner_iters + 1;
+    const double gs = inner == 1 ? g : fc.gamma_start;
+    S->buf = fc.buf ^ 1;
+    S->iters = iters;
+    S->inner_iters = inner;
+    if (inner == 1) S->gamma_start = g;
     S->gamma = g; S->pi = pi; S->rho = rho; S->mu = mu;
     if (!isfinite(g) || !isfinite(pi) || !(pi > 0.0)) {
       if (g == 0.0) {
@@ -179,9 +232,9 @@ __device__ void finalize_cg(const CGArgs<T>& a, int v, double* scratch, double* 
         S->phase = PH_DONE;
         atomicAdd(a.n_done, 1);
       }
-    } else if (g <= fmax(S->thr_rel * S->gamma_start, S->thr_abs2)) {
+    } else if (g <= fmax(fc.thr_rel * gs, fc.thr_abs2)) {
       S->phase = PH_RESID;
-    } else if (S->iters >= a.prm->k_max) {
+    } else if (iters >= fc.k_max) {
       S->capped = 1;
       S->phase = PH_RESID;
     } else {
@@ -337,6 +390,7 @@ __global__ void __launch_bounds__(NTC, sizeof(T) == 4 ? 2 : 1) k_cg(CGArgs<T> a,
   __shared__ double red[NT / 32][4];
   __shared__ double scratch[NT / 32 + 1];
   __shared__ double sh_qb[MAXB];
+  __shared__ FinCache<T> fc;
   __shared__ int s_last, s_abort, s_issued;
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + L::off_bar);
   uint64_t* empty = full + NS;
@@ -396,8 +450,28 @@ __global__ void __launch_bounds__(NTC, sizeof(T) == 4 ? 2 : 1) k_cg(CGArgs<T> a,
       State4<T>* __restrict__ s_new = a.s[cur ^ 1];
       if (tid < nb) {
         const int gb = body0 + tid;
-        const T rn = next_r(a.sb[B + gb], a.sb[3 * B + gb], alpha);
-        s_pb[tid] = a.prm->fixed_bodies ? T(0) : next_p(rn, a.sb[2 * B + gb], beta);
+        const T xb = a.sb[gb], rb = a.sb[B + gb], pb = a.sb[2 * B + gb], qb = a.sb[3 * B + gb];
+        fc.sb[0][tid] = xb;
+        fc.sb[1][tid] = rb;
+        fc.sb[2][tid] = pb;
+        fc.sb[3][tid] = qb;
+        s_pb[tid] = a.prm->fixed_bodies ? T(0) : next_p(next_r(rb, qb, alpha), pb, beta);
+      }
+      if (tid <= nb) fc.bptr[tid] = a.m.body_ptr[body0 + tid];
+      if (tid == NT - 1) {
+        const VarState& S = a.st[v];
+        fc.alpha = S.alpha;
+        fc.beta = S.beta;
+        fc.gamma_start = S.gamma_start;
+        fc.thr_rel = S.thr_rel;
+        fc.thr_abs2 = S.thr_abs2;
+        fc.iters = S.iters;
+        fc.inner_iters = S.inner_iters;
+        fc.buf = cur;
+        fc.k_max = a.prm->k_max;
+        fc.fixed = a.prm->fixed_bodies;
+        fc.seg0 = a.sc.var_seg0[v];
+        fc.seg1 = a.sc.var_seg1[v];
       }
       named_bar_sync(CONSUMER_BAR, NT);
       for (int t = t0; t < t1; ++t, ++q) {
@@ -413,6 +487,7 @@ __global__ void __launch_bounds__(NTC, sizeof(T) == 4 ? 2 : 1) k_cg(CGArgs<T> a,
         const long long tb = base + (long long)ij.y * P + ij.x;
         // pass 1: own strip and the halo ring -> p tile, effective tags
         T rn4[STRIP], pn4[STRIP], xn4[STRIP];
+        int bs4[STRIP];                           // slot of a BODY node in body_nodes
         uint8_t tg4[STRIP];
         if (ok) {
 #pragma unroll
@@ -423,14 +498,20 @@ __global__ void __launch_bounds__(NTC, sizeof(T) == 4 ? 2 : 1) k_cg(CGArgs<T> a,
             const uint8_t tg = in ? Tg[lj * L::TBW + li + 15] : K_INACT;
             const int kind = tg & KIND_MASK;
             T rn = T(0), pn = T(0), xn = T(0);
+            int bs = -1;
             if (kind == K_FREE) {
               const State4<T> o = staged_state<T>(Ss, li, lj);
               rn = next_r(o.r, o.q, alpha);
               xn = next_x(o.x, o.p, alpha);
               pn = next_p(rn, o.p, beta);
             } else if (kind == K_BODY) {
-              pn = s_pb[a.m.bid[tb + (long long)(row_lo + u) * P + col]];
+              const int e = slot_of(staged_state<T>(Ss, li, lj).x);
+              if (e >= fc.bptr[0] && e < fc.bptr[nb]) {
+                bs = e;
+                pn = s_pb[body_of_slot(fc.bptr, nb, e)];
+              }
             }
+            bs4[u] = bs;
             pt[lj * W + li] = pn;
             tt[lj * W + li] = tg;
             rn4[u] = rn; pn4[u] = pn; xn4[u] = xn; tg4[u] = tg;
@@ -451,7 +532,8 @@ __global__ void __launch_bounds__(NTC, sizeof(T) == 4 ? 2 : 1) k_cg(CGArgs<T> a,
                 const State4<T> o = staged_state<T>(Ss, li, lj);
                 hp = next_p(next_r(o.r, o.q, alpha), o.p, beta);
               } else if (hk == K_BODY) {
-                hp = s_pb[a.m.bid[tb + (long long)(lj - 1) * P + (li - 1)]];
+                const int e = slot_of(staged_state<T>(Ss, li, lj).x);
+                if (e >= fc.bptr[0] && e < fc.bptr[nb]) hp = s_pb[body_of_slot(fc.bptr, nb, e)];
               }
             }
             pt[lj * W + li] = hp;
@@ -498,11 +580,12 @@ __global__ void __launch_bounds__(NTC, sizeof(T) == 4 ? 2 : 1) k_cg(CGArgs<T> a,
               const T y = q4_row_nb<T>(nbh, cr[u + 1], cl[u + 1], cl[u], cr[u], Ks, col + 4, row_lo + u + 1, n, P,
                                        kplane<T>(a.m), plane, kr);
               State4<T> o;
-              o.x = xn4[u];
+              o.x = kind == K_BODY ? slot_bits(bs4[u], T(0)) : xn4[u];
               o.r = rn4[u];
               o.p = pn4[u];
               o.q = y;
-              s_new[n] = o;          // BODY nodes carry only q (x, r, p are zero there)
+              s_new[n] = o;          // BODY nodes: x = slot bits, r = 0, p = the body's p, q = row of A p
+              if (kind == K_BODY && bs4[u] >= 0) a.bq[bs4[u]] = (double)y;   // slot was range-checked
               if (kind == K_FREE) {
                 yq[u] = y;
                 rr[u] = rn4[u];
@@ -540,15 +623,12 @@ __global__ void __launch_bounds__(NTC, sizeof(T) == 4 ? 2 : 1) k_cg(CGArgs<T> a,
         for (int w = 0; w < NT / 32; ++w) sum += red[w][k];
         a.sc.partial[sg * 4 + k] = sum;
       }
-      __threadfence();
-      const int done = atomicAdd(&a.sc.counter[v], 1);
+      // release this CTA's stores (ordered before by the barrier), acquire the others'
+      const int done = atom_add_acq_rel_gpu(&a.sc.counter[v], 1);
       s_last = (done == seg_count(a.sc, v) - 1);
     }
     __syncthreads();
-    if (s_last) {
-      __threadfence();
-      finalize_cg<T>(a, v, scratch, sh_qb);
-    }
+    if (s_last) finalize_cg<T, NTC>(a, v, nb, body0, fc, scratch, sh_qb, reinterpret_cast<double*>(smem), L::off_bar / 8);
     __syncthreads();
   }
 }
@@ -688,15 +768,11 @@ __global__ void __launch_bounds__(NT) k_resid(ResidArgs<T> a) {
       double s = 0.0;
       for (int w = 0; w < NT / 32; ++w) s += red[w];
       a.sc.partial[sg * 4] = s;
-      __threadfence();
-      const int done = atomicAdd(&a.sc.counter[v], 1);
+      const int done = atom_add_acq_rel_gpu(&a.sc.counter[v], 1);
       s_last = (done == seg_count(a.sc, v) - 1);
     }
     __syncthreads();
-    if (s_last) {
-      __threadfence();
-      finalize_resid<T>(a, v, scratch, sh_rb);
-    }
+    if (s_last) finalize_resid<T>(a, v, scratch, sh_rb);
     __syncthreads();
   }
 }
@@ -718,6 +794,17 @@ __global__ void k_fold(const DevVariant* var, const int* tile_var, const int2* t
   State4<T>* s = sbuf[st[v].buf];
   x64[n] = x64[n] + (double)s[n].x;
   s[n].x = T(0);
+}
+
+// Seed the slot bits into the x field of every BODY node's record in both ping-pong
+// buffers (the fused CG step carries them forward from then on).
+template <typename T>
+__global__ void k_seed_slots(const long long* body_nodes, int n_slots, State4<T>* s0, State4<T>* s1) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n_slots) return;
+  const long long n = body_nodes[e];
+  s0[n].x = slot_bits(e, T(0));
+  s1[n].x = slot_bits(e, T(0));
 }
 
 // ---------------------------------------------------------------- init / export
@@ -958,7 +1045,8 @@ static CgConfig& cg_config(Batch& b, int precision, int ns) {
   std::vector<uint8_t> gen(b.Tcg);
   PF_CUDA(cudaMemcpy(gen.data(), b.tile_cg_gen, b.Tcg, cudaMemcpyDeviceToHost));
   std::vector<double> cost(b.Tcg);
-  const double gw = precision == PF_FP64 ? 1.4 : 1.6;
+  double gw = precision == PF_FP64 ? 1.4 : 2.15;
+  if (const char* e = std::getenv("PFQ4_GEN_WEIGHT")) gw = std::max(1.0, std::atof(e));
   for (long long k = 0; k < b.Tcg; ++k) cost[k] = gen[k] ? gw : 1.0;
   c.sc = build_sched(b, tc, c.G, &cost);
   c.sc.tile_ij = b.tile_cg_ij;
@@ -1101,6 +1189,7 @@ static void fill_cg_args(Batch& b, CGArgs<T>& a, State4<T>* const st[2], T* sb, 
   a.s[0] = st[0];
   a.s[1] = st[1];
   a.sb = sb;
+  a.bq = b.bq;
   a.B = std::max(1, b.B);
   a.n_done = b.n_done;
 }
@@ -1242,6 +1331,12 @@ pf_status solve_core(Batch& b, double U, const pf_solve_opts& o, double* dev_psi
     if (prec == PF_FP64) PF_CUDA(cudaMemsetAsync(b.st64[k], 0, b.Vtot * sizeof(State4<double>), s));
     else PF_CUDA(cudaMemsetAsync(b.st32[k], 0, b.Vtot * sizeof(State4<float>), s));
   }
+  const int n_slots = b.h_body_ptr.empty() ? 0 : b.h_body_ptr[b.B];
+  if (n_slots > 0) {
+    const unsigned g = (unsigned)((n_slots + 255) / 256);
+    if (prec == PF_FP64) k_seed_slots<double><<<g, 256, 0, s>>>(b.body_nodes, n_slots, b.st64[0], b.st64[1]);
+    else k_seed_slots<float><<<g, 256, 0, s>>>(b.body_nodes, n_slots, b.st32[0], b.st32[1]);
+  }
   k_init<<<(unsigned)b.T, dim3(TX, TY), 0, s>>>(b.d_var, b.tile_var, b.tile_ij, b.tag, b.X, b.Vtot, U,
                                                 b.Uv_active ? b.d_Uv : nullptr, warm, b.x64, b.w64);
   PF_CUDA(cudaGetLastError());
@@ -1279,7 +1374,7 @@ pf_status solve_core(Batch& b, double U, const pf_solve_opts& o, double* dev_psi
     if (hdone[0] >= b.nv) break;
   }
   PF_CUDA(cudaEventRecord(b.ev[4], s));
-  b.launches += 1 + launches + (long long)rlaunches * 2;
+  b.launches += 1 + (n_slots > 0 ? 1 : 0) + launches + (long long)rlaunches * 2;
   std::vector<VarState> fin(b.nv);
   PF_CUDA(cudaMemcpyAsync(fin.data(), b.state, b.nv * sizeof(VarState), cudaMemcpyDeviceToHost, s));
   PF_CUDA(cudaStreamSynchronize(s));
