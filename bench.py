@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--cpu-iters", type=int, default=60, help="oracle CG iterations in the CPU sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--tune", dest="tune", action="store_true", default=True,
+                    help="re-balance the persistent CG schedule from timed launches (default)")
+    ap.add_argument("--no-tune", dest="tune", action="store_false")
     return ap.parse_args()
 
 
@@ -208,7 +211,8 @@ def run_ours(args, rank, world, local):
 
     def step(host_out=None):
         g = api.batch_build(cs)
-        res = api.psi_solve(g, U=1.0, tol=args.tol, precision=prec, inner_tol=args.inner_tol)
+        res = api.psi_solve(g, U=1.0, tol=args.tol, precision=prec, inner_tol=args.inner_tol,
+                            tune_schedule=args.tune)
         cps = [api.copfi(g, v, 3, 4, 1.0) for v in range(len(cs))]
         if host_out is not None:
             host_out.copy_(res.psi, non_blocking=True)

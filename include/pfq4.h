@@ -92,6 +92,12 @@ typedef struct pf_solve_opts {
     double inner_tol;      /* PF_MIXED: relative residual reduction of each inner FP32 solve */
     int chunk;             /* CG iterations per captured graph launch (0 = automatic) */
     int warm_start;        /* 1: start from the previous solution held by the handle */
+    int tune_schedule;     /* 1: on the first such solve of the handle, run a few CG iterations
+                              as timed launches and move the persistent kernel's tile ranges so
+                              that every CTA's measured time evens out (kept for later solves).
+                              This changes the order in which the dot products are summed:
+                              results agree with an untuned solve to rounding, not bit for bit.
+                              0: schedule from the static per-tile cost estimate (deterministic). */
 } pf_solve_opts;
 
 typedef struct pf_solve_info {

@@ -32,7 +32,8 @@ class pf_mesh_stats(C.Structure):
 
 class pf_solve_opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("k_max", C.c_longlong), ("precision", C.c_int),
-                ("inner_tol", C.c_double), ("chunk", C.c_int), ("warm_start", C.c_int)]
+                ("inner_tol", C.c_double), ("chunk", C.c_int), ("warm_start", C.c_int),
+                ("tune_schedule", C.c_int)]
 
 
 class pf_solve_info(C.Structure):

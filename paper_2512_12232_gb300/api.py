@@ -197,11 +197,12 @@ def apply(mesh: Mesh, p: torch.Tensor, precision=PF_FP64):
 
 
 def psi_solve(mesh: Mesh, U=1.0, tol=1e-8, precision=PF_MIXED, k_max=10_000_000, inner_tol=1e-4,
-              chunk=0, warm_start=False, want_psi=True, raise_on_failure=True, method="mpc") -> SolveResult:
+              chunk=0, warm_start=False, want_psi=True, raise_on_failure=True, method="mpc",
+              tune_schedule=False) -> SolveResult:
     """Solve for psi.  method="mpc": CG on the multi-point-constraint system;
     method="schur": body values through the Schur complement (N_b + 1 fixed-body solves)."""
     opts = L.pf_solve_opts(float(tol), int(k_max), int(precision), float(inner_tol), int(chunk),
-                           int(bool(warm_start)))
+                           int(bool(warm_start)), int(bool(tune_schedule)))
     total = int(mesh.node_offsets[-1])
     psi = torch.empty(total, dtype=torch.float64, device="cuda") if want_psi else None
     nb = mesh.body_offsets[-1]

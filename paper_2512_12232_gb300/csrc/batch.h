@@ -30,6 +30,14 @@ struct CgConfig {                  // persistent grid + schedule of one fused-CG
   int G = 0;
   int smem = 0;
   Sched sc{};
+  // schedule: host copies and the device arrays it is written to in place
+  std::vector<int> tile_var;         // [tiles]
+  std::vector<double> tile_cost;     // [tiles] relative cost estimate (refined by timed launches)
+  std::vector<int> cut;              // [G+1] first tile of each CTA
+  int *d_cta_seg = nullptr, *d_seg_var = nullptr, *d_seg_t0 = nullptr, *d_seg_t1 = nullptr;
+  int *d_var_seg0 = nullptr, *d_var_seg1 = nullptr;
+  unsigned long long* d_cta_ns = nullptr;   // [G] tile-phase time per CTA of a timed launch
+  int tune_rounds = 0;               // timing-driven re-balances done
 };
 
 struct Batch;
@@ -75,9 +83,11 @@ struct Batch {
   long long Tcg = 0;
   int2* tile_cg_ij = nullptr;
   int* tile_cg_var = nullptr;
-  uint8_t* tile_cg_gen = nullptr;    // 1 if a cell used by the tile has stored coefficients
+  uint8_t* tile_cg_gen = nullptr;    // bit 0 / bit 1: a cell used by the tile needs stored FP64 / FP32 coefficients
+  int* tile_cg_act = nullptr;        // nodes of the tile with an operator row (FREE or BODY)
   CgConfig cg_cfg[2][3];             // [precision][stages - 2]
   int cg_stages = 2;
+  bool cg_tune = false;              // re-balance the fused-CG schedule from timed launches
   int nsm = 0;
   long long Rtot = 0;                // rows of the batch's 2-D node arrays (Vtot / P)
   int P = 0;                         // common row pitch

@@ -36,6 +36,8 @@ constexpr uint8_t CELL_ACTIVE = 4;   // cell (i, j) whose corner 0 is this node 
 constexpr uint8_t CELL_GENERAL = 8;  // ... and has a displaced corner: stored K_e is used
 constexpr uint8_t DISPLACED = 16;    // node moved by the mesh generator (d != 0)
 constexpr uint8_t RING = 32;         // node on the outer boundary of the box
+constexpr uint8_t CELL_GEN32 = 64;   // general cell whose FP32 coefficients differ from the FP32
+                                     // rectangle constants (the FP32 operator needs stored K_e)
 
 // solver phases (per variant)
 constexpr int PH_CG = 0, PH_RESID = 1, PH_DONE = 2;
@@ -93,6 +95,7 @@ struct Sched {                 // persistent tile schedule
   double* partial;             // [S][4]
   int* counter;                // [nv] finished segments in the current launch
   int n_cta;
+  unsigned long long* cta_ns;  // [G] tile-phase time of each CTA (timed fused-CG launches), else null
 };
 
 struct MeshDev {

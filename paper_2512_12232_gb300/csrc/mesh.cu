@@ -228,7 +228,9 @@ __global__ void k_stiffness(const DevVariant* var, const int* tile_var, const in
         K32i[6 * n + m] = (float)k6[m];
       }
       if (disp) {
-        tag[n] = t | CELL_GENERAL;
+        bool differs32 = false;
+        for (int m = 0; m < 6; ++m) differs32 |= (float)k6[m] != V.kr32[m];
+        tag[n] = t | CELL_GENERAL | (differs32 ? CELL_GEN32 : 0);
         atomicAdd((unsigned long long*)&cnt[4], 1ull);
       }
       atomic_min_double(&dmin, dm);
@@ -239,21 +241,42 @@ __global__ void k_stiffness(const DevVariant* var, const int* tile_var, const in
   if (tid == 0 && dmin < 1e300) atomic_min_double(&detmin[c.v], dmin);
 }
 
+__device__ int block_exscan(int x, int* total, int* sh /* >= 9 */);
+
 // 5b. per fused-CG tile: does any cell used by the tile (cells i0-1 .. i0+CTX-1,
-//     j0-1 .. j0+CTY-1 of its variant) carry stored coefficients?
+//     j0-1 .. j0+CTY-1 of its variant) carry stored coefficients (bit 0: FP64 operator,
+//     bit 1: FP32 operator), and how many of its nodes carry an operator row (FREE or
+//     BODY)?  Both feed the cost estimate of the fused-CG schedule.
 __global__ void k_tile_general(const DevVariant* var, const int* tile_var, const int2* tile_ij, const uint8_t* tag,
-                               uint8_t* gen) {
+                               uint8_t* gen, int* act) {
+  __shared__ int sh[NT / 32 + 1];
   const long long t = blockIdx.x;
   const DevVariant& V = var[tile_var[t]];
   const int2 ij = tile_ij[t];
-  int any = 0;
+  int g64 = 0, g32 = 0, na = 0;
   for (int q = linear_tid(); q < (CTX + 1) * (CTY + 1); q += NT) {
     const int i = ij.x - 1 + q % (CTX + 1), j = ij.y - 1 + q / (CTX + 1);
-    if (i >= 0 && j >= 0 && i < V.nx && j < V.ny)
-      any |= (tag[V.base + (long long)j * V.P + i] & CELL_GENERAL) != 0;
+    if (i >= 0 && j >= 0 && i < V.nx && j < V.ny) {
+      const uint8_t c = tag[V.base + (long long)j * V.P + i];
+      g64 |= (c & CELL_GENERAL) != 0;
+      g32 |= (c & CELL_GEN32) != 0;
+    }
   }
-  any = __syncthreads_or(any);
-  if (linear_tid() == 0) gen[t] = (uint8_t)any;
+  for (int q = linear_tid(); q < CTX * CTY; q += NT) {
+    const int i = ij.x + q % CTX, j = ij.y + q / CTX;
+    if (i <= V.nx && j <= V.ny) {
+      const int k = tag[V.base + (long long)j * V.P + i] & KIND_MASK;
+      na += (k == K_FREE || k == K_BODY);
+    }
+  }
+  g64 = __syncthreads_or(g64);
+  g32 = __syncthreads_or(g32);
+  int tot;
+  block_exscan(na, &tot, sh);
+  if (linear_tid() == 0) {
+    gen[t] = (uint8_t)(g64 | (g32 << 1));
+    act[t] = tot;
+  }
 }
 
 // Block-wide exclusive scan of one int per thread (256 threads, 1-D linear id).
@@ -514,6 +537,7 @@ void build_batch(Batch& b, const pf_grid* grids, const int* body_offsets, const 
   b.tile_cg_ij = upload(b, cij);
   b.tile_cg_var = upload(b, cvar);
   b.tile_cg_gen = (uint8_t*)dev_alloc(b, std::max<long long>(1, b.Tcg));
+  b.tile_cg_act = (int*)dev_alloc(b, std::max<long long>(1, b.Tcg) * sizeof(int));
   b.tag = (uint8_t*)dev_alloc(b, Vt);
   b.bid = (int*)dev_alloc(b, Vt * sizeof(int));
   b.X = (double*)dev_alloc(b, 2 * Vt * sizeof(double));
@@ -554,7 +578,8 @@ void build_batch(Batch& b, const pf_grid* grids, const int* body_offsets, const 
   k_finalize<<<grid, blk, 0, s>>>(b.d_var, b.tile_var, b.tile_ij, dA, b.tag, b.X, Vt);
   k_stiffness<<<grid, blk, 0, s>>>(b.d_var, b.tile_var, b.tile_ij, b.tag, b.X, Vt, b.K64, b.K32, b.K32i, b.d_stats_i,
                                    b.d_detmin);
-  k_tile_general<<<(unsigned)b.Tcg, blk, 0, s>>>(b.d_var, b.tile_cg_var, b.tile_cg_ij, b.tag, b.tile_cg_gen);
+  k_tile_general<<<(unsigned)b.Tcg, blk, 0, s>>>(b.d_var, b.tile_cg_var, b.tile_cg_ij, b.tag, b.tile_cg_gen,
+                                                 b.tile_cg_act);
   PF_CUDA(cudaGetLastError());
 
   // ---- body node and edge lists

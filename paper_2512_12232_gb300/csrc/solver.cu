@@ -112,6 +112,10 @@ __device__ __forceinline__ double warp_sum(double x) {
   return x;
 }
 
+// Shared-memory doubles the finaliser stages per pass (fixed, so that the summation
+// order does not depend on the pipeline depth).
+constexpr int FIN_CAP = 8192;
+
 // What the end of an iteration needs from global memory, loaded by the consumer warps
 // at the start of each segment so that the serial finaliser issues no dependent loads.
 template <typename T>
@@ -120,7 +124,7 @@ struct FinCache {
   int bptr[MAXB + 1];        // body_ptr of the variant's bodies (global slots)
   double alpha, beta, gamma_start, thr_rel, thr_abs2;
   long long iters, inner_iters, k_max;
-  int seg0, seg1, buf, fixed;
+  int seg0, seg1, buf, fixed; // seg0/seg1: the variant's segments
 };
 
 // A BODY node has no x, r or p of its own (its value is the body's unknown), so the x
@@ -147,49 +151,60 @@ __device__ __forceinline__ int body_of_slot(const int* bptr, int nb, int e) {
 // CTA); gbuf is shared memory of gcap >= 4 * MAXB doubles that no copy is writing.
 template <typename T, int NTHR>
 __device__ __noinline__ void finalize_cg(const CGArgs<T>& a, int v, int nb, int body0, const FinCache<T>& fc, double* scratch,
-                            double* sh_qb, double* gbuf, int gcap) {
+                            double* sh_qb, double* gbuf) {
   VarState* S = &a.st[v];
   const int tid = linear_tid(), warp = tid >> 5, lane = tid & 31;
   constexpr int NW = NTHR / 32;
+  static_assert(NW >= 5, "finaliser needs warps 0-3 for the dots and at least one body warp");
   constexpr int GB = 8;                      // independent loads in flight per thread
+  constexpr int HALF = FIN_CAP / 2;          // doubles per staging region
   double* d = scratch;                       // d[0..3]: the four dots over FREE nodes
-  // warps 0-3: dot k = warp over the variant's segment partials (fixed order)
-  if (warp < 4) {
-    double s = 0.0;
-    for (int sg = fc.seg0 + lane; sg < fc.seg1; sg += 32) s += __ldcg(&a.sc.partial[sg * 4 + warp]);
-    s = warp_sum(s);
-    if (lane == 0) d[warp] = s;
-  }
-  // collapsed body rows of q: every thread fetches body-node q values (stored by slot
-  // during the iteration) into shared memory, then one warp per body sums its entries
-  // in a fixed order, chunk by chunk
+  double* gp = gbuf;                         // staged segment partials [HALF]
+  double* gq = gbuf + HALF;                  // staged body-node rows of A p [HALF]
+  // Both sums are staged through shared memory in passes of fixed size (independent
+  // loads, one round trip per pass) and added in a fixed order: warps 0-3 take dot k =
+  // warp over the variant's segment partials in segment order; warps 4.. take the
+  // collapsed body rows of A p (stored by slot during the iteration), one warp per body.
+  const int nparts = (fc.seg1 - fc.seg0) * 4;
+  const int e0 = fc.bptr[0], nq = fc.bptr[nb] - e0;
   for (int k = tid; k < nb; k += NTHR) sh_qb[k] = 0.0;
-  const int e0 = fc.bptr[0], e1 = fc.bptr[nb];
-  for (int c0 = e0; c0 < e1; c0 += gcap) {
-    const int c1 = min(e1, c0 + gcap);
-    for (int b = c0; b < c1; b += GB * NTHR) {
-      double val[GB];
+  double dsum = 0.0;
+  for (int off = 0; off < max(nparts, nq); off += HALF) {
+    const int np = min(HALF, nparts - off), nqq = min(HALF, nq - off);
+    for (int b = 0; b < max(np, nqq); b += GB * NTHR) {
+      double vp[GB], vq[GB];
 #pragma unroll
       for (int u = 0; u < GB; ++u) {
         const int e = b + u * NTHR + tid;
-        val[u] = e < c1 ? __ldcg(&a.bq[e]) : 0.0;
+        vp[u] = e < np ? __ldcg(&a.sc.partial[fc.seg0 * 4 + off + e]) : 0.0;
+        vq[u] = e < nqq ? __ldcg(&a.bq[e0 + off + e]) : 0.0;
       }
 #pragma unroll
       for (int u = 0; u < GB; ++u) {
         const int e = b + u * NTHR + tid;
-        if (e < c1) gbuf[e - c0] = val[u];
+        if (e < np) gp[e] = vp[u];
+        if (e < nqq) gq[e] = vq[u];
       }
     }
     __syncthreads();
-    for (int k = warp; k < nb; k += NW) {
-      const int b0 = max(c0, fc.bptr[k]), b1 = min(c1, fc.bptr[k + 1]);
-      double s = 0.0;
-      for (int e = b0 + lane; e < b1; e += 32) s += gbuf[e - c0];
-      s = warp_sum(s);
-      if (lane == 0) sh_qb[k] += s;
+    if (warp < 4) {
+      for (int j = lane; j < np / 4; j += 32) dsum += gp[j * 4 + warp];
+    } else {
+      for (int k = warp - 4; k < nb; k += NW - 4) {
+        const int b0 = max(off, fc.bptr[k] - e0), b1 = min(off + nqq, fc.bptr[k + 1] - e0);
+        double sq = 0.0;
+        for (int e = b0 + lane; e < b1; e += 32) sq += gq[e - off];
+        sq = warp_sum(sq);
+        if (lane == 0) sh_qb[k] += sq;
+      }
     }
     __syncthreads();
   }
+  if (warp < 4) {
+    dsum = warp_sum(dsum);
+    if (lane == 0) d[warp] = dsum;
+  }
+  __syncthreads();
   // body unknowns, one thread per body; their dot contributions are added in body order
   double* contrib = gbuf;                    // [4][MAXB]
   const T alpha = (T)fc.alpha, beta = (T)fc.beta;
@@ -299,7 +314,8 @@ __device__ __forceinline__ T q4_row_nb(const T (&p)[3][3], uint8_t c0, uint8_t c
   const T pc = p[1][1];
   const T dE = p[1][2] - pc, dW = p[1][0] - pc, dN = p[2][1] - pc, dS = p[0][1] - pc;
   const T dNE = p[2][2] - pc, dNW = p[2][0] - pc, dSE = p[0][2] - pc, dSW = p[0][0] - pc;
-  constexpr uint8_t FLAGS = CELL_ACTIVE | CELL_GENERAL;
+  constexpr uint8_t GEN = sizeof(T) == 4 ? CELL_GEN32 : CELL_GENERAL;   // cells that need stored K_e
+  constexpr uint8_t FLAGS = CELL_ACTIVE | GEN;
   if ((c0 & FLAGS) == CELL_ACTIVE && (c1 & FLAGS) == CELL_ACTIVE && (c2 & FLAGS) == CELL_ACTIVE &&
       (c3 & FLAGS) == CELL_ACTIVE) {
     // four undisplaced rectangles: K23 = K01, K12 = K03, K13 = K02, so the row is
@@ -319,19 +335,19 @@ __device__ __forceinline__ T q4_row_nb(const T (&p)[3][3], uint8_t c0, uint8_t c
   T y = T(0);
   if (c0 & CELL_ACTIVE) {                         // node is corner 0 of cell (i, j)
     T k01 = kr[0], k02 = kr[1], k03 = kr[2];
-    if (c0 & CELL_GENERAL) { k01 = coef(0, krow, kcol, n); k02 = coef(1, krow, kcol, n); k03 = coef(2, krow, kcol, n); }
+    if (c0 & GEN) { k01 = coef(0, krow, kcol, n); k02 = coef(1, krow, kcol, n); k03 = coef(2, krow, kcol, n); }
     y += k01 * dE + k02 * dNE + k03 * dN;
   }
   if (c1 & CELL_ACTIVE) {                         // corner 1 of cell (i-1, j)
     T k01 = kr[0], k12 = kr[3], k13 = kr[4];
-    if (c1 & CELL_GENERAL) {
+    if (c1 & GEN) {
       k01 = coef(0, krow, kcol - 1, n - 1); k12 = coef(3, krow, kcol - 1, n - 1); k13 = coef(4, krow, kcol - 1, n - 1);
     }
     y += k01 * dW + k12 * dN + k13 * dNW;
   }
   if (c2 & CELL_ACTIVE) {                         // corner 2 of cell (i-1, j-1)
     T k02 = kr[1], k12 = kr[3], k23 = kr[5];
-    if (c2 & CELL_GENERAL) {
+    if (c2 & GEN) {
       const long long c = n - P - 1;
       k02 = coef(1, krow - 1, kcol - 1, c); k12 = coef(3, krow - 1, kcol - 1, c); k23 = coef(5, krow - 1, kcol - 1, c);
     }
@@ -339,7 +355,7 @@ __device__ __forceinline__ T q4_row_nb(const T (&p)[3][3], uint8_t c0, uint8_t c
   }
   if (c3 & CELL_ACTIVE) {                         // corner 3 of cell (i, j-1)
     T k03 = kr[2], k13 = kr[4], k23 = kr[5];
-    if (c3 & CELL_GENERAL) {
+    if (c3 & GEN) {
       const long long c = n - P;
       k03 = coef(2, krow - 1, kcol, c); k13 = coef(4, krow - 1, kcol, c); k23 = coef(5, krow - 1, kcol, c);
     }
@@ -385,6 +401,7 @@ __device__ __forceinline__ State4<T> staged_state(const State4<T>* Ss, int li, i
 template <typename T, int NS>
 __global__ void __launch_bounds__(NTC, sizeof(T) == 4 ? 2 : 1) k_cg(CGArgs<T> a, const __grid_constant__ CgMaps mp) {
   using L = CgSmem<T, NS>;
+  static_assert(L::off_bar >= FIN_CAP * 8, "the finaliser stages FIN_CAP doubles in the stage memory");
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ T s_pb[MAXB];
   __shared__ double red[NT / 32][4];
@@ -412,6 +429,8 @@ __global__ void __launch_bounds__(NTC, sizeof(T) == 4 ? 2 : 1) k_cg(CGArgs<T> a,
     s_issued = 0;
   }
   __syncthreads();
+  __shared__ unsigned long long s_t0;             // timed launches: start of this CTA's tile phase
+  if (a.sc.cta_ns && tid == 0) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(s_t0));
   int q = 0;                                      // tiles consumed (consumers) / issued (producer) so far
   for (int sg = a.sc.cta_seg[blockIdx.x]; sg < a.sc.cta_seg[blockIdx.x + 1]; ++sg) {
     const int v = a.sc.seg_var[sg];
@@ -436,7 +455,7 @@ __global__ void __launch_bounds__(NTC, sizeof(T) == 4 ? 2 : 1) k_cg(CGArgs<T> a,
           if (*(volatile int*)&s_abort) break;
           fence_proxy_async_smem();
           cg_issue<T>(mp, cur, smem + s * L::stage_bytes, &full[s], a.sc.tile_ij[t], row0, a.Rtot,
-                      a.tile_gen[t] != 0);
+                      (a.tile_gen[t] & (sizeof(T) == 4 ? 2 : 1)) != 0);
           s_issued = q + 1;
         }
       }
@@ -623,12 +642,17 @@ __global__ void __launch_bounds__(NTC, sizeof(T) == 4 ? 2 : 1) k_cg(CGArgs<T> a,
         for (int w = 0; w < NT / 32; ++w) sum += red[w][k];
         a.sc.partial[sg * 4 + k] = sum;
       }
+      if (a.sc.cta_ns && sg + 1 == a.sc.cta_seg[blockIdx.x + 1]) {
+        unsigned long long t_end;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_end));
+        a.sc.cta_ns[blockIdx.x] = t_end - s_t0;
+      }
       // release this CTA's stores (ordered before by the barrier), acquire the others'
       const int done = atom_add_acq_rel_gpu(&a.sc.counter[v], 1);
       s_last = (done == seg_count(a.sc, v) - 1);
     }
     __syncthreads();
-    if (s_last) finalize_cg<T, NTC>(a, v, nb, body0, fc, scratch, sh_qb, reinterpret_cast<double*>(smem), L::off_bar / 8);
+    if (s_last) finalize_cg<T, NTC>(a, v, nb, body0, fc, scratch, sh_qb, reinterpret_cast<double*>(smem));
     __syncthreads();
   }
 }
@@ -1025,7 +1049,65 @@ static const void* cg_func(int precision, int ns) {
   return ns == 4 ? cg_kernel<float, 4>() : ns == 3 ? cg_kernel<float, 3>() : cg_kernel<float, 2>();
 }
 
-// Persistent grid (occupancy x SMs) and tile schedule of one CG configuration, built once.
+// Cut points of the fused-CG schedule (contiguous tile ranges of equal estimated cost)
+// and the segments they make at variant boundaries, written to the configuration's
+// device arrays in place (graphs captured with these pointers stay valid).
+static void cg_sched_write(Batch& b, CgConfig& c) {
+  const int G = c.G, T = (int)c.tile_cost.size();
+  double total = 0.0;
+  for (double x : c.tile_cost) total += x;
+  c.cut.assign(G + 1, 0);
+  int k = 0;
+  double run = 0.0;
+  for (int g = 0; g <= G; ++g) {
+    const double target = total * g / G;
+    while (k < T && run + 0.5 * c.tile_cost[k] < target) run += c.tile_cost[k++];
+    c.cut[g] = (g == G) ? T : k;
+  }
+  std::vector<int> cta_seg(G + 1), seg_var, seg_t0, seg_t1;
+  for (int g = 0; g < G; ++g) {
+    cta_seg[g] = (int)seg_var.size();
+    for (int t = c.cut[g]; t < c.cut[g + 1]; ++t) {
+      const int v = c.tile_var[t];
+      if (t == c.cut[g] || c.tile_var[t - 1] != v) {
+        seg_var.push_back(v);
+        seg_t0.push_back(t);
+        seg_t1.push_back(t + 1);
+      } else {
+        seg_t1.back() = t + 1;
+      }
+    }
+  }
+  cta_seg[G] = (int)seg_var.size();
+  const int S = (int)seg_var.size();
+  if (S > G + b.nv) throw Error{PF_ECUDA, "internal: fused-CG schedule has too many segments"};
+  std::vector<int> vs0(b.nv, 0), vs1(b.nv, 0), seen(b.nv, 0);
+  for (int i = 0; i < S; ++i) {
+    const int v = seg_var[i];
+    if (!seen[v]) { vs0[v] = i; seen[v] = 1; }
+    vs1[v] = i + 1;
+  }
+  cudaStream_t s = b.stream;
+  PF_CUDA(cudaMemcpyAsync(c.d_cta_seg, cta_seg.data(), (G + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
+  if (S > 0) {
+    PF_CUDA(cudaMemcpyAsync(c.d_seg_var, seg_var.data(), S * sizeof(int), cudaMemcpyHostToDevice, s));
+    PF_CUDA(cudaMemcpyAsync(c.d_seg_t0, seg_t0.data(), S * sizeof(int), cudaMemcpyHostToDevice, s));
+    PF_CUDA(cudaMemcpyAsync(c.d_seg_t1, seg_t1.data(), S * sizeof(int), cudaMemcpyHostToDevice, s));
+  }
+  PF_CUDA(cudaMemcpyAsync(c.d_var_seg0, vs0.data(), b.nv * sizeof(int), cudaMemcpyHostToDevice, s));
+  PF_CUDA(cudaMemcpyAsync(c.d_var_seg1, vs1.data(), b.nv * sizeof(int), cudaMemcpyHostToDevice, s));
+  PF_CUDA(cudaStreamSynchronize(s));       // the host vectors go out of scope
+}
+
+// Re-balance rounds of the first tuned solve on a handle and launches timed per round
+// (the last launch of a round is the one measured).
+constexpr int CG_TUNE_ROUNDS = 2;
+constexpr int CG_TUNE_LAUNCHES = 2;
+
+// Persistent grid (occupancy x SMs) and tile schedule of one CG configuration.  The
+// first estimate of a tile's cost is a fit of measured per-CTA times of the
+// five-cylinder workload on GB300: a fixed part, a part per node with an operator row
+// and, for tiles that need stored coefficients, the extra coefficient boxes.
 static CgConfig& cg_config(Batch& b, int precision, int ns) {
   CgConfig& c = b.cg_cfg[precision][ns - 2];
   if (c.ready) return c;
@@ -1034,25 +1116,67 @@ static CgConfig& cg_config(Batch& b, int precision, int ns) {
   PF_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   int occ = 0;
   PF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, f, NTC, smem));
-  std::vector<int> tc(b.Tcg);
+  const long long T = b.Tcg;
+  std::vector<uint8_t> gen(std::max<long long>(1, T));
+  std::vector<int> act(std::max<long long>(1, T));
+  PF_CUDA(cudaMemcpy(gen.data(), b.tile_cg_gen, T, cudaMemcpyDeviceToHost));
+  PF_CUDA(cudaMemcpy(act.data(), b.tile_cg_act, T * sizeof(int), cudaMemcpyDeviceToHost));
+  const int gbit = precision == PF_FP64 ? 1 : 2;
+  const double w_gen = precision == PF_FP64 ? 0.6 : 1.47;
+  c.tile_var.assign(T, 0);
+  c.tile_cost.assign(T, 0.0);
   long long t = 0;
   for (int v = 0; v < b.nv; ++v) {
     const long long n = (long long)((b.hv[v].g.nx + 1 + CTX - 1) / CTX) * ((b.hv[v].g.ny + 1 + CTY - 1) / CTY);
-    for (long long k = 0; k < n; ++k) tc[t++] = v;
+    for (long long k = 0; k < n; ++k, ++t) {
+      c.tile_var[t] = v;
+      c.tile_cost[t] = 1.46 + 0.00042 * act[t] + ((gen[t] & gbit) ? w_gen : 0.0);
+    }
   }
-  c.G = (int)std::min<long long>((long long)b.nsm * std::max(1, occ), b.Tcg);
-  // relative cost of a tile with stored coefficients (extra TMA planes + general rows)
-  std::vector<uint8_t> gen(b.Tcg);
-  PF_CUDA(cudaMemcpy(gen.data(), b.tile_cg_gen, b.Tcg, cudaMemcpyDeviceToHost));
-  std::vector<double> cost(b.Tcg);
-  double gw = precision == PF_FP64 ? 1.4 : 2.15;
-  if (const char* e = std::getenv("PFQ4_GEN_WEIGHT")) gw = std::max(1.0, std::atof(e));
-  for (long long k = 0; k < b.Tcg; ++k) cost[k] = gen[k] ? gw : 1.0;
-  c.sc = build_sched(b, tc, c.G, &cost);
-  c.sc.tile_ij = b.tile_cg_ij;
+  c.G = (int)std::max<long long>(1, std::min<long long>((long long)b.nsm * std::max(1, occ), T));
+  const int G = c.G, Smax = G + b.nv;
+  c.d_cta_seg = (int*)dev_alloc(b, (G + 1) * sizeof(int));
+  c.d_seg_var = (int*)dev_alloc(b, Smax * sizeof(int));
+  c.d_seg_t0 = (int*)dev_alloc(b, Smax * sizeof(int));
+  c.d_seg_t1 = (int*)dev_alloc(b, Smax * sizeof(int));
+  c.d_var_seg0 = (int*)dev_alloc(b, b.nv * sizeof(int));
+  c.d_var_seg1 = (int*)dev_alloc(b, b.nv * sizeof(int));
+  c.d_cta_ns = (unsigned long long*)dev_alloc(b, G * sizeof(unsigned long long));
+  int* counter = (int*)dev_alloc(b, b.nv * sizeof(int));
+  PF_CUDA(cudaMemset(counter, 0, b.nv * sizeof(int)));
+  Sched sc{};
+  sc.cta_seg = c.d_cta_seg;
+  sc.seg_var = c.d_seg_var;
+  sc.seg_t0 = c.d_seg_t0;
+  sc.seg_t1 = c.d_seg_t1;
+  sc.var_seg0 = c.d_var_seg0;
+  sc.var_seg1 = c.d_var_seg1;
+  sc.counter = counter;
+  sc.partial = (double*)dev_alloc(b, (size_t)Smax * 4 * sizeof(double));
+  sc.n_cta = G;
+  sc.tile_ij = b.tile_cg_ij;
+  sc.cta_ns = nullptr;
+  c.sc = sc;
+  cg_sched_write(b, c);
   c.smem = smem;
+  c.tune_rounds = 0;
   c.ready = true;
   return c;
+}
+
+// Re-balance from the measured tile-phase time of every CTA: the cost of each tile in
+// CTA g's range is scaled by (time of g) / (estimated cost of g), then the cut points are
+// recomputed.  This moves segment boundaries, so the dot products are summed in another
+// order: results agree with an untuned solve to rounding, not bit for bit.
+static void cg_rebalance(Batch& b, CgConfig& c, const std::vector<unsigned long long>& ns) {
+  for (int g = 0; g < c.G; ++g) {
+    double est = 0.0;
+    for (int t = c.cut[g]; t < c.cut[g + 1]; ++t) est += c.tile_cost[t];
+    if (est <= 0.0 || ns[g] == 0) continue;
+    const double f = (double)ns[g] * 1e-3 / est;     // microseconds per unit of estimate
+    for (int t = c.cut[g]; t < c.cut[g + 1]; ++t) c.tile_cost[t] *= f;
+  }
+  cg_sched_write(b, c);
 }
 
 static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
@@ -1213,14 +1337,17 @@ static void fill_resid_args(Batch& b, ResidArgs<T>& a, State4<T>* const st[2], T
   a.n_done = b.n_done;
 }
 
-// the k_cg launches of one chunk (captured once as a graph)
-static void launch_cg_chunk(Batch& b, int precision, int chunk, cudaStream_t s) {
+// the k_cg launches of one chunk (captured once as a graph); timed launches record
+// every CTA's tile-phase time for the schedule re-balance
+static void launch_cg_chunk(Batch& b, int precision, int chunk, cudaStream_t s, bool timed = false) {
   const dim3 blk(TX, NTC / TX);
   const int ns = b.cg_stages;
   CgConfig& c = cg_config(b, precision, ns);
+  Sched sc = c.sc;
+  if (timed) sc.cta_ns = c.d_cta_ns;
   if (precision == PF_FP64) {
     CGArgs<double> a;
-    fill_cg_args<double>(b, a, b.st64, b.sb64, c.sc);
+    fill_cg_args<double>(b, a, b.st64, b.sb64, sc);
     for (int k = 0; k < chunk; ++k) {
       if (ns == 4) k_cg<double, 4><<<c.G, blk, c.smem, s>>>(a, b.maps[0]);
       else if (ns == 3) k_cg<double, 3><<<c.G, blk, c.smem, s>>>(a, b.maps[0]);
@@ -1228,7 +1355,7 @@ static void launch_cg_chunk(Batch& b, int precision, int chunk, cudaStream_t s) 
     }
   } else {
     CGArgs<float> a;
-    fill_cg_args<float>(b, a, b.st32, b.sb32, c.sc);
+    fill_cg_args<float>(b, a, b.st32, b.sb32, sc);
     for (int k = 0; k < chunk; ++k) {
       if (ns == 4) k_cg<float, 4><<<c.G, blk, c.smem, s>>>(a, b.maps[1]);
       else if (ns == 3) k_cg<float, 3><<<c.G, blk, c.smem, s>>>(a, b.maps[1]);
@@ -1302,6 +1429,8 @@ pf_status solve_core(Batch& b, double U, const pf_solve_opts& o, double* dev_psi
     const char* e = getenv("PFQ4_CG_STAGES");
     const int ns = e ? atoi(e) : 2;
     b.cg_stages = (ns >= 2 && ns <= 4) ? ns : 2;
+    const char* tu = getenv("PFQ4_CG_TUNE");   // overrides the option when set
+    b.cg_tune = tu ? atoi(tu) != 0 : o.tune_schedule != 0;
   }
   cudaStream_t s = b.stream;
   SolveParams sp{};
@@ -1353,6 +1482,28 @@ pf_status solve_core(Batch& b, double U, const pf_solve_opts& o, double* dev_psi
   int* hdone = b.h_poll;
   double cg_ms = 0, res_ms = 0;
   long long launches = 0, rlaunches = 1;
+  // Optional timing-driven re-balance of the schedule on the first tuned solve of the
+  // handle: a few of this solve's CG iterations run as timed launches, then the cut
+  // points move so that every CTA's measured tile time evens out.
+  CgConfig& cc = cg_config(b, prec, b.cg_stages);
+  if (b.cg_tune && o.k_max > 0 && (long long)cc.tile_cost.size() >= 2LL * cc.G) {
+    for (; cc.tune_rounds < CG_TUNE_ROUNDS; ++cc.tune_rounds) {
+      PF_CUDA(cudaMemsetAsync(cc.d_cta_ns, 0, cc.G * sizeof(unsigned long long), s));
+      PF_CUDA(cudaEventRecord(b.ev[0], s));
+      launch_cg_chunk(b, prec, CG_TUNE_LAUNCHES, s, true);
+      PF_CUDA(cudaEventRecord(b.ev[1], s));
+      std::vector<unsigned long long> tns(cc.G);
+      PF_CUDA(cudaMemcpyAsync(tns.data(), cc.d_cta_ns, cc.G * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+      PF_CUDA(cudaMemcpyAsync(hdone, b.n_done, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+      PF_CUDA(cudaStreamSynchronize(s));
+      float ms = 0;
+      PF_CUDA(cudaEventElapsedTime(&ms, b.ev[0], b.ev[1]));
+      cg_ms += ms;
+      launches += CG_TUNE_LAUNCHES;
+      if (hdone[1]) throw Error{PF_ETIMEOUT, "a bounded wait in the CG kernel gave up (TMA tile not delivered)"};
+      cg_rebalance(b, cc, tns);
+    }
+  }
   // k_max == 0 (internal use): only the initial residual, which measures ||b||
   const long long max_chunks = o.k_max == 0 ? 0 : o.k_max / chunk + 1000;
   for (long long c = 0; c < max_chunks; ++c) {
