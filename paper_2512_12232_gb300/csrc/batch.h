@@ -34,6 +34,8 @@ struct CgConfig {                  // persistent grid + schedule of one fused-CG
   std::vector<int> tile_var;         // [tiles]
   std::vector<double> tile_cost;     // [tiles] relative cost estimate (refined by timed launches)
   std::vector<int> cut;              // [G+1] first tile of each CTA
+  std::vector<char> active;          // [nv] variants the cut points were balanced over
+  std::vector<int> h_cta_seg, h_seg_var, h_seg_t0, h_seg_t1, h_vs0, h_vs1;   // host copies of the arrays
   int *d_cta_seg = nullptr, *d_seg_var = nullptr, *d_seg_t0 = nullptr, *d_seg_t1 = nullptr;
   int *d_var_seg0 = nullptr, *d_var_seg1 = nullptr;
   unsigned long long* d_cta_ns = nullptr;   // [G] tile-phase time per CTA of a timed launch
@@ -142,11 +144,13 @@ struct Batch {
   cudaStream_t graph_stream[2] = {nullptr, nullptr};
   int graph_chunk[2] = {0, 0};
   int graph_stages[2] = {0, 0};
-  cudaEvent_t ev[6] = {};
+  static constexpr int N_EV = 12;    // 0-5: solve-level timing, 6-11: two chunk slots x 3
+  cudaEvent_t ev[N_EV] = {};
   pf_timing timing{};
   double cg_bytes_per_node[2] = {0, 0};
 
-  int* h_poll = nullptr;             // pinned host word for the convergence poll
+  int* h_poll = nullptr;             // pinned [2 slots][2]: finished variants, bounded-wait flag
+  VarState* h_vs = nullptr;          // pinned [2 slots][nv]: variant states after each chunk
   long long launches = 0;            // kernel launches issued by this handle
 
   std::vector<std::pair<void*, size_t>> allocs;

@@ -159,9 +159,10 @@ void pf_batch_destroy(pf_batch* h) {
   if (!b) return;
   for (int k = 0; k < 2; ++k)
     if (b->graph[k]) cudaGraphExecDestroy(b->graph[k]);
-  for (int k = 0; k < 6; ++k)
+  for (int k = 0; k < Batch::N_EV; ++k)
     if (b->ev[k]) cudaEventDestroy(b->ev[k]);
   if (b->h_poll) cudaFreeHost(b->h_poll);
+  if (b->h_vs) cudaFreeHost(b->h_vs);
   dev_free_all(*b);
   delete b;
 }

@@ -74,9 +74,10 @@ struct BatchGuard {
     if (p) {
       for (int k = 0; k < 2; ++k)
         if (p->graph[k]) cudaGraphExecDestroy(p->graph[k]);
-      for (int k = 0; k < 6; ++k)
+      for (int k = 0; k < Batch::N_EV; ++k)
         if (p->ev[k]) cudaEventDestroy(p->ev[k]);
       if (p->h_poll) cudaFreeHost(p->h_poll);
+      if (p->h_vs) cudaFreeHost(p->h_vs);
       dev_free_all(*p);
       delete p;
     }

@@ -802,22 +802,26 @@ __global__ void __launch_bounds__(NT) k_resid(ResidArgs<T> a) {
 }
 
 // Fold the CG correction into the FP64 solution before the true residual (pointwise,
-// its own launch so no tile ever sees a half-updated neighbour).
+// its own launch so no tile ever sees a half-updated neighbour).  Persistent over the
+// residual kernel's schedule, so a launch with no variant to refine costs next to nothing.
 template <typename T>
-__global__ void k_fold(const DevVariant* var, const int* tile_var, const int2* tile_ij, const uint8_t* tag,
-                       const VarState* st, double* x64, State4<T>* const* sbuf) {
-  const long long t = blockIdx.x;
-  const int v = tile_var[t];
-  if (st[v].phase != PH_RESID) return;
-  const DevVariant& V = var[v];
-  const int2 ij = tile_ij[t];
-  const int i = ij.x + threadIdx.x, j = ij.y + threadIdx.y;
-  if (i > V.nx || j > V.ny) return;
-  const long long n = V.base + (long long)j * V.P + i;
-  if ((tag[n] & KIND_MASK) != K_FREE) return;
-  State4<T>* s = sbuf[st[v].buf];
-  x64[n] = x64[n] + (double)s[n].x;
-  s[n].x = T(0);
+__global__ void __launch_bounds__(NT) k_fold(const DevVariant* var, Sched sc, const uint8_t* tag,
+                                             const VarState* st, double* x64, State4<T>* const* sbuf) {
+  for (int sg = sc.cta_seg[blockIdx.x]; sg < sc.cta_seg[blockIdx.x + 1]; ++sg) {
+    const int v = sc.seg_var[sg];
+    if (st[v].phase != PH_RESID) continue;
+    const DevVariant& V = var[v];
+    State4<T>* s = sbuf[st[v].buf];
+    for (int t = sc.seg_t0[sg]; t < sc.seg_t1[sg]; ++t) {
+      const int2 ij = sc.tile_ij[t];
+      const int i = ij.x + threadIdx.x, j = ij.y + threadIdx.y;
+      if (i > V.nx || j > V.ny) continue;
+      const long long n = V.base + (long long)j * V.P + i;
+      if ((tag[n] & KIND_MASK) != K_FREE) continue;
+      x64[n] = x64[n] + (double)s[n].x;
+      s[n].x = T(0);
+    }
+  }
 }
 
 // Seed the slot bits into the x field of every BODY node's record in both ping-pong
@@ -1049,54 +1053,64 @@ static const void* cg_func(int precision, int ns) {
   return ns == 4 ? cg_kernel<float, 4>() : ns == 3 ? cg_kernel<float, 3>() : cg_kernel<float, 2>();
 }
 
-// Cut points of the fused-CG schedule (contiguous tile ranges of equal estimated cost)
-// and the segments they make at variant boundaries, written to the configuration's
-// device arrays in place (graphs captured with these pointers stay valid).
+// Cut points of the fused-CG schedule (contiguous tile ranges of equal estimated cost
+// over the variants still marked active; tiles of finished variants count as free) and
+// the segments they make at variant boundaries, written to the configuration's device
+// arrays in place (graphs captured with these pointers stay valid).  The copies are
+// ordered on the stream after the work already queued.
 static void cg_sched_write(Batch& b, CgConfig& c) {
   const int G = c.G, T = (int)c.tile_cost.size();
+  if ((int)c.active.size() != b.nv) c.active.assign(b.nv, 1);
+  auto cost = [&](int t) { return c.active[c.tile_var[t]] ? c.tile_cost[t] : 0.0; };
   double total = 0.0;
-  for (double x : c.tile_cost) total += x;
+  for (int t = 0; t < T; ++t) total += cost(t);
   c.cut.assign(G + 1, 0);
   int k = 0;
   double run = 0.0;
   for (int g = 0; g <= G; ++g) {
     const double target = total * g / G;
-    while (k < T && run + 0.5 * c.tile_cost[k] < target) run += c.tile_cost[k++];
+    while (k < T && run + 0.5 * cost(k) < target) run += cost(k++);
     c.cut[g] = (g == G) ? T : k;
   }
-  std::vector<int> cta_seg(G + 1), seg_var, seg_t0, seg_t1;
+  c.h_cta_seg.assign(G + 1, 0);
+  c.h_seg_var.clear();
+  c.h_seg_t0.clear();
+  c.h_seg_t1.clear();
   for (int g = 0; g < G; ++g) {
-    cta_seg[g] = (int)seg_var.size();
+    c.h_cta_seg[g] = (int)c.h_seg_var.size();
     for (int t = c.cut[g]; t < c.cut[g + 1]; ++t) {
       const int v = c.tile_var[t];
       if (t == c.cut[g] || c.tile_var[t - 1] != v) {
-        seg_var.push_back(v);
-        seg_t0.push_back(t);
-        seg_t1.push_back(t + 1);
+        c.h_seg_var.push_back(v);
+        c.h_seg_t0.push_back(t);
+        c.h_seg_t1.push_back(t + 1);
       } else {
-        seg_t1.back() = t + 1;
+        c.h_seg_t1.back() = t + 1;
       }
     }
   }
-  cta_seg[G] = (int)seg_var.size();
-  const int S = (int)seg_var.size();
+  c.h_cta_seg[G] = (int)c.h_seg_var.size();
+  const int S = (int)c.h_seg_var.size();
   if (S > G + b.nv) throw Error{PF_ECUDA, "internal: fused-CG schedule has too many segments"};
-  std::vector<int> vs0(b.nv, 0), vs1(b.nv, 0), seen(b.nv, 0);
+  c.h_vs0.assign(b.nv, 0);
+  c.h_vs1.assign(b.nv, 0);
+  std::vector<char> seen(b.nv, 0);
   for (int i = 0; i < S; ++i) {
-    const int v = seg_var[i];
-    if (!seen[v]) { vs0[v] = i; seen[v] = 1; }
-    vs1[v] = i + 1;
+    const int v = c.h_seg_var[i];
+    if (!seen[v]) { c.h_vs0[v] = i; seen[v] = 1; }
+    c.h_vs1[v] = i + 1;
   }
+  // pageable sources: each call returns once its data is staged, so the host vectors
+  // may change afterwards
   cudaStream_t s = b.stream;
-  PF_CUDA(cudaMemcpyAsync(c.d_cta_seg, cta_seg.data(), (G + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
+  PF_CUDA(cudaMemcpyAsync(c.d_cta_seg, c.h_cta_seg.data(), (G + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
   if (S > 0) {
-    PF_CUDA(cudaMemcpyAsync(c.d_seg_var, seg_var.data(), S * sizeof(int), cudaMemcpyHostToDevice, s));
-    PF_CUDA(cudaMemcpyAsync(c.d_seg_t0, seg_t0.data(), S * sizeof(int), cudaMemcpyHostToDevice, s));
-    PF_CUDA(cudaMemcpyAsync(c.d_seg_t1, seg_t1.data(), S * sizeof(int), cudaMemcpyHostToDevice, s));
+    PF_CUDA(cudaMemcpyAsync(c.d_seg_var, c.h_seg_var.data(), S * sizeof(int), cudaMemcpyHostToDevice, s));
+    PF_CUDA(cudaMemcpyAsync(c.d_seg_t0, c.h_seg_t0.data(), S * sizeof(int), cudaMemcpyHostToDevice, s));
+    PF_CUDA(cudaMemcpyAsync(c.d_seg_t1, c.h_seg_t1.data(), S * sizeof(int), cudaMemcpyHostToDevice, s));
   }
-  PF_CUDA(cudaMemcpyAsync(c.d_var_seg0, vs0.data(), b.nv * sizeof(int), cudaMemcpyHostToDevice, s));
-  PF_CUDA(cudaMemcpyAsync(c.d_var_seg1, vs1.data(), b.nv * sizeof(int), cudaMemcpyHostToDevice, s));
-  PF_CUDA(cudaStreamSynchronize(s));       // the host vectors go out of scope
+  PF_CUDA(cudaMemcpyAsync(c.d_var_seg0, c.h_vs0.data(), b.nv * sizeof(int), cudaMemcpyHostToDevice, s));
+  PF_CUDA(cudaMemcpyAsync(c.d_var_seg1, c.h_vs1.data(), b.nv * sizeof(int), cudaMemcpyHostToDevice, s));
 }
 
 // Re-balance rounds of the first tuned solve on a handle and launches timed per round
@@ -1236,7 +1250,7 @@ void ensure_solver_memory(Batch& b, int precision) {
     PF_CUDA(cudaMemsetAsync(b.sb64, 0, 4 * B * sizeof(double), b.stream));
     PF_CUDA(cudaMemsetAsync(b.sb32, 0, 4 * B * sizeof(float), b.stream));
     b.bnorm2_unit.assign(b.nv, -1.0);
-    for (int k = 0; k < 6; ++k) PF_CUDA(cudaEventCreate(&b.ev[k]));
+    for (int k = 0; k < Batch::N_EV; ++k) PF_CUDA(cudaEventCreate(&b.ev[k]));
   }
   if (precision == PF_FP64 && !b.st64[0]) {
     for (int k = 0; k < 2; ++k) b.st64[k] = (State4<double>*)dev_alloc(b, V * sizeof(State4<double>));
@@ -1368,14 +1382,12 @@ static void launch_cg_chunk(Batch& b, int precision, int chunk, cudaStream_t s, 
 static void launch_resid_only(Batch& b, int precision, cudaStream_t s) {
   const dim3 blk(TX, TY);
   if (precision == PF_FP64) {
-    k_fold<double><<<(unsigned)b.T, blk, 0, s>>>(b.d_var, b.tile_var, b.tile_ij, b.tag, b.state, b.x64,
-                                                 (State4<double>* const*)b.d_sbuf);
+    k_fold<double><<<b.G, blk, 0, s>>>(b.d_var, b.sched, b.tag, b.state, b.x64, (State4<double>* const*)b.d_sbuf);
     ResidArgs<double> ra;
     fill_resid_args<double>(b, ra, b.st64, b.sb64, 0);
     k_resid<double><<<b.G, blk, 0, s>>>(ra);
   } else {
-    k_fold<float><<<(unsigned)b.T, blk, 0, s>>>(b.d_var, b.tile_var, b.tile_ij, b.tag, b.state, b.x64,
-                                                (State4<float>* const*)(b.d_sbuf + 2));
+    k_fold<float><<<b.G, blk, 0, s>>>(b.d_var, b.sched, b.tag, b.state, b.x64, (State4<float>* const*)(b.d_sbuf + 2));
     ResidArgs<float> ra;
     fill_resid_args<float>(b, ra, b.st32, b.sb32, 1);
     k_resid<float><<<b.G, blk, 0, s>>>(ra);
@@ -1478,7 +1490,7 @@ pf_status solve_core(Batch& b, double U, const pf_solve_opts& o, double* dev_psi
     chunk = nodes > (8LL << 20) ? 16 : (nodes > (1LL << 20) ? 64 : 256);
   }
   cudaGraphExec_t ex = get_graph(b, prec, chunk);
-  if (!b.h_poll) PF_CUDA(cudaMallocHost(&b.h_poll, 2 * sizeof(int)));
+  if (!b.h_poll) PF_CUDA(cudaMallocHost(&b.h_poll, 4 * sizeof(int)));
   int* hdone = b.h_poll;
   double cg_ms = 0, res_ms = 0;
   long long launches = 0, rlaunches = 1;
@@ -1486,6 +1498,10 @@ pf_status solve_core(Batch& b, double U, const pf_solve_opts& o, double* dev_psi
   // handle: a few of this solve's CG iterations run as timed launches, then the cut
   // points move so that every CTA's measured tile time evens out.
   CgConfig& cc = cg_config(b, prec, b.cg_stages);
+  if (cc.active.size() != (size_t)b.nv || std::find(cc.active.begin(), cc.active.end(), 0) != cc.active.end()) {
+    cc.active.assign(b.nv, 1);                   // a solve starts with every variant running
+    cg_sched_write(b, cc);
+  }
   if (b.cg_tune && o.k_max > 0 && (long long)cc.tile_cost.size() >= 2LL * cc.G) {
     for (; cc.tune_rounds < CG_TUNE_ROUNDS; ++cc.tune_rounds) {
       PF_CUDA(cudaMemsetAsync(cc.d_cta_ns, 0, cc.G * sizeof(unsigned long long), s));
@@ -1506,26 +1522,73 @@ pf_status solve_core(Batch& b, double U, const pf_solve_opts& o, double* dev_psi
   }
   // k_max == 0 (internal use): only the initial residual, which measures ||b||
   const long long max_chunks = o.k_max == 0 ? 0 : o.k_max / chunk + 1000;
-  for (long long c = 0; c < max_chunks; ++c) {
-    PF_CUDA(cudaEventRecord(b.ev[0], s));
+  // Chunks are queued two ahead of the host: slot k holds events (start, after the CG
+  // graph, after the refinement kernels) and the pinned poll words / variant states
+  // copied after it.  The host retires a slot by waiting on its last event.
+  constexpr int SLOTS = 2;
+  if (!b.h_vs) PF_CUDA(cudaMallocHost(&b.h_vs, SLOTS * std::max(1, b.nv) * sizeof(VarState)));
+  auto cost_of_active = [&](const std::vector<char>& act) {
+    double x = 0.0;
+    for (size_t t = 0; t < cc.tile_cost.size(); ++t) x += act[cc.tile_var[t]] ? cc.tile_cost[t] : 0.0;
+    return x;
+  };
+  double active_cost = cost_of_active(cc.active);   // estimated cost the schedule is balanced over
+  auto issue = [&](long long c) {
+    const int k = (int)(c % SLOTS);
+    PF_CUDA(cudaEventRecord(b.ev[6 + 3 * k], s));
     PF_CUDA(cudaGraphLaunch(ex, s));
-    PF_CUDA(cudaEventRecord(b.ev[1], s));
+    PF_CUDA(cudaEventRecord(b.ev[7 + 3 * k], s));
     launch_resid_only(b, prec, s);
-    PF_CUDA(cudaEventRecord(b.ev[2], s));
-    PF_CUDA(cudaMemcpyAsync(hdone, b.n_done, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
-    PF_CUDA(cudaStreamSynchronize(s));
+    PF_CUDA(cudaMemcpyAsync(hdone + 2 * k, b.n_done, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    PF_CUDA(cudaMemcpyAsync(b.h_vs + (size_t)k * b.nv, b.state, b.nv * sizeof(VarState), cudaMemcpyDeviceToHost, s));
+    PF_CUDA(cudaEventRecord(b.ev[8 + 3 * k], s));
+  };
+  bool finished = false;
+  auto retire = [&](long long c) {
+    const int k = (int)(c % SLOTS);
+    PF_CUDA(cudaEventSynchronize(b.ev[8 + 3 * k]));
     float ms1 = 0, ms2 = 0;
-    PF_CUDA(cudaEventElapsedTime(&ms1, b.ev[0], b.ev[1]));
-    PF_CUDA(cudaEventElapsedTime(&ms2, b.ev[1], b.ev[2]));
+    PF_CUDA(cudaEventElapsedTime(&ms1, b.ev[6 + 3 * k], b.ev[7 + 3 * k]));
+    PF_CUDA(cudaEventElapsedTime(&ms2, b.ev[7 + 3 * k], b.ev[8 + 3 * k]));
     cg_ms += ms1;
     res_ms += ms2;
     launches += chunk;
     rlaunches += 1;
-    if (hdone[1]) throw Error{PF_ETIMEOUT, "a bounded wait in the CG kernel gave up (TMA tile not delivered)"};
-    if (hdone[0] >= b.nv) break;
+    if (hdone[2 * k + 1]) throw Error{PF_ETIMEOUT, "a bounded wait in the CG kernel gave up (TMA tile not delivered)"};
+    if (hdone[2 * k] >= b.nv) {
+      finished = true;
+      return;
+    }
+    // spread the grid over the variants still running once enough work has finished
+    std::vector<char> act(b.nv);
+    for (int v = 0; v < b.nv; ++v) act[v] = b.h_vs[(size_t)k * b.nv + v].phase != PH_DONE;
+    const double now = cost_of_active(act);
+    if (now < 0.9 * active_cost) {
+      cc.active = act;
+      cg_sched_write(b, cc);
+      active_cost = now;
+    }
+  };
+  long long issued = 0, retired = 0;
+  while (!finished && issued < max_chunks) {
+    issue(issued++);
+    if (issued - retired >= SLOTS) retire(retired++);
+  }
+  while (retired < issued) {
+    // chunks queued after the last variant finished run as no-ops; account for them
+    if (finished) {
+      const int k = (int)(retired % SLOTS);
+      PF_CUDA(cudaEventSynchronize(b.ev[8 + 3 * k]));
+      ++retired;
+      continue;
+    }
+    retire(retired++);
   }
   PF_CUDA(cudaEventRecord(b.ev[4], s));
-  b.launches += 1 + (n_slots > 0 ? 1 : 0) + launches + (long long)rlaunches * 2;
+  // kernels launched: k_init, slot seeding, the tuning launches and every queued chunk
+  // (CG graph + fold + residual), no-op chunks after the last variant finished included
+  const long long tuned_launches = launches - (long long)(rlaunches - 1) * chunk;
+  b.launches += 1 + (n_slots > 0 ? 1 : 0) + tuned_launches + issued * chunk + (1 + issued) * 2;
   std::vector<VarState> fin(b.nv);
   PF_CUDA(cudaMemcpyAsync(fin.data(), b.state, b.nv * sizeof(VarState), cudaMemcpyDeviceToHost, s));
   PF_CUDA(cudaStreamSynchronize(s));
