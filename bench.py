@@ -15,6 +15,15 @@ kernel against the measured copy bandwidth and the batched solves per second.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
+`--config` selects another workload of the same hot path for separate measurements
+(the default, c2, is the headline line above):
+    c1  one cylinder, 128x64 grid, 50 sweeps (validation case)
+    c3  the five-cylinder layout at delta=0.25 on an 8192x4096 grid (33.6 M nodes)
+    c4  256-variant parametric sweep (seed 0): jittered five-cylinder layouts,
+        nx in {256, 288, ..., 1024}, ny = nx/2, one batch; reports solves/s
+    c5  64-variant gradient study (seed 1), 1024x512: solve + adjoint CoPFI shape
+        gradient per variant; reports gradients/s
+
 Under torchrun (N > 1) every rank solves its own copy of the batch (independent
 problems, no collective on the data path: "weak" scaling); rank 0 prints one JSON
 line with the whole-job value.  `--impl reference` times the CPU oracle (the plain
@@ -56,6 +65,7 @@ def parse():
     ap.add_argument("--cpu-iters", type=int, default=60, help="oracle CG iterations in the CPU sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--config", choices=["c1", "c2", "c3", "c4", "c5"], default="c2")
     ap.add_argument("--tune", dest="tune", action="store_true", default=True,
                     help="re-balance the persistent CG schedule from timed launches (default)")
     ap.add_argument("--no-tune", dest="tune", action="store_false")
@@ -64,8 +74,26 @@ def parse():
 
 def cases(args):
     from paper_2512_12232_gb300 import workloads as W
+    if args.config == "c1":
+        return [W.single_cylinder()]
+    if args.config == "c3":
+        return [W.five_cylinder_case(0.25, 8192, 4096, SWEEPS)]
+    if args.config == "c4":
+        return W.parametric_sweep(256, seed=0)
+    if args.config == "c5":
+        return W.gradient_study(64, seed=1, nx=1024)
     ds = (list(DELTAS) * ((args.variants + len(DELTAS) - 1) // len(DELTAS)))[: args.variants]
     return [W.five_cylinder_case(d, args.nx, args.nx // 2, SWEEPS) for d in ds]
+
+
+def workload_name(args, n_cases):
+    if args.config == "c2" and args.nx == NX and args.variants == 5 and args.precision == "mixed":
+        return WORKLOAD
+    names = {"c1": "single_cylinder_128x64_S50", "c3": "five_cylinders_8192x4096_S200_delta0.25",
+             "c4": "parametric_sweep_256_variants_nx256-1024_S200_seed0",
+             "c5": "gradient_study_64_variants_1024x512_S200_seed1_copfi_adjoint"}
+    base = names.get(args.config, f"five_cylinders_{args.nx}x{args.nx // 2}_x{n_cases}")
+    return f"{base}_{args.precision}_{args.tol:g}"
 
 
 def peaks():
@@ -150,11 +178,23 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ CPU oracle sample
+def oracle_case(args):
+    """The variant the CPU oracle is timed on: the workload's own for c1, c2 (delta =
+    0.25), c4 and c5; for c3 the same layout at 2048x1024 (the oracle's rate per
+    DOF-iteration does not depend on the grid size, and a 33.6 M-node FP64 assembly
+    on the host is far outside a bounded sample)."""
+    from paper_2512_12232_gb300 import workloads as W
+    if args.config == "c3":
+        return W.five_cylinder_case(0.25, 2048, 1024, SWEEPS)
+    cs = cases(args)
+    return cs[1 % len(cs)] if args.config == "c2" else cs[0]
+
+
 def oracle_sample(args, iters, reps=1):
-    """The oracle's element-by-element CG (Appendix A) on one full-size variant:
-    returns (DOF-iters/s, seconds, n_dof).  Setup (mesh, element matrices) untimed."""
+    """The oracle's element-by-element CG (Appendix A) on one variant: returns
+    (DOF-iters/s, seconds, n_dof).  Setup (mesh, element matrices) untimed."""
     from oracle import mesh as OM, solve as OS, system as OSY
-    c = cases(args)[1 % args.variants]
+    c = oracle_case(args)
     m = OM.build_mesh(c.grid, c.bodies, c.sweeps, c.bc)
     s = OSY.assemble(m, 1.0)
     times = []
@@ -170,7 +210,7 @@ def run_reference(args, rank, world):
         return 0
     iters = max(1, args.cpu_iters // 3)
     from oracle import mesh as OM, solve as OS, system as OSY
-    c = cases(args)[1 % args.variants]
+    c = oracle_case(args)
     m = OM.build_mesh(c.grid, c.bodies, c.sweeps, c.bc)
     s = OSY.assemble(m, 1.0)
     kind, body = m.kind.ravel(), m.body.ravel()
@@ -182,12 +222,12 @@ def run_reference(args, rank, world):
     el = time.perf_counter() - t
     value = s.n_dof * iters * args.steps / el
     sample = (f"oracle element-by-element CG (Appendix A), {iters} iterations per step on one "
-              f"{c.nx}x{c.ny} five-cylinder variant (delta={c.meta['delta']}, N_dof={s.n_dof}); mesh and "
-              f"element matrices built untimed")
+              f"{c.nx}x{c.ny} variant '{c.name}' (N_dof={s.n_dof}); mesh and element matrices built untimed")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": "one variant, fixed CG iterations"},
+            "data": "synthetic", "config": {"workload": workload_name(args, len(cases(args))),
+                                            "sample": "one variant, fixed CG iterations"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -213,7 +253,10 @@ def run_ours(args, rank, world, local):
         g = api.batch_build(cs)
         res = api.psi_solve(g, U=1.0, tol=args.tol, precision=prec, inner_tol=args.inner_tol,
                             tune_schedule=args.tune)
-        cps = [api.copfi(g, v, 3, 4, 1.0) for v in range(len(cs))]
+        if args.config == "c5":
+            api.grad(g, api.PF_OBJ_COPFI, 3, 4, 1.0, args.tol, want_dX=False)
+        # CoPFI of the gap between the two stacked bodies (the single-cylinder case has none)
+        cps = [] if args.config == "c1" else [api.copfi(g, v, 3, 4, 1.0) for v in range(len(cs))]
         if host_out is not None:
             host_out.copy_(res.psi, non_blocking=True)
         tm = g.timing()
@@ -263,8 +306,9 @@ def run_ours(args, rank, world, local):
         e2e_el = time.perf_counter() - t
         e2e_units = sum(sum(st[v]["n_dof"] * res.info[v]["iters"] for v in range(len(cs)))
                         for res, _, _, st in e2e_rec)
-        h2d = len(cs) * 40 + (len(cs) + 1) * 4 + 5 * len(cs) * 24 + 16
-        d2h = 8 * int(nodes) + 8 * 5 * len(cs) + 32 * len(cs)
+        nbody = sum(len(c.bodies) for c in cs)
+        h2d = len(cs) * 40 + (len(cs) + 1) * 4 + nbody * 24 + 16        # grids, offsets, bodies, sides
+        d2h = 8 * int(nodes) + 8 * nbody + 32 * len(cs)                 # psi, body psi, solve records
         e2e = [e2e_units, e2e_el, h2d, d2h]
 
     # whole-job aggregation: units summed over ranks, time = max over ranks
@@ -301,7 +345,8 @@ def run_ours(args, rank, world, local):
         v, times, ndof = oracle_sample(args, args.cpu_iters)
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"{args.cpu_iters} iterations of the oracle's element-by-element CG on one "
-                         f"{args.nx}x{args.nx // 2} variant (N_dof={ndof}), {min(times):.1f} s"}
+                         f"{oracle_case(args).nx}x{oracle_case(args).ny} variant (N_dof={ndof}), "
+                         f"{min(times):.1f} s"}
     clocks = clk.summary()
     iters = [res.info[v]["iters"] for v in range(len(cs)) for res in [records[-1][0]]]
     line = {
@@ -309,14 +354,15 @@ def run_ours(args, rank, world, local):
         "warmup": args.warmup, "ms_per_step": 1e3 * vals[1] / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD if (args.nx == NX and args.variants == 5 and args.precision == "mixed")
-                   else f"five_cylinders_{args.nx}x{args.nx // 2}_x{args.variants}_{args.precision}",
+        "config": {"workload": workload_name(args, len(cs)),
                    "variants": len(cs), "nodes_per_step": int(nodes), "tol": args.tol,
                    "precision": "FP32 operator+vectors, FP64 dots/scalars/true residual/refinement"
                    if args.precision == "mixed" else "FP64",
                    "inner_tol": args.inner_tol, "parallelism": f"replicas x{world}",
-                   "l2": "inputs larger than L2: each step builds fresh meshes; 5-variant working set > 500 MB"},
-        "solves_per_s": vals[2] / vals[1], "all_converged": ok, "iters_per_variant": iters,
+                   "l2": "inputs larger than L2: each step builds fresh meshes (working set "
+                         f"{int(nodes) * 48 / 1e6:.0f} MB of CG state and coefficients, L2 is 126 MB)"},
+        "solves_per_s": vals[2] / vals[1], "all_converged": ok,
+        "iters_per_variant": iters if len(iters) <= 8 else {"min": min(iters), "max": max(iters)},
         "copfi": [cp for cp, _ in records[-1][1]],
         "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": int(launches),
         "e2e": ({"value": e2e[0] / e2e[1], "unit": UNIT, "h2d_bytes_per_step": e2e[2],

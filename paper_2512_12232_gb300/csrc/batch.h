@@ -18,6 +18,7 @@ struct HostVariant {
   int tiles_x, tiles_y;
   long long tile0;             // first tile of the variant in the tile list
   pf_mesh_stats stats;
+  long long n_gen32_cells = 0;  // general cells whose FP32 coefficients differ from the rectangle's
 };
 
 struct Error {                 // thrown inside the library, converted to pf_status at the ABI

@@ -171,10 +171,10 @@ __global__ void k_stiffness(const DevVariant* var, const int* tile_var, const in
                             long long* stats_i, double* detmin) {
   TileCtx c = tile_ctx(var, tile_var, tile_ij);
   const DevVariant& V = var[c.v];
-  __shared__ long long cnt[5];
+  __shared__ long long cnt[6];
   __shared__ double dmin;
   const int tid = linear_tid();
-  if (tid < 5) cnt[tid] = 0;
+  if (tid < 6) cnt[tid] = 0;
   if (tid == 0) dmin = 1e300;
   __syncthreads();
   if (c.in) {
@@ -232,12 +232,13 @@ __global__ void k_stiffness(const DevVariant* var, const int* tile_var, const in
         for (int m = 0; m < 6; ++m) differs32 |= (float)k6[m] != V.kr32[m];
         tag[n] = t | CELL_GENERAL | (differs32 ? CELL_GEN32 : 0);
         atomicAdd((unsigned long long*)&cnt[4], 1ull);
+        if (differs32) atomicAdd((unsigned long long*)&cnt[5], 1ull);
       }
       atomic_min_double(&dmin, dm);
     }
   }
   __syncthreads();
-  if (tid < 5 && cnt[tid]) atomicAdd((unsigned long long*)&stats_i[c.v * 6 + tid], (unsigned long long)cnt[tid]);
+  if (tid < 6 && cnt[tid]) atomicAdd((unsigned long long*)&stats_i[c.v * 6 + tid], (unsigned long long)cnt[tid]);
   if (tid == 0 && dmin < 1e300) atomic_min_double(&detmin[c.v], dmin);
 }
 
@@ -245,15 +246,18 @@ __device__ int block_exscan(int x, int* total, int* sh /* >= 9 */);
 
 // 5b. per fused-CG tile: does any cell used by the tile (cells i0-1 .. i0+CTX-1,
 //     j0-1 .. j0+CTY-1 of its variant) carry stored coefficients (bit 0: FP64 operator,
-//     bit 1: FP32 operator), and how many of its nodes carry an operator row (FREE or
-//     BODY)?  Both feed the cost estimate of the fused-CG schedule.
+//     bit 1: FP32 operator); is the tile "plain" for that operator (bit 2: FP64, bit 3:
+//     FP32): every node of its window i0-1 .. i0+CTX, j0-1 .. j0+CTY exists and is FREE
+//     (so every cell is active) and no cell needs stored coefficients, which lets the
+//     fused CG step skip the tags; and how many of its nodes carry an operator row
+//     (FREE or BODY)?  The counts feed the cost estimate of the fused-CG schedule.
 __global__ void k_tile_general(const DevVariant* var, const int* tile_var, const int2* tile_ij, const uint8_t* tag,
                                uint8_t* gen, int* act) {
   __shared__ int sh[NT / 32 + 1];
   const long long t = blockIdx.x;
   const DevVariant& V = var[tile_var[t]];
   const int2 ij = tile_ij[t];
-  int g64 = 0, g32 = 0, na = 0;
+  int g64 = 0, g32 = 0, na = 0, allfree = 1;
   for (int q = linear_tid(); q < (CTX + 1) * (CTY + 1); q += NT) {
     const int i = ij.x - 1 + q % (CTX + 1), j = ij.y - 1 + q / (CTX + 1);
     if (i >= 0 && j >= 0 && i < V.nx && j < V.ny) {
@@ -269,12 +273,18 @@ __global__ void k_tile_general(const DevVariant* var, const int* tile_var, const
       na += (k == K_FREE || k == K_BODY);
     }
   }
+  for (int q = linear_tid(); q < (CTX + 2) * (CTY + 2); q += NT) {
+    const int i = ij.x - 1 + q % (CTX + 2), j = ij.y - 1 + q / (CTX + 2);
+    if (i < 0 || j < 0 || i > V.nx || j > V.ny) allfree = 0;
+    else if ((tag[V.base + (long long)j * V.P + i] & KIND_MASK) != K_FREE) allfree = 0;
+  }
   g64 = __syncthreads_or(g64);
   g32 = __syncthreads_or(g32);
+  allfree = __syncthreads_and(allfree);
   int tot;
   block_exscan(na, &tot, sh);
   if (linear_tid() == 0) {
-    gen[t] = (uint8_t)(g64 | (g32 << 1));
+    gen[t] = (uint8_t)(g64 | (g32 << 1) | ((allfree && !g64) << 2) | ((allfree && !g32) << 3));
     act[t] = tot;
   }
 }
@@ -633,6 +643,7 @@ void build_batch(Batch& b, const pf_grid* grids, const int* body_offsets, const 
     S.n_inactive = st[v * 6 + 2];
     S.n_active_cells = st[v * 6 + 3];
     S.n_general_cells = st[v * 6 + 4];
+    b.hv[v].n_gen32_cells = st[v * 6 + 5];
     S.n_bodies = H.nb;
     S.n_dof = S.n_free + H.nb;
     S.n_boundary_edges = b.h_edge_ptr[H.body0 + H.nb] - b.h_edge_ptr[H.body0];

@@ -286,7 +286,8 @@ struct CgSmem {
   static constexpr int kbox_bytes = align((CTY + 1) * 6 * KHALF * (int)sizeof(T));
   static constexpr int stage_bytes = off_k + (kTmaK ? 2 * kbox_bytes : 0);
   static constexpr int kplane_bytes = align(KB * (int)sizeof(T));
-  static constexpr int tx_base = SB * (int)sizeof(T) + TBW * (CTY + 2);
+  static constexpr int tx_tag = TBW * (CTY + 2);
+  static constexpr int tx_base = SB * (int)sizeof(T) + tx_tag;
   static constexpr int tx_k = kTmaK ? 6 * KB * (int)sizeof(T) : 0;
   // after the NS stages: two p tiles with halo, two effective-tag tiles, barriers
   static constexpr int ptile_bytes = align((CTX + 2) * (CTY + 2) * (int)sizeof(T));
@@ -300,6 +301,17 @@ struct CgSmem {
                     stage_bytes % 128 == 0,
                 "TMA destinations must start on 128-byte boundaries");
 };
+
+// Row of the operator at a node whose four cells are active rectangles with the
+// closed-form constants kr: K23 = K01, K12 = K03, K13 = K02, so the row is
+// 2 K01 (dE + dW) + 2 K03 (dN + dS) + K02 (sum of the diagonal differences).
+template <typename T>
+__device__ __forceinline__ T q4_row_rect(const T (&p)[3][3], const T* kr) {
+  const T pc = p[1][1];
+  const T dE = p[1][2] - pc, dW = p[1][0] - pc, dN = p[2][1] - pc, dS = p[0][1] - pc;
+  const T dNE = p[2][2] - pc, dNW = p[2][0] - pc, dSE = p[0][2] - pc, dSW = p[0][0] - pc;
+  return T(2) * kr[0] * (dE + dW) + T(2) * kr[2] * (dN + dS) + kr[1] * ((dNE + dSW) + (dNW + dSE));
+}
 
 // Row of the operator at one node from its 3x3 neighbourhood p[3][3] (p[1][1] = the
 // node, first index = row j-1, j, j+1, second = column i-1, i, i+1) and the tags of its
@@ -317,11 +329,8 @@ __device__ __forceinline__ T q4_row_nb(const T (&p)[3][3], uint8_t c0, uint8_t c
   constexpr uint8_t GEN = sizeof(T) == 4 ? CELL_GEN32 : CELL_GENERAL;   // cells that need stored K_e
   constexpr uint8_t FLAGS = CELL_ACTIVE | GEN;
   if ((c0 & FLAGS) == CELL_ACTIVE && (c1 & FLAGS) == CELL_ACTIVE && (c2 & FLAGS) == CELL_ACTIVE &&
-      (c3 & FLAGS) == CELL_ACTIVE) {
-    // four undisplaced rectangles: K23 = K01, K12 = K03, K13 = K02, so the row is
-    // 2 K01 (dE + dW) + 2 K03 (dN + dS) + K02 (sum of the diagonal differences)
-    return T(2) * kr[0] * (dE + dW) + T(2) * kr[2] * (dN + dS) + kr[1] * ((dNE + dSW) + (dNW + dSE));
-  }
+      (c3 & FLAGS) == CELL_ACTIVE)
+    return q4_row_rect<T>(p, kr);
   // coefficient m of the cell whose corner 0 is at box column kc, box row kr_, global index g
   auto coef = [&](int m, int kr_, int kc, long long g) -> T {
     if constexpr (L::kTmaK) {
@@ -367,14 +376,14 @@ __device__ __forceinline__ T q4_row_nb(const T (&p)[3][3], uint8_t c0, uint8_t c
 // Issue the TMA loads of tile t into stage s (one thread).
 template <typename T>
 __device__ __forceinline__ void cg_issue(const CgMaps& mp, int cur, unsigned char* stage, uint64_t* bar,
-                                         int2 ij, int row0, long long Rtot, bool gen) {
+                                         int2 ij, int row0, long long Rtot, bool gen, bool plain) {
   using L = CgSmem<T, 2>;   // stage layout does not depend on the stage count
   const int x0 = ij.x - 4, y0 = row0 + ij.y - 1;
-  mbar_arrive_expect_tx(bar, L::tx_base + (gen ? L::tx_k : 0));
+  mbar_arrive_expect_tx(bar, L::tx_base - (plain ? L::tx_tag : 0) + (gen ? L::tx_k : 0));
   // state records viewed as a [rows][4 P] array: two boxes of SHALF nodes (long rows)
   tma_load_2d(stage + L::off_s, &mp.s[cur], 4 * (ij.x - 1), y0, bar);
   tma_load_2d(stage + L::off_s + L::sbox_bytes, &mp.s[cur], 4 * (ij.x - 1 + L::SHALF), y0, bar);
-  tma_load_2d(stage + L::off_t, &mp.tag, ij.x - 16, y0, bar);
+  if (!plain) tma_load_2d(stage + L::off_t, &mp.tag, ij.x - 16, y0, bar);   // plain tiles need no tags
   if constexpr (L::kTmaK) {
     if (gen) {
       // interleaved coefficients as a [rows][6 P] array: two boxes of KHALF cells
@@ -408,6 +417,8 @@ __global__ void __launch_bounds__(NTC, sizeof(T) == 4 ? 2 : 1) k_cg(CGArgs<T> a,
   __shared__ double scratch[NT / 32 + 1];
   __shared__ double sh_qb[MAXB];
   __shared__ FinCache<T> fc;
+  __shared__ int2 s_tij[NS];                      // tile of each stage, written by the producer
+  __shared__ int s_tfl[NS];                       // its flags (bit 0: coefficient boxes, bit 1: plain)
   __shared__ int s_last, s_abort, s_issued;
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + L::off_bar);
   uint64_t* empty = full + NS;
@@ -454,8 +465,12 @@ __global__ void __launch_bounds__(NTC, sizeof(T) == 4 ? 2 : 1) k_cg(CGArgs<T> a,
           }
           if (*(volatile int*)&s_abort) break;
           fence_proxy_async_smem();
-          cg_issue<T>(mp, cur, smem + s * L::stage_bytes, &full[s], a.sc.tile_ij[t], row0, a.Rtot,
-                      (a.tile_gen[t] & (sizeof(T) == 4 ? 2 : 1)) != 0);
+          const int2 tij = a.sc.tile_ij[t];
+          const int fl = a.tile_gen[t];
+          const bool gen = (fl & (sizeof(T) == 4 ? 2 : 1)) != 0, plain = (fl & (sizeof(T) == 4 ? 8 : 4)) != 0;
+          s_tij[s] = tij;                         // published to the consumers by the arrive below
+          s_tfl[s] = (gen ? 1 : 0) | (plain ? 2 : 0);
+          cg_issue<T>(mp, cur, smem + s * L::stage_bytes, &full[s], tij, row0, a.Rtot, gen, plain);
           s_issued = q + 1;
         }
       }
@@ -498,8 +513,9 @@ __global__ void __launch_bounds__(NTC, sizeof(T) == 4 ? 2 : 1) k_cg(CGArgs<T> a,
         unsigned char* st = smem + s * L::stage_bytes;
         T* pt = reinterpret_cast<T*>(smem + L::off_ptile + (q & 1) * L::ptile_bytes);
         uint8_t* tt = reinterpret_cast<uint8_t*>(smem + L::off_ttile + (q & 1) * L::ttile_bytes);
-        const int2 ij = a.sc.tile_ij[t];
         const bool ok = mbar_wait(&full[s], (q / NS) & 1);
+        const int2 ij = s_tij[s];
+        const bool plain = (s_tfl[s] & 2) != 0;
         const State4<T>* Ss = reinterpret_cast<const State4<T>*>(st + L::off_s);
         const uint8_t* Tg = reinterpret_cast<const uint8_t*>(st + L::off_t);
         const T* Ks = reinterpret_cast<const T*>(st + L::off_k);
@@ -508,7 +524,29 @@ __global__ void __launch_bounds__(NTC, sizeof(T) == 4 ? 2 : 1) k_cg(CGArgs<T> a,
         T rn4[STRIP], pn4[STRIP], xn4[STRIP];
         int bs4[STRIP];                           // slot of a BODY node in body_nodes
         uint8_t tg4[STRIP];
-        if (ok) {
+        if (ok && plain) {
+          // every node of the window is FREE and every cell active with rectangle constants
+#pragma unroll
+          for (int u = 0; u < STRIP; ++u) {
+            const int li = 1 + col, lj = 1 + row_lo + u;
+            const State4<T> o = staged_state<T>(Ss, li, lj);
+            const T rn = next_r(o.r, o.q, alpha);
+            const T pn = next_p(rn, o.p, beta);
+            pt[lj * W + li] = pn;
+            rn4[u] = rn; pn4[u] = pn; xn4[u] = next_x(o.x, o.p, alpha);
+            tg4[u] = K_FREE;
+            bs4[u] = -1;
+          }
+          for (int h = warp + (NT / 32) * lane; h < NH; h += NT) {
+            int li, lj;
+            if (h < W) { li = h; lj = 0; }
+            else if (h < 2 * W) { li = h - W; lj = CTY + 1; }
+            else if (h < 2 * W + CTY) { li = 0; lj = 1 + (h - 2 * W); }
+            else { li = CTX + 1; lj = 1 + (h - 2 * W - CTY); }
+            const State4<T> o = staged_state<T>(Ss, li, lj);
+            pt[lj * W + li] = next_p(next_r(o.r, o.q, alpha), o.p, beta);
+          }
+        } else if (ok) {
 #pragma unroll
           for (int u = 0; u < STRIP; ++u) {
             const int li = 1 + col, lj = 1 + row_lo + u;
@@ -567,7 +605,37 @@ __global__ void __launch_bounds__(NTC, sizeof(T) == 4 ? 2 : 1) k_cg(CGArgs<T> a,
           break;
         }
         // pass 2: operator rows of the strip from a register window of the p tile
-        {
+        if (plain) {
+          const int li = 1 + col;
+          T win[STRIP + 2][3];
+#pragma unroll
+          for (int r = 0; r < STRIP + 2; ++r) {
+            const int lj = row_lo + r;
+            win[r][0] = pt[lj * W + li - 1];
+            win[r][1] = pt[lj * W + li];
+            win[r][2] = pt[lj * W + li + 1];
+          }
+          T yq[STRIP];
+#pragma unroll
+          for (int u = 0; u < STRIP; ++u) {
+            const long long n = tb + (long long)(row_lo + u) * P + col;
+            const T nbh[3][3] = {{win[u][0], win[u][1], win[u][2]},
+                                 {win[u + 1][0], win[u + 1][1], win[u + 1][2]},
+                                 {win[u + 2][0], win[u + 2][1], win[u + 2][2]}};
+            const T y = q4_row_rect<T>(nbh, kr);
+            State4<T> o;
+            o.x = xn4[u];
+            o.r = rn4[u];
+            o.p = pn4[u];
+            o.q = y;
+            s_new[n] = o;
+            yq[u] = y;
+          }
+          acc.add4(0, rn4, rn4);
+          acc.add4(1, pn4, yq);
+          acc.add4(2, rn4, yq);
+          acc.add4(3, yq, yq);
+        } else {
           const int li = 1 + col;
           T win[STRIP + 2][3];
           uint8_t cl[STRIP + 1], cr[STRIP + 1];     // cells (i-1, j) and (i, j) for rows j0-1 .. j0+3
@@ -1608,8 +1676,9 @@ pf_status solve_core(Batch& b, double U, const pf_solve_opts& o, double* dev_psi
     const double per_node_free = prec == PF_MIXED ? 32.0 : 64.0;
     const double per_body = prec == PF_MIXED ? 20.0 : 36.0;
     const double per_gen = prec == PF_MIXED ? 24.0 : 48.0;
-    const double bv = per_node_free * M.n_free + per_body * M.n_body_nodes + 1.0 * M.n_nodes +
-                      per_gen * M.n_general_cells;
+    // coefficient bytes: the cells whose stored K_e the operator of this precision reads
+    const long long n_gen = prec == PF_MIXED ? b.hv[v].n_gen32_cells : M.n_general_cells;
+    const double bv = per_node_free * M.n_free + per_body * M.n_body_nodes + 1.0 * M.n_nodes + per_gen * n_gen;
     bytes_done += bv * (double)S.iters;
     if (info) {
       info[v].iters = S.iters;
