@@ -234,6 +234,31 @@ def run_reference(args, rank, world):
     return 0
 
 
+# ------------------------------------------------------------------ multi-rank
+def aggregate(vals, e2e, dist, device):
+    """Whole-job numbers over ranks: units summed, times the maximum over ranks.
+    vals = [units, seconds, solves]; e2e = [units, seconds, h2d bytes, d2h bytes] or None.
+    `dist` is torch.distributed (or None for one rank); `device` holds the reduction
+    tensors ("cuda" under NCCL, "cpu" under gloo)."""
+    import torch
+    vals = list(vals)
+    if dist is None:
+        return vals, e2e
+    t = torch.tensor([vals[0], vals[2]], dtype=torch.float64, device=device)
+    dist.all_reduce(t)
+    mx = torch.tensor([vals[1]], dtype=torch.float64, device=device)
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    vals = [t[0].item(), mx.item(), t[1].item()]
+    if e2e:
+        e2e = list(e2e)
+        t2 = torch.tensor([e2e[0]], dtype=torch.float64, device=device)
+        dist.all_reduce(t2)
+        m2 = torch.tensor([e2e[1]], dtype=torch.float64, device=device)
+        dist.all_reduce(m2, op=dist.ReduceOp.MAX)
+        e2e[0], e2e[1] = t2.item(), m2.item()
+    return vals, e2e
+
+
 # ------------------------------------------------------------------ GPU arm
 def run_ours(args, rank, world, local):
     import numpy as np
@@ -311,20 +336,7 @@ def run_ours(args, rank, world, local):
         d2h = 8 * int(nodes) + 8 * nbody + 32 * len(cs)                 # psi, body psi, solve records
         e2e = [e2e_units, e2e_el, h2d, d2h]
 
-    # whole-job aggregation: units summed over ranks, time = max over ranks
-    vals = [dof_iters, elapsed, solves]
-    if dist:
-        t = torch.tensor([dof_iters, solves], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t)
-        mx = torch.tensor([elapsed], dtype=torch.float64, device="cuda")
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        vals = [t[0].item(), mx.item(), t[1].item()]
-        if e2e:
-            t2 = torch.tensor([e2e[0]], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t2)
-            m2 = torch.tensor([e2e[1]], dtype=torch.float64, device="cuda")
-            dist.all_reduce(m2, op=dist.ReduceOp.MAX)
-            e2e[0], e2e[1] = t2.item(), m2.item()
+    vals, e2e = aggregate([dof_iters, elapsed, solves], e2e, dist, "cuda")
     if rank != 0:
         if dist:
             dist.destroy_process_group()
