@@ -207,6 +207,15 @@ pf_status pf_psi_solve_schur(pf_batch* b, double U, const pf_solve_opts* opts, d
 /* Device-event timing of the last pf_psi_solve on this handle. */
 pf_status pf_last_timing(const pf_batch* b, pf_timing* out);
 
+/* Test hook for failure detection without a GPU fault.  With enable = 1, every fused CG
+   launch of later solves on this handle has CTA 0 skip the copies of its first tile and
+   caps each mbarrier wait at 1024 polls, so the consumer warps' bounded wait on that
+   stage gives up: the kernel records the failure in a device flag, drains the copies it
+   did issue, returns, and the solve returns PF_ETIMEOUT.  No wait is unbounded, nothing
+   faults and the CUDA context stays usable.  The handle's iterate is then undefined:
+   destroy it.  enable = 0 restores normal launches.  PF_EINVAL for a NULL handle. */
+pf_status pf_test_wait_timeout(pf_batch* b, int enable);
+
 /* Surface tangential velocity on body `body` of variant v after a solve
    (section "Velocity Field and Surface Tangential Velocity"): for every boundary edge
    (edge of an active cell whose end nodes are distinct BODY nodes of this body),

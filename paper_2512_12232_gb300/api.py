@@ -173,6 +173,10 @@ class Mesh:
         check(L.load().pf_last_timing(self.handle, C.byref(t)))
         return {k: getattr(t, k) for k, _ in L.pf_timing._fields_}
 
+    def test_wait_timeout(self, enable=True):
+        """Test hook: later solves make a bounded device wait give up (PF_ETIMEOUT)."""
+        check(L.load().pf_test_wait_timeout(self.handle, int(bool(enable))))
+
 
 def mesh_build(grid, bodies, sweeps, bc=(0, 0, 0, 0)) -> Mesh:
     """One variant: grid = (x0, x1, y0, y1, nx, ny), bodies = rows of (cx, cy, r)."""

@@ -145,6 +145,8 @@ struct Batch {
   cudaStream_t graph_stream[2] = {nullptr, nullptr};
   int graph_chunk[2] = {0, 0};
   int graph_stages[2] = {0, 0};
+  int graph_drop[2] = {0, 0};
+  int test_drop = 0;                 // test hook (pf_test_wait_timeout): see the header
   static constexpr int N_EV = 12;    // 0-5: solve-level timing, 6-11: two chunk slots x 3
   cudaEvent_t ev[N_EV] = {};
   pf_timing timing{};

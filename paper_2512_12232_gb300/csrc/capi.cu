@@ -255,6 +255,14 @@ pf_status pf_psi_solve_schur(pf_batch* h, double U, const pf_solve_opts* opts, d
   });
 }
 
+pf_status pf_test_wait_timeout(pf_batch* h, int enable) {
+  return guarded([&]() -> pf_status {
+    if (!h) throw Error{PF_EINVAL, "NULL handle"};
+    ((Batch*)h)->test_drop = enable ? 1 : 0;
+    return PF_OK;
+  });
+}
+
 pf_status pf_last_timing(const pf_batch* h, pf_timing* out) {
   return guarded([&]() -> pf_status {
     const Batch* b = (const Batch*)h;

@@ -49,6 +49,8 @@ struct CGArgs {
   const uint8_t* tile_gen;  // per fused-CG tile: stored coefficients needed
   long long Rtot;           // rows of the batch's 2-D node arrays
   int* err;                 // set to 1 if a bounded wait gave up
+  int poll_limit;           // polls of one mbarrier wait before it gives up
+  int test_drop;            // test hook: CTA 0 never issues the copies of its first tile
 };
 
 template <typename T>
@@ -458,12 +460,16 @@ __global__ void __launch_bounds__(NTC, sizeof(T) == 4 ? 2 : 1) k_cg(CGArgs<T> a,
       if (lane == 0) {
         for (int t = t0; t < t1; ++t, ++q) {
           const int s = q % NS, use = q / NS;
-          if (use > 0 && !mbar_wait(&empty[s], (use - 1) & 1)) {
+          if (use > 0 && !mbar_wait(&empty[s], (use - 1) & 1, a.poll_limit)) {
             atomicExch(a.err, 1);
             s_abort = 1;
             break;
           }
           if (*(volatile int*)&s_abort) break;
+          if (a.test_drop && blockIdx.x == 0 && q == 0) {
+            s_issued = q + 1;                     // the consumers' wait on this stage must give up
+            continue;
+          }
           fence_proxy_async_smem();
           const int2 tij = a.sc.tile_ij[t];
           const int fl = a.tile_gen[t];
@@ -513,7 +519,7 @@ __global__ void __launch_bounds__(NTC, sizeof(T) == 4 ? 2 : 1) k_cg(CGArgs<T> a,
         unsigned char* st = smem + s * L::stage_bytes;
         T* pt = reinterpret_cast<T*>(smem + L::off_ptile + (q & 1) * L::ptile_bytes);
         uint8_t* tt = reinterpret_cast<uint8_t*>(smem + L::off_ttile + (q & 1) * L::ttile_bytes);
-        const bool ok = mbar_wait(&full[s], (q / NS) & 1);
+        const bool ok = mbar_wait(&full[s], (q / NS) & 1, a.poll_limit);
         const int2 ij = s_tij[s];
         const bool plain = (s_tfl[s] & 2) != 0;
         const State4<T>* Ss = reinterpret_cast<const State4<T>*>(st + L::off_s);
@@ -695,7 +701,7 @@ __global__ void __launch_bounds__(NTC, sizeof(T) == 4 ? 2 : 1) k_cg(CGArgs<T> a,
     if (s_abort) {
       // drain loads issued but not consumed (bounded), then leave
       if (tid == 0)
-        for (int k = q; k < s_issued; ++k) mbar_wait(&full[k % NS], (k / NS) & 1);
+        for (int k = q; k < s_issued; ++k) mbar_wait(&full[k % NS], (k / NS) & 1, a.poll_limit);
       __syncthreads();
       return;
     }
@@ -1398,6 +1404,8 @@ static void fill_cg_args(Batch& b, CGArgs<T>& a, State4<T>* const st[2], T* sb, 
   a.bq = b.bq;
   a.B = std::max(1, b.B);
   a.n_done = b.n_done;
+  a.poll_limit = b.test_drop ? 1024 : MBAR_POLL_LIMIT;
+  a.test_drop = b.test_drop;
 }
 
 template <typename T>
@@ -1464,9 +1472,11 @@ static void launch_resid_only(Batch& b, int precision, cudaStream_t s) {
 }
 
 static cudaGraphExec_t get_graph(Batch& b, int precision, int chunk) {
-  if (b.graph[precision] && b.graph_chunk[precision] == chunk && b.graph_stages[precision] == b.cg_stages)
+  if (b.graph[precision] && b.graph_chunk[precision] == chunk && b.graph_stages[precision] == b.cg_stages &&
+      b.graph_drop[precision] == b.test_drop)
     return b.graph[precision];
   b.graph_stages[precision] = b.cg_stages;
+  b.graph_drop[precision] = b.test_drop;
   cg_config(b, precision, b.cg_stages);   // schedule set-up synchronises: do it before capturing
   if (b.graph[precision]) {
     cudaGraphExecDestroy(b.graph[precision]);

@@ -60,10 +60,10 @@ __device__ __forceinline__ void named_bar_sync(int id, int count) {
 }
 
 // Poll the barrier until the phase with the given parity has completed, at most
-// MBAR_POLL_LIMIT times; returns false if it gave up.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// `limit` times; returns false if it gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int limit = MBAR_POLL_LIMIT) {
   const uint32_t a = smem_u32(bar);
-  for (int it = 0; it < MBAR_POLL_LIMIT; ++it) {
+  for (int it = 0; it < limit; ++it) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred P1;\n\t"
