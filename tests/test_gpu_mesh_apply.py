@@ -85,3 +85,21 @@ def test_invalid_inputs_rejected(api):
         api.mesh_build((-4.0, 4.0, -3.0, 3.0, 32, 24), [[2.8, 0.0, 1.0]], 5)
     with pytest.raises(PfError, match="EINVAL"):
         api.mesh_build((-4.0, 4.0, -3.0, 3.0, 1, 24), [], 5)
+
+
+def test_inverted_cell_is_reported_and_solve_refused(api):
+    """A coarse grid with no smoothing where one projected boundary node folds a cell
+    (the oracle's minimum det J over the Gauss points is about -1.45e-3): the GPU mesh
+    reports the same minimum det J and the solve refuses with PF_EMESH_INVALID."""
+    from oracle import mesh as OM, element as OE
+    from paper_2512_12232_gb300._lib import PfError
+    grid = (-4.0, 4.0, -2.0, 2.0, 32, 16)
+    body = [[-0.91, -0.45, 0.67]]
+    m = OM.build_mesh(grid, np.array(body), 0, (0, 0, 0, 0))
+    _, dm = OE.q4_stiffness(OM.cell_coords(m)[m.active])
+    assert dm.min() < 0
+    with api.mesh_build(grid, body, 0) as g:
+        st = g.stats(0)
+        assert st["min_detJ"] == pytest.approx(dm.min(), rel=1e-9)
+        with pytest.raises(PfError, match="EMESH_INVALID"):
+            api.psi_solve(g, U=1.0, tol=1e-8, precision=api.PF_MIXED)
