@@ -432,6 +432,20 @@ __global__ void __launch_bounds__(NTC, sizeof(T) == 4 ? 2 : 1) k_cg(CGArgs<T> a,
   const long long plane = a.m.Vtot;
   constexpr int W = CTX + 2;
   constexpr int NH = 2 * W + 2 * CTY;             // halo ring positions
+  static_assert(NH <= NT, "one halo position per consumer thread at most");
+  // this thread's halo-ring position (the same for every tile): li | lj << 8, or -1
+  int hpos = -1;
+  {
+    const int h = warp + (NT / 32) * lane;
+    if (!producer && h < NH) {
+      int li, lj;
+      if (h < W) { li = h; lj = 0; }
+      else if (h < 2 * W) { li = h - W; lj = CTY + 1; }
+      else if (h < 2 * W + CTY) { li = 0; lj = 1 + (h - 2 * W); }
+      else { li = CTX + 1; lj = 1 + (h - 2 * W - CTY); }
+      hpos = li | (lj << 8);
+    }
+  }
   if (tid == 0) {
     for (int k = 0; k < NS; ++k) {
       mbar_init(&full[k], 1);
@@ -543,12 +557,8 @@ __global__ void __launch_bounds__(NTC, sizeof(T) == 4 ? 2 : 1) k_cg(CGArgs<T> a,
             tg4[u] = K_FREE;
             bs4[u] = -1;
           }
-          for (int h = warp + (NT / 32) * lane; h < NH; h += NT) {
-            int li, lj;
-            if (h < W) { li = h; lj = 0; }
-            else if (h < 2 * W) { li = h - W; lj = CTY + 1; }
-            else if (h < 2 * W + CTY) { li = 0; lj = 1 + (h - 2 * W); }
-            else { li = CTX + 1; lj = 1 + (h - 2 * W - CTY); }
+          if (hpos >= 0) {
+            const int li = hpos & 255, lj = hpos >> 8;
             const State4<T> o = staged_state<T>(Ss, li, lj);
             pt[lj * W + li] = next_p(next_r(o.r, o.q, alpha), o.p, beta);
           }
@@ -579,12 +589,8 @@ __global__ void __launch_bounds__(NTC, sizeof(T) == 4 ? 2 : 1) k_cg(CGArgs<T> a,
             tt[lj * W + li] = tg;
             rn4[u] = rn; pn4[u] = pn; xn4[u] = xn; tg4[u] = tg;
           }
-          for (int h = warp + (NT / 32) * lane; h < NH; h += NT) {
-            int li, lj;
-            if (h < W) { li = h; lj = 0; }
-            else if (h < 2 * W) { li = h - W; lj = CTY + 1; }
-            else if (h < 2 * W + CTY) { li = 0; lj = 1 + (h - 2 * W); }
-            else { li = CTX + 1; lj = 1 + (h - 2 * W - CTY); }
+          if (hpos >= 0) {
+            const int li = hpos & 255, lj = hpos >> 8;
             const int i = ij.x - 1 + li, j = ij.y - 1 + lj;
             uint8_t ht = K_INACT;
             T hp = T(0);
@@ -618,7 +624,7 @@ __global__ void __launch_bounds__(NTC, sizeof(T) == 4 ? 2 : 1) k_cg(CGArgs<T> a,
           for (int r = 0; r < STRIP + 2; ++r) {
             const int lj = row_lo + r;
             win[r][0] = pt[lj * W + li - 1];
-            win[r][1] = pt[lj * W + li];
+            win[r][1] = (r >= 1 && r <= STRIP) ? pn4[r - 1] : pt[lj * W + li];   // own strip in registers
             win[r][2] = pt[lj * W + li + 1];
           }
           T yq[STRIP];
@@ -649,7 +655,7 @@ __global__ void __launch_bounds__(NTC, sizeof(T) == 4 ? 2 : 1) k_cg(CGArgs<T> a,
           for (int r = 0; r < STRIP + 2; ++r) {
             const int lj = row_lo + r;
             win[r][0] = pt[lj * W + li - 1];
-            win[r][1] = pt[lj * W + li];
+            win[r][1] = (r >= 1 && r <= STRIP) ? pn4[r - 1] : pt[lj * W + li];   // own strip in registers
             win[r][2] = pt[lj * W + li + 1];
           }
 #pragma unroll
