@@ -117,6 +117,7 @@ typedef struct pf_timing {
     double cg_bytes_per_launch;  /* algorithmic HBM bytes of one fused CG launch, averaged over the
                                     launches of the solve (variants already converged move nothing) */
     long long kernel_launches;   /* kernels launched by this handle since it was built (mesh + solves) */
+    int cg_stages;               /* pipeline depth of the fused CG kernel in the last solve (2..4) */
 } pf_timing;
 
 typedef struct pf_batch pf_batch;   /* opaque: one or more mesh variants and their solver state */

@@ -45,7 +45,7 @@ class pf_timing(C.Structure):
     _fields_ = [("cg_kernel_ms", C.c_double), ("cg_launches", C.c_longlong),
                 ("residual_kernel_ms", C.c_double), ("residual_launches", C.c_longlong),
                 ("solve_ms", C.c_double), ("cg_bytes_per_launch", C.c_double),
-                ("kernel_launches", C.c_longlong)]
+                ("kernel_launches", C.c_longlong), ("cg_stages", C.c_int)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)

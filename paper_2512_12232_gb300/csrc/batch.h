@@ -91,6 +91,8 @@ struct Batch {
   CgConfig cg_cfg[2][3];             // [precision][stages - 2]
   int cg_stages = 2;
   bool cg_tune = false;              // re-balance the fused-CG schedule from timed launches
+  int tuned_stages[2] = {2, 2};     // pipeline depth picked by the autotuner, per precision
+  bool stages_tuned[2] = {false, false};
   int nsm = 0;
   long long Rtot = 0;                // rows of the batch's 2-D node arrays (Vtot / P)
   int P = 0;                         // common row pitch

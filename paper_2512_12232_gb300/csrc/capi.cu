@@ -269,6 +269,7 @@ pf_status pf_last_timing(const pf_batch* h, pf_timing* out) {
     if (!b || !out) throw Error{PF_EINVAL, "NULL argument"};
     *out = b->timing;
     out->kernel_launches = b->launches;
+    out->cg_stages = b->cg_stages;
     return PF_OK;
   });
 }

@@ -1330,7 +1330,8 @@ void ensure_solver_memory(Batch& b, int precision) {
     PF_CUDA(cudaMemsetAsync(b.sb64, 0, 4 * B * sizeof(double), b.stream));
     PF_CUDA(cudaMemsetAsync(b.sb32, 0, 4 * B * sizeof(float), b.stream));
     b.bnorm2_unit.assign(b.nv, -1.0);
-    for (int k = 0; k < Batch::N_EV; ++k) PF_CUDA(cudaEventCreate(&b.ev[k]));
+    for (int k = 0; k < Batch::N_EV; ++k)
+      if (!b.ev[k]) PF_CUDA(cudaEventCreate(&b.ev[k]));
   }
   if (precision == PF_FP64 && !b.st64[0]) {
     for (int k = 0; k < 2; ++k) b.st64[k] = (State4<double>*)dev_alloc(b, V * sizeof(State4<double>));
@@ -1522,8 +1523,8 @@ pf_status solve_core(Batch& b, double U, const pf_solve_opts& o, double* dev_psi
   const int prec = o.precision;
   ensure_solver_memory(b, prec);
   {
-    const char* e = getenv("PFQ4_CG_STAGES");
-    const int ns = e ? atoi(e) : 2;
+    const char* e = getenv("PFQ4_CG_STAGES");      // a fixed pipeline depth, else the tuned one
+    const int ns = e ? atoi(e) : b.tuned_stages[prec];
     b.cg_stages = (ns >= 2 && ns <= 4) ? ns : 2;
     const char* tu = getenv("PFQ4_CG_TUNE");   // overrides the option when set
     b.cg_tune = tu ? atoi(tu) != 0 : o.tune_schedule != 0;
@@ -1573,14 +1574,45 @@ pf_status solve_core(Batch& b, double U, const pf_solve_opts& o, double* dev_psi
     for (auto& H : b.hv) nodes += H.stats.n_nodes;
     chunk = nodes > (8LL << 20) ? 16 : (nodes > (1LL << 20) ? 64 : 256);
   }
-  cudaGraphExec_t ex = get_graph(b, prec, chunk);
   if (!b.h_poll) PF_CUDA(cudaMallocHost(&b.h_poll, 4 * sizeof(int)));
   int* hdone = b.h_poll;
   double cg_ms = 0, res_ms = 0;
   long long launches = 0, rlaunches = 1;
-  // Optional timing-driven re-balance of the schedule on the first tuned solve of the
-  // handle: a few of this solve's CG iterations run as timed launches, then the cut
-  // points move so that every CTA's measured tile time evens out.
+  // Optional autotuning on the first tuned solve of the handle, with this solve's own CG
+  // iterations run as timed launches: (1) the pipeline depth NS in {2, 3, 4} with the
+  // shortest launch (each configuration has its own grid and schedule), then (2) a
+  // re-balance of that configuration's cut points so that every CTA's measured tile
+  // time evens out.
+  auto timed_launches = [&](int n, bool per_cta) {
+    PF_CUDA(cudaEventRecord(b.ev[0], s));
+    launch_cg_chunk(b, prec, n, s, per_cta);
+    PF_CUDA(cudaEventRecord(b.ev[1], s));
+    PF_CUDA(cudaMemcpyAsync(hdone, b.n_done, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    PF_CUDA(cudaStreamSynchronize(s));
+    float ms = 0;
+    PF_CUDA(cudaEventElapsedTime(&ms, b.ev[0], b.ev[1]));
+    cg_ms += ms;
+    launches += n;
+    if (hdone[1]) throw Error{PF_ETIMEOUT, "a bounded wait in the CG kernel gave up (TMA tile not delivered)"};
+    return (double)ms / n;
+  };
+  const bool tune = b.cg_tune && o.k_max > 0 && !getenv("PFQ4_CG_STAGES");
+  if (tune && !b.stages_tuned[prec]) {
+    double best = 1e300;
+    int best_ns = b.cg_stages;
+    for (int ns = 2; ns <= 4; ++ns) {
+      b.cg_stages = ns;
+      CgConfig& c = cg_config(b, prec, ns);
+      c.active.assign(b.nv, 1);
+      cg_sched_write(b, c);
+      const double per = timed_launches(CG_TUNE_LAUNCHES, false);
+      if (per < best) { best = per; best_ns = ns; }
+    }
+    b.cg_stages = best_ns;
+    b.tuned_stages[prec] = best_ns;
+    b.stages_tuned[prec] = true;
+  }
+  cudaGraphExec_t ex = get_graph(b, prec, chunk);
   CgConfig& cc = cg_config(b, prec, b.cg_stages);
   if (cc.active.size() != (size_t)b.nv || std::find(cc.active.begin(), cc.active.end(), 0) != cc.active.end()) {
     cc.active.assign(b.nv, 1);                   // a solve starts with every variant running
@@ -1589,18 +1621,9 @@ pf_status solve_core(Batch& b, double U, const pf_solve_opts& o, double* dev_psi
   if (b.cg_tune && o.k_max > 0 && (long long)cc.tile_cost.size() >= 2LL * cc.G) {
     for (; cc.tune_rounds < CG_TUNE_ROUNDS; ++cc.tune_rounds) {
       PF_CUDA(cudaMemsetAsync(cc.d_cta_ns, 0, cc.G * sizeof(unsigned long long), s));
-      PF_CUDA(cudaEventRecord(b.ev[0], s));
-      launch_cg_chunk(b, prec, CG_TUNE_LAUNCHES, s, true);
-      PF_CUDA(cudaEventRecord(b.ev[1], s));
+      timed_launches(CG_TUNE_LAUNCHES, true);
       std::vector<unsigned long long> tns(cc.G);
-      PF_CUDA(cudaMemcpyAsync(tns.data(), cc.d_cta_ns, cc.G * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
-      PF_CUDA(cudaMemcpyAsync(hdone, b.n_done, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
-      PF_CUDA(cudaStreamSynchronize(s));
-      float ms = 0;
-      PF_CUDA(cudaEventElapsedTime(&ms, b.ev[0], b.ev[1]));
-      cg_ms += ms;
-      launches += CG_TUNE_LAUNCHES;
-      if (hdone[1]) throw Error{PF_ETIMEOUT, "a bounded wait in the CG kernel gave up (TMA tile not delivered)"};
+      PF_CUDA(cudaMemcpy(tns.data(), cc.d_cta_ns, cc.G * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
       cg_rebalance(b, cc, tns);
     }
   }
