@@ -337,6 +337,18 @@ def run_ours(args, rank, world, local):
         e2e = [e2e_units, e2e_el, h2d, d2h]
 
     vals, e2e = aggregate([dof_iters, elapsed, solves], e2e, dist, "cuda")
+
+    # c3: bandwidth of the stand-alone Q4 operator (no conversions, no body sums), FP32 and FP64
+    apply_sweep = None
+    if args.config == "c3" and rank == 0:
+        g = api.batch_build(cs)
+        hbm = peaks().get("hbm_gbs") or 6800.0
+        apply_sweep = {}
+        for name, pr in (("fp32", api.PF_MIXED), ("fp64", api.PF_FP64)):
+            us, by = g.apply_timing(pr, reps=50)
+            apply_sweep[name] = {"us_per_apply": us, "algorithmic_bytes": by, "GB/s": by / us / 1e3,
+                                 "frac_of_measured_hbm": by / us / 1e3 / hbm}
+        g.close()
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -378,6 +390,7 @@ def run_ours(args, rank, world, local):
         "iters_per_variant": iters if len(iters) <= 8 else {"min": min(iters), "max": max(iters)},
         "copfi": [cp for cp, _ in records[-1][1]],
         "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": int(launches),
+        **({"apply_sweep": apply_sweep} if apply_sweep else {}),
         "e2e": ({"value": e2e[0] / e2e[1], "unit": UNIT, "h2d_bytes_per_step": e2e[2],
                  "d2h_bytes_per_step": e2e[3]} if e2e else None),
     }

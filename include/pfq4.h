@@ -205,6 +205,17 @@ pf_status pf_psi_solve(pf_batch* b, double U, const pf_solve_opts* opts, double*
 pf_status pf_psi_solve_schur(pf_batch* b, double U, const pf_solve_opts* opts, double* dev_psi,
                              double* body_psi, pf_solve_info* info, void* stream);
 
+/* Bandwidth measurement of the stand-alone operator (section "Matrix-Free Conjugate
+   Gradient ..."; the same node-centric Q4 gather as pf_apply): `reps` back-to-back
+   applications (after 3 untimed ones) on the handle's internal padded vectors, with no
+   layout conversion and no body sums, timed with CUDA events on `stream`.  Outputs the
+   mean microseconds per application and its algorithmic bytes (p read and y written at
+   every node, one tag byte per node, six coefficients of every cell whose coefficients in
+   this precision differ from the closed-form rectangle's).  PF_EINVAL for a NULL handle,
+   reps < 1 or an invalid precision. */
+pf_status pf_apply_timing(pf_batch* b, int precision, int reps, double* us_per_apply, double* bytes_per_apply,
+                          void* stream);
+
 /* Device-event timing of the last pf_psi_solve on this handle. */
 pf_status pf_last_timing(const pf_batch* b, pf_timing* out);
 

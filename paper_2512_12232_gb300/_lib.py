@@ -68,6 +68,7 @@ _SIGS = {
     "pf_psi_solve": (C.c_int, [P, C.c_double, C.POINTER(pf_solve_opts), P, P, P, P]),
     "pf_psi_solve_schur": (C.c_int, [P, C.c_double, C.POINTER(pf_solve_opts), P, P, P, P]),
     "pf_test_wait_timeout": (C.c_int, [P, C.c_int]),
+    "pf_apply_timing": (C.c_int, [P, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), P]),
     "pf_last_timing": (C.c_int, [P, C.POINTER(pf_timing)]),
     "pf_surface_velocity": (C.c_int, [P, C.c_int, C.c_int, P, P, C.c_int, C.POINTER(C.c_int), P]),
     "pf_copfi": (C.c_int, [P, C.c_int, C.c_int, C.c_int, C.c_double, C.POINTER(C.c_double),

@@ -173,6 +173,12 @@ class Mesh:
         check(L.load().pf_last_timing(self.handle, C.byref(t)))
         return {k: getattr(t, k) for k, _ in L.pf_timing._fields_}
 
+    def apply_timing(self, precision=PF_MIXED, reps=100):
+        """(microseconds, algorithmic bytes) of one stand-alone operator application."""
+        us, by = C.c_double(), C.c_double()
+        check(L.load().pf_apply_timing(self.handle, int(precision), int(reps), C.byref(us), C.byref(by), _stream()))
+        return us.value, by.value
+
     def test_wait_timeout(self, enable=True):
         """Test hook: later solves make a bounded device wait give up (PF_ETIMEOUT)."""
         check(L.load().pf_test_wait_timeout(self.handle, int(bool(enable))))

@@ -178,6 +178,7 @@ void export_tags(Batch& b, int v, int8_t* kind, int32_t* body);
 // solver.cu
 void make_schedule(Batch& b);
 void ensure_solver_memory(Batch& b, int precision);
+void apply_timing(Batch& b, int precision, int reps, double* us, double* bytes);
 void apply_operator(Batch& b, int precision, const double* dev_p, double* dev_y, double* body_sums);
 pf_status psi_solve(Batch& b, double U, const pf_solve_opts& o, double* dev_psi, double* body_psi,
                     pf_solve_info* info);

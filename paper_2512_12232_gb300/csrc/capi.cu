@@ -255,6 +255,17 @@ pf_status pf_psi_solve_schur(pf_batch* h, double U, const pf_solve_opts* opts, d
   });
 }
 
+pf_status pf_apply_timing(pf_batch* h, int precision, int reps, double* us, double* bytes, void* stream) {
+  return guarded([&]() -> pf_status {
+    Batch* b = (Batch*)h;
+    if (!b) throw Error{PF_EINVAL, "NULL handle"};
+    if (precision != PF_FP64 && precision != PF_MIXED) throw Error{PF_EINVAL, "invalid precision"};
+    bind(b, stream);
+    apply_timing(*b, precision, reps, us, bytes);
+    return PF_OK;
+  });
+}
+
 pf_status pf_test_wait_timeout(pf_batch* h, int enable) {
   return guarded([&]() -> pf_status {
     if (!h) throw Error{PF_EINVAL, "NULL handle"};

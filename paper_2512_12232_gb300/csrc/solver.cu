@@ -318,9 +318,10 @@ __device__ __forceinline__ T q4_row_rect(const T (&p)[3][3], const T* kr) {
 // Row of the operator at one node from its 3x3 neighbourhood p[3][3] (p[1][1] = the
 // node, first index = row j-1, j, j+1, second = column i-1, i, i+1) and the tags of its
 // four cells: c0 = (i, j), c1 = (i-1, j), c2 = (i-1, j-1), c3 = (i, j-1).  Displaced
-// cells read their six coefficients from the staged planes (FP32) or global memory
-// (FP64); undisplaced cells use the closed-form rectangle constants kr.
-template <typename T>
+// cells read their six coefficients from the staged boxes (STAGED: the fused kernel's
+// FP32 path) or from the global planes; undisplaced cells use the closed-form rectangle
+// constants kr.
+template <typename T, bool STAGED = sizeof(T) == 4>
 __device__ __forceinline__ T q4_row_nb(const T (&p)[3][3], uint8_t c0, uint8_t c1, uint8_t c2, uint8_t c3,
                                        const T* ks, int kcol, int krow, long long n, int P,
                                        const T* __restrict__ Kg, long long plane, const T* kr) {
@@ -335,7 +336,7 @@ __device__ __forceinline__ T q4_row_nb(const T (&p)[3][3], uint8_t c0, uint8_t c
     return q4_row_rect<T>(p, kr);
   // coefficient m of the cell whose corner 0 is at box column kc, box row kr_, global index g
   auto coef = [&](int m, int kr_, int kc, long long g) -> T {
-    if constexpr (L::kTmaK) {
+    if constexpr (STAGED) {
       // two boxes of [CTY+1][6*KHALF], cells interleaved (6 coefficients per cell)
       const int half = kc >= L::KHALF;
       return ks[half * (L::kbox_bytes / (int)sizeof(T)) + kr_ * (6 * L::KHALF) + (kc - half * L::KHALF) * 6 + m];
@@ -976,42 +977,109 @@ __global__ void k_from_padded(const DevVariant* var, const long long* lbase, con
 }
 
 // one tile per CTA: y = A p at FREE and BODY nodes (p used as given everywhere)
+// Stand-alone operator y = A p on the padded vectors (pf_apply, pf_apply_timing): one
+// 64x16 tile of the fused-CG tile list per CTA.  The p window with its one-node halo
+// is read as an aligned superset (columns i0-4 .. i0+67) with 16-byte loads, and the tag
+// bytes of non-plain tiles as aligned 4-byte words; every load of the window is issued
+// before any is stored to shared memory, and elements off the grid are set to 0.  Each
+// thread then forms the rows of a 4-node vertical strip exactly as the fused kernel
+// does, reading stored coefficients from the global planes for the cells that need
+// them.  Nodes without an operator row get 0; nodes outside the grid are not written.
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { using type = float4; static constexpr int n = 4; };
+template <> struct Vec16<double> { using type = double2; static constexpr int n = 2; };
+
 template <typename T>
-__global__ void __launch_bounds__(NT) k_apply(MeshDev m, const int* tile_var, const int2* tile_ij, const T* p, T* y) {
-  __shared__ T ps[TY + 2][SW];
-  __shared__ uint8_t ts[TY + 2][SW];
-  const long long t = blockIdx.x;
-  const int v = tile_var[t];
-  const DevVariant& V = m.var[v];
+__global__ void __launch_bounds__(NT) k_apply(MeshDev m, const int* tile_var, const int2* tile_ij,
+                                              const uint8_t* tile_flags, const T* __restrict__ p, T* __restrict__ y) {
+  using V16 = typename Vec16<T>::type;
+  constexpr int VN = Vec16<T>::n;                 // elements per 16-byte load
+  constexpr int AW = CTX + 8;                     // window row: columns i0-4 .. i0+CTX+3
+  constexpr int H = CTY + 2;
+  constexpr int NV = AW / VN;                     // 16-byte loads per row
+  constexpr int NLP = (H * NV + NT - 1) / NT;
+  constexpr int NW = AW / 4;                      // tag words per row
+  constexpr int NLT = (H * NW + NT - 1) / NT;
+  __shared__ __align__(16) T ps[H * AW];
+  __shared__ __align__(16) uint32_t ts32[H * NW];
+  const uint8_t* ts = reinterpret_cast<const uint8_t*>(ts32);
+  const int t = blockIdx.x;
+  const DevVariant& V = m.var[tile_var[t]];
   const int2 ij = tile_ij[t];
+  const bool plain = (tile_flags[t] & (sizeof(T) == 4 ? 8 : 4)) != 0;
   const int tid = linear_tid();
-  const int i = ij.x + threadIdx.x, j = ij.y + threadIdx.y;
-  const bool in = (i <= V.nx) && (j <= V.ny);
-  const long long n = V.base + (long long)j * V.P + i;
-  const uint8_t tg = in ? m.tag[n] : K_INACT;
-  ps[threadIdx.y + 1][threadIdx.x + 1] = in ? p[n] : T(0);
-  ts[threadIdx.y + 1][threadIdx.x + 1] = tg;
-  if (tid < NHALO) {
-    int li, lj;
-    halo_pos(tid, li, lj);
-    const int hi = ij.x - 1 + li, hj = ij.y - 1 + lj;
-    uint8_t ht = K_INACT;
-    T hp = T(0);
-    if (hi >= 0 && hj >= 0 && hi <= V.nx && hj <= V.ny) {
-      const long long hn = V.base + (long long)hj * V.P + hi;
-      ht = m.tag[hn];
-      hp = p[hn];
+  const long long base = V.base;
+  const int P = V.P, nx = V.nx, ny = V.ny;
+  // Loads start at multiples of 4 columns inside a row whose pitch is a multiple of 32,
+  // so none crosses the row end; rows or loads wholly off the grid are not read.
+  V16 pv[NLP];
+  uint32_t tv[NLT];
+#pragma unroll
+  for (int k = 0; k < NLP; ++k) {
+    const int q = tid + k * NT;
+    const int w = q % NV, lj = q / NV;
+    const int i = ij.x - 4 + VN * w, j = ij.y - 1 + lj;
+    const bool in = q < H * NV && j >= 0 && j <= ny && i + VN - 1 >= 0 && i <= nx;
+    V16 z;
+    memset(&z, 0, sizeof(z));
+    pv[k] = in ? __ldg(reinterpret_cast<const V16*>(p + base + (long long)j * P + i)) : z;
+  }
+#pragma unroll
+  for (int k = 0; k < NLT; ++k) {
+    const int q = tid + k * NT;
+    const int w = q % NW, lj = q / NW;
+    const int i = ij.x - 4 + 4 * w, j = ij.y - 1 + lj;
+    const bool in = !plain && q < H * NW && j >= 0 && j <= ny && i >= 0 && i <= nx;
+    tv[k] = in ? __ldg(reinterpret_cast<const uint32_t*>(m.tag + base + (long long)j * P + i)) : 0u;
+  }
+#pragma unroll
+  for (int k = 0; k < NLP; ++k) {
+    const int q = tid + k * NT;
+    if (q < H * NV) {
+      const int w = q % NV;
+      const int i = ij.x - 4 + VN * w;
+      T e[VN];
+      memcpy(e, &pv[k], sizeof(e));
+#pragma unroll
+      for (int c = 0; c < VN; ++c)
+        if (i + c < 0 || i + c > nx) e[c] = T(0);
+      memcpy(&ps[q * VN], e, sizeof(e));
     }
-    ps[lj][li] = hp;
-    ts[lj][li] = ht;
+  }
+#pragma unroll
+  for (int k = 0; k < NLT; ++k) {
+    const int q = tid + k * NT;
+    if (q < H * NW) ts32[q] = tv[k];
   }
   __syncthreads();
-  if (!in) return;
-  const int kind = tg & KIND_MASK;
-  T out = T(0);
-  if (kind == K_FREE || kind == K_BODY)
-    out = q4_row<T>(ps, ts, threadIdx.x + 1, threadIdx.y + 1, n, V.P, kplane<T>(m), m.Vtot, krect<T>(V));
-  y[n] = out;
+  T kr[6];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) kr[c] = krect<T>(V)[c];
+  const int col = tid % CTX, row_lo = (tid / CTX) * STRIP;
+  const int i = ij.x + col;
+  if (i > nx) return;
+  // window node (li, lj) (li = i - i0 + 1) sits at column li + 3 of the stored rows
+#pragma unroll
+  for (int u = 0; u < STRIP; ++u) {
+    const int j = ij.y + row_lo + u;
+    if (j > ny) break;
+    const int c = col + 4, lj = 1 + row_lo + u;
+    const long long n = base + (long long)j * P + i;
+    const T nbh[3][3] = {{ps[(lj - 1) * AW + c - 1], ps[(lj - 1) * AW + c], ps[(lj - 1) * AW + c + 1]},
+                         {ps[lj * AW + c - 1], ps[lj * AW + c], ps[lj * AW + c + 1]},
+                         {ps[(lj + 1) * AW + c - 1], ps[(lj + 1) * AW + c], ps[(lj + 1) * AW + c + 1]}};
+    T out = T(0);
+    if (plain) {
+      out = q4_row_rect<T>(nbh, kr);
+    } else {
+      const uint8_t tg = ts[lj * AW + c];
+      const int kind = tg & KIND_MASK;
+      if (kind == K_FREE || kind == K_BODY)
+        out = q4_row_nb<T, false>(nbh, tg, ts[lj * AW + c - 1], ts[(lj - 1) * AW + c - 1], ts[(lj - 1) * AW + c],
+                                  nullptr, 0, 0, n, P, kplane<T>(m), m.Vtot, kr);
+    }
+    y[n] = out;
+  }
 }
 
 // collapsed body rows: one CTA per global body, fixed-order sum
@@ -1365,13 +1433,57 @@ static double* body_sum_scratch(Batch& b) {
   return b.d_bsum;
 }
 
-void apply_operator(Batch& b, int precision, const double* dev_p, double* dev_y, double* body_sums) {
+static void ensure_apply_buffers(Batch& b) {
   if (!b.ap64[0]) {
     for (int k = 0; k < 2; ++k) {
       b.ap64[k] = (double*)dev_alloc(b, b.Vtot * sizeof(double));
       b.ap32[k] = (float*)dev_alloc(b, b.Vtot * sizeof(float));
     }
   }
+}
+
+template <typename T>
+static void launch_apply(Batch& b, const MeshDev& m, const T* p, T* y) {
+  k_apply<T><<<(unsigned)b.Tcg, NT, 0, b.stream>>>(m, b.tile_cg_var, b.tile_cg_ij, b.tile_cg_gen, p, y);
+}
+
+// Mean time of `reps` back-to-back stand-alone operator applications on the handle's
+// padded vectors (no layout conversion, no body sums) and their algorithmic bytes: p
+// read and y written at every node, one tag byte per node and the six stored
+// coefficients of every cell whose coefficients differ from the rectangle's in this
+// precision.
+void apply_timing(Batch& b, int precision, int reps, double* us, double* bytes) {
+  if (reps < 1) throw Error{PF_EINVAL, "reps must be >= 1"};
+  ensure_apply_buffers(b);
+  for (int k = 0; k < 2; ++k)
+    if (!b.ev[k]) PF_CUDA(cudaEventCreate(&b.ev[k]));
+  const MeshDev m = mesh_dev(b);
+  const size_t es = precision == PF_FP64 ? sizeof(double) : sizeof(float);
+  PF_CUDA(cudaMemsetAsync(precision == PF_FP64 ? (void*)b.ap64[0] : (void*)b.ap32[0], 0, b.Vtot * es, b.stream));
+  auto launch = [&]() {
+    if (precision == PF_FP64) launch_apply<double>(b, m, b.ap64[0], b.ap64[1]);
+    else launch_apply<float>(b, m, b.ap32[0], b.ap32[1]);
+  };
+  for (int k = 0; k < 3; ++k) launch();      // warm-up
+  PF_CUDA(cudaEventRecord(b.ev[0], b.stream));
+  for (int k = 0; k < reps; ++k) launch();
+  PF_CUDA(cudaEventRecord(b.ev[1], b.stream));
+  PF_CUDA(cudaGetLastError());
+  PF_CUDA(cudaEventSynchronize(b.ev[1]));
+  float ms = 0;
+  PF_CUDA(cudaEventElapsedTime(&ms, b.ev[0], b.ev[1]));
+  b.launches += 3 + reps;
+  double by = 0.0;
+  for (const HostVariant& H : b.hv) {
+    const long long ng = precision == PF_FP64 ? H.stats.n_general_cells : H.n_gen32_cells;
+    by += (2.0 * es + 1.0) * (double)H.stats.n_nodes + 6.0 * es * (double)ng;
+  }
+  if (us) *us = 1e3 * ms / reps;
+  if (bytes) *bytes = by;
+}
+
+void apply_operator(Batch& b, int precision, const double* dev_p, double* dev_y, double* body_sums) {
+  ensure_apply_buffers(b);
   long long* lb = lbase_cached(b);
   const MeshDev m = mesh_dev(b);
   const dim3 g2(512, b.nv);
@@ -1379,13 +1491,13 @@ void apply_operator(Batch& b, int precision, const double* dev_p, double* dev_y,
   if (precision == PF_FP64) {
     k_to_padded<double><<<g2, 256, 0, b.stream>>>(b.d_var, lb, dev_p, b.ap64[0]);
     PF_CUDA(cudaMemsetAsync(b.ap64[1], 0, b.Vtot * sizeof(double), b.stream));
-    k_apply<double><<<(unsigned)b.T, dim3(TX, TY), 0, b.stream>>>(m, b.tile_var, b.tile_ij, b.ap64[0], b.ap64[1]);
+    launch_apply<double>(b, m, b.ap64[0], b.ap64[1]);
     k_from_padded<double><<<g2, 256, 0, b.stream>>>(b.d_var, lb, b.ap64[1], dev_y);
     if (b.B) k_body_sums<double><<<b.B, dim3(TX, TY), 0, b.stream>>>(m, b.ap64[1], sums);
   } else {
     k_to_padded<float><<<g2, 256, 0, b.stream>>>(b.d_var, lb, dev_p, b.ap32[0]);
     PF_CUDA(cudaMemsetAsync(b.ap32[1], 0, b.Vtot * sizeof(float), b.stream));
-    k_apply<float><<<(unsigned)b.T, dim3(TX, TY), 0, b.stream>>>(m, b.tile_var, b.tile_ij, b.ap32[0], b.ap32[1]);
+    launch_apply<float>(b, m, b.ap32[0], b.ap32[1]);
     k_from_padded<float><<<g2, 256, 0, b.stream>>>(b.d_var, lb, b.ap32[1], dev_y);
     if (b.B) k_body_sums<float><<<b.B, dim3(TX, TY), 0, b.stream>>>(m, b.ap32[1], sums);
   }
