@@ -977,132 +977,108 @@ __global__ void k_from_padded(const DevVariant* var, const long long* lbase, con
 }
 
 // one tile per CTA: y = A p at FREE and BODY nodes (p used as given everywhere)
-// Stand-alone operator y = A p on the padded vectors (pf_apply, pf_apply_timing).
-// Persistent CTAs walk the fused-CG tile list (64x16 tiles) with a stride of the grid
-// size.  A tile's p window with its one-node halo is read as an aligned superset
-// (columns i0-4 .. i0+67) with 16-byte loads, and the tag bytes of non-plain tiles as
-// aligned 4-byte words, into registers; the loads of the next tile are in flight while
-// the current one is computed from a double-buffered shared window (elements off the
-// grid are set to 0).  Each thread forms the rows of a 4-node vertical strip exactly as
-// the fused kernel does, reading stored coefficients from the global planes for the
-// cells that need them.  Nodes without an operator row get 0; nodes outside the grid
-// are not written.
+// Stand-alone operator y = A p on the padded vectors (pf_apply, pf_apply_timing): one
+// 64x16 tile of the fused-CG tile list per CTA.  The p window with its one-node halo
+// is read as an aligned superset (columns i0-4 .. i0+67) with 16-byte loads, and the tag
+// bytes of non-plain tiles as aligned 4-byte words; every load of the window is issued
+// before any is stored to shared memory, and elements off the grid are set to 0.  Each
+// thread then forms the rows of a 4-node vertical strip exactly as the fused kernel
+// does, reading stored coefficients from the global planes for the cells that need
+// them.  Nodes without an operator row get 0; nodes outside the grid are not written.
 template <typename T> struct Vec16;
 template <> struct Vec16<float> { using type = float4; static constexpr int n = 4; };
 template <> struct Vec16<double> { using type = double2; static constexpr int n = 2; };
 
 template <typename T>
-struct ApplyWin {
+__global__ void __launch_bounds__(NT) k_apply(MeshDev m, const int* tile_var, const int2* tile_ij,
+                                              const uint8_t* tile_flags, const T* __restrict__ p, T* __restrict__ y) {
   using V16 = typename Vec16<T>::type;
-  static constexpr int VN = Vec16<T>::n;          // elements per 16-byte load
-  static constexpr int AW = CTX + 8;              // window row: columns i0-4 .. i0+CTX+3
-  static constexpr int H = CTY + 2;
-  static constexpr int NV = AW / VN;              // 16-byte loads per row
-  static constexpr int NLP = (H * NV + NT - 1) / NT;
-  static constexpr int NW = AW / 4;               // tag words per row
-  static constexpr int NLT = (H * NW + NT - 1) / NT;
+  constexpr int VN = Vec16<T>::n;                 // elements per 16-byte load
+  constexpr int AW = CTX + 8;                     // window row: columns i0-4 .. i0+CTX+3
+  constexpr int H = CTY + 2;
+  constexpr int NV = AW / VN;                     // 16-byte loads per row
+  constexpr int NLP = (H * NV + NT - 1) / NT;
+  constexpr int NW = AW / 4;                      // tag words per row
+  constexpr int NLT = (H * NW + NT - 1) / NT;
+  __shared__ __align__(16) T ps[H * AW];
+  __shared__ __align__(16) uint32_t ts32[H * NW];
+  const uint8_t* ts = reinterpret_cast<const uint8_t*>(ts32);
+  const int t = blockIdx.x;
+  const DevVariant& V = m.var[tile_var[t]];
+  const int2 ij = tile_ij[t];
+  const bool plain = (tile_flags[t] & (sizeof(T) == 4 ? 8 : 4)) != 0;
+  const int tid = linear_tid();
+  const long long base = V.base;
+  const int P = V.P, nx = V.nx, ny = V.ny;
+  // Loads start at multiples of 4 columns inside a row whose pitch is a multiple of 32,
+  // so none crosses the row end; rows or loads wholly off the grid are not read.
   V16 pv[NLP];
   uint32_t tv[NLT];
-  // Loads start at multiples of 4 columns inside a row whose pitch is a multiple of
-  // 32, so none crosses the row end; loads wholly off the grid are not issued.
-  __device__ __forceinline__ void load(const MeshDev& m, const DevVariant& V, int2 ij, bool plain, const T* p,
-                                       int tid) {
 #pragma unroll
-    for (int k = 0; k < NLP; ++k) {
-      const int q = tid + k * NT;
-      const int w = q % NV, lj = q / NV;
-      const int i = ij.x - 4 + VN * w, j = ij.y - 1 + lj;
-      const bool in = q < H * NV && j >= 0 && j <= V.ny && i + VN - 1 >= 0 && i <= V.nx;
-      V16 z;
-      memset(&z, 0, sizeof(z));
-      pv[k] = in ? __ldg(reinterpret_cast<const V16*>(p + V.base + (long long)j * V.P + i)) : z;
-    }
+  for (int k = 0; k < NLP; ++k) {
+    const int q = tid + k * NT;
+    const int w = q % NV, lj = q / NV;
+    const int i = ij.x - 4 + VN * w, j = ij.y - 1 + lj;
+    const bool in = q < H * NV && j >= 0 && j <= ny && i + VN - 1 >= 0 && i <= nx;
+    V16 z;
+    memset(&z, 0, sizeof(z));
+    pv[k] = in ? __ldg(reinterpret_cast<const V16*>(p + base + (long long)j * P + i)) : z;
+  }
 #pragma unroll
-    for (int k = 0; k < NLT; ++k) {
-      const int q = tid + k * NT;
-      const int w = q % NW, lj = q / NW;
-      const int i = ij.x - 4 + 4 * w, j = ij.y - 1 + lj;
-      const bool in = !plain && q < H * NW && j >= 0 && j <= V.ny && i >= 0 && i <= V.nx;
-      tv[k] = in ? __ldg(reinterpret_cast<const uint32_t*>(m.tag + V.base + (long long)j * V.P + i)) : 0u;
+  for (int k = 0; k < NLT; ++k) {
+    const int q = tid + k * NT;
+    const int w = q % NW, lj = q / NW;
+    const int i = ij.x - 4 + 4 * w, j = ij.y - 1 + lj;
+    const bool in = !plain && q < H * NW && j >= 0 && j <= ny && i >= 0 && i <= nx;
+    tv[k] = in ? __ldg(reinterpret_cast<const uint32_t*>(m.tag + base + (long long)j * P + i)) : 0u;
+  }
+#pragma unroll
+  for (int k = 0; k < NLP; ++k) {
+    const int q = tid + k * NT;
+    if (q < H * NV) {
+      const int w = q % NV;
+      const int i = ij.x - 4 + VN * w;
+      T e[VN];
+      memcpy(e, &pv[k], sizeof(e));
+#pragma unroll
+      for (int c = 0; c < VN; ++c)
+        if (i + c < 0 || i + c > nx) e[c] = T(0);
+      memcpy(&ps[q * VN], e, sizeof(e));
     }
   }
-  __device__ __forceinline__ void store(T* ps, uint32_t* ts32, const DevVariant& V, int2 ij, int tid) const {
 #pragma unroll
-    for (int k = 0; k < NLP; ++k) {
-      const int q = tid + k * NT;
-      if (q < H * NV) {
-        const int i = ij.x - 4 + VN * (q % NV);
-        T e[VN];
-        memcpy(e, &pv[k], sizeof(e));
-#pragma unroll
-        for (int c = 0; c < VN; ++c)
-          if (i + c < 0 || i + c > V.nx) e[c] = T(0);
-        memcpy(&ps[q * VN], e, sizeof(e));
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < NLT; ++k) {
-      const int q = tid + k * NT;
-      if (q < H * NW) ts32[q] = tv[k];
-    }
+  for (int k = 0; k < NLT; ++k) {
+    const int q = tid + k * NT;
+    if (q < H * NW) ts32[q] = tv[k];
   }
-};
-
-template <typename T>
-__global__ void __launch_bounds__(NT) k_apply(MeshDev m, const int* tile_var, const int2* tile_ij,
-                                              const uint8_t* tile_flags, int ntiles, const T* __restrict__ p,
-                                              T* __restrict__ y) {
-  using Win = ApplyWin<T>;
-  constexpr int AW = Win::AW, H = Win::H, NW = Win::NW;
-  __shared__ __align__(16) T ps[2][H * AW];
-  __shared__ __align__(16) uint32_t ts32[2][H * NW];
-  const int tid = linear_tid();
+  __syncthreads();
+  T kr[6];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) kr[c] = krect<T>(V)[c];
   const int col = tid % CTX, row_lo = (tid / CTX) * STRIP;
-  constexpr uint8_t PLAIN = sizeof(T) == 4 ? 8 : 4;
-  int t = blockIdx.x;
-  if (t >= ntiles) return;
-  Win win;
-  win.load(m, m.var[tile_var[t]], tile_ij[t], (tile_flags[t] & PLAIN) != 0, p, tid);
-  for (int buf = 0;; buf ^= 1) {
-    const DevVariant& V = m.var[tile_var[t]];
-    const int2 ij = tile_ij[t];
-    const bool plain = (tile_flags[t] & PLAIN) != 0;
-    win.store(ps[buf], ts32[buf], V, ij, tid);
-    // one barrier per tile: a thread can rewrite this buffer only after every thread has
-    // passed the next tile's barrier, i.e. finished computing from it
-    __syncthreads();
-    const int tn = t + gridDim.x;
-    if (tn < ntiles) win.load(m, m.var[tile_var[tn]], tile_ij[tn], (tile_flags[tn] & PLAIN) != 0, p, tid);
-    const T* pw = ps[buf];
-    const uint8_t* tw = reinterpret_cast<const uint8_t*>(ts32[buf]);
-    T kr[6];
+  const int i = ij.x + col;
+  if (i > nx) return;
+  // window node (li, lj) (li = i - i0 + 1) sits at column li + 3 of the stored rows
 #pragma unroll
-    for (int c = 0; c < 6; ++c) kr[c] = krect<T>(V)[c];
-    const int i = ij.x + col;
-    // window node (li, lj) (li = i - i0 + 1) sits at column li + 3 of the stored rows
-#pragma unroll
-    for (int u = 0; u < STRIP; ++u) {
-      const int j = ij.y + row_lo + u;
-      if (i > V.nx || j > V.ny) break;
-      const int c = col + 4, lj = 1 + row_lo + u;
-      const long long n = V.base + (long long)j * V.P + i;
-      const T nbh[3][3] = {{pw[(lj - 1) * AW + c - 1], pw[(lj - 1) * AW + c], pw[(lj - 1) * AW + c + 1]},
-                           {pw[lj * AW + c - 1], pw[lj * AW + c], pw[lj * AW + c + 1]},
-                           {pw[(lj + 1) * AW + c - 1], pw[(lj + 1) * AW + c], pw[(lj + 1) * AW + c + 1]}};
-      T out = T(0);
-      if (plain) {
-        out = q4_row_rect<T>(nbh, kr);
-      } else {
-        const uint8_t tg = tw[lj * AW + c];
-        const int kind = tg & KIND_MASK;
-        if (kind == K_FREE || kind == K_BODY)
-          out = q4_row_nb<T, false>(nbh, tg, tw[lj * AW + c - 1], tw[(lj - 1) * AW + c - 1], tw[(lj - 1) * AW + c],
-                                    nullptr, 0, 0, n, V.P, kplane<T>(m), m.Vtot, kr);
-      }
-      y[n] = out;
+  for (int u = 0; u < STRIP; ++u) {
+    const int j = ij.y + row_lo + u;
+    if (j > ny) break;
+    const int c = col + 4, lj = 1 + row_lo + u;
+    const long long n = base + (long long)j * P + i;
+    const T nbh[3][3] = {{ps[(lj - 1) * AW + c - 1], ps[(lj - 1) * AW + c], ps[(lj - 1) * AW + c + 1]},
+                         {ps[lj * AW + c - 1], ps[lj * AW + c], ps[lj * AW + c + 1]},
+                         {ps[(lj + 1) * AW + c - 1], ps[(lj + 1) * AW + c], ps[(lj + 1) * AW + c + 1]}};
+    T out = T(0);
+    if (plain) {
+      out = q4_row_rect<T>(nbh, kr);
+    } else {
+      const uint8_t tg = ts[lj * AW + c];
+      const int kind = tg & KIND_MASK;
+      if (kind == K_FREE || kind == K_BODY)
+        out = q4_row_nb<T, false>(nbh, tg, ts[lj * AW + c - 1], ts[(lj - 1) * AW + c - 1], ts[(lj - 1) * AW + c],
+                                  nullptr, 0, 0, n, P, kplane<T>(m), m.Vtot, kr);
     }
-    if (tn >= ntiles) break;
-    t = tn;
+    y[n] = out;
   }
 }
 
@@ -1466,22 +1442,9 @@ static void ensure_apply_buffers(Batch& b) {
   }
 }
 
-// persistent grid of the stand-alone operator: resident CTAs per SM x SMs, at most one
-// CTA per tile
 template <typename T>
 static void launch_apply(Batch& b, const MeshDev& m, const T* p, T* y) {
-  static int occ[2] = {0, 0};
-  int& o = occ[sizeof(T) == 8];
-  if (o == 0) PF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_apply<T>, NT, 0));
-  int nsm = b.nsm;
-  if (nsm <= 0) {
-    int dev = 0;
-    PF_CUDA(cudaGetDevice(&dev));
-    PF_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  }
-  const long long G = std::min<long long>((long long)nsm * std::max(1, o), b.Tcg);
-  k_apply<T><<<(unsigned)std::max<long long>(1, G), NT, 0, b.stream>>>(m, b.tile_cg_var, b.tile_cg_ij, b.tile_cg_gen,
-                                                                        (int)b.Tcg, p, y);
+  k_apply<T><<<(unsigned)b.Tcg, NT, 0, b.stream>>>(m, b.tile_cg_var, b.tile_cg_ij, b.tile_cg_gen, p, y);
 }
 
 // Mean time of `reps` back-to-back stand-alone operator applications on the handle's
