@@ -617,7 +617,7 @@ void build_batch(Batch& b, const pf_grid* grids, const int* body_offsets, const 
   PF_CUDA(cudaMemcpyAsync(b.body_ptr, b.h_body_ptr.data(), (b.B + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
   PF_CUDA(cudaMemcpyAsync(b.edge_ptr, b.h_edge_ptr.data(), (b.B + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
   b.body_nodes = (long long*)dev_alloc(b, std::max(1, b.h_body_ptr[b.B]) * sizeof(long long));
-  b.bq = (double*)dev_alloc(b, 2 * std::max(1, b.h_body_ptr[b.B]) * sizeof(double));   // two launch-parity copies
+  b.bq = (double*)dev_alloc(b, std::max(1, b.h_body_ptr[b.B]) * sizeof(double));
   b.edge_rec = (long long*)dev_alloc(b, std::max(1, b.h_edge_ptr[b.B]) * sizeof(long long));
   if (b.B > 0) {
     k_body_nodes<<<b.B, blk, 0, s>>>(b.d_var, b.d_body_var, b.d_bbox, b.tag, b.bid, nullptr, b.body_ptr,

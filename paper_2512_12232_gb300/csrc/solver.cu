@@ -38,18 +38,12 @@ namespace pfq4 {
 template <typename T>
 struct CGArgs {
   MeshDev m;
-  Sched sc;                 // sc.partial: this launch's segment partials
-  const VarState* stR;      // variant states this launch starts from ...
-  VarState* stW;            // ... and the copy it writes for the next launch
+  Sched sc;
+  VarState* st;
   const SolveParams* prm;
   State4<T>* s[2];          // ping-pong state, parity VarState::buf holds the current one
-  const T* sbR;             // [4][B] body x, r, p, q this launch starts from ...
-  T* sbW;                   // ... and the copy it writes
-  const double* bqR;        // [body nodes] rows of A p at BODY nodes of the previous launch ...
-  double* bqW;              // ... and of this launch (slot order of body_nodes)
-  const double* partR;      // segment partials of the previous launch
-  int defer;                // finish the previous launch's iteration first (it left it open)
-  int finalize;             // the last CTA of each variant finishes this launch's iteration
+  T* sb;                    // [4][B] body x, r, p, q of the CG
+  double* bq;               // [body nodes] q at each BODY node (slot order of body_nodes)
   int B;
   int* n_done;
   const uint8_t* tile_gen;  // per fused-CG tile: stored coefficients needed
@@ -120,16 +114,19 @@ __device__ __forceinline__ double warp_sum(double x) {
   return x;
 }
 
-// What one iteration of a variant needs besides its tiles, loaded by the consumer warps
-// at the start of each segment: the variant's state and body scalars for this
-// iteration, its body-node slot ranges and its segments of the schedule.
+// Shared-memory doubles the finaliser stages per pass (fixed, so that the summation
+// order does not depend on the pipeline depth).
+constexpr int FIN_CAP = 8192;
+
+// What the end of an iteration needs from global memory, loaded by the consumer warps
+// at the start of each segment so that the serial finaliser issues no dependent loads.
 template <typename T>
 struct FinCache {
-  VarState vs;               // state of this iteration (alpha, beta, counters, buffer parity)
-  T sb[4][MAXB];             // body x, r, p, q of this iteration
+  T sb[4][MAXB];             // body x, r, p, q before this iteration
   int bptr[MAXB + 1];        // body_ptr of the variant's bodies (global slots)
-  long long k_max;
-  int seg0, seg1, fixed;     // seg0/seg1: the variant's segments
+  double alpha, beta, gamma_start, thr_rel, thr_abs2;
+  long long iters, inner_iters, k_max;
+  int seg0, seg1, buf, fixed; // seg0/seg1: the variant's segments
 };
 
 // A BODY node has no x, r or p of its own (its value is the body's unknown), so the x
@@ -152,105 +149,119 @@ __device__ __forceinline__ int body_of_slot(const int* bptr, int nb, int e) {
   return lo;
 }
 
-// Sums of one finished iteration of a variant, in a fixed order: warps 0-3 take dot
-// k = warp over the variant's segment partials (lane-strided, then the warp tree); the
-// other warps take the collapsed body rows of A p, one warp per body, over the body's
-// slots of bq (lane-strided, then the warp tree).  Loads are independent, so several
-// are in flight per lane.  d[4] and qb[nb] are shared memory; the caller synchronises.
-template <int NW>
-__device__ __forceinline__ void reduce_iteration(const double* part, int seg0, int seg1, const double* bq,
-                                                 const int* bptr, int nb, double* d, double* qb, int warp, int lane) {
-  static_assert(NW >= 5, "four dot warps and at least one body warp");
-  if (warp < 4) {
-    double s = 0.0;
-    for (int sg = seg0 + lane; sg < seg1; sg += 32) s += __ldcg(&part[sg * 4 + warp]);
-    s = warp_sum(s);
-    if (lane == 0) d[warp] = s;
-  } else if (warp < NW) {
-    for (int k = warp - 4; k < nb; k += NW - 4) {
-      const int e1 = bptr[k + 1];
-      double s = 0.0;
-#pragma unroll 16
-      for (int e = bptr[k] + lane; e < e1; e += 32) s += __ldcg(&bq[e]);
-      s = warp_sum(s);
-      if (lane == 0) qb[k] = s;
-    }
-  }
-}
-
-// One step of the CG recurrence of a variant after an iteration (section "Matrix-Free
-// Conjugate Gradient with Multiple Constraint Enforcement", Appendix A Algorithm), in one
-// thread.  From the state S that the iteration used and its sums (d: the four dots over
-// FREE nodes; qb: the collapsed body rows of A p): update the body unknowns with the
-// iteration's alpha and beta, complete the dots with their terms in body order, take the
-// stopping test and form the next alpha and beta (single-reduction form:
-// |r_{k+1}|^2 = r.r - 2 alpha r.q + alpha^2 q.q).  n_done, if not null, counts a variant
-// that breaks down.
-template <typename T>
-__device__ void cg_scalar_step(VarState& S, T (&sb)[4][MAXB], const double* d, const double* qb, int nb, int fixed,
-                               long long k_max, int* n_done) {
-  const T alpha = (T)S.alpha, beta = (T)S.beta;
-  double dd[4] = {d[0], d[1], d[2], d[3]};
-  const int nbu = fixed ? 0 : nb;
-  for (int k = 0; k < nbu; ++k) {
-    const T pb = sb[2][k];
-    const T rn = next_r(sb[1][k], sb[3][k], alpha);
-    const T pn = next_p(rn, pb, beta);
-    const T xn = next_x(sb[0][k], pb, alpha);
-    const T qn = (T)qb[k];
-    sb[0][k] = xn;
-    sb[1][k] = rn;
-    sb[2][k] = pn;
-    sb[3][k] = qn;
-    dd[0] += (double)rn * (double)rn;
-    dd[1] += (double)pn * (double)qn;
-    dd[2] += (double)rn * (double)qn;
-    dd[3] += (double)qn * (double)qn;
-  }
-  const double g = dd[0], pi = dd[1], rho = dd[2], mu = dd[3];
-  S.buf ^= 1;
-  S.iters += 1;
-  S.inner_iters += 1;
-  if (S.inner_iters == 1) S.gamma_start = g;
-  S.gamma = g; S.pi = pi; S.rho = rho; S.mu = mu;
-  if (!isfinite(g) || !isfinite(pi) || !(pi > 0.0)) {
-    if (g == 0.0) {
-      S.phase = PH_RESID;
-    } else {
-      S.status = PF_EBREAKDOWN;
-      S.phase = PH_DONE;
-      if (n_done) atomicAdd(n_done, 1);
-    }
-  } else if (g <= fmax(S.thr_rel * S.gamma_start, S.thr_abs2)) {
-    S.phase = PH_RESID;
-  } else if (S.iters >= k_max) {
-    S.capped = 1;
-    S.phase = PH_RESID;
-  } else {
-    const double al = g / pi;
-    const double gn = g - 2.0 * al * rho + al * al * mu;
-    S.alpha = al;
-    S.beta = gn > 0.0 ? gn / g : 0.0;
-  }
-}
-
-// The last CTA of variant v to finish the last launch of a chunk (all NTHR threads)
-// completes that launch's iteration and writes the next state and body scalars.
+// Runs in the last CTA of variant v to finish an iteration (all NTHR threads of the
+// CTA); gbuf is shared memory of gcap >= 4 * MAXB doubles that no copy is writing.
 template <typename T, int NTHR>
-__device__ __noinline__ void finalize_cg(const CGArgs<T>& a, int v, int nb, int body0, FinCache<T>& fc, double* d,
-                                         double* qb) {
+__device__ __noinline__ void finalize_cg(const CGArgs<T>& a, int v, int nb, int body0, const FinCache<T>& fc, double* scratch,
+                            double* sh_qb, double* gbuf) {
+  VarState* S = &a.st[v];
   const int tid = linear_tid(), warp = tid >> 5, lane = tid & 31;
-  reduce_iteration<NTHR / 32>(a.sc.partial, fc.seg0, fc.seg1, a.bqW, fc.bptr, nb, d, qb, warp, lane);
+  constexpr int NW = NTHR / 32;
+  static_assert(NW >= 5, "finaliser needs warps 0-3 for the dots and at least one body warp");
+  constexpr int GB = 8;                      // independent loads in flight per thread
+  constexpr int HALF = FIN_CAP / 2;          // doubles per staging region
+  double* d = scratch;                       // d[0..3]: the four dots over FREE nodes
+  double* gp = gbuf;                         // staged segment partials [HALF]
+  double* gq = gbuf + HALF;                  // staged body-node rows of A p [HALF]
+  // Both sums are staged through shared memory in passes of fixed size (independent
+  // loads, one round trip per pass) and added in a fixed order: warps 0-3 take dot k =
+  // warp over the variant's segment partials in segment order; warps 4.. take the
+  // collapsed body rows of A p (stored by slot during the iteration), one warp per body.
+  const int nparts = (fc.seg1 - fc.seg0) * 4;
+  const int e0 = fc.bptr[0], nq = fc.bptr[nb] - e0;
+  for (int k = tid; k < nb; k += NTHR) sh_qb[k] = 0.0;
+  double dsum = 0.0;
+  for (int off = 0; off < max(nparts, nq); off += HALF) {
+    const int np = min(HALF, nparts - off), nqq = min(HALF, nq - off);
+    for (int b = 0; b < max(np, nqq); b += GB * NTHR) {
+      double vp[GB], vq[GB];
+#pragma unroll
+      for (int u = 0; u < GB; ++u) {
+        const int e = b + u * NTHR + tid;
+        vp[u] = e < np ? __ldcg(&a.sc.partial[fc.seg0 * 4 + off + e]) : 0.0;
+        vq[u] = e < nqq ? __ldcg(&a.bq[e0 + off + e]) : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < GB; ++u) {
+        const int e = b + u * NTHR + tid;
+        if (e < np) gp[e] = vp[u];
+        if (e < nqq) gq[e] = vq[u];
+      }
+    }
+    __syncthreads();
+    if (warp < 4) {
+      for (int j = lane; j < np / 4; j += 32) dsum += gp[j * 4 + warp];
+    } else {
+      for (int k = warp - 4; k < nb; k += NW - 4) {
+        const int b0 = max(off, fc.bptr[k] - e0), b1 = min(off + nqq, fc.bptr[k + 1] - e0);
+        double sq = 0.0;
+        for (int e = b0 + lane; e < b1; e += 32) sq += gq[e - off];
+        sq = warp_sum(sq);
+        if (lane == 0) sh_qb[k] += sq;
+      }
+    }
+    __syncthreads();
+  }
+  if (warp < 4) {
+    dsum = warp_sum(dsum);
+    if (lane == 0) d[warp] = dsum;
+  }
+  __syncthreads();
+  // body unknowns, one thread per body; their dot contributions are added in body order
+  double* contrib = gbuf;                    // [4][MAXB]
+  const T alpha = (T)fc.alpha, beta = (T)fc.beta;
+  const int nbu = fc.fixed ? 0 : nb;
+  const int B = a.B;
+  for (int k = tid; k < nbu; k += NTHR) {
+    const int gb = body0 + k;
+    const T pb = fc.sb[2][k];
+    const T rn = next_r(fc.sb[1][k], fc.sb[3][k], alpha);
+    const T pn = next_p(rn, pb, beta);
+    const T xn = next_x(fc.sb[0][k], pb, alpha);
+    const T qn = (T)sh_qb[k];
+    a.sb[gb] = xn;
+    a.sb[B + gb] = rn;
+    a.sb[2 * B + gb] = pn;
+    a.sb[3 * B + gb] = qn;
+    contrib[k] = (double)rn * (double)rn;
+    contrib[MAXB + k] = (double)pn * (double)qn;
+    contrib[2 * MAXB + k] = (double)rn * (double)qn;
+    contrib[3 * MAXB + k] = (double)qn * (double)qn;
+  }
   __syncthreads();
   if (tid == 0) {
-    cg_scalar_step<T>(fc.vs, fc.sb, d, qb, nb, fc.fixed, fc.k_max, a.n_done);
-    a.stW[v] = fc.vs;
+    double dd[4] = {d[0], d[1], d[2], d[3]};
+    for (int k = 0; k < nbu; ++k)
+      for (int j = 0; j < 4; ++j) dd[j] += contrib[j * MAXB + k];
+    const double g = dd[0], pi = dd[1], rho = dd[2], mu = dd[3];
+    const long long iters = fc.iters + 1, inner = fc.inner_iters + 1;
+    const double gs = inner == 1 ? g : fc.gamma_start;
+    S->buf = fc.buf ^ 1;
+    S->iters = iters;
+    S->inner_iters = inner;
+    if (inner == 1) S->gamma_start = g;
+    S->gamma = g; S->pi = pi; S->rho = rho; S->mu = mu;
+    if (!isfinite(g) || !isfinite(pi) || !(pi > 0.0)) {
+      if (g == 0.0) {
+        S->phase = PH_RESID;
+      } else {
+        S->status = PF_EBREAKDOWN;
+        S->phase = PH_DONE;
+        atomicAdd(a.n_done, 1);
+      }
+    } else if (g <= fmax(fc.thr_rel * gs, fc.thr_abs2)) {
+      S->phase = PH_RESID;
+    } else if (iters >= fc.k_max) {
+      S->capped = 1;
+      S->phase = PH_RESID;
+    } else {
+      const double al = g / pi;
+      const double gn = g - 2.0 * al * rho + al * al * mu;
+      S->alpha = al;
+      S->beta = gn > 0.0 ? gn / g : 0.0;
+    }
     a.sc.counter[v] = 0;
   }
-  __syncthreads();
-  const int B = a.B;
-  for (int k = tid; k < nb; k += NTHR)
-    for (int j = 0; j < 4; ++j) a.sbW[j * B + body0 + k] = fc.sb[j][k];
 }
 
 // Shared-memory layout of one pipeline stage of k_cg (T = float or double).  Tiles are
@@ -402,6 +413,7 @@ __device__ __forceinline__ State4<T> staged_state(const State4<T>* Ss, int li, i
 template <typename T, int NS>
 __global__ void __launch_bounds__(NTC, sizeof(T) == 4 ? 2 : 1) k_cg(CGArgs<T> a, const __grid_constant__ CgMaps mp) {
   using L = CgSmem<T, NS>;
+  static_assert(L::off_bar >= FIN_CAP * 8, "the finaliser stages FIN_CAP doubles in the stage memory");
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ T s_pb[MAXB];
   __shared__ double red[NT / 32][4];
@@ -450,21 +462,11 @@ __global__ void __launch_bounds__(NTC, sizeof(T) == 4 ? 2 : 1) k_cg(CGArgs<T> a,
   int q = 0;                                      // tiles consumed (consumers) / issued (producer) so far
   for (int sg = a.sc.cta_seg[blockIdx.x]; sg < a.sc.cta_seg[blockIdx.x + 1]; ++sg) {
     const int v = a.sc.seg_var[sg];
+    if (a.st[v].phase != PH_CG) continue;
     const DevVariant& Vg = a.m.var[v];
     const int nx = Vg.nx, ny = Vg.ny, P = Vg.P, row0 = Vg.row0, nb = Vg.nb, body0 = Vg.body0;
-    // the CTA holding the variant's first segment writes its state for the next launch
-    const bool designated = sg == a.sc.var_seg0[v];
-    if (a.stR[v].phase != PH_CG) {
-      // not iterating: carry the state and body scalars forward unchanged
-      if (designated) {
-        if (tid == 0) a.stW[v] = a.stR[v];
-        for (int k = tid; k < 4 * nb; k += NTC) a.sbW[(k / nb) * B + body0 + k % nb] = a.sbR[(k / nb) * B + body0 + k % nb];
-      }
-      continue;
-    }
     const long long base = Vg.base;
-    // the previous launch, if it left its iteration open, wrote the other record buffer
-    const int cur = a.defer ? (a.stR[v].buf ^ 1) : a.stR[v].buf;
+    const int cur = a.st[v].buf;
     const int t0 = a.sc.seg_t0[sg], t1 = a.sc.seg_t1[sg];
     Acc<T> acc;
     acc.zero();
@@ -499,36 +501,33 @@ __global__ void __launch_bounds__(NTC, sizeof(T) == 4 ? 2 : 1) k_cg(CGArgs<T> a,
       T kr[6];
 #pragma unroll
       for (int m = 0; m < 6; ++m) kr[m] = krect<T>(Vg)[m];
+      const T alpha = (T)a.st[v].alpha, beta = (T)a.st[v].beta;
       State4<T>* __restrict__ s_new = a.s[cur ^ 1];
-      // state of this iteration: the one the last launch wrote, completed here first if
-      // that launch left its iteration open (its sums are ready once it has ended)
-      for (int k = tid; k < 4 * nb; k += NT) fc.sb[k / nb][k % nb] = a.sbR[(k / nb) * B + body0 + k % nb];
+      if (tid < nb) {
+        const int gb = body0 + tid;
+        const T xb = a.sb[gb], rb = a.sb[B + gb], pb = a.sb[2 * B + gb], qb = a.sb[3 * B + gb];
+        fc.sb[0][tid] = xb;
+        fc.sb[1][tid] = rb;
+        fc.sb[2][tid] = pb;
+        fc.sb[3][tid] = qb;
+        s_pb[tid] = a.prm->fixed_bodies ? T(0) : next_p(next_r(rb, qb, alpha), pb, beta);
+      }
       if (tid <= nb) fc.bptr[tid] = a.m.body_ptr[body0 + tid];
       if (tid == NT - 1) {
-        fc.vs = a.stR[v];
+        const VarState& S = a.st[v];
+        fc.alpha = S.alpha;
+        fc.beta = S.beta;
+        fc.gamma_start = S.gamma_start;
+        fc.thr_rel = S.thr_rel;
+        fc.thr_abs2 = S.thr_abs2;
+        fc.iters = S.iters;
+        fc.inner_iters = S.inner_iters;
+        fc.buf = cur;
         fc.k_max = a.prm->k_max;
         fc.fixed = a.prm->fixed_bodies;
         fc.seg0 = a.sc.var_seg0[v];
         fc.seg1 = a.sc.var_seg1[v];
       }
-      named_bar_sync(CONSUMER_BAR, NT);
-      if (a.defer) {
-        reduce_iteration<NT / 32>(a.partR, fc.seg0, fc.seg1, a.bqR, fc.bptr, nb, scratch, sh_qb, warp, lane);
-        named_bar_sync(CONSUMER_BAR, NT);
-        if (tid == 0)
-          cg_scalar_step<T>(fc.vs, fc.sb, scratch, sh_qb, nb, fc.fixed, fc.k_max, designated ? a.n_done : nullptr);
-        named_bar_sync(CONSUMER_BAR, NT);
-      }
-      if (designated) {
-        if (tid == 0) a.stW[v] = fc.vs;
-        for (int k = tid; k < 4 * nb; k += NT) a.sbW[(k / nb) * B + body0 + k % nb] = fc.sb[k / nb][k % nb];
-      }
-      // a variant that has just converged (or broken down) only drains the tiles that
-      // the producer already asked for
-      const bool stop = fc.vs.phase != PH_CG;
-      const T alpha = (T)fc.vs.alpha, beta = (T)fc.vs.beta;
-      if (tid < nb)
-        s_pb[tid] = fc.fixed ? T(0) : next_p(next_r(fc.sb[1][tid], fc.sb[3][tid], alpha), fc.sb[2][tid], beta);
       named_bar_sync(CONSUMER_BAR, NT);
       for (int t = t0; t < t1; ++t, ++q) {
         const int s = q % NS;
@@ -546,7 +545,7 @@ __global__ void __launch_bounds__(NTC, sizeof(T) == 4 ? 2 : 1) k_cg(CGArgs<T> a,
         T rn4[STRIP], pn4[STRIP], xn4[STRIP];
         int bs4[STRIP];                           // slot of a BODY node in body_nodes
         uint8_t tg4[STRIP];
-        if (ok && !stop && plain) {
+        if (ok && plain) {
           // every node of the window is FREE and every cell active with rectangle constants
 #pragma unroll
           for (int u = 0; u < STRIP; ++u) {
@@ -564,7 +563,7 @@ __global__ void __launch_bounds__(NTC, sizeof(T) == 4 ? 2 : 1) k_cg(CGArgs<T> a,
             const State4<T> o = staged_state<T>(Ss, li, lj);
             pt[lj * W + li] = next_p(next_r(o.r, o.q, alpha), o.p, beta);
           }
-        } else if (ok && !stop) {
+        } else if (ok) {
 #pragma unroll
           for (int u = 0; u < STRIP; ++u) {
             const int li = 1 + col, lj = 1 + row_lo + u;
@@ -619,8 +618,7 @@ __global__ void __launch_bounds__(NTC, sizeof(T) == 4 ? 2 : 1) k_cg(CGArgs<T> a,
           break;
         }
         // pass 2: operator rows of the strip from a register window of the p tile
-        if (stop) {
-        } else if (plain) {
+        if (plain) {
           const int li = 1 + col;
           T win[STRIP + 2][3];
 #pragma unroll
@@ -687,7 +685,7 @@ __global__ void __launch_bounds__(NTC, sizeof(T) == 4 ? 2 : 1) k_cg(CGArgs<T> a,
               o.p = pn4[u];
               o.q = y;
               s_new[n] = o;          // BODY nodes: x = slot bits, r = 0, p = the body's p, q = row of A p
-              if (kind == K_BODY && bs4[u] >= 0) a.bqW[bs4[u]] = (double)y;   // slot was range-checked
+              if (kind == K_BODY && bs4[u] >= 0) a.bq[bs4[u]] = (double)y;   // slot was range-checked
               if (kind == K_FREE) {
                 yq[u] = y;
                 rr[u] = rn4[u];
@@ -714,10 +712,6 @@ __global__ void __launch_bounds__(NTC, sizeof(T) == 4 ? 2 : 1) k_cg(CGArgs<T> a,
       __syncthreads();
       return;
     }
-    if (fc.vs.phase != PH_CG) {                    // drained only: no sums, no arrival
-      __syncthreads();
-      continue;
-    }
     double w4[4];
     acc.warp_reduce(w4);
     if (lane == 0 && !producer)
@@ -729,21 +723,17 @@ __global__ void __launch_bounds__(NTC, sizeof(T) == 4 ? 2 : 1) k_cg(CGArgs<T> a,
         for (int w = 0; w < NT / 32; ++w) sum += red[w][k];
         a.sc.partial[sg * 4 + k] = sum;
       }
-      s_last = 0;
       if (a.sc.cta_ns && sg + 1 == a.sc.cta_seg[blockIdx.x + 1]) {
         unsigned long long t_end;
         asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_end));
         a.sc.cta_ns[blockIdx.x] = t_end - s_t0;
       }
-      // only the last launch of a chunk finishes its iteration here: release this CTA's
-      // stores (ordered before by the barrier), acquire the others'
-      if (a.finalize) {
-        const int done = atom_add_acq_rel_gpu(&a.sc.counter[v], 1);
-        s_last = (done == seg_count(a.sc, v) - 1);
-      }
+      // release this CTA's stores (ordered before by the barrier), acquire the others'
+      const int done = atom_add_acq_rel_gpu(&a.sc.counter[v], 1);
+      s_last = (done == seg_count(a.sc, v) - 1);
     }
     __syncthreads();
-    if (s_last) finalize_cg<T, NTC>(a, v, nb, body0, fc, scratch, sh_qb);
+    if (s_last) finalize_cg<T, NTC>(a, v, nb, body0, fc, scratch, sh_qb, reinterpret_cast<double*>(smem));
     __syncthreads();
   }
 }
@@ -1324,7 +1314,7 @@ static CgConfig& cg_config(Batch& b, int precision, int ns) {
   sc.var_seg0 = c.d_var_seg0;
   sc.var_seg1 = c.d_var_seg1;
   sc.counter = counter;
-  sc.partial = (double*)dev_alloc(b, (size_t)2 * Smax * 4 * sizeof(double));   // two launch-parity copies
+  sc.partial = (double*)dev_alloc(b, (size_t)Smax * 4 * sizeof(double));
   sc.n_cta = G;
   sc.tile_ij = b.tile_cg_ij;
   sc.cta_ns = nullptr;
@@ -1395,10 +1385,10 @@ void ensure_solver_memory(Batch& b, int precision) {
     b.x64 = (double*)dev_alloc(b, V * sizeof(double));
     b.w64 = (double*)dev_alloc(b, V * sizeof(double));
     b.sol64 = (double*)dev_alloc(b, B * sizeof(double));
-    b.sb64 = (double*)dev_alloc(b, 2 * 4 * B * sizeof(double));   // two launch-parity copies
-    b.sb32 = (float*)dev_alloc(b, 2 * 4 * B * sizeof(float));
+    b.sb64 = (double*)dev_alloc(b, 4 * B * sizeof(double));
+    b.sb32 = (float*)dev_alloc(b, 4 * B * sizeof(float));
     b.sbr64 = (double*)dev_alloc(b, B * sizeof(double));
-    b.state = (VarState*)dev_alloc(b, 2 * b.nv * sizeof(VarState));   // two launch-parity copies
+    b.state = (VarState*)dev_alloc(b, b.nv * sizeof(VarState));
     b.params = (SolveParams*)dev_alloc(b, sizeof(SolveParams));
     b.n_done = (int*)dev_alloc(b, 2 * sizeof(int));
     b.d_err = b.n_done + 1;
@@ -1519,36 +1509,19 @@ void apply_operator(Batch& b, int precision, const double* dev_p, double* dev_y,
 }
 
 template <typename T>
-// Arguments of launch k of a chunk (L = k & 1): the variant states, body scalars, body
-// rows and segment partials have two copies each; launch k reads copy L and writes copy
-// L ^ 1 (body rows and partials: writes copy L, reads the previous launch's L ^ 1).
-// Chunks have an even length, so before and after a chunk everything is in copy 0.
-// defer: the previous launch left its iteration open (every launch but the first);
-// finalize: the last launch closes its own iteration.
-static void fill_cg_args(Batch& b, CGArgs<T>& a, State4<T>* const st[2], T* sb, const Sched& sc, int L, bool defer,
-                         bool finalize) {
-  const int Bm = std::max(1, b.B);
-  const size_t ns = (size_t)std::max(1, b.h_body_ptr.empty() ? 0 : b.h_body_ptr[b.B]);
-  const size_t smax = (size_t)sc.n_cta + b.nv;
+static void fill_cg_args(Batch& b, CGArgs<T>& a, State4<T>* const st[2], T* sb, const Sched& sc) {
   a.m = mesh_dev(b);
   a.sc = sc;
-  a.sc.partial = sc.partial + (size_t)L * smax * 4;
-  a.partR = sc.partial + (size_t)(L ^ 1) * smax * 4;
   a.tile_gen = b.tile_cg_gen;
   a.Rtot = b.Rtot;
   a.err = b.d_err;
-  a.stR = b.state + (size_t)L * b.nv;
-  a.stW = b.state + (size_t)(L ^ 1) * b.nv;
+  a.st = b.state;
   a.prm = b.params;
   a.s[0] = st[0];
   a.s[1] = st[1];
-  a.sbR = sb + (size_t)L * 4 * Bm;
-  a.sbW = sb + (size_t)(L ^ 1) * 4 * Bm;
-  a.bqW = b.bq + (size_t)L * ns;
-  a.bqR = b.bq + (size_t)(L ^ 1) * ns;
-  a.defer = defer ? 1 : 0;
-  a.finalize = finalize ? 1 : 0;
-  a.B = Bm;
+  a.sb = sb;
+  a.bq = b.bq;
+  a.B = std::max(1, b.B);
   a.n_done = b.n_done;
   a.poll_limit = b.test_drop ? 1024 : MBAR_POLL_LIMIT;
   a.test_drop = b.test_drop;
@@ -1581,19 +1554,18 @@ static void launch_cg_chunk(Batch& b, int precision, int chunk, cudaStream_t s, 
   CgConfig& c = cg_config(b, precision, ns);
   Sched sc = c.sc;
   if (timed) sc.cta_ns = c.d_cta_ns;
-  if (chunk < 2 || chunk % 2) throw Error{PF_ECUDA, "internal: fused-CG chunks have an even length"};
   if (precision == PF_FP64) {
+    CGArgs<double> a;
+    fill_cg_args<double>(b, a, b.st64, b.sb64, sc);
     for (int k = 0; k < chunk; ++k) {
-      CGArgs<double> a;
-      fill_cg_args<double>(b, a, b.st64, b.sb64, sc, k & 1, k > 0, k == chunk - 1);
       if (ns == 4) k_cg<double, 4><<<c.G, blk, c.smem, s>>>(a, b.maps[0]);
       else if (ns == 3) k_cg<double, 3><<<c.G, blk, c.smem, s>>>(a, b.maps[0]);
       else k_cg<double, 2><<<c.G, blk, c.smem, s>>>(a, b.maps[0]);
     }
   } else {
+    CGArgs<float> a;
+    fill_cg_args<float>(b, a, b.st32, b.sb32, sc);
     for (int k = 0; k < chunk; ++k) {
-      CGArgs<float> a;
-      fill_cg_args<float>(b, a, b.st32, b.sb32, sc, k & 1, k > 0, k == chunk - 1);
       if (ns == 4) k_cg<float, 4><<<c.G, blk, c.smem, s>>>(a, b.maps[1]);
       else if (ns == 3) k_cg<float, 3><<<c.G, blk, c.smem, s>>>(a, b.maps[1]);
       else k_cg<float, 2><<<c.G, blk, c.smem, s>>>(a, b.maps[1]);
@@ -1714,7 +1686,6 @@ pf_status solve_core(Batch& b, double U, const pf_solve_opts& o, double* dev_psi
     for (auto& H : b.hv) nodes += H.stats.n_nodes;
     chunk = nodes > (8LL << 20) ? 16 : (nodes > (1LL << 20) ? 64 : 256);
   }
-  chunk = std::max(2, chunk + (chunk & 1));   // fused-CG chunks have an even length
   if (!b.h_poll) PF_CUDA(cudaMallocHost(&b.h_poll, 4 * sizeof(int)));
   int* hdone = b.h_poll;
   double cg_ms = 0, res_ms = 0;
