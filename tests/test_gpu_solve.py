@@ -140,3 +140,22 @@ def test_schur_form_on_a_batch(api):
         m, s, u, psi_ref = oracle_solution(c, 1.0)
         np.testing.assert_allclose(r.body_psi[5 * v:5 * v + 5], u[s.n_free:], rtol=0, atol=1e-7)
         assert r.info[v]["status"] == 0
+
+
+def test_tuned_schedule_matches_untuned(api):
+    """The autotuned path (pipeline depth trials, timed re-balance of the persistent
+    schedule, kept for later solves on the handle) changes only the summation order: its
+    solutions match an untuned FP64 solve of the same batch within the solve tolerances,
+    on the tuning call and on a second call that reuses the tuning."""
+    cases = W.parametric_sweep(4, seed=7, nx_choices=(768, 1024))   # >= 2 tiles per CTA: the re-balance runs
+    with api.batch_build(cases) as g:
+        ref = api.psi_solve(g, U=1.0, tol=1e-13, precision=api.PF_FP64).psi.cpu().numpy()
+        for _ in range(2):
+            r = api.psi_solve(g, U=1.0, tol=1e-8, precision=api.PF_MIXED, tune_schedule=True)
+            assert r.status == 0
+            assert all(i["status"] == 0 and i["rel_true_residual"] <= 1e-8 for i in r.info)
+            assert g.timing()["cg_stages"] in (2, 3, 4)
+            assert rel_l2(r.psi.cpu().numpy(), ref) <= 1e-4
+        r64 = api.psi_solve(g, U=1.0, tol=1e-13, precision=api.PF_FP64, tune_schedule=True)
+        assert r64.status == 0
+        assert rel_l2(r64.psi.cpu().numpy(), ref) <= FP64_TOL
