@@ -164,8 +164,9 @@ __device__ void atomic_min_double(double* addr, double val) {
   }
 }
 
-// 5. Q4 element matrices of the active cells (2x2 Gauss), FP64 and FP32 copies,
-//    CELL_GENERAL flag, per-variant counts and min det J.
+// 5. Q4 element matrices (2x2 Gauss), FP64 and FP32 copies, of the active cells with a
+//    displaced corner (every reader uses the closed-form constants for the others),
+//    CELL_GENERAL / CELL_GEN32 flags, per-variant counts and min det J.
 __global__ void k_stiffness(const DevVariant* var, const int* tile_var, const int2* tile_ij,
                             uint8_t* tag, const double* X, long long Vtot, double* K64, float* K32, float* K32i,
                             long long* stats_i, double* detmin) {
@@ -187,54 +188,58 @@ __global__ void k_stiffness(const DevVariant* var, const int* tile_var, const in
     if (t & CELL_ACTIVE) {
       atomicAdd((unsigned long long*)&cnt[3], 1ull);
       const long long idx[4] = {n, n + 1, n + 1 + V.P, n + V.P};
-      double x[4], y[4];
       bool disp = false;
-      for (int a = 0; a < 4; ++a) {
-        x[a] = X[idx[a]];
-        y[a] = X[Vtot + idx[a]];
-        disp |= (tag[idx[a]] & DISPLACED) != 0;
-      }
-      const double g = 0.57735026918962576451;   // 1/sqrt(3)
-      const double xi_a[4] = {-1, 1, 1, -1}, eta_a[4] = {-1, -1, 1, 1};
-      const double gx[4] = {-g, g, g, -g}, gy[4] = {-g, -g, g, g};
-      double K[4][4] = {};
-      double dm = 1e300;
-      for (int q = 0; q < 4; ++q) {
-        double dxi[4], deta[4];
+      for (int a = 0; a < 4; ++a) disp |= (tag[idx[a]] & DISPLACED) != 0;
+      if (!disp) {
+        // an undisplaced hx-by-hy rectangle: every reader of stored K_e uses the
+        // closed-form constants for it, and det J = (hx/2)(hy/2) at every Gauss point
+        atomic_min_double(&dmin, 0.25 * V.hx * V.hy);
+      } else {
+        double x[4], y[4];
         for (int a = 0; a < 4; ++a) {
-          dxi[a] = 0.25 * xi_a[a] * (1.0 + eta_a[a] * gy[q]);
-          deta[a] = 0.25 * eta_a[a] * (1.0 + xi_a[a] * gx[q]);
+          x[a] = X[idx[a]];
+          y[a] = X[Vtot + idx[a]];
         }
-        double j00 = 0, j01 = 0, j10 = 0, j11 = 0;
-        for (int a = 0; a < 4; ++a) {
-          j00 += dxi[a] * x[a]; j01 += dxi[a] * y[a];
-          j10 += deta[a] * x[a]; j11 += deta[a] * y[a];
+        const double g = 0.57735026918962576451;   // 1/sqrt(3)
+        const double xi_a[4] = {-1, 1, 1, -1}, eta_a[4] = {-1, -1, 1, 1};
+        const double gx[4] = {-g, g, g, -g}, gy[4] = {-g, -g, g, g};
+        double K[4][4] = {};
+        double dm = 1e300;
+        for (int q = 0; q < 4; ++q) {
+          double dxi[4], deta[4];
+          for (int a = 0; a < 4; ++a) {
+            dxi[a] = 0.25 * xi_a[a] * (1.0 + eta_a[a] * gy[q]);
+            deta[a] = 0.25 * eta_a[a] * (1.0 + xi_a[a] * gx[q]);
+          }
+          double j00 = 0, j01 = 0, j10 = 0, j11 = 0;
+          for (int a = 0; a < 4; ++a) {
+            j00 += dxi[a] * x[a]; j01 += dxi[a] * y[a];
+            j10 += deta[a] * x[a]; j11 += deta[a] * y[a];
+          }
+          const double det = j00 * j11 - j01 * j10;
+          dm = fmin(dm, det);
+          const double inv = 1.0 / det;
+          double bx[4], by[4];
+          for (int a = 0; a < 4; ++a) {
+            bx[a] = (j11 * dxi[a] - j01 * deta[a]) * inv;
+            by[a] = (-j10 * dxi[a] + j00 * deta[a]) * inv;
+          }
+          for (int a = 0; a < 4; ++a)
+            for (int b2 = a + 1; b2 < 4; ++b2) K[a][b2] += det * (bx[a] * bx[b2] + by[a] * by[b2]);
         }
-        const double det = j00 * j11 - j01 * j10;
-        dm = fmin(dm, det);
-        const double inv = 1.0 / det;
-        double bx[4], by[4];
-        for (int a = 0; a < 4; ++a) {
-          bx[a] = (j11 * dxi[a] - j01 * deta[a]) * inv;
-          by[a] = (-j10 * dxi[a] + j00 * deta[a]) * inv;
+        const double k6[6] = {K[0][1], K[0][2], K[0][3], K[1][2], K[1][3], K[2][3]};
+        for (int m = 0; m < 6; ++m) {
+          K64[m * Vtot + n] = k6[m];
+          K32[m * Vtot + n] = (float)k6[m];
+          K32i[6 * n + m] = (float)k6[m];
         }
-        for (int a = 0; a < 4; ++a)
-          for (int b2 = a + 1; b2 < 4; ++b2) K[a][b2] += det * (bx[a] * bx[b2] + by[a] * by[b2]);
-      }
-      const double k6[6] = {K[0][1], K[0][2], K[0][3], K[1][2], K[1][3], K[2][3]};
-      for (int m = 0; m < 6; ++m) {
-        K64[m * Vtot + n] = k6[m];
-        K32[m * Vtot + n] = (float)k6[m];
-        K32i[6 * n + m] = (float)k6[m];
-      }
-      if (disp) {
         bool differs32 = false;
         for (int m = 0; m < 6; ++m) differs32 |= (float)k6[m] != V.kr32[m];
         tag[n] = t | CELL_GENERAL | (differs32 ? CELL_GEN32 : 0);
         atomicAdd((unsigned long long*)&cnt[4], 1ull);
         if (differs32) atomicAdd((unsigned long long*)&cnt[5], 1ull);
+        atomic_min_double(&dmin, dm);
       }
-      atomic_min_double(&dmin, dm);
     }
   }
   __syncthreads();
