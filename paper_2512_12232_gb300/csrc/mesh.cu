@@ -109,37 +109,79 @@ __global__ void k_kinds(const DevVariant* var, const int* tile_var, const int2* 
   d0[n] = d;
 }
 
-// 3. one Jacobi sweep: nodes outside every body and off the outer ring take the
-//    average of their four neighbours, summed W, E, S, N, divided by 4.  Before sweep s
-//    (0-based) the displacement is exactly zero farther than s cells from every body
-//    node, so a tile farther than s + 1 cells from every body's node box is all zeros
-//    in both ping-pong buffers and is skipped (bit-identical result, less traffic).
-__global__ void k_jacobi(const DevVariant* var, const int* tile_var, const int2* tile_ij,
-                         const int* bid, const uint8_t* tag, const int4* bbox, int sweep,
-                         const double2* __restrict__ src, double2* __restrict__ dst) {
-  TileCtx c = tile_ctx(var, tile_var, tile_ij);
-  const DevVariant& V = var[c.v];
+// 3. Jacobi sweeps, JK per launch (temporal blocking): nodes outside every body and off
+//    the outer ring take the average of their four neighbours, summed W, E, S, N,
+//    divided by 4; other nodes keep their value.  A CTA loads the window of its 64x16
+//    tile with a JK-node halo once, runs the sweeps in a double-buffered shared window
+//    (after s sweeps the window is exact at distance >= s from its edge) and writes its
+//    tile: every node sees the same neighbour values as with one launch per sweep, so
+//    the result is bit-identical.  After sweep s (0-based) the displacement is exactly
+//    zero farther than s + 1 cells from every body node, so a tile farther than the
+//    reach of the launch's last sweep from every body's node box is all zeros in both
+//    ping-pong buffers and is skipped.
+constexpr int JK = 4;
+constexpr int JRW = CTX + 2 * JK, JRH = CTY + 2 * JK;      // window 72 x 24
+constexpr int JACOBI_SMEM = 2 * JRW * JRH * (int)sizeof(double2) + JRW * JRH;
+
+__global__ void __launch_bounds__(NT) k_jacobi(const DevVariant* var, const int* tile_var, const int2* tile_ij,
+                                               const int* bid, const uint8_t* tag, const int4* bbox, int sweep0,
+                                               int nsw, const double2* __restrict__ src, double2* __restrict__ dst) {
+  extern __shared__ __align__(16) unsigned char jsm[];
+  double2* w0 = reinterpret_cast<double2*>(jsm);
+  double2* w1 = w0 + JRW * JRH;
+  uint8_t* upd = reinterpret_cast<uint8_t*>(w1 + JRW * JRH);
+  const int t = blockIdx.x;
+  const DevVariant& V = var[tile_var[t]];
+  const int2 ij = tile_ij[t];
   {
-    const int2 ij = tile_ij[blockIdx.x];
-    const int reach = sweep + 1;
+    const int reach = sweep0 + nsw;
     bool near = false;
     for (int k = 0; k < V.nb && !near; ++k) {
       const int4 bx = bbox[V.body0 + k];
-      near = ij.x <= bx.y + reach && ij.x + TX - 1 >= bx.x - reach && ij.y <= bx.w + reach &&
-             ij.y + TY - 1 >= bx.z - reach;
+      near = ij.x <= bx.y + reach && ij.x + CTX - 1 >= bx.x - reach && ij.y <= bx.w + reach &&
+             ij.y + CTY - 1 >= bx.z - reach;
     }
     if (!near) return;
   }
-  if (!c.in) return;
-  const long long n = c.n;
-  double2 out = src[n];
-  if (bid[n] < 0 && !(tag[n] & RING)) {
-    const double2 w = src[n - 1], e = src[n + 1], s = src[n - V.P], nn = src[n + V.P];
-    const double sx = __dadd_rn(__dadd_rn(__dadd_rn(w.x, e.x), s.x), nn.x);
-    const double sy = __dadd_rn(__dadd_rn(__dadd_rn(w.y, e.y), s.y), nn.y);
-    out = make_double2(__ddiv_rn(sx, 4.0), __ddiv_rn(sy, 4.0));
+  const int tid = linear_tid();
+  for (int q = tid; q < JRW * JRH; q += NT) {
+    const int i = ij.x - JK + q % JRW, j = ij.y - JK + q / JRW;
+    double2 v = make_double2(0.0, 0.0);
+    uint8_t u = 0;
+    if (i >= 0 && j >= 0 && i <= V.nx && j <= V.ny) {
+      const long long n = V.base + (long long)j * V.P + i;
+      v = src[n];
+      u = bid[n] < 0 && !(tag[n] & RING);
+    }
+    w0[q] = v;
+    upd[q] = u;
   }
-  dst[n] = out;
+  __syncthreads();
+  double2* a = w0;
+  double2* b = w1;
+  for (int sw = 0; sw < nsw; ++sw) {
+    for (int q = tid; q < JRW * JRH; q += NT) {
+      const int ri = q % JRW, rj = q / JRW;
+      double2 out = a[q];
+      // an updatable node is off the ring, so its four neighbours lie in the grid; at
+      // the window edge the value is stale but lies farther than nsw from the tile
+      if (upd[q] && ri > 0 && ri < JRW - 1 && rj > 0 && rj < JRH - 1) {
+        const double2 w = a[q - 1], e = a[q + 1], s = a[q - JRW], nn = a[q + JRW];
+        const double sx = __dadd_rn(__dadd_rn(__dadd_rn(w.x, e.x), s.x), nn.x);
+        const double sy = __dadd_rn(__dadd_rn(__dadd_rn(w.y, e.y), s.y), nn.y);
+        out = make_double2(__ddiv_rn(sx, 4.0), __ddiv_rn(sy, 4.0));
+      }
+      b[q] = out;
+    }
+    __syncthreads();
+    double2* tmp = a;
+    a = b;
+    b = tmp;
+  }
+  for (int q = tid; q < CTX * CTY; q += NT) {
+    const int i = ij.x + q % CTX, j = ij.y + q / CTX;
+    if (i <= V.nx && j <= V.ny) dst[V.base + (long long)j * V.P + i] = a[(JK + q / CTX) * JRW + JK + q % CTX];
+  }
 }
 
 // 4. final coordinates x = x_grid + d and the DISPLACED flag.
@@ -586,8 +628,11 @@ void build_batch(Batch& b, const pf_grid* grids, const int* body_offsets, const 
   k_kinds<<<grid, blk, 0, s>>>(b.d_var, b.tile_var, b.tile_ij, b.d_bodies, b.bid, b.tag, dA, bc[0], bc[1],
                                bc[2], bc[3], err);
   PF_CUDA(cudaMemcpyAsync(dB, dA, Vt * sizeof(double2), cudaMemcpyDeviceToDevice, s));
-  for (int it = 0; it < sweeps; ++it) {
-    k_jacobi<<<grid, blk, 0, s>>>(b.d_var, b.tile_var, b.tile_ij, b.bid, b.tag, b.d_bbox, it, dA, dB);
+  if (sweeps > 0) PF_CUDA(cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, JACOBI_SMEM));
+  for (int it = 0; it < sweeps; it += JK) {
+    const int nsw = std::min(JK, sweeps - it);
+    k_jacobi<<<(unsigned)b.Tcg, NT, JACOBI_SMEM, s>>>(b.d_var, b.tile_cg_var, b.tile_cg_ij, b.bid, b.tag, b.d_bbox, it,
+                                                      nsw, dA, dB);
     std::swap(dA, dB);
   }
   k_finalize<<<grid, blk, 0, s>>>(b.d_var, b.tile_var, b.tile_ij, dA, b.tag, b.X, Vt);
@@ -660,7 +705,7 @@ void build_batch(Batch& b, const pf_grid* grids, const int* body_offsets, const 
   dev_free(b, dB);
   dev_free(b, err);
   dev_free(b, cnt);
-  b.launches += 8 + sweeps + (b.B > 0 ? 4 : 0);
+  b.launches += 8 + (sweeps + JK - 1) / JK + (b.B > 0 ? 4 : 0);
   make_schedule(b);
 }
 
