@@ -59,7 +59,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--tol", type=float, default=1e-8)
-    ap.add_argument("--inner-tol", type=float, default=1e-4)
+    ap.add_argument("--inner-tol", type=float, default=2e-7)
     ap.add_argument("--nx", type=int, default=NX)
     ap.add_argument("--variants", type=int, default=len(DELTAS))
     ap.add_argument("--cpu-iters", type=int, default=60, help="oracle CG iterations in the CPU sample")

@@ -206,7 +206,7 @@ def apply(mesh: Mesh, p: torch.Tensor, precision=PF_FP64):
     return y, np.array(sums[:nb])
 
 
-def psi_solve(mesh: Mesh, U=1.0, tol=1e-8, precision=PF_MIXED, k_max=10_000_000, inner_tol=1e-4,
+def psi_solve(mesh: Mesh, U=1.0, tol=1e-8, precision=PF_MIXED, k_max=10_000_000, inner_tol=2e-7,
               chunk=0, warm_start=False, want_psi=True, raise_on_failure=True, method="mpc",
               tune_schedule=False) -> SolveResult:
     """Solve for psi.  method="mpc": CG on the multi-point-constraint system;

@@ -234,7 +234,7 @@ pf_status pf_psi_solve(pf_batch* h, double U, const pf_solve_opts* opts, double*
     o.tol = 1e-8;
     o.k_max = 10000000;
     o.precision = PF_MIXED;
-    o.inner_tol = 1e-4;
+    o.inner_tol = PF_DEFAULT_INNER_TOL;
     if (opts) o = *opts;
     return psi_solve(*b, U, o, dev_psi, body_psi, info);
   });
@@ -249,7 +249,7 @@ pf_status pf_psi_solve_schur(pf_batch* h, double U, const pf_solve_opts* opts, d
     o.tol = 1e-8;
     o.k_max = 10000000;
     o.precision = PF_MIXED;
-    o.inner_tol = 1e-4;
+    o.inner_tol = PF_DEFAULT_INNER_TOL;
     if (opts) o = *opts;
     return schur_solve(*b, U, o, dev_psi, body_psi, info);
   });

@@ -272,7 +272,7 @@ pf_status shape_gradient(Batch& b, int obj, int lo, int hi, double U, double tol
   o.tol = tol;
   o.k_max = 100000000;
   o.precision = PF_MIXED;
-  o.inner_tol = 1e-4;
+  o.inner_tol = PF_DEFAULT_INNER_TOL;
   b.rhs_active = true;
   pf_status st = PF_OK;
   try {

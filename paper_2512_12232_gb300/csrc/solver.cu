@@ -1644,7 +1644,7 @@ pf_status solve_core(Batch& b, double U, const pf_solve_opts& o, double* dev_psi
   cudaStream_t s = b.stream;
   SolveParams sp{};
   sp.tol2 = o.tol * o.tol;
-  const double itol = o.inner_tol > 0 ? o.inner_tol : 1e-4;
+  const double itol = o.inner_tol > 0 ? o.inner_tol : PF_DEFAULT_INNER_TOL;
   sp.inner_rel2 = itol * itol;
   sp.k_max = o.k_max;
   sp.mixed = prec == PF_MIXED;
