@@ -150,7 +150,8 @@ __device__ __forceinline__ int body_of_slot(const int* bptr, int nb, int e) {
 }
 
 // Runs in the last CTA of variant v to finish an iteration (all NTHR threads of the
-// CTA); gbuf is shared memory of gcap >= 4 * MAXB doubles that no copy is writing.
+// CTA); gbuf is the CTA's stage memory (at least FIN_CAP doubles), which no copy is
+// writing once the CTA's tiles are consumed.
 template <typename T, int NTHR>
 __device__ __noinline__ void finalize_cg(const CGArgs<T>& a, int v, int nb, int body0, const FinCache<T>& fc, double* scratch,
                             double* sh_qb, double* gbuf) {
@@ -287,7 +288,6 @@ struct CgSmem {
   // two coefficient boxes, each starting on a 128-byte boundary (TMA destination alignment)
   static constexpr int kbox_bytes = align((CTY + 1) * 6 * KHALF * (int)sizeof(T));
   static constexpr int stage_bytes = off_k + (kTmaK ? 2 * kbox_bytes : 0);
-  static constexpr int kplane_bytes = align(KB * (int)sizeof(T));
   static constexpr int tx_tag = TBW * (CTY + 2);
   static constexpr int tx_base = SB * (int)sizeof(T) + tx_tag;
   static constexpr int tx_k = kTmaK ? 6 * KB * (int)sizeof(T) : 0;
