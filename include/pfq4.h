@@ -263,6 +263,21 @@ pf_status pf_grad(pf_batch* b, int objective, int body_lo, int body_hi, double U
 /* Bytes of device memory held by the handle. */
 size_t pf_workspace_bytes(const pf_batch* b);
 
+/* Names of the calls above for callers that think of a handle as one mesh or as a batch
+   (a pf_mesh_build handle is a batch of one variant):
+   pf_mesh_info: counts of variant 0 (nodes, DOF, boundary edges, min det J), any output
+   may be NULL; PF_EINVAL for a NULL handle.
+   pf_batch_solve: pf_psi_solve without the nodal psi output.
+   pf_batch_grad: pf_grad.
+   pf_mesh_destroy: pf_batch_destroy. */
+pf_status pf_mesh_info(const pf_batch* b, long long* n_nodes, long long* n_dof, int* n_boundary_edges,
+                       double* min_detJ);
+pf_status pf_batch_solve(pf_batch* b, double U, const pf_solve_opts* opts, double* body_psi, pf_solve_info* info,
+                         void* stream);
+pf_status pf_batch_grad(pf_batch* b, int objective, int body_lo, int body_hi, double U, double tol,
+                        double* dev_dJdX, double* dJdc, double* J, void* stream);
+void pf_mesh_destroy(pf_batch* b);
+
 const char* pf_last_error(void);
 
 #ifdef __cplusplus

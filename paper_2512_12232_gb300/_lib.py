@@ -75,6 +75,11 @@ _SIGS = {
                            C.POINTER(C.c_double)]),
     "pf_grad": (C.c_int, [P, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, P, P, P, P]),
     "pf_workspace_bytes": (C.c_size_t, [P]),
+    "pf_mesh_info": (C.c_int, [P, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), C.POINTER(C.c_int),
+                               C.POINTER(C.c_double)]),
+    "pf_batch_solve": (C.c_int, [P, C.c_double, C.POINTER(pf_solve_opts), P, P, P]),
+    "pf_batch_grad": (C.c_int, [P, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, P, P, P, P]),
+    "pf_mesh_destroy": (None, [P]),
     "pf_last_error": (C.c_char_p, []),
 }
 EXPORTED = tuple(_SIGS)

@@ -255,3 +255,44 @@ def grad(mesh: Mesh, objective=PF_OBJ_COPFI, lo=3, hi=4, U=1.0, tol=1e-12, want_
     check(L.load().pf_grad(mesh.handle, int(objective), int(lo), int(hi), float(U), float(tol), _ptr(dX), dc, J,
                            _stream()))
     return dX, np.array(dc[:2 * nb]).reshape(nb, 2), np.array(J[:])
+
+
+def mesh_info(mesh: Mesh) -> dict:
+    """Counts of variant 0: nodes, DOF, boundary edges and the minimum det J."""
+    nn, nd, ne, dj = C.c_longlong(), C.c_longlong(), C.c_int(), C.c_double()
+    check(L.load().pf_mesh_info(mesh.handle, C.byref(nn), C.byref(nd), C.byref(ne), C.byref(dj)))
+    return {"n_nodes": nn.value, "n_dof": nd.value, "n_boundary_edges": ne.value, "min_detJ": dj.value}
+
+
+def batch_solve(mesh: Mesh, U=1.0, tol=1e-8, precision=PF_MIXED, k_max=10_000_000, inner_tol=2e-7, chunk=0,
+                warm_start=False, raise_on_failure=True, tune_schedule=False) -> SolveResult:
+    """Solve every variant of the batch; body psi and per-variant info only (no nodal psi)."""
+    opts = L.pf_solve_opts(float(tol), int(k_max), int(precision), float(inner_tol), int(chunk),
+                           int(bool(warm_start)), int(bool(tune_schedule)))
+    nb = mesh.body_offsets[-1]
+    bpsi = (C.c_double * max(1, nb))()
+    info = (L.pf_solve_info * mesh.n_variants)()
+    code = L.load().pf_batch_solve(mesh.handle, float(U), C.byref(opts), bpsi, info, _stream())
+    if raise_on_failure:
+        check(code)
+    infos = [{k: getattr(i, k) for k, _ in L.pf_solve_info._fields_} for i in info]
+    return SolveResult(None, np.array(bpsi[:nb]), infos, code)
+
+
+def batch_grad(mesh: Mesh, objective=PF_OBJ_COPFI, lo=3, hi=4, U=1.0, tol=1e-12, want_dX=True):
+    """Adjoint shape gradient of every variant after a solve (same outputs as grad)."""
+    total = int(mesh.node_offsets[-1])
+    dX = torch.empty((total, 2), dtype=torch.float64, device="cuda") if want_dX else None
+    nb = mesh.body_offsets[-1]
+    dc = (C.c_double * max(1, 2 * nb))()
+    J = (C.c_double * mesh.n_variants)()
+    check(L.load().pf_batch_grad(mesh.handle, int(objective), int(lo), int(hi), float(U), float(tol), _ptr(dX), dc,
+                                 J, _stream()))
+    return dX, np.array(dc[:2 * nb]).reshape(nb, 2), np.array(J[:])
+
+
+def mesh_destroy(mesh: Mesh) -> None:
+    """Release the handle's device memory (the Mesh object is unusable afterwards)."""
+    if getattr(mesh, "_h", None) is not None:
+        L.load().pf_mesh_destroy(mesh._h)
+        mesh._h = None

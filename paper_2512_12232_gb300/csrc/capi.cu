@@ -319,6 +319,30 @@ pf_status pf_copfi(const pf_batch* h, int variant, int body_lo, int body_hi, dou
   });
 }
 
+pf_status pf_mesh_info(const pf_batch* h, long long* n_nodes, long long* n_dof, int* n_boundary_edges,
+                       double* min_detJ) {
+  pf_mesh_stats st;
+  const pf_status rc = pf_mesh_stats_get(h, 0, &st);
+  if (rc != PF_OK) return rc;
+  if (n_nodes) *n_nodes = st.n_nodes;
+  if (n_dof) *n_dof = st.n_dof;
+  if (n_boundary_edges) *n_boundary_edges = st.n_boundary_edges;
+  if (min_detJ) *min_detJ = st.min_detJ;
+  return PF_OK;
+}
+
+pf_status pf_batch_solve(pf_batch* h, double U, const pf_solve_opts* opts, double* body_psi, pf_solve_info* info,
+                         void* stream) {
+  return pf_psi_solve(h, U, opts, nullptr, body_psi, info, stream);
+}
+
+pf_status pf_batch_grad(pf_batch* h, int objective, int body_lo, int body_hi, double U, double tol, double* dev_dJdX,
+                        double* dJdc, double* J, void* stream) {
+  return pf_grad(h, objective, body_lo, body_hi, U, tol, dev_dJdX, dJdc, J, stream);
+}
+
+void pf_mesh_destroy(pf_batch* h) { pf_batch_destroy(h); }
+
 pf_status pf_grad(pf_batch* h, int objective, int body_lo, int body_hi, double U, double tol, double* dev_dJdX,
                   double* dJdc, double* J, void* stream) {
   return guarded([&]() -> pf_status {

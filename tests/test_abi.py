@@ -45,6 +45,11 @@ def test_error_path_without_gpu(lib_path):
     assert b"NULL" in lib.pf_last_error() or len(lib.pf_last_error()) > 0
     assert lib.pf_set_allocator(_lib.ALLOC_FN(), _lib.FREE_FN(), None) == _lib.PF_OK
     assert lib.pf_workspace_bytes(None) == 0
+    n = C.c_longlong()
+    assert lib.pf_mesh_info(None, C.byref(n), None, None, None) == _lib.PF_EINVAL
+    assert lib.pf_batch_solve(None, 1.0, None, None, None, None) == _lib.PF_EINVAL
+    assert lib.pf_batch_grad(None, 0, 3, 4, 1.0, 1e-12, None, None, None, None) == _lib.PF_EINVAL
+    lib.pf_mesh_destroy(None)  # a NULL handle is a no-op, as for pf_batch_destroy
 
 
 def test_product_path_fails_loudly_without_library(tmp_path):

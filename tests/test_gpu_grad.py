@@ -90,3 +90,28 @@ def test_autograd_function(api):
     J_ref, _, dc_ref, _ = OG.gradient(m, CASE.sweeps, 1.0, 3, 4, 0)
     assert abs(J.item() - J_ref) <= 1e-9
     np.testing.assert_allclose(c.grad.numpy(), dc_ref, rtol=0, atol=1e-7 * np.abs(dc_ref).max())
+
+
+def test_batch_entry_points_agree_with_solve_and_grad(api):
+    """pf_mesh_info / pf_batch_solve / pf_batch_grad / pf_mesh_destroy give what the
+    calls they name give (to solve tolerance: a second solve on the same handle may
+    run on a re-balanced schedule, which changes the order of the dot-product sums)."""
+    cases = W.gradient_study(2, seed=3, nx=128)
+    g = api.batch_build(cases)
+    st = g.stats(0)
+    info = api.mesh_info(g)
+    assert info == {k: st[k] for k in ("n_nodes", "n_dof", "n_boundary_edges", "min_detJ")}
+    r1 = api.psi_solve(g, U=1.0, tol=1e-12, precision=api.PF_MIXED)
+    dX1, dc1, J1 = api.grad(g, 0, 3, 4, 1.0, 1e-12)
+    r2 = api.batch_solve(g, U=1.0, tol=1e-12, precision=api.PF_MIXED)
+    dX2, dc2, J2 = api.batch_grad(g, 0, 3, 4, 1.0, 1e-12)
+    assert r2.psi is None
+    assert all(i["status"] == 0 for i in r2.info)
+    np.testing.assert_allclose(r2.body_psi, r1.body_psi, rtol=0, atol=1e-9 * np.abs(r1.body_psi).max())
+    np.testing.assert_allclose(J2, J1, rtol=1e-9)
+    np.testing.assert_allclose(dc2, dc1, rtol=0, atol=1e-7 * np.abs(dc1).max())
+    np.testing.assert_allclose(dX2.cpu().numpy(), dX1.cpu().numpy(), rtol=0,
+                               atol=1e-7 * dX1.abs().max().item())
+    api.mesh_destroy(g)
+    with pytest.raises(RuntimeError, match="closed"):
+        g.handle
