@@ -125,6 +125,13 @@ struct Batch {
   float* sb32 = nullptr;             // [4][B] mixed-mode CG body values x, r, p, q
   double* ap64[2] = {nullptr, nullptr};   // pf_apply scratch (padded in / out)
   float* ap32[2] = {nullptr, nullptr};
+  CgMaps ap_maps[2];                 // TMA descriptors of the operator kernel (FP64, FP32): s[0] = p input, tag
+  int ap_G[2] = {0, 0};              // its persistent grid per precision (0: not configured yet)
+  int* ap_err = nullptr;             // device flag: a bounded wait of the operator kernel gave up
+  int4* ap_groups = nullptr;         // operator kernel work items: groups of adjacent tiles (descriptors)
+  long long ap_ngroups = 0;
+  unsigned long long* ap_ticket = nullptr;   // its work counter (tickets taken so far)
+  unsigned long long ap_ticket_base = 0;     // tickets consumed by the launches queued so far
   double* sbr64 = nullptr;           // [B] FP64 true-residual body rows
   double* d_rhsb = nullptr;          // [B] body-row right-hand side of the adjoint solve
   bool rhs_active = false;

@@ -39,6 +39,12 @@ constexpr uint8_t RING = 32;         // node on the outer boundary of the box
 constexpr uint8_t CELL_GEN32 = 64;   // general cell whose FP32 coefficients differ from the FP32
                                      // rectangle constants (the FP32 operator needs stored K_e)
 
+// per-tile flags of the fused-CG tile list (k_tile_general)
+constexpr uint8_t TILE_GEN64 = 1;     // a cell of the tile's window needs stored FP64 K_e
+constexpr uint8_t TILE_GEN32 = 2;     // ... stored FP32 K_e
+constexpr uint8_t TILE_PLAIN64 = 4;   // window all FREE, no TILE_GEN64 cell
+constexpr uint8_t TILE_PLAIN32 = 8;   // window all FREE, no TILE_GEN32 cell
+
 // solver phases (per variant)
 constexpr int PH_CG = 0, PH_RESID = 1, PH_DONE = 2;
 

@@ -331,7 +331,8 @@ __global__ void k_tile_general(const DevVariant* var, const int* tile_var, const
   int tot;
   block_exscan(na, &tot, sh);
   if (linear_tid() == 0) {
-    gen[t] = (uint8_t)(g64 | (g32 << 1) | ((allfree && !g64) << 2) | ((allfree && !g32) << 3));
+    gen[t] = (uint8_t)((g64 ? TILE_GEN64 : 0) | (g32 ? TILE_GEN32 : 0) | (allfree && !g64 ? TILE_PLAIN64 : 0) |
+                       (allfree && !g32 ? TILE_PLAIN32 : 0));
     act[t] = tot;
   }
 }

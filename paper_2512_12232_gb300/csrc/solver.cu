@@ -488,7 +488,8 @@ __global__ void __launch_bounds__(NTC, sizeof(T) == 4 ? 2 : 1) k_cg(CGArgs<T> a,
           fence_proxy_async_smem();
           const int2 tij = a.sc.tile_ij[t];
           const int fl = a.tile_gen[t];
-          const bool gen = (fl & (sizeof(T) == 4 ? 2 : 1)) != 0, plain = (fl & (sizeof(T) == 4 ? 8 : 4)) != 0;
+          const bool gen = (fl & (sizeof(T) == 4 ? TILE_GEN32 : TILE_GEN64)) != 0,
+                     plain = (fl & (sizeof(T) == 4 ? TILE_PLAIN32 : TILE_PLAIN64)) != 0;
           s_tij[s] = tij;                         // published to the consumers by the arrive below
           s_tfl[s] = (gen ? 1 : 0) | (plain ? 2 : 0);
           cg_issue<T>(mp, cur, smem + s * L::stage_bytes, &full[s], tij, row0, a.Rtot, gen, plain);
@@ -976,110 +977,187 @@ __global__ void k_from_padded(const DevVariant* var, const long long* lbase, con
   }
 }
 
-// one tile per CTA: y = A p at FREE and BODY nodes (p used as given everywhere)
-// Stand-alone operator y = A p on the padded vectors (pf_apply, pf_apply_timing): one
-// 64x16 tile of the fused-CG tile list per CTA.  The p window with its one-node halo
-// is read as an aligned superset (columns i0-4 .. i0+67) with 16-byte loads, and the tag
-// bytes of non-plain tiles as aligned 4-byte words; every load of the window is issued
-// before any is stored to shared memory, and elements off the grid are set to 0.  Each
-// thread then forms the rows of a 4-node vertical strip exactly as the fused kernel
-// does, reading stored coefficients from the global planes for the cells that need
-// them.  Nodes without an operator row get 0; nodes outside the grid are not written.
-template <typename T> struct Vec16;
-template <> struct Vec16<float> { using type = float4; static constexpr int n = 4; };
-template <> struct Vec16<double> { using type = double2; static constexpr int n = 2; };
+// Stand-alone operator y = A p on the padded vectors (pf_apply, pf_apply_timing).  The
+// tile list is cut into groups of up to AG horizontally adjacent tiles of one tile row;
+// a group's p window (nodes i0-4 .. i0+AG*CTX+3, rows j0-1 .. j0+CTY) has long contiguous
+// rows in HBM (800 bytes of FP32 p for AG = 3).  Persistent CTAs take groups from a
+// ticket counter (tiles whose cells need stored coefficients cost several times a
+// plain tile, so a static split leaves SMs idle); with no reduction, the order does not
+// matter.  A producer warp stages each group's p window and, unless every tile of the
+// group is plain, its tag window (i0-16 .. i0+AG*CTX+15) with TMA into a ring of NS
+// stages; eight consumer warps each form the rows of one 4-node vertical strip per tile
+// exactly as the fused kernel does (stored coefficients come from the global planes
+// for the cells that need them) and release the stage.  Nodes without an operator row
+// get 0; nodes outside the grid are not written.  A wait that gives up sets *err and
+// the CTA stops.
+//
+// Group descriptor (int4): x = i0 | tiles << 20 | FP32 plain bits << 24 | FP64 plain
+// bits << 28, y = j0, z = variant, w = the batch row of j0.  Tickets: every CTA claims
+// one ticket past its last group, so a launch consumes n_groups + gridDim.x tickets
+// from `ticket_base` on.
+constexpr int AG = 3;                             // tiles per group
+static_assert(AG <= 4, "plain bits of a group: 4 per precision");
+template <typename T, int NS>
+struct ApSmem {
+  static constexpr int AW = AG * CTX + 8;         // p box width: x start i0-4 (4 (i0-4) or 8 (i0-4) bytes)
+  static constexpr int H = CTY + 2;
+  static constexpr int TBW = AG * CTX + 32;       // tag box width: x start i0-16
+  static constexpr int align(int b) { return (b + 127) / 128 * 128; }
+  static constexpr int p_bytes = H * AW * (int)sizeof(T);
+  static constexpr int t_bytes = H * TBW;
+  static constexpr int off_t = align(p_bytes);
+  static constexpr int stage_bytes = off_t + align(t_bytes);
+  static constexpr int off_bar = NS * stage_bytes;
+  static constexpr int total = off_bar + 2 * NS * 8;
+  static_assert(off_t % 128 == 0 && stage_bytes % 128 == 0, "TMA destinations must start on 128-byte boundaries");
+  static_assert(AW <= 256 && TBW <= 256 && (AW * sizeof(T)) % 16 == 0 && TBW % 16 == 0,
+                "TMA boxes: at most 256 elements, rows of a multiple of 16 bytes");
+  static_assert(CTX % 16 == 0, "box x coordinates (i0-4) sizeof(T) and i0-16 bytes must be multiples of 16");
+};
+template <typename T> struct ApStages;
+template <> struct ApStages<float> { static constexpr int ns = 4; };
+template <> struct ApStages<double> { static constexpr int ns = 3; };
 
-template <typename T>
-__global__ void __launch_bounds__(NT) k_apply(MeshDev m, const int* tile_var, const int2* tile_ij,
-                                              const uint8_t* tile_flags, const T* __restrict__ p, T* __restrict__ y) {
-  using V16 = typename Vec16<T>::type;
-  constexpr int VN = Vec16<T>::n;                 // elements per 16-byte load
-  constexpr int AW = CTX + 8;                     // window row: columns i0-4 .. i0+CTX+3
-  constexpr int H = CTY + 2;
-  constexpr int NV = AW / VN;                     // 16-byte loads per row
-  constexpr int NLP = (H * NV + NT - 1) / NT;
-  constexpr int NW = AW / 4;                      // tag words per row
-  constexpr int NLT = (H * NW + NT - 1) / NT;
-  __shared__ __align__(16) T ps[H * AW];
-  __shared__ __align__(16) uint32_t ts32[H * NW];
-  const uint8_t* ts = reinterpret_cast<const uint8_t*>(ts32);
-  const int t = blockIdx.x;
-  const DevVariant& V = m.var[tile_var[t]];
-  const int2 ij = tile_ij[t];
-  const bool plain = (tile_flags[t] & (sizeof(T) == 4 ? 8 : 4)) != 0;
-  const int tid = linear_tid();
-  const long long base = V.base;
-  const int P = V.P, nx = V.nx, ny = V.ny;
-  // Loads start at multiples of 4 columns inside a row whose pitch is a multiple of 32,
-  // so none crosses the row end; rows or loads wholly off the grid are not read.
-  V16 pv[NLP];
-  uint32_t tv[NLT];
-#pragma unroll
-  for (int k = 0; k < NLP; ++k) {
-    const int q = tid + k * NT;
-    const int w = q % NV, lj = q / NV;
-    const int i = ij.x - 4 + VN * w, j = ij.y - 1 + lj;
-    const bool in = q < H * NV && j >= 0 && j <= ny && i + VN - 1 >= 0 && i <= nx;
-    V16 z;
-    memset(&z, 0, sizeof(z));
-    pv[k] = in ? __ldg(reinterpret_cast<const V16*>(p + base + (long long)j * P + i)) : z;
-  }
-#pragma unroll
-  for (int k = 0; k < NLT; ++k) {
-    const int q = tid + k * NT;
-    const int w = q % NW, lj = q / NW;
-    const int i = ij.x - 4 + 4 * w, j = ij.y - 1 + lj;
-    const bool in = !plain && q < H * NW && j >= 0 && j <= ny && i >= 0 && i <= nx;
-    tv[k] = in ? __ldg(reinterpret_cast<const uint32_t*>(m.tag + base + (long long)j * P + i)) : 0u;
-  }
-#pragma unroll
-  for (int k = 0; k < NLP; ++k) {
-    const int q = tid + k * NT;
-    if (q < H * NV) {
-      const int w = q % NV;
-      const int i = ij.x - 4 + VN * w;
-      T e[VN];
-      memcpy(e, &pv[k], sizeof(e));
-#pragma unroll
-      for (int c = 0; c < VN; ++c)
-        if (i + c < 0 || i + c > nx) e[c] = T(0);
-      memcpy(&ps[q * VN], e, sizeof(e));
+template <typename T, int NS>
+__global__ void __launch_bounds__(NTC) k_apply(MeshDev m, const int4* __restrict__ groups, long long n_groups,
+                                               unsigned long long* ticket, unsigned long long ticket_base,
+                                               T* __restrict__ y, const __grid_constant__ CgMaps mp, int* err,
+                                               int poll_limit) {
+  using L = ApSmem<T, NS>;
+  constexpr int AW = L::AW, TBW = L::TBW;
+  constexpr int PSHIFT = sizeof(T) == 4 ? 24 : 28;
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ int4 s_grp[NS];                      // the group in each stage (tiles = 0: end marker)
+  __shared__ int s_abort, s_issued;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + L::off_bar);
+  uint64_t* empty = full + NS;
+  const int tid = threadIdx.y * TX + threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) {
+    for (int k = 0; k < NS; ++k) {
+      mbar_init(&full[k], 1);
+      mbar_init(&empty[k], NT / 32);
     }
-  }
-#pragma unroll
-  for (int k = 0; k < NLT; ++k) {
-    const int q = tid + k * NT;
-    if (q < H * NW) ts32[q] = tv[k];
+    fence_mbar_init();
+    s_abort = 0;
+    s_issued = 0;
   }
   __syncthreads();
-  T kr[6];
-#pragma unroll
-  for (int c = 0; c < 6; ++c) kr[c] = krect<T>(V)[c];
-  const int col = tid % CTX, row_lo = (tid / CTX) * STRIP;
-  const int i = ij.x + col;
-  if (i > nx) return;
-  // window node (li, lj) (li = i - i0 + 1) sits at column li + 3 of the stored rows
-#pragma unroll
-  for (int u = 0; u < STRIP; ++u) {
-    const int j = ij.y + row_lo + u;
-    if (j > ny) break;
-    const int c = col + 4, lj = 1 + row_lo + u;
-    const long long n = base + (long long)j * P + i;
-    const T nbh[3][3] = {{ps[(lj - 1) * AW + c - 1], ps[(lj - 1) * AW + c], ps[(lj - 1) * AW + c + 1]},
-                         {ps[lj * AW + c - 1], ps[lj * AW + c], ps[lj * AW + c + 1]},
-                         {ps[(lj + 1) * AW + c - 1], ps[(lj + 1) * AW + c], ps[(lj + 1) * AW + c + 1]}};
-    T out = T(0);
-    if (plain) {
-      out = q4_row_rect<T>(nbh, kr);
-    } else {
-      const uint8_t tg = ts[lj * AW + c];
-      const int kind = tg & KIND_MASK;
-      if (kind == K_FREE || kind == K_BODY)
-        out = q4_row_nb<T, false>(nbh, tg, ts[lj * AW + c - 1], ts[(lj - 1) * AW + c - 1], ts[(lj - 1) * AW + c],
-                                  nullptr, 0, 0, n, P, kplane<T>(m), m.Vtot, kr);
+  if (warp == NT / 32) {
+    // ---- TMA producer (lane 0): the next group is claimed and its descriptor loaded
+    // before waiting for the current group's stage
+    if (lane == 0) {
+      int q = 0;
+      long long item = (long long)(atomicAdd(ticket, 1ULL) - ticket_base);
+      int4 d = (item >= 0 && item < n_groups) ? groups[item] : make_int4(0, 0, 0, 0);
+      bool stop = false;
+      while (item >= 0 && item < n_groups) {
+        const long long nitem = (long long)(atomicAdd(ticket, 1ULL) - ticket_base);
+        const int4 nd = (nitem >= 0 && nitem < n_groups) ? groups[nitem] : d;
+        const int s = q % NS, use = q / NS;
+        if (use > 0 && !mbar_wait(&empty[s], (use - 1) & 1, poll_limit)) {
+          atomicExch(err, 1);
+          s_abort = 1;
+          stop = true;
+          break;
+        }
+        fence_proxy_async_smem();
+        const int x = d.x & 0xfffff, g = (d.x >> 20) & 15, pl = (d.x >> PSHIFT) & 15;
+        const bool all_plain = pl == (1 << g) - 1;
+        s_grp[s] = make_int4(x, d.y, d.z, g | (pl << 4));   // published to the consumers by the arrive below
+        unsigned char* st = smem + s * L::stage_bytes;
+        mbar_arrive_expect_tx(&full[s], L::p_bytes + (all_plain ? 0 : L::t_bytes));
+        tma_load_2d(st, &mp.s[0], x - 4, d.w - 1, &full[s]);
+        if (!all_plain) tma_load_2d(st + L::off_t, &mp.tag, x - 16, d.w - 1, &full[s]);
+        s_issued = ++q;
+        item = nitem;
+        d = nd;
+      }
+      // end marker: a stage with no tiles, completed by a plain arrival
+      if (!stop) {
+        const int s = q % NS, use = q / NS;
+        if (use > 0 && !mbar_wait(&empty[s], (use - 1) & 1, poll_limit)) {
+          atomicExch(err, 1);
+          s_abort = 1;
+        } else {
+          s_grp[s] = make_int4(0, 0, 0, 0);
+          mbar_arrive(&full[s]);
+        }
+      }
     }
-    y[n] = out;
+  } else {
+    // ---- consumers: warps run independently, each releasing a stage once it is done
+    const int col = tid % CTX, row_lo = (tid / CTX) * STRIP;
+    int lastv = -1, nx = 0, ny = 0, P = 0;
+    long long base = 0;
+    T kr[6];
+    for (int q = 0;; ++q) {
+      const int s = q % NS;
+      if (!mbar_wait(&full[s], (q / NS) & 1, poll_limit)) {
+        atomicExch(err, 1);
+        s_abort = 1;
+        break;
+      }
+      const int4 gd = s_grp[s];
+      const int g = gd.w & 15;
+      if (g == 0) break;                          // the producer's end marker
+      const int2 ij = make_int2(gd.x, gd.y);
+      const int v = gd.z;
+      if (v != lastv) {
+        const DevVariant& V = m.var[v];
+        nx = V.nx; ny = V.ny; P = V.P; base = V.base;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) kr[c] = krect<T>(V)[c];
+        lastv = v;
+      }
+      const unsigned char* st = smem + s * L::stage_bytes;
+      const T* ps = reinterpret_cast<const T*>(st);                    // box origin (i0-4, j0-1)
+      const uint8_t* Tg = st + L::off_t;                               // box origin (i0-16, j0-1)
+      // flags of cell (i0 + ci, j0 + cj), 0 for cells outside the variant
+      auto cellf = [&](int ci, int cj) -> uint8_t {
+        return ((unsigned)(ij.x + ci) < (unsigned)nx && (unsigned)(ij.y + cj) < (unsigned)ny)
+                   ? Tg[(cj + 1) * TBW + ci + 16]
+                   : (uint8_t)0;
+      };
+      for (int u = 0; u < g; ++u) {
+        const int c = u * CTX + col;              // column inside the group
+        const int i = ij.x + c;
+        if (i > nx) break;
+        const bool plain = (gd.w >> (4 + u)) & 1;
+        T win[STRIP + 2][3];                      // p around the strip: box rows row_lo .. row_lo+5
+#pragma unroll
+        for (int r = 0; r < STRIP + 2; ++r)
+#pragma unroll
+          for (int cc = 0; cc < 3; ++cc) win[r][cc] = ps[(row_lo + r) * AW + c + 3 + cc];
+#pragma unroll
+        for (int w = 0; w < STRIP; ++w) {
+          const int rl = row_lo + w, j = ij.y + rl;
+          if (j > ny) break;
+          const long long n = base + (long long)j * P + i;
+          const T nbh[3][3] = {{win[w][0], win[w][1], win[w][2]},
+                               {win[w + 1][0], win[w + 1][1], win[w + 1][2]},
+                               {win[w + 2][0], win[w + 2][1], win[w + 2][2]}};
+          T out = T(0);
+          if (plain) {
+            out = q4_row_rect<T>(nbh, kr);
+          } else {
+            const int kind = Tg[(rl + 1) * TBW + c + 16] & KIND_MASK;
+            if (kind == K_FREE || kind == K_BODY)
+              out = q4_row_nb<T, false>(nbh, cellf(c, rl), cellf(c - 1, rl), cellf(c - 1, rl - 1),
+                                        cellf(c, rl - 1), nullptr, 0, 0, n, P, kplane<T>(m), m.Vtot, kr);
+          }
+          y[n] = out;
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[s]);
+    }
   }
+  __syncthreads();
+  if (s_abort && tid == 0) {
+    // only the last NS issued groups can still be in flight: wait for them (bounded)
+    for (int k = max(0, s_issued - NS); k < s_issued; ++k) mbar_wait(&full[k % NS], (k / NS) & 1, poll_limit);
+  }
+  __syncthreads();
 }
 
 // collapsed body rows: one CTA per global body, fixed-order sum
@@ -1283,7 +1361,7 @@ static CgConfig& cg_config(Batch& b, int precision, int ns) {
   std::vector<int> act(std::max<long long>(1, T));
   PF_CUDA(cudaMemcpy(gen.data(), b.tile_cg_gen, T, cudaMemcpyDeviceToHost));
   PF_CUDA(cudaMemcpy(act.data(), b.tile_cg_act, T * sizeof(int), cudaMemcpyDeviceToHost));
-  const int gbit = precision == PF_FP64 ? 1 : 2;
+  const int gbit = precision == PF_FP64 ? TILE_GEN64 : TILE_GEN32;
   const double w_gen = precision == PF_FP64 ? 0.6 : 1.47;
   c.tile_var.assign(T, 0);
   c.tile_cost.assign(T, 0.0);
@@ -1433,18 +1511,85 @@ static double* body_sum_scratch(Batch& b) {
   return b.d_bsum;
 }
 
+// The operator kernel reads p from the first scratch buffer of its precision through
+// TMA descriptors made once here, and writes the second.
 static void ensure_apply_buffers(Batch& b) {
   if (!b.ap64[0]) {
     for (int k = 0; k < 2; ++k) {
       b.ap64[k] = (double*)dev_alloc(b, b.Vtot * sizeof(double));
       b.ap32[k] = (float*)dev_alloc(b, b.Vtot * sizeof(float));
     }
+    b.ap_err = (int*)dev_alloc(b, sizeof(int));
+    PF_CUDA(cudaMemsetAsync(b.ap_err, 0, sizeof(int), b.stream));
+    b.ap_ticket = (unsigned long long*)dev_alloc(b, sizeof(unsigned long long));
+    PF_CUDA(cudaMemsetAsync(b.ap_ticket, 0, sizeof(unsigned long long), b.stream));
+    b.ap_ticket_base = 0;
+    // work items: up to AG consecutive tiles of one variant and tile row
+    const long long T = b.Tcg;
+    std::vector<int2> ij(T);
+    std::vector<int> var(T);
+    std::vector<uint8_t> fl(T);
+    PF_CUDA(cudaMemcpy(ij.data(), b.tile_cg_ij, T * sizeof(int2), cudaMemcpyDeviceToHost));
+    PF_CUDA(cudaMemcpy(var.data(), b.tile_cg_var, T * sizeof(int), cudaMemcpyDeviceToHost));
+    PF_CUDA(cudaMemcpy(fl.data(), b.tile_cg_gen, T, cudaMemcpyDeviceToHost));
+    std::vector<int4> gr;
+    for (long long t = 0; t < T;) {
+      int g = 1;
+      while (g < AG && t + g < T && var[t + g] == var[t] && ij[t + g].y == ij[t].y) ++g;
+      int pl32 = 0, pl64 = 0;
+      for (int k = 0; k < g; ++k) {
+        pl32 |= ((fl[t + k] & TILE_PLAIN32) != 0) << k;
+        pl64 |= ((fl[t + k] & TILE_PLAIN64) != 0) << k;
+      }
+      if (ij[t].x >= (1 << 20)) throw Error{PF_EINVAL, "grid too wide for the operator kernel (nx >= 2^20)"};
+      const HostVariant& H = b.hv[var[t]];
+      const int row0 = (int)(H.base / H.P);
+      gr.push_back(make_int4(ij[t].x | (g << 20) | (pl32 << 24) | (pl64 << 28), ij[t].y, var[t], row0 + ij[t].y));
+      t += g;
+    }
+    b.ap_ngroups = (long long)gr.size();
+    b.ap_groups = (int4*)dev_alloc(b, std::max<size_t>(1, gr.size()) * sizeof(int4));
+    PF_CUDA(cudaMemcpy(b.ap_groups, gr.data(), gr.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    using L64 = ApSmem<double, ApStages<double>::ns>;
+    using L32 = ApSmem<float, ApStages<float>::ns>;
+    encode_2d(&b.ap_maps[0].s[0], b.ap64[0], CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 8, b.P, b.Rtot, L64::AW, L64::H);
+    encode_2d(&b.ap_maps[0].tag, b.tag, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, b.P, b.Rtot, L64::TBW, L64::H);
+    encode_2d(&b.ap_maps[1].s[0], b.ap32[0], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, b.P, b.Rtot, L32::AW, L32::H);
+    encode_2d(&b.ap_maps[1].tag, b.tag, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, b.P, b.Rtot, L32::TBW, L32::H);
   }
 }
 
+// y = A p with p in the first scratch buffer of T's precision (persistent grid: SMs x
+// resident CTAs, at most one CTA per work item).
 template <typename T>
-static void launch_apply(Batch& b, const MeshDev& m, const T* p, T* y) {
-  k_apply<T><<<(unsigned)b.Tcg, NT, 0, b.stream>>>(m, b.tile_cg_var, b.tile_cg_ij, b.tile_cg_gen, p, y);
+static void launch_apply(Batch& b, const MeshDev& m, T* y) {
+  constexpr int NS = ApStages<T>::ns;
+  using L = ApSmem<T, NS>;
+  const int k = sizeof(T) == 8 ? 0 : 1;
+  if (!b.ap_G[k]) {
+    const void* f = (const void*)k_apply<T, NS>;
+    PF_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, L::total));
+    int occ = 0;
+    PF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, f, NTC, L::total));
+    b.ap_G[k] = (int)std::max<long long>(1, std::min<long long>((long long)b.nsm * std::max(1, occ), b.ap_ngroups));
+  }
+  k_apply<T, NS><<<b.ap_G[k], dim3(TX, NTC / TX), L::total, b.stream>>>(
+      m, b.ap_groups, b.ap_ngroups, b.ap_ticket, b.ap_ticket_base, y, b.ap_maps[k], b.ap_err, MBAR_POLL_LIMIT);
+  b.ap_ticket_base += (unsigned long long)b.ap_ngroups + (unsigned long long)b.ap_G[k];
+}
+
+// After the stream has been synchronised: did a bounded wait of the operator kernel give up?
+static void check_apply_err(Batch& b) {
+  int e = 0;
+  PF_CUDA(cudaMemcpyAsync(&e, b.ap_err, sizeof(int), cudaMemcpyDeviceToHost, b.stream));
+  PF_CUDA(cudaStreamSynchronize(b.stream));
+  if (e) {
+    // a CTA that stopped early took fewer tickets: restart the count
+    PF_CUDA(cudaMemsetAsync(b.ap_err, 0, sizeof(int), b.stream));
+    PF_CUDA(cudaMemsetAsync(b.ap_ticket, 0, sizeof(unsigned long long), b.stream));
+    b.ap_ticket_base = 0;
+    throw Error{PF_ETIMEOUT, "a bounded wait in the operator kernel gave up (TMA tile not delivered)"};
+  }
 }
 
 // Mean time of `reps` back-to-back stand-alone operator applications on the handle's
@@ -1461,8 +1606,8 @@ void apply_timing(Batch& b, int precision, int reps, double* us, double* bytes) 
   const size_t es = precision == PF_FP64 ? sizeof(double) : sizeof(float);
   PF_CUDA(cudaMemsetAsync(precision == PF_FP64 ? (void*)b.ap64[0] : (void*)b.ap32[0], 0, b.Vtot * es, b.stream));
   auto launch = [&]() {
-    if (precision == PF_FP64) launch_apply<double>(b, m, b.ap64[0], b.ap64[1]);
-    else launch_apply<float>(b, m, b.ap32[0], b.ap32[1]);
+    if (precision == PF_FP64) launch_apply<double>(b, m, b.ap64[1]);
+    else launch_apply<float>(b, m, b.ap32[1]);
   };
   for (int k = 0; k < 3; ++k) launch();      // warm-up
   PF_CUDA(cudaEventRecord(b.ev[0], b.stream));
@@ -1472,6 +1617,7 @@ void apply_timing(Batch& b, int precision, int reps, double* us, double* bytes) 
   PF_CUDA(cudaEventSynchronize(b.ev[1]));
   float ms = 0;
   PF_CUDA(cudaEventElapsedTime(&ms, b.ev[0], b.ev[1]));
+  check_apply_err(b);
   b.launches += 3 + reps;
   double by = 0.0;
   for (const HostVariant& H : b.hv) {
@@ -1491,13 +1637,13 @@ void apply_operator(Batch& b, int precision, const double* dev_p, double* dev_y,
   if (precision == PF_FP64) {
     k_to_padded<double><<<g2, 256, 0, b.stream>>>(b.d_var, lb, dev_p, b.ap64[0]);
     PF_CUDA(cudaMemsetAsync(b.ap64[1], 0, b.Vtot * sizeof(double), b.stream));
-    launch_apply<double>(b, m, b.ap64[0], b.ap64[1]);
+    launch_apply<double>(b, m, b.ap64[1]);
     k_from_padded<double><<<g2, 256, 0, b.stream>>>(b.d_var, lb, b.ap64[1], dev_y);
     if (b.B) k_body_sums<double><<<b.B, dim3(TX, TY), 0, b.stream>>>(m, b.ap64[1], sums);
   } else {
     k_to_padded<float><<<g2, 256, 0, b.stream>>>(b.d_var, lb, dev_p, b.ap32[0]);
     PF_CUDA(cudaMemsetAsync(b.ap32[1], 0, b.Vtot * sizeof(float), b.stream));
-    launch_apply<float>(b, m, b.ap32[0], b.ap32[1]);
+    launch_apply<float>(b, m, b.ap32[1]);
     k_from_padded<float><<<g2, 256, 0, b.stream>>>(b.d_var, lb, b.ap32[1], dev_y);
     if (b.B) k_body_sums<float><<<b.B, dim3(TX, TY), 0, b.stream>>>(m, b.ap32[1], sums);
   }
@@ -1506,6 +1652,7 @@ void apply_operator(Batch& b, int precision, const double* dev_p, double* dev_y,
     PF_CUDA(cudaMemcpyAsync(body_sums, sums, b.B * sizeof(double), cudaMemcpyDeviceToHost, b.stream));
   }
   PF_CUDA(cudaStreamSynchronize(b.stream));
+  check_apply_err(b);
 }
 
 template <typename T>
