@@ -1128,6 +1128,18 @@ __global__ void __launch_bounds__(NTC) k_apply(MeshDev m, const int4* __restrict
         for (int r = 0; r < STRIP + 2; ++r)
 #pragma unroll
           for (int cc = 0; cc < 3; ++cc) win[r][cc] = ps[(row_lo + r) * AW + c + 3 + cc];
+        if (plain) {
+          // a plain tile's window is inside the grid: no bounds checks
+          T* yo = y + base + (long long)(ij.y + row_lo) * P + i;
+#pragma unroll
+          for (int w = 0; w < STRIP; ++w) {
+            const T nbh[3][3] = {{win[w][0], win[w][1], win[w][2]},
+                                 {win[w + 1][0], win[w + 1][1], win[w + 1][2]},
+                                 {win[w + 2][0], win[w + 2][1], win[w + 2][2]}};
+            yo[(long long)w * P] = q4_row_rect<T>(nbh, kr);
+          }
+          continue;
+        }
 #pragma unroll
         for (int w = 0; w < STRIP; ++w) {
           const int rl = row_lo + w, j = ij.y + rl;
@@ -1137,14 +1149,10 @@ __global__ void __launch_bounds__(NTC) k_apply(MeshDev m, const int4* __restrict
                                {win[w + 1][0], win[w + 1][1], win[w + 1][2]},
                                {win[w + 2][0], win[w + 2][1], win[w + 2][2]}};
           T out = T(0);
-          if (plain) {
-            out = q4_row_rect<T>(nbh, kr);
-          } else {
-            const int kind = Tg[(rl + 1) * TBW + c + 16] & KIND_MASK;
-            if (kind == K_FREE || kind == K_BODY)
-              out = q4_row_nb<T, false>(nbh, cellf(c, rl), cellf(c - 1, rl), cellf(c - 1, rl - 1),
-                                        cellf(c, rl - 1), nullptr, 0, 0, n, P, kplane<T>(m), m.Vtot, kr);
-          }
+          const int kind = Tg[(rl + 1) * TBW + c + 16] & KIND_MASK;
+          if (kind == K_FREE || kind == K_BODY)
+            out = q4_row_nb<T, false>(nbh, cellf(c, rl), cellf(c - 1, rl), cellf(c - 1, rl - 1), cellf(c, rl - 1),
+                                      nullptr, 0, 0, n, P, kplane<T>(m), m.Vtot, kr);
           y[n] = out;
         }
       }
