@@ -320,8 +320,9 @@ __device__ __forceinline__ T q4_row_rect(const T (&p)[3][3], const T* kr) {
 // four cells: c0 = (i, j), c1 = (i-1, j), c2 = (i-1, j-1), c3 = (i, j-1).  Displaced
 // cells read their six coefficients from the staged boxes (STAGED: the fused kernel's
 // FP32 path) or from the global planes; undisplaced cells use the closed-form rectangle
-// constants kr.
-template <typename T, bool STAGED = sizeof(T) == 4>
+// constants kr.  HOIST (global planes only): issue all of a node's coefficient loads
+// before the first use, at the cost of 12 more live registers.
+template <typename T, bool STAGED = sizeof(T) == 4, bool HOIST = false>
 __device__ __forceinline__ T q4_row_nb(const T (&p)[3][3], uint8_t c0, uint8_t c1, uint8_t c2, uint8_t c3,
                                        const T* ks, int kcol, int krow, long long n, int P,
                                        const T* __restrict__ Kg, long long plane, const T* kr) {
@@ -334,6 +335,33 @@ __device__ __forceinline__ T q4_row_nb(const T (&p)[3][3], uint8_t c0, uint8_t c
   if ((c0 & FLAGS) == CELL_ACTIVE && (c1 & FLAGS) == CELL_ACTIVE && (c2 & FLAGS) == CELL_ACTIVE &&
       (c3 & FLAGS) == CELL_ACTIVE)
     return q4_row_rect<T>(p, kr);
+  if constexpr (!STAGED && HOIST) {
+    // global planes: every coefficient load is issued before the first is used (one
+    // round trip per node instead of one per displaced cell); same arithmetic as below
+    T a0 = kr[0], a1 = kr[1], a2 = kr[2];         // cell (i, j):         K01 K02 K03
+    T b0 = kr[0], b1 = kr[3], b2 = kr[4];         // cell (i-1, j):       K01 K12 K13
+    T e0 = kr[1], e1 = kr[3], e2 = kr[5];         // cell (i-1, j-1):     K02 K12 K23
+    T f0 = kr[2], f1 = kr[4], f2 = kr[5];         // cell (i, j-1):       K03 K13 K23
+    if (c0 & GEN) { a0 = __ldg(Kg + n); a1 = __ldg(Kg + plane + n); a2 = __ldg(Kg + 2 * plane + n); }
+    if (c1 & GEN) {
+      const long long c = n - 1;
+      b0 = __ldg(Kg + c); b1 = __ldg(Kg + 3 * plane + c); b2 = __ldg(Kg + 4 * plane + c);
+    }
+    if (c2 & GEN) {
+      const long long c = n - P - 1;
+      e0 = __ldg(Kg + plane + c); e1 = __ldg(Kg + 3 * plane + c); e2 = __ldg(Kg + 5 * plane + c);
+    }
+    if (c3 & GEN) {
+      const long long c = n - P;
+      f0 = __ldg(Kg + 2 * plane + c); f1 = __ldg(Kg + 4 * plane + c); f2 = __ldg(Kg + 5 * plane + c);
+    }
+    T y = T(0);
+    if (c0 & CELL_ACTIVE) y += a0 * dE + a1 * dNE + a2 * dN;
+    if (c1 & CELL_ACTIVE) y += b0 * dW + b1 * dN + b2 * dNW;
+    if (c2 & CELL_ACTIVE) y += e0 * dSW + e1 * dS + e2 * dW;
+    if (c3 & CELL_ACTIVE) y += f0 * dS + f1 * dSE + f2 * dE;
+    return y;
+  }
   // coefficient m of the cell whose corner 0 is at box column kc, box row kr_, global index g
   auto coef = [&](int m, int kr_, int kc, long long g) -> T {
     if constexpr (STAGED) {
@@ -1019,7 +1047,7 @@ template <> struct ApStages<float> { static constexpr int ns = 4; };
 template <> struct ApStages<double> { static constexpr int ns = 3; };
 
 template <typename T, int NS>
-__global__ void __launch_bounds__(NTC) k_apply(MeshDev m, const int4* __restrict__ groups, long long n_groups,
+__global__ void __launch_bounds__(NTC, sizeof(T) == 4 ? 3 : 1) k_apply(MeshDev m, const int4* __restrict__ groups, long long n_groups,
                                                unsigned long long* ticket, unsigned long long ticket_base,
                                                T* __restrict__ y, const __grid_constant__ CgMaps mp, int* err,
                                                int poll_limit) {
@@ -1151,8 +1179,8 @@ __global__ void __launch_bounds__(NTC) k_apply(MeshDev m, const int4* __restrict
           T out = T(0);
           const int kind = Tg[(rl + 1) * TBW + c + 16] & KIND_MASK;
           if (kind == K_FREE || kind == K_BODY)
-            out = q4_row_nb<T, false>(nbh, cellf(c, rl), cellf(c - 1, rl), cellf(c - 1, rl - 1), cellf(c, rl - 1),
-                                      nullptr, 0, 0, n, P, kplane<T>(m), m.Vtot, kr);
+            out = q4_row_nb<T, false, true>(nbh, cellf(c, rl), cellf(c - 1, rl), cellf(c - 1, rl - 1),
+                                            cellf(c, rl - 1), nullptr, 0, 0, n, P, kplane<T>(m), m.Vtot, kr);
           y[n] = out;
         }
       }
