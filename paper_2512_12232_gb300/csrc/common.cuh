@@ -255,42 +255,36 @@ __device__ __forceinline__ T q4_row(const T (*ps)[SW], const uint8_t (*ts)[SW], 
   const T dN = ps[lj + 1][li] - pc, dS = ps[lj - 1][li] - pc;
   const T dNE = ps[lj + 1][li + 1] - pc, dNW = ps[lj + 1][li - 1] - pc;
   const T dSE = ps[lj - 1][li + 1] - pc, dSW = ps[lj - 1][li - 1] - pc;
+  // the four cells' tags, then every stored coefficient the node needs (all loads are
+  // issued before the first is used), then the sum over the cells
+  const uint8_t t0 = ts[lj][li];                // cell (i, j): node is corner 0
+  const uint8_t t1 = ts[lj][li - 1];            // cell (i-1, j): corner 1
+  const uint8_t t2 = ts[lj - 1][li - 1];        // cell (i-1, j-1): corner 2
+  const uint8_t t3 = ts[lj - 1][li];            // cell (i, j-1): corner 3
+  T a0 = kr[0], a1 = kr[1], a2 = kr[2];         // K01 K02 K03 of cell (i, j)
+  T b0 = kr[0], b1 = kr[3], b2 = kr[4];         // K01 K12 K13 of cell (i-1, j)
+  T e0 = kr[1], e1 = kr[3], e2 = kr[5];         // K02 K12 K23 of cell (i-1, j-1)
+  T f0 = kr[2], f1 = kr[4], f2 = kr[5];         // K03 K13 K23 of cell (i, j-1)
+  if ((t0 & (CELL_ACTIVE | CELL_GENERAL)) == (CELL_ACTIVE | CELL_GENERAL)) {
+    a0 = __ldg(K + n); a1 = __ldg(K + plane + n); a2 = __ldg(K + 2 * plane + n);
+  }
+  if ((t1 & (CELL_ACTIVE | CELL_GENERAL)) == (CELL_ACTIVE | CELL_GENERAL)) {
+    const long long c = n - 1;
+    b0 = __ldg(K + c); b1 = __ldg(K + 3 * plane + c); b2 = __ldg(K + 4 * plane + c);
+  }
+  if ((t2 & (CELL_ACTIVE | CELL_GENERAL)) == (CELL_ACTIVE | CELL_GENERAL)) {
+    const long long c = n - P - 1;
+    e0 = __ldg(K + plane + c); e1 = __ldg(K + 3 * plane + c); e2 = __ldg(K + 5 * plane + c);
+  }
+  if ((t3 & (CELL_ACTIVE | CELL_GENERAL)) == (CELL_ACTIVE | CELL_GENERAL)) {
+    const long long c = n - P;
+    f0 = __ldg(K + 2 * plane + c); f1 = __ldg(K + 4 * plane + c); f2 = __ldg(K + 5 * plane + c);
+  }
   T y = T(0);
-  uint8_t t = ts[lj][li];                      // cell (i, j): node is corner 0
-  if (t & CELL_ACTIVE) {
-    T k01 = kr[0], k02 = kr[1], k03 = kr[2];
-    if (t & CELL_GENERAL) {
-      k01 = __ldg(K + n); k02 = __ldg(K + plane + n); k03 = __ldg(K + 2 * plane + n);
-    }
-    y += k01 * dE + k02 * dNE + k03 * dN;
-  }
-  t = ts[lj][li - 1];                          // cell (i-1, j): corner 1
-  if (t & CELL_ACTIVE) {
-    T k01 = kr[0], k12 = kr[3], k13 = kr[4];
-    if (t & CELL_GENERAL) {
-      const long long c = n - 1;
-      k01 = __ldg(K + c); k12 = __ldg(K + 3 * plane + c); k13 = __ldg(K + 4 * plane + c);
-    }
-    y += k01 * dW + k12 * dN + k13 * dNW;
-  }
-  t = ts[lj - 1][li - 1];                      // cell (i-1, j-1): corner 2
-  if (t & CELL_ACTIVE) {
-    T k02 = kr[1], k12 = kr[3], k23 = kr[5];
-    if (t & CELL_GENERAL) {
-      const long long c = n - P - 1;
-      k02 = __ldg(K + plane + c); k12 = __ldg(K + 3 * plane + c); k23 = __ldg(K + 5 * plane + c);
-    }
-    y += k02 * dSW + k12 * dS + k23 * dW;
-  }
-  t = ts[lj - 1][li];                          // cell (i, j-1): corner 3
-  if (t & CELL_ACTIVE) {
-    T k03 = kr[2], k13 = kr[4], k23 = kr[5];
-    if (t & CELL_GENERAL) {
-      const long long c = n - P;
-      k03 = __ldg(K + 2 * plane + c); k13 = __ldg(K + 4 * plane + c); k23 = __ldg(K + 5 * plane + c);
-    }
-    y += k03 * dS + k13 * dSE + k23 * dE;
-  }
+  if (t0 & CELL_ACTIVE) y += a0 * dE + a1 * dNE + a2 * dN;
+  if (t1 & CELL_ACTIVE) y += b0 * dW + b1 * dN + b2 * dNW;
+  if (t2 & CELL_ACTIVE) y += e0 * dSW + e1 * dS + e2 * dW;
+  if (t3 & CELL_ACTIVE) y += f0 * dS + f1 * dSE + f2 * dE;
   return y;
 }
 

@@ -342,16 +342,16 @@ __device__ __forceinline__ T q4_row_nb(const T (&p)[3][3], uint8_t c0, uint8_t c
     T b0 = kr[0], b1 = kr[3], b2 = kr[4];         // cell (i-1, j):       K01 K12 K13
     T e0 = kr[1], e1 = kr[3], e2 = kr[5];         // cell (i-1, j-1):     K02 K12 K23
     T f0 = kr[2], f1 = kr[4], f2 = kr[5];         // cell (i, j-1):       K03 K13 K23
-    if (c0 & GEN) { a0 = __ldg(Kg + n); a1 = __ldg(Kg + plane + n); a2 = __ldg(Kg + 2 * plane + n); }
-    if (c1 & GEN) {
+    if ((c0 & FLAGS) == FLAGS) { a0 = __ldg(Kg + n); a1 = __ldg(Kg + plane + n); a2 = __ldg(Kg + 2 * plane + n); }
+    if ((c1 & FLAGS) == FLAGS) {
       const long long c = n - 1;
       b0 = __ldg(Kg + c); b1 = __ldg(Kg + 3 * plane + c); b2 = __ldg(Kg + 4 * plane + c);
     }
-    if (c2 & GEN) {
+    if ((c2 & FLAGS) == FLAGS) {
       const long long c = n - P - 1;
       e0 = __ldg(Kg + plane + c); e1 = __ldg(Kg + 3 * plane + c); e2 = __ldg(Kg + 5 * plane + c);
     }
-    if (c3 & GEN) {
+    if ((c3 & FLAGS) == FLAGS) {
       const long long c = n - P;
       f0 = __ldg(Kg + 2 * plane + c); f1 = __ldg(Kg + 4 * plane + c); f2 = __ldg(Kg + 5 * plane + c);
     }
@@ -706,8 +706,9 @@ __global__ void __launch_bounds__(NTC, sizeof(T) == 4 ? 2 : 1) k_cg(CGArgs<T> a,
               const T nbh[3][3] = {{win[u][0], win[u][1], win[u][2]},
                                    {win[u + 1][0], win[u + 1][1], win[u + 1][2]},
                                    {win[u + 2][0], win[u + 2][1], win[u + 2][2]}};
-              const T y = q4_row_nb<T>(nbh, cr[u + 1], cl[u + 1], cl[u], cr[u], Ks, col + 4, row_lo + u + 1, n, P,
-                                       kplane<T>(a.m), plane, kr);
+              const T y = q4_row_nb<T, sizeof(T) == 4, sizeof(T) == 8>(nbh, cr[u + 1], cl[u + 1], cl[u], cr[u], Ks,
+                                                                       col + 4, row_lo + u + 1, n, P, kplane<T>(a.m),
+                                                                       plane, kr);
               State4<T> o;
               o.x = kind == K_BODY ? slot_bits(bs4[u], T(0)) : xn4[u];
               o.r = rn4[u];
