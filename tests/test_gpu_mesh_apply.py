@@ -77,6 +77,41 @@ def test_operator_matches_oracle(api, case):
     np.testing.assert_allclose(b32, body_ref, rtol=0, atol=1e-5 * scale * 10)
 
 
+def test_operator_after_many_launches(api):
+    """The operator kernel hands out work from a counter that persists across launches
+    and precisions: after many timed launches of both, pf_apply on a two-variant batch
+    still matches the oracle, and two calls agree bit for bit (which CTA takes which
+    group of tiles changes nothing in a node's arithmetic)."""
+    cases = [W.five_cylinder_case(0.5, 200, 100, 20), W.five_cylinder_case(1.0, 263, 131, 20)]   # one sweep count per batch
+    refs = []
+    for c in cases:
+        m = OM.build_mesh(c.grid, c.bodies, c.sweeps, c.bc)
+        s = OSY.assemble(m, 1.0)
+        p = W.random_vector(m.n_nodes, seed=5)
+        p[m.kind.ravel() == OM.INACTIVE] = 0.0
+        kind = m.kind.ravel()
+        ref = np.where((kind == OM.FREE) | (kind == OM.BODY), OSY.full_operator_apply(s, p), 0.0)
+        refs.append((p, ref))
+    p_all = np.concatenate([p for p, _ in refs])
+    with api.batch_build(cases) as g:
+        for prec in (api.PF_MIXED, api.PF_FP64, api.PF_MIXED):
+            g.apply_timing(prec, reps=7)
+        out = {}
+        for prec in (api.PF_FP64, api.PF_MIXED):
+            y1, _ = api.apply(g, torch.from_numpy(p_all), prec)
+            y2, _ = api.apply(g, torch.from_numpy(p_all), prec)
+            assert torch.equal(y1, y2)
+            out[prec] = y1.cpu().numpy()
+    off = 0
+    for p, ref in refs:
+        scale = np.abs(ref).max()
+        y64 = out[api.PF_FP64][off:off + p.size]
+        y32 = out[api.PF_MIXED][off:off + p.size]
+        assert np.abs(y64 - ref).max() <= 1e-12 * scale
+        assert rel_l2(y32, ref) <= 2e-6
+        off += p.size
+
+
 def test_invalid_inputs_rejected(api):
     from paper_2512_12232_gb300._lib import PfError
     with pytest.raises(PfError, match="EINVAL"):
