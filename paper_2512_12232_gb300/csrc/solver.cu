@@ -756,7 +756,7 @@ __global__ void __launch_bounds__(NTC, sizeof(T) == 4 ? 2 : 1) k_cg(CGArgs<T> a,
       if (a.sc.cta_ns && sg + 1 == a.sc.cta_seg[blockIdx.x + 1]) {
         unsigned long long t_end;
         asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_end));
-        a.sc.cta_ns[blockIdx.x] = t_end - s_t0;
+        a.sc.cta_ns[blockIdx.x] += t_end - s_t0;   // summed over the launches of a timed round
       }
       // release this CTA's stores (ordered before by the barrier), acquire the others'
       const int done = atom_add_acq_rel_gpu(&a.sc.counter[v], 1);
@@ -1377,9 +1377,16 @@ static void cg_sched_write(Batch& b, CgConfig& c) {
 }
 
 // Re-balance rounds of the first tuned solve on a handle and launches timed per round
-// (the last launch of a round is the one measured).
-constexpr int CG_TUNE_ROUNDS = 2;
+// (each CTA's tile-phase time is summed over the launches of a round); PFQ4_CG_TUNE_ROUNDS
+// and PFQ4_CG_TUNE_LAUNCHES override them.
+constexpr int CG_TUNE_ROUNDS = 4;
 constexpr int CG_TUNE_LAUNCHES = 2;
+static int env_int(const char* name, int dflt, int lo, int hi) {
+  const char* e = getenv(name);
+  if (!e) return dflt;
+  const int v = atoi(e);
+  return (v >= lo && v <= hi) ? v : dflt;
+}
 
 // Persistent grid (occupancy x SMs) and tile schedule of one CG configuration.  The
 // first estimate of a tile's cost is a fit of measured per-CTA times of the
@@ -1915,9 +1922,11 @@ pf_status solve_core(Batch& b, double U, const pf_solve_opts& o, double* dev_psi
     cg_sched_write(b, cc);
   }
   if (b.cg_tune && o.k_max > 0 && (long long)cc.tile_cost.size() >= 2LL * cc.G) {
-    for (; cc.tune_rounds < CG_TUNE_ROUNDS; ++cc.tune_rounds) {
+    const int rounds = env_int("PFQ4_CG_TUNE_ROUNDS", CG_TUNE_ROUNDS, 0, 16);
+    const int per_round = env_int("PFQ4_CG_TUNE_LAUNCHES", CG_TUNE_LAUNCHES, 1, 16);
+    for (; cc.tune_rounds < rounds; ++cc.tune_rounds) {
       PF_CUDA(cudaMemsetAsync(cc.d_cta_ns, 0, cc.G * sizeof(unsigned long long), s));
-      timed_launches(CG_TUNE_LAUNCHES, true);
+      timed_launches(per_round, true);
       std::vector<unsigned long long> tns(cc.G);
       PF_CUDA(cudaMemcpy(tns.data(), cc.d_cta_ns, cc.G * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
       cg_rebalance(b, cc, tns);
