@@ -275,7 +275,9 @@ def run_ours(args, rank, world, local):
     prec = api.PF_MIXED if args.precision == "mixed" else api.PF_FP64
 
     def step(host_out=None):
-        g = api.batch_build(cs)
+        t_mesh = time.perf_counter()
+        g = api.batch_build(cs)                  # returns after the device mesh is complete
+        t_mesh = time.perf_counter() - t_mesh
         res = api.psi_solve(g, U=1.0, tol=args.tol, precision=prec, inner_tol=args.inner_tol,
                             tune_schedule=args.tune)
         if args.config == "c5":
@@ -285,6 +287,7 @@ def run_ours(args, rank, world, local):
         if host_out is not None:
             host_out.copy_(res.psi, non_blocking=True)
         tm = g.timing()
+        tm["mesh_build_ms"] = 1e3 * t_mesh
         st = [g.stats(v) for v in range(len(cs))]
         g.close()
         return res, cps, tm, st
@@ -317,6 +320,13 @@ def run_ours(args, rank, world, local):
     cg_bytes = sum(tm["cg_bytes_per_launch"] * tm["cg_launches"] for _, _, tm, _ in records)
     launches = sum(tm["kernel_launches"] for _, _, tm, _ in records)
     nodes = sum(st[v]["n_nodes"] for v in range(len(cs)) for st in [records[0][3]])
+    # per-step averages: mesh build (host wall time, ends in a device synchronisation), the
+    # whole solve (device events, tuning launches included), its fused-CG and refinement
+    # kernels, and the rest of the step (outputs, gradient, copies, teardown)
+    n_rec = max(1, len(records))
+    breakdown = {k: sum(tm[src] for _, _, tm, _ in records) / n_rec
+                 for k, src in (("mesh_build", "mesh_build_ms"), ("solve", "solve_ms"), ("cg_kernels", "cg_kernel_ms"),
+                                ("refinement_kernels", "residual_kernel_ms"))}
 
     # e2e: the public API with host buffers (geometry in, psi field and body values out)
     e2e = None
@@ -397,6 +407,7 @@ def run_ours(args, rank, world, local):
         "iters_per_variant": iters if len(iters) <= 8 else {"min": min(iters), "max": max(iters)},
         "copfi": [cp for cp, _ in records[-1][1]],
         "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": int(launches),
+        "breakdown_ms": {**breakdown, "rest": 1e3 * vals[1] / args.steps - breakdown["mesh_build"] - breakdown["solve"]},
         **({"apply_sweep": apply_sweep} if apply_sweep else {}),
         "e2e": ({"value": e2e[0] / e2e[1], "unit": UNIT, "h2d_bytes_per_step": e2e[2],
                  "d2h_bytes_per_step": e2e[3]} if e2e else None),

@@ -97,15 +97,14 @@ struct Batch {
   long long Rtot = 0;                // rows of the batch's 2-D node arrays (Vtot / P)
   int P = 0;                         // common row pitch
 
-  // tiles and persistent schedule
+  // 32x8 tiles (mesh build, refinement kernels)
   long long T = 0;
   int2* tile_ij = nullptr;           // [T]
   int* tile_var = nullptr;           // [T]
-  int G = 0, S = 0;
-  int *cta_seg = nullptr, *seg_var = nullptr, *seg_t0 = nullptr, *seg_t1 = nullptr;
-  int *var_seg0 = nullptr, *var_seg1 = nullptr, *counter = nullptr;
-  double* partial = nullptr;
-  Sched sched{};
+  // refinement kernels (k_fold, k_resid): a (rgx, variants) grid
+  int rgx = 0;                       // CTAs per variant
+  double* rpart = nullptr;           // [variants][rgx] partial sums
+  int* rcounter = nullptr;           // [variants] arrivals per launch
 
   // solver state
   VarState* state = nullptr;         // [nv]

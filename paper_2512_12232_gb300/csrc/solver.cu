@@ -53,10 +53,17 @@ struct CGArgs {
   int test_drop;            // test hook: CTA 0 never issues the copies of its first tile
 };
 
+// The refinement kernels (k_fold, k_resid) run on a (gx, variants) grid: row v handles
+// variant v, its 32x8 tiles cut into gx contiguous shares, one per CTA.  A variant that
+// refines is spread over gx CTAs however many variants the batch holds (a contiguous
+// schedule over the whole tile list left a refining variant of a large batch on a few
+// SMs), and the rows of variants that do not refine exit after one load.
 template <typename T>
 struct ResidArgs {
   MeshDev m;
-  Sched sc;
+  int gx;                   // CTAs per variant
+  double* rpart;            // [variants][gx] partial sums of r.r, fixed order
+  int* counter;             // [variants] CTAs of the row done in this launch
   VarState* st;
   const SolveParams* prm;
   double* x64;              // solution, Dirichlet values in place (read only here)
@@ -88,15 +95,6 @@ template <typename T>
 __device__ __forceinline__ T next_x(T x, T p, T alpha) { return x + alpha * p; }
 
 __device__ __forceinline__ int seg_count(const Sched& sc, int v) { return sc.var_seg1[v] - sc.var_seg0[v]; }
-
-// Sum of the per-segment partials of variant v (fixed order); all threads get sums.
-__device__ void reduce_partials(const Sched& sc, int v, int nk, double* out, double* scratch) {
-  double s[4] = {0, 0, 0, 0};
-  const int tid = linear_tid();
-  for (int sg = sc.var_seg0[v] + tid; sg < sc.var_seg1[v]; sg += NT)
-    for (int k = 0; k < nk; ++k) s[k] += __ldcg(&sc.partial[sg * 4 + k]);
-  for (int k = 0; k < nk; ++k) out[k] = block_sum(s[k], scratch);
-}
 
 // Sum of a node vector over the nodes of one body (fixed order), all threads get it.
 template <typename T>
@@ -774,7 +772,11 @@ __device__ void finalize_resid(const ResidArgs<T>& a, int v, double* scratch, do
   const DevVariant& V = a.m.var[v];
   VarState* S = &a.st[v];
   double d[1];
-  reduce_partials(a.sc, v, 1, d, scratch);
+  {
+    double s = 0.0;
+    for (int k = linear_tid(); k < a.gx; k += NT) s += __ldcg(&a.rpart[(long long)v * a.gx + k]);
+    d[0] = block_sum(s, scratch);
+  }
   for (int k = 0; k < V.nb; ++k) {
     const double s = body_gather<double>(a.m, V.body0 + k, a.w64, scratch);
     if (linear_tid() == 0) sh_rb[k] = (a.rhsb ? a.rhsb[V.body0 + k] : 0.0) - s;
@@ -822,8 +824,15 @@ __device__ void finalize_resid(const ResidArgs<T>& a, int v, double* scratch, do
       S->thr_rel = a.mixed ? a.prm->inner_rel2 : 0.0;
       S->thr_abs2 = (a.mixed ? 0.25 : 0.5) * tol2 * S->bnorm2;
     }
-    a.sc.counter[v] = 0;
+    a.counter[v] = 0;
   }
+}
+
+// Tiles [t0, t1) of variant v's 32x8 tile grid taken by CTA column bx of gx.
+__device__ __forceinline__ void resid_share(const DevVariant& V, int gx, int bx, long long& t0, long long& t1) {
+  const long long nt = (long long)V.tiles_x * V.tiles_y;
+  t0 = nt * bx / gx;
+  t1 = nt * (bx + 1) / gx;
 }
 
 template <typename T>
@@ -837,101 +846,100 @@ __global__ void __launch_bounds__(NT) k_resid(ResidArgs<T> a) {
   __shared__ int s_last;
   const int tid = linear_tid(), lane = tid & 31, warp = tid >> 5;
   const long long plane = a.m.Vtot;
-  for (int sg = a.sc.cta_seg[blockIdx.x]; sg < a.sc.cta_seg[blockIdx.x + 1]; ++sg) {
-    const int v = a.sc.seg_var[sg];
-    if (a.st[v].phase != PH_RESID) continue;
-    const DevVariant& V = a.m.var[v];
-    if (tid < V.nb) {
-      const int gb = V.body0 + tid;
-      s_xb[tid] = a.sol[gb] + (double)a.sb[gb];
-    }
-    const int cur = a.st[v].buf;
-    State4<T>* __restrict__ s_out = a.s[cur];
-    __syncthreads();
-    double acc = 0.0;
-    for (int t = a.sc.seg_t0[sg]; t < a.sc.seg_t1[sg]; ++t) {
-      const int2 ij = a.sc.tile_ij[t];
-      const int i = ij.x + threadIdx.x, j = ij.y + threadIdx.y;
-      const bool in = (i <= V.nx) && (j <= V.ny);
-      const long long n = V.base + (long long)j * V.P + i;
-      const uint8_t tg = in ? a.m.tag[n] : K_INACT;
-      const int kind = tg & KIND_MASK;
-      double u = 0.0;
-      if (kind == K_FREE || kind == K_DIR) u = a.x64[n];
-      else if (kind == K_BODY) u = s_xb[a.m.bid[n]];
-      ps[threadIdx.y + 1][threadIdx.x + 1] = u;
-      ts[threadIdx.y + 1][threadIdx.x + 1] = tg;
-      if (tid < NHALO) {
-        int li, lj;
-        halo_pos(tid, li, lj);
-        const int hi = ij.x - 1 + li, hj = ij.y - 1 + lj;
-        uint8_t ht = K_INACT;
-        double hu = 0.0;
-        if (hi >= 0 && hj >= 0 && hi <= V.nx && hj <= V.ny) {
-          const long long hn = V.base + (long long)hj * V.P + hi;
-          ht = a.m.tag[hn];
-          const int hk = ht & KIND_MASK;
-          if (hk == K_FREE || hk == K_DIR) hu = a.x64[hn];
-          else if (hk == K_BODY) hu = s_xb[a.m.bid[hn]];
-        }
-        ps[lj][li] = hu;
-        ts[lj][li] = ht;
+  const int v = blockIdx.y, bx = blockIdx.x;
+  if (a.st[v].phase != PH_RESID) return;          // the whole row leaves: nothing to refine
+  const DevVariant& V = a.m.var[v];
+  if (tid < V.nb) {
+    const int gb = V.body0 + tid;
+    s_xb[tid] = a.sol[gb] + (double)a.sb[gb];
+  }
+  const int cur = a.st[v].buf;
+  State4<T>* __restrict__ s_out = a.s[cur];
+  __syncthreads();
+  double acc = 0.0;
+  long long t0, t1;
+  resid_share(V, a.gx, bx, t0, t1);
+  for (long long t = t0; t < t1; ++t) {
+    const int2 ij = make_int2((int)(t % V.tiles_x) * TX, (int)(t / V.tiles_x) * TY);
+    const int i = ij.x + threadIdx.x, j = ij.y + threadIdx.y;
+    const bool in = (i <= V.nx) && (j <= V.ny);
+    const long long n = V.base + (long long)j * V.P + i;
+    const uint8_t tg = in ? a.m.tag[n] : K_INACT;
+    const int kind = tg & KIND_MASK;
+    double u = 0.0;
+    if (kind == K_FREE || kind == K_DIR) u = a.x64[n];
+    else if (kind == K_BODY) u = s_xb[a.m.bid[n]];
+    ps[threadIdx.y + 1][threadIdx.x + 1] = u;
+    ts[threadIdx.y + 1][threadIdx.x + 1] = tg;
+    if (tid < NHALO) {
+      int li, lj;
+      halo_pos(tid, li, lj);
+      const int hi = ij.x - 1 + li, hj = ij.y - 1 + lj;
+      uint8_t ht = K_INACT;
+      double hu = 0.0;
+      if (hi >= 0 && hj >= 0 && hi <= V.nx && hj <= V.ny) {
+        const long long hn = V.base + (long long)hj * V.P + hi;
+        ht = a.m.tag[hn];
+        const int hk = ht & KIND_MASK;
+        if (hk == K_FREE || hk == K_DIR) hu = a.x64[hn];
+        else if (hk == K_BODY) hu = s_xb[a.m.bid[hn]];
       }
-      __syncthreads();
-      if (kind == K_FREE || kind == K_BODY) {
-        const double y = q4_row<double>(ps, ts, threadIdx.x + 1, threadIdx.y + 1, n, V.P, a.m.K64, plane, V.kr64);
-        if (kind == K_FREE) {
-          const double r = -y;
-          State4<T> o;
-          o.x = T(0);
-          o.r = (T)r;
-          o.p = T(0);
-          o.q = T(0);
-          s_out[n] = o;
-          acc = fma(r, r, acc);
-        } else {
-          a.w64[n] = y;
-        }
+      ps[lj][li] = hu;
+      ts[lj][li] = ht;
+    }
+    __syncthreads();
+    if (kind == K_FREE || kind == K_BODY) {
+      const double y = q4_row<double>(ps, ts, threadIdx.x + 1, threadIdx.y + 1, n, V.P, a.m.K64, plane, V.kr64);
+      if (kind == K_FREE) {
+        const double r = -y;
+        State4<T> o;
+        o.x = T(0);
+        o.r = (T)r;
+        o.p = T(0);
+        o.q = T(0);
+        s_out[n] = o;
+        acc = fma(r, r, acc);
+      } else {
+        a.w64[n] = y;
       }
-      __syncthreads();
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) red[warp] = acc;
-    __syncthreads();
-    if (tid == 0) {
-      double s = 0.0;
-      for (int w = 0; w < NT / 32; ++w) s += red[w];
-      a.sc.partial[sg * 4] = s;
-      const int done = atom_add_acq_rel_gpu(&a.sc.counter[v], 1);
-      s_last = (done == seg_count(a.sc, v) - 1);
-    }
-    __syncthreads();
-    if (s_last) finalize_resid<T>(a, v, scratch, sh_rb);
     __syncthreads();
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) red[warp] = acc;
+  __syncthreads();
+  if (tid == 0) {
+    double s = 0.0;
+    for (int w = 0; w < NT / 32; ++w) s += red[w];
+    a.rpart[(long long)v * a.gx + bx] = s;
+    // release this CTA's stores (ordered before by the barrier), acquire the others'
+    const int done = atom_add_acq_rel_gpu(&a.counter[v], 1);
+    s_last = (done == a.gx - 1);
+  }
+  __syncthreads();
+  if (s_last) finalize_resid<T>(a, v, scratch, sh_rb);
 }
 
 // Fold the CG correction into the FP64 solution before the true residual (pointwise,
-// its own launch so no tile ever sees a half-updated neighbour).  Persistent over the
-// residual kernel's schedule, so a launch with no variant to refine costs next to nothing.
+// its own launch so no tile ever sees a half-updated neighbour).  Same (gx, variants)
+// grid as k_resid: a launch with no variant to refine costs one load per CTA.
 template <typename T>
-__global__ void __launch_bounds__(NT) k_fold(const DevVariant* var, Sched sc, const uint8_t* tag,
-                                             const VarState* st, double* x64, State4<T>* const* sbuf) {
-  for (int sg = sc.cta_seg[blockIdx.x]; sg < sc.cta_seg[blockIdx.x + 1]; ++sg) {
-    const int v = sc.seg_var[sg];
-    if (st[v].phase != PH_RESID) continue;
-    const DevVariant& V = var[v];
-    State4<T>* s = sbuf[st[v].buf];
-    for (int t = sc.seg_t0[sg]; t < sc.seg_t1[sg]; ++t) {
-      const int2 ij = sc.tile_ij[t];
-      const int i = ij.x + threadIdx.x, j = ij.y + threadIdx.y;
-      if (i > V.nx || j > V.ny) continue;
-      const long long n = V.base + (long long)j * V.P + i;
-      if ((tag[n] & KIND_MASK) != K_FREE) continue;
-      x64[n] = x64[n] + (double)s[n].x;
-      s[n].x = T(0);
-    }
+__global__ void __launch_bounds__(NT) k_fold(const DevVariant* var, int gx, const uint8_t* tag, const VarState* st,
+                                             double* x64, State4<T>* const* sbuf) {
+  const int v = blockIdx.y;
+  if (st[v].phase != PH_RESID) return;
+  const DevVariant& V = var[v];
+  State4<T>* s = sbuf[st[v].buf];
+  long long t0, t1;
+  resid_share(V, gx, blockIdx.x, t0, t1);
+  for (long long t = t0; t < t1; ++t) {
+    const int i = (int)(t % V.tiles_x) * TX + threadIdx.x, j = (int)(t / V.tiles_x) * TY + threadIdx.y;
+    if (i > V.nx || j > V.ny) continue;
+    const long long n = V.base + (long long)j * V.P + i;
+    if ((tag[n] & KIND_MASK) != K_FREE) continue;
+    x64[n] = x64[n] + (double)s[n].x;
+    s[n].x = T(0);
   }
 }
 
@@ -1222,81 +1230,19 @@ static MeshDev mesh_dev(const Batch& b) {
 // Persistent schedule over a tile list: CTA c owns a contiguous range of tiles, cut into
 // segments at variant boundaries.  With per-tile costs the ranges hold equal cost
 // (tiles with stored coefficients move and compute more), else equal tile counts.
-static Sched build_sched(Batch& b, const std::vector<int>& tv, int G, const std::vector<double>* cost = nullptr) {
-  const long long T = (long long)tv.size();
-  std::vector<long long> cut(G + 1, 0);
-  if (cost) {
-    double total = 0.0;
-    for (double c : *cost) total += c;
-    long long t = 0;
-    double run = 0.0;
-    for (int c = 0; c <= G; ++c) {
-      const double target = total * c / G;
-      while (t < T && run + 0.5 * (*cost)[t] < target) run += (*cost)[t++];
-      cut[c] = (c == G) ? T : t;
-    }
-  } else {
-    for (int c = 0; c <= G; ++c) cut[c] = (long long)c * T / G;
-  }
-  std::vector<int> cta_seg(G + 1), seg_var, seg_t0, seg_t1;
-  for (long long c = 0; c < G; ++c) {
-    const long long t0 = cut[c], t1 = cut[c + 1];
-    cta_seg[c] = (int)seg_var.size();
-    long long s0 = t0;
-    for (long long t = t0; t < t1; ++t) {
-      if (t + 1 == t1 || tv[t + 1] != tv[t]) {
-        seg_var.push_back(tv[t]);
-        seg_t0.push_back((int)s0);
-        seg_t1.push_back((int)(t + 1));
-        s0 = t + 1;
-      }
-    }
-  }
-  cta_seg[G] = (int)seg_var.size();
-  const int S = (int)seg_var.size();
-  std::vector<int> vs0(b.nv, 0), vs1(b.nv, 0);
-  std::vector<int> seen(b.nv, 0);
-  for (int sgi = 0; sgi < S; ++sgi) {
-    const int v = seg_var[sgi];
-    if (!seen[v]) { vs0[v] = sgi; seen[v] = 1; }
-    vs1[v] = sgi + 1;
-  }
-  auto up = [&](const std::vector<int>& h) {
-    int* d = (int*)dev_alloc(b, std::max<size_t>(1, h.size()) * sizeof(int));
-    PF_CUDA(cudaMemcpyAsync(d, h.data(), h.size() * sizeof(int), cudaMemcpyHostToDevice, b.stream));
-    return d;
-  };
-  Sched sc{};
-  sc.cta_seg = up(cta_seg);
-  sc.seg_var = up(seg_var);
-  sc.seg_t0 = up(seg_t0);
-  sc.seg_t1 = up(seg_t1);
-  sc.var_seg0 = up(vs0);
-  sc.var_seg1 = up(vs1);
-  int* counter = (int*)dev_alloc(b, b.nv * sizeof(int));
-  PF_CUDA(cudaMemsetAsync(counter, 0, b.nv * sizeof(int), b.stream));
-  sc.counter = counter;
-  sc.partial = (double*)dev_alloc(b, (size_t)std::max(1, S) * 4 * sizeof(double));
-  sc.n_cta = G;
-  PF_CUDA(cudaStreamSynchronize(b.stream));
-  return sc;
-}
-
 void make_schedule(Batch& b) {
   int dev = 0, nsm = 0;
   PF_CUDA(cudaGetDevice(&dev));
   PF_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  // residual kernel: 32 x 8 tiles
+  // refinement kernels: every variant gets the resident grid's share of CTAs, at least 64
   int oR32 = 0, oR64 = 0;
   PF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&oR32, k_resid<float>, NT, 0));
   PF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&oR64, k_resid<double>, NT, 0));
-  std::vector<int> tv(b.T);
-  for (int v = 0; v < b.nv; ++v)
-    for (long long t = b.hv[v].tile0; t < b.hv[v].tile0 + (long long)b.hv[v].tiles_x * b.hv[v].tiles_y; ++t) tv[t] = v;
-  b.G = (int)std::min<long long>((long long)nsm * std::max(1, std::min(oR32, oR64)), b.T);
-  b.sched = build_sched(b, tv, b.G);
-  b.sched.tile_ij = b.tile_ij;
-  b.S = 0;
+  const int resident = nsm * std::max(1, std::min(oR32, oR64));
+  b.rgx = std::max(64, resident / std::max(1, b.nv));
+  b.rpart = (double*)dev_alloc(b, (size_t)b.nv * b.rgx * sizeof(double));
+  b.rcounter = (int*)dev_alloc(b, (size_t)b.nv * sizeof(int));
+  PF_CUDA(cudaMemsetAsync(b.rcounter, 0, (size_t)b.nv * sizeof(int), b.stream));
   b.nsm = nsm;
 }
 
@@ -1721,7 +1667,9 @@ static void fill_cg_args(Batch& b, CGArgs<T>& a, State4<T>* const st[2], T* sb, 
 template <typename T>
 static void fill_resid_args(Batch& b, ResidArgs<T>& a, State4<T>* const st[2], T* sb, int mixed) {
   a.m = mesh_dev(b);
-  a.sc = b.sched;
+  a.gx = b.rgx;
+  a.rpart = b.rpart;
+  a.counter = b.rcounter;
   a.st = b.state;
   a.prm = b.params;
   a.x64 = b.x64;
@@ -1767,16 +1715,17 @@ static void launch_cg_chunk(Batch& b, int precision, int chunk, cudaStream_t s, 
 
 static void launch_resid_only(Batch& b, int precision, cudaStream_t s) {
   const dim3 blk(TX, TY);
+  const dim3 rg(b.rgx, b.nv);
   if (precision == PF_FP64) {
-    k_fold<double><<<b.G, blk, 0, s>>>(b.d_var, b.sched, b.tag, b.state, b.x64, (State4<double>* const*)b.d_sbuf);
+    k_fold<double><<<rg, blk, 0, s>>>(b.d_var, b.rgx, b.tag, b.state, b.x64, (State4<double>* const*)b.d_sbuf);
     ResidArgs<double> ra;
     fill_resid_args<double>(b, ra, b.st64, b.sb64, 0);
-    k_resid<double><<<b.G, blk, 0, s>>>(ra);
+    k_resid<double><<<rg, blk, 0, s>>>(ra);
   } else {
-    k_fold<float><<<b.G, blk, 0, s>>>(b.d_var, b.sched, b.tag, b.state, b.x64, (State4<float>* const*)(b.d_sbuf + 2));
+    k_fold<float><<<rg, blk, 0, s>>>(b.d_var, b.rgx, b.tag, b.state, b.x64, (State4<float>* const*)(b.d_sbuf + 2));
     ResidArgs<float> ra;
     fill_resid_args<float>(b, ra, b.st32, b.sb32, 1);
-    k_resid<float><<<b.G, blk, 0, s>>>(ra);
+    k_resid<float><<<rg, blk, 0, s>>>(ra);
   }
   PF_CUDA(cudaGetLastError());
 }
