@@ -160,12 +160,16 @@ __global__ void __launch_bounds__(NT) k_jacobi(const DevVariant* var, const int*
   double2* a = w0;
   double2* b = w1;
   for (int sw = 0; sw < nsw; ++sw) {
-    for (int q = tid; q < JRW * JRH; q += NT) {
-      const int ri = q % JRW, rj = q / JRW;
+    // after sweep sw only nodes at distance >= sw + 1 from the window edge are read again
+    // (by later sweeps, or as the tile), so the sweep covers that rectangle alone; the
+    // values outside it go stale, as the edge does, and are never used
+    const int rw = JRW - 2 * (sw + 1), rh = JRH - 2 * (sw + 1);
+    for (int k = tid; k < rw * rh; k += NT) {
+      const int ri = sw + 1 + k % rw, rj = sw + 1 + k / rw;
+      const int q = rj * JRW + ri;
       double2 out = a[q];
-      // an updatable node is off the ring, so its four neighbours lie in the grid; at
-      // the window edge the value is stale but lies farther than nsw from the tile
-      if (upd[q] && ri > 0 && ri < JRW - 1 && rj > 0 && rj < JRH - 1) {
+      // an updatable node is off the ring, so its four neighbours lie in the grid
+      if (upd[q]) {
         const double2 w = a[q - 1], e = a[q + 1], s = a[q - JRW], nn = a[q + JRW];
         const double sx = __dadd_rn(__dadd_rn(__dadd_rn(w.x, e.x), s.x), nn.x);
         const double sy = __dadd_rn(__dadd_rn(__dadd_rn(w.y, e.y), s.y), nn.y);
