@@ -103,10 +103,37 @@ def peaks():
         return {}
 
 
+def _code_only(src: str) -> str:
+    """C/C++ source without comments and blank lines (string and character literals kept),
+    so that an edit of a comment does not count as a change of the kernel."""
+    out, i, n = [], 0, len(src)
+    while i < n:
+        c = src[i]
+        if c in "\"'":                           # literal: copy through its closing quote
+            j = i + 1
+            while j < n and src[j] != c:
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        elif src.startswith("//", i):
+            j = src.find("\n", i)
+            i = n if j < 0 else j
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+        else:
+            out.append(c)
+            i += 1
+    return "\n".join(line.rstrip() for line in "".join(out).splitlines() if line.strip())
+
+
 def kernel_source_hash():
+    """First 16 hex digits of the SHA-256 of the code (comments removed) of common.cuh
+    followed by solver.cu: the sources of the fused CG kernel."""
     h = hashlib.sha256()
     for f in ("common.cuh", "solver.cu"):
-        h.update(open(os.path.join(ROOT, "paper_2512_12232_gb300", "csrc", f), "rb").read())
+        with open(os.path.join(ROOT, "paper_2512_12232_gb300", "csrc", f)) as fh:
+            h.update(_code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -6,11 +6,14 @@
 // corner 0 (i, j).  Columns nx+1 .. P-1 are padding (tag INACTIVE, values 0) and are
 // never read as neighbours: tile loaders bounds-check against (nx, ny).
 //
-// One tile = 32 x 8 nodes = one 256-thread CTA pass.  Tiles of all variants form one
-// list (variant-major, row-major inside a variant).  Solver kernels run a persistent
-// grid: CTA b owns a contiguous range of the tile list, cut into "segments" at
-// variant boundaries; per-segment partial reductions are summed in a fixed order by
-// the last CTA to finish a variant, so every reduction is deterministic.
+// Two tilings of every variant (variant-major lists, row-major inside a variant):
+// 32 x 8 nodes (mesh build and the FP64 refinement kernels, one 256-thread CTA pass
+// per tile) and 64 x 16 nodes (the fused CG step and the stand-alone operator).  The
+// fused CG step runs a persistent grid: CTA b owns a contiguous range of the 64 x 16
+// list, cut into "segments" at variant boundaries.  The refinement kernels run one
+// grid row per variant, each CTA a fixed share of the variant's tiles.  Either way
+// partial sums are written to fixed slots and summed in a fixed order by the last CTA
+// to finish a variant, so every reduction is deterministic.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
