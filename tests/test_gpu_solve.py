@@ -77,6 +77,29 @@ def test_mixed_batch_reaches_tolerance_and_matches(api):
         assert rel_l2(psi_b[offs[v]:offs[v + 1]], psi_ref) <= 1e-4
 
 
+def test_many_variant_batch(api):
+    """44 variants: every refinement kernel row has 64 CTAs; the four single-cylinder
+    variants have 45 tiles each, so some CTAs of their rows get an empty share.  Variants
+    refine and finish at different times."""
+    cyl = [W.Case(-10.0, 10.0, -5.0, 5.0, 128, 64, np.array([[0.0, 0.0, 0.5]]), 20) for _ in range(4)]
+    cases = cyl[:2] + W.parametric_sweep(40, seed=7, nx_choices=(256, 288), sweeps=20) + cyl[2:]
+    with api.batch_build(cases) as g:
+        mixed = api.psi_solve(g, U=1.0, tol=1e-8, precision=api.PF_MIXED)
+        assert all(i["status"] == 0 and i["rel_true_residual"] <= 1e-8 for i in mixed.info)
+        res = api.psi_solve(g, U=1.0, tol=1e-13, precision=api.PF_FP64)
+        psi_b = res.psi.cpu().numpy()
+        offs, boffs = g.node_offsets, g.body_offsets
+    assert len({i["iters"] for i in res.info}) > 1          # variants converge at different counts
+    for v, c in enumerate(cases):
+        with api.mesh_build(c.grid, c.bodies, c.sweeps, c.bc) as g1:
+            r1 = api.psi_solve(g1, U=1.0, tol=1e-13, precision=api.PF_FP64)
+        assert rel_l2(psi_b[offs[v]:offs[v + 1]], r1.psi.cpu().numpy()) <= 1e-11, v
+    for v in (0, 17, 43):
+        m, s, u, psi_ref = oracle_solution(cases[v], 1.0)
+        assert rel_l2(psi_b[offs[v]:offs[v + 1]], psi_ref) <= FP64_TOL
+        np.testing.assert_allclose(res.body_psi[boffs[v]:boffs[v + 1]], u[s.n_free:], rtol=0, atol=BODY_TOL)
+
+
 def test_solve_is_deterministic(api):
     c = W.five_cylinder_case(0.5, 160, 80, 20)
     outs = []
