@@ -155,12 +155,27 @@ __global__ void k_shape_nodes(const DevVariant* var, const int* tile_var, const 
 }
 
 // One transposed Jacobi sweep: out_m = [m fixed] in_m + sum over updated neighbours n of in_n / 4.
+// Only the body nodes' values are read after the last sweep, and a sweep moves a value
+// one node, so after this sweep only nodes within `reach` (the sweeps still to come) of a
+// body node matter.  A tile farther than that from every body's node box (Chebyshev
+// distance, a lower bound of the number of hops) is skipped: its stale values are only
+// ever read by nodes that are themselves too far to matter.
 __global__ void k_jacobi_T(const DevVariant* var, const int* tile_var, const int2* tile_ij, const uint8_t* tag,
-                           const int* bid, long long Vtot, const double* in, double* out) {
+                           const int* bid, const int4* bbox, int reach, long long Vtot, const double* in,
+                           double* out) {
   const long long t = blockIdx.x;
   const int v = tile_var[t];
   const DevVariant& V = var[v];
   const int2 ij = tile_ij[t];
+  {
+    bool near = false;
+    for (int k = 0; k < V.nb && !near; ++k) {
+      const int4 bx = bbox[V.body0 + k];
+      near = ij.x <= bx.y + reach && ij.x + TX - 1 >= bx.x - reach && ij.y <= bx.w + reach &&
+             ij.y + TY - 1 >= bx.z - reach;
+    }
+    if (!near) return;
+  }
   const int i = ij.x + threadIdx.x, j = ij.y + threadIdx.y;
   if (i > V.nx || j > V.ny) return;
   const long long n = V.base + (long long)j * V.P + i;
@@ -300,7 +315,8 @@ pf_status shape_gradient(Batch& b, int obj, int lo, int hi, double U, double tol
     double* c = b.gradT;
     PF_CUDA(cudaMemsetAsync(c, 0, 2 * Vt * sizeof(double), s));
     for (int k = 0; k < b.sweeps; ++k) {
-      k_jacobi_T<<<(unsigned)b.T, blk, 0, s>>>(b.d_var, b.tile_var, b.tile_ij, b.tag, b.bid, Vt, a, c);
+      k_jacobi_T<<<(unsigned)b.T, blk, 0, s>>>(b.d_var, b.tile_var, b.tile_ij, b.tag, b.bid, b.d_bbox,
+                                               b.sweeps - 1 - k, Vt, a, c);
       std::swap(a, c);
     }
     PF_CUDA(cudaGetLastError());
