@@ -6,7 +6,7 @@ onto it, each receiving the displacement d = x_boundary - x_grid; the displaceme
 is propagated into the domain by a Laplace problem for d with d = d_i on the
 bodies and d = 0 on the grid-aligned outer boundary; finally x_new = x_old + d.
 
-Readings taken where the paper is silent (each is listed in the design doc):
+Readings taken where the paper is silent:
   * "immediately inside" = an inside node that is a corner of at least one active
     cell, where a cell is active iff at least one corner lies outside every body;
     a node is inside body k iff (x-cx)^2 + (y-cy)^2 <= r^2 (ties count as inside);

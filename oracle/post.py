@@ -3,7 +3,7 @@
 Section "Velocity Field and Surface Tangential Velocity": u_t ~ (psi_c - psi_b) / d_nc
 with psi_b the body's stream-function value, psi_c the average psi of the adjacent
 fluid element and d_nc the perpendicular distance from the element centroid to the
-boundary edge.  Readings (listed in the design doc): a boundary edge is an edge of an
+boundary edge.  Readings where the paper is silent: a boundary edge is an edge of an
 active cell whose two end nodes are BODY nodes of the same body at distinct
 positions; the centroid is the mean of the four corners; u_t keeps its sign;
 theta is the polar angle of the edge midpoint about the body centre in degrees,
