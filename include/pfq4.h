@@ -236,6 +236,14 @@ pf_status pf_last_timing(const pf_batch* b, pf_timing* out);
    destroy it.  enable = 0 restores normal launches.  PF_EINVAL for a NULL handle. */
 pf_status pf_test_wait_timeout(pf_batch* b, int enable);
 
+/* Element velocity field of variant v after a solve (section "Velocity Field and Surface
+   Tangential Velocity", u = dpsi/dy, v = -dpsi/dx; the velocity-magnitude field of the
+   results): the gradient of the bilinear interpolant of the solved psi at the centre of
+   every cell, through the isoparametric map.  dev_u and dev_v are caller-owned device
+   arrays of nx*ny doubles, cell (i, j) at j*nx + i; inactive cells get 0.  PF_EINVAL for a
+   NULL handle or output, a variant out of range, or a handle with no solve yet. */
+pf_status pf_velocity_field(pf_batch* b, int variant, double* dev_u, double* dev_v, void* stream);
+
 /* Surface tangential velocity on body `body` of variant v after a solve
    (section "Velocity Field and Surface Tangential Velocity"): for every boundary edge
    (edge of an active cell whose end nodes are distinct BODY nodes of this body),

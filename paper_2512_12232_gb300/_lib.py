@@ -71,6 +71,7 @@ _SIGS = {
     "pf_apply_timing": (C.c_int, [P, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), P]),
     "pf_last_timing": (C.c_int, [P, C.POINTER(pf_timing)]),
     "pf_surface_velocity": (C.c_int, [P, C.c_int, C.c_int, P, P, C.c_int, C.POINTER(C.c_int), P]),
+    "pf_velocity_field": (C.c_int, [P, C.c_int, P, P, P]),
     "pf_copfi": (C.c_int, [P, C.c_int, C.c_int, C.c_int, C.c_double, C.POINTER(C.c_double),
                            C.POINTER(C.c_double)]),
     "pf_grad": (C.c_int, [P, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, P, P, P, P]),

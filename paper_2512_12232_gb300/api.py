@@ -237,6 +237,16 @@ def surface_velocity(mesh: Mesh, v=0, body=0):
     return np.array(th[:n]), np.array(ut[:n])
 
 
+def velocity_field(mesh: Mesh, v=0):
+    """(u, v) at the centre of every cell of variant v after a solve, as (ny, nx) tensors on
+    the device (u = dpsi/dy, v = -dpsi/dx; 0 on inactive cells)."""
+    nx, ny = mesh.grids[v][4], mesh.grids[v][5]
+    u = torch.empty((ny, nx), dtype=torch.float64, device="cuda")
+    w = torch.empty((ny, nx), dtype=torch.float64, device="cuda")
+    check(L.load().pf_velocity_field(mesh.handle, v, _ptr(u), _ptr(w), _stream()))
+    return u, w
+
+
 def copfi(mesh: Mesh, v=0, lo=3, hi=4, U=1.0):
     """(CoPFI, Q) = ((C_hi - C_lo) / (U (cy_hi - cy_lo)), C_hi - C_lo) after a solve."""
     c = C.c_double()

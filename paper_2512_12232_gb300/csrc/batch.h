@@ -183,6 +183,7 @@ void export_tags(Batch& b, int v, int8_t* kind, int32_t* body);
 
 // solver.cu
 void make_schedule(Batch& b);
+void velocity_field(Batch& b, int v, double* dev_u, double* dev_v);
 void ensure_solver_memory(Batch& b, int precision);
 void apply_timing(Batch& b, int precision, int reps, double* us, double* bytes);
 void apply_operator(Batch& b, int precision, const double* dev_p, double* dev_y, double* body_sums);

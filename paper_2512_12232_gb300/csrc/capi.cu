@@ -285,6 +285,16 @@ pf_status pf_last_timing(const pf_batch* h, pf_timing* out) {
   });
 }
 
+pf_status pf_velocity_field(pf_batch* h, int variant, double* dev_u, double* dev_v, void* stream) {
+  return guarded([&]() -> pf_status {
+    Batch* b = (Batch*)h;
+    bind(b, stream);
+    check_variant(b, variant);
+    velocity_field(*b, variant, dev_u, dev_v);
+    return PF_OK;
+  });
+}
+
 pf_status pf_surface_velocity(pf_batch* h, int variant, int body, double* theta_deg, double* ut, int cap,
                               int* count, void* stream) {
   return guarded([&]() -> pf_status {

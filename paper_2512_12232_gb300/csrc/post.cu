@@ -45,7 +45,58 @@ __global__ void k_surface_velocity(const DevVariant* var, int v, int gb, const p
   theta[e - e0] = t;
 }
 
+// Element velocity of the solved psi: u = dpsi/dy, v = -dpsi/dx of the bilinear
+// interpolant at the cell centre (xi = eta = 0), where dN_a/dxi = xi_a / 4 and
+// dN_a/deta = eta_a / 4, through the isoparametric Jacobian.  One thread per logical cell
+// (i, j), i < nx, j < ny, written at j*nx + i; inactive cells get 0.  Corners of an active
+// cell are never inactive; BODY corners carry their body's value.
+__global__ void k_velocity_field(const DevVariant* var, int v, const uint8_t* tag, const int* bid, const double* X,
+                                 long long Vtot, const double* x64, const double* xb, double* u_out, double* v_out) {
+  const DevVariant& V = var[v];
+  const long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (m >= (long long)V.nx * V.ny) return;
+  const int i = (int)(m % V.nx), j = (int)(m / V.nx);
+  const long long n = V.base + (long long)j * V.P + i;
+  if (!(tag[n] & CELL_ACTIVE)) {
+    u_out[m] = 0.0;
+    v_out[m] = 0.0;
+    return;
+  }
+  const long long idx[4] = {n, n + 1, n + 1 + V.P, n + V.P};   // corners counter-clockwise
+  const double dxi[4] = {-0.25, 0.25, 0.25, -0.25}, deta[4] = {-0.25, -0.25, 0.25, 0.25};
+  double f[4], j00 = 0.0, j01 = 0.0, j10 = 0.0, j11 = 0.0;
+  for (int c = 0; c < 4; ++c) {
+    const int kind = tag[idx[c]] & KIND_MASK;
+    f[c] = kind == K_BODY ? xb[V.body0 + bid[idx[c]]] : x64[idx[c]];
+    const double x = X[idx[c]], y = X[Vtot + idx[c]];
+    j00 += x * dxi[c];
+    j01 += y * dxi[c];
+    j10 += x * deta[c];
+    j11 += y * deta[c];
+  }
+  const double det = j00 * j11 - j01 * j10;
+  double fx = 0.0, fy = 0.0;
+  for (int c = 0; c < 4; ++c) {
+    fx += (j11 * dxi[c] - j01 * deta[c]) / det * f[c];
+    fy += (-j10 * dxi[c] + j00 * deta[c]) / det * f[c];
+  }
+  u_out[m] = fy;
+  v_out[m] = -fx;
+}
+
 }  // namespace
+
+void velocity_field(Batch& b, int v, double* dev_u, double* dev_v) {
+  if (!b.solved) throw Error{PF_EINVAL, "no solution on this handle yet"};
+  if (!dev_u || !dev_v) throw Error{PF_EINVAL, "NULL output"};
+  const long long ncell = (long long)b.hv[v].g.nx * b.hv[v].g.ny;
+  if (ncell == 0) return;
+  k_velocity_field<<<(unsigned)((ncell + 255) / 256), 256, 0, b.stream>>>(b.d_var, v, b.tag, b.bid, b.X, b.Vtot,
+                                                                          b.x64, b.sol64, dev_u, dev_v);
+  PF_CUDA(cudaGetLastError());
+  b.launches += 1;
+  PF_CUDA(cudaStreamSynchronize(b.stream));
+}
 
 int surface_velocity(Batch& b, int v, int body, double* theta, double* ut, int cap) {
   if (!b.solved) throw Error{PF_EINVAL, "no solution on this handle yet"};

@@ -50,6 +50,7 @@ def test_error_path_without_gpu(lib_path):
     assert lib.pf_batch_solve(None, 1.0, None, None, None, None) == _lib.PF_EINVAL
     assert lib.pf_batch_grad(None, 0, 3, 4, 1.0, 1e-12, None, None, None, None) == _lib.PF_EINVAL
     lib.pf_mesh_destroy(None)  # a NULL handle is a no-op, as for pf_batch_destroy
+    assert lib.pf_velocity_field(None, 0, None, None, None) == _lib.PF_EINVAL
 
 
 def test_product_path_fails_loudly_without_library(tmp_path):

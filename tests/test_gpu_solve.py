@@ -100,6 +100,23 @@ def test_many_variant_batch(api):
         np.testing.assert_allclose(res.body_psi[boffs[v]:boffs[v + 1]], u[s.n_free:], rtol=0, atol=BODY_TOL)
 
 
+def test_velocity_field_matches_oracle(api):
+    """Element velocities (u, v) = (dpsi/dy, -dpsi/dx) at cell centres against the
+    oracle's, both from their own FP64 solutions; inactive cells are 0."""
+    from oracle import potential as OPO
+    c = W.five_cylinder_case(0.25, 160, 80, 20)
+    m, s, u, psi_ref = oracle_solution(c, 1.0)
+    uo, vo = OPO.velocity_from_psi(m, psi_ref)
+    with api.mesh_build(c.grid, c.bodies, c.sweeps, c.bc) as g:
+        api.psi_solve(g, U=1.0, tol=1e-13, precision=api.PF_FP64)
+        ug, vg = (t.cpu().numpy() for t in api.velocity_field(g, 0))
+    assert ug.shape == (c.ny, c.nx)
+    scale = max(np.abs(uo).max(), np.abs(vo).max())
+    np.testing.assert_allclose(ug[m.active], uo, rtol=0, atol=1e-8 * scale)
+    np.testing.assert_allclose(vg[m.active], vo, rtol=0, atol=1e-8 * scale)
+    assert np.all(ug[~m.active] == 0.0) and np.all(vg[~m.active] == 0.0)
+
+
 def test_solve_is_deterministic(api):
     c = W.five_cylinder_case(0.5, 160, 80, 20)
     outs = []
