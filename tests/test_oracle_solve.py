@@ -100,6 +100,60 @@ def test_surface_velocity_approaches_two_u_sin_theta():
     assert err[1] < 0.75 * err[0] and err[1] < 0.3
 
 
+def exact_inclined_stream_psi(x, y, a, U=1.0, alpha=0.0):
+    """Uniform stream at angle alpha past a cylinder of radius a at the origin:
+    psi = U (y cos(alpha) - x sin(alpha)) (1 - a^2/r^2), zero on the cylinder."""
+    r2 = np.maximum(x * x + y * y, 1e-300)
+    return U * (y * np.cos(alpha) - x * np.sin(alpha)) * (1.0 - a * a / r2)
+
+
+def _cylinder_surface_velocity(nx, alpha, U=1.0):
+    c = W.Case(-4.0, 4.0, -2.0, 2.0, nx, nx // 2, np.array([[0.0, 0.0, 0.5]]), 3 * nx // 8)
+    m = M.build_mesh(c.grid, c.bodies, c.sweeps, c.bc)
+    g = exact_inclined_stream_psi(m.x, m.y, 0.5, U, alpha).ravel()
+    sysm = S.assemble(m, g=g)
+    u, psi = SV.solve_direct(sysm)
+    return P.surface_velocity(m, psi, u[sysm.n_free:], 0)
+
+
+@pytest.mark.parametrize("alpha_deg", [0.0, 30.0])
+def test_signed_surface_velocity_and_theta_convention(alpha_deg):
+    """Section "Velocity Field and Surface Tangential Velocity": u_t = (psi_c - psi_b) / d_nc
+    is the outward normal derivative of psi, so on the exact-data cylinder it converges to
+    d psi / d r at r = a, which is 2U sin(theta - alpha) with theta the polar angle
+    counter-clockwise from +x (downstream for alpha = 0).  The signed values are compared
+    (no absolute values), at two refinements with a falling error.  For alpha = 0 the
+    speed is positive over the top (theta near 90) and negative under the bottom (near 270).
+    A clockwise theta or one counted counter-clockwise from the upstream axis misses the
+    signed profile by O(1) at either angle; theta counted clockwise from the upstream axis
+    agrees with it at alpha = 0 (fore-aft symmetry of the flow), and at alpha = 30 degrees,
+    where the profile has no mirror symmetry, it misses by O(1) as well."""
+    alpha = np.radians(alpha_deg)
+    errs = []
+    for nx in (128, 256):
+        th, ut = _cylinder_surface_velocity(nx, alpha)
+        ref = 2.0 * np.sin(np.radians(th) - alpha)
+        errs.append(np.mean(np.abs(ut - ref)))
+        if nx == 256:
+            wrong = {"clockwise": -np.radians(th), "from_upstream_cw": np.pi - np.radians(th),
+                     "from_upstream_ccw": np.radians(th) - np.pi}
+            for name, t_wrong in wrong.items():
+                if alpha_deg == 0.0 and name == "from_upstream_cw":
+                    continue          # fore-aft symmetric at alpha = 0: only alpha = 30 tells it apart
+                assert np.mean(np.abs(ut - 2.0 * np.sin(t_wrong - alpha))) > 0.5, name
+            if alpha_deg == 0.0:
+                top = np.abs(th - 90.0) < 30.0
+                bottom = np.abs(th - 270.0) < 30.0
+                assert top.sum() > 5 and bottom.sum() > 5
+                assert np.all(ut[top] > 0.0) and np.all(ut[bottom] < 0.0)
+            # least-squares fit u_t ~ a sin(theta) + b cos(theta): the exact profile has
+            # a = 2U cos(alpha), b = -2U sin(alpha) (amplitude and phase of the signed curve)
+            t = np.radians(th)
+            (a_fit, b_fit), *_ = np.linalg.lstsq(np.stack([np.sin(t), np.cos(t)], axis=1), ut, rcond=None)
+            assert abs(a_fit - 2.0 * np.cos(alpha)) < 0.1 and abs(b_fit + 2.0 * np.sin(alpha)) < 0.1, (a_fit, b_fit)
+    assert errs[1] < 0.75 * errs[0] and errs[1] < 0.3, errs
+
+
 def test_paper_validation_channel_body_value_is_one_half():
     """Validation section: walls psi = 0 (bottom) and psi = 1 (top), natural inlet and
     outlet, a centred cylinder; the paper reports 0.50001959 against the exact 0.5."""
