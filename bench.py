@@ -1,33 +1,40 @@
 #!/usr/bin/env python
 """Benchmark of the matrix-free Q4 stream-function solve on GB300.
 
-Workload (one step = the whole hot path over one batch of synthetic input):
-five cylinders of diameter 1 in [-20,20]x[-10,10] on a 2048x1024 background grid,
-200 smoothing sweeps, the five gap ratios delta in {0.1, 0.25, 0.5, 1, 2} as one
-batch of five variants: mesh build (classify, project, smooth, element matrices)
--> mixed-precision solve (FP32 matrix-free operator and vectors, FP64 reductions,
-FP64 true residual and iterative refinement) to a relative true residual of 1e-8
--> body stream-function values, CoPFI and the nodal psi field.
+Workload (one step = the whole hot path over one batch of synthetic input): the
+256-variant parametric sweep of the five-cylinder layout (seed 0): gap ratio delta
+uniform in [0.1, 2], every centre jittered by N(0, 0.05^2), background grids of uneven
+sizes nx in {256, 288, ..., 1024}, ny = nx/2 on [-20,20]x[-10,10], 200 smoothing sweeps,
+all 256 variants in one batch: mesh build (classify, project, smooth, element matrices)
+-> mixed-precision solve (FP32 matrix-free operator and vectors, FP64 reductions, FP64
+true residual and iterative refinement) of every variant to a relative true residual of
+1e-8 in one persistent fused launch per CG iteration (graph-captured chunks)
+-> body stream-function values, CoPFI and the nodal psi fields.
 
-Metric: CG DOF-iterations per second (sum over variants of N_dof x CG iterations,
-per second of the whole step), with the HBM bandwidth of the fused CG-iteration
-kernel against the measured copy bandwidth and the batched solves per second.
+Metric: CG DOF-iterations per second (sum over variants of N_dof x CG iterations, per
+second of the whole step) as `value`, batched solves per second beside it, and the HBM
+bandwidth of the fused CG-iteration kernel against the measured copy bandwidth.  After the
+timed region the line adds `plain_fp64` (the same workload solved in FP64 to the same
+1e-8, timed the same way) and `parity` (the error of two variants' psi, body values and
+CoPFI against the CPU oracle's direct solutions).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-`--config` selects another workload of the same hot path for separate measurements
-(the default, c2, is the headline line above):
+`--config` selects another workload of the same hot path (the default, c4, is the line
+above):
     c1  one cylinder, 128x64 grid, 50 sweeps (validation case)
-    c3  the five-cylinder layout at delta=0.25 on an 8192x4096 grid (33.6 M nodes)
-    c4  256-variant parametric sweep (seed 0): jittered five-cylinder layouts,
-        nx in {256, 288, ..., 1024}, ny = nx/2, one batch; reports solves/s
+    c2  five cylinders on 2048x1024, delta in {0.1, 0.25, 0.5, 1, 2}, 200 sweeps
+    c3  the five-cylinder layout at delta=0.25 on an 8192x4096 grid (33.6 M nodes),
+        plus the bandwidth of the stand-alone operator (`apply_sweep`)
     c5  64-variant gradient study (seed 1), 1024x512: solve + adjoint CoPFI shape
         gradient per variant; reports gradients/s
+`--apply-sweep` times only the stand-alone operator on the selected workload.
 
 Under torchrun (N > 1) every rank solves its own copy of the batch (independent
 problems, no collective on the data path: "weak" scaling); rank 0 prints one JSON
 line with the whole-job value.  `--impl reference` times the CPU oracle (the plain
-FP64 numpy implementation the tests compare against) on a bounded sample.
+FP64 numpy implementation the tests compare against) on a bounded sample, one process
+per host core.
 """
 from __future__ import annotations
 
@@ -49,10 +56,10 @@ METRIC = "CG DOF-iters/s & HBM GB/s of matrix-free Q4 apply; batched solves/s at
 UNIT = "DOF-iters/s"
 DELTAS = (0.1, 0.25, 0.5, 1.0, 2.0)
 NX, NY, SWEEPS = 2048, 1024, 200
-WORKLOAD = "five_cylinders_2048x1024_S200_delta{0.1,0.25,0.5,1,2}_batched_mixed_1e-8"
+WORKLOAD = "parametric_sweep_256_variants_nx256-1024_S200_seed0_mixed_1e-8"
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -61,16 +68,24 @@ def parse():
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--inner-tol", type=float, default=2e-7)
-    ap.add_argument("--nx", type=int, default=NX)
-    ap.add_argument("--variants", type=int, default=len(DELTAS))
-    ap.add_argument("--cpu-iters", type=int, default=60, help="oracle CG iterations in the CPU sample")
+    ap.add_argument("--nx", type=int, default=NX, help="c2: background grid width")
+    ap.add_argument("--variants", type=int, default=None, help="c2: number of variants (default 5), "
+                    "c4: first variants of the sweep (default 256)")
+    ap.add_argument("--cpu-units", type=float, default=5e7,
+                    help="oracle DOF-iterations per host process in one CPU sample")
+    ap.add_argument("--cpu-procs", type=int, default=0, help="host processes of the CPU oracle (0: all cores)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--config", choices=["c1", "c2", "c3", "c4", "c5"], default="c2")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain-FP64 comparison block")
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--no-parity", action="store_true", help="skip the oracle parity block")
+    ap.add_argument("--apply-sweep", action="store_true", help="time only the stand-alone operator")
+    ap.add_argument("--apply-reps", type=int, default=100)
+    ap.add_argument("--config", choices=["c1", "c2", "c3", "c4", "c5"], default="c4")
     ap.add_argument("--tune", dest="tune", action="store_true", default=True,
                     help="re-balance the persistent CG schedule from timed launches (default)")
     ap.add_argument("--no-tune", dest="tune", action="store_false")
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 def cases(args):
@@ -80,20 +95,24 @@ def cases(args):
     if args.config == "c3":
         return [W.five_cylinder_case(0.25, 8192, 4096, SWEEPS)]
     if args.config == "c4":
-        return W.parametric_sweep(256, seed=0)
+        return W.parametric_sweep(256, seed=0)[: args.variants or 256]
     if args.config == "c5":
         return W.gradient_study(64, seed=1, nx=1024)
-    ds = (list(DELTAS) * ((args.variants + len(DELTAS) - 1) // len(DELTAS)))[: args.variants]
+    nv = args.variants or len(DELTAS)
+    ds = (list(DELTAS) * ((nv + len(DELTAS) - 1) // len(DELTAS)))[:nv]
     return [W.five_cylinder_case(d, args.nx, args.nx // 2, SWEEPS) for d in ds]
 
 
 def workload_name(args, n_cases):
-    if args.config == "c2" and args.nx == NX and args.variants == 5 and args.precision == "mixed":
+    if args.config == "c4" and n_cases == 256 and args.precision == "mixed" and args.tol == 1e-8:
         return WORKLOAD
     names = {"c1": "single_cylinder_128x64_S50", "c3": "five_cylinders_8192x4096_S200_delta0.25",
-             "c4": "parametric_sweep_256_variants_nx256-1024_S200_seed0",
+             "c4": f"parametric_sweep_{n_cases}_variants_nx256-1024_S200_seed0",
              "c5": "gradient_study_64_variants_1024x512_S200_seed1_copfi_adjoint"}
-    base = names.get(args.config, f"five_cylinders_{args.nx}x{args.nx // 2}_x{n_cases}")
+    if args.config == "c2" and args.nx == NX and n_cases == 5:
+        base = "five_cylinders_2048x1024_S200_delta{0.1,0.25,0.5,1,2}_batched"
+    else:
+        base = names.get(args.config, f"five_cylinders_{args.nx}x{args.nx // 2}_x{n_cases}")
     return f"{base}_{args.precision}_{args.tol:g}"
 
 
@@ -138,10 +157,16 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(nodes_per_launch):
-    """DRAM bytes per fused CG launch from the committed ncu summary, scaled to this
-    launch by node count; None if absent or if the kernel sources changed since."""
-    path = os.path.join(ROOT, "profiles", "k_cg_mixed_five_cylinders.md")
+TRAFFIC_PROFILE = {"c2": "k_cg_mixed_five_cylinders.md", "c4": "k_cg_mixed_parametric_sweep.md"}
+
+
+def ncu_traffic(config, nodes_per_launch):
+    """DRAM bytes per fused CG launch from the committed ncu summary of this workload,
+    scaled to the average nodes one launch processes; None if absent or if the kernel
+    sources changed since."""
+    if config not in TRAFFIC_PROFILE:
+        return None
+    path = os.path.join(ROOT, "profiles", TRAFFIC_PROFILE[config])
     try:
         txt = open(path).read()
     except OSError:
@@ -220,60 +245,165 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ CPU oracle sample
-def oracle_case(args):
-    """The variant the CPU oracle is timed on: the workload's own for c1, c2 (delta =
-    0.25), c4 and c5; for c3 the same layout at 2048x1024 (the oracle's rate per
-    DOF-iteration does not depend on the grid size, and a 33.6 M-node FP64 assembly
-    on the host is far outside a bounded sample)."""
+def oracle_cases(args):
+    """The variants the CPU oracle is timed on: the workload's own for c1, c2, c4 and c5;
+    for c3 the same layout at 2048x1024 (the oracle's rate per DOF-iteration does not
+    depend on the grid size, and a 33.6 M-node FP64 assembly on the host is far outside
+    a bounded sample)."""
     from paper_2512_12232_gb300 import workloads as W
     if args.config == "c3":
-        return W.five_cylinder_case(0.25, 2048, 1024, SWEEPS)
-    cs = cases(args)
-    return cs[1 % len(cs)] if args.config == "c2" else cs[0]
+        return [W.five_cylinder_case(0.25, 2048, 1024, SWEEPS)]
+    return cases(args)
 
 
-def oracle_sample(args, iters, reps=1):
-    """The oracle's element-by-element CG (Appendix A) on one variant: returns
-    (DOF-iters/s, seconds, n_dof).  Setup (mesh, element matrices) untimed."""
+def _oracle_proc(case, units, conn, barrier):
+    """One host process of the CPU sample: builds its variant's mesh and element matrices
+    (untimed), then on every request runs the oracle's element-by-element CG (Appendix A)
+    for a fixed number of iterations between two wall-clock stamps."""
+    import numpy as np  # noqa: F401  (imported here: the process starts from scratch)
+
     from oracle import mesh as OM, solve as OS, system as OSY
-    c = oracle_case(args)
-    m = OM.build_mesh(c.grid, c.bodies, c.sweeps, c.bc)
+    m = OM.build_mesh(case.grid, case.bodies, case.sweeps, case.bc)
     s = OSY.assemble(m, 1.0)
-    times = []
-    for _ in range(reps):
-        t = time.perf_counter()
-        OS.cg_paper(s, m.kind.ravel(), m.body.ravel(), tol=0.0, k_max=iters, criterion="paper")
-        times.append(time.perf_counter() - t)
-    return s.n_dof * iters / min(times), times, s.n_dof
+    kind, body = m.kind.ravel(), m.body.ravel()
+    iters = max(2, int(round(units / s.n_dof)))
+    conn.send((s.n_dof, iters))
+    while conn.recv():
+        barrier.wait(timeout=900)
+        t0 = time.time()
+        OS.cg_paper(s, kind, body, tol=0.0, k_max=iters, criterion="paper")
+        conn.send((s.n_dof * iters, t0, time.time()))
+
+
+class OracleSample:
+    """The CPU oracle timed on the host cores: one spawned process per core, each on one
+    variant of the workload (variants assigned round-robin), started together by a
+    barrier.  A step's rate is the DOF-iterations of all processes divided by the wall
+    time from the first start to the last end."""
+
+    def __init__(self, case_list, procs=0, units=5e7):
+        import multiprocessing as mp
+        n = procs if procs > 0 else (os.cpu_count() or 1)
+        n = max(1, min(n, 64))
+        ctx = mp.get_context("spawn")
+        env = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+        for k in env:
+            os.environ[k] = "1"          # one thread per process: the processes are the parallelism
+        try:
+            self.barrier = ctx.Barrier(n)
+            self.conns, self.procs = [], []
+            for w in range(n):
+                a, b = ctx.Pipe()
+                p = ctx.Process(target=_oracle_proc, args=(case_list[w % len(case_list)], units, b, self.barrier),
+                                daemon=True)
+                p.start()
+                self.conns.append(a)
+                self.procs.append(p)
+        finally:
+            for k, v in env.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+        self.info = [c.recv() for c in self.conns]
+        self.n = n
+        self.case_list = case_list
+
+    def step(self):
+        for c in self.conns:
+            c.send(True)
+        out = [c.recv() for c in self.conns]
+        units = sum(o[0] for o in out)
+        wall = max(o[2] for o in out) - min(o[1] for o in out)
+        return units, wall
+
+    def describe(self):
+        sizes = sorted({(c.nx, c.ny) for c in self.case_list[: self.n]})
+        its = sorted({i for _, i in self.info})
+        return (f"oracle element-by-element CG (Appendix A) in {self.n} host processes, one variant each "
+                f"({len(set(range(min(self.n, len(self.case_list)))))} distinct variants, grids "
+                f"{sizes[0][0]}x{sizes[0][1]} to {sizes[-1][0]}x{sizes[-1][1]}), {its[0]}-{its[-1]} iterations "
+                f"per process per step; mesh and element matrices built untimed")
+
+    def close(self):
+        for c in self.conns:
+            try:
+                c.send(False)
+            except Exception:
+                pass
+        for p in self.procs:
+            p.join(timeout=10)
+            if p.is_alive():
+                p.terminate()
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
-    iters = max(1, args.cpu_iters // 3)
-    from oracle import mesh as OM, solve as OS, system as OSY
-    c = oracle_case(args)
-    m = OM.build_mesh(c.grid, c.bodies, c.sweeps, c.bc)
-    s = OSY.assemble(m, 1.0)
-    kind, body = m.kind.ravel(), m.body.ravel()
-    for _ in range(args.warmup):
-        OS.cg_paper(s, kind, body, tol=0.0, k_max=iters, criterion="paper")
-    t = time.perf_counter()
-    for _ in range(args.steps):
-        OS.cg_paper(s, kind, body, tol=0.0, k_max=iters, criterion="paper")
-    el = time.perf_counter() - t
-    value = s.n_dof * iters * args.steps / el
-    sample = (f"oracle element-by-element CG (Appendix A), {iters} iterations per step on one "
-              f"{c.nx}x{c.ny} variant '{c.name}' (N_dof={s.n_dof}); mesh and element matrices built untimed")
+    smp = OracleSample(oracle_cases(args), args.cpu_procs, args.cpu_units)
+    try:
+        for _ in range(args.warmup):
+            smp.step()
+        units, wall = 0.0, 0.0
+        for _ in range(args.steps):
+            u, w = smp.step()
+            units += u
+            wall += w
+    finally:
+        smp.close()
+    value = units / wall
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": workload_name(args, len(cases(args))),
-                                            "sample": "one variant, fixed CG iterations"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+                                            "sample": "fixed CG iterations per host process and step"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": smp.n, "kind": "oracle",
+                             "sample": smp.describe()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+# ------------------------------------------------------------------ parity against the oracle
+def _oracle_direct(case):
+    """The oracle's direct solution of one variant (runs in a spawned process)."""
+    from oracle import mesh as OM, solve as OS, system as OSY
+    m = OM.build_mesh(case.grid, case.bodies, case.sweeps, case.bc)
+    s = OSY.assemble(m, 1.0)
+    u, psi = OS.solve_direct(s)
+    return {"psi": psi, "C": u[s.n_free:], "A": s.A.tocsr(), "b": s.b, "dof": s.dof}
+
+
+def parity_variants(cs):
+    """Two variants of the batch whose results are compared with the oracle: the first one
+    and the largest one."""
+    big = max(range(len(cs)), key=lambda v: cs[v].n_nodes)
+    return sorted({0, big})
+
+
+def parity_block(api, cs, res, offs, boffs, cps, picks, refs, tol):
+    """Errors of the solve's outputs for the picked variants against the oracle: relative
+    L2 of nodal psi, max |C_k - C_k*|, |CoPFI - CoPFI*| (bodies 3, 4), and the relative
+    residual of the GPU solution recomputed with the oracle's matrix."""
+    import numpy as np
+    out = []
+    psi = res.psi.cpu().numpy()
+    for v, ref in zip(picks, refs):
+        c = cs[v]
+        pv = psi[offs[v]:offs[v + 1]]
+        ug = np.empty(ref["A"].shape[0])
+        k = ref["dof"] >= 0
+        ug[ref["dof"][k]] = pv[k]
+        C = res.body_psi[boffs[v]:boffs[v + 1]]
+        row = {"variant": v, "grid": f"{c.nx}x{c.ny}", "n_dof": int(ref["A"].shape[0]),
+               "rel_l2_psi": float(np.linalg.norm(pv - ref["psi"]) / np.linalg.norm(ref["psi"])),
+               "max_abs_body_psi": float(np.abs(C - ref["C"]).max()) if len(C) else 0.0,
+               "rel_residual_by_oracle": float(np.linalg.norm(ref["b"] - ref["A"] @ ug) / np.linalg.norm(ref["b"]))}
+        if len(c.bodies) >= 5:
+            dy = c.bodies[4][1] - c.bodies[3][1]
+            row["abs_copfi"] = float(abs(cps[v] - (ref["C"][4] - ref["C"][3]) / dy))
+        out.append(row)
+    return {"oracle": "direct sparse LU of the reduced system (FP64)", "tol": tol, "variants": out}
 
 
 # ------------------------------------------------------------------ multi-rank
@@ -302,6 +432,25 @@ def aggregate(vals, e2e, dist, device):
 
 
 # ------------------------------------------------------------------ GPU arm
+def _apply_sweep(api, cs, reps, hbm):
+    """Bandwidth of the stand-alone Q4 operator (no conversions, no body sums), FP32 and
+    FP64: timings of `reps` back-to-back applications each (ten for FP32, three for the
+    FP64 operator, which is bound by FP64 arithmetic), best and median."""
+    g = api.batch_build(cs)
+    out = {}
+    for name, pr, n_t, r in (("fp32", api.PF_MIXED, 10, reps), ("fp64", api.PF_FP64, 3, max(1, reps // 5))):
+        ts = []
+        for _ in range(n_t):
+            us, by = g.apply_timing(pr, reps=r)
+            ts.append(us)
+        best, med = min(ts), float(statistics.median(ts))
+        out[name] = {"us_per_apply": med, "us_best": best, "timings": n_t, "reps_per_timing": r,
+                     "algorithmic_bytes": by, "GB/s": by / med / 1e3, "GB/s_best": by / best / 1e3,
+                     "frac_of_measured_hbm": by / med / 1e3 / hbm}
+    g.close()
+    return out
+
+
 def run_ours(args, rank, world, local):
     import numpy as np
     import torch
@@ -315,12 +464,20 @@ def run_ours(args, rank, world, local):
     api.use_torch_allocator()
     cs = cases(args)
     prec = api.PF_MIXED if args.precision == "mixed" else api.PF_FP64
+    hbm = peaks().get("hbm_gbs")
+    if args.apply_sweep:
+        if rank == 0:
+            sw = _apply_sweep(api, cs, args.apply_reps, hbm or 6800.0)
+            print(json.dumps({"workload": workload_name(args, len(cs)), "apply_sweep": sw}), flush=True)
+        if dist:
+            dist.destroy_process_group()
+        return 0
 
-    def step(host_out=None):
+    def step(p=prec, host_out=None, keep=False):
         t_mesh = time.perf_counter()
         g = api.batch_build(cs)                  # returns after the device mesh is complete
         t_mesh = time.perf_counter() - t_mesh
-        res = api.psi_solve(g, U=1.0, tol=args.tol, precision=prec, inner_tol=args.inner_tol,
+        res = api.psi_solve(g, U=1.0, tol=args.tol, precision=p, inner_tol=args.inner_tol,
                             tune_schedule=args.tune)
         if args.config == "c5":
             api.grad(g, api.PF_OBJ_COPFI, 3, 4, 1.0, args.tol, want_dX=False)
@@ -331,37 +488,53 @@ def run_ours(args, rank, world, local):
         tm = g.timing()
         tm["mesh_build_ms"] = 1e3 * t_mesh
         st = [g.stats(v) for v in range(len(cs))]
+        if keep:
+            return res, cps, tm, st, g
         g.close()
         return res, cps, tm, st
 
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
+    def timed(p, n_steps, n_warm, clocks_index=None):
+        for _ in range(n_warm):
+            step(p)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        stream = torch.cuda.current_stream()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        recs = []
+        clk = ClockSampler(clocks_index) if clocks_index is not None else None
+        if clk:
+            clk.__enter__()
+        try:
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(n_steps):
+                recs.append(step(p))
+            e1.record(stream)
+            torch.cuda.synchronize()
+        finally:
+            if clk:
+                clk.__exit__(None, None, None)
+        return recs, e0.elapsed_time(e1) / 1e3, (clk.summary() if clk else None)
+
+    def units_of(recs):
+        return sum(sum(st[v]["n_dof"] * res.info[v]["iters"] for v in range(len(cs))) for res, _, _, st in recs)
+
+    records, elapsed, clocks = timed(prec, args.steps, args.warmup, local)
     if dist:
         dist.barrier()
-    stream = torch.cuda.current_stream()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    records = []
-    with ClockSampler(local) as clk:
-        torch.cuda.synchronize()
-        e0.record(stream)
-        for _ in range(args.steps):
-            records.append(step())
-        e1.record(stream)
-        torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    elapsed = e0.elapsed_time(e1) / 1e3
-    dof_iters = sum(sum(st[v]["n_dof"] * res.info[v]["iters"] for v in range(len(cs)))
-                    for res, _, _, st in records)
-    solves = sum(len(cs) for _ in records)
+    dof_iters = units_of(records)
+    solves = len(cs) * len(records)
     ok = all(i["status"] == 0 and i["rel_true_residual"] <= args.tol for res, _, _, _ in records for i in res.info)
     cg_ms = sum(tm["cg_kernel_ms"] for _, _, tm, _ in records)
     cg_launches = sum(tm["cg_launches"] for _, _, tm, _ in records)
     cg_bytes = sum(tm["cg_bytes_per_launch"] * tm["cg_launches"] for _, _, tm, _ in records)
     launches = sum(tm["kernel_launches"] for _, _, tm, _ in records)
     nodes = sum(st[v]["n_nodes"] for v in range(len(cs)) for st in [records[0][3]])
+    # nodes one fused CG launch processes, averaged over the launches (finished variants drop out)
+    node_launches = sum(sum(st[v]["n_nodes"] * res.info[v]["iters"] for v in range(len(cs)))
+                        for res, _, _, st in records)
     # per-step averages: mesh build (host wall time, ends in a device synchronisation), the
     # whole solve (device events, tuning launches included), its fused-CG and refinement
     # kernels, and the rest of the step (outputs, gradient, copies, teardown)
@@ -378,59 +551,74 @@ def run_ours(args, rank, world, local):
         if dist:
             dist.barrier()
         t = time.perf_counter()
-        e2e_rec = [step(host) for _ in range(args.steps)]
+        e2e_rec = [step(prec, host) for _ in range(args.steps)]
         torch.cuda.synchronize()
         e2e_el = time.perf_counter() - t
-        e2e_units = sum(sum(st[v]["n_dof"] * res.info[v]["iters"] for v in range(len(cs)))
-                        for res, _, _, st in e2e_rec)
         nbody = sum(len(c.bodies) for c in cs)
         h2d = len(cs) * 40 + (len(cs) + 1) * 4 + nbody * 24 + 16        # grids, offsets, bodies, sides
         d2h = 8 * int(nodes) + 8 * nbody + 32 * len(cs)                 # psi, body psi, solve records
-        e2e = [e2e_units, e2e_el, h2d, d2h]
+        e2e = [units_of(e2e_rec), e2e_el, h2d, d2h]
 
     vals, e2e = aggregate([dof_iters, elapsed, solves], e2e, dist, "cuda")
 
-    # c3: bandwidth of the stand-alone Q4 operator (no conversions, no body sums), FP32 and FP64
     apply_sweep = None
     if args.config == "c3" and rank == 0:
-        g = api.batch_build(cs)
-        hbm = peaks().get("hbm_gbs") or 6800.0
-        apply_sweep = {}
-        # ten timings of 100 back-to-back applications each (the FP64 operator, bound by
-        # FP64 arithmetic, gets 3 of 20): best and median
-        for name, pr, n_t, reps in (("fp32", api.PF_MIXED, 10, 100), ("fp64", api.PF_FP64, 3, 20)):
-            ts = []
-            for _ in range(n_t):
-                us, by = g.apply_timing(pr, reps=reps)
-                ts.append(us)
-            best, med = min(ts), float(statistics.median(ts))
-            apply_sweep[name] = {"us_per_apply": med, "us_best": best, "timings": n_t, "reps_per_timing": reps,
-                                 "algorithmic_bytes": by, "GB/s": by / med / 1e3, "GB/s_best": by / best / 1e3,
-                                 "frac_of_measured_hbm": by / med / 1e3 / hbm}
-        g.close()
+        apply_sweep = _apply_sweep(api, cs, args.apply_reps, hbm or 6800.0)
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return 0
-    pk = peaks()
-    hbm = pk.get("hbm_gbs")
+
+    # plain FP64: the same workload and tolerance, timed the same way
+    fp64 = None
+    if args.precision == "mixed" and not args.no_fp64:
+        rec64, el64, clk64 = timed(api.PF_FP64, args.fp64_steps, 1, local)
+        u64 = units_of(rec64)
+        cgl = sum(tm["cg_launches"] for _, _, tm, _ in rec64)
+        it64 = [res.info[v]["iters"] for v in range(len(cs)) for res in [rec64[-1][0]]]
+        fp64 = {"value": u64 / el64, "unit": UNIT, "steps": args.fp64_steps, "ms_per_step": 1e3 * el64 / args.fp64_steps,
+                "solves_per_s": len(cs) * len(rec64) / el64,
+                "all_converged": all(i["status"] == 0 and i["rel_true_residual"] <= args.tol
+                                     for res, _, _, _ in rec64 for i in res.info),
+                "iters_per_variant": {"min": min(it64), "max": max(it64)},
+                "avg_cg_launch_us": 1e3 * sum(tm["cg_kernel_ms"] for _, _, tm, _ in rec64) / cgl if cgl else None,
+                "clocks": clk64,
+                "mixed_over_fp64_solves_per_s": (vals[2] / vals[1]) / (len(cs) * len(rec64) / el64)}
+
+    # parity: the errors of this solve's outputs against the oracle on two variants
+    parity = None
+    if not args.no_parity and args.config != "c3":
+        import multiprocessing as mp
+        picks = parity_variants(cs) if len(cs) > 1 else [0]
+        with mp.get_context("spawn").Pool(len(picks)) as pool:
+            refs = pool.map(_oracle_direct, [cs[v] for v in picks])
+        res, cps, _, _, g = step(prec, keep=True)
+        parity = parity_block(api, cs, res, g.node_offsets, g.body_offsets, [c for c, _ in cps] if cps else [],
+                              picks, refs, args.tol)
+        g.close()
+    elif args.config == "c3":
+        parity = {"skipped": "a direct oracle solve of the 33.6 M-node grid is outside a bounded sample; "
+                             "tests/test_gpu_full_size.py holds the 2048x1024 batch against the oracle"}
+
     achieved = cg_bytes / (cg_ms / 1e3) / 1e9 if cg_ms > 0 else None
-    traffic = ncu_traffic(nodes)
+    traffic = ncu_traffic(args.config, node_launches / cg_launches) if cg_launches else None
     roofline = {"bound": "hbm", "kernel": "k_cg<float> (fused CG iteration: r, x, p updates + Q4 apply + 4 dots)",
                 "achieved": achieved, "peak": hbm if hbm else 6800.0,
                 "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if hbm else "fallback 6.8 TB/s",
                 "unit": "GB/s", "frac": (achieved / hbm) if (achieved and hbm) else None,
                 "traffic": traffic,
                 "algorithmic_bytes_per_launch": cg_bytes / cg_launches if cg_launches else None,
-                "avg_launch_us": 1e3 * cg_ms / cg_launches if cg_launches else None}
+                "avg_launch_us": 1e3 * cg_ms / cg_launches if cg_launches else None,
+                "avg_nodes_per_launch": node_launches / cg_launches if cg_launches else None}
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        v, times, ndof = oracle_sample(args, args.cpu_iters)
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{args.cpu_iters} iterations of the oracle's element-by-element CG on one "
-                         f"{oracle_case(args).nx}x{oracle_case(args).ny} variant (N_dof={ndof}), "
-                         f"{min(times):.1f} s"}
-    clocks = clk.summary()
+        smp = OracleSample(oracle_cases(args), args.cpu_procs, args.cpu_units)
+        try:
+            u, w = smp.step()
+        finally:
+            smp.close()
+        cpu = {"value": u / w, "unit": UNIT, "cores": smp.n, "kind": "oracle",
+               "sample": f"{smp.describe()}; {w:.1f} s wall"}
     iters = [res.info[v]["iters"] for v in range(len(cs)) for res in [records[-1][0]]]
     line = {
         "metric": METRIC, "value": vals[0] / vals[1], "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -447,10 +635,11 @@ def run_ours(args, rank, world, local):
         "solves_per_s": vals[2] / vals[1], "all_converged": ok,
         "cg_stages": records[-1][2].get("cg_stages"), "schedule_tuned": bool(args.tune),
         "iters_per_variant": iters if len(iters) <= 8 else {"min": min(iters), "max": max(iters)},
-        "copfi": [cp for cp, _ in records[-1][1]],
+        "copfi": [cp for cp, _ in records[-1][1]] if len(cs) <= 8 else None,
         "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": int(launches),
         "breakdown_ms": {**breakdown, "rest": 1e3 * vals[1] / args.steps - breakdown["mesh_build"] - breakdown["solve"]},
         **({"apply_sweep": apply_sweep} if apply_sweep else {}),
+        "plain_fp64": fp64, "parity": parity,
         "e2e": ({"value": e2e[0] / e2e[1], "unit": UNIT, "h2d_bytes_per_step": e2e[2],
                  "d2h_bytes_per_step": e2e[3]} if e2e else None),
     }

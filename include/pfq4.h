@@ -92,8 +92,20 @@ typedef struct pf_mesh_stats {
    where 1e-4 needs 3170, at the same 1e-8 true residual. */
 #define PF_DEFAULT_INNER_TOL 2e-7
 
+/* Stopping rules of a solve (pf_solve_opts.criterion). */
+enum { PF_TOL_REL_TRUE = 0,     /* ||b - A u||_2 / ||b||_2 <= tol, the FP64 true residual of the reduced
+                                   system recomputed at every refinement (the library's default) */
+       PF_TOL_PAPER_ABS = 1 };  /* the stopping test of Appendix A (Algorithm): the sum of squares of
+                                   the reduced residual, sum r^2 over the free rows and the collapsed
+                                   body rows, below tol (absolute; tol is compared with the square,
+                                   as the algorithm compares r_norm = sum r^2).  Each inner CG stops on
+                                   its recurrence residual sum r^2 <= tol as the algorithm does (PF_FP64)
+                                   or at a quarter of it (PF_MIXED); the FP64 true residual then
+                                   confirms sum r^2 <= tol or refines again */
+
 typedef struct pf_solve_opts {
-    double tol;            /* stop when ||b - A u||_2 / ||b||_2 <= tol (true residual, FP64) */
+    double tol;            /* PF_TOL_REL_TRUE: stop when ||b - A u||_2 / ||b||_2 <= tol (true residual,
+                              FP64); PF_TOL_PAPER_ABS: stop when sum r^2 <= tol */
     long long k_max;       /* cap on the total CG iterations per variant */
     int precision;         /* PF_FP64 or PF_MIXED */
     double inner_tol;      /* PF_MIXED: relative residual reduction of each inner FP32 solve
@@ -106,6 +118,7 @@ typedef struct pf_solve_opts {
                               This changes the order in which the dot products are summed:
                               results agree with an untuned solve to rounding, not bit for bit.
                               0: schedule from the static per-tile cost estimate (deterministic). */
+    int criterion;         /* PF_TOL_REL_TRUE (0) or PF_TOL_PAPER_ABS (1); any other value: PF_EINVAL */
 } pf_solve_opts;
 
 typedef struct pf_solve_info {
@@ -177,6 +190,10 @@ pf_status pf_mesh_tags(const pf_batch* b, int variant, int8_t* dev_kind, int32_t
 pf_status pf_apply(pf_batch* b, int precision, const double* dev_p, double* dev_y,
                    double* body_sums, void* stream);
 
+/* Largest total number of bodies a handle may hold for pf_apply_noalloc (the size of its
+   fixed device array of collapsed body rows). */
+#define PF_NOALLOC_MAX_BODIES 4096
+
 /* Allocation-free form of pf_apply (the paper has no counterpart: this exists for the
    library's callers).  For callers that cannot allocate device memory when they apply
    the operator - code whose device memory is all owned by a framework arena or caching
@@ -184,12 +201,15 @@ pf_status pf_apply(pf_batch* b, int precision, const double* dev_p, double* dev_
    synchronise the device and can fail under memory pressure.  Same arguments, results
    and layout as pf_apply; it allocates nothing: the input and output vectors are read
    and written in place, and the collapsed body rows go through a fixed device array of
-   4096 doubles (32 KB) that every GPU loading the library keeps until exit.  A handle
-   with more than 4096 bodies in total is rejected with PF_EINVAL.  The first call on a
-   device looks up that array's device address (once per device); make that first call
-   before any stream capture.  Every call on a device shares the array and it keeps the
-   last call's contents; each call overwrites what it reads back.  Calls that overlap on
-   the GPU (e.g. on two streams at once) race on it. */
+   PF_NOALLOC_MAX_BODIES doubles (32 KB) that every GPU loading the library keeps until
+   exit.  A handle with more than PF_NOALLOC_MAX_BODIES bodies in total is rejected with
+   PF_EINVAL.  The handle is only read, never modified.  The first call on a device looks
+   up that array's device address (once per device) and keeps it for the life of the
+   process, so the library is not to be used across a cudaDeviceReset; make that first
+   call before any stream capture.  The call waits for `stream` to finish its work before
+   returning.  Every call on a device shares the array and it keeps the last call's
+   contents; each call overwrites what it reads back.  Calls that overlap on the GPU
+   (e.g. on two streams at once) race on it. */
 pf_status pf_apply_noalloc(const pf_batch* b, int precision, const double* dev_p, double* dev_y,
                            double* body_sums, void* stream);
 

@@ -21,10 +21,11 @@ import numpy as np
 import torch
 
 from . import _lib as L
-from ._lib import PF_FP64, PF_MIXED, PF_OBJ_COPFI, PF_OBJ_GAP_FLOW, check
+from ._lib import PF_FP64, PF_MIXED, PF_OBJ_COPFI, PF_OBJ_GAP_FLOW, PF_TOL_PAPER_ABS, PF_TOL_REL_TRUE, check
 
 __all__ = ["Mesh", "SolveResult", "mesh_build", "batch_build", "psi_solve", "apply", "surface_velocity",
-           "copfi", "grad", "use_torch_allocator", "PF_FP64", "PF_MIXED", "PF_OBJ_COPFI", "PF_OBJ_GAP_FLOW"]
+           "copfi", "grad", "use_torch_allocator", "PF_FP64", "PF_MIXED", "PF_OBJ_COPFI", "PF_OBJ_GAP_FLOW",
+           "PF_TOL_REL_TRUE", "PF_TOL_PAPER_ABS"]
 
 
 def _stream():
@@ -206,13 +207,20 @@ def apply(mesh: Mesh, p: torch.Tensor, precision=PF_FP64):
     return y, np.array(sums[:nb])
 
 
+def _opts(tol, k_max, precision, inner_tol, chunk, warm_start, tune_schedule, criterion):
+    crit = {"relative": PF_TOL_REL_TRUE, "paper": PF_TOL_PAPER_ABS}.get(criterion, criterion)
+    return L.pf_solve_opts(float(tol), int(k_max), int(precision), float(inner_tol), int(chunk),
+                           int(bool(warm_start)), int(bool(tune_schedule)), int(crit))
+
+
 def psi_solve(mesh: Mesh, U=1.0, tol=1e-8, precision=PF_MIXED, k_max=10_000_000, inner_tol=2e-7,
               chunk=0, warm_start=False, want_psi=True, raise_on_failure=True, method="mpc",
-              tune_schedule=False) -> SolveResult:
+              tune_schedule=False, criterion="relative") -> SolveResult:
     """Solve for psi.  method="mpc": CG on the multi-point-constraint system;
-    method="schur": body values through the Schur complement (N_b + 1 fixed-body solves)."""
-    opts = L.pf_solve_opts(float(tol), int(k_max), int(precision), float(inner_tol), int(chunk),
-                           int(bool(warm_start)), int(bool(tune_schedule)))
+    method="schur": body values through the Schur complement (N_b + 1 fixed-body solves).
+    criterion="relative": stop on the FP64 true residual ||b - A u|| / ||b|| <= tol;
+    criterion="paper": the Appendix A test, sum r^2 <= tol (PF_TOL_PAPER_ABS)."""
+    opts = _opts(tol, k_max, precision, inner_tol, chunk, warm_start, tune_schedule, criterion)
     total = int(mesh.node_offsets[-1])
     psi = torch.empty(total, dtype=torch.float64, device="cuda") if want_psi else None
     nb = mesh.body_offsets[-1]
@@ -275,10 +283,9 @@ def mesh_info(mesh: Mesh) -> dict:
 
 
 def batch_solve(mesh: Mesh, U=1.0, tol=1e-8, precision=PF_MIXED, k_max=10_000_000, inner_tol=2e-7, chunk=0,
-                warm_start=False, raise_on_failure=True, tune_schedule=False) -> SolveResult:
+                warm_start=False, raise_on_failure=True, tune_schedule=False, criterion="relative") -> SolveResult:
     """Solve every variant of the batch; body psi and per-variant info only (no nodal psi)."""
-    opts = L.pf_solve_opts(float(tol), int(k_max), int(precision), float(inner_tol), int(chunk),
-                           int(bool(warm_start)), int(bool(tune_schedule)))
+    opts = _opts(tol, k_max, precision, inner_tol, chunk, warm_start, tune_schedule, criterion)
     nb = mesh.body_offsets[-1]
     bpsi = (C.c_double * max(1, nb))()
     info = (L.pf_solve_info * mesh.n_variants)()

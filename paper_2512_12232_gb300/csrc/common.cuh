@@ -87,6 +87,8 @@ template <> struct __align__(32) State4<double> { double x, r, p, q; };
 
 struct SolveParams {
   double tol2;                 // tol^2
+  double tol_abs;              // paper_abs: the bound on sum r^2
+  int paper_abs;               // 1: stop on sum r^2 <= tol_abs (PF_TOL_PAPER_ABS), 0: on the relative residual
   double inner_rel2;           // inner_tol^2 (mixed) or 0
   long long k_max;
   int mixed;
@@ -119,9 +121,13 @@ struct MeshDev {
 };
 
 // ---------------------------------------------------------------- reductions
-// Compensated two-float accumulation (Knuth TwoSum + exact FMA products): the
-// FP32 path accumulates dot products with ~2^-44 relative error per operation and
-// converts to FP64 once per warp, so no FP64 instruction is issued per node.
+// Compensated two-float accumulation (Knuth TwoSum + exact FMA products, the Dot2
+// scheme of Ogita, Rump and Oishi): every FP32 product x*y is split exactly into
+// p + e with e = fma(x, y, -p), p is added to the high word with TwoSum and the two
+// error terms go to the low word.  A thread's partial sum is thus as accurate as a
+// sum in twice the working precision (~2^-48 relative error per addition for
+// same-sign terms), and it is converted to FP64 once per warp, so no FP64
+// instruction is issued per node.
 struct FF { float hi, lo; };
 
 __device__ __forceinline__ void ff_add_prod(FF& a, float x, float y) {
@@ -181,18 +187,19 @@ template <> struct Acc<float> {
     for (int k = 0; k < 4; ++k) v[k] = FF{0.f, 0.f};
   }
   __device__ void add(int k, float x, float y) { ff_add_prod(v[k], x, y); }
-  // a thread's two products of one tile: each rounded to FP32 and summed in FP32, the
-  // pair sum accumulated with compensation (error <= 2^-23 (|x1 y1| + |x2 y2|) per pair,
-  // no growth with the number of pairs beyond the two-float accumulation error)
-  __device__ void add2(int k, float x1, float y1, float x2, float y2) { ff_add_value(v[k], fmaf(x1, y1, x2 * y2)); }
-  // a thread's N products of one tile strip: each rounded to FP32, summed in FP32, the
-  // group sum accumulated with compensation (error <= N 2^-24 sum |x_u y_u| per group)
+  // a thread's two products: each split exactly into p + e (TwoProd via fmaf) and added
+  // to the two-float accumulator with TwoSum, so no product is rounded
+  __device__ void add2(int k, float x1, float y1, float x2, float y2) {
+    ff_add_prod(v[k], x1, y1);
+    ff_add_prod(v[k], x2, y2);
+  }
+  // a thread's N products of one tile strip, each exact (TwoProd), summed with TwoSum
+  // into the two-float accumulator: the only roundings are the accumulator's own
+  // (about 2^-48 relative per addition for same-sign terms, as for a double-length sum)
   template <int N>
   __device__ void add4(int k, const float (&x)[N], const float (&y)[N]) {
-    float g = x[0] * y[0];
 #pragma unroll
-    for (int u = 1; u < N; ++u) g = fmaf(x[u], y[u], g);
-    ff_add_value(v[k], g);
+    for (int u = 0; u < N; ++u) ff_add_prod(v[k], x[u], y[u]);
   }
   __device__ void warp_reduce(double out[4]) {
 #pragma unroll

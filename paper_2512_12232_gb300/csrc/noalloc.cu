@@ -12,14 +12,15 @@
 // The scratch array is shared by every call on a device and keeps the last call's
 // contents; each call overwrites every slot it reads back, so nothing needs clearing
 // between calls.  Calls whose work overlaps on the GPU (for example on two streams at
-// once) race on that array.
+// once) race on that array.  The call runs on the stream it is given and never touches
+// the handle's own state, so a const handle stays unchanged.
 #include <mutex>
 
 #include "batch.h"
 
 namespace pfq4 {
 
-constexpr int NOALLOC_MAX_BODIES = 4096;
+constexpr int NOALLOC_MAX_BODIES = PF_NOALLOC_MAX_BODIES;
 
 // Collapsed body rows of the last pf_apply_noalloc call on this device.
 static __device__ __align__(256) double g_apply_noalloc_scratch[NOALLOC_MAX_BODIES];
@@ -30,7 +31,9 @@ std::mutex g_setup_mutex;
 constexpr int MAX_DEVICES = 64;
 double* g_scratch_ptr[MAX_DEVICES] = {};
 
-// Device address of the scratch array for the current device (set up once per device).
+// Device address of the scratch array for the current device, looked up on the first
+// call made with that device current and kept for the life of the process (a
+// cudaDeviceReset reloads the module, so the library is not used across one).
 double* scratch_for_current_device() {
   int dev = -1;
   PF_CUDA(cudaGetDevice(&dev));
@@ -126,8 +129,10 @@ __global__ void __launch_bounds__(NT) k_body_rows_logical(MeshDev m, const int* 
 
 }  // namespace
 
-// Same operator and outputs as apply_operator, without any device allocation.
-void apply_operator_noalloc(Batch& b, int precision, const double* dev_p, double* dev_y, double* body_sums) {
+// Same operator and outputs as apply_operator, without any device allocation, on
+// stream s; reads the handle only.
+void apply_operator_noalloc(const Batch& b, int precision, const double* dev_p, double* dev_y, double* body_sums,
+                            cudaStream_t s) {
   if (b.B > NOALLOC_MAX_BODIES)
     throw Error{PF_EINVAL, "pf_apply_noalloc: the handle has " + std::to_string(b.B) +
                                " bodies; the allocation-free scratch holds at most " +
@@ -144,17 +149,16 @@ void apply_operator_noalloc(Batch& b, int precision, const double* dev_p, double
   m.Vtot = b.Vtot;
   const dim3 blk(TX, TY);
   if (precision == PF_FP64)
-    k_apply_logical<double><<<(unsigned)b.T, blk, 0, b.stream>>>(m, b.tile_var, b.tile_ij, dev_p, dev_y);
+    k_apply_logical<double><<<(unsigned)b.T, blk, 0, s>>>(m, b.tile_var, b.tile_ij, dev_p, dev_y);
   else
-    k_apply_logical<float><<<(unsigned)b.T, blk, 0, b.stream>>>(m, b.tile_var, b.tile_ij, dev_p, dev_y);
+    k_apply_logical<float><<<(unsigned)b.T, blk, 0, s>>>(m, b.tile_var, b.tile_ij, dev_p, dev_y);
   PF_CUDA(cudaGetLastError());
   if (b.B > 0) {
-    k_body_rows_logical<<<b.B, blk, 0, b.stream>>>(m, b.d_body_var, dev_y, sums);
+    k_body_rows_logical<<<b.B, blk, 0, s>>>(m, b.d_body_var, dev_y, sums);
     PF_CUDA(cudaGetLastError());
-    if (body_sums)
-      PF_CUDA(cudaMemcpyAsync(body_sums, sums, b.B * sizeof(double), cudaMemcpyDeviceToHost, b.stream));
+    if (body_sums) PF_CUDA(cudaMemcpyAsync(body_sums, sums, b.B * sizeof(double), cudaMemcpyDeviceToHost, s));
   }
-  PF_CUDA(cudaStreamSynchronize(b.stream));
+  PF_CUDA(cudaStreamSynchronize(s));
 }
 
 }  // namespace pfq4
@@ -164,15 +168,14 @@ using namespace pfq4;
 extern "C" pf_status pf_apply_noalloc(const pf_batch* h, int precision, const double* dev_p, double* dev_y,
                                       double* body_sums, void* stream) {
   try {
-    Batch* b = (Batch*)h;
+    const Batch* b = (const Batch*)h;
     if (!b) throw Error{PF_EINVAL, "NULL handle"};
     int dev = -1;
     PF_CUDA(cudaGetDevice(&dev));
     if (dev != b->device) throw Error{PF_EINVAL, "call made with another device current than the handle's"};
     if (!dev_p || !dev_y) throw Error{PF_EINVAL, "NULL vector"};
     if (precision != PF_FP64 && precision != PF_MIXED) throw Error{PF_EINVAL, "invalid precision"};
-    b->stream = (cudaStream_t)stream;
-    apply_operator_noalloc(*b, precision, dev_p, dev_y, body_sums);
+    apply_operator_noalloc(*b, precision, dev_p, dev_y, body_sums, (cudaStream_t)stream);
     return PF_OK;
   } catch (const Error& e) {
     set_last_error(e.msg);

@@ -14,7 +14,7 @@ def run(extra_env=None):
         env.pop(k, None)
     env.update(extra_env or {})
     return subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--config", "c1", "--steps", "2",
-                           "--warmup", "1"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=300)
+                           "--warmup", "1", "--cpu-units", "2e6", "--cpu-procs", "2"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=300)
 
 
 def test_reference_arm_prints_one_contract_line():
@@ -27,7 +27,7 @@ def test_reference_arm_prints_one_contract_line():
     assert d["unit"] == "DOF-iters/s" and d["higher_is_better"] is True
     assert d["value"] > 0 and d["steps"] == 2 and d["warmup"] == 1 and d["n_gpus"] == 1
     cb = d["cpu_baseline"]
-    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    assert cb["kind"] == "oracle" and cb["cores"] == 2 and cb["value"] == d["value"] and cb["sample"]
     e2e = d["e2e"]
     assert e2e["value"] == d["value"] and e2e["unit"] == d["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0

@@ -8,7 +8,7 @@ import torch
 
 from oracle import mesh as OM, post as OP
 from paper_2512_12232_gb300 import workloads as W
-from tests.gpu_util import oracle_solution, rel_l2
+from tests.gpu_util import oracle_solution, reduced_error, rel_l2, residual_error_bound
 
 pytestmark = pytest.mark.gpu
 
@@ -73,8 +73,8 @@ def test_mixed_batch_reaches_tolerance_and_matches(api):
         offs = g.node_offsets
     for v, c in enumerate(cases):
         assert res.info[v]["status"] == 0 and res.info[v]["rel_true_residual"] <= 1e-8
-        m, s, u, psi_ref = oracle_solution(c, 1.0)
-        assert rel_l2(psi_b[offs[v]:offs[v + 1]], psi_ref) <= 1e-4
+        # a relative true residual <= 1e-8 bounds the error by 1e-8 ||b|| / lambda_min(A)
+        assert reduced_error(c, psi_b[offs[v]:offs[v + 1]]) <= residual_error_bound(c, 1e-8), v
 
 
 def test_many_variant_batch(api):
@@ -115,6 +115,26 @@ def test_velocity_field_matches_oracle(api):
     np.testing.assert_allclose(ug[m.active], uo, rtol=0, atol=1e-8 * scale)
     np.testing.assert_allclose(vg[m.active], vo, rtol=0, atol=1e-8 * scale)
     assert np.all(ug[~m.active] == 0.0) and np.all(vg[~m.active] == 0.0)
+
+
+def test_velocity_field_of_later_variants_matches_oracle(api):
+    """The same field for variants after the first of a batch with uneven grids: covers the
+    variant's base offset, the row padding and the body-value offset into the solution."""
+    from oracle import potential as OPO
+    cases = [W.five_cylinder_case(0.25, 160, 80, 20), W.single_cylinder(),
+             W.five_cylinder_case(1.0, 200, 100, 30)]
+    with api.batch_build(cases, sweeps=20) as g:
+        api.psi_solve(g, U=1.0, tol=1e-13, precision=api.PF_FP64)
+        fields = [tuple(t.cpu().numpy() for t in api.velocity_field(g, v)) for v in (1, 2)]
+    for (ug, vg), c in zip(fields, cases[1:]):
+        c = W.Case(c.x0, c.x1, c.y0, c.y1, c.nx, c.ny, c.bodies, 20, c.bc)
+        m, s, u, psi_ref = oracle_solution(c, 1.0)
+        uo, vo = OPO.velocity_from_psi(m, psi_ref)
+        assert ug.shape == (c.ny, c.nx)
+        scale = max(np.abs(uo).max(), np.abs(vo).max())
+        np.testing.assert_allclose(ug[m.active], uo, rtol=0, atol=1e-8 * scale)
+        np.testing.assert_allclose(vg[m.active], vo, rtol=0, atol=1e-8 * scale)
+        assert np.all(ug[~m.active] == 0.0) and np.all(vg[~m.active] == 0.0)
 
 
 def test_solve_is_deterministic(api):
@@ -185,17 +205,59 @@ def test_schur_form_on_a_batch(api):
 def test_tuned_schedule_matches_untuned(api):
     """The autotuned path (pipeline depth trials, timed re-balance of the persistent
     schedule, kept for later solves on the handle) changes only the summation order: its
-    solutions match an untuned FP64 solve of the same batch within the solve tolerances,
-    on the tuning call and on a second call that reuses the tuning."""
+    solutions match the oracle's direct solutions within what the solve tolerance allows
+    (error <= tol ||b|| / lambda_min(A)), on the tuning call and on a second call that
+    reuses the tuning, and to 1e-10 in FP64 at 1e-13."""
     cases = W.parametric_sweep(4, seed=7, nx_choices=(768, 1024))   # >= 2 tiles per CTA: the re-balance runs
     with api.batch_build(cases) as g:
-        ref = api.psi_solve(g, U=1.0, tol=1e-13, precision=api.PF_FP64).psi.cpu().numpy()
+        offs = g.node_offsets
         for _ in range(2):
             r = api.psi_solve(g, U=1.0, tol=1e-8, precision=api.PF_MIXED, tune_schedule=True)
             assert r.status == 0
             assert all(i["status"] == 0 and i["rel_true_residual"] <= 1e-8 for i in r.info)
             assert g.timing()["cg_stages"] in (2, 3, 4)
-            assert rel_l2(r.psi.cpu().numpy(), ref) <= 1e-4
+            psi = r.psi.cpu().numpy()
+            for v, c in enumerate(cases):
+                assert reduced_error(c, psi[offs[v]:offs[v + 1]]) <= residual_error_bound(c, 1e-8), v
         r64 = api.psi_solve(g, U=1.0, tol=1e-13, precision=api.PF_FP64, tune_schedule=True)
         assert r64.status == 0
-        assert rel_l2(r64.psi.cpu().numpy(), ref) <= FP64_TOL
+        psi = r64.psi.cpu().numpy()
+        for v, c in enumerate(cases):
+            m, s, u, psi_ref = oracle_solution(c, 1.0)
+            assert rel_l2(psi[offs[v]:offs[v + 1]], psi_ref) <= FP64_TOL, v
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_paper_stopping_rule_matches_oracle_cg(api, prec):
+    """PF_TOL_PAPER_ABS (Appendix A, the algorithm's test on r_norm = sum r^2): the solve
+    stops once the sum of squares of the reduced residual is below tol.  In FP64 the inner
+    CG stops on its recurrence residual exactly as the algorithm does, so the iteration
+    count matches the oracle's element-by-element CG (plus the one launch that measures the
+    final residual), and both iterates are the same to the accuracy the test allows."""
+    from oracle import solve as OS
+    c = W.five_cylinder_case(0.5, 160, 80, 20)
+    m, s, u, psi_ref = oracle_solution(c, 1.0)
+    tol = 1e-16
+    x, psik, it, rn = OS.cg_paper(s, m.kind.ravel(), m.body.ravel(), tol=tol, criterion="paper")
+    assert rn <= tol
+    p = api.PF_FP64 if prec == "fp64" else api.PF_MIXED
+    with api.mesh_build(c.grid, c.bodies, c.sweeps, c.bc) as g:
+        res = api.psi_solve(g, U=1.0, tol=tol, precision=p, criterion="paper")
+    info = res.info[0]
+    bn2 = float(s.b @ s.b)
+    assert info["status"] == 0
+    assert info["rel_true_residual"] ** 2 * bn2 <= tol * (1 + 1e-9)
+    psi = res.psi.cpu().numpy()
+    if prec == "fp64":
+        assert abs(info["iters"] - (it + 1)) <= 2, (info["iters"], it)
+        assert rel_l2(psi, x) <= 1e-9
+        np.testing.assert_allclose(res.body_psi, psik, rtol=0, atol=1e-9)
+    # sum r^2 <= 1e-16 bounds the error against the direct solution as it does the oracle's
+    assert rel_l2(psi, psi_ref) <= 10 * max(rel_l2(x, psi_ref), 1e-12)
+
+
+def test_invalid_stopping_criterion_is_refused(api):
+    c = W.single_cylinder()
+    with api.mesh_build(c.grid, c.bodies, c.sweeps, c.bc) as g:
+        res = api.psi_solve(g, U=1.0, tol=1e-8, criterion=7, raise_on_failure=False)
+    assert res.status == 1
