@@ -175,6 +175,26 @@ pf_status pf_mesh_stats_get(const pf_batch* b, int variant, pf_mesh_stats* out);
 /* Final node coordinates of variant v: dev_xy[n][2] (x, y), logical order, FP64. */
 pf_status pf_mesh_coords(const pf_batch* b, int variant, double* dev_xy, void* stream);
 
+/* Replace the node coordinates of variant v with caller-given ones (dev_xy[n][2], logical
+   order, FP64), keeping the topology as built: node kinds, body membership, active cells
+   and boundary edges do not change.  The element matrices (section "Weak formulation"),
+   the cell and tile flags and min det J are recomputed from the new coordinates; a later
+   pf_psi_solve, pf_grad or pf_apply works on them.  This is the input side of a shape
+   optimisation over node coordinates (dJ/dX from pf_grad is the gradient at these
+   coordinates).  Returns PF_EMESH_INVALID (coordinates kept) if det J <= 0 at a Gauss point
+   of an active cell of any variant; the handle then refuses solves until valid coordinates
+   are set.  Earlier solutions on the handle are discarded. */
+pf_status pf_mesh_set_coords(pf_batch* b, int variant, const double* dev_xy, void* stream);
+
+/* Vector-Jacobian product of the mesh generator (section "Body-Conforming Grid
+   Generation"): given a cotangent dev_gX[n][2] on the final node coordinates of every
+   variant (device, logical order, variants concatenated), return in gc[total bodies][2]
+   (host) the cotangent on the body centres through the radial projection of the body
+   nodes and the S Jacobi smoothing sweeps (which are linear in the projection
+   displacement): gc = (dX/dc)^T gX at fixed topology.  pf_grad's dJdc is this product of
+   its dJ/dX plus the objective's own dependence on the centres. */
+pf_status pf_coords_vjp(pf_batch* b, const double* dev_gX, double* gc, void* stream);
+
 /* Node classification of variant v: dev_kind[n] = PF_NODE_*, dev_body[n] = body index
    (local to the variant) for BODY nodes, else -1.  Either pointer may be NULL. */
 pf_status pf_mesh_tags(const pf_batch* b, int variant, int8_t* dev_kind, int32_t* dev_body, void* stream);
@@ -255,6 +275,24 @@ pf_status pf_last_timing(const pf_batch* b, pf_timing* out);
    faults and the CUDA context stays usable.  The handle's iterate is then undefined:
    destroy it.  enable = 0 restores normal launches.  PF_EINVAL for a NULL handle. */
 pf_status pf_test_wait_timeout(pf_batch* b, int enable);
+
+/* Velocity potential phi of every variant (section "Governing Equation": u = grad phi,
+   nabla^2 phi = 0; the contour lines of phi and psi form the flow net).  The same Q4
+   operator and fused CG kernels as pf_psi_solve, with the constraints of phi: phi = U*x on
+   the inlet and outlet sides (x = x0, x = x1), no flux (the natural condition) on the
+   other two sides and on every body, and every node that is neither inactive nor on the
+   inlet / outlet an unknown (body nodes included: there is no multi-point constraint).
+   The boundary kinds given to pf_batch_build concern psi and are not used here.
+   dev_phi: optional device output [total nodes] (logical order, inactive nodes = 0).
+   info: optional host output [n_variants]; opts as pf_psi_solve (NULL: mixed, 1e-8).
+   Returns PF_OK if every variant reached tol, else the first failing variant's status. */
+pf_status pf_phi_solve(pf_batch* b, double U, const pf_solve_opts* opts, double* dev_phi, pf_solve_info* info,
+                       void* stream);
+
+/* Element velocity of the last pf_phi_solve, u = dphi/dx and v = dphi/dy at the centre of
+   every cell of variant v (same layout and rules as pf_velocity_field).  PF_EINVAL before a
+   phi solve. */
+pf_status pf_phi_velocity_field(pf_batch* b, int variant, double* dev_u, double* dev_v, void* stream);
 
 /* Element velocity field of variant v after a solve (section "Velocity Field and Surface
    Tangential Velocity", u = dpsi/dy, v = -dpsi/dx; the velocity-magnitude field of the

@@ -58,6 +58,37 @@ def jacobi_matrix(mesh: Mesh):
                          shape=(N, N))
 
 
+def centre_chain(mesh: Mesh, sweeps: int, gX):
+    """Cotangent on the body centres of a cotangent gX (N, 2) on the final node
+    coordinates, through the mesh generator X = X_grid + M^S d0(c): S transposed Jacobi
+    sweeps, then the radial projection's Jacobian at every body node's background
+    position.  The topology is held fixed."""
+    M = jacobi_matrix(mesh)
+    MT = M.T.tocsr()
+    gd = np.asarray(gX, dtype=np.float64).reshape(-1, 2).copy()
+    for _ in range(sweeps):
+        gd = MT @ gd
+    out = np.zeros((len(mesh.bodies), 2))
+    kind = mesh.kind.ravel()
+    body = mesh.body.ravel()
+    xg = mesh.xg.ravel()
+    yg = mesh.yg.ravel()
+    for k, (cx, cy, r) in enumerate(mesh.bodies):
+        nodes = np.flatnonzero((kind == BODY) & (body == k))
+        ex = xg[nodes] - cx
+        ey = yg[nodes] - cy
+        rho = np.sqrt(ex * ex + ey * ey)
+        ux, uy = ex / rho, ey / rho
+        s = r / rho
+        # Jp = I - s (I - u u^T), symmetric
+        j00 = 1.0 - s * (1.0 - ux * ux)
+        j01 = s * ux * uy
+        j11 = 1.0 - s * (1.0 - uy * uy)
+        out[k, 0] = np.sum(j00 * gd[nodes, 0] + j01 * gd[nodes, 1])
+        out[k, 1] = np.sum(j01 * gd[nodes, 0] + j11 * gd[nodes, 1])
+    return out
+
+
 def gradient(mesh: Mesh, sweeps: int, U: float, lo: int, hi: int, obj=OBJ_COPFI, system=None):
     """Returns (J, dJ/dX (N,2), dJ/dc (n_bodies,2), psi)."""
     if system is None:
@@ -86,30 +117,7 @@ def gradient(mesh: Mesh, sweeps: int, U: float, lo: int, hi: int, obj=OBJ_COPFI,
     KL = full_operator_apply(system, Lam)
     dmask = mesh.kind.ravel() == DIRICHLET
     dJdX[dmask, 1] -= U * KL[dmask]
-    # chain to the centres: transpose smoothing, then the projection Jacobian
-    M = jacobi_matrix(mesh)
-    MT = M.T.tocsr()
-    gd = dJdX.copy()
-    for _ in range(sweeps):
-        gd = MT @ gd
-    dJdc = np.zeros((len(bodies), 2))
-    kind = mesh.kind.ravel()
-    body = mesh.body.ravel()
-    xg = mesh.xg.ravel()
-    yg = mesh.yg.ravel()
-    for k, (cx, cy, r) in enumerate(bodies):
-        nodes = np.flatnonzero((kind == BODY) & (body == k))
-        ex = xg[nodes] - cx
-        ey = yg[nodes] - cy
-        rho = np.sqrt(ex * ex + ey * ey)
-        ux, uy = ex / rho, ey / rho
-        s = r / rho
-        # Jp = I - s (I - u u^T), symmetric
-        j00 = 1.0 - s * (1.0 - ux * ux)
-        j01 = s * ux * uy
-        j11 = 1.0 - s * (1.0 - uy * uy)
-        dJdc[k, 0] = np.sum(j00 * gd[nodes, 0] + j01 * gd[nodes, 1])
-        dJdc[k, 1] = np.sum(j01 * gd[nodes, 0] + j11 * gd[nodes, 1])
+    dJdc = centre_chain(mesh, sweeps, dJdX)
     if obj == OBJ_COPFI:
         dJdc[hi, 1] += -J / dy
         dJdc[lo, 1] += J / dy

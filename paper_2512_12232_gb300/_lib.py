@@ -64,10 +64,14 @@ _SIGS = {
     "pf_mesh_stats_get": (C.c_int, [P, C.c_int, C.POINTER(pf_mesh_stats)]),
     "pf_mesh_coords": (C.c_int, [P, C.c_int, P, P]),
     "pf_mesh_tags": (C.c_int, [P, C.c_int, P, P, P]),
+    "pf_mesh_set_coords": (C.c_int, [P, C.c_int, P, P]),
+    "pf_coords_vjp": (C.c_int, [P, P, P, P]),
     "pf_apply": (C.c_int, [P, C.c_int, P, P, P, P]),
     "pf_apply_noalloc": (C.c_int, [P, C.c_int, P, P, P, P]),
     "pf_psi_solve": (C.c_int, [P, C.c_double, C.POINTER(pf_solve_opts), P, P, P, P]),
     "pf_psi_solve_schur": (C.c_int, [P, C.c_double, C.POINTER(pf_solve_opts), P, P, P, P]),
+    "pf_phi_solve": (C.c_int, [P, C.c_double, C.POINTER(pf_solve_opts), P, P, P]),
+    "pf_phi_velocity_field": (C.c_int, [P, C.c_int, P, P, P]),
     "pf_test_wait_timeout": (C.c_int, [P, C.c_int]),
     "pf_apply_timing": (C.c_int, [P, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), P]),
     "pf_last_timing": (C.c_int, [P, C.POINTER(pf_timing)]),

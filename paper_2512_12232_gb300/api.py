@@ -163,6 +163,25 @@ class Mesh:
         check(L.load().pf_mesh_coords(self.handle, v, _ptr(out), _stream()))
         return out
 
+    def set_coords(self, xy, v=0):
+        """Replace variant v's node coordinates ((nodes, 2) float64), topology fixed; returns
+        the status (PF_OK, or PF_EMESH_INVALID if a cell folds)."""
+        xy = torch.as_tensor(xy).to(device="cuda", dtype=torch.float64).contiguous()
+        if tuple(xy.shape) != (self.n_nodes[v], 2):
+            raise ValueError(f"coordinates must have shape ({self.n_nodes[v]}, 2)")
+        return check(L.load().pf_mesh_set_coords(self.handle, v, _ptr(xy), _stream()), allow=(L.PF_EMESH_INVALID,))
+
+    def coords_vjp(self, gX):
+        """(dX/dc)^T gX: cotangent on the body centres ((bodies, 2) numpy) of a cotangent gX on
+        every variant's node coordinates ((total nodes, 2) tensor)."""
+        gX = torch.as_tensor(gX).to(device="cuda", dtype=torch.float64).contiguous()
+        if tuple(gX.shape) != (int(self.node_offsets[-1]), 2):
+            raise ValueError("cotangent must have shape (total nodes, 2)")
+        nb = self.body_offsets[-1]
+        gc = (C.c_double * max(1, 2 * nb))()
+        check(L.load().pf_coords_vjp(self.handle, _ptr(gX), gc, _stream()))
+        return np.array(gc[:2 * nb]).reshape(nb, 2)
+
     def tags(self, v=0):
         kind = torch.empty(self.n_nodes[v], dtype=torch.int8, device="cuda")
         body = torch.empty(self.n_nodes[v], dtype=torch.int32, device="cuda")
@@ -252,6 +271,29 @@ def velocity_field(mesh: Mesh, v=0):
     u = torch.empty((ny, nx), dtype=torch.float64, device="cuda")
     w = torch.empty((ny, nx), dtype=torch.float64, device="cuda")
     check(L.load().pf_velocity_field(mesh.handle, v, _ptr(u), _ptr(w), _stream()))
+    return u, w
+
+
+def phi_solve(mesh: Mesh, U=1.0, tol=1e-8, precision=PF_MIXED, k_max=10_000_000, inner_tol=2e-7, chunk=0,
+              raise_on_failure=True, tune_schedule=False, criterion="relative"):
+    """Velocity potential: phi = U x on the inlet and outlet sides, no flux on the walls and
+    bodies.  Returns (phi (total nodes,) float64 tensor, per-variant info dicts, status)."""
+    opts = _opts(tol, k_max, precision, inner_tol, chunk, False, tune_schedule, criterion)
+    phi = torch.empty(int(mesh.node_offsets[-1]), dtype=torch.float64, device="cuda")
+    info = (L.pf_solve_info * mesh.n_variants)()
+    code = L.load().pf_phi_solve(mesh.handle, float(U), C.byref(opts), _ptr(phi), info, _stream())
+    if raise_on_failure:
+        check(code)
+    return phi, [{k: getattr(i, k) for k, _ in L.pf_solve_info._fields_} for i in info], code
+
+
+def phi_velocity_field(mesh: Mesh, v=0):
+    """(u, v) = grad phi at the centre of every cell of variant v after a phi solve, as
+    (ny, nx) tensors (0 on inactive cells)."""
+    nx, ny = mesh.grids[v][4], mesh.grids[v][5]
+    u = torch.empty((ny, nx), dtype=torch.float64, device="cuda")
+    w = torch.empty((ny, nx), dtype=torch.float64, device="cuda")
+    check(L.load().pf_phi_velocity_field(mesh.handle, v, _ptr(u), _ptr(w), _stream()))
     return u, w
 
 

@@ -143,6 +143,8 @@ struct Batch {
   double* gradT = nullptr;           // [2][Vtot] ping-pong partner of gradX
   double* cellG = nullptr;           // [8][Vtot] per-cell shape derivatives
   void** d_vecs = nullptr;           // device list of the vectors k_init clears
+  bool dirichlet_x = false;          // Dirichlet data U x (the velocity potential) instead of U y
+  Batch* phi = nullptr;              // velocity-potential view of this mesh (made on first use)
   bool solved = false;
   double lastU = 0.0;
   int last_precision = -1;
@@ -179,14 +181,17 @@ void set_last_error(const std::string& msg);
 void build_batch(Batch& b, const pf_grid* grids, const int* body_offsets, const pf_body* bodies,
                  int nv, int sweeps, const int bc[4]);
 void export_coords(Batch& b, int v, double* dev_xy);
+void set_coords(Batch& b, int v, const double* dev_xy);
+void tile_flags(Batch& b);
 void export_tags(Batch& b, int v, int8_t* kind, int32_t* body);
 
 // solver.cu
 void make_schedule(Batch& b);
-void velocity_field(Batch& b, int v, double* dev_u, double* dev_v);
+void velocity_field(Batch& b, int v, double* dev_u, double* dev_v, int potential = 0);
 void ensure_solver_memory(Batch& b, int precision);
 void apply_timing(Batch& b, int precision, int reps, double* us, double* bytes);
 void apply_operator(Batch& b, int precision, const double* dev_p, double* dev_y, double* body_sums);
+void refresh_apply_groups(Batch& b);
 pf_status psi_solve(Batch& b, double U, const pf_solve_opts& o, double* dev_psi, double* body_psi,
                     pf_solve_info* info);
 pf_status solve_core(Batch& b, double U, const pf_solve_opts& o, double* dev_psi, double* body_psi,
@@ -202,8 +207,14 @@ pf_status schur_solve(Batch& b, double U, const pf_solve_opts& o, double* dev_ps
 // post.cu
 int surface_velocity(Batch& b, int v, int body, double* theta, double* ut, int cap);
 
+// phi.cu
+pf_status phi_solve(Batch& b, double U, const pf_solve_opts& o, double* dev_phi, pf_solve_info* info);
+void phi_velocity_field(Batch& b, int v, double* dev_u, double* dev_v);
+void destroy_phi_view(Batch& b);
+
 // grad.cu
 pf_status shape_gradient(Batch& b, int obj, int lo, int hi, double U, double tol, double* dev_dJdX,
                          double* dJdc, double* J);
+void coords_vjp(Batch& b, const double* dev_gX, double* gc);
 
 }  // namespace pfq4

@@ -157,6 +157,7 @@ pf_status pf_mesh_build(const pf_grid* grid, const pf_body* bodies, int n_bodies
 void pf_batch_destroy(pf_batch* h) {
   Batch* b = (Batch*)h;
   if (!b) return;
+  destroy_phi_view(*b);
   for (int k = 0; k < 2; ++k)
     if (b->graph[k]) cudaGraphExecDestroy(b->graph[k]);
   for (int k = 0; k < Batch::N_EV; ++k)
@@ -198,6 +199,27 @@ pf_status pf_mesh_coords(const pf_batch* h, int variant, double* dev_xy, void* s
     if (!dev_xy) throw Error{PF_EINVAL, "dev_xy is NULL"};
     export_coords(*b, variant, dev_xy);
     PF_CUDA(cudaStreamSynchronize(b->stream));
+    return PF_OK;
+  });
+}
+
+pf_status pf_mesh_set_coords(pf_batch* h, int variant, const double* dev_xy, void* stream) {
+  return guarded([&]() -> pf_status {
+    Batch* b = (Batch*)h;
+    bind(b, stream);
+    check_variant(b, variant);
+    if (!dev_xy) throw Error{PF_EINVAL, "dev_xy is NULL"};
+    set_coords(*b, variant, dev_xy);
+    return b->valid ? PF_OK : PF_EMESH_INVALID;
+  });
+}
+
+pf_status pf_coords_vjp(pf_batch* h, const double* dev_gX, double* gc, void* stream) {
+  return guarded([&]() -> pf_status {
+    Batch* b = (Batch*)h;
+    bind(b, stream);
+    if (!dev_gX || (!gc && b->B > 0)) throw Error{PF_EINVAL, "NULL argument"};
+    coords_vjp(*b, dev_gX, gc);
     return PF_OK;
   });
 }
@@ -252,6 +274,31 @@ pf_status pf_psi_solve_schur(pf_batch* h, double U, const pf_solve_opts* opts, d
     o.inner_tol = PF_DEFAULT_INNER_TOL;
     if (opts) o = *opts;
     return schur_solve(*b, U, o, dev_psi, body_psi, info);
+  });
+}
+
+pf_status pf_phi_solve(pf_batch* h, double U, const pf_solve_opts* opts, double* dev_phi, pf_solve_info* info,
+                       void* stream) {
+  return guarded([&]() -> pf_status {
+    Batch* b = (Batch*)h;
+    bind(b, stream);
+    pf_solve_opts o{};
+    o.tol = 1e-8;
+    o.k_max = 10000000;
+    o.precision = PF_MIXED;
+    o.inner_tol = PF_DEFAULT_INNER_TOL;
+    if (opts) o = *opts;
+    return phi_solve(*b, U, o, dev_phi, info);
+  });
+}
+
+pf_status pf_phi_velocity_field(pf_batch* h, int variant, double* dev_u, double* dev_v, void* stream) {
+  return guarded([&]() -> pf_status {
+    Batch* b = (Batch*)h;
+    bind(b, stream);
+    check_variant(b, variant);
+    phi_velocity_field(*b, variant, dev_u, dev_v);
+    return PF_OK;
   });
 }
 

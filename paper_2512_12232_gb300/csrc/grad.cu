@@ -242,7 +242,68 @@ __global__ void k_export_grad(const DevVariant* var, const long long* lbase, lon
   }
 }
 
+// Inverse of k_export_grad: a logical [nodes][2] cotangent into the padded planes.
+__global__ void k_import_grad(const DevVariant* var, const long long* lbase, long long Vtot, const double* in,
+                              double* g) {
+  const int v = blockIdx.y;
+  const DevVariant& V = var[v];
+  const long long N = (long long)(V.nx + 1) * (V.ny + 1);
+  for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < N; m += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(m % (V.nx + 1)), j = (int)(m / (V.nx + 1));
+    const long long n = V.base + (long long)j * V.P + i;
+    g[n] = in[2 * (lbase[v] + m)];
+    g[Vtot + n] = in[2 * (lbase[v] + m) + 1];
+  }
+}
+
 }  // namespace
+
+static void ensure_grad_memory(Batch& b) {
+  if (b.psi_save) return;
+  const long long Vt = b.Vtot;
+  const int B = std::max(1, b.B);
+  b.psi_save = (double*)dev_alloc(b, Vt * sizeof(double));
+  b.sol_save = (double*)dev_alloc(b, B * sizeof(double));
+  b.d_rhsb = (double*)dev_alloc(b, B * sizeof(double));
+  b.gradX = (double*)dev_alloc(b, 2 * Vt * sizeof(double));
+  b.gradT = (double*)dev_alloc(b, 2 * Vt * sizeof(double));
+  b.cellG = (double*)dev_alloc(b, 8 * Vt * sizeof(double));
+}
+
+// Centre cotangent of the coordinate cotangent held in b.gradX (padded planes, consumed):
+// the S transposed smoothing sweeps, then the projection Jacobian summed over each body's
+// nodes.  Host output [B][2].
+static void centre_chain(Batch& b, double* gc) {
+  cudaStream_t s = b.stream;
+  const long long Vt = b.Vtot;
+  const dim3 blk(TX, TY);
+  double* a = b.gradX;
+  double* c = b.gradT;
+  PF_CUDA(cudaMemsetAsync(c, 0, 2 * Vt * sizeof(double), s));
+  for (int k = 0; k < b.sweeps; ++k) {
+    k_jacobi_T<<<(unsigned)b.T, blk, 0, s>>>(b.d_var, b.tile_var, b.tile_ij, b.tag, b.bid, b.d_bbox,
+                                             b.sweeps - 1 - k, Vt, a, c);
+    std::swap(a, c);
+  }
+  PF_CUDA(cudaGetLastError());
+  double* out = b.cellG;   // reuse as a [B][2] result buffer
+  if (b.B > 0) {
+    k_centre_grad<<<b.B, blk, 0, s>>>(b.d_var, b.d_body_var, b.d_bodies, b.body_ptr, b.body_nodes, Vt, a, out);
+    PF_CUDA(cudaGetLastError());
+    PF_CUDA(cudaMemcpyAsync(gc, out, 2 * b.B * sizeof(double), cudaMemcpyDeviceToHost, s));
+  }
+  PF_CUDA(cudaStreamSynchronize(s));
+  b.launches += b.sweeps + (b.B > 0 ? 1 : 0);
+}
+
+void coords_vjp(Batch& b, const double* dev_gX, double* gc) {
+  ensure_grad_memory(b);
+  PF_CUDA(cudaMemsetAsync(b.gradX, 0, 2 * b.Vtot * sizeof(double), b.stream));
+  k_import_grad<<<dim3(256, b.nv), 256, 0, b.stream>>>(b.d_var, lbase_cached(b), b.Vtot, dev_gX, b.gradX);
+  PF_CUDA(cudaGetLastError());
+  b.launches += 1;
+  centre_chain(b, gc);
+}
 
 pf_status shape_gradient(Batch& b, int obj, int lo, int hi, double U, double tol, double* dev_dJdX, double* dJdc,
                          double* J) {
@@ -271,14 +332,7 @@ pf_status shape_gradient(Batch& b, int obj, int lo, int hi, double U, double tol
     rhs[g0 + hi] += w[v];
     rhs[g0 + lo] -= w[v];
   }
-  if (!b.psi_save) {
-    b.psi_save = (double*)dev_alloc(b, Vt * sizeof(double));
-    b.sol_save = (double*)dev_alloc(b, B * sizeof(double));
-    b.d_rhsb = (double*)dev_alloc(b, B * sizeof(double));
-    b.gradX = (double*)dev_alloc(b, 2 * Vt * sizeof(double));
-    b.gradT = (double*)dev_alloc(b, 2 * Vt * sizeof(double));
-    b.cellG = (double*)dev_alloc(b, 8 * Vt * sizeof(double));
-  }
+  ensure_grad_memory(b);
   PF_CUDA(cudaMemcpyAsync(b.psi_save, b.x64, Vt * sizeof(double), cudaMemcpyDeviceToDevice, s));
   PF_CUDA(cudaMemcpyAsync(b.sol_save, b.sol64, B * sizeof(double), cudaMemcpyDeviceToDevice, s));
   PF_CUDA(cudaMemcpyAsync(b.d_rhsb, rhs.data(), B * sizeof(double), cudaMemcpyHostToDevice, s));
@@ -311,22 +365,7 @@ pf_status shape_gradient(Batch& b, int obj, int lo, int hi, double U, double tol
     PF_CUDA(cudaGetLastError());
   }
   if (dJdc) {
-    double* a = b.gradX;
-    double* c = b.gradT;
-    PF_CUDA(cudaMemsetAsync(c, 0, 2 * Vt * sizeof(double), s));
-    for (int k = 0; k < b.sweeps; ++k) {
-      k_jacobi_T<<<(unsigned)b.T, blk, 0, s>>>(b.d_var, b.tile_var, b.tile_ij, b.tag, b.bid, b.d_bbox,
-                                               b.sweeps - 1 - k, Vt, a, c);
-      std::swap(a, c);
-    }
-    PF_CUDA(cudaGetLastError());
-    double* out = b.cellG;   // reuse as a [B][2] result buffer
-    if (b.B > 0) {
-      k_centre_grad<<<b.B, blk, 0, s>>>(b.d_var, b.d_body_var, b.d_bodies, b.body_ptr, b.body_nodes, Vt, a, out);
-      PF_CUDA(cudaGetLastError());
-      PF_CUDA(cudaMemcpyAsync(dJdc, out, 2 * b.B * sizeof(double), cudaMemcpyDeviceToHost, s));
-    }
-    PF_CUDA(cudaStreamSynchronize(s));
+    centre_chain(b, dJdc);
     if (obj == PF_OBJ_COPFI) {
       for (int v = 0; v < b.nv; ++v) {
         const int g0 = b.hv[v].body0;
@@ -340,7 +379,7 @@ pf_status shape_gradient(Batch& b, int obj, int lo, int hi, double U, double tol
   PF_CUDA(cudaMemcpyAsync(b.sol64, b.sol_save, B * sizeof(double), cudaMemcpyDeviceToDevice, s));
   PF_CUDA(cudaStreamSynchronize(s));
   b.lastU = U;
-  b.launches += 2 + (dev_dJdX ? 1 : 0) + (dJdc ? b.sweeps + 1 : 0);
+  b.launches += 2 + (dev_dJdX ? 1 : 0);
   if (J)
     for (int v = 0; v < b.nv; ++v) J[v] = Jv[v];
   return st;

@@ -449,6 +449,24 @@ __global__ void k_body_edges(const DevVariant* var, const int* body_var, const i
   if (pass == 0 && linear_tid() == 0) count[gb] = run;
 }
 
+// Caller-given node coordinates of variant v (logical order, [n][2]): X and the
+// DISPLACED flag (set where the node is off its background-grid position); the cell
+// flags of stored coefficients are cleared for k_stiffness to set again.
+__global__ void k_set_coords(const DevVariant* var, int v, const double* xy, uint8_t* tag, double* X, long long Vtot) {
+  const DevVariant& V = var[v];
+  const long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long N = (long long)(V.nx + 1) * (V.ny + 1);
+  if (m >= N) return;
+  const int i = (int)(m % (V.nx + 1)), j = (int)(m / (V.nx + 1));
+  const long long n = V.base + (long long)j * V.P + i;
+  const double x = xy[2 * m], y = xy[2 * m + 1];
+  X[n] = x;
+  X[Vtot + n] = y;
+  uint8_t t = tag[n] & (uint8_t)~(DISPLACED | CELL_GENERAL | CELL_GEN32);
+  if (x != grid_x(V, i) || y != grid_y(V, j)) t |= DISPLACED;
+  tag[n] = t;
+}
+
 // export kernels: padded -> logical order
 __global__ void k_export_coords(const DevVariant* var, int v, const double* X, long long Vtot,
                                 double* xy) {
@@ -715,6 +733,55 @@ void build_batch(Batch& b, const pf_grid* grids, const int* body_offsets, const 
   dev_free(b, cnt);
   b.launches += 8 + (sweeps + JK - 1) / JK + (b.B > 0 ? 4 : 0);
   make_schedule(b);
+}
+
+// Per-tile flags and operator-row counts of every fused-CG tile from the handle's tags.
+void tile_flags(Batch& b) {
+  k_tile_general<<<(unsigned)b.Tcg, dim3(TX, TY), 0, b.stream>>>(b.d_var, b.tile_cg_var, b.tile_cg_ij, b.tag,
+                                                                b.tile_cg_gen, b.tile_cg_act);
+  PF_CUDA(cudaGetLastError());
+}
+
+// Replace variant v's node coordinates (topology held fixed: node kinds, body membership
+// and active cells stay as built) and recompute what depends on them: the element
+// matrices of cells with a displaced corner, the cell and tile flags, the per-variant
+// counts and min det J.
+void set_coords(Batch& b, int v, const double* dev_xy) {
+  HostVariant& H = b.hv[v];
+  const long long N = (long long)(H.g.nx + 1) * (H.g.ny + 1);
+  cudaStream_t s = b.stream;
+  const long long Vt = b.Vtot;
+  k_set_coords<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(b.d_var, v, dev_xy, b.tag, b.X, Vt);
+  PF_CUDA(cudaMemsetAsync(b.d_stats_i + 6 * v, 0, 6 * sizeof(long long), s));
+  const double big = 1e300;
+  PF_CUDA(cudaMemcpyAsync(b.d_detmin + v, &big, sizeof(double), cudaMemcpyHostToDevice, s));
+  const dim3 blk(TX, TY);
+  const unsigned nt = (unsigned)((long long)H.tiles_x * H.tiles_y);
+  k_stiffness<<<nt, blk, 0, s>>>(b.d_var, b.tile_var + H.tile0, b.tile_ij + H.tile0, b.tag, b.X, Vt, b.K64, b.K32,
+                                 b.K32i, b.d_stats_i, b.d_detmin);
+  // the variant's fused-CG tiles follow those of the variants before it
+  long long t0 = 0;
+  for (int u = 0; u < v; ++u)
+    t0 += (long long)((b.hv[u].g.nx + 1 + CTX - 1) / CTX) * ((b.hv[u].g.ny + 1 + CTY - 1) / CTY);
+  const unsigned ntc = (unsigned)((long long)((H.g.nx + 1 + CTX - 1) / CTX) * ((H.g.ny + 1 + CTY - 1) / CTY));
+  k_tile_general<<<ntc, blk, 0, s>>>(b.d_var, b.tile_cg_var + t0, b.tile_cg_ij + t0, b.tag, b.tile_cg_gen + t0,
+                                     b.tile_cg_act + t0);
+  PF_CUDA(cudaGetLastError());
+  long long st[6];
+  double dmin = 0.0;
+  PF_CUDA(cudaMemcpyAsync(st, b.d_stats_i + 6 * v, sizeof(st), cudaMemcpyDeviceToHost, s));
+  PF_CUDA(cudaMemcpyAsync(&dmin, b.d_detmin + v, sizeof(double), cudaMemcpyDeviceToHost, s));
+  PF_CUDA(cudaStreamSynchronize(s));
+  H.stats.n_general_cells = st[4];
+  H.n_gen32_cells = st[5];
+  H.stats.min_detJ = dmin;
+  b.valid = true;
+  for (const HostVariant& G : b.hv)
+    if (!(G.stats.min_detJ > 0.0)) b.valid = false;
+  b.launches += 3;
+  refresh_apply_groups(b);   // the stand-alone operator's plain-tile bits follow the tile flags
+  destroy_phi_view(b);       // its tile flags were made from the old coordinates
+  b.solved = false;          // any earlier solution belongs to the old coordinates
 }
 
 void export_coords(Batch& b, int v, double* dev_xy) {

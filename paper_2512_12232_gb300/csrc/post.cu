@@ -50,8 +50,10 @@ __global__ void k_surface_velocity(const DevVariant* var, int v, int gb, const p
 // dN_a/deta = eta_a / 4, through the isoparametric Jacobian.  One thread per logical cell
 // (i, j), i < nx, j < ny, written at j*nx + i; inactive cells get 0.  Corners of an active
 // cell are never inactive; BODY corners carry their body's value.
+// potential = 1: the field is the velocity potential, u = dphi/dx and v = dphi/dy.
 __global__ void k_velocity_field(const DevVariant* var, int v, const uint8_t* tag, const int* bid, const double* X,
-                                 long long Vtot, const double* x64, const double* xb, double* u_out, double* v_out) {
+                                 long long Vtot, const double* x64, const double* xb, int potential, double* u_out,
+                                 double* v_out) {
   const DevVariant& V = var[v];
   const long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (m >= (long long)V.nx * V.ny) return;
@@ -80,19 +82,19 @@ __global__ void k_velocity_field(const DevVariant* var, int v, const uint8_t* ta
     fx += (j11 * dxi[c] - j01 * deta[c]) / det * f[c];
     fy += (-j10 * dxi[c] + j00 * deta[c]) / det * f[c];
   }
-  u_out[m] = fy;
-  v_out[m] = -fx;
+  u_out[m] = potential ? fx : fy;
+  v_out[m] = potential ? fy : -fx;
 }
 
 }  // namespace
 
-void velocity_field(Batch& b, int v, double* dev_u, double* dev_v) {
+void velocity_field(Batch& b, int v, double* dev_u, double* dev_v, int potential) {
   if (!b.solved) throw Error{PF_EINVAL, "no solution on this handle yet"};
   if (!dev_u || !dev_v) throw Error{PF_EINVAL, "NULL output"};
   const long long ncell = (long long)b.hv[v].g.nx * b.hv[v].g.ny;
   if (ncell == 0) return;
   k_velocity_field<<<(unsigned)((ncell + 255) / 256), 256, 0, b.stream>>>(b.d_var, v, b.tag, b.bid, b.X, b.Vtot,
-                                                                          b.x64, b.sol64, dev_u, dev_v);
+                                                                          b.x64, b.sol64, potential, dev_u, dev_v);
   PF_CUDA(cudaGetLastError());
   b.launches += 1;
   PF_CUDA(cudaStreamSynchronize(b.stream));

@@ -959,9 +959,10 @@ __global__ void k_seed_slots(const long long* body_nodes, int n_slots, State4<T>
 }
 
 // ---------------------------------------------------------------- init / export
+// Dirichlet data g = U * gcoord (gcoord: the y plane of the coordinates for psi = U y, the x
+// plane for phi = U x), the warm-start or zero initial guess elsewhere.
 __global__ void k_init(const DevVariant* var, const int* tile_var, const int2* tile_ij, const uint8_t* tag,
-                       const double* X, long long Vtot, double U0, const double* Uv, int warm, double* x64,
-                       double* w64) {
+                       const double* gcoord, double U0, const double* Uv, int warm, double* x64, double* w64) {
   const long long t = blockIdx.x;
   const int v = tile_var[t];
   const double U = Uv ? Uv[v] : U0;
@@ -972,7 +973,7 @@ __global__ void k_init(const DevVariant* var, const int* tile_var, const int2* t
   const long long n = V.base + (long long)j * V.P + i;
   const int kind = (i <= V.nx) ? (tag[n] & KIND_MASK) : K_INACT;
   double u = 0.0;
-  if (kind == K_DIR) u = __dmul_rn(U, X[Vtot + n]);
+  if (kind == K_DIR) u = __dmul_rn(U, gcoord[n]);
   else if (kind == K_FREE && warm) u = x64[n];
   x64[n] = u;
   w64[n] = 0.0;
@@ -1518,32 +1519,7 @@ static void ensure_apply_buffers(Batch& b) {
     b.ap_ticket = (unsigned long long*)dev_alloc(b, sizeof(unsigned long long));
     PF_CUDA(cudaMemsetAsync(b.ap_ticket, 0, sizeof(unsigned long long), b.stream));
     b.ap_ticket_base = 0;
-    // work items: up to AG consecutive tiles of one variant and tile row
-    const long long T = b.Tcg;
-    std::vector<int2> ij(T);
-    std::vector<int> var(T);
-    std::vector<uint8_t> fl(T);
-    PF_CUDA(cudaMemcpy(ij.data(), b.tile_cg_ij, T * sizeof(int2), cudaMemcpyDeviceToHost));
-    PF_CUDA(cudaMemcpy(var.data(), b.tile_cg_var, T * sizeof(int), cudaMemcpyDeviceToHost));
-    PF_CUDA(cudaMemcpy(fl.data(), b.tile_cg_gen, T, cudaMemcpyDeviceToHost));
-    std::vector<int4> gr;
-    for (long long t = 0; t < T;) {
-      int g = 1;
-      while (g < AG && t + g < T && var[t + g] == var[t] && ij[t + g].y == ij[t].y) ++g;
-      int pl32 = 0, pl64 = 0;
-      for (int k = 0; k < g; ++k) {
-        pl32 |= ((fl[t + k] & TILE_PLAIN32) != 0) << k;
-        pl64 |= ((fl[t + k] & TILE_PLAIN64) != 0) << k;
-      }
-      if (ij[t].x >= (1 << 20)) throw Error{PF_EINVAL, "grid too wide for the operator kernel (nx >= 2^20)"};
-      const HostVariant& H = b.hv[var[t]];
-      const int row0 = (int)(H.base / H.P);
-      gr.push_back(make_int4(ij[t].x | (g << 20) | (pl32 << 24) | (pl64 << 28), ij[t].y, var[t], row0 + ij[t].y));
-      t += g;
-    }
-    b.ap_ngroups = (long long)gr.size();
-    b.ap_groups = (int4*)dev_alloc(b, std::max<size_t>(1, gr.size()) * sizeof(int4));
-    PF_CUDA(cudaMemcpy(b.ap_groups, gr.data(), gr.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    refresh_apply_groups(b);
     using L64 = ApSmem<double, ApStages<double>::ns>;
     using L32 = ApSmem<float, ApStages<float>::ns>;
     encode_2d(&b.ap_maps[0].s[0], b.ap64[0], CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 8, b.P, b.Rtot, L64::AW, L64::H);
@@ -1551,6 +1527,43 @@ static void ensure_apply_buffers(Batch& b) {
     encode_2d(&b.ap_maps[1].s[0], b.ap32[0], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, b.P, b.Rtot, L32::AW, L32::H);
     encode_2d(&b.ap_maps[1].tag, b.tag, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, b.P, b.Rtot, L32::TBW, L32::H);
   }
+}
+
+// Work items of the operator kernel: up to AG consecutive tiles of one variant and tile
+// row, with each tile's plain bits (written in place once the buffers exist; the tile
+// flags change when node coordinates are replaced).
+void refresh_apply_groups(Batch& b) {
+  if (!b.ap64[0]) return;                 // made with the operator buffers on first use
+  const long long T = b.Tcg;
+  std::vector<int2> ij(T);
+  std::vector<int> var(T);
+  std::vector<uint8_t> fl(T);
+  PF_CUDA(cudaMemcpyAsync(ij.data(), b.tile_cg_ij, T * sizeof(int2), cudaMemcpyDeviceToHost, b.stream));
+  PF_CUDA(cudaMemcpyAsync(var.data(), b.tile_cg_var, T * sizeof(int), cudaMemcpyDeviceToHost, b.stream));
+  PF_CUDA(cudaMemcpyAsync(fl.data(), b.tile_cg_gen, T, cudaMemcpyDeviceToHost, b.stream));
+  PF_CUDA(cudaStreamSynchronize(b.stream));
+  std::vector<int4> gr;
+  for (long long t = 0; t < T;) {
+    int g = 1;
+    while (g < AG && t + g < T && var[t + g] == var[t] && ij[t + g].y == ij[t].y) ++g;
+    int pl32 = 0, pl64 = 0;
+    for (int k = 0; k < g; ++k) {
+      pl32 |= ((fl[t + k] & TILE_PLAIN32) != 0) << k;
+      pl64 |= ((fl[t + k] & TILE_PLAIN64) != 0) << k;
+    }
+    if (ij[t].x >= (1 << 20)) throw Error{PF_EINVAL, "grid too wide for the operator kernel (nx >= 2^20)"};
+    const HostVariant& H = b.hv[var[t]];
+    const int row0 = (int)(H.base / H.P);
+    gr.push_back(make_int4(ij[t].x | (g << 20) | (pl32 << 24) | (pl64 << 28), ij[t].y, var[t], row0 + ij[t].y));
+    t += g;
+  }
+  if (!b.ap_groups) {
+    b.ap_ngroups = (long long)gr.size();
+    b.ap_groups = (int4*)dev_alloc(b, std::max<size_t>(1, gr.size()) * sizeof(int4));
+  }
+  // pageable source: the call returns once the data is staged
+  PF_CUDA(cudaMemcpyAsync(b.ap_groups, gr.data(), gr.size() * sizeof(int4), cudaMemcpyHostToDevice, b.stream));
+  PF_CUDA(cudaStreamSynchronize(b.stream));
 }
 
 // y = A p with p in the first scratch buffer of T's precision (persistent grid: SMs x
@@ -1823,7 +1836,8 @@ pf_status solve_core(Batch& b, double U, const pf_solve_opts& o, double* dev_psi
     if (prec == PF_FP64) k_seed_slots<double><<<g, 256, 0, s>>>(b.body_nodes, n_slots, b.st64[0], b.st64[1]);
     else k_seed_slots<float><<<g, 256, 0, s>>>(b.body_nodes, n_slots, b.st32[0], b.st32[1]);
   }
-  k_init<<<(unsigned)b.T, dim3(TX, TY), 0, s>>>(b.d_var, b.tile_var, b.tile_ij, b.tag, b.X, b.Vtot, U,
+  k_init<<<(unsigned)b.T, dim3(TX, TY), 0, s>>>(b.d_var, b.tile_var, b.tile_ij, b.tag,
+                                                b.X + (b.dirichlet_x ? 0 : b.Vtot), U,
                                                 b.Uv_active ? b.d_Uv : nullptr, warm, b.x64, b.w64);
   PF_CUDA(cudaGetLastError());
   PF_CUDA(cudaEventRecord(b.ev[3], s));

@@ -51,6 +51,8 @@ def test_error_path_without_gpu(lib_path):
     assert lib.pf_batch_grad(None, 0, 3, 4, 1.0, 1e-12, None, None, None, None) == _lib.PF_EINVAL
     lib.pf_mesh_destroy(None)  # a NULL handle is a no-op, as for pf_batch_destroy
     assert lib.pf_velocity_field(None, 0, None, None, None) == _lib.PF_EINVAL
+    assert lib.pf_mesh_set_coords(None, 0, None, None) == _lib.PF_EINVAL
+    assert lib.pf_coords_vjp(None, None, None, None) == _lib.PF_EINVAL
 
 
 def test_product_path_fails_loudly_without_library(tmp_path):

@@ -115,3 +115,100 @@ def test_batch_entry_points_agree_with_solve_and_grad(api):
     api.mesh_destroy(g)
     with pytest.raises(RuntimeError, match="closed"):
         g.handle
+
+
+def _smooth_perturbation(m, amp):
+    """A smooth displacement field that vanishes on the outer ring and on body nodes."""
+    x, y = m.x, m.y
+    Lx, Ly = x.max() - x.min(), y.max() - y.min()
+    s = np.sin(np.pi * (x - x.min()) / Lx) * np.sin(np.pi * (y - y.min()) / Ly)
+    keep = (m.kind == OM.FREE).astype(np.float64)
+    return amp * s * np.cos(3.0 * y) * keep, amp * s * np.sin(2.0 * x) * keep
+
+
+def test_set_coords_solves_and_differentiates_at_the_given_coordinates(api):
+    """pf_mesh_set_coords: the solve and dJ/dX on caller-given node coordinates (a smooth
+    perturbation of the generated mesh) match the oracle assembled on the same coordinates;
+    setting the generated coordinates back reproduces the original solve bit for bit."""
+    m = OM.build_mesh(CASE.grid, CASE.bodies, CASE.sweeps, CASE.bc)
+    h = (CASE.x1 - CASE.x0) / CASE.nx
+    px, py = _smooth_perturbation(m, 0.2 * h)
+    m.x, m.y = m.x + px, m.y + py
+    J_ref, dX_ref, dc_ref, psi_ref = OG.gradient(m, CASE.sweeps, 1.0, 3, 4, 0)
+    xy_new = torch.from_numpy(np.stack([m.x.ravel(), m.y.ravel()], axis=1))
+    with api.mesh_build(CASE.grid, CASE.bodies, CASE.sweeps, CASE.bc) as g:
+        xy0 = g.coords()
+        r0 = api.psi_solve(g, U=1.0, tol=1e-13, precision=api.PF_FP64).psi.cpu().numpy()
+        assert g.set_coords(xy_new) == 0
+        assert g.stats()["n_general_cells"] > 0
+        np.testing.assert_array_equal(g.coords().cpu().numpy(), xy_new.numpy())
+        r1 = api.psi_solve(g, U=1.0, tol=1e-13, precision=api.PF_FP64)
+        psi1 = r1.psi.cpu().numpy()
+        dX, dc, J = api.grad(g, 0, 3, 4, 1.0, 1e-13)
+        assert g.set_coords(xy0) == 0
+        r2 = api.psi_solve(g, U=1.0, tol=1e-13, precision=api.PF_FP64).psi.cpu().numpy()
+    assert np.linalg.norm(psi1 - psi_ref) <= 1e-10 * np.linalg.norm(psi_ref)
+    assert abs(J[0] - J_ref) <= 1e-10 * max(1.0, abs(J_ref))
+    dX = dX.cpu().numpy()
+    assert np.abs(dX - dX_ref).max() <= 1e-8 * np.abs(dX_ref).max()
+    np.testing.assert_array_equal(r2, r0)
+
+
+def test_set_coords_refuses_a_folded_cell(api):
+    m = OM.build_mesh(CASE.grid, CASE.bodies, CASE.sweeps, CASE.bc)
+    with api.mesh_build(CASE.grid, CASE.bodies, CASE.sweeps, CASE.bc) as g:
+        xy = g.coords().clone()
+        k = (m.ny // 2) * (m.nx + 1) + 5          # a free node far from the bodies
+        xy[k, 0] += 3.0 * (CASE.x1 - CASE.x0) / CASE.nx
+        assert g.set_coords(xy) == 2              # PF_EMESH_INVALID
+        res = api.psi_solve(g, U=1.0, tol=1e-10, raise_on_failure=False)
+        assert res.status == 2
+
+
+def test_coords_vjp_matches_oracle_chain(api):
+    """pf_coords_vjp against the oracle's transpose of the mesh generator (transposed
+    smoothing sweeps and the projection Jacobian) on a random cotangent, on a batch."""
+    cases = [CASE, W.five_cylinder_case(0.4, 128, 64, 12)]
+    rng = np.random.default_rng(11)
+    with api.batch_build(cases, sweeps=20) as g:
+        gX = rng.standard_normal((int(g.node_offsets[-1]), 2))
+        gc = g.coords_vjp(torch.from_numpy(gX))
+        offs = g.node_offsets
+    for v, c in enumerate(cases):
+        m = OM.build_mesh(c.grid, c.bodies, 20, c.bc)
+        ref = OG.centre_chain(m, 20, gX[offs[v]:offs[v + 1]])
+        np.testing.assert_allclose(gc[5 * v:5 * v + 5], ref, rtol=0, atol=1e-11 * np.abs(ref).max())
+
+
+def test_autograd_through_node_coordinates(api):
+    """X = mesh_coords(c), J = objective_at_coords(X, c): dJ/dX equals pf_grad's (and the
+    oracle's), dJ/dc equals the one-step objective(c) and the oracle's total gradient, and a
+    central difference of J along a random direction in X agrees with dJ/dX."""
+    from paper_2512_12232_gb300 import autograd as AG
+    c = torch.tensor(CASE.bodies[:, :2], dtype=torch.float64, requires_grad=True)
+    X = AG.mesh_coords(c, CASE.bodies[:, 2], CASE.grid, CASE.sweeps)
+    X.retain_grad()
+    J = AG.objective_at_coords(X, c, CASE.bodies[:, 2], CASE.grid, CASE.sweeps, tol=1e-13)
+    J.backward()
+    m = OM.build_mesh(CASE.grid, CASE.bodies, CASE.sweeps, CASE.bc)
+    J_ref, dX_ref, dc_ref, _ = OG.gradient(m, CASE.sweeps, 1.0, 3, 4, 0)
+    assert abs(J.item() - J_ref) <= 1e-9
+    gX = X.grad.cpu().numpy()
+    assert np.abs(gX - dX_ref).max() <= 1e-8 * np.abs(dX_ref).max()
+    np.testing.assert_allclose(c.grad.numpy(), dc_ref, rtol=0, atol=1e-7 * np.abs(dc_ref).max())
+    c2 = torch.tensor(CASE.bodies[:, :2], dtype=torch.float64, requires_grad=True)
+    AG.copfi(c2, CASE.bodies[:, 2], CASE.grid, CASE.sweeps, tol=1e-13).backward()
+    np.testing.assert_allclose(c.grad.numpy(), c2.grad.numpy(), rtol=0, atol=1e-9 * np.abs(dc_ref).max())
+    # directional derivative along a smooth field in X-space
+    px, py = _smooth_perturbation(m, 1.0)
+    d = torch.from_numpy(np.stack([px.ravel(), py.ravel()], axis=1)).cuda()
+    eps = 1e-6
+    Js = []
+    with api.mesh_build(CASE.grid, CASE.bodies, CASE.sweeps, CASE.bc) as g:
+        for sgn in (1.0, -1.0):
+            assert g.set_coords(X.detach() + sgn * eps * d) == 0
+            api.psi_solve(g, U=1.0, tol=1e-13, precision=api.PF_FP64)
+            Js.append(api.copfi(g, 0, 3, 4, 1.0)[0])
+    fd = (Js[0] - Js[1]) / (2 * eps)
+    an = float((X.grad * d).sum())
+    assert abs(fd - an) <= 1e-5 * abs(an) + 1e-7, (fd, an)
