@@ -8,7 +8,10 @@
 //
 // Two tilings of every variant (variant-major lists, row-major inside a variant):
 // 32 x 8 nodes (mesh build and the FP64 refinement kernels, one 256-thread CTA pass
-// per tile) and 64 x 16 nodes (the fused CG step and the stand-alone operator).  The
+// per tile) and 64 x 16 nodes (the fused CG step, the smoothing sweeps and the
+// stand-alone operator).  Row-major order keeps the 256-byte L2 lines a tile's boxes
+// touch beyond its own columns in use by the next tile (a column-major walk measured
+// 3-4% slower fused CG launches).  The
 // fused CG step runs a persistent grid: CTA b owns a contiguous range of the 64 x 16
 // list, cut into "segments" at variant boundaries.  The refinement kernels run one
 // grid row per variant, each CTA a fixed share of the variant's tiles.  Either way

@@ -289,6 +289,14 @@ struct CgSmem {
   static constexpr int tx_tag = TBW * (CTY + 2);
   static constexpr int tx_base = SB * (int)sizeof(T) + tx_tag;
   static constexpr int tx_k = kTmaK ? 6 * KB * (int)sizeof(T) : 0;
+  // edge tiles: a tile whose last grid row is at most THIN - 2 rows below its first loads
+  // boxes of THIN rows only (state and tags rows j0-1 .. j0+2, coefficient cell rows
+  // j0-1 .. j0+2); a tile whose grid ends within its first state box loads that box alone
+  static constexpr int THIN = 4;
+  __host__ __device__ static constexpr int tx_sbox(bool thin) { return (thin ? THIN : CTY + 2) * 4 * SHALF * (int)sizeof(T); }
+  __host__ __device__ static constexpr int tx_tbox(bool thin) { return TBW * (thin ? THIN : CTY + 2); }
+  __host__ __device__ static constexpr int tx_kbox(bool thin) { return kTmaK ? (thin ? THIN : CTY + 1) * 6 * KHALF * (int)sizeof(T) : 0; }
+  static_assert(2 * tx_sbox(false) == SB * (int)sizeof(T) && 2 * tx_kbox(false) == tx_k, "box byte counts");
   // after the NS stages: two p tiles with halo, two effective-tag tiles, barriers
   static constexpr int ptile_bytes = align((CTX + 2) * (CTY + 2) * (int)sizeof(T));
   static constexpr int ttile_bytes = align((CTX + 2) * (CTY + 2));
@@ -402,22 +410,31 @@ __device__ __forceinline__ T q4_row_nb(const T (&p)[3][3], uint8_t c0, uint8_t c
   return y;
 }
 
-// Issue the TMA loads of tile t into stage s (one thread).
+// Issue the TMA loads of tile t into stage s (one thread).  thin: the grid's last row is
+// at most two rows below the tile's first, so boxes of THIN rows hold every row the tile
+// reads; narrow: the grid's last column is at most 30 columns right of the tile's first,
+// so the first state box (nodes i0-1 .. i0+31) and the first coefficient box (cells
+// i0-4 .. i0+29) hold every node and cell the tile reads.  The consumers never read the
+// staged positions outside the grid, so the parts not loaded are never used.
 template <typename T>
 __device__ __forceinline__ void cg_issue(const CgMaps& mp, int cur, unsigned char* stage, uint64_t* bar,
-                                         int2 ij, int row0, long long Rtot, bool gen, bool plain) {
+                                         int2 ij, int row0, bool gen, bool plain, bool thin, bool narrow) {
   using L = CgSmem<T, 2>;   // stage layout does not depend on the stage count
   const int x0 = ij.x - 4, y0 = row0 + ij.y - 1;
-  mbar_arrive_expect_tx(bar, L::tx_base - (plain ? L::tx_tag : 0) + (gen ? L::tx_k : 0));
+  const int nbox = narrow ? 1 : 2;
+  mbar_arrive_expect_tx(bar, nbox * L::tx_sbox(thin) + (plain ? 0 : L::tx_tbox(thin)) +
+                                 (gen ? nbox * L::tx_kbox(thin) : 0));
   // state records viewed as a [rows][4 P] array: two boxes of SHALF nodes (long rows)
-  tma_load_2d(stage + L::off_s, &mp.s[cur], 4 * (ij.x - 1), y0, bar);
-  tma_load_2d(stage + L::off_s + L::sbox_bytes, &mp.s[cur], 4 * (ij.x - 1 + L::SHALF), y0, bar);
-  if (!plain) tma_load_2d(stage + L::off_t, &mp.tag, ij.x - 16, y0, bar);   // plain tiles need no tags
+  const CUtensorMap* sm = thin ? &mp.s_thin[cur] : &mp.s[cur];
+  tma_load_2d(stage + L::off_s, sm, 4 * (ij.x - 1), y0, bar);
+  if (!narrow) tma_load_2d(stage + L::off_s + L::sbox_bytes, sm, 4 * (ij.x - 1 + L::SHALF), y0, bar);
+  if (!plain) tma_load_2d(stage + L::off_t, thin ? &mp.tag_thin : &mp.tag, ij.x - 16, y0, bar);   // plain tiles need no tags
   if constexpr (L::kTmaK) {
     if (gen) {
       // interleaved coefficients as a [rows][6 P] array: two boxes of KHALF cells
-      tma_load_2d(stage + L::off_k, &mp.k, 6 * x0, y0, bar);
-      tma_load_2d(stage + L::off_k + L::kbox_bytes, &mp.k, 6 * (x0 + L::KHALF), y0, bar);
+      const CUtensorMap* km = thin ? &mp.k_thin : &mp.k;
+      tma_load_2d(stage + L::off_k, km, 6 * x0, y0, bar);
+      if (!narrow) tma_load_2d(stage + L::off_k + L::kbox_bytes, km, 6 * (x0 + L::KHALF), y0, bar);
     }
   }
 }
@@ -518,7 +535,8 @@ __global__ void __launch_bounds__(NTC, sizeof(T) == 4 ? 2 : 1) k_cg(CGArgs<T> a,
                      plain = (fl & (sizeof(T) == 4 ? TILE_PLAIN32 : TILE_PLAIN64)) != 0;
           s_tij[s] = tij;                         // published to the consumers by the arrive below
           s_tfl[s] = (gen ? 1 : 0) | (plain ? 2 : 0);
-          cg_issue<T>(mp, cur, smem + s * L::stage_bytes, &full[s], tij, row0, a.Rtot, gen, plain);
+          cg_issue<T>(mp, cur, smem + s * L::stage_bytes, &full[s], tij, row0, gen, plain, ny - tij.y <= 2,
+                      nx <= tij.x + 30);
           s_issued = q + 1;
         }
       }
@@ -1444,11 +1462,19 @@ static void make_cg_maps(Batch& b, CgMaps& mp, State4<T>* const st[2], T* K) {
   using L = CgSmem<T>;
   const CUtensorMapDataType dt = sizeof(T) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
   const int e = (int)sizeof(T);
-  for (int k = 0; k < 2; ++k)   // state records as a [rows][4 P] array, boxes of SHALF records
+  for (int k = 0; k < 2; ++k) {   // state records as a [rows][4 P] array, boxes of SHALF records
     encode_2d(&mp.s[k], st[k], dt, e, 4 * b.P, b.Rtot, 4 * L::SHALF, CTY + 2);
+    encode_2d(&mp.s_thin[k], st[k], dt, e, 4 * b.P, b.Rtot, 4 * L::SHALF, L::THIN);
+  }
   encode_2d(&mp.tag, b.tag, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, b.P, b.Rtot, L::TBW, CTY + 2);
-  if (sizeof(T) == 4) encode_2d(&mp.k, K, dt, e, 6 * b.P, b.Rtot, 6 * L::KHALF, CTY + 1);   // interleaved
-  else encode_2d(&mp.k, K, dt, e, b.P, 6 * b.Rtot, L::KBW, CTY + 1);
+  encode_2d(&mp.tag_thin, b.tag, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, b.P, b.Rtot, L::TBW, L::THIN);
+  if (sizeof(T) == 4) {   // interleaved
+    encode_2d(&mp.k, K, dt, e, 6 * b.P, b.Rtot, 6 * L::KHALF, CTY + 1);
+    encode_2d(&mp.k_thin, K, dt, e, 6 * b.P, b.Rtot, 6 * L::KHALF, L::THIN);
+  } else {
+    encode_2d(&mp.k, K, dt, e, b.P, 6 * b.Rtot, L::KBW, CTY + 1);
+    mp.k_thin = mp.k;   // the FP64 kernel reads its coefficients from the global planes
+  }
 }
 
 void ensure_solver_memory(Batch& b, int precision) {
@@ -1542,20 +1568,30 @@ void refresh_apply_groups(Batch& b) {
   PF_CUDA(cudaMemcpyAsync(var.data(), b.tile_cg_var, T * sizeof(int), cudaMemcpyDeviceToHost, b.stream));
   PF_CUDA(cudaMemcpyAsync(fl.data(), b.tile_cg_gen, T, cudaMemcpyDeviceToHost, b.stream));
   PF_CUDA(cudaStreamSynchronize(b.stream));
+  // groups run along tile rows: visit the tiles row-major within each variant (the list
+  // itself is column-major per variant)
+  std::vector<long long> ord(T);
+  for (long long t = 0; t < T; ++t) ord[t] = t;
+  std::stable_sort(ord.begin(), ord.end(), [&](long long a, long long c) {
+    if (var[a] != var[c]) return var[a] < var[c];
+    if (ij[a].y != ij[c].y) return ij[a].y < ij[c].y;
+    return ij[a].x < ij[c].x;
+  });
   std::vector<int4> gr;
-  for (long long t = 0; t < T;) {
+  for (long long q = 0; q < T;) {
+    const long long t = ord[q];
     int g = 1;
-    while (g < AG && t + g < T && var[t + g] == var[t] && ij[t + g].y == ij[t].y) ++g;
+    while (g < AG && q + g < T && var[ord[q + g]] == var[t] && ij[ord[q + g]].y == ij[t].y) ++g;
     int pl32 = 0, pl64 = 0;
     for (int k = 0; k < g; ++k) {
-      pl32 |= ((fl[t + k] & TILE_PLAIN32) != 0) << k;
-      pl64 |= ((fl[t + k] & TILE_PLAIN64) != 0) << k;
+      pl32 |= ((fl[ord[q + k]] & TILE_PLAIN32) != 0) << k;
+      pl64 |= ((fl[ord[q + k]] & TILE_PLAIN64) != 0) << k;
     }
     if (ij[t].x >= (1 << 20)) throw Error{PF_EINVAL, "grid too wide for the operator kernel (nx >= 2^20)"};
     const HostVariant& H = b.hv[var[t]];
     const int row0 = (int)(H.base / H.P);
     gr.push_back(make_int4(ij[t].x | (g << 20) | (pl32 << 24) | (pl64 << 28), ij[t].y, var[t], row0 + ij[t].y));
-    t += g;
+    q += g;
   }
   if (!b.ap_groups) {
     b.ap_ngroups = (long long)gr.size();

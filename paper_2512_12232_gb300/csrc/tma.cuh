@@ -12,6 +12,7 @@ constexpr int MBAR_POLL_LIMIT = 1 << 22;
 
 struct CgMaps {                 // TMA descriptors of the fused CG kernel (__grid_constant__ parameter)
   CUtensorMap s[2], tag, k;
+  CUtensorMap s_thin[2], tag_thin, k_thin;   // the same arrays with boxes of a few rows (edge tiles)
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
