@@ -79,6 +79,10 @@ def parse(argv=None):
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain-FP64 comparison block")
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-parity", action="store_true", help="skip the oracle parity block")
+    ap.add_argument("--precond", choices=["none", "mg"], default="none",
+                    help="preconditioner of the timed solves (none: the paper's CG)")
+    ap.add_argument("--no-mg", action="store_true", help="skip the multigrid-preconditioned comparison block")
+    ap.add_argument("--mg-steps", type=int, default=3)
     ap.add_argument("--apply-sweep", action="store_true", help="time only the stand-alone operator")
     ap.add_argument("--apply-reps", type=int, default=100)
     ap.add_argument("--config", choices=["c1", "c2", "c3", "c4", "c5"], default="c4")
@@ -473,12 +477,12 @@ def run_ours(args, rank, world, local):
             dist.destroy_process_group()
         return 0
 
-    def step(p=prec, host_out=None, keep=False):
+    def step(p=prec, host_out=None, keep=False, pre=args.precond):
         t_mesh = time.perf_counter()
         g = api.batch_build(cs)                  # returns after the device mesh is complete
         t_mesh = time.perf_counter() - t_mesh
         res = api.psi_solve(g, U=1.0, tol=args.tol, precision=p, inner_tol=args.inner_tol,
-                            tune_schedule=args.tune)
+                            tune_schedule=args.tune and pre == "none", preconditioner=pre)
         if args.config == "c5":
             api.grad(g, api.PF_OBJ_COPFI, 3, 4, 1.0, args.tol, want_dX=False)
         # CoPFI of the gap between the two stacked bodies (the single-cylinder case has none)
@@ -493,9 +497,9 @@ def run_ours(args, rank, world, local):
         g.close()
         return res, cps, tm, st
 
-    def timed(p, n_steps, n_warm, clocks_index=None):
+    def timed(p, n_steps, n_warm, clocks_index=None, pre=args.precond):
         for _ in range(n_warm):
-            step(p)
+            step(p, pre=pre)
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
@@ -510,7 +514,7 @@ def run_ours(args, rank, world, local):
             torch.cuda.synchronize()
             e0.record(stream)
             for _ in range(n_steps):
-                recs.append(step(p))
+                recs.append(step(p, pre=pre))
             e1.record(stream)
             torch.cuda.synchronize()
         finally:
@@ -585,6 +589,22 @@ def run_ours(args, rank, world, local):
                 "clocks": clk64,
                 "mixed_over_fp64_solves_per_s": (vals[2] / vals[1]) / (len(cs) * len(rec64) / el64)}
 
+    # the same workload with the multigrid-preconditioned CG (same tolerance, refinement and
+    # outputs), timed the same way: the time-to-solution lever beyond the paper's CG
+    mg = None
+    if args.precision == "mixed" and args.precond == "none" and not args.no_mg:
+        recm, elm, clkm = timed(prec, args.mg_steps, 1, local, pre="mg")
+        itm = [res.info[v]["iters"] for v in range(len(cs)) for res in [recm[-1][0]]]
+        mg = {"value": units_of(recm) / elm, "unit": UNIT, "steps": args.mg_steps,
+              "ms_per_step": 1e3 * elm / args.mg_steps, "solves_per_s": len(cs) * len(recm) / elm,
+              "all_converged": all(i["status"] == 0 and i["rel_true_residual"] <= args.tol
+                                   for res, _, _, _ in recm for i in res.info),
+              "iters_per_variant": itm if len(itm) <= 8 else {"min": min(itm), "max": max(itm)},
+              "breakdown_ms": {k: sum(tm[src] for _, _, tm, _ in recm) / len(recm)
+                               for k, src in (("mesh_build", "mesh_build_ms"), ("solve", "solve_ms"))},
+              "clocks": clkm,
+              "mg_over_cg_solves_per_s": (len(cs) * len(recm) / elm) / (vals[2] / vals[1])}
+
     # parity: the errors of this solve's outputs against the oracle on two variants
     parity = None
     if not args.no_parity and args.config != "c3":
@@ -630,6 +650,8 @@ def run_ours(args, rank, world, local):
                    "precision": "FP32 operator+vectors, FP64 dots/scalars/true residual/refinement"
                    if args.precision == "mixed" else "FP64",
                    "inner_tol": args.inner_tol, "parallelism": f"replicas x{world}",
+                   "preconditioner": "none (the paper's CG)" if args.precond == "none"
+                   else "geometric multigrid V(2,2) (PF_PRECOND_MG)",
                    "l2": "inputs larger than L2: each step builds fresh meshes (working set "
                          f"{int(nodes) * 48 / 1e6:.0f} MB of CG state and coefficients, L2 is 126 MB)"},
         "solves_per_s": vals[2] / vals[1], "all_converged": ok,
@@ -639,7 +661,7 @@ def run_ours(args, rank, world, local):
         "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": int(launches),
         "breakdown_ms": {**breakdown, "rest": 1e3 * vals[1] / args.steps - breakdown["mesh_build"] - breakdown["solve"]},
         **({"apply_sweep": apply_sweep} if apply_sweep else {}),
-        "plain_fp64": fp64, "parity": parity,
+        "plain_fp64": fp64, "mg_pcg": mg, "parity": parity,
         "e2e": ({"value": e2e[0] / e2e[1], "unit": UNIT, "h2d_bytes_per_step": e2e[2],
                  "d2h_bytes_per_step": e2e[3]} if e2e else None),
     }

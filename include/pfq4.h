@@ -103,6 +103,17 @@ enum { PF_TOL_REL_TRUE = 0,     /* ||b - A u||_2 / ||b||_2 <= tol, the FP64 true
                                    or at a quarter of it (PF_MIXED); the FP64 true residual then
                                    confirms sum r^2 <= tol or refines again */
 
+/* Preconditioners of a solve (pf_solve_opts.preconditioner; an extension beyond the paper,
+   whose Appendix A CG is unpreconditioned and needs a number of iterations that grows with the
+   grid).  PF_PRECOND_MG: each CG iteration applies one V(2,2)-cycle of geometric multigrid on
+   the logical node grid of every variant to the free unknowns (Galerkin coarse operators,
+   bilinear interpolation, constraints injected on coarse nodes, damped Jacobi smoothing) and
+   the inverse diagonal of the collapsed body row to each body unknown.  The preconditioner is
+   a fixed symmetric positive-definite operator, so the iterates converge to the same solution;
+   convergence is decided by the same FP64 true residual and refinement.  The hierarchy is
+   built on the first such solve of a handle (and again after pf_mesh_set_coords). */
+enum { PF_PRECOND_NONE = 0, PF_PRECOND_MG = 1 };
+
 typedef struct pf_solve_opts {
     double tol;            /* PF_TOL_REL_TRUE: stop when ||b - A u||_2 / ||b||_2 <= tol (true residual,
                               FP64); PF_TOL_PAPER_ABS: stop when sum r^2 <= tol */
@@ -119,6 +130,8 @@ typedef struct pf_solve_opts {
                               results agree with an untuned solve to rounding, not bit for bit.
                               0: schedule from the static per-tile cost estimate (deterministic). */
     int criterion;         /* PF_TOL_REL_TRUE (0) or PF_TOL_PAPER_ABS (1); any other value: PF_EINVAL */
+    int preconditioner;    /* PF_PRECOND_NONE (0): the paper's CG; PF_PRECOND_MG (1): CG preconditioned by a
+                              geometric multigrid V-cycle (PF_MIXED only); any other value: PF_EINVAL */
 } pf_solve_opts;
 
 typedef struct pf_solve_info {

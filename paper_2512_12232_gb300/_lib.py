@@ -11,6 +11,7 @@ STATUS_NAMES = {0: "PF_OK", 1: "PF_EINVAL", 2: "PF_EMESH_INVALID", 3: "PF_ENOT_C
                 4: "PF_EBREAKDOWN", 5: "PF_ETIMEOUT", 6: "PF_ECUDA", 7: "PF_ENOMEM"}
 PF_FP64, PF_MIXED = 0, 1
 PF_TOL_REL_TRUE, PF_TOL_PAPER_ABS = 0, 1
+PF_PRECOND_NONE, PF_PRECOND_MG = 0, 1
 PF_OBJ_COPFI, PF_OBJ_GAP_FLOW = 0, 1
 
 
@@ -34,7 +35,7 @@ class pf_mesh_stats(C.Structure):
 class pf_solve_opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("k_max", C.c_longlong), ("precision", C.c_int),
                 ("inner_tol", C.c_double), ("chunk", C.c_int), ("warm_start", C.c_int),
-                ("tune_schedule", C.c_int), ("criterion", C.c_int)]
+                ("tune_schedule", C.c_int), ("criterion", C.c_int), ("preconditioner", C.c_int)]
 
 
 class pf_solve_info(C.Structure):

@@ -226,20 +226,22 @@ def apply(mesh: Mesh, p: torch.Tensor, precision=PF_FP64):
     return y, np.array(sums[:nb])
 
 
-def _opts(tol, k_max, precision, inner_tol, chunk, warm_start, tune_schedule, criterion):
+def _opts(tol, k_max, precision, inner_tol, chunk, warm_start, tune_schedule, criterion, preconditioner="none"):
     crit = {"relative": PF_TOL_REL_TRUE, "paper": PF_TOL_PAPER_ABS}.get(criterion, criterion)
+    pre = {"none": L.PF_PRECOND_NONE, "mg": L.PF_PRECOND_MG}.get(preconditioner, preconditioner)
     return L.pf_solve_opts(float(tol), int(k_max), int(precision), float(inner_tol), int(chunk),
-                           int(bool(warm_start)), int(bool(tune_schedule)), int(crit))
+                           int(bool(warm_start)), int(bool(tune_schedule)), int(crit), int(pre))
 
 
 def psi_solve(mesh: Mesh, U=1.0, tol=1e-8, precision=PF_MIXED, k_max=10_000_000, inner_tol=2e-7,
               chunk=0, warm_start=False, want_psi=True, raise_on_failure=True, method="mpc",
-              tune_schedule=False, criterion="relative") -> SolveResult:
+              tune_schedule=False, criterion="relative", preconditioner="none") -> SolveResult:
     """Solve for psi.  method="mpc": CG on the multi-point-constraint system;
     method="schur": body values through the Schur complement (N_b + 1 fixed-body solves).
     criterion="relative": stop on the FP64 true residual ||b - A u|| / ||b|| <= tol;
-    criterion="paper": the Appendix A test, sum r^2 <= tol (PF_TOL_PAPER_ABS)."""
-    opts = _opts(tol, k_max, precision, inner_tol, chunk, warm_start, tune_schedule, criterion)
+    criterion="paper": the Appendix A test, sum r^2 <= tol (PF_TOL_PAPER_ABS).
+    preconditioner="mg": CG preconditioned by a multigrid V-cycle (PF_PRECOND_MG, mixed)."""
+    opts = _opts(tol, k_max, precision, inner_tol, chunk, warm_start, tune_schedule, criterion, preconditioner)
     total = int(mesh.node_offsets[-1])
     psi = torch.empty(total, dtype=torch.float64, device="cuda") if want_psi else None
     nb = mesh.body_offsets[-1]
@@ -275,10 +277,10 @@ def velocity_field(mesh: Mesh, v=0):
 
 
 def phi_solve(mesh: Mesh, U=1.0, tol=1e-8, precision=PF_MIXED, k_max=10_000_000, inner_tol=2e-7, chunk=0,
-              raise_on_failure=True, tune_schedule=False, criterion="relative"):
+              raise_on_failure=True, tune_schedule=False, criterion="relative", preconditioner="none"):
     """Velocity potential: phi = U x on the inlet and outlet sides, no flux on the walls and
     bodies.  Returns (phi (total nodes,) float64 tensor, per-variant info dicts, status)."""
-    opts = _opts(tol, k_max, precision, inner_tol, chunk, False, tune_schedule, criterion)
+    opts = _opts(tol, k_max, precision, inner_tol, chunk, False, tune_schedule, criterion, preconditioner)
     phi = torch.empty(int(mesh.node_offsets[-1]), dtype=torch.float64, device="cuda")
     info = (L.pf_solve_info * mesh.n_variants)()
     code = L.load().pf_phi_solve(mesh.handle, float(U), C.byref(opts), _ptr(phi), info, _stream())
@@ -325,9 +327,10 @@ def mesh_info(mesh: Mesh) -> dict:
 
 
 def batch_solve(mesh: Mesh, U=1.0, tol=1e-8, precision=PF_MIXED, k_max=10_000_000, inner_tol=2e-7, chunk=0,
-                warm_start=False, raise_on_failure=True, tune_schedule=False, criterion="relative") -> SolveResult:
+                warm_start=False, raise_on_failure=True, tune_schedule=False, criterion="relative",
+                preconditioner="none") -> SolveResult:
     """Solve every variant of the batch; body psi and per-variant info only (no nodal psi)."""
-    opts = _opts(tol, k_max, precision, inner_tol, chunk, warm_start, tune_schedule, criterion)
+    opts = _opts(tol, k_max, precision, inner_tol, chunk, warm_start, tune_schedule, criterion, preconditioner)
     nb = mesh.body_offsets[-1]
     bpsi = (C.c_double * max(1, nb))()
     info = (L.pf_solve_info * mesh.n_variants)()

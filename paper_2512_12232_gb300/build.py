@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libpfq4.so")
-SOURCES = ["mesh.cu", "solver.cu", "schur.cu", "post.cu", "grad.cu", "phi.cu", "capi.cu", "noalloc.cu"]
+SOURCES = ["mesh.cu", "solver.cu", "mg.cu", "schur.cu", "post.cu", "grad.cu", "phi.cu", "capi.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 

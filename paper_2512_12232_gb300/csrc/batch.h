@@ -43,6 +43,24 @@ struct CgConfig {                  // persistent grid + schedule of one fused-CG
   int tune_rounds = 0;               // timing-driven re-balances done
 };
 
+// One coarse level (l >= 1) of the geometric multigrid preconditioner, all variants packed:
+// variant v's level-l nodes (i, j) at off[v] + j (nx_l + 1) + i, each variant's block
+// starting on a multiple of 256 nodes (a 256-thread block never spans two variants).
+struct MgLevel {
+  long long n = 0;                   // nodes including the padding of every variant's block
+  long long nblk = 0;                // 256-node blocks
+  std::vector<long long> off;        // [nv] first node of the variant's block (-1: no such level)
+  std::vector<int2> dims;            // [nv] (nx_l, ny_l) cells
+  long long* d_off = nullptr;
+  int2* d_dims = nullptr;
+  int* d_blkvar = nullptr;           // [nblk] variant of each block
+  uint8_t* act = nullptr;            // coarse node carries an unknown
+  double* A64 = nullptr;             // [9][n] Galerkin stencil (setup precision)
+  float* A32 = nullptr;              // [9][n] the same in FP32 (the cycle)
+  float* dinv = nullptr;             // omega / diagonal at active nodes, else 0
+  float *r = nullptr, *za = nullptr, *zb = nullptr, *res = nullptr;
+};
+
 struct Batch;
 void* dev_alloc(Batch& b, size_t bytes);
 void dev_free(Batch& b, void* p);
@@ -143,6 +161,20 @@ struct Batch {
   double* gradT = nullptr;           // [2][Vtot] ping-pong partner of gradX
   double* cellG = nullptr;           // [8][Vtot] per-cell shape derivatives
   void** d_vecs = nullptr;           // device list of the vectors k_init clears
+  // multigrid-preconditioned CG (mg.cu): hierarchy made on the first such solve
+  bool pcg_active = false;           // the current solve runs the preconditioned CG
+  bool mg_ready = false;
+  int mg_L = 0;                      // levels of the deepest variant
+  std::vector<int> mg_Lv;            // [nv] levels per variant (>= 2)
+  int* d_mg_Lv = nullptr;
+  long long* d_tile0 = nullptr;      // [nv + 1] first 32x8 tile of each variant
+  std::vector<MgLevel> mg;           // [mg_L]; entry 0 unused (the fine level is the mesh itself)
+  float *mg_x = nullptr, *mg_r = nullptr, *mg_z = nullptr, *mg_t = nullptr, *mg_res = nullptr;
+  float *mg_p[2] = {nullptr, nullptr}, *mg_q = nullptr, *mg_dinv0 = nullptr;
+  double* mg_part = nullptr;         // [T] per-tile partial sums of one dot product
+  double* mg_Abb = nullptr;          // [B] diagonal of the collapsed body rows
+  cudaGraphExec_t graph_pcg = nullptr;
+  int graph_pcg_chunk = 0;
   bool dirichlet_x = false;          // Dirichlet data U x (the velocity potential) instead of U y
   Batch* phi = nullptr;              // velocity-potential view of this mesh (made on first use)
   bool solved = false;
@@ -199,6 +231,11 @@ pf_status solve_core(Batch& b, double U, const pf_solve_opts& o, double* dev_psi
 long long* lbase_cached(Batch& b);
 void export_psi(Batch& b, double* dev_psi);
 void body_values(Batch& b, std::vector<double>& C);
+
+// mg.cu
+void mg_setup(Batch& b);
+void launch_pcg_chunk(Batch& b, int iters, cudaStream_t s);
+void destroy_mg(Batch& b);
 
 // schur.cu
 pf_status schur_solve(Batch& b, double U, const pf_solve_opts& o, double* dev_psi, double* body_psi,

@@ -781,6 +781,7 @@ void set_coords(Batch& b, int v, const double* dev_xy) {
   b.launches += 3;
   refresh_apply_groups(b);   // the stand-alone operator's plain-tile bits follow the tile flags
   destroy_phi_view(b);       // its tile flags were made from the old coordinates
+  destroy_mg(b);             // and the multigrid operators from the old element matrices
   b.solved = false;          // any earlier solution belongs to the old coordinates
 }
 

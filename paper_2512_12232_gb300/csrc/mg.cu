@@ -1,0 +1,914 @@
+// Multigrid-preconditioned Conjugate Gradient for the stream-function system (an
+// extension beyond the paper, whose Appendix A CG is unpreconditioned; its iteration
+// count grows with the grid, about 2,100 iterations on a 1024x512 grid).
+//
+// Preconditioner M^-1 (symmetric positive definite, the same every iteration):
+//   * free unknowns: one V(2,2)-cycle of geometric multigrid on the logical node grid of
+//     each variant.  Level 0 is the mesh itself with its Q4 element matrices (the FP32
+//     operator of the CG); level l+1 has ceil(n_l / 2) cells per direction, coarse node I
+//     sitting on fine node min(2I, n_l).  Interpolation P is bilinear along the index
+//     lines (an odd fine node takes half of each coarse neighbour, the last node of an odd
+//     line copies its coarse node).  A coarse node carries an unknown only if the fine node
+//     under it does (constraints are injected), and P has no entries for constrained
+//     nodes.  Coarse operators are Galerkin products A_{l+1} = P^T A_l P (9-point
+//     stencils, formed once in FP64).  Smoother: damped Jacobi (omega = 0.85), two sweeps
+//     before and two after the coarse correction; the coarsest level (at most 17 x 17
+//     nodes) takes a fixed number of Jacobi sweeps from zero.  Jacobi with a fixed sweep
+//     count is a fixed symmetric operator, so the cycle is a valid CG preconditioner.
+//   * body unknowns (one per body, the multi-point constraint): the inverse diagonal of
+//     the collapsed body row, sum over the body's nodes n, m of A(n, m).
+//
+// The CG iteration itself is the paper's with the preconditioner inserted:
+//   x += alpha p, r -= alpha q; z = M^-1 r; beta = (r.z) / (r.z)_old; p = z + beta p;
+//   q = A p; alpha = (r.z) / (p.q),
+// one kernel per step over all variants of the batch, with per-variant scalars formed
+// by small finaliser kernels (one CTA per variant, partial sums added in a fixed order,
+// so repeated solves are bitwise identical).  The vectors are FP32 planes in the padded
+// node layout; the FP64 true residual and the iterative refinement are the kernels of
+// the unpreconditioned solve (k_fold, k_resid), which restart this CG from the FP64
+// residual until the outer tolerance is met.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "batch.h"
+
+namespace pfq4 {
+
+namespace {
+
+constexpr float MG_OMEGA = 0.85f;        // Jacobi damping (smoothing factor ~1/3 for Q4 Laplace stencils)
+constexpr int MG_CMAX = 16;              // coarsen while a level has more than this many cells per direction
+constexpr int MG_COARSE_SWEEPS = 300;    // Jacobi sweeps of the coarsest solve
+constexpr int MG_MAXC = 17 * 17;         // nodes of a coarsest level at most
+
+// ---------------------------------------------------------------- index rules
+// Weight of coarse index I in the interpolation of fine index i on a line of n cells.
+__device__ __forceinline__ double pw(int i, int n, int I) {
+  if ((i & 1) == 0) return I == (i >> 1) ? 1.0 : 0.0;
+  if (i == n) return I == ((i + 1) >> 1) ? 1.0 : 0.0;
+  return (I == ((i - 1) >> 1) || I == ((i + 1) >> 1)) ? 0.5 : 0.0;
+}
+// Coarse parents of fine index i: count, indices and weights.
+__device__ __forceinline__ int parents(int i, int n, int* I, double* w) {
+  if ((i & 1) == 0) { I[0] = i >> 1; w[0] = 1.0; return 1; }
+  if (i == n) { I[0] = (i + 1) >> 1; w[0] = 1.0; return 1; }
+  I[0] = (i - 1) >> 1; I[1] = (i + 1) >> 1; w[0] = w[1] = 0.5;
+  return 2;
+}
+__device__ __forceinline__ int fine_of(int I, int n) { return min(2 * I, n); }
+
+// Row of the fine (level-0) operator at node n = (i, j) as a 9-point stencil in FP64,
+// slot (dy + 1) * 3 + (dx + 1): off-diagonal entries summed over the active cells that
+// contain both nodes, the diagonal minus their sum (every element row sums to zero).
+__device__ void fine_stencil(const MeshDev& m, const DevVariant& V, long long n, int i, int j, double st[9]) {
+  for (int k = 0; k < 9; ++k) st[k] = 0.0;
+  const long long plane = m.Vtot;
+  const long long P = V.P;
+  auto coef = [&](long long c, int mm, bool gen) { return gen ? m.K64[mm * plane + c] : V.kr64[mm]; };
+  // cell (i, j): node is corner 0: K01 -> E, K02 -> NE, K03 -> N
+  if (i < V.nx && j < V.ny && (m.tag[n] & CELL_ACTIVE)) {
+    const bool g = m.tag[n] & CELL_GENERAL;
+    st[5] += coef(n, 0, g); st[8] += coef(n, 1, g); st[7] += coef(n, 2, g);
+  }
+  // cell (i-1, j): corner 1: K01 -> W, K12 -> N, K13 -> NW
+  if (i > 0 && j < V.ny && (m.tag[n - 1] & CELL_ACTIVE)) {
+    const long long c = n - 1;
+    const bool g = m.tag[c] & CELL_GENERAL;
+    st[3] += coef(c, 0, g); st[7] += coef(c, 3, g); st[6] += coef(c, 4, g);
+  }
+  // cell (i-1, j-1): corner 2: K02 -> SW, K12 -> S, K23 -> W
+  if (i > 0 && j > 0 && (m.tag[n - P - 1] & CELL_ACTIVE)) {
+    const long long c = n - P - 1;
+    const bool g = m.tag[c] & CELL_GENERAL;
+    st[0] += coef(c, 1, g); st[1] += coef(c, 3, g); st[3] += coef(c, 5, g);
+  }
+  // cell (i, j-1): corner 3: K03 -> S, K13 -> SE, K23 -> E
+  if (j > 0 && i < V.nx && (m.tag[n - P] & CELL_ACTIVE)) {
+    const long long c = n - P;
+    const bool g = m.tag[c] & CELL_GENERAL;
+    st[1] += coef(c, 2, g); st[2] += coef(c, 4, g); st[5] += coef(c, 5, g);
+  }
+  double s = 0.0;
+  for (int k = 0; k < 9; ++k)
+    if (k != 4) s += st[k];
+  st[4] = -s;
+}
+
+// Node of a packed coarse level handled by this thread: variant, (i, j) and the index,
+// or false for padding / variants without the level.
+struct LvNode {
+  int v, i, j, nx, ny;
+  long long k;
+};
+__device__ __forceinline__ bool lv_node(const long long* off, const int2* dims, const int* blkvar, LvNode& q) {
+  const int v = blkvar[blockIdx.x];
+  if (v < 0) return false;
+  const long long o = off[v];
+  if (o < 0) return false;
+  const int2 d = dims[v];
+  const long long loc = (long long)blockIdx.x * blockDim.x + threadIdx.x - o;
+  if (loc >= (long long)(d.x + 1) * (d.y + 1)) return false;
+  q.v = v;
+  q.nx = d.x;
+  q.ny = d.y;
+  q.i = (int)(loc % (d.x + 1));
+  q.j = (int)(loc / (d.x + 1));
+  q.k = o + loc;
+  return true;
+}
+
+struct LvArgs {              // one coarse level, device view
+  const long long* off;
+  const int2* dims;
+  const int* blkvar;
+  long long n;
+  const uint8_t* act;
+  const float* A;            // [9][n]
+  const float* dinv;
+  float *r, *za, *zb, *res;
+};
+
+// ---------------------------------------------------------------- setup kernels
+// Activity of level l+1 from level l (l = 0: FREE nodes of the mesh).
+__global__ void k_mg_act(LvArgs c, const uint8_t* act_f, const long long* off_f, const int2* dims_f,
+                         const DevVariant* var, const uint8_t* tag, uint8_t* act_c) {
+  LvNode q;
+  if (!lv_node(c.off, c.dims, c.blkvar, q)) return;
+  const int2 df = off_f ? dims_f[q.v] : make_int2(var[q.v].nx, var[q.v].ny);
+  const int fi = fine_of(q.i, df.x), fj = fine_of(q.j, df.y);
+  uint8_t a;
+  if (off_f) a = act_f[off_f[q.v] + (long long)fj * (df.x + 1) + fi];
+  else a = (tag[var[q.v].base + (long long)fj * var[q.v].P + fi] & KIND_MASK) == K_FREE;
+  act_c[q.k] = a;
+}
+
+// Galerkin stencil of coarse node I = sum_{a, b} P(a, I) A_f(a, b) P(b, J) over active
+// fine nodes a, b, in FP64, with its FP32 copy and the Jacobi factor.
+__global__ void k_mg_rap(LvArgs c, double* A64c, float* A32c, float* dinvc, MeshDev m, const uint8_t* act_f,
+                         const double* A64f, const long long* off_f, const int2* dims_f, long long nf) {
+  LvNode q;
+  if (!lv_node(c.off, c.dims, c.blkvar, q)) return;
+  double acc[9];
+  for (int k = 0; k < 9; ++k) acc[k] = 0.0;
+  const DevVariant& V = m.var[q.v];
+  const bool fine0 = off_f == nullptr;
+  const int2 df = fine0 ? make_int2(V.nx, V.ny) : dims_f[q.v];
+  const long long of = fine0 ? 0 : off_f[q.v];
+  auto fidx = [&](int i, int j) -> long long {
+    return fine0 ? V.base + (long long)j * V.P + i : of + (long long)j * (df.x + 1) + i;
+  };
+  auto factive = [&](int i, int j) -> bool {
+    const long long n = fidx(i, j);
+    return fine0 ? ((m.tag[n] & KIND_MASK) == K_FREE) : act_f[n] != 0;
+  };
+  if (c.act[q.k]) {
+    const int fx = fine_of(q.i, df.x), fy = fine_of(q.j, df.y);
+    for (int ay = fy - 1; ay <= fy + 1; ++ay) {
+      if (ay < 0 || ay > df.y) continue;
+      const double wy = pw(ay, df.y, q.j);
+      if (wy == 0.0) continue;
+      for (int ax = fx - 1; ax <= fx + 1; ++ax) {
+        if (ax < 0 || ax > df.x) continue;
+        const double wa = pw(ax, df.x, q.i) * wy;
+        if (wa == 0.0 || !factive(ax, ay)) continue;
+        double st[9];
+        const long long na = fidx(ax, ay);
+        if (fine0) fine_stencil(m, V, na, ax, ay, st);
+        else
+          for (int k = 0; k < 9; ++k) st[k] = A64f[k * nf + na];
+        for (int dy = -1; dy <= 1; ++dy)
+          for (int dx = -1; dx <= 1; ++dx) {
+            const double sv = st[(dy + 1) * 3 + dx + 1];
+            const int bx = ax + dx, by = ay + dy;
+            if (sv == 0.0 || bx < 0 || by < 0 || bx > df.x || by > df.y || !factive(bx, by)) continue;
+            int Ix[2], Iy[2];
+            double wx[2], wyb[2];
+            const int nxp = parents(bx, df.x, Ix, wx), nyp = parents(by, df.y, Iy, wyb);
+            for (int u = 0; u < nyp; ++u)
+              for (int t = 0; t < nxp; ++t) {
+                const int ddx = Ix[t] - q.i, ddy = Iy[u] - q.j;
+                if (ddx < -1 || ddx > 1 || ddy < -1 || ddy > 1) continue;
+                if (!c.act[q.k + (long long)ddy * (q.nx + 1) + ddx]) continue;
+                acc[(ddy + 1) * 3 + ddx + 1] += wa * sv * wx[t] * wyb[u];
+              }
+          }
+      }
+    }
+  }
+  for (int k = 0; k < 9; ++k) {
+    A64c[k * c.n + q.k] = acc[k];
+    A32c[k * c.n + q.k] = (float)acc[k];
+  }
+  dinvc[q.k] = (c.act[q.k] && acc[4] > 0.0) ? (float)(MG_OMEGA / acc[4]) : 0.0f;
+}
+
+// Jacobi factor of the fine level: omega / diagonal at FREE nodes.
+__global__ void k_mg_dinv0(MeshDev m, const int* tile_var, const int2* tile_ij, float* dinv0) {
+  const DevVariant& V = m.var[tile_var[blockIdx.x]];
+  const int2 ij = tile_ij[blockIdx.x];
+  const int i = ij.x + threadIdx.x, j = ij.y + threadIdx.y;
+  if (i > V.nx || j > V.ny) return;
+  const long long n = V.base + (long long)j * V.P + i;
+  float d = 0.0f;
+  if ((m.tag[n] & KIND_MASK) == K_FREE) {
+    double st[9];
+    fine_stencil(m, V, n, i, j, st);
+    d = st[4] > 0.0 ? (float)(MG_OMEGA / st[4]) : 0.0f;
+  }
+  dinv0[n] = d;
+}
+
+// Diagonal of each collapsed body row: sum over the body's nodes n of the stencil
+// entries A(n, m) towards nodes m of the same body (one CTA per body, fixed order).
+__global__ void __launch_bounds__(NT) k_mg_body_diag(MeshDev m, const int* body_var, double* Abb) {
+  __shared__ double scratch[NT / 32 + 1];
+  const int gb = blockIdx.x;
+  const DevVariant& V = m.var[body_var[gb]];
+  const int kb = gb - V.body0;
+  double s = 0.0;
+  for (int e = m.body_ptr[gb] + linear_tid(); e < m.body_ptr[gb + 1]; e += NT) {
+    const long long n = m.body_nodes[e];
+    const long long rem = n - V.base;
+    const int i = (int)(rem % V.P), j = (int)(rem / V.P);
+    double st[9];
+    fine_stencil(m, V, n, i, j, st);
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int bi = i + dx, bj = j + dy;
+        if (bi < 0 || bj < 0 || bi > V.nx || bj > V.ny) continue;
+        const long long nb = n + (long long)dy * V.P + dx;
+        if ((m.tag[nb] & KIND_MASK) == K_BODY && m.bid[nb] == kb) s += st[(dy + 1) * 3 + dx + 1];
+      }
+  }
+  s = block_sum(s, scratch);
+  if (linear_tid() == 0) Abb[gb] = s;
+}
+
+// ---------------------------------------------------------------- cycle kernels, fine level
+struct FineArgs {
+  MeshDev m;
+  const int* tile_var;
+  const int2* tile_ij;
+  const VarState* st;
+  const float* dinv0;
+  float *x, *r, *z, *t, *res, *q;
+  float* p[2];
+  const float* sb;           // [4][B] body CG values x, r, p, q
+  int B;
+  double* part;              // [T] partial sums of the kernel's dot product
+};
+
+// Tile of a FREE-only field (zero at every other node and outside the grid) with its
+// one-node halo, and the tags, in shared memory.
+__device__ __forceinline__ void load_free_tile(const DevVariant& V, int2 ij, const float* f, const uint8_t* tag,
+                                               float (*ps)[SW], uint8_t (*ts)[SW]) {
+  const int tid = linear_tid();
+  const int i = ij.x + threadIdx.x, j = ij.y + threadIdx.y;
+  const bool in = i <= V.nx && j <= V.ny;
+  const long long n = V.base + (long long)j * V.P + i;
+  const uint8_t tg = in ? tag[n] : K_INACT;
+  ps[threadIdx.y + 1][threadIdx.x + 1] = (tg & KIND_MASK) == K_FREE ? f[n] : 0.0f;
+  ts[threadIdx.y + 1][threadIdx.x + 1] = tg;
+  if (tid < NHALO) {
+    int li, lj;
+    halo_pos(tid, li, lj);
+    const int hi = ij.x - 1 + li, hj = ij.y - 1 + lj;
+    uint8_t ht = K_INACT;
+    float hv = 0.0f;
+    if (hi >= 0 && hj >= 0 && hi <= V.nx && hj <= V.ny) {
+      const long long hn = V.base + (long long)hj * V.P + hi;
+      ht = tag[hn];
+      if ((ht & KIND_MASK) == K_FREE) hv = f[hn];
+    }
+    ps[lj][li] = hv;
+    ts[lj][li] = ht;
+  }
+}
+
+// Block sum of one exact FP32 product per thread (TwoProd into a two-float, warp
+// reduction, FP64 across warps in a fixed order), written to part[blockIdx.x].
+__device__ __forceinline__ void block_dot(float x, float y, double* part, double* sh) {
+  Acc<float> acc;
+  acc.zero();
+  acc.add(0, x, y);
+  double w[4];
+  acc.warp_reduce(w);
+  const int tid = linear_tid(), lane = tid & 31, wp = tid >> 5;
+  if (lane == 0) sh[wp] = w[0];
+  __syncthreads();
+  if (tid == 0) {
+    double s = 0.0;
+    for (int k = 0; k < NT / 32; ++k) s += sh[k];
+    part[blockIdx.x] = s;
+  }
+}
+
+// x += alpha p, r -= alpha q, z = dinv r (the first pre-smoothing sweep from zero); r.r.
+__global__ void __launch_bounds__(NT) k_mg0_update(FineArgs a) {
+  __shared__ double sh[NT / 32];
+  const int v = a.tile_var[blockIdx.x];
+  const VarState& S = a.st[v];
+  if (S.phase != PH_CG) return;
+  const DevVariant& V = a.m.var[v];
+  const int2 ij = a.tile_ij[blockIdx.x];
+  const int i = ij.x + threadIdx.x, j = ij.y + threadIdx.y;
+  const float alpha = (float)S.alpha;
+  float rn = 0.0f;
+  if (i <= V.nx && j <= V.ny) {
+    const long long n = V.base + (long long)j * V.P + i;
+    if ((a.m.tag[n] & KIND_MASK) == K_FREE) {
+      const float pn = a.p[S.buf][n];
+      a.x[n] = a.x[n] + alpha * pn;
+      rn = a.r[n] - alpha * a.q[n];
+      a.r[n] = rn;
+      a.z[n] = a.dinv0[n] * rn;
+    }
+  }
+  block_dot(rn, rn, a.part, sh);
+}
+
+// One Jacobi sweep on the fine level: zo = zi + dinv (r - A zi) at FREE nodes.  mode 1
+// also returns res = r - A zi instead (no update); mode 2 adds the partial r.zo.
+template <int MODE>
+__global__ void __launch_bounds__(NT) k_mg0_sweep(FineArgs a, const float* zi, float* zo) {
+  __shared__ float ps[TY + 2][SW];
+  __shared__ uint8_t ts[TY + 2][SW];
+  __shared__ double sh[NT / 32];
+  const int v = a.tile_var[blockIdx.x];
+  if (a.st[v].phase != PH_CG) return;
+  const DevVariant& V = a.m.var[v];
+  const int2 ij = a.tile_ij[blockIdx.x];
+  load_free_tile(V, ij, zi, a.m.tag, ps, ts);
+  __syncthreads();
+  const int i = ij.x + threadIdx.x, j = ij.y + threadIdx.y;
+  float rz = 0.0f, zv = 0.0f;
+  if (i <= V.nx && j <= V.ny) {
+    const long long n = V.base + (long long)j * V.P + i;
+    if ((ts[threadIdx.y + 1][threadIdx.x + 1] & KIND_MASK) == K_FREE) {
+      const float y = q4_row<float>(ps, ts, threadIdx.x + 1, threadIdx.y + 1, n, V.P, a.m.K32, a.m.Vtot, V.kr32);
+      const float rr = a.r[n] - y;
+      if (MODE == 1) {
+        zo[n] = rr;
+      } else {
+        zv = ps[threadIdx.y + 1][threadIdx.x + 1] + a.dinv0[n] * rr;
+        zo[n] = zv;
+        rz = a.r[n];
+      }
+    }
+  }
+  if (MODE == 2) block_dot(rz, zv, a.part, sh);
+}
+
+// t += P e (prolongation from level 1, FREE nodes).
+__global__ void __launch_bounds__(NT) k_mg0_prolong(FineArgs a, LvArgs c, const int* Lv) {
+  const int v = a.tile_var[blockIdx.x];
+  if (a.st[v].phase != PH_CG) return;
+  const DevVariant& V = a.m.var[v];
+  const int2 ij = a.tile_ij[blockIdx.x];
+  const int i = ij.x + threadIdx.x, j = ij.y + threadIdx.y;
+  if (i > V.nx || j > V.ny) return;
+  const long long n = V.base + (long long)j * V.P + i;
+  if ((a.m.tag[n] & KIND_MASK) != K_FREE) return;
+  const int2 dc = c.dims[v];
+  const long long oc = c.off[v];
+  int Ix[2], Iy[2];
+  double wx[2], wy[2];
+  const int nxp = parents(i, V.nx, Ix, wx), nyp = parents(j, V.ny, Iy, wy);
+  double e = 0.0;
+  for (int u = 0; u < nyp; ++u)
+    for (int t = 0; t < nxp; ++t) {
+      const long long k = oc + (long long)Iy[u] * (dc.x + 1) + Ix[t];
+      if (c.act[k]) e += wx[t] * wy[u] * (double)c.zb[k];
+    }
+  a.t[n] = a.t[n] + (float)e;
+}
+
+// p = z + beta p at FREE nodes, the body's p at BODY nodes, 0 elsewhere (into the other
+// buffer); q = A p at FREE and BODY nodes; partial p.q over FREE nodes.
+__global__ void __launch_bounds__(NT) k_mg0_apply(FineArgs a) {
+  __shared__ float ps[TY + 2][SW];
+  __shared__ uint8_t ts[TY + 2][SW];
+  __shared__ double sh[NT / 32];
+  const int v = a.tile_var[blockIdx.x];
+  const VarState& S = a.st[v];
+  if (S.phase != PH_CG) return;
+  const DevVariant& V = a.m.var[v];
+  const int2 ij = a.tile_ij[blockIdx.x];
+  const float beta = (float)S.beta;
+  const float* pold = a.p[S.buf];
+  const float* pb = a.sb + 2 * a.B;
+  auto pval = [&](long long n, uint8_t tg) -> float {
+    const int kind = tg & KIND_MASK;
+    if (kind == K_FREE) return a.t[n] + beta * pold[n];
+    if (kind == K_BODY) return pb[V.body0 + a.m.bid[n]];
+    return 0.0f;
+  };
+  const int tid = linear_tid();
+  const int i = ij.x + threadIdx.x, j = ij.y + threadIdx.y;
+  const bool in = i <= V.nx && j <= V.ny;
+  const long long n = V.base + (long long)j * V.P + i;
+  const uint8_t tg = in ? a.m.tag[n] : K_INACT;
+  const float pn = in ? pval(n, tg) : 0.0f;
+  ps[threadIdx.y + 1][threadIdx.x + 1] = pn;
+  ts[threadIdx.y + 1][threadIdx.x + 1] = tg;
+  if (tid < NHALO) {
+    int li, lj;
+    halo_pos(tid, li, lj);
+    const int hi = ij.x - 1 + li, hj = ij.y - 1 + lj;
+    uint8_t ht = K_INACT;
+    float hv = 0.0f;
+    if (hi >= 0 && hj >= 0 && hi <= V.nx && hj <= V.ny) {
+      const long long hn = V.base + (long long)hj * V.P + hi;
+      ht = a.m.tag[hn];
+      hv = pval(hn, ht);
+    }
+    ps[lj][li] = hv;
+    ts[lj][li] = ht;
+  }
+  __syncthreads();
+  float pq_p = 0.0f, pq_q = 0.0f;
+  if (in) {
+    const int kind = tg & KIND_MASK;
+    float* pnew = a.p[S.buf ^ 1];
+    if (kind == K_FREE || kind == K_BODY) {
+      const float y = q4_row<float>(ps, ts, threadIdx.x + 1, threadIdx.y + 1, n, V.P, a.m.K32, a.m.Vtot, V.kr32);
+      a.q[n] = y;
+      if (kind == K_FREE) {
+        pnew[n] = pn;
+        pq_p = pn;
+        pq_q = y;
+      }
+    }
+  }
+  block_dot(pq_p, pq_q, a.part, sh);
+}
+
+// ---------------------------------------------------------------- cycle kernels, coarse levels
+// r_c = P^T res_f (res_f of level l = 0 in the padded mesh layout, or of a packed level)
+// and z_c = dinv r_c, for variants whose coarsest level is below this one.
+__global__ void __launch_bounds__(256) k_mg_restrict(LvArgs c, int lc, const int* Lv, const VarState* st,
+                                                     const DevVariant* var, const float* res_f,
+                                                     const long long* off_f, const int2* dims_f) {
+  LvNode q;
+  if (!lv_node(c.off, c.dims, c.blkvar, q)) return;
+  if (st[q.v].phase != PH_CG || lc > Lv[q.v] - 1) return;
+  float rc = 0.0f;
+  if (c.act[q.k]) {
+    const bool fine0 = off_f == nullptr;
+    const DevVariant& V = var[q.v];
+    const int2 df = fine0 ? make_int2(V.nx, V.ny) : dims_f[q.v];
+    const long long of = fine0 ? 0 : off_f[q.v];
+    const int fx = fine_of(q.i, df.x), fy = fine_of(q.j, df.y);
+    double s = 0.0;
+    for (int ay = fy - 1; ay <= fy + 1; ++ay) {
+      if (ay < 0 || ay > df.y) continue;
+      const double wy = pw(ay, df.y, q.j);
+      if (wy == 0.0) continue;
+      for (int ax = fx - 1; ax <= fx + 1; ++ax) {
+        if (ax < 0 || ax > df.x) continue;
+        const double w = pw(ax, df.x, q.i) * wy;
+        if (w == 0.0) continue;
+        const long long na = fine0 ? V.base + (long long)ay * V.P + ax : of + (long long)ay * (df.x + 1) + ax;
+        s += w * (double)res_f[na];     // res is zero at every node without an unknown
+      }
+    }
+    rc = (float)s;
+  }
+  c.r[q.k] = rc;
+  c.za[q.k] = c.dinv[q.k] * rc;
+}
+
+// Jacobi sweep on a packed level: zo = zi + dinv (r - A zi); MODE 1: res = r - A zi.
+template <int MODE>
+__global__ void __launch_bounds__(256) k_mg_sweep(LvArgs c, int l, const int* Lv, const VarState* st,
+                                                  const float* zi, float* zo) {
+  LvNode q;
+  if (!lv_node(c.off, c.dims, c.blkvar, q)) return;
+  if (st[q.v].phase != PH_CG || l >= Lv[q.v] - 1) return;
+  float out = 0.0f;
+  if (c.act[q.k]) {
+    float y = 0.0f;
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int bi = q.i + dx, bj = q.j + dy;
+        if (bi < 0 || bj < 0 || bi > q.nx || bj > q.ny) continue;
+        y += c.A[((dy + 1) * 3 + dx + 1) * c.n + q.k] * zi[q.k + (long long)dy * (q.nx + 1) + dx];
+      }
+    const float rr = c.r[q.k] - y;
+    out = MODE == 1 ? rr : zi[q.k] + c.dinv[q.k] * rr;
+  }
+  zo[q.k] = out;
+}
+
+// zb_f += P zb_c on a packed fine level (l >= 1).
+__global__ void __launch_bounds__(256) k_mg_prolong(LvArgs f, LvArgs c, int l, const int* Lv, const VarState* st) {
+  LvNode q;
+  if (!lv_node(f.off, f.dims, f.blkvar, q)) return;
+  if (st[q.v].phase != PH_CG || l >= Lv[q.v] - 1 || !f.act[q.k]) return;
+  const int2 dc = c.dims[q.v];
+  const long long oc = c.off[q.v];
+  int Ix[2], Iy[2];
+  double wx[2], wy[2];
+  const int nxp = parents(q.i, q.nx, Ix, wx), nyp = parents(q.j, q.ny, Iy, wy);
+  double e = 0.0;
+  for (int u = 0; u < nyp; ++u)
+    for (int t = 0; t < nxp; ++t) {
+      const long long k = oc + (long long)Iy[u] * (dc.x + 1) + Ix[t];
+      if (c.act[k]) e += wx[t] * wy[u] * (double)c.zb[k];
+    }
+  f.zb[q.k] = f.zb[q.k] + (float)e;
+}
+
+// Coarsest level of every variant (its own level Lv - 1): a fixed number of Jacobi
+// sweeps from zero in shared memory, result in zb.  One CTA per variant.
+struct CoarseTab {
+  LvArgs lv[16];
+};
+__global__ void __launch_bounds__(256) k_mg_coarse(CoarseTab ct, const int* Lv, const VarState* st) {
+  __shared__ float sA[9][MG_MAXC];
+  __shared__ float sd[MG_MAXC], sr[MG_MAXC], z0[MG_MAXC], z1[MG_MAXC];
+  const int v = blockIdx.x;
+  if (st[v].phase != PH_CG) return;
+  const LvArgs& c = ct.lv[Lv[v] - 1];
+  const long long o = c.off[v];
+  const int2 d = c.dims[v];
+  const int nn = (d.x + 1) * (d.y + 1);
+  if (o < 0 || nn > MG_MAXC) return;
+  for (int k = threadIdx.x; k < nn; k += blockDim.x) {
+    for (int s = 0; s < 9; ++s) sA[s][k] = c.A[s * c.n + o + k];
+    sd[k] = c.dinv[o + k];
+    sr[k] = c.r[o + k];
+    z0[k] = 0.0f;
+  }
+  __syncthreads();
+  float* a = z0;
+  float* b = z1;
+  for (int it = 0; it < MG_COARSE_SWEEPS; ++it) {
+    for (int k = threadIdx.x; k < nn; k += blockDim.x) {
+      const int i = k % (d.x + 1), j = k / (d.x + 1);
+      float y = 0.0f;
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int bi = i + dx, bj = j + dy;
+          if (bi < 0 || bj < 0 || bi > d.x || bj > d.y) continue;
+          y += sA[(dy + 1) * 3 + dx + 1][k] * a[k + dy * (d.x + 1) + dx];
+        }
+      b[k] = a[k] + sd[k] * (sr[k] - y);
+    }
+    __syncthreads();
+    float* tmp = a;
+    a = b;
+    b = tmp;
+  }
+  for (int k = threadIdx.x; k < nn; k += blockDim.x) c.zb[o + k] = a[k];
+}
+
+// ---------------------------------------------------------------- finalisers (one CTA per variant)
+struct FinArgs {
+  VarState* st;
+  const SolveParams* prm;
+  const long long* tile0;    // [nv + 1]
+  const double* part;
+  MeshDev m;
+  float* sb;                 // [4][B]
+  const double* Abb;
+  const float* q;            // fine q plane (body rows gathered from it)
+  int B;
+  int* n_done;
+};
+
+__device__ double fin_sum(const FinArgs& a, int v, double* scratch) {
+  double s = 0.0;
+  for (long long t = a.tile0[v] + linear_tid(); t < a.tile0[v + 1]; t += NT) s += a.part[t];
+  return block_sum(s, scratch);
+}
+
+// After the update: body x, r; r.r; the inner stopping test.
+__global__ void __launch_bounds__(NT) k_mg_finA(FinArgs a) {
+  __shared__ double scratch[NT / 32 + 1];
+  const int v = blockIdx.x;
+  VarState* S = &a.st[v];
+  if (S->phase != PH_CG) return;
+  const double rr_free = fin_sum(a, v, scratch);
+  if (linear_tid() != 0) return;
+  const DevVariant& V = a.m.var[v];
+  const int B = a.B;
+  const float alpha = (float)S->alpha;
+  double rr = rr_free;
+  if (!a.prm->fixed_bodies) {
+    for (int k = 0; k < V.nb; ++k) {
+      const int gb = V.body0 + k;
+      a.sb[gb] = a.sb[gb] + alpha * a.sb[2 * B + gb];
+      const float rb = a.sb[B + gb] - alpha * a.sb[3 * B + gb];
+      a.sb[B + gb] = rb;
+      rr += (double)rb * (double)rb;
+    }
+  }
+  if (S->inner_iters == 0) S->gamma_start = rr;
+  S->gamma = rr;
+  if (!isfinite(rr)) {
+    S->status = PF_EBREAKDOWN;
+    S->phase = PH_DONE;
+    atomicAdd(a.n_done, 1);
+  } else if (rr <= fmax(S->thr_rel * S->gamma_start, S->thr_abs2)) {
+    S->phase = PH_RESID;
+  } else if (S->iters >= a.prm->k_max) {
+    S->capped = 1;
+    S->phase = PH_RESID;
+  }
+}
+
+// After the cycle: body z = r / diagonal; r.z; beta; the body's new search direction.
+__global__ void __launch_bounds__(NT) k_mg_finB(FinArgs a) {
+  __shared__ double scratch[NT / 32 + 1];
+  const int v = blockIdx.x;
+  VarState* S = &a.st[v];
+  if (S->phase != PH_CG) return;
+  const double rz_free = fin_sum(a, v, scratch);
+  if (linear_tid() != 0) return;
+  const DevVariant& V = a.m.var[v];
+  const int B = a.B;
+  double rz = rz_free;
+  float zb[MAXB];
+  const int nbu = a.prm->fixed_bodies ? 0 : V.nb;
+  for (int k = 0; k < nbu; ++k) {
+    const int gb = V.body0 + k;
+    const float rb = a.sb[B + gb];
+    zb[k] = a.Abb[gb] > 0.0 ? (float)(rb / a.Abb[gb]) : 0.0f;
+    rz += (double)rb * (double)zb[k];
+  }
+  const double beta = S->inner_iters == 0 ? 0.0 : rz / S->rho;
+  S->beta = beta;
+  S->rho = rz;
+  for (int k = 0; k < nbu; ++k) {
+    const int gb = V.body0 + k;
+    a.sb[2 * B + gb] = zb[k] + (float)beta * a.sb[2 * B + gb];
+  }
+}
+
+// After the apply: collapsed body rows of q; p.q; alpha; iteration count; buffer flip.
+__global__ void __launch_bounds__(NT) k_mg_finC(FinArgs a) {
+  __shared__ double scratch[NT / 32 + 1];
+  __shared__ double sq[MAXB];
+  const int v = blockIdx.x;
+  VarState* S = &a.st[v];
+  if (S->phase != PH_CG) return;
+  const double pq_free = fin_sum(a, v, scratch);
+  const DevVariant& V = a.m.var[v];
+  const int nbu = a.prm->fixed_bodies ? 0 : V.nb;
+  for (int k = 0; k < nbu; ++k) {
+    double s = 0.0;
+    const int gb = V.body0 + k;
+    for (int e = a.m.body_ptr[gb] + linear_tid(); e < a.m.body_ptr[gb + 1]; e += NT)
+      s += (double)a.q[a.m.body_nodes[e]];
+    s = block_sum(s, scratch);
+    if (linear_tid() == 0) sq[k] = s;
+  }
+  if (linear_tid() != 0) return;
+  const int B = a.B;
+  double pq = pq_free;
+  for (int k = 0; k < nbu; ++k) {
+    const int gb = V.body0 + k;
+    const float qb = (float)sq[k];
+    a.sb[3 * B + gb] = qb;
+    pq += (double)a.sb[2 * B + gb] * (double)qb;
+  }
+  S->pi = pq;
+  S->iters += 1;
+  S->inner_iters += 1;
+  S->buf ^= 1;
+  if (!isfinite(pq) || !(pq > 0.0)) {
+    if (S->gamma == 0.0) {
+      S->alpha = 0.0;
+      S->phase = PH_RESID;
+    } else {
+      S->status = PF_EBREAKDOWN;
+      S->phase = PH_DONE;
+      atomicAdd(a.n_done, 1);
+    }
+    return;
+  }
+  S->alpha = S->rho / pq;
+}
+
+LvArgs lv_args(MgLevel& L) {
+  LvArgs c;
+  c.off = L.d_off;
+  c.dims = L.d_dims;
+  c.blkvar = L.d_blkvar;
+  c.n = L.n;
+  c.act = L.act;
+  c.A = L.A32;
+  c.dinv = L.dinv;
+  c.r = L.r;
+  c.za = L.za;
+  c.zb = L.zb;
+  c.res = L.res;
+  return c;
+}
+
+MeshDev mesh_view(const Batch& b) {
+  MeshDev m;
+  m.var = b.d_var;
+  m.tag = b.tag;
+  m.bid = b.bid;
+  m.body_ptr = b.body_ptr;
+  m.body_nodes = b.body_nodes;
+  m.K64 = b.K64;
+  m.K32 = b.K32;
+  m.Vtot = b.Vtot;
+  return m;
+}
+
+}  // namespace
+
+// The operators of the hierarchy depend on the node coordinates: after they change, the
+// next preconditioned solve forms them again (the level layout and arrays are kept).
+void destroy_mg(Batch& b) { b.mg_ready = false; }
+
+static void mg_layout(Batch& b);
+
+// The hierarchy: per-variant level counts, packed coarse levels, Galerkin operators,
+// Jacobi factors, the body diagonals and the FP32 vector planes of the fine level.
+void mg_setup(Batch& b) {
+  if (b.mg_ready) return;
+  if (b.nv > 0 && b.Vtot > 0 && !b.mg_x) {
+    const size_t V = (size_t)b.Vtot * sizeof(float);
+    float** planes[] = {&b.mg_x, &b.mg_r, &b.mg_z, &b.mg_t, &b.mg_res, &b.mg_p[0], &b.mg_p[1], &b.mg_q, &b.mg_dinv0};
+    for (float** pl : planes) {
+      *pl = (float*)dev_alloc(b, V);
+      PF_CUDA(cudaMemsetAsync(*pl, 0, V, b.stream));
+    }
+    b.mg_part = (double*)dev_alloc(b, std::max<long long>(1, b.T) * sizeof(double));
+    b.mg_Abb = (double*)dev_alloc(b, std::max(1, b.B) * sizeof(double));
+    std::vector<long long> t0(b.nv + 1, 0);
+    for (int v = 0; v < b.nv; ++v) t0[v + 1] = t0[v] + (long long)b.hv[v].tiles_x * b.hv[v].tiles_y;
+    b.d_tile0 = (long long*)dev_alloc(b, (b.nv + 1) * sizeof(long long));
+    PF_CUDA(cudaMemcpyAsync(b.d_tile0, t0.data(), (b.nv + 1) * sizeof(long long), cudaMemcpyHostToDevice, b.stream));
+  }
+  if (b.mg.empty()) mg_layout(b);
+  const int L = b.mg_L;
+  const MeshDev m = mesh_view(b);
+  cudaStream_t s = b.stream;
+  k_mg_dinv0<<<(unsigned)b.T, dim3(TX, TY), 0, s>>>(m, b.tile_var, b.tile_ij, b.mg_dinv0);
+  if (b.B > 0) k_mg_body_diag<<<b.B, dim3(TX, TY), 0, s>>>(m, b.d_body_var, b.mg_Abb);
+  for (int l = 1; l < L; ++l) {
+    MgLevel& M = b.mg[l];
+    if (M.nblk == 0) continue;
+    const LvArgs c = lv_args(M);
+    const bool f0 = l == 1;
+    MgLevel& F = b.mg[l - 1];
+    k_mg_act<<<(unsigned)M.nblk, 256, 0, s>>>(c, f0 ? nullptr : F.act, f0 ? nullptr : F.d_off,
+                                               f0 ? nullptr : F.d_dims, b.d_var, b.tag, M.act);
+    k_mg_rap<<<(unsigned)M.nblk, 256, 0, s>>>(c, M.A64, M.A32, M.dinv, m, f0 ? nullptr : F.act,
+                                               f0 ? nullptr : F.A64, f0 ? nullptr : F.d_off,
+                                               f0 ? nullptr : F.d_dims, f0 ? 0 : F.n);
+  }
+  PF_CUDA(cudaGetLastError());
+  b.launches += 1 + (b.B > 0 ? 1 : 0) + 2 * (L - 1);
+  b.mg_ready = true;
+}
+
+// Level counts and the packed layout of every coarse level, allocated once per handle.
+static void mg_layout(Batch& b) {
+  // levels per variant: coarsen while a level has more than MG_CMAX cells in a direction
+  b.mg_Lv.assign(b.nv, 1);
+  std::vector<std::vector<int2>> dims(b.nv);
+  int L = 1;
+  for (int v = 0; v < b.nv; ++v) {
+    int nx = b.hv[v].g.nx, ny = b.hv[v].g.ny;
+    dims[v].push_back(make_int2(nx, ny));
+    do {
+      nx = (nx + 1) / 2;
+      ny = (ny + 1) / 2;
+      dims[v].push_back(make_int2(nx, ny));
+    } while (std::max(nx, ny) > MG_CMAX);
+    b.mg_Lv[v] = (int)dims[v].size();
+    L = std::max(L, b.mg_Lv[v]);
+  }
+  if (L > 16) throw Error{PF_EINVAL, "grid too large for the multigrid hierarchy"};
+  b.mg_L = L;
+  if (!b.d_mg_Lv) b.d_mg_Lv = (int*)dev_alloc(b, b.nv * sizeof(int));
+  PF_CUDA(cudaMemcpyAsync(b.d_mg_Lv, b.mg_Lv.data(), b.nv * sizeof(int), cudaMemcpyHostToDevice, b.stream));
+  b.mg.assign(L, MgLevel());
+  for (int l = 1; l < L; ++l) {
+    MgLevel& M = b.mg[l];
+    M.off.assign(b.nv, -1);
+    M.dims.assign(b.nv, make_int2(0, 0));
+    long long o = 0;
+    std::vector<int> blkvar;
+    for (int v = 0; v < b.nv; ++v) {
+      if (l >= b.mg_Lv[v]) continue;
+      const int2 d = dims[v][l];
+      const long long nn = (long long)(d.x + 1) * (d.y + 1);
+      const long long nb = (nn + 255) / 256;
+      M.off[v] = o;
+      M.dims[v] = d;
+      for (long long k = 0; k < nb; ++k) blkvar.push_back(v);
+      o += nb * 256;
+    }
+    M.n = std::max<long long>(o, 256);
+    M.nblk = (long long)blkvar.size();
+    if (blkvar.empty()) blkvar.push_back(-1);
+    M.d_off = (long long*)dev_alloc(b, b.nv * sizeof(long long));
+    M.d_dims = (int2*)dev_alloc(b, b.nv * sizeof(int2));
+    M.d_blkvar = (int*)dev_alloc(b, blkvar.size() * sizeof(int));
+    PF_CUDA(cudaMemcpyAsync(M.d_off, M.off.data(), b.nv * sizeof(long long), cudaMemcpyHostToDevice, b.stream));
+    PF_CUDA(cudaMemcpyAsync(M.d_dims, M.dims.data(), b.nv * sizeof(int2), cudaMemcpyHostToDevice, b.stream));
+    PF_CUDA(cudaMemcpyAsync(M.d_blkvar, blkvar.data(), blkvar.size() * sizeof(int), cudaMemcpyHostToDevice,
+                            b.stream));
+    M.act = (uint8_t*)dev_alloc(b, M.n);
+    M.A64 = (double*)dev_alloc(b, 9 * M.n * sizeof(double));
+    M.A32 = (float*)dev_alloc(b, 9 * M.n * sizeof(float));
+    M.dinv = (float*)dev_alloc(b, M.n * sizeof(float));
+    M.r = (float*)dev_alloc(b, M.n * sizeof(float));
+    M.za = (float*)dev_alloc(b, M.n * sizeof(float));
+    M.zb = (float*)dev_alloc(b, M.n * sizeof(float));
+    M.res = (float*)dev_alloc(b, M.n * sizeof(float));
+    PF_CUDA(cudaMemsetAsync(M.act, 0, M.n, b.stream));
+    for (float* f : {M.r, M.za, M.zb, M.res, M.dinv}) PF_CUDA(cudaMemsetAsync(f, 0, M.n * sizeof(float), b.stream));
+    PF_CUDA(cudaMemsetAsync(M.A64, 0, 9 * M.n * sizeof(double), b.stream));
+    PF_CUDA(cudaMemsetAsync(M.A32, 0, 9 * M.n * sizeof(float), b.stream));
+  }
+}
+
+// `iters` preconditioned CG iterations for every variant in the CG phase (captured as a
+// graph by the solve loop).
+void launch_pcg_chunk(Batch& b, int iters, cudaStream_t s) {
+  FineArgs a;
+  a.m = mesh_view(b);
+  a.tile_var = b.tile_var;
+  a.tile_ij = b.tile_ij;
+  a.st = b.state;
+  a.dinv0 = b.mg_dinv0;
+  a.x = b.mg_x;
+  a.r = b.mg_r;
+  a.z = b.mg_z;
+  a.t = b.mg_t;
+  a.res = b.mg_res;
+  a.q = b.mg_q;
+  a.p[0] = b.mg_p[0];
+  a.p[1] = b.mg_p[1];
+  a.sb = b.sb32;
+  a.B = std::max(1, b.B);
+  a.part = b.mg_part;
+  FinArgs f;
+  f.st = b.state;
+  f.prm = b.params;
+  f.tile0 = b.d_tile0;
+  f.part = b.mg_part;
+  f.m = a.m;
+  f.sb = b.sb32;
+  f.Abb = b.mg_Abb;
+  f.q = b.mg_q;
+  f.B = std::max(1, b.B);
+  f.n_done = b.n_done;
+  CoarseTab ct;
+  std::memset(&ct, 0, sizeof(ct));
+  for (int l = 1; l < b.mg_L; ++l) ct.lv[l] = lv_args(b.mg[l]);
+  const unsigned T = (unsigned)b.T, nv = (unsigned)b.nv;
+  const dim3 blk(TX, TY);
+  const int L = b.mg_L;
+  for (int it = 0; it < iters; ++it) {
+    k_mg0_update<<<T, blk, 0, s>>>(a);
+    k_mg_finA<<<nv, blk, 0, s>>>(f);
+    // descent: level 0 second sweep (z -> t), residual, restriction to level 1
+    k_mg0_sweep<0><<<T, blk, 0, s>>>(a, b.mg_z, b.mg_t);
+    k_mg0_sweep<1><<<T, blk, 0, s>>>(a, b.mg_t, b.mg_res);
+    for (int l = 1; l < L; ++l) {
+      MgLevel& M = b.mg[l];
+      if (M.nblk == 0) continue;
+      const LvArgs c = lv_args(M);
+      if (l == 1) {
+        k_mg_restrict<<<(unsigned)M.nblk, 256, 0, s>>>(c, l, b.d_mg_Lv, b.state, b.d_var, b.mg_res, nullptr, nullptr);
+      } else {
+        MgLevel& F = b.mg[l - 1];
+        k_mg_restrict<<<(unsigned)M.nblk, 256, 0, s>>>(c, l, b.d_mg_Lv, b.state, b.d_var, F.res, F.d_off, F.d_dims);
+      }
+      // pre-smoothing of the level (variants whose coarsest level this is skip: the coarse
+      // solve below takes their restricted residual)
+      k_mg_sweep<0><<<(unsigned)M.nblk, 256, 0, s>>>(c, l, b.d_mg_Lv, b.state, M.za, M.zb);
+      k_mg_sweep<1><<<(unsigned)M.nblk, 256, 0, s>>>(c, l, b.d_mg_Lv, b.state, M.zb, M.res);
+    }
+    k_mg_coarse<<<nv, 256, 0, s>>>(ct, b.d_mg_Lv, b.state);
+    // ascent
+    for (int l = L - 2; l >= 1; --l) {
+      MgLevel& M = b.mg[l];
+      if (M.nblk == 0) continue;
+      const LvArgs c = lv_args(M);
+      k_mg_prolong<<<(unsigned)M.nblk, 256, 0, s>>>(c, lv_args(b.mg[l + 1]), l, b.d_mg_Lv, b.state);
+      k_mg_sweep<0><<<(unsigned)M.nblk, 256, 0, s>>>(c, l, b.d_mg_Lv, b.state, M.zb, M.za);
+      k_mg_sweep<0><<<(unsigned)M.nblk, 256, 0, s>>>(c, l, b.d_mg_Lv, b.state, M.za, M.zb);
+    }
+    k_mg0_prolong<<<T, blk, 0, s>>>(a, lv_args(b.mg[1]), b.d_mg_Lv);
+    k_mg0_sweep<0><<<T, blk, 0, s>>>(a, b.mg_t, b.mg_z);
+    k_mg0_sweep<2><<<T, blk, 0, s>>>(a, b.mg_z, b.mg_t);
+    k_mg_finB<<<nv, blk, 0, s>>>(f);
+    k_mg0_apply<<<T, blk, 0, s>>>(a);
+    k_mg_finC<<<nv, blk, 0, s>>>(f);
+  }
+  PF_CUDA(cudaGetLastError());
+}
+
+}  // namespace pfq4

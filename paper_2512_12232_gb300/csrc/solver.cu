@@ -76,6 +76,7 @@ struct ResidArgs {
   int B;
   int mixed;
   int* n_done;
+  float* rplane;            // preconditioned CG: the restarted residual goes to this FP32 plane
 };
 
 template <typename T> __device__ __forceinline__ const T* kplane(const MeshDev& m);
@@ -914,12 +915,16 @@ __global__ void __launch_bounds__(NT) k_resid(ResidArgs<T> a) {
       const double y = q4_row<double>(ps, ts, threadIdx.x + 1, threadIdx.y + 1, n, V.P, a.m.K64, plane, V.kr64);
       if (kind == K_FREE) {
         const double r = -y;
-        State4<T> o;
-        o.x = T(0);
-        o.r = (T)r;
-        o.p = T(0);
-        o.q = T(0);
-        s_out[n] = o;
+        if (a.rplane) {
+          a.rplane[n] = (float)r;
+        } else {
+          State4<T> o;
+          o.x = T(0);
+          o.r = (T)r;
+          o.p = T(0);
+          o.q = T(0);
+          s_out[n] = o;
+        }
         acc = fma(r, r, acc);
       } else {
         a.w64[n] = y;
@@ -948,7 +953,7 @@ __global__ void __launch_bounds__(NT) k_resid(ResidArgs<T> a) {
 // grid as k_resid: a launch with no variant to refine costs one load per CTA.
 template <typename T>
 __global__ void __launch_bounds__(NT) k_fold(const DevVariant* var, int gx, const uint8_t* tag, const VarState* st,
-                                             double* x64, State4<T>* const* sbuf) {
+                                             double* x64, State4<T>* const* sbuf, float* xplane) {
   const int v = blockIdx.y;
   if (st[v].phase != PH_RESID) return;
   const DevVariant& V = var[v];
@@ -960,6 +965,11 @@ __global__ void __launch_bounds__(NT) k_fold(const DevVariant* var, int gx, cons
     if (i > V.nx || j > V.ny) continue;
     const long long n = V.base + (long long)j * V.P + i;
     if ((tag[n] & KIND_MASK) != K_FREE) continue;
+    if (xplane) {                       // preconditioned CG keeps its correction in a plane
+      x64[n] = x64[n] + (double)xplane[n];
+      xplane[n] = 0.0f;
+      continue;
+    }
     x64[n] = x64[n] + (double)s[n].x;
     s[n].x = T(0);
   }
@@ -1736,6 +1746,7 @@ static void fill_resid_args(Batch& b, ResidArgs<T>& a, State4<T>* const st[2], T
   a.B = std::max(1, b.B);
   a.mixed = mixed;
   a.n_done = b.n_done;
+  a.rplane = b.pcg_active ? b.mg_r : nullptr;
 }
 
 // the k_cg launches of one chunk (captured once as a graph); timed launches record
@@ -1770,12 +1781,14 @@ static void launch_resid_only(Batch& b, int precision, cudaStream_t s) {
   const dim3 blk(TX, TY);
   const dim3 rg(b.rgx, b.nv);
   if (precision == PF_FP64) {
-    k_fold<double><<<rg, blk, 0, s>>>(b.d_var, b.rgx, b.tag, b.state, b.x64, (State4<double>* const*)b.d_sbuf);
+    k_fold<double><<<rg, blk, 0, s>>>(b.d_var, b.rgx, b.tag, b.state, b.x64, (State4<double>* const*)b.d_sbuf,
+                                      nullptr);
     ResidArgs<double> ra;
     fill_resid_args<double>(b, ra, b.st64, b.sb64, 0);
     k_resid<double><<<rg, blk, 0, s>>>(ra);
   } else {
-    k_fold<float><<<rg, blk, 0, s>>>(b.d_var, b.rgx, b.tag, b.state, b.x64, (State4<float>* const*)(b.d_sbuf + 2));
+    k_fold<float><<<rg, blk, 0, s>>>(b.d_var, b.rgx, b.tag, b.state, b.x64, (State4<float>* const*)(b.d_sbuf + 2),
+                                     b.pcg_active ? b.mg_x : nullptr);
     ResidArgs<float> ra;
     fill_resid_args<float>(b, ra, b.st32, b.sb32, 1);
     k_resid<float><<<rg, blk, 0, s>>>(ra);
@@ -1809,6 +1822,37 @@ static cudaGraphExec_t get_graph(Batch& b, int precision, int chunk) {
   return ex;
 }
 
+// Iterations per captured graph of the preconditioned CG (each about 40 kernels).
+constexpr int PCG_CHUNK = 4;
+
+static int pcg_launches_per_iter(const Batch& b) {
+  int n = 11;                                    // fine level and finalisers
+  for (int l = 1; l < b.mg_L; ++l)
+    if (b.mg[l].nblk > 0) n += 3 + (l <= b.mg_L - 2 ? 3 : 0);
+  return n;
+}
+
+static cudaGraphExec_t get_pcg_graph(Batch& b, int chunk) {
+  if (b.graph_pcg && b.graph_pcg_chunk == chunk) return b.graph_pcg;
+  if (b.graph_pcg) {
+    cudaGraphExecDestroy(b.graph_pcg);
+    b.graph_pcg = nullptr;
+  }
+  cudaStream_t cs;
+  PF_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaGraph_t g;
+  PF_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  launch_pcg_chunk(b, chunk, cs);
+  PF_CUDA(cudaStreamEndCapture(cs, &g));
+  cudaGraphExec_t ex;
+  PF_CUDA(cudaGraphInstantiate(&ex, g, 0));
+  PF_CUDA(cudaGraphDestroy(g));
+  PF_CUDA(cudaStreamDestroy(cs));
+  b.graph_pcg = ex;
+  b.graph_pcg_chunk = chunk;
+  return ex;
+}
+
 pf_status psi_solve(Batch& b, double U, const pf_solve_opts& o, double* dev_psi, double* body_psi,
                     pf_solve_info* info) {
   if (o.k_max < 1) throw Error{PF_EINVAL, "k_max must be >= 1"};
@@ -1828,7 +1872,22 @@ pf_status solve_core(Batch& b, double U, const pf_solve_opts& o, double* dev_psi
   if (o.criterion != PF_TOL_REL_TRUE && o.criterion != PF_TOL_PAPER_ABS)
     throw Error{PF_EINVAL, "invalid stopping criterion"};
   const int prec = o.precision;
+  if (o.preconditioner != PF_PRECOND_NONE && o.preconditioner != PF_PRECOND_MG)
+    throw Error{PF_EINVAL, "invalid preconditioner"};
+  const bool pcg = o.preconditioner == PF_PRECOND_MG;
+  if (pcg && prec != PF_MIXED) throw Error{PF_EINVAL, "the multigrid-preconditioned CG runs in PF_MIXED precision"};
   ensure_solver_memory(b, prec);
+  // the preconditioned path is active for this solve only (also when it throws)
+  struct PcgScope {
+    Batch& b;
+    ~PcgScope() { b.pcg_active = false; }
+  } pcg_scope{b};
+  b.pcg_active = pcg;
+  if (pcg) {
+    mg_setup(b);
+    for (float* f : {b.mg_x, b.mg_p[0], b.mg_p[1], b.mg_q, b.mg_r})
+      PF_CUDA(cudaMemsetAsync(f, 0, b.Vtot * sizeof(float), b.stream));
+  }
   {
     const char* e = getenv("PFQ4_CG_STAGES");      // a fixed pipeline depth, else the tuned one
     const int ns = e ? atoi(e) : b.tuned_stages[prec];
@@ -1879,6 +1938,7 @@ pf_status solve_core(Batch& b, double U, const pf_solve_opts& o, double* dev_psi
   PF_CUDA(cudaEventRecord(b.ev[3], s));
   launch_resid_only(b, prec, s);
   int chunk = o.chunk > 0 ? o.chunk : 0;
+  if (pcg && chunk == 0) chunk = PCG_CHUNK;
   if (chunk == 0) {
     long long nodes = 0;
     for (auto& H : b.hv) nodes += H.stats.n_nodes;
@@ -1906,7 +1966,7 @@ pf_status solve_core(Batch& b, double U, const pf_solve_opts& o, double* dev_psi
     if (hdone[1]) throw Error{PF_ETIMEOUT, "a bounded wait in the CG kernel gave up (TMA tile not delivered)"};
     return (double)ms / n;
   };
-  const bool tune = b.cg_tune && o.k_max > 0 && !getenv("PFQ4_CG_STAGES");
+  const bool tune = b.cg_tune && o.k_max > 0 && !getenv("PFQ4_CG_STAGES") && !pcg;
   if (tune && !b.stages_tuned[prec]) {
     double best = 1e300;
     int best_ns = b.cg_stages;
@@ -1922,13 +1982,14 @@ pf_status solve_core(Batch& b, double U, const pf_solve_opts& o, double* dev_psi
     b.tuned_stages[prec] = best_ns;
     b.stages_tuned[prec] = true;
   }
-  cudaGraphExec_t ex = get_graph(b, prec, chunk);
+  cudaGraphExec_t ex = pcg ? get_pcg_graph(b, chunk) : get_graph(b, prec, chunk);
   CgConfig& cc = cg_config(b, prec, b.cg_stages);
-  if (cc.active.size() != (size_t)b.nv || std::find(cc.active.begin(), cc.active.end(), 0) != cc.active.end()) {
+  if (!pcg &&
+      (cc.active.size() != (size_t)b.nv || std::find(cc.active.begin(), cc.active.end(), 0) != cc.active.end())) {
     cc.active.assign(b.nv, 1);                   // a solve starts with every variant running
     cg_sched_write(b, cc);
   }
-  if (b.cg_tune && o.k_max > 0 && (long long)cc.tile_cost.size() >= 2LL * cc.G) {
+  if (!pcg && b.cg_tune && o.k_max > 0 && (long long)cc.tile_cost.size() >= 2LL * cc.G) {
     const int rounds = env_int("PFQ4_CG_TUNE_ROUNDS", CG_TUNE_ROUNDS, 0, 16);
     const int per_round = env_int("PFQ4_CG_TUNE_LAUNCHES", CG_TUNE_LAUNCHES, 1, 16);
     for (; cc.tune_rounds < rounds; ++cc.tune_rounds) {
@@ -1978,6 +2039,7 @@ pf_status solve_core(Batch& b, double U, const pf_solve_opts& o, double* dev_psi
       finished = true;
       return;
     }
+    if (pcg) return;                             // its kernels take every variant's tiles each launch
     // spread the grid over the variants still running once enough work has finished
     std::vector<char> act(b.nv);
     for (int v = 0; v < b.nv; ++v) act[v] = b.h_vs[(size_t)k * b.nv + v].phase != PH_DONE;
@@ -2007,7 +2069,8 @@ pf_status solve_core(Batch& b, double U, const pf_solve_opts& o, double* dev_psi
   // kernels launched: k_init, slot seeding, the tuning launches and every queued chunk
   // (CG graph + fold + residual), no-op chunks after the last variant finished included
   const long long tuned_launches = launches - (long long)(rlaunches - 1) * chunk;
-  b.launches += 1 + (n_slots > 0 ? 1 : 0) + tuned_launches + issued * chunk + (1 + issued) * 2;
+  b.launches += 1 + (n_slots > 0 ? 1 : 0) + tuned_launches + issued * chunk * (pcg ? pcg_launches_per_iter(b) : 1) +
+                (1 + issued) * 2;
   std::vector<VarState> fin(b.nv);
   PF_CUDA(cudaMemcpyAsync(fin.data(), b.state, b.nv * sizeof(VarState), cudaMemcpyDeviceToHost, s));
   PF_CUDA(cudaStreamSynchronize(s));
@@ -2030,7 +2093,7 @@ pf_status solve_core(Batch& b, double U, const pf_solve_opts& o, double* dev_psi
     // coefficient bytes: the cells whose stored K_e the operator of this precision reads
     const long long n_gen = prec == PF_MIXED ? b.hv[v].n_gen32_cells : M.n_general_cells;
     const double bv = per_node_free * M.n_free + per_body * M.n_body_nodes + 1.0 * M.n_nodes + per_gen * n_gen;
-    bytes_done += bv * (double)S.iters;
+    if (!pcg) bytes_done += bv * (double)S.iters;
     if (info) {
       info[v].iters = S.iters;
       info[v].refinements = std::max(0, S.n_resid - 1);

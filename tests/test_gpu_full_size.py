@@ -9,8 +9,8 @@ the oracle's direct solves of the same 5 systems.
   it within the tolerance, and the error of psi, of the body values and of CoPFI stays
   within what that residual allows: ||u - u*||_2 <= ||b - A u||_2 / lambda_min(A), with
   lambda_min(A) from a Lanczos run on the oracle's factorised A.
-* Tight solves: mixed to 1e-12 (psi to 1e-6 relative L2, body values to 1e-8) and FP64
-  to 1e-13 (psi to 1e-10).
+* Tight solves: mixed to 1e-12 (psi to 1e-6 relative L2, body values to 1e-8), the same
+  with the multigrid-preconditioned CG, and FP64 to 1e-13 (psi to 1e-10).
 
 The oracle's five solves run in a spawn pool, one process per variant."""
 import multiprocessing as mp
@@ -108,12 +108,12 @@ def test_full_size_benchmark_solve_error_is_within_its_residual_bound(api, full_
               f"|dCoPFI| {abs(cps[v] - cp_ref):.2e}, residual {resid:.2e}, bound on |e| {e_bound:.2e}")
 
 
-@pytest.mark.parametrize("prec,tol,bound", [("mixed", 1e-12, 1e-6), ("fp64", 1e-13, 1e-10)])
+@pytest.mark.parametrize("prec,tol,bound", [("mixed", 1e-12, 1e-6), ("fp64", 1e-13, 1e-10), ("mixed_mg", 1e-12, 1e-6)])
 def test_full_size_tight_solves_match_oracle(api, full_size, prec, tol, bound):
     cases, ref = full_size
-    p = api.PF_MIXED if prec == "mixed" else api.PF_FP64
+    p = api.PF_FP64 if prec == "fp64" else api.PF_MIXED
     with api.batch_build(cases) as g:
-        res = api.psi_solve(g, U=1.0, tol=tol, precision=p)
+        res = api.psi_solve(g, U=1.0, tol=tol, precision=p, preconditioner="mg" if prec == "mixed_mg" else "none")
         psi = res.psi.cpu().numpy()
         offs = g.node_offsets
     for v, r in enumerate(ref):

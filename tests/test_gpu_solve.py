@@ -261,3 +261,49 @@ def test_invalid_stopping_criterion_is_refused(api):
     with api.mesh_build(c.grid, c.bodies, c.sweeps, c.bc) as g:
         res = api.psi_solve(g, U=1.0, tol=1e-8, criterion=7, raise_on_failure=False)
     assert res.status == 1
+
+
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_mg_preconditioned_solve_matches_oracle(api, case):
+    """PF_PRECOND_MG: the multigrid-preconditioned CG converges to the oracle's solution
+    (mixed precision after refinement: psi to 1e-6, body values to 1e-8) in fewer CG
+    iterations than the unpreconditioned CG of the paper."""
+    U = 1.3
+    m, s, u, psi_ref = oracle_solution(case, U)
+    with api.mesh_build(case.grid, case.bodies, case.sweeps, case.bc) as g:
+        res = api.psi_solve(g, U=U, tol=1e-12, precision=api.PF_MIXED, preconditioner="mg")
+        plain = api.psi_solve(g, U=U, tol=1e-12, precision=api.PF_MIXED)
+    assert res.status == 0 and res.info[0]["status"] == 0
+    assert res.info[0]["rel_true_residual"] <= 1e-12
+    assert rel_l2(res.psi.cpu().numpy(), psi_ref) <= MIXED_TOL
+    np.testing.assert_allclose(res.body_psi, u[s.n_free:], rtol=0, atol=BODY_TOL)
+    if case.nx >= 128:
+        assert 3 * res.info[0]["iters"] < plain.info[0]["iters"], (res.info[0]["iters"], plain.info[0]["iters"])
+
+
+def test_mg_preconditioned_batch(api):
+    """An uneven batch (grids of 256 to 384 cells wide, so the variants have different
+    numbers of multigrid levels) solved to 1e-8: every variant within the residual bound
+    of the oracle's solution, and deterministic."""
+    cases = W.parametric_sweep(6, seed=5, nx_choices=(256, 288, 320, 384))
+    outs = []
+    with api.batch_build(cases) as g:
+        for _ in range(2):
+            r = api.psi_solve(g, U=1.0, tol=1e-8, precision=api.PF_MIXED, preconditioner="mg")
+            outs.append(r.psi.cpu().numpy())
+        plain = api.psi_solve(g, U=1.0, tol=1e-8, precision=api.PF_MIXED)
+        offs = g.node_offsets
+    assert np.array_equal(outs[0], outs[1])
+    for v, c in enumerate(cases):
+        assert r.info[v]["status"] == 0 and r.info[v]["rel_true_residual"] <= 1e-8
+        assert reduced_error(c, outs[0][offs[v]:offs[v + 1]]) <= residual_error_bound(c, 1e-8), v
+        assert 3 * r.info[v]["iters"] < plain.info[v]["iters"], v
+
+
+def test_mg_preconditioner_needs_mixed_precision(api):
+    c = W.single_cylinder()
+    with api.mesh_build(c.grid, c.bodies, c.sweeps, c.bc) as g:
+        res = api.psi_solve(g, U=1.0, tol=1e-8, precision=api.PF_FP64, preconditioner="mg", raise_on_failure=False)
+        assert res.status == 1
+        res = api.psi_solve(g, U=1.0, tol=1e-8, preconditioner=5, raise_on_failure=False)
+        assert res.status == 1
