@@ -258,9 +258,10 @@ __device__ __forceinline__ void halo_pos(int h, int& li, int& lj) {
 // sum_{b != a} K_e[a,b] (p_b - p_a), which equals (K_e p_e)_a because every row of
 // K_e sums to zero.  Inactive cells contribute nothing.  Cell coefficients come
 // from the stored planes for displaced cells and from `kr` (closed-form rectangle)
-// otherwise.  n: padded node index, P: pitch, K: [6][plane].
-template <typename T>
-__device__ __forceinline__ T q4_row(const T (*ps)[SW], const uint8_t (*ts)[SW], int li, int lj,
+// otherwise.  n: padded node index, P: pitch, K: [6][plane]; W: the shared tiles' row
+// width (tile width + 2).
+template <typename T, int W = SW>
+__device__ __forceinline__ T q4_row(const T (*ps)[W], const uint8_t (*ts)[W], int li, int lj,
                                     long long n, int P, const T* __restrict__ K, long long plane,
                                     const T* kr) {
   const T pc = ps[lj][li];

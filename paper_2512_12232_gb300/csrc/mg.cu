@@ -13,7 +13,7 @@
 //     nodes.  Coarse operators are Galerkin products A_{l+1} = P^T A_l P (9-point
 //     stencils, formed once in FP64).  Smoother: damped Jacobi (omega = 0.85), two sweeps
 //     before and two after the coarse correction; the coarsest level (at most 17 x 17
-//     nodes) takes a fixed number of Jacobi sweeps from zero.  Jacobi with a fixed sweep
+//     nodes) takes 100 Jacobi sweeps from zero.  Jacobi with a fixed sweep
 //     count is a fixed symmetric operator, so the cycle is a valid CG preconditioner.
 //   * body unknowns (one per body, the multi-point constraint): the inverse diagonal of
 //     the collapsed body row, sum over the body's nodes n, m of A(n, m).
@@ -39,7 +39,7 @@ namespace {
 
 constexpr float MG_OMEGA = 0.85f;        // Jacobi damping (smoothing factor ~1/3 for Q4 Laplace stencils)
 constexpr int MG_CMAX = 16;              // coarsen while a level has more than this many cells per direction
-constexpr int MG_COARSE_SWEEPS = 300;    // Jacobi sweeps of the coarsest solve
+constexpr int MG_COARSE_SWEEPS = 100;    // Jacobi sweeps of the coarsest solve
 constexpr int MG_MAXC = 17 * 17;         // nodes of a coarsest level at most
 
 // ---------------------------------------------------------------- index rules
@@ -57,6 +57,18 @@ __device__ __forceinline__ int parents(int i, int n, int* I, double* w) {
   return 2;
 }
 __device__ __forceinline__ int fine_of(int I, int n) { return min(2 * I, n); }
+// The same rules in FP32 for the cycle (the weights 1 and 1/2 are exact in FP32).
+__device__ __forceinline__ float pwf(int i, int n, int I) {
+  if ((i & 1) == 0) return I == (i >> 1) ? 1.0f : 0.0f;
+  if (i == n) return I == ((i + 1) >> 1) ? 1.0f : 0.0f;
+  return (I == ((i - 1) >> 1) || I == ((i + 1) >> 1)) ? 0.5f : 0.0f;
+}
+__device__ __forceinline__ int parentsf(int i, int n, int* I, float* w) {
+  if ((i & 1) == 0) { I[0] = i >> 1; w[0] = 1.0f; return 1; }
+  if (i == n) { I[0] = (i + 1) >> 1; w[0] = 1.0f; return 1; }
+  I[0] = (i - 1) >> 1; I[1] = (i + 1) >> 1; w[0] = w[1] = 0.5f;
+  return 2;
+}
 
 // Row of the fine (level-0) operator at node n = (i, j) as a 9-point stencil in FP64,
 // slot (dy + 1) * 3 + (dx + 1): off-diagonal entries summed over the active cells that
@@ -246,9 +258,20 @@ __global__ void __launch_bounds__(NT) k_mg_body_diag(MeshDev m, const int* body_
 }
 
 // ---------------------------------------------------------------- cycle kernels, fine level
+// The fine-level kernels run on the 64 x 16 tiles of the fused CG step, 256 threads per
+// tile, each thread a vertical strip of 4 nodes (column tid % 64, rows 4 (tid / 64) ..
+// + 3), with the tile's one-node halo in shared memory.  Every FP32 plane of the cycle
+// is zero at nodes without an unknown (only FREE nodes are ever written), so values and
+// tags are loaded together, without a tag-dependent second load.
+constexpr int FW = CTX + 2;                 // shared tile width (66)
+constexpr int FH = CTY + 2;                 // shared tile height (18)
+constexpr int FS = CTY * CTX / NT;          // nodes per thread (4)
+constexpr int FNH = 2 * FW + 2 * CTY;       // halo positions (164)
+static_assert(FS * NT == CTX * CTY && FNH <= NT, "fine-level tile mapping");
+
 struct FineArgs {
   MeshDev m;
-  const int* tile_var;
+  const int* tile_var;       // fused-CG tile list (64 x 16)
   const int2* tile_ij;
   const VarState* st;
   const float* dinv0;
@@ -256,42 +279,76 @@ struct FineArgs {
   float* p[2];
   const float* sb;           // [4][B] body CG values x, r, p, q
   int B;
-  double* part;              // [T] partial sums of the kernel's dot product
+  double* part;              // [tiles] partial sums of the kernel's dot product
+  const long long* c_off;    // level 1 (the prolongation folded into the first post-sweep)
+  const int2* c_dims;
+  const float* c_zb;
 };
 
-// Tile of a FREE-only field (zero at every other node and outside the grid) with its
-// one-node halo, and the tags, in shared memory.
-__device__ __forceinline__ void load_free_tile(const DevVariant& V, int2 ij, const float* f, const uint8_t* tag,
-                                               float (*ps)[SW], uint8_t (*ts)[SW]) {
-  const int tid = linear_tid();
-  const int i = ij.x + threadIdx.x, j = ij.y + threadIdx.y;
-  const bool in = i <= V.nx && j <= V.ny;
-  const long long n = V.base + (long long)j * V.P + i;
-  const uint8_t tg = in ? tag[n] : K_INACT;
-  ps[threadIdx.y + 1][threadIdx.x + 1] = (tg & KIND_MASK) == K_FREE ? f[n] : 0.0f;
-  ts[threadIdx.y + 1][threadIdx.x + 1] = tg;
-  if (tid < NHALO) {
+__device__ __forceinline__ void halo_pos66(int h, int& li, int& lj) {
+  if (h < FW) { li = h; lj = 0; }
+  else if (h < 2 * FW) { li = h - FW; lj = CTY + 1; }
+  else if (h < 2 * FW + CTY) { li = 0; lj = 1 + (h - 2 * FW); }
+  else { li = CTX + 1; lj = 1 + (h - 2 * FW - CTY); }
+}
+
+// P e at fine node (i, j) of variant v: the bilinear interpolation from level 1.
+__device__ __forceinline__ float coarse_interp(const FineArgs& a, int v, const DevVariant& V, int i, int j) {
+  const int2 dc = a.c_dims[v];
+  const long long oc = a.c_off[v];
+  int Ix[2], Iy[2];
+  float wx[2], wy[2];
+  const int nxp = parentsf(i, V.nx, Ix, wx), nyp = parentsf(j, V.ny, Iy, wy);
+  float e = 0.0f;
+  for (int u = 0; u < nyp; ++u)
+    for (int t = 0; t < nxp; ++t) e += wx[t] * wy[u] * a.c_zb[oc + (long long)Iy[u] * (dc.x + 1) + Ix[t]];
+  return e;
+}
+
+// Tile (with halo) of the fine plane f into ps and the tags into ts; PROL: f + P e at
+// FREE nodes (coarse values are zero at inactive coarse nodes).
+template <bool PROL>
+__device__ __forceinline__ void load_tile66(const FineArgs& a, int v, const DevVariant& V, int2 ij, const float* f,
+                                            float (*ps)[FW], uint8_t (*ts)[FW]) {
+  const int tid = linear_tid(), col = tid % CTX, r0 = (tid / CTX) * FS;
+  const int i = ij.x + col;
+#pragma unroll
+  for (int u = 0; u < FS; ++u) {
+    const int j = ij.y + r0 + u;
+    const bool in = i <= V.nx && j <= V.ny;
+    const long long n = V.base + (long long)j * V.P + i;
+    const uint8_t tg = in ? a.m.tag[n] : K_INACT;
+    float val = in ? f[n] : 0.0f;
+    if (PROL && in) {
+      const float e = coarse_interp(a, v, V, i, j);
+      if ((tg & KIND_MASK) == K_FREE) val += e;
+    }
+    ps[1 + r0 + u][1 + col] = val;
+    ts[1 + r0 + u][1 + col] = tg;
+  }
+  if (tid < FNH) {
     int li, lj;
-    halo_pos(tid, li, lj);
+    halo_pos66(tid, li, lj);
     const int hi = ij.x - 1 + li, hj = ij.y - 1 + lj;
     uint8_t ht = K_INACT;
     float hv = 0.0f;
     if (hi >= 0 && hj >= 0 && hi <= V.nx && hj <= V.ny) {
       const long long hn = V.base + (long long)hj * V.P + hi;
-      ht = tag[hn];
-      if ((ht & KIND_MASK) == K_FREE) hv = f[hn];
+      ht = a.m.tag[hn];
+      hv = f[hn];
+      if (PROL) {
+        const float e = coarse_interp(a, v, V, hi, hj);
+        if ((ht & KIND_MASK) == K_FREE) hv += e;
+      }
     }
     ps[lj][li] = hv;
     ts[lj][li] = ht;
   }
 }
 
-// Block sum of one exact FP32 product per thread (TwoProd into a two-float, warp
-// reduction, FP64 across warps in a fixed order), written to part[blockIdx.x].
-__device__ __forceinline__ void block_dot(float x, float y, double* part, double* sh) {
-  Acc<float> acc;
-  acc.zero();
-  acc.add(0, x, y);
+// Block sum of the threads' two-float dot accumulators (FP64 across warps, fixed order)
+// into part[blockIdx.x].
+__device__ __forceinline__ void block_dot_acc(Acc<float>& acc, double* part, double* sh) {
   double w[4];
   acc.warp_reduce(w);
   const int tid = linear_tid(), lane = tid & 31, wp = tid >> 5;
@@ -305,6 +362,9 @@ __device__ __forceinline__ void block_dot(float x, float y, double* part, double
 }
 
 // x += alpha p, r -= alpha q, z = dinv r (the first pre-smoothing sweep from zero); r.r.
+// Pointwise, FREE nodes only; a node is FREE exactly when its Jacobi factor is positive
+// (every free node lies on an active cell), so no tag is needed.  (q is also written at
+// BODY nodes, for the collapsed body rows, so the test matters.)
 __global__ void __launch_bounds__(NT) k_mg0_update(FineArgs a) {
   __shared__ double sh[NT / 32];
   const int v = a.tile_var[blockIdx.x];
@@ -312,83 +372,90 @@ __global__ void __launch_bounds__(NT) k_mg0_update(FineArgs a) {
   if (S.phase != PH_CG) return;
   const DevVariant& V = a.m.var[v];
   const int2 ij = a.tile_ij[blockIdx.x];
-  const int i = ij.x + threadIdx.x, j = ij.y + threadIdx.y;
+  const int tid = linear_tid(), col = tid % CTX, r0 = (tid / CTX) * FS;
+  const int i = ij.x + col;
   const float alpha = (float)S.alpha;
-  float rn = 0.0f;
-  if (i <= V.nx && j <= V.ny) {
-    const long long n = V.base + (long long)j * V.P + i;
-    if ((a.m.tag[n] & KIND_MASK) == K_FREE) {
-      const float pn = a.p[S.buf][n];
-      a.x[n] = a.x[n] + alpha * pn;
-      rn = a.r[n] - alpha * a.q[n];
-      a.r[n] = rn;
-      a.z[n] = a.dinv0[n] * rn;
+  const float* pc = a.p[S.buf];
+  float rn[FS];
+#pragma unroll
+  for (int u = 0; u < FS; ++u) {
+    rn[u] = 0.0f;
+    const int j = ij.y + r0 + u;
+    if (i <= V.nx && j <= V.ny) {
+      const long long n = V.base + (long long)j * V.P + i;
+      const float pn = pc[n], xn = a.x[n], rr = a.r[n], qn = a.q[n], dn = a.dinv0[n];
+      if (dn > 0.0f) {
+        a.x[n] = xn + alpha * pn;
+        rn[u] = rr - alpha * qn;
+        a.r[n] = rn[u];
+        a.z[n] = dn * rn[u];
+      }
     }
   }
-  block_dot(rn, rn, a.part, sh);
+  Acc<float> acc;
+  acc.zero();
+  acc.add4(0, rn, rn);
+  block_dot_acc(acc, a.part, sh);
 }
 
-// One Jacobi sweep on the fine level: zo = zi + dinv (r - A zi) at FREE nodes.  mode 1
-// also returns res = r - A zi instead (no update); mode 2 adds the partial r.zo.
-template <int MODE>
+// One Jacobi sweep on the fine level: zo = zi + dinv (r - A zi) (at nodes without an
+// unknown dinv = 0 and zi = 0, so zo = 0 there).  MODE 1: res = r - A zi at FREE nodes
+// (0 elsewhere).  MODE 2: MODE 0 and the partial r.zo.  PROL: zi is first corrected by
+// the prolongation from level 1 (the correction is not stored).
+template <int MODE, bool PROL>
 __global__ void __launch_bounds__(NT) k_mg0_sweep(FineArgs a, const float* zi, float* zo) {
-  __shared__ float ps[TY + 2][SW];
-  __shared__ uint8_t ts[TY + 2][SW];
+  __shared__ float ps[FH][FW];
+  __shared__ uint8_t ts[FH][FW];
   __shared__ double sh[NT / 32];
   const int v = a.tile_var[blockIdx.x];
   if (a.st[v].phase != PH_CG) return;
   const DevVariant& V = a.m.var[v];
   const int2 ij = a.tile_ij[blockIdx.x];
-  load_free_tile(V, ij, zi, a.m.tag, ps, ts);
-  __syncthreads();
-  const int i = ij.x + threadIdx.x, j = ij.y + threadIdx.y;
-  float rz = 0.0f, zv = 0.0f;
-  if (i <= V.nx && j <= V.ny) {
+  const int tid = linear_tid(), col = tid % CTX, r0 = (tid / CTX) * FS;
+  const int i = ij.x + col;
+  float rv[FS], dv[FS];
+#pragma unroll
+  for (int u = 0; u < FS; ++u) {
+    const int j = ij.y + r0 + u;
+    const bool in = i <= V.nx && j <= V.ny;
     const long long n = V.base + (long long)j * V.P + i;
-    if ((ts[threadIdx.y + 1][threadIdx.x + 1] & KIND_MASK) == K_FREE) {
-      const float y = q4_row<float>(ps, ts, threadIdx.x + 1, threadIdx.y + 1, n, V.P, a.m.K32, a.m.Vtot, V.kr32);
-      const float rr = a.r[n] - y;
-      if (MODE == 1) {
-        zo[n] = rr;
-      } else {
-        zv = ps[threadIdx.y + 1][threadIdx.x + 1] + a.dinv0[n] * rr;
-        zo[n] = zv;
-        rz = a.r[n];
-      }
+    rv[u] = in ? a.r[n] : 0.0f;
+    dv[u] = in && MODE != 1 ? a.dinv0[n] : 0.0f;
+  }
+  load_tile66<PROL>(a, v, V, ij, zi, ps, ts);
+  __syncthreads();
+  float zout[FS];
+#pragma unroll
+  for (int u = 0; u < FS; ++u) {
+    zout[u] = 0.0f;
+    const int j = ij.y + r0 + u;
+    if (i > V.nx || j > V.ny) continue;
+    const long long n = V.base + (long long)j * V.P + i;
+    const int li = 1 + col, lj = 1 + r0 + u;
+    const uint8_t tg = ts[lj][li];
+    if ((tg & KIND_MASK) != K_FREE) continue;   // zo, res are zero there already
+    const float y = q4_row<float, FW>(ps, ts, li, lj, n, V.P, a.m.K32, a.m.Vtot, V.kr32);
+    const float rr = rv[u] - y;
+    if (MODE == 1) {
+      zo[n] = rr;
+    } else {
+      zout[u] = ps[lj][li] + dv[u] * rr;
+      zo[n] = zout[u];
     }
   }
-  if (MODE == 2) block_dot(rz, zv, a.part, sh);
-}
-
-// t += P e (prolongation from level 1, FREE nodes).
-__global__ void __launch_bounds__(NT) k_mg0_prolong(FineArgs a, LvArgs c, const int* Lv) {
-  const int v = a.tile_var[blockIdx.x];
-  if (a.st[v].phase != PH_CG) return;
-  const DevVariant& V = a.m.var[v];
-  const int2 ij = a.tile_ij[blockIdx.x];
-  const int i = ij.x + threadIdx.x, j = ij.y + threadIdx.y;
-  if (i > V.nx || j > V.ny) return;
-  const long long n = V.base + (long long)j * V.P + i;
-  if ((a.m.tag[n] & KIND_MASK) != K_FREE) return;
-  const int2 dc = c.dims[v];
-  const long long oc = c.off[v];
-  int Ix[2], Iy[2];
-  double wx[2], wy[2];
-  const int nxp = parents(i, V.nx, Ix, wx), nyp = parents(j, V.ny, Iy, wy);
-  double e = 0.0;
-  for (int u = 0; u < nyp; ++u)
-    for (int t = 0; t < nxp; ++t) {
-      const long long k = oc + (long long)Iy[u] * (dc.x + 1) + Ix[t];
-      if (c.act[k]) e += wx[t] * wy[u] * (double)c.zb[k];
-    }
-  a.t[n] = a.t[n] + (float)e;
+  if (MODE == 2) {
+    Acc<float> acc;
+    acc.zero();
+    acc.add4(0, rv, zout);
+    block_dot_acc(acc, a.part, sh);
+  }
 }
 
 // p = z + beta p at FREE nodes, the body's p at BODY nodes, 0 elsewhere (into the other
-// buffer); q = A p at FREE and BODY nodes; partial p.q over FREE nodes.
+// buffer); q = A p at FREE and BODY nodes; partial p.q over FREE nodes.  z is the plane t.
 __global__ void __launch_bounds__(NT) k_mg0_apply(FineArgs a) {
-  __shared__ float ps[TY + 2][SW];
-  __shared__ uint8_t ts[TY + 2][SW];
+  __shared__ float ps[FH][FW];
+  __shared__ uint8_t ts[FH][FW];
   __shared__ double sh[NT / 32];
   const int v = a.tile_var[blockIdx.x];
   const VarState& S = a.st[v];
@@ -397,24 +464,27 @@ __global__ void __launch_bounds__(NT) k_mg0_apply(FineArgs a) {
   const int2 ij = a.tile_ij[blockIdx.x];
   const float beta = (float)S.beta;
   const float* pold = a.p[S.buf];
+  float* pnew = a.p[S.buf ^ 1];
   const float* pb = a.sb + 2 * a.B;
+  const int tid = linear_tid(), col = tid % CTX, r0 = (tid / CTX) * FS;
+  const int i = ij.x + col;
+  // t + beta p_old is zero at nodes without an unknown; BODY nodes take the body's value
   auto pval = [&](long long n, uint8_t tg) -> float {
-    const int kind = tg & KIND_MASK;
-    if (kind == K_FREE) return a.t[n] + beta * pold[n];
-    if (kind == K_BODY) return pb[V.body0 + a.m.bid[n]];
-    return 0.0f;
+    const float f = a.t[n] + beta * pold[n];
+    return (tg & KIND_MASK) == K_BODY ? pb[V.body0 + a.m.bid[n]] : f;
   };
-  const int tid = linear_tid();
-  const int i = ij.x + threadIdx.x, j = ij.y + threadIdx.y;
-  const bool in = i <= V.nx && j <= V.ny;
-  const long long n = V.base + (long long)j * V.P + i;
-  const uint8_t tg = in ? a.m.tag[n] : K_INACT;
-  const float pn = in ? pval(n, tg) : 0.0f;
-  ps[threadIdx.y + 1][threadIdx.x + 1] = pn;
-  ts[threadIdx.y + 1][threadIdx.x + 1] = tg;
-  if (tid < NHALO) {
+#pragma unroll
+  for (int u = 0; u < FS; ++u) {
+    const int j = ij.y + r0 + u;
+    const bool in = i <= V.nx && j <= V.ny;
+    const long long n = V.base + (long long)j * V.P + i;
+    const uint8_t tg = in ? a.m.tag[n] : K_INACT;
+    ps[1 + r0 + u][1 + col] = in ? pval(n, tg) : 0.0f;
+    ts[1 + r0 + u][1 + col] = tg;
+  }
+  if (tid < FNH) {
     int li, lj;
-    halo_pos(tid, li, lj);
+    halo_pos66(tid, li, lj);
     const int hi = ij.x - 1 + li, hj = ij.y - 1 + lj;
     uint8_t ht = K_INACT;
     float hv = 0.0f;
@@ -427,21 +497,29 @@ __global__ void __launch_bounds__(NT) k_mg0_apply(FineArgs a) {
     ts[lj][li] = ht;
   }
   __syncthreads();
-  float pq_p = 0.0f, pq_q = 0.0f;
-  if (in) {
-    const int kind = tg & KIND_MASK;
-    float* pnew = a.p[S.buf ^ 1];
-    if (kind == K_FREE || kind == K_BODY) {
-      const float y = q4_row<float>(ps, ts, threadIdx.x + 1, threadIdx.y + 1, n, V.P, a.m.K32, a.m.Vtot, V.kr32);
-      a.q[n] = y;
-      if (kind == K_FREE) {
-        pnew[n] = pn;
-        pq_p = pn;
-        pq_q = y;
-      }
+  float pp[FS], qq[FS];
+#pragma unroll
+  for (int u = 0; u < FS; ++u) {
+    pp[u] = 0.0f;
+    qq[u] = 0.0f;
+    const int j = ij.y + r0 + u;
+    if (i > V.nx || j > V.ny) continue;
+    const long long n = V.base + (long long)j * V.P + i;
+    const int li = 1 + col, lj = 1 + r0 + u;
+    const int kind = ts[lj][li] & KIND_MASK;
+    if (kind != K_FREE && kind != K_BODY) continue;
+    const float y = q4_row<float, FW>(ps, ts, li, lj, n, V.P, a.m.K32, a.m.Vtot, V.kr32);
+    a.q[n] = y;
+    if (kind == K_FREE) {
+      pnew[n] = ps[lj][li];
+      pp[u] = ps[lj][li];
+      qq[u] = y;
     }
   }
-  block_dot(pq_p, pq_q, a.part, sh);
+  Acc<float> acc;
+  acc.zero();
+  acc.add4(0, pp, qq);
+  block_dot_acc(acc, a.part, sh);
 }
 
 // ---------------------------------------------------------------- cycle kernels, coarse levels
@@ -460,20 +538,21 @@ __global__ void __launch_bounds__(256) k_mg_restrict(LvArgs c, int lc, const int
     const int2 df = fine0 ? make_int2(V.nx, V.ny) : dims_f[q.v];
     const long long of = fine0 ? 0 : off_f[q.v];
     const int fx = fine_of(q.i, df.x), fy = fine_of(q.j, df.y);
-    double s = 0.0;
-    for (int ay = fy - 1; ay <= fy + 1; ++ay) {
-      if (ay < 0 || ay > df.y) continue;
-      const double wy = pw(ay, df.y, q.j);
-      if (wy == 0.0) continue;
-      for (int ax = fx - 1; ax <= fx + 1; ++ax) {
-        if (ax < 0 || ax > df.x) continue;
-        const double w = pw(ax, df.x, q.i) * wy;
-        if (w == 0.0) continue;
+    float s = 0.0f;
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy) {
+      const int ay = fy + dy;
+      const float wy = (ay < 0 || ay > df.y) ? 0.0f : pwf(ay, df.y, q.j);
+#pragma unroll
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int ax = fx + dx;
+        const float w = (ax < 0 || ax > df.x) ? 0.0f : pwf(ax, df.x, q.i) * wy;
+        if (w == 0.0f) continue;
         const long long na = fine0 ? V.base + (long long)ay * V.P + ax : of + (long long)ay * (df.x + 1) + ax;
-        s += w * (double)res_f[na];     // res is zero at every node without an unknown
+        s += w * res_f[na];     // res is zero at every node without an unknown
       }
     }
-    rc = (float)s;
+    rc = s;
   }
   c.r[q.k] = rc;
   c.za[q.k] = c.dinv[q.k] * rc;
@@ -486,38 +565,35 @@ __global__ void __launch_bounds__(256) k_mg_sweep(LvArgs c, int l, const int* Lv
   LvNode q;
   if (!lv_node(c.off, c.dims, c.blkvar, q)) return;
   if (st[q.v].phase != PH_CG || l >= Lv[q.v] - 1) return;
-  float out = 0.0f;
-  if (c.act[q.k]) {
-    float y = 0.0f;
-    for (int dy = -1; dy <= 1; ++dy)
-      for (int dx = -1; dx <= 1; ++dx) {
-        const int bi = q.i + dx, bj = q.j + dy;
-        if (bi < 0 || bj < 0 || bi > q.nx || bj > q.ny) continue;
-        y += c.A[((dy + 1) * 3 + dx + 1) * c.n + q.k] * zi[q.k + (long long)dy * (q.nx + 1) + dx];
-      }
-    const float rr = c.r[q.k] - y;
-    out = MODE == 1 ? rr : zi[q.k] + c.dinv[q.k] * rr;
-  }
-  zo[q.k] = out;
+  // the stencil, r, dinv and z are zero at inactive nodes: no activity test needed
+  float y = 0.0f;
+#pragma unroll
+  for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+    for (int dx = -1; dx <= 1; ++dx) {
+      const int bi = q.i + dx, bj = q.j + dy;
+      if (bi < 0 || bj < 0 || bi > q.nx || bj > q.ny) continue;
+      y += c.A[((dy + 1) * 3 + dx + 1) * c.n + q.k] * zi[q.k + (long long)dy * (q.nx + 1) + dx];
+    }
+  const float rr = c.r[q.k] - y;
+  zo[q.k] = MODE == 1 ? rr : zi[q.k] + c.dinv[q.k] * rr;
 }
 
 // zb_f += P zb_c on a packed fine level (l >= 1).
 __global__ void __launch_bounds__(256) k_mg_prolong(LvArgs f, LvArgs c, int l, const int* Lv, const VarState* st) {
   LvNode q;
   if (!lv_node(f.off, f.dims, f.blkvar, q)) return;
-  if (st[q.v].phase != PH_CG || l >= Lv[q.v] - 1 || !f.act[q.k]) return;
+  if (st[q.v].phase != PH_CG || l >= Lv[q.v] - 1) return;
+  const uint8_t act = f.act[q.k];
   const int2 dc = c.dims[q.v];
   const long long oc = c.off[q.v];
   int Ix[2], Iy[2];
-  double wx[2], wy[2];
-  const int nxp = parents(q.i, q.nx, Ix, wx), nyp = parents(q.j, q.ny, Iy, wy);
-  double e = 0.0;
+  float wx[2], wy[2];
+  const int nxp = parentsf(q.i, q.nx, Ix, wx), nyp = parentsf(q.j, q.ny, Iy, wy);
+  float e = 0.0f;     // coarse values are zero at inactive coarse nodes
   for (int u = 0; u < nyp; ++u)
-    for (int t = 0; t < nxp; ++t) {
-      const long long k = oc + (long long)Iy[u] * (dc.x + 1) + Ix[t];
-      if (c.act[k]) e += wx[t] * wy[u] * (double)c.zb[k];
-    }
-  f.zb[q.k] = f.zb[q.k] + (float)e;
+    for (int t = 0; t < nxp; ++t) e += wx[t] * wy[u] * c.zb[oc + (long long)Iy[u] * (dc.x + 1) + Ix[t]];
+  if (act) f.zb[q.k] = f.zb[q.k] + e;
 }
 
 // Coarsest level of every variant (its own level Lv - 1): a fixed number of Jacobi
@@ -740,10 +816,12 @@ void mg_setup(Batch& b) {
       *pl = (float*)dev_alloc(b, V);
       PF_CUDA(cudaMemsetAsync(*pl, 0, V, b.stream));
     }
-    b.mg_part = (double*)dev_alloc(b, std::max<long long>(1, b.T) * sizeof(double));
+    b.mg_part = (double*)dev_alloc(b, std::max<long long>(1, b.Tcg) * sizeof(double));
     b.mg_Abb = (double*)dev_alloc(b, std::max(1, b.B) * sizeof(double));
+    // the fine-level kernels run on the fused-CG tiles (64 x 16), variant-major
     std::vector<long long> t0(b.nv + 1, 0);
-    for (int v = 0; v < b.nv; ++v) t0[v + 1] = t0[v] + (long long)b.hv[v].tiles_x * b.hv[v].tiles_y;
+    for (int v = 0; v < b.nv; ++v)
+      t0[v + 1] = t0[v] + (long long)((b.hv[v].g.nx + 1 + CTX - 1) / CTX) * ((b.hv[v].g.ny + 1 + CTY - 1) / CTY);
     b.d_tile0 = (long long*)dev_alloc(b, (b.nv + 1) * sizeof(long long));
     PF_CUDA(cudaMemcpyAsync(b.d_tile0, t0.data(), (b.nv + 1) * sizeof(long long), cudaMemcpyHostToDevice, b.stream));
   }
@@ -838,8 +916,8 @@ static void mg_layout(Batch& b) {
 void launch_pcg_chunk(Batch& b, int iters, cudaStream_t s) {
   FineArgs a;
   a.m = mesh_view(b);
-  a.tile_var = b.tile_var;
-  a.tile_ij = b.tile_ij;
+  a.tile_var = b.tile_cg_var;
+  a.tile_ij = b.tile_cg_ij;
   a.st = b.state;
   a.dinv0 = b.mg_dinv0;
   a.x = b.mg_x;
@@ -853,6 +931,9 @@ void launch_pcg_chunk(Batch& b, int iters, cudaStream_t s) {
   a.sb = b.sb32;
   a.B = std::max(1, b.B);
   a.part = b.mg_part;
+  a.c_off = b.mg[1].d_off;
+  a.c_dims = b.mg[1].d_dims;
+  a.c_zb = b.mg[1].zb;
   FinArgs f;
   f.st = b.state;
   f.prm = b.params;
@@ -867,15 +948,15 @@ void launch_pcg_chunk(Batch& b, int iters, cudaStream_t s) {
   CoarseTab ct;
   std::memset(&ct, 0, sizeof(ct));
   for (int l = 1; l < b.mg_L; ++l) ct.lv[l] = lv_args(b.mg[l]);
-  const unsigned T = (unsigned)b.T, nv = (unsigned)b.nv;
+  const unsigned T = (unsigned)b.Tcg, nv = (unsigned)b.nv;
   const dim3 blk(TX, TY);
   const int L = b.mg_L;
   for (int it = 0; it < iters; ++it) {
     k_mg0_update<<<T, blk, 0, s>>>(a);
     k_mg_finA<<<nv, blk, 0, s>>>(f);
     // descent: level 0 second sweep (z -> t), residual, restriction to level 1
-    k_mg0_sweep<0><<<T, blk, 0, s>>>(a, b.mg_z, b.mg_t);
-    k_mg0_sweep<1><<<T, blk, 0, s>>>(a, b.mg_t, b.mg_res);
+    k_mg0_sweep<0, false><<<T, blk, 0, s>>>(a, b.mg_z, b.mg_t);
+    k_mg0_sweep<1, false><<<T, blk, 0, s>>>(a, b.mg_t, b.mg_res);
     for (int l = 1; l < L; ++l) {
       MgLevel& M = b.mg[l];
       if (M.nblk == 0) continue;
@@ -901,9 +982,9 @@ void launch_pcg_chunk(Batch& b, int iters, cudaStream_t s) {
       k_mg_sweep<0><<<(unsigned)M.nblk, 256, 0, s>>>(c, l, b.d_mg_Lv, b.state, M.zb, M.za);
       k_mg_sweep<0><<<(unsigned)M.nblk, 256, 0, s>>>(c, l, b.d_mg_Lv, b.state, M.za, M.zb);
     }
-    k_mg0_prolong<<<T, blk, 0, s>>>(a, lv_args(b.mg[1]), b.d_mg_Lv);
-    k_mg0_sweep<0><<<T, blk, 0, s>>>(a, b.mg_t, b.mg_z);
-    k_mg0_sweep<2><<<T, blk, 0, s>>>(a, b.mg_z, b.mg_t);
+    // post-smoothing of level 0, the first sweep on t + P e (the correction from level 1)
+    k_mg0_sweep<0, true><<<T, blk, 0, s>>>(a, b.mg_t, b.mg_z);
+    k_mg0_sweep<2, false><<<T, blk, 0, s>>>(a, b.mg_z, b.mg_t);
     k_mg_finB<<<nv, blk, 0, s>>>(f);
     k_mg0_apply<<<T, blk, 0, s>>>(a);
     k_mg_finC<<<nv, blk, 0, s>>>(f);
