@@ -16,6 +16,10 @@ Readings taken where the paper is silent:
     on the logical grid, d_n <- (d_W + d_E + d_S + d_N) / 4 summed in that order,
     over nodes that are outside every body and not on the outer ring.
 
+Polygonal bodies and the Kutta condition (the wake point held at the body's value)
+follow `oracle.shapes`; they are appended after the circles, so body k < n_circles is
+a circle and the others are polygons in the given order.
+
 Every expression is written so that it is a sequence of individually rounded IEEE
 float64 operations (numpy applies no fused multiply-add), which makes the result
 reproducible bit for bit by any implementation that performs the same operations.
@@ -25,6 +29,8 @@ from __future__ import annotations
 from dataclasses import dataclass
 
 import numpy as np
+
+from . import shapes as SH
 
 FREE, DIRICHLET, BODY, INACTIVE = 0, 1, 2, 3
 BC_DIRICHLET_UY, BC_NATURAL = 0, 1
@@ -45,23 +51,50 @@ class Mesh:
     kind: np.ndarray     # (ny+1, nx+1) int8: FREE / DIRICHLET / BODY / INACTIVE
     body: np.ndarray     # (ny+1, nx+1) int32: body index for BODY nodes (and inside nodes), else -1
     active: np.ndarray   # (ny, nx) bool: cell (i, j) active
-    bodies: np.ndarray   # (n_bodies, 3)
+    bodies: np.ndarray   # (n_bodies, 3): circles (cx, cy, r); polygons (ref x, ref y, 0)
     bc: tuple
     dx0: np.ndarray      # initial (projection) displacement, before smoothing
     dy0: np.ndarray
+    polygons: tuple = ()          # polygon bodies (after the circles)
+    wake: np.ndarray = None       # (ny+1, nx+1) bool: Kutta wake nodes (held at their body's value)
+    wake_node: tuple = ()         # per polygon: flat index of its wake node, or -1
 
     @property
     def n_nodes(self):
         return (self.nx + 1) * (self.ny + 1)
 
 
-def validate_inputs(grid, bodies):
-    """Host checks: positive sizes, bodies disjoint and at least 2h inside the box."""
+def body_boxes(bodies, polygons):
+    """Axis-aligned bounding box (xmin, xmax, ymin, ymax) of every body."""
+    out = [(cx - r, cx + r, cy - r, cy + r) for cx, cy, r in np.asarray(bodies).reshape(-1, 3)]
+    for p in polygons:
+        v = p.vertices
+        out.append((v[:, 0].min(), v[:, 0].max(), v[:, 1].min(), v[:, 1].max()))
+    return out
+
+
+def validate_inputs(grid, bodies, polygons=()):
+    """Host checks: positive sizes, bodies disjoint and at least 2h inside the box.
+    Polygons need at least 3 vertices in counter-clockwise order, and their bounding
+    boxes may not overlap any other body's (a conservative disjointness test)."""
     x0, x1, y0, y1, nx, ny = grid
     if nx < 2 or ny < 2 or not (x1 > x0) or not (y1 > y0):
         raise MeshError("invalid grid")
     hx = (x1 - x0) / nx
     hy = (y1 - y0) / ny
+    for k, p in enumerate(polygons):
+        if len(p.vertices) < 3 or not (SH.signed_area(p.vertices) > 0):
+            raise MeshError(f"polygon {k}: needs >= 3 vertices in counter-clockwise order")
+        if p.kutta >= len(p.vertices):
+            raise MeshError(f"polygon {k}: Kutta vertex out of range")
+    nc = len(np.asarray(bodies).reshape(-1, 3))
+    boxes = body_boxes(bodies, polygons)
+    for k, (bx0, bx1, by0, by1) in enumerate(boxes[nc:], start=nc):
+        if bx0 < x0 + 2 * hx or bx1 > x1 - 2 * hx or by0 < y0 + 2 * hy or by1 > y1 - 2 * hy:
+            raise MeshError(f"body {k} is within 2h of the outer boundary")
+        for c, (cx0, cx1, cy0, cy1) in enumerate(boxes):
+            if c != k and not (bx1 < cx0 or cx1 < bx0 or by1 < cy0 or cy1 < by0):
+                raise MeshError(f"bodies {k} and {c} have overlapping bounding boxes")
     b = np.asarray(bodies, dtype=np.float64).reshape(-1, 3)
     for k, (cx, cy, r) in enumerate(b):
         if not (r > 0):
@@ -88,13 +121,19 @@ def background_grid(grid):
     return xg, yg
 
 
-def classify(xg, yg, bodies):
+def classify(xg, yg, bodies, polygons=()):
     """Inside test of every node against every body; returns body index or -1."""
     body = np.full(xg.shape, -1, dtype=np.int32)
     for k, (cx, cy, r) in enumerate(bodies):
         dx = xg - cx
         dy = yg - cy
         inside = (dx * dx + dy * dy) <= r * r
+        if np.any(inside & (body >= 0)):
+            raise MeshError("node inside two bodies")
+        body[inside] = k
+    for q, p in enumerate(polygons):
+        k = len(bodies) + q
+        inside = SH.inside_polygon(xg, yg, p.vertices)
         if np.any(inside & (body >= 0)):
             raise MeshError("node inside two bodies")
         body[inside] = k
@@ -128,10 +167,16 @@ def node_kinds(body, bc):
     return kind, active
 
 
-def project(xg, yg, body, kind, bodies):
-    """Initial displacement: radial projection of every BODY node onto its circle."""
+def project(xg, yg, body, kind, bodies, polygons=()):
+    """Initial displacement: radial projection of every BODY node onto its circle, or
+    the nearest point of its polygon."""
     dx0 = np.zeros_like(xg)
     dy0 = np.zeros_like(yg)
+    for q, p in enumerate(polygons):
+        m = (kind == BODY) & (body == len(bodies) + q)
+        qx, qy = SH.nearest_on_polygon(xg[m], yg[m], p.vertices)
+        dx0[m] = qx - xg[m]
+        dy0[m] = qy - yg[m]
     for k, (cx, cy, r) in enumerate(bodies):
         m = (kind == BODY) & (body == k)
         ex = xg[m] - cx
@@ -146,9 +191,12 @@ def project(xg, yg, body, kind, bodies):
     return dx0, dy0
 
 
-def smoothing_mask(kind, body):
-    """Nodes updated by the Jacobi sweeps: outside every body, not on the outer ring."""
+def smoothing_mask(kind, body, wake=None):
+    """Nodes updated by the Jacobi sweeps: outside every body, not on the outer ring and
+    not a Kutta wake node (which keeps its position on the wake line)."""
     m = body < 0
+    if wake is not None:
+        m = m & ~wake
     m[0, :] = False
     m[-1, :] = False
     m[:, 0] = False
@@ -170,18 +218,45 @@ def jacobi_sweeps(d, mask, sweeps):
     return d
 
 
-def build_mesh(grid, bodies, sweeps, bc=(0, 0, 0, 0)) -> Mesh:
-    """Background grid -> classify -> project -> S smoothing sweeps -> x = x_grid + d."""
-    bodies = validate_inputs(grid, bodies)
+def kutta_nodes(xg, yg, body, kind, dx0, dy0, bodies, polygons, hx):
+    """Kutta condition of every polygon that asks for it: the fluid node nearest to the
+    wake point W = T + hx w (T the trailing edge, w the bisector) moves onto W (it stays
+    a fluid node; the solve holds it at the body's value, `oracle.system.kutta_rows`).  Returns the wake-node mask and, per polygon, the
+    flat index of its wake node (-1 without a Kutta condition)."""
+    wake = np.zeros(xg.shape, dtype=bool)
+    wake_node = []
+    for q, p in enumerate(polygons):
+        if p.kutta < 0:
+            wake_node.append(-1)
+            continue
+        k = len(bodies) + q
+        T, _, W = SH.kutta_points(p, hx)
+        nw = SH.nearest_node(xg, yg, kind == FREE, W[0], W[1])
+        j, i = divmod(nw, xg.shape[1])
+        dx0[j, i] = W[0] - xg[j, i]
+        dy0[j, i] = W[1] - yg[j, i]
+        wake[j, i] = True
+        wake_node.append(nw)
+    return wake, tuple(wake_node)
+
+
+def build_mesh(grid, bodies, sweeps, bc=(0, 0, 0, 0), polygons=()) -> Mesh:
+    """Background grid -> classify -> project (and Kutta points) -> S smoothing sweeps ->
+    x = x_grid + d."""
+    polygons = tuple(polygons)
+    bodies = validate_inputs(grid, bodies, polygons)
     x0, x1, y0, y1, nx, ny = grid
     xg, yg = background_grid(grid)
-    body = classify(xg, yg, bodies)
+    body = classify(xg, yg, bodies, polygons)
     kind, active = node_kinds(body, bc)
-    dx0, dy0 = project(xg, yg, body, kind, bodies)
-    mask = smoothing_mask(kind, body)
+    dx0, dy0 = project(xg, yg, body, kind, bodies, polygons)
+    wake, wake_node = kutta_nodes(xg, yg, body, kind, dx0, dy0, bodies, polygons, (x1 - x0) / nx)
+    mask = smoothing_mask(kind, body, wake)
     dx = jacobi_sweeps(dx0, mask, sweeps)
     dy = jacobi_sweeps(dy0, mask, sweeps)
-    return Mesh(nx, ny, xg + dx, yg + dy, xg, yg, kind, body, active, bodies, tuple(bc), dx0, dy0)
+    rows = np.concatenate([bodies, np.array([[p.ref[0], p.ref[1], 0.0] for p in polygons]).reshape(-1, 3)])
+    return Mesh(nx, ny, xg + dx, yg + dy, xg, yg, kind, body, active, rows, tuple(bc), dx0, dy0, polygons, wake,
+                wake_node)
 
 
 def cell_coords(mesh: Mesh):

@@ -31,11 +31,13 @@ def boundary_edges(mesh: Mesh, k: int):
     cn = cell_nodes(nx, ny)
     out = []
     js, is_ = np.nonzero(mesh.active)
+    wake = mesh.wake.ravel() if mesh.wake is not None else np.zeros(kind.shape, dtype=bool)
     for j, i in zip(js, is_):                      # row-major order
         nodes = cn[j, i]
         for a in range(4):
             na, nb_ = nodes[a], nodes[(a + 1) % 4]
             if (kind[na] == BODY and kind[nb_] == BODY and body[na] == k and body[nb_] == k
+                    and not wake[na] and not wake[nb_]
                     and (X[na] != X[nb_] or Y[na] != Y[nb_])):
                 out.append((j, i, a))
     return out

@@ -154,3 +154,12 @@ def solve_schur(system: System, kind, body):
     C = np.linalg.solve(S, rhs) if nb else np.zeros(0)
     u = np.concatenate([psi0 + Phi @ C, C])
     return u, expand(system, u), S
+
+
+def solve_kutta(system: System, mesh):
+    """Solution of the reduced system with the Kutta rows of `system.kutta_rows` (a sparse
+    LU of the non-symmetric matrix); returns (u, nodal psi)."""
+    from .system import kutta_rows
+    A, b = kutta_rows(system, mesh)
+    u = spla.spsolve(A.tocsc(), b) if A.shape[0] else np.zeros(0)
+    return u, expand(system, u)

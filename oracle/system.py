@@ -112,3 +112,25 @@ def full_operator_apply(system: System, v):
     y = np.zeros_like(v)
     np.add.at(y, system.cells.ravel(), ye.ravel())
     return y
+
+
+def kutta_rows(system: System, mesh: Mesh):
+    """The reduced system with the Kutta condition (section "Boundary Conditions"): for
+    every polygon body k with a Kutta condition, its equation - the collapsed body row,
+    i.e. zero circulation around the body - is replaced by psi(W) - C_k = 0, W the wake
+    node on the trailing-edge bisector, so that the body streamline psi = C_k leaves the
+    trailing edge along the bisector and the circulation follows from the solution.
+    Returns (A, b) of the modified, no longer symmetric, system."""
+    A = system.A.tolil(copy=True)
+    b = system.b.copy()
+    n_circ = system.n_bodies - len(mesh.polygons)
+    for q, nw in enumerate(mesh.wake_node):
+        if nw < 0:
+            continue
+        row = system.n_free + n_circ + q
+        A.rows[row] = []
+        A.data[row] = []
+        A[row, system.dof[nw]] = 1.0
+        A[row, row] = -1.0
+        b[row] = 0.0
+    return A.tocsr(), b

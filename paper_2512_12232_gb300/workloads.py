@@ -120,6 +120,24 @@ def gradient_study(n_variants: int = 64, seed: int = 1, nx: int = 1024, sweeps: 
             for _ in range(n_variants)]
 
 
+PAPER_TABLE1_DELTAS = (0.3, 0.4, 0.5, 0.6, 0.7)
+
+
+def paper_channel_case(delta: float, nx: int = 403, ny: int = 201, sweeps: int = 60) -> Case:
+    """The paper's channel layout (Results section, Table 1): [0,1]x[0,0.5] with walls
+    psi = 0 (bottom) and psi = U/2 (top) and natural inlet and outlet; three cylinders of
+    diameter 0.2 on the axis y = 0.25 and two of diameter 0.1 above and below it with
+    centre distance h_c = delta * h_d (h_d = 0.5, the channel height).  The x positions
+    are assumed (the paper gives them only in a figure); the grid is chosen so that no
+    node lies exactly on a circle.  With U = 2 the walls carry psi = 0 and 1."""
+    hd, yc = 0.5, 0.25
+    hc = delta * hd
+    bodies = np.array([[0.15, yc, 0.1], [0.55, yc, 0.1], [0.85, yc, 0.1],
+                       [0.35, yc - hc / 2, 0.05], [0.35, yc + hc / 2, 0.05]])
+    return Case(0.0, 1.0, 0.0, 0.5, nx, ny, bodies, sweeps, bc=(BC_NATURAL, BC_NATURAL, BC_DIRICHLET_UY, BC_DIRICHLET_UY),
+                name=f"paper_channel_d{delta:g}", meta={"delta": delta})
+
+
 def random_vector(n: int, seed: int) -> np.ndarray:
     """Seeded standard-normal float64 vector (used as an operator input)."""
     return np.random.default_rng(seed).standard_normal(n)

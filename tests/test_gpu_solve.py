@@ -307,3 +307,26 @@ def test_mg_preconditioner_needs_mixed_precision(api):
         assert res.status == 1
         res = api.psi_solve(g, U=1.0, tol=1e-8, preconditioner=5, raise_on_failure=False)
         assert res.status == 1
+
+
+@pytest.mark.parametrize("pre", ["none", "mg"])
+def test_paper_channel_gap_ratio_sweep(api, pre):
+    """The paper's channel (walls psi = 0 / 1, natural inlet and outlet) at the gap ratios
+    of Table 1 as one batch: body values equal the oracle's, and the table's structure
+    holds (psi_1 = 0.5 on the axis, psi_4 + psi_5 = 1, CoPFI = Q54 / delta below 1 and
+    rising with delta).  The printed values themselves are parity-unpinned (the cylinder
+    x positions exist only in a figure)."""
+    cases = [W.paper_channel_case(d) for d in W.PAPER_TABLE1_DELTAS]
+    prec = api.PF_FP64 if pre == "none" else api.PF_MIXED
+    with api.batch_build(cases) as g:
+        res = api.psi_solve(g, U=2.0, tol=1e-13 if pre == "none" else 1e-12, precision=prec, preconditioner=pre)
+        cps = [api.copfi(g, v, 3, 4, 2.0) for v in range(len(cases))]
+    assert res.status == 0
+    prev = -1.0
+    for v, (c, (cp, q)) in enumerate(zip(cases, cps)):
+        m, s, u, psi_ref = oracle_solution(c, 2.0)
+        C = res.body_psi[5 * v:5 * v + 5]
+        np.testing.assert_allclose(C, u[s.n_free:], rtol=0, atol=BODY_TOL)
+        assert np.abs(C[:3] - 0.5).max() < 1e-8 and abs(C[3] + C[4] - 1.0) < 1e-8
+        assert abs(cp - q / c.meta["delta"]) < 1e-12 and 0.0 < cp < 1.0 and cp > prev
+        prev = cp

@@ -1,0 +1,133 @@
+"""Pins of the oracle's polygonal bodies and Kutta condition (oracle/shapes.py):
+brute-force and closed-form geometry, a many-sided polygon against the circle, the
+exact flow past an ellipse, and the exact flow past a Joukowski airfoil with the
+circulation of the Kutta condition (paper, section "Boundary Conditions")."""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+from oracle import mesh as M, post as P, shapes as SH, solve as SV, system as S
+
+
+def test_inside_polygon_matches_a_brute_force_winding_number():
+    rng = np.random.default_rng(0)
+    v = SH.ellipse(1.3, 0.6, 37, cx=0.2, cy=-0.1, angle=0.4).vertices
+    px, py = rng.uniform(-1.5, 1.5, 2000), rng.uniform(-1.2, 1.2, 2000)
+    ins = SH.inside_polygon(px, py, v)
+    for x, y, got in zip(px[:400], py[:400], ins[:400]):
+        ang = np.arctan2(v[:, 1] - y, v[:, 0] - x)
+        wind = np.sum((np.diff(np.append(ang, ang[0])) + np.pi) % (2 * np.pi) - np.pi) / (2 * np.pi)
+        assert got == (abs(round(wind)) == 1)
+
+
+def test_nearest_point_on_a_square():
+    sq = np.array([[0.0, 0.0], [2.0, 0.0], [2.0, 1.0], [0.0, 1.0]])
+    qx, qy = SH.nearest_on_polygon(np.array([1.0, 0.3, 1.9, 3.0]), np.array([0.2, 0.5, 0.95, 2.0]), sq)
+    np.testing.assert_array_equal(qx, [1.0, 0.0, 1.9, 2.0])
+    np.testing.assert_array_equal(qy, [0.0, 0.5, 1.0, 1.0])
+
+
+def test_many_sided_polygon_meshes_like_the_circle():
+    """A regular 4096-gon inscribed in a circle gives the circle's classification except
+    for nodes within the polygon's sagitta of the circle, and nearly the same flow."""
+    grid = (-4.0, 4.0, -2.0, 2.0, 96, 48)
+    r = 0.77
+    t = 2.0 * np.pi * (np.arange(4096) + 0.5) / 4096
+    poly = SH.Polygon(np.stack([0.1 + r * np.cos(t), 0.05 + r * np.sin(t)], axis=1), ref=(0.1, 0.05))
+    mc = M.build_mesh(grid, np.array([[0.1, 0.05, r]]), 20)
+    mp = M.build_mesh(grid, np.zeros((0, 3)), 20, polygons=[poly])
+    dist = np.hypot(mc.xg - 0.1, mc.yg - 0.05)
+    band = np.abs(dist - r) < r * (1 - np.cos(np.pi / 4096)) * 4
+    assert np.array_equal((mc.kind == M.BODY)[~band], (mp.kind == M.BODY)[~band])
+    # the nearest point of a chord and the radial projection differ by at most the node's
+    # distance to the boundary times the chord's turn, h * pi / 4096
+    tol = (8.0 / 96) * np.pi / 4096 * 1.01
+    assert np.abs(mp.x - mc.x).max() < tol and np.abs(mp.y - mc.y).max() < tol
+    uc, _ = SV.solve_direct(S.assemble(mc, 1.0))
+    up, _ = SV.solve_direct(S.assemble(mp, 1.0))
+    assert abs(uc[-1] - up[-1]) < 1e-4
+
+
+def test_ellipse_flow_converges_to_the_exact_solution():
+    """Exact Dirichlet data of the flow past an ellipse (no circulation): the body value is
+    the exact 0 up to the discretisation, the nodal error falls with refinement, and the
+    boundary-edge speed approaches the exact surface speed."""
+    a, b, alpha = 0.8, 0.4, np.radians(10.0)
+    errs = []
+    for nx in (96, 192):
+        ell = SH.ellipse(a, b, 720, angle=-alpha)
+        grid = (-4.0, 4.0, -2.0, 2.0, nx, nx // 2)
+        m = M.build_mesh(grid, np.zeros((0, 3)), nx // 4, polygons=[ell])
+        g = SH.ellipse_psi(m.x.ravel(), m.y.ravel(), a, b, 1.0, alpha)
+        s = S.assemble(m, g=g)
+        u, psi = SV.solve_direct(s)
+        live = (m.kind == M.FREE).ravel()
+        errs.append(np.abs(psi - g)[live].max())
+        assert abs(u[-1]) < 0.02
+    assert errs[1] < 0.6 * errs[0], errs
+
+
+def _airfoil_case(nx, alpha_deg, kutta=True, ny=None):
+    af = SH.joukowski_airfoil(0.5, 0.08, 400, alpha=np.radians(alpha_deg))
+    if not kutta:
+        af.kutta = -1
+    grid = (-3.0, 3.0, -1.5, 1.5, nx, ny or nx // 2)
+    m = M.build_mesh(grid, np.zeros((0, 3)), nx // 4, polygons=[af])
+    g, psi_b = SH.joukowski_psi(m.x.ravel(), m.y.ravel(), af, 1.0, kutta=True)
+    return af, m, S.assemble(m, g=g), psi_b
+
+
+def test_kutta_condition_recovers_the_joukowski_circulation():
+    """Joukowski airfoil at 6 degrees with the exact Dirichlet data of the flow with the
+    Kutta circulation Gamma = -4 pi U R sin(alpha): with the wake point held at the body's
+    value the body value converges to the exact one; with the zero-circulation equation it
+    stays far away.  A wake direction pointing into the body (a sign mistake) fails."""
+    errs = []
+    for nx in (128, 256, 512):
+        af, m, s, psi_b = _airfoil_case(nx, 6.0)
+        u, psi = SV.solve_kutta(s, m)
+        errs.append(abs(u[s.n_free] - psi_b))
+        u0, _ = SV.solve_direct(s)
+        assert abs(u0[s.n_free] - psi_b) > 0.1
+    assert errs[2] < 0.5 * errs[1] < 0.25 * errs[0] and errs[2] < 1e-3, errs
+    # planted mistake: the wake point on the other side of the trailing edge
+    af, m, s, psi_b = _airfoil_case(256, 6.0)
+    T, w, W = SH.kutta_points(af, 6.0 / 256)
+    bad = SH.nearest_node(m.xg, m.yg, m.kind == M.FREE, T[0] - 4 * (W[0] - T[0]), T[1] - 4 * (W[1] - T[1]) + 0.1)
+    m2 = M.Mesh(**{**m.__dict__, "wake_node": (bad,)})
+    u2, _ = SV.solve_kutta(S.assemble(m2, g=s.g), m2)
+    assert abs(u2[s.n_free] - psi_b) > 10 * errs[1]
+
+
+def test_kutta_condition_is_inactive_for_a_symmetric_flow():
+    """At zero angle of attack the symmetric airfoil carries no circulation: the
+    zero-circulation body value vanishes and the Kutta body value nearly does (the grid has
+    no node on the symmetry axis, so only the wake node, moved onto the axis, breaks the
+    mirror symmetry of the mesh), far below the 0.066 of 6 degrees."""
+    af, m, s, psi_b = _airfoil_case(128, 0.0, ny=65)
+    s = S.assemble(m, 1.0)
+    u, _ = SV.solve_kutta(s, m)
+    u0, _ = SV.solve_direct(s)
+    assert abs(u0[s.n_free]) < 1e-6 and abs(u[s.n_free]) < 1e-4
+
+
+def test_kutta_rows_replace_only_the_body_equation():
+    af, m, s, psi_b = _airfoil_case(128, 6.0)
+    A, b = S.kutta_rows(s, m)
+    n = s.n_free
+    assert (A[:n] != s.A[:n]).nnz == 0 and np.array_equal(b[:n], s.b[:n])
+    row = A[n].toarray().ravel()
+    assert row[n] == -1.0 and row[s.dof[m.wake_node[0]]] == 1.0 and np.count_nonzero(row) == 2
+    assert m.kind.ravel()[m.wake_node[0]] == M.FREE and m.wake.sum() == 1
+    # the wake node sits on the wake line, one grid spacing from the trailing edge
+    T, w, W = SH.kutta_points(af, 6.0 / 128)
+    assert m.x.ravel()[m.wake_node[0]] == W[0] and m.y.ravel()[m.wake_node[0]] == W[1]
+
+
+def test_boundary_edges_of_a_polygon_skip_the_wake_node():
+    af, m, s, psi_b = _airfoil_case(128, 6.0)
+    u, psi = SV.solve_kutta(s, m)
+    edges = P.boundary_edges(m, 0)
+    assert len(edges) > 20
+    th, ut = P.surface_velocity(m, psi, u[s.n_free:], 0)
+    assert np.all(np.isfinite(ut)) and th.size == len(edges)

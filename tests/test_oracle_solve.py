@@ -171,17 +171,7 @@ def test_paper_validation_channel_body_value_is_one_half():
 
 
 def paper_like_channel(delta, nx=403, ny=201, S_=60):
-    """Five cylinders in the channel [0,1]x[0,0.5] (walls psi = 0 / 1, natural inlet
-    and outlet): 1, 2, 3 of D = 0.2 on the axis, 4 and 5 of D = 0.1 transverse with
-    centre distance h_c = delta * h_d.  The x positions are an assumption; the grid
-    is chosen so that no node lies exactly on a circle (no rounding-decided ties)."""
-    hd = 0.5
-    yc = 0.25
-    hc = delta * hd
-    bodies = np.array([[0.15, yc, 0.1], [0.55, yc, 0.1], [0.85, yc, 0.1],
-                       [0.35, yc - hc / 2, 0.05], [0.35, yc + hc / 2, 0.05]])
-    return W.Case(0.0, 1.0, 0.0, 0.5, nx, ny, bodies, S_,
-                  bc=(W.BC_NATURAL, W.BC_NATURAL, W.BC_DIRICHLET_UY, W.BC_DIRICHLET_UY))
+    return W.paper_channel_case(delta, nx, ny, S_)
 
 
 def test_table1_structure_symmetry_and_trend():
