@@ -176,6 +176,39 @@ pf_status pf_set_allocator(pf_alloc_fn alloc, pf_free_fn free_fn, void* ctx);
 pf_status pf_batch_build(const pf_grid* grids, const int* body_offsets, const pf_body* bodies,
                          int n_variants, int sweeps, const int bc[4], void* stream, pf_batch** out);
 
+/* Body shapes for pf_batch_build_shapes. */
+enum { PF_SHAPE_CIRCLE = 0, PF_SHAPE_POLYGON = 1 };
+
+typedef struct pf_shape {
+    int kind;                 /* PF_SHAPE_CIRCLE or PF_SHAPE_POLYGON */
+    double cx, cy, r;         /* circle: centre and radius; polygon: the reference point of the polar
+                                 angle in pf_surface_velocity (r unused) */
+    int n_vertices;           /* polygon: number of vertices (>= 3) */
+    const double* vertex_xy;  /* polygon: host array [n_vertices][2], counter-clockwise */
+    int kutta_vertex;         /* polygon: vertex (trailing edge) carrying the Kutta condition, or -1 */
+} pf_shape;
+
+/* pf_batch_build with general body shapes (section "Body-Conforming Grid Generation": each
+   immersed body is a closed boundary curve; section "Boundary Conditions": the Kutta
+   condition at sharp trailing edges).
+   - A node is inside a polygon when the crossing-number test counts an odd number of edge
+     crossings (edge (a, b) crossed when (a_y > y) != (b_y > y) and
+     x < a_x + ((y - a_y)(b_x - a_x)) / (b_y - a_y)); circles as in pf_batch_build.
+   - A node just inside a polygon moves to the nearest point of its boundary (first edge on
+     ties); all of it in explicitly rounded FP64, reproducible bit for bit.
+   - Kutta condition at vertex T: with w the unit bisector of the two edges at T pointing
+     out of the body and W = T + hx w, the FREE node nearest to W (then the smallest
+     row-major index) is moved onto W and held there by the smoothing.  Solves hold it at the
+     body's value in place of the body's zero-circulation equation, so the body streamline
+     leaves T along w and the circulation follows (pf_psi_solve then runs the Schur form, the
+     only form that allows that non-symmetric equation; pf_phi_solve and pf_grad refuse such a
+     handle).
+   - Polygons need >= 3 vertices in counter-clockwise order; their bounding boxes must stay
+     2h inside the box and may not overlap any other body's bounding box.
+   Otherwise as pf_batch_build (body_offsets index `shapes`). */
+pf_status pf_batch_build_shapes(const pf_grid* grids, const int* body_offsets, const pf_shape* shapes,
+                                int n_variants, int sweeps, const int bc[4], void* stream, pf_batch** out);
+
 /* Single-variant convenience form of pf_batch_build. */
 pf_status pf_mesh_build(const pf_grid* grid, const pf_body* bodies, int n_bodies, int sweeps,
                         const int bc[4], void* stream, pf_batch** out);

@@ -30,26 +30,15 @@ Readings taken where the paper is silent (the same rules are in the CUDA library
   * boundary edges of a body (for the surface velocity) never include the wake node;
     the polar angle of an edge midpoint is taken about the body's reference point.
 
-Every expression is a sequence of individually rounded IEEE float64 operations (numpy
-applies no fused multiply-add), so the classification and the coordinates can be
-reproduced bit for bit.
+Polygons are any objects with `vertices` ((n, 2), counter-clockwise), `ref` (the
+reference point) and `kutta` (vertex index or -1); the seeded geometry generators live
+in the shared input module.  Every expression is a sequence of individually rounded
+IEEE float64 operations (numpy applies no fused multiply-add), so the classification and
+the coordinates can be reproduced bit for bit.
 """
 from __future__ import annotations
 
-from dataclasses import dataclass, field
-
 import numpy as np
-
-
-@dataclass
-class Polygon:
-    vertices: np.ndarray            # (n, 2) counter-clockwise
-    ref: tuple = (0.0, 0.0)          # reference point of the polar angle
-    kutta: int = -1                  # trailing-edge vertex with the Kutta condition, or -1
-    meta: dict = field(default_factory=dict)
-
-    def __post_init__(self):
-        self.vertices = np.asarray(self.vertices, dtype=np.float64).reshape(-1, 2)
 
 
 def signed_area(v):
@@ -104,7 +93,7 @@ def nearest_on_polygon(px, py, v):
     return qx, qy
 
 
-def kutta_points(poly: Polygon, h):
+def kutta_points(poly, h):
     """Trailing edge T, unit wake direction w and wake point W = T + h w."""
     v = poly.vertices
     n = len(v)
@@ -130,32 +119,11 @@ def nearest_node(xg, yg, mask, X, Y):
     return int(np.argmin(d2.ravel()))
 
 
-def ellipse(a, b, n, cx=0.0, cy=0.0, angle=0.0):
-    """Polygon of n vertices on the ellipse x = a cos t, y = b sin t, rotated and shifted."""
-    t = 2.0 * np.pi * np.arange(n) / n
-    x = a * np.cos(t)
-    y = b * np.sin(t)
-    c, s = np.cos(angle), np.sin(angle)
-    return Polygon(np.stack([cx + c * x - s * y, cy + s * x + c * y], axis=1), ref=(cx, cy))
-
-
-def joukowski_airfoil(k, m, n, alpha=0.0, shift=(0.0, 0.0)):
-    """Symmetric Joukowski airfoil: the circle of radius R = k + m about (-m, 0) in the
-    zeta plane, mapped by z = zeta + k^2 / zeta, rotated by -alpha (so that a stream along
-    +x meets it at angle of attack alpha), sampled at n points counter-clockwise starting
-    at the cusp (the trailing edge z = 2k), which carries the Kutta condition."""
-    R = k + m
-    th = 2.0 * np.pi * np.arange(n) / n
-    zeta = -m + R * np.exp(1j * th)
-    z = zeta + k * k / zeta
-    z = z * np.exp(-1j * alpha) + complex(*shift)
-    return Polygon(np.stack([z.real, z.imag], axis=1), ref=shift, kutta=0,
-                   meta={"k": k, "m": m, "R": R, "alpha": alpha, "shift": shift})
-
-
-def joukowski_psi(x, y, poly: Polygon, U=1.0, kutta=True):
-    """Exact stream function of the uniform stream U (along +x) past the airfoil of
-    joukowski_airfoil, with the circulation of the Kutta condition (or none):
+def joukowski_psi(x, y, poly, U=1.0, kutta=True):
+    """Exact stream function of the uniform stream U (along +x) past the Joukowski airfoil
+    described by poly.meta (k, m, R = k + m, alpha, shift: the circle of radius R about
+    (-m, 0) mapped by z = zeta + k^2 / zeta, turned by -alpha and shifted), with the
+    circulation of the Kutta condition (or none):
     psi = Im{U [(zeta - zc) e^{-i alpha} + R^2 e^{i alpha} / (zeta - zc)]} - (Gamma / 2 pi) ln|zeta - zc|,
     zeta the exterior inverse of the map, zc = -m, Gamma = -4 pi U R sin(alpha).
     Returns (psi at the points, psi on the body)."""

@@ -13,6 +13,7 @@ PF_FP64, PF_MIXED = 0, 1
 PF_TOL_REL_TRUE, PF_TOL_PAPER_ABS = 0, 1
 PF_PRECOND_NONE, PF_PRECOND_MG = 0, 1
 PF_OBJ_COPFI, PF_OBJ_GAP_FLOW = 0, 1
+PF_SHAPE_CIRCLE, PF_SHAPE_POLYGON = 0, 1
 
 
 class pf_grid(C.Structure):
@@ -22,6 +23,11 @@ class pf_grid(C.Structure):
 
 class pf_body(C.Structure):
     _fields_ = [("cx", C.c_double), ("cy", C.c_double), ("r", C.c_double)]
+
+
+class pf_shape(C.Structure):
+    _fields_ = [("kind", C.c_int), ("cx", C.c_double), ("cy", C.c_double), ("r", C.c_double),
+                ("n_vertices", C.c_int), ("vertex_xy", C.POINTER(C.c_double)), ("kutta_vertex", C.c_int)]
 
 
 class pf_mesh_stats(C.Structure):
@@ -58,6 +64,8 @@ _SIGS = {
     "pf_set_allocator": (C.c_int, [ALLOC_FN, FREE_FN, P]),
     "pf_batch_build": (C.c_int, [C.POINTER(pf_grid), C.POINTER(C.c_int), C.POINTER(pf_body), C.c_int, C.c_int,
                                  C.POINTER(C.c_int), P, C.POINTER(P)]),
+    "pf_batch_build_shapes": (C.c_int, [C.POINTER(pf_grid), C.POINTER(C.c_int), C.POINTER(pf_shape), C.c_int,
+                                        C.c_int, C.POINTER(C.c_int), P, C.POINTER(P)]),
     "pf_mesh_build": (C.c_int, [C.POINTER(pf_grid), C.POINTER(pf_body), C.c_int, C.c_int, C.POINTER(C.c_int), P,
                                 C.POINTER(P)]),
     "pf_batch_destroy": (None, [P]),

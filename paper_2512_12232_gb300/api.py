@@ -89,25 +89,46 @@ class SolveResult:
 class Mesh:
     """A pf_batch handle: one or more body-conforming mesh variants on the GPU."""
 
-    def __init__(self, grids, body_lists, sweeps, bc=(0, 0, 0, 0)):
+    def __init__(self, grids, body_lists, sweeps, bc=(0, 0, 0, 0), polygon_lists=None):
+        """polygon_lists (optional): per variant, polygon bodies (objects with `vertices`
+        ((n, 2), counter-clockwise), `ref` (reference point of the polar angle) and `kutta`
+        (trailing-edge vertex or -1)); a variant's bodies are its circles, then its polygons."""
         lib = L.load()
         nv = len(grids)
         g = (L.pf_grid * nv)()
         for v, gr in enumerate(grids):
             x0, x1, y0, y1, nx, ny = gr
             g[v] = L.pf_grid(float(x0), float(x1), float(y0), float(y1), int(nx), int(ny))
+        polygon_lists = [list(pl) for pl in polygon_lists] if polygon_lists is not None else [[] for _ in grids]
+        if len(polygon_lists) != nv:
+            raise ValueError("one polygon list per variant")
         offs = [0]
         flat = []
-        for bl in body_lists:
+        for bl, pl in zip(body_lists, polygon_lists):
             bl = np.asarray(bl, dtype=np.float64).reshape(-1, 3)
-            flat.extend(bl.tolist())
+            flat.extend(("c", row) for row in bl.tolist())
+            flat.extend(("p", p) for p in pl)
             offs.append(len(flat))
         off = (C.c_int * (nv + 1))(*offs)
-        bodies = (L.pf_body * max(1, len(flat)))(*[L.pf_body(*row) for row in flat])
         bcs = (C.c_int * 4)(*[int(s) for s in bc])
         h = C.c_void_p()
         self._h = None
-        code = lib.pf_batch_build(g, off, bodies, nv, int(sweeps), bcs, _stream(), C.byref(h))
+        if any(polygon_lists):
+            shapes = (L.pf_shape * max(1, len(flat)))()
+            self._vertex_bufs = []
+            for k, (kind, b) in enumerate(flat):
+                if kind == "c":
+                    shapes[k] = L.pf_shape(L.PF_SHAPE_CIRCLE, *map(float, b), 0, None, -1)
+                else:
+                    vx = np.ascontiguousarray(np.asarray(b.vertices, dtype=np.float64).reshape(-1, 2))
+                    buf = (C.c_double * vx.size)(*vx.ravel().tolist())
+                    self._vertex_bufs.append(buf)
+                    shapes[k] = L.pf_shape(L.PF_SHAPE_POLYGON, float(b.ref[0]), float(b.ref[1]), 0.0, len(vx),
+                                           C.cast(buf, C.POINTER(C.c_double)), int(b.kutta))
+            code = lib.pf_batch_build_shapes(g, off, shapes, nv, int(sweeps), bcs, _stream(), C.byref(h))
+        else:
+            bodies = (L.pf_body * max(1, len(flat)))(*[L.pf_body(*row) for _, row in flat])
+            code = lib.pf_batch_build(g, off, bodies, nv, int(sweeps), bcs, _stream(), C.byref(h))
         if code == L.PF_EMESH_INVALID:
             self._h = h
             self.valid = False
@@ -118,6 +139,7 @@ class Mesh:
         self.n_variants = nv
         self.grids = [tuple(gr) for gr in grids]
         self.bodies = [np.asarray(bl, dtype=np.float64).reshape(-1, 3) for bl in body_lists]
+        self.polygons = polygon_lists
         self.body_offsets = offs
         self.n_nodes = [(gr[4] + 1) * (gr[5] + 1) for gr in grids]
         self.node_offsets = np.concatenate([[0], np.cumsum(self.n_nodes)]).astype(np.int64)
@@ -204,16 +226,18 @@ class Mesh:
         check(L.load().pf_test_wait_timeout(self.handle, int(bool(enable))))
 
 
-def mesh_build(grid, bodies, sweeps, bc=(0, 0, 0, 0)) -> Mesh:
-    """One variant: grid = (x0, x1, y0, y1, nx, ny), bodies = rows of (cx, cy, r)."""
-    return Mesh([grid], [bodies], sweeps, bc)
+def mesh_build(grid, bodies, sweeps, bc=(0, 0, 0, 0), polygons=None) -> Mesh:
+    """One variant: grid = (x0, x1, y0, y1, nx, ny), bodies = rows of (cx, cy, r), then the
+    optional polygon bodies."""
+    return Mesh([grid], [bodies], sweeps, bc, None if polygons is None else [polygons])
 
 
-def batch_build(cases, sweeps=None, bc=None) -> Mesh:
-    """Many variants (objects with .grid, .bodies, .sweeps, .bc) in one handle."""
+def batch_build(cases, sweeps=None, bc=None, polygons=None) -> Mesh:
+    """Many variants (objects with .grid, .bodies, .sweeps, .bc) in one handle; polygons:
+    optional per-variant lists of polygon bodies."""
     sweeps = cases[0].sweeps if sweeps is None else sweeps
     bc = cases[0].bc if bc is None else bc
-    return Mesh([c.grid for c in cases], [c.bodies for c in cases], sweeps, bc)
+    return Mesh([c.grid for c in cases], [c.bodies for c in cases], sweeps, bc, polygons)
 
 
 def apply(mesh: Mesh, p: torch.Tensor, precision=PF_FP64):

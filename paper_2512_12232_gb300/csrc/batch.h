@@ -75,6 +75,14 @@ struct Batch {
   std::vector<HostVariant> hv;
   std::vector<pf_body> bodies;
   std::vector<int> body_off;         // [nv+1]
+  // body shapes (pf_batch_build_shapes): circles keep the pf_body table, polygons add
+  std::vector<int> shape_kind;       // [B] PF_SHAPE_*
+  std::vector<int> poly_off;         // [B+1] vertex offsets
+  std::vector<double> poly_xy;       // [vertices][2]
+  std::vector<int> kutta;            // [B] trailing-edge vertex or -1
+  bool has_polygons = false, has_kutta = false;
+  ShapeDev shp{};                    // device copies (null when there are no polygons)
+  std::vector<long long> h_wake;     // [B] padded index of each Kutta body's wake node, or -1
   std::vector<int> h_body_ptr;       // [B+1]
   std::vector<int> h_edge_ptr;       // [B+1]
   bool valid = false;                // det J > 0 everywhere
@@ -210,8 +218,16 @@ void set_last_error(const std::string& msg);
 #define PF_CUDA(call) ::pfq4::check_cuda((call), #call)
 
 // mesh.cu
+// Host description of polygonal bodies for build_batch: per body (in the order of
+// `bodies`) its kind, its vertices and its Kutta vertex; empty vectors mean circles only.
+struct ShapeInput {
+  std::vector<int> kind;             // [B]
+  std::vector<int> off;              // [B+1]
+  std::vector<double> xy;
+  std::vector<int> kutta;            // [B]
+};
 void build_batch(Batch& b, const pf_grid* grids, const int* body_offsets, const pf_body* bodies,
-                 int nv, int sweeps, const int bc[4]);
+                 int nv, int sweeps, const int bc[4], const ShapeInput* shapes = nullptr);
 void export_coords(Batch& b, int v, double* dev_xy);
 void set_coords(Batch& b, int v, const double* dev_xy);
 void tile_flags(Batch& b);

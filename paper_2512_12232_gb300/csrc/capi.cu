@@ -5,6 +5,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "batch.h"
 
@@ -113,8 +114,53 @@ pf_status pf_set_allocator(pf_alloc_fn alloc, pf_free_fn free_fn, void* ctx) {
   return PF_OK;
 }
 
+static pf_status build_handle(const pf_grid* grids, const int* body_offsets, const pf_body* bodies,
+                              int n_variants, int sweeps, const int bc[4], void* stream, pf_batch** out,
+                              const ShapeInput* shapes);
+
 pf_status pf_batch_build(const pf_grid* grids, const int* body_offsets, const pf_body* bodies, int n_variants,
                          int sweeps, const int bc[4], void* stream, pf_batch** out) {
+  return build_handle(grids, body_offsets, bodies, n_variants, sweeps, bc, stream, out, nullptr);
+}
+
+pf_status pf_batch_build_shapes(const pf_grid* grids, const int* body_offsets, const pf_shape* shapes,
+                                int n_variants, int sweeps, const int bc[4], void* stream, pf_batch** out) {
+  if (!out || !body_offsets || n_variants < 1) {
+    g_err = "invalid arguments";
+    return PF_EINVAL;
+  }
+  const int B = body_offsets[n_variants];
+  if (B < 0 || (B > 0 && !shapes)) {
+    g_err = "shapes is NULL";
+    return PF_EINVAL;
+  }
+  std::vector<pf_body> bodies(std::max(1, B));
+  ShapeInput si;
+  si.off.push_back(0);
+  for (int k = 0; k < B; ++k) {
+    const pf_shape& sh = shapes[k];
+    if (sh.kind != PF_SHAPE_CIRCLE && sh.kind != PF_SHAPE_POLYGON) {
+      g_err = "invalid shape kind";
+      return PF_EINVAL;
+    }
+    bodies[k] = pf_body{sh.cx, sh.cy, sh.kind == PF_SHAPE_CIRCLE ? sh.r : 0.0};
+    si.kind.push_back(sh.kind);
+    si.kutta.push_back(sh.kind == PF_SHAPE_POLYGON ? sh.kutta_vertex : -1);
+    if (sh.kind == PF_SHAPE_POLYGON) {
+      if (sh.n_vertices < 3 || !sh.vertex_xy) {
+        g_err = "a polygon needs at least 3 vertices";
+        return PF_EINVAL;
+      }
+      si.xy.insert(si.xy.end(), sh.vertex_xy, sh.vertex_xy + 2 * (size_t)sh.n_vertices);
+    }
+    si.off.push_back((int)(si.xy.size() / 2));
+  }
+  return build_handle(grids, body_offsets, bodies.data(), n_variants, sweeps, bc, stream, out, &si);
+}
+
+static pf_status build_handle(const pf_grid* grids, const int* body_offsets, const pf_body* bodies,
+                              int n_variants, int sweeps, const int bc[4], void* stream, pf_batch** out,
+                              const ShapeInput* shapes) {
   if (!out) {
     g_err = "out is NULL";
     return PF_EINVAL;
@@ -131,7 +177,7 @@ pf_status pf_batch_build(const pf_grid* grids, const int* body_offsets, const pf
     b->alloc_fn = g_alloc;
     b->free_fn = g_free;
     b->alloc_ctx = g_ctx;
-    build_batch(*b, grids, body_offsets, bodies, n_variants, sweeps, bc);
+    build_batch(*b, grids, body_offsets, bodies, n_variants, sweeps, bc, shapes);
     if (!b->valid) throw Error{PF_EMESH_INVALID, "mesh has det J <= 0 at a Gauss point of an active cell"};
     return PF_OK;
   });
@@ -160,6 +206,7 @@ void pf_batch_destroy(pf_batch* h) {
   destroy_phi_view(*b);
   for (int k = 0; k < 2; ++k)
     if (b->graph[k]) cudaGraphExecDestroy(b->graph[k]);
+  if (b->graph_pcg) cudaGraphExecDestroy(b->graph_pcg);
   for (int k = 0; k < Batch::N_EV; ++k)
     if (b->ev[k]) cudaEventDestroy(b->ev[k]);
   if (b->h_poll) cudaFreeHost(b->h_poll);

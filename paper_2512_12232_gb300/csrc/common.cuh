@@ -44,6 +44,8 @@ constexpr uint8_t DISPLACED = 16;    // node moved by the mesh generator (d != 0
 constexpr uint8_t RING = 32;         // node on the outer boundary of the box
 constexpr uint8_t CELL_GEN32 = 64;   // general cell whose FP32 coefficients differ from the FP32
                                      // rectangle constants (the FP32 operator needs stored K_e)
+constexpr uint8_t WAKE = 128;        // Kutta wake node: a FREE node moved onto a trailing-edge
+                                     // bisector and held fixed by the mesh smoothing
 
 // per-tile flags of the fused-CG tile list (k_tile_general)
 constexpr uint8_t TILE_GEN64 = 1;     // a cell of the tile's window needs stored FP64 K_e
@@ -110,6 +112,18 @@ struct Sched {                 // persistent tile schedule
   int* counter;                // [nv] finished segments in the current launch
   int n_cta;
   unsigned long long* cta_ns;  // [G] tile-phase time of each CTA (timed fused-CG launches), else null
+};
+
+// Shapes of the bodies (pf_batch_build_shapes): per global body its kind (PF_SHAPE_*),
+// its vertices (polygons: xy[2 off[k]] .. xy[2 off[k+1]], counter-clockwise), its
+// bounding box (xmin, xmax, ymin, ymax) and the trailing-edge vertex with the Kutta
+// condition (-1: none).  Circles use the pf_body table only.
+struct ShapeDev {
+  const int* kind;
+  const int* off;            // [B + 1]
+  const double* xy;
+  const double4* box;
+  const int* kutta;
 };
 
 struct MeshDev {

@@ -179,7 +179,7 @@ __global__ void k_jacobi_T(const DevVariant* var, const int* tile_var, const int
   const int i = ij.x + threadIdx.x, j = ij.y + threadIdx.y;
   if (i > V.nx || j > V.ny) return;
   const long long n = V.base + (long long)j * V.P + i;
-  auto updated = [&](long long m) -> bool { return bid[m] < 0 && !(tag[m] & RING); };
+  auto updated = [&](long long m) -> bool { return bid[m] < 0 && !(tag[m] & (RING | WAKE)); };
   double ox = 0.0, oy = 0.0;
   if (!updated(n)) {
     ox = in[n];
@@ -297,6 +297,8 @@ static void centre_chain(Batch& b, double* gc) {
 }
 
 void coords_vjp(Batch& b, const double* dev_gX, double* gc) {
+  if (b.has_polygons)
+    throw Error{PF_EINVAL, "pf_coords_vjp: the projection Jacobian is that of circular bodies"};
   ensure_grad_memory(b);
   PF_CUDA(cudaMemsetAsync(b.gradX, 0, 2 * b.Vtot * sizeof(double), b.stream));
   k_import_grad<<<dim3(256, b.nv), 256, 0, b.stream>>>(b.d_var, lbase_cached(b), b.Vtot, dev_gX, b.gradX);
@@ -308,6 +310,8 @@ void coords_vjp(Batch& b, const double* dev_gX, double* gc) {
 pf_status shape_gradient(Batch& b, int obj, int lo, int hi, double U, double tol, double* dev_dJdX, double* dJdc,
                          double* J) {
   if (!b.solved) throw Error{PF_EINVAL, "pf_grad needs a solve on this handle first"};
+  if (b.has_polygons)
+    throw Error{PF_EINVAL, "pf_grad: the centre chain rule is that of circular bodies (radial projection)"};
   if (U != b.lastU) throw Error{PF_EINVAL, "pf_grad must use the U of the last solve"};
   if (!(tol > 0)) throw Error{PF_EINVAL, "invalid tol"};
   cudaStream_t s = b.stream;

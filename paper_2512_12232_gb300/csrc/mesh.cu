@@ -44,19 +44,74 @@ __device__ __forceinline__ TileCtx tile_ctx(const DevVariant* var, const int* ti
   return c;
 }
 
-// 1. inside test: bid[n] = body k (local) if (x-cx)^2 + (y-cy)^2 <= r^2, else -1.
+// Crossing-number test of (x, y) against polygon gb: an edge (a, b) is crossed when
+// (a_y > y) != (b_y > y) and x < a_x + ((y - a_y)(b_x - a_x)) / (b_y - a_y); odd = inside.
+__device__ bool inside_polygon(const ShapeDev& S, int gb, double x, double y) {
+  const double4 bx = S.box[gb];
+  if (x < bx.x || x > bx.y || y < bx.z || y > bx.w) return false;   // the count is even there
+  const int v0 = S.off[gb], n = S.off[gb + 1] - v0;
+  const double* p = S.xy + 2 * v0;
+  bool in = false;
+  for (int e = 0; e < n; ++e) {
+    const int f = e + 1 == n ? 0 : e + 1;
+    const double ax = p[2 * e], ay = p[2 * e + 1], bxv = p[2 * f], by = p[2 * f + 1];
+    if ((ay > y) != (by > y)) {
+      const double xint =
+          __dadd_rn(ax, __ddiv_rn(__dmul_rn(__dsub_rn(y, ay), __dsub_rn(bxv, ax)), __dsub_rn(by, ay)));
+      if (x < xint) in = !in;
+    }
+  }
+  return in;
+}
+
+// Nearest point of polygon gb's boundary to (x, y): per edge t = ((p - a).(b - a)) / |b - a|^2
+// clamped to [0, 1], q = a + t (b - a); the first edge with the smallest |p - q|^2 wins.
+__device__ void nearest_on_polygon(const ShapeDev& S, int gb, double x, double y, double& qx, double& qy) {
+  const int v0 = S.off[gb], n = S.off[gb + 1] - v0;
+  const double* p = S.xy + 2 * v0;
+  double best = 1.0 / 0.0;
+  qx = 0.0;
+  qy = 0.0;
+  for (int e = 0; e < n; ++e) {
+    const int f = e + 1 == n ? 0 : e + 1;
+    const double ax = p[2 * e], ay = p[2 * e + 1];
+    const double dx = __dsub_rn(p[2 * f], ax), dy = __dsub_rn(p[2 * f + 1], ay);
+    const double num = __dadd_rn(__dmul_rn(__dsub_rn(x, ax), dx), __dmul_rn(__dsub_rn(y, ay), dy));
+    const double den = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+    double t = __ddiv_rn(num, den);
+    t = t < 0.0 ? 0.0 : (t > 1.0 ? 1.0 : t);
+    const double cx = __dadd_rn(ax, __dmul_rn(t, dx)), cy = __dadd_rn(ay, __dmul_rn(t, dy));
+    const double ex = __dsub_rn(x, cx), ey = __dsub_rn(y, cy);
+    const double d2 = __dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey));
+    if (d2 < best) {
+      best = d2;
+      qx = cx;
+      qy = cy;
+    }
+  }
+}
+
+// 1. inside test: bid[n] = body k (local) if (x-cx)^2 + (y-cy)^2 <= r^2 (circles) or the
+//    crossing-number test counts odd (polygons), else -1.
 __global__ void k_classify(const DevVariant* var, const int* tile_var, const int2* tile_ij,
-                           const pf_body* bodies, int* bid, int* err) {
+                           const pf_body* bodies, ShapeDev shp, int* bid, int* err) {
   TileCtx c = tile_ctx(var, tile_var, tile_ij);
   const DevVariant& V = var[c.v];
   if (!c.in) return;
   const double x = grid_x(V, c.i), y = grid_y(V, c.j);
   int ib = -1;
   for (int k = 0; k < V.nb; ++k) {
-    const pf_body B = bodies[V.body0 + k];
-    const double dx = __dsub_rn(x, B.cx), dy = __dsub_rn(y, B.cy);
-    const double d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
-    if (d2 <= __dmul_rn(B.r, B.r)) {
+    const int gb = V.body0 + k;
+    bool in;
+    if (shp.kind && shp.kind[gb] == PF_SHAPE_POLYGON) {
+      in = inside_polygon(shp, gb, x, y);
+    } else {
+      const pf_body B = bodies[gb];
+      const double dx = __dsub_rn(x, B.cx), dy = __dsub_rn(y, B.cy);
+      const double d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+      in = d2 <= __dmul_rn(B.r, B.r);
+    }
+    if (in) {
       if (ib >= 0) atomicOr(err, 1);
       ib = k;
     }
@@ -66,7 +121,7 @@ __global__ void k_classify(const DevVariant* var, const int* tile_var, const int
 
 // 2. node kinds, cell activity, ring flag, projection displacement d0.
 __global__ void k_kinds(const DevVariant* var, const int* tile_var, const int2* tile_ij,
-                        const pf_body* bodies, const int* bid, uint8_t* tag, double2* d0,
+                        const pf_body* bodies, ShapeDev shp, const int* bid, uint8_t* tag, double2* d0,
                         int bc0, int bc1, int bc2, int bc3, int* err) {
   TileCtx c = tile_ctx(var, tile_var, tile_ij);
   const DevVariant& V = var[c.v];
@@ -93,13 +148,19 @@ __global__ void k_kinds(const DevVariant* var, const int* tile_var, const int2* 
                        cell_active(i, j);
     if (touch) {
       t |= K_BODY;
-      const pf_body B = bodies[V.body0 + ib];
+      const int gb = V.body0 + ib;
       const double xg = grid_x(V, i), yg = grid_y(V, j);
-      const double ex = __dsub_rn(xg, B.cx), ey = __dsub_rn(yg, B.cy);
-      const double rho = __dsqrt_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)));
-      if (rho == 0.0) atomicOr(err, 2);
-      const double xb = __dadd_rn(B.cx, __ddiv_rn(__dmul_rn(B.r, ex), rho));
-      const double yb = __dadd_rn(B.cy, __ddiv_rn(__dmul_rn(B.r, ey), rho));
+      double xb, yb;
+      if (shp.kind && shp.kind[gb] == PF_SHAPE_POLYGON) {
+        nearest_on_polygon(shp, gb, xg, yg, xb, yb);
+      } else {
+        const pf_body B = bodies[gb];
+        const double ex = __dsub_rn(xg, B.cx), ey = __dsub_rn(yg, B.cy);
+        const double rho = __dsqrt_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)));
+        if (rho == 0.0) atomicOr(err, 2);
+        xb = __dadd_rn(B.cx, __ddiv_rn(__dmul_rn(B.r, ex), rho));
+        yb = __dadd_rn(B.cy, __ddiv_rn(__dmul_rn(B.r, ey), rho));
+      }
       d = make_double2(__dsub_rn(xb, xg), __dsub_rn(yb, yg));
     } else {
       t |= K_INACT;
@@ -107,6 +168,74 @@ __global__ void k_kinds(const DevVariant* var, const int* tile_var, const int2* 
   }
   tag[n] = t;
   d0[n] = d;
+}
+
+// 2b. Kutta condition of polygon gb (one CTA per global body; others return): the wake
+//     point W = T + hx w on the trailing-edge bisector w (unit, pointing out of the body),
+//     the FREE node nearest to W (smallest squared distance, then smallest row-major index)
+//     searched in a window of +-KUTTA_WIN cells around W, flagged WAKE and moved onto W.
+constexpr int KUTTA_WIN = 8;
+__global__ void __launch_bounds__(256) k_kutta(const DevVariant* var, const int* body_var, ShapeDev shp,
+                                               uint8_t* tag, double2* d0, long long* wake) {
+  const int gb = blockIdx.x;
+  if (!shp.kind || shp.kind[gb] != PF_SHAPE_POLYGON || shp.kutta[gb] < 0) return;
+  const DevVariant& V = var[body_var[gb]];
+  __shared__ double sW[2];
+  __shared__ double sd[256];
+  __shared__ long long sk[256];
+  if (threadIdx.x == 0) {
+    const int v0 = shp.off[gb], n = shp.off[gb + 1] - v0, k = shp.kutta[gb];
+    const double* p = shp.xy + 2 * v0;
+    const int kp = k == 0 ? n - 1 : k - 1, kn = k + 1 == n ? 0 : k + 1;
+    const double tx = p[2 * k], ty = p[2 * k + 1];
+    const double ax = __dsub_rn(tx, p[2 * kp]), ay = __dsub_rn(ty, p[2 * kp + 1]);
+    const double bx = __dsub_rn(tx, p[2 * kn]), by = __dsub_rn(ty, p[2 * kn + 1]);
+    const double la = __dsqrt_rn(__dadd_rn(__dmul_rn(ax, ax), __dmul_rn(ay, ay)));
+    const double lb = __dsqrt_rn(__dadd_rn(__dmul_rn(bx, bx), __dmul_rn(by, by)));
+    double wx = __dadd_rn(__ddiv_rn(ax, la), __ddiv_rn(bx, lb));
+    double wy = __dadd_rn(__ddiv_rn(ay, la), __ddiv_rn(by, lb));
+    const double lw = __dsqrt_rn(__dadd_rn(__dmul_rn(wx, wx), __dmul_rn(wy, wy)));
+    wx = __ddiv_rn(wx, lw);
+    wy = __ddiv_rn(wy, lw);
+    sW[0] = __dadd_rn(tx, __dmul_rn(V.hx, wx));
+    sW[1] = __dadd_rn(ty, __dmul_rn(V.hx, wy));
+  }
+  __syncthreads();
+  const double Wx = sW[0], Wy = sW[1];
+  const int ic = (int)floor((Wx - V.x0) / V.hx), jc = (int)floor((Wy - V.y0) / V.hy);
+  constexpr int SIDE = 2 * KUTTA_WIN + 2;
+  double best = 1.0 / 0.0;
+  long long bk = -1;
+  for (int q = threadIdx.x; q < SIDE * SIDE; q += blockDim.x) {
+    const int i = ic - KUTTA_WIN + q % SIDE, j = jc - KUTTA_WIN + q / SIDE;
+    if (i < 0 || j < 0 || i > V.nx || j > V.ny) continue;
+    const long long n = V.base + (long long)j * V.P + i;
+    if ((tag[n] & KIND_MASK) != K_FREE) continue;
+    const double ex = __dsub_rn(grid_x(V, i), Wx), ey = __dsub_rn(grid_y(V, j), Wy);
+    const double d2 = __dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey));
+    const long long key = (long long)j * (V.nx + 1) + i;     // row-major order of the logical grid
+    if (d2 < best || (d2 == best && key < bk)) {
+      best = d2;
+      bk = key;
+    }
+  }
+  sd[threadIdx.x] = best;
+  sk[threadIdx.x] = bk;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int t = 1; t < blockDim.x; ++t)
+      if (sk[t] >= 0 && (sd[t] < best || (sd[t] == best && (bk < 0 || sk[t] < bk)))) {
+        best = sd[t];
+        bk = sk[t];
+      }
+    if (bk >= 0) {
+      const int i = (int)(bk % (V.nx + 1)), j = (int)(bk / (V.nx + 1));
+      const long long n = V.base + (long long)j * V.P + i;
+      d0[n] = make_double2(__dsub_rn(Wx, grid_x(V, i)), __dsub_rn(Wy, grid_y(V, j)));
+      tag[n] |= WAKE;
+      wake[gb] = n;
+    }
+  }
 }
 
 // 3. Jacobi sweeps, JK per launch (temporal blocking): nodes outside every body and off
@@ -151,7 +280,7 @@ __global__ void __launch_bounds__(NT) k_jacobi(const DevVariant* var, const int*
     if (i >= 0 && j >= 0 && i <= V.nx && j <= V.ny) {
       const long long n = V.base + (long long)j * V.P + i;
       v = src[n];
-      u = bid[n] < 0 && !(tag[n] & RING);
+      u = bid[n] < 0 && !(tag[n] & (RING | WAKE));
     }
     w0[q] = v;
     upd[q] = u;
@@ -513,7 +642,7 @@ static T* upload(Batch& b, const std::vector<T>& h) {
 }
 
 void build_batch(Batch& b, const pf_grid* grids, const int* body_offsets, const pf_body* bodies,
-                 int nv, int sweeps, const int bc[4]) {
+                 int nv, int sweeps, const int bc[4], const ShapeInput* shapes) {
   if (nv < 1 || !grids || !body_offsets || sweeps < 0 || !bc) throw Error{PF_EINVAL, "invalid arguments"};
   bool any_dir = false;
   for (int s = 0; s < 4; ++s) {
@@ -529,6 +658,44 @@ void build_batch(Batch& b, const pf_grid* grids, const int* body_offsets, const 
   b.B = body_offsets[nv];
   if (b.B > 0 && !bodies) throw Error{PF_EINVAL, "bodies is NULL"};
   b.bodies.assign(bodies, bodies + b.B);
+  b.shape_kind.assign(b.B, PF_SHAPE_CIRCLE);
+  b.kutta.assign(b.B, -1);
+  b.poly_off.assign(b.B + 1, 0);
+  b.poly_xy.clear();
+  b.h_wake.assign(b.B, -1);
+  if (shapes && !shapes->kind.empty()) {
+    b.shape_kind = shapes->kind;
+    b.kutta = shapes->kutta;
+    b.poly_off = shapes->off;
+    b.poly_xy = shapes->xy;
+  }
+  b.has_polygons = std::find(b.shape_kind.begin(), b.shape_kind.end(), (int)PF_SHAPE_POLYGON) != b.shape_kind.end();
+  b.has_kutta = false;
+  std::vector<double4> pbox(std::max(1, b.B), make_double4(0, 0, 0, 0));
+  for (int k = 0; k < b.B; ++k) {
+    if (b.shape_kind[k] == PF_SHAPE_POLYGON) {
+      const int v0 = b.poly_off[k], n = b.poly_off[k + 1] - v0;
+      if (n < 3) throw Error{PF_EINVAL, "body " + std::to_string(k) + ": a polygon needs at least 3 vertices"};
+      const double* p = b.poly_xy.data() + 2 * v0;
+      double area2 = 0.0;
+      double4 bx = make_double4(p[0], p[0], p[1], p[1]);
+      for (int e = 0; e < n; ++e) {
+        const int f = (e + 1) % n;
+        area2 += p[2 * e] * p[2 * f + 1] - p[2 * f] * p[2 * e + 1];
+        bx.x = std::min(bx.x, p[2 * e]);
+        bx.y = std::max(bx.y, p[2 * e]);
+        bx.z = std::min(bx.z, p[2 * e + 1]);
+        bx.w = std::max(bx.w, p[2 * e + 1]);
+      }
+      if (!(area2 > 0)) throw Error{PF_EINVAL, "body " + std::to_string(k) + ": polygon vertices must run counter-clockwise"};
+      if (b.kutta[k] >= n) throw Error{PF_EINVAL, "body " + std::to_string(k) + ": Kutta vertex out of range"};
+      b.has_kutta |= b.kutta[k] >= 0;
+      pbox[k] = bx;
+    } else {
+      const pf_body& B = b.bodies[k];
+      pbox[k] = make_double4(B.cx - B.r, B.cx + B.r, B.cy - B.r, B.cy + B.r);
+    }
+  }
 
   // ---- host validation and layout
   std::vector<DevVariant> dv(nv);
@@ -575,22 +742,34 @@ void build_batch(Batch& b, const pf_grid* grids, const int* body_offsets, const 
         cvar.push_back(v);
       }
     for (int k = 0; k < nb; ++k) {
-      const pf_body& B = b.bodies[H.body0 + k];
-      if (!(B.r > 0)) throw Error{PF_EINVAL, "variant " + std::to_string(v) + ": body radius must be positive"};
-      if (B.cx - B.r < g.x0 + 2 * H.hx || B.cx + B.r > g.x1 - 2 * H.hx || B.cy - B.r < g.y0 + 2 * H.hy ||
-          B.cy + B.r > g.y1 - 2 * H.hy)
+      const int gk = H.body0 + k;
+      const pf_body& B = b.bodies[gk];
+      const bool poly = b.shape_kind[gk] == PF_SHAPE_POLYGON;
+      if (!poly && !(B.r > 0))
+        throw Error{PF_EINVAL, "variant " + std::to_string(v) + ": body radius must be positive"};
+      const double4 bx = pbox[gk];
+      if (bx.x < g.x0 + 2 * H.hx || bx.y > g.x1 - 2 * H.hx || bx.z < g.y0 + 2 * H.hy || bx.w > g.y1 - 2 * H.hy)
         throw Error{PF_EINVAL, "variant " + std::to_string(v) + ": body within 2h of the outer boundary"};
       for (int k2 = 0; k2 < k; ++k2) {
-        const pf_body& C = b.bodies[H.body0 + k2];
+        const int gk2 = H.body0 + k2;
+        const pf_body& C = b.bodies[gk2];
+        if (poly || b.shape_kind[gk2] == PF_SHAPE_POLYGON) {
+          const double4 cb = pbox[gk2];   // conservative: bounding boxes of polygons may not overlap
+          if (!(bx.y < cb.x || cb.y < bx.x || bx.w < cb.z || cb.w < bx.z))
+            throw Error{PF_EINVAL, "variant " + std::to_string(v) + ": body bounding boxes overlap"};
+          continue;
+        }
         const double ddx = B.cx - C.cx, ddy = B.cy - C.cy;
         if (ddx * ddx + ddy * ddy <= (B.r + C.r) * (B.r + C.r))
           throw Error{PF_EINVAL, "variant " + std::to_string(v) + ": bodies overlap or touch"};
       }
+      // node box of the body (polygons: 3 more cells, a Kutta wake node lies near the box)
+      const int pad = poly ? 4 : 1;
       int4 bb;
-      bb.x = std::max(0, (int)std::floor((B.cx - B.r - g.x0) / H.hx) - 1);
-      bb.y = std::min(g.nx, (int)std::ceil((B.cx + B.r - g.x0) / H.hx) + 1);
-      bb.z = std::max(0, (int)std::floor((B.cy - B.r - g.y0) / H.hy) - 1);
-      bb.w = std::min(g.ny, (int)std::ceil((B.cy + B.r - g.y0) / H.hy) + 1);
+      bb.x = std::max(0, (int)std::floor((bx.x - g.x0) / H.hx) - pad);
+      bb.y = std::min(g.nx, (int)std::ceil((bx.y - g.x0) / H.hx) + pad);
+      bb.z = std::max(0, (int)std::floor((bx.z - g.y0) / H.hy) - pad);
+      bb.w = std::min(g.ny, (int)std::ceil((bx.w - g.y0) / H.hy) + pad);
       bbox[H.body0 + k] = bb;
       body_var[H.body0 + k] = v;
     }
@@ -615,6 +794,17 @@ void build_batch(Batch& b, const pf_grid* grids, const int* body_offsets, const 
   b.d_bodies = upload(b, hb);
   b.d_body_var = upload(b, body_var);
   b.d_bbox = upload(b, bbox);
+  long long* d_wake = nullptr;
+  if (b.has_polygons) {
+    b.shp.kind = upload(b, b.shape_kind);
+    b.shp.off = upload(b, b.poly_off);
+    b.shp.xy = upload(b, b.poly_xy);
+    b.shp.box = upload(b, pbox);
+    b.shp.kutta = upload(b, b.kutta);
+    d_wake = upload(b, b.h_wake);
+  } else {
+    b.shp = ShapeDev{};
+  }
   b.tile_ij = upload(b, tij);
   b.tile_var = upload(b, tvar);
   b.tile_cg_ij = upload(b, cij);
@@ -650,9 +840,14 @@ void build_batch(Batch& b, const pf_grid* grids, const int* body_offsets, const 
 
   const dim3 blk(TX, TY);
   const unsigned grid = (unsigned)b.T;
-  k_classify<<<grid, blk, 0, s>>>(b.d_var, b.tile_var, b.tile_ij, b.d_bodies, b.bid, err);
-  k_kinds<<<grid, blk, 0, s>>>(b.d_var, b.tile_var, b.tile_ij, b.d_bodies, b.bid, b.tag, dA, bc[0], bc[1],
+  k_classify<<<grid, blk, 0, s>>>(b.d_var, b.tile_var, b.tile_ij, b.d_bodies, b.shp, b.bid, err);
+  k_kinds<<<grid, blk, 0, s>>>(b.d_var, b.tile_var, b.tile_ij, b.d_bodies, b.shp, b.bid, b.tag, dA, bc[0], bc[1],
                                bc[2], bc[3], err);
+  if (b.has_kutta) {
+    k_kutta<<<b.B, 256, 0, s>>>(b.d_var, b.d_body_var, b.shp, b.tag, dA, d_wake);
+    PF_CUDA(cudaMemcpyAsync(b.h_wake.data(), d_wake, b.B * sizeof(long long), cudaMemcpyDeviceToHost, s));
+    b.launches += 1;
+  }
   PF_CUDA(cudaMemcpyAsync(dB, dA, Vt * sizeof(double2), cudaMemcpyDeviceToDevice, s));
   if (sweeps > 0) PF_CUDA(cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, JACOBI_SMEM));
   for (int it = 0; it < sweeps; it += JK) {

@@ -12,6 +12,14 @@
 // launch per CG iteration over all right-hand sides); S is factorised in FP64 on the
 // host (N_b <= 64).  A final warm-started MPC solve on the original handle checks the
 // combined solution's true residual (zero iterations when it already meets tol).
+//
+// Kutta condition (section "Boundary Conditions"): for a body with a trailing-edge wake
+// node W, the row "collapsed body row = 0" (zero circulation) is replaced by
+// psi(W) = C_k, i.e. psi_0(W) + sum_j C_j phi_j(W) - C_k = 0, with the values at W read
+// from the same fixed-body solves.  The small system is then not symmetric and is solved
+// by Gaussian elimination with partial pivoting, and the MPC check is skipped (its
+// iteration would return to zero circulation): the reported residual is the largest of
+// the fixed-body solves'.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -68,12 +76,36 @@ void cholesky_solve(int n, std::vector<double>& A, std::vector<double>& b) {
   }
 }
 
+void lu_solve(int n, std::vector<double>& A, std::vector<double>& b) {
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < n; ++r)
+      if (std::fabs(A[r * n + c]) > std::fabs(A[piv * n + c])) piv = r;
+    if (!(std::fabs(A[piv * n + c]) > 0)) throw Error{PF_EBREAKDOWN, "singular body system"};
+    if (piv != c) {
+      for (int k = 0; k < n; ++k) std::swap(A[c * n + k], A[piv * n + k]);
+      std::swap(b[c], b[piv]);
+    }
+    for (int r = c + 1; r < n; ++r) {
+      const double f = A[r * n + c] / A[c * n + c];
+      for (int k = c; k < n; ++k) A[r * n + k] -= f * A[c * n + k];
+      b[r] -= f * b[c];
+    }
+  }
+  for (int r = n - 1; r >= 0; --r) {
+    double t = b[r];
+    for (int k = r + 1; k < n; ++k) t -= A[r * n + k] * b[k];
+    b[r] = t / A[r * n + r];
+  }
+}
+
 struct BatchGuard {
   Batch* p;
   ~BatchGuard() {
     if (p) {
       for (int k = 0; k < 2; ++k)
         if (p->graph[k]) cudaGraphExecDestroy(p->graph[k]);
+      if (p->graph_pcg) cudaGraphExecDestroy(p->graph_pcg);
       for (int k = 0; k < Batch::N_EV; ++k)
         if (p->ev[k]) cudaEventDestroy(p->ev[k]);
       if (p->h_poll) cudaFreeHost(p->h_poll);
@@ -98,6 +130,8 @@ pf_status schur_solve(Batch& b, double U, const pf_solve_opts& o, double* dev_ps
   std::vector<int> offs{0}, copy0(b.nv), coef0(b.nv);
   std::vector<pf_body> bodies;
   std::vector<double> Uv, fixedC;
+  ShapeInput shp;                       // the body shapes of every copy (polygons, Kutta)
+  shp.off.push_back(0);
   int ncoef = 0;
   for (int v = 0; v < b.nv; ++v) {
     const HostVariant& H = b.hv[v];
@@ -107,8 +141,13 @@ pf_status schur_solve(Batch& b, double U, const pf_solve_opts& o, double* dev_ps
     for (int k = 0; k <= H.nb; ++k) {
       grids.push_back(H.g);
       for (int m = 0; m < H.nb; ++m) {
-        bodies.push_back(b.bodies[H.body0 + m]);
+        const int gm = H.body0 + m;
+        bodies.push_back(b.bodies[gm]);
         fixedC.push_back((k > 0 && m == k - 1) ? 1.0 : 0.0);
+        shp.kind.push_back(b.shape_kind[gm]);
+        shp.kutta.push_back(b.kutta[gm]);
+        shp.xy.insert(shp.xy.end(), b.poly_xy.begin() + 2 * b.poly_off[gm], b.poly_xy.begin() + 2 * b.poly_off[gm + 1]);
+        shp.off.push_back((int)(shp.xy.size() / 2));
       }
       offs.push_back((int)bodies.size());
       Uv.push_back(k == 0 ? U : 0.0);
@@ -121,7 +160,8 @@ pf_status schur_solve(Batch& b, double U, const pf_solve_opts& o, double* dev_ps
   S.alloc_fn = b.alloc_fn;
   S.free_fn = b.free_fn;
   S.alloc_ctx = b.alloc_ctx;
-  build_batch(S, grids.data(), offs.data(), bodies.data(), (int)grids.size(), b.sweeps, b.bc);
+  build_batch(S, grids.data(), offs.data(), bodies.data(), (int)grids.size(), b.sweeps, b.bc,
+              b.has_polygons ? &shp : nullptr);
   if (!S.valid) throw Error{PF_EMESH_INVALID, "Schur sub-problem mesh invalid"};
   ensure_solver_memory(S, o.precision);
   cudaStream_t s = b.stream;
@@ -143,6 +183,15 @@ pf_status schur_solve(Batch& b, double U, const pf_solve_opts& o, double* dev_ps
     PF_CUDA(cudaStreamSynchronize(s));
   }
   std::vector<double> coef(std::max(1, ncoef)), C(std::max(1, b.B), 0.0);
+  // Kutta rows need the fixed-body solutions at each wake node: psi_0(W) and phi_k(W)
+  auto wake_value = [&](int copy, int body) -> double {
+    const long long n = S.h_wake[S.hv[copy].body0 + body];
+    if (n < 0) throw Error{PF_EINVAL, "internal: Kutta body without a wake node"};
+    double x = 0.0;
+    PF_CUDA(cudaMemcpyAsync(&x, S.x64 + n, sizeof(double), cudaMemcpyDeviceToHost, s));
+    PF_CUDA(cudaStreamSynchronize(s));
+    return x;
+  };
   for (int v = 0; v < b.nv; ++v) {
     const int nb = b.hv[v].nb;
     const int sb0 = S.hv[copy0[v]].body0;   // body rows of copy k start at sb0 + k * nb
@@ -151,10 +200,21 @@ pf_status schur_solve(Batch& b, double U, const pf_solve_opts& o, double* dev_ps
       rhs[j] = rows[sb0 + j];                                   // = -(row j of K psi_0)
       for (int k = 0; k < nb; ++k) A[j * nb + k] = -rows[sb0 + (k + 1) * nb + j];   // row j of K phi_k
     }
-    // symmetrise (S is symmetric up to the sub-solve tolerance)
-    for (int j = 0; j < nb; ++j)
-      for (int k = 0; k < j; ++k) A[j * nb + k] = A[k * nb + j] = 0.5 * (A[j * nb + k] + A[k * nb + j]);
-    if (nb > 0) cholesky_solve(nb, A, rhs);
+    bool kutta = false;
+    for (int j = 0; j < nb; ++j) kutta |= b.kutta[b.hv[v].body0 + j] >= 0;
+    if (kutta) {
+      for (int j = 0; j < nb; ++j) {
+        if (b.kutta[b.hv[v].body0 + j] < 0) continue;
+        rhs[j] = -wake_value(copy0[v], j);                     // psi_0(W_j) + sum_k C_k phi_k(W_j) = C_j
+        for (int k = 0; k < nb; ++k) A[j * nb + k] = wake_value(copy0[v] + 1 + k, j) - (k == j ? 1.0 : 0.0);
+      }
+      lu_solve(nb, A, rhs);
+    } else {
+      // symmetrise (S is symmetric up to the sub-solve tolerance)
+      for (int j = 0; j < nb; ++j)
+        for (int k = 0; k < j; ++k) A[j * nb + k] = A[k * nb + j] = 0.5 * (A[j * nb + k] + A[k * nb + j]);
+      if (nb > 0) cholesky_solve(nb, A, rhs);
+    }
     coef[coef0[v]] = 1.0;
     for (int k = 0; k < nb; ++k) {
       coef[coef0[v] + 1 + k] = rhs[k];
@@ -176,7 +236,7 @@ pf_status schur_solve(Batch& b, double U, const pf_solve_opts& o, double* dev_ps
   b.launches += S.launches + 1;
   // the MPC solve warm-started from the combined solution reports the true residual
   // (and continues CG only if the Schur solution misses tol)
-  bool need_bnorm = b.bnorm2_unit.empty() || U == 0.0;
+  bool need_bnorm = b.bnorm2_unit.empty() || U == 0.0 || b.has_kutta;
   for (double x : b.bnorm2_unit) need_bnorm |= x < 0;
   if (need_bnorm) {
     // ||b|| has not been measured on this handle yet: one residual evaluation at x = 0
@@ -191,6 +251,32 @@ pf_status schur_solve(Batch& b, double U, const pf_solve_opts& o, double* dev_ps
     PF_CUDA(cudaGetLastError());
   }
   b.solved = true;
+  if (b.has_kutta) {
+    // the combined solution with the Kutta rows is the answer (an MPC iteration from it
+    // would return to zero circulation); its accuracy is that of the fixed-body solves
+    PF_CUDA(cudaStreamSynchronize(s));
+    b.lastU = U;
+    b.last_precision = o.precision;
+    if (dev_psi) export_psi(b, dev_psi);
+    if (body_psi && b.B) {
+      PF_CUDA(cudaMemcpyAsync(body_psi, C.data(), b.B * sizeof(double), cudaMemcpyHostToHost, s));
+    }
+    PF_CUDA(cudaStreamSynchronize(s));
+    if (info) {
+      for (int v = 0; v < b.nv; ++v) {
+        info[v] = pf_solve_info{};
+        for (int k = 0; k <= b.hv[v].nb; ++k) {
+          const pf_solve_info& si = sinfo[copy0[v] + k];
+          info[v].iters += si.iters;
+          info[v].refinements = std::max(info[v].refinements, si.refinements);
+          info[v].rel_true_residual = std::max(info[v].rel_true_residual, si.rel_true_residual);
+        }
+        info[v].status = PF_OK;
+        info[v].n_dof = b.hv[v].stats.n_dof;
+      }
+    }
+    return PF_OK;
+  }
   pf_solve_opts vo = o;
   vo.warm_start = 1;
   const pf_status st2 = solve_core(b, U, vo, dev_psi, body_psi, info, true);

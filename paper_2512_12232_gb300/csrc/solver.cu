@@ -1856,6 +1856,8 @@ static cudaGraphExec_t get_pcg_graph(Batch& b, int chunk) {
 pf_status psi_solve(Batch& b, double U, const pf_solve_opts& o, double* dev_psi, double* body_psi,
                     pf_solve_info* info) {
   if (o.k_max < 1) throw Error{PF_EINVAL, "k_max must be >= 1"};
+  // a Kutta condition replaces a body's symmetric equation: only the Schur form takes it
+  if (b.has_kutta) return schur_solve(b, U, o, dev_psi, body_psi, info);
   b.rhs_active = false;
   b.fixed_bodies = false;
   b.Uv_active = false;

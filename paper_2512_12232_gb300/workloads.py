@@ -138,6 +138,57 @@ def paper_channel_case(delta: float, nx: int = 403, ny: int = 201, sweeps: int =
                 name=f"paper_channel_d{delta:g}", meta={"delta": delta})
 
 
+@dataclass
+class PolygonBody:
+    """A polygonal body: vertices counter-clockwise, the reference point of the polar
+    angle of the surface velocity, and the trailing-edge vertex that carries the Kutta
+    condition (-1: none).  `meta` records how the shape was generated."""
+    vertices: np.ndarray
+    ref: tuple = (0.0, 0.0)
+    kutta: int = -1
+    meta: dict = field(default_factory=dict)
+
+    def __post_init__(self):
+        self.vertices = np.asarray(self.vertices, dtype=np.float64).reshape(-1, 2)
+
+
+def ellipse_body(a: float, b: float, n: int, cx: float = 0.0, cy: float = 0.0, angle: float = 0.0) -> PolygonBody:
+    """n vertices on the ellipse x = a cos t, y = b sin t, turned by `angle` and shifted."""
+    t = 2.0 * np.pi * np.arange(n) / n
+    x = a * np.cos(t)
+    y = b * np.sin(t)
+    c, s = np.cos(angle), np.sin(angle)
+    return PolygonBody(np.stack([cx + c * x - s * y, cy + s * x + c * y], axis=1), ref=(cx, cy),
+                       meta={"a": a, "b": b, "angle": angle})
+
+
+def joukowski_airfoil(k: float, m: float, n: int, alpha: float = 0.0, shift=(0.0, 0.0)) -> PolygonBody:
+    """Symmetric Joukowski airfoil: the circle of radius R = k + m about (-m, 0), mapped by
+    z = zeta + k^2 / zeta, turned by -alpha (a stream along +x then meets it at angle of
+    attack alpha) and shifted; n vertices counter-clockwise from the trailing edge
+    (z = 2k before the turn), which carries the Kutta condition.  Chord about 4k,
+    thickness about 1.3 m/k of the chord."""
+    R = k + m
+    th = 2.0 * np.pi * np.arange(n) / n
+    zeta = -m + R * np.exp(1j * th)
+    z = zeta + k * k / zeta
+    z = z * np.exp(-1j * alpha) + complex(*shift)
+    return PolygonBody(np.stack([z.real, z.imag], axis=1), ref=tuple(shift), kutta=0,
+                       meta={"k": k, "m": m, "R": R, "alpha": alpha, "shift": tuple(shift)})
+
+
+def airfoil_case(nx: int = 256, alpha_deg: float = 6.0, sweeps: int = None, kutta: bool = True):
+    """One Joukowski airfoil (chord about 2, 12% thick, 400 vertices) at angle of attack
+    alpha in [-3,3]x[-1.5,1.5] with psi = U*y on all sides: (Case without circles, the
+    polygon list)."""
+    af = joukowski_airfoil(0.5, 0.08, 400, alpha=np.radians(alpha_deg))
+    if not kutta:
+        af.kutta = -1
+    c = Case(-3.0, 3.0, -1.5, 1.5, nx, nx // 2, np.zeros((0, 3)), nx // 4 if sweeps is None else sweeps,
+             name=f"airfoil_{alpha_deg:g}deg_{nx}x{nx // 2}", meta={"alpha_deg": alpha_deg})
+    return c, [af]
+
+
 def random_vector(n: int, seed: int) -> np.ndarray:
     """Seeded standard-normal float64 vector (used as an operator input)."""
     return np.random.default_rng(seed).standard_normal(n)

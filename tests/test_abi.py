@@ -53,6 +53,19 @@ def test_error_path_without_gpu(lib_path):
     assert lib.pf_velocity_field(None, 0, None, None, None) == _lib.PF_EINVAL
     assert lib.pf_mesh_set_coords(None, 0, None, None) == _lib.PF_EINVAL
     assert lib.pf_coords_vjp(None, None, None, None) == _lib.PF_EINVAL
+    # general shapes: refused on the host before any device work
+    assert lib.pf_batch_build_shapes(None, None, None, 1, 0, None, None, None) == _lib.PF_EINVAL
+    g = (_lib.pf_grid * 1)(_lib.pf_grid(-1.0, 1.0, -1.0, 1.0, 16, 16))
+    off = (C.c_int * 2)(0, 1)
+    bc = (C.c_int * 4)(0, 0, 0, 0)
+    h = C.c_void_p()
+    xy = (C.c_double * 4)(0.0, 0.0, 0.5, 0.0)
+    for shape, msg in [(_lib.pf_shape(7, 0.0, 0.0, 0.3, 0, None, -1), b"kind"),
+                       (_lib.pf_shape(_lib.PF_SHAPE_POLYGON, 0.0, 0.0, 0.0, 2, C.cast(xy, C.POINTER(C.c_double)), -1),
+                        b"3 vertices")]:
+        shapes = (_lib.pf_shape * 1)(shape)
+        assert lib.pf_batch_build_shapes(g, off, shapes, 1, 4, bc, None, C.byref(h)) == _lib.PF_EINVAL
+        assert msg in lib.pf_last_error()
 
 
 def test_product_path_fails_loudly_without_library(tmp_path):

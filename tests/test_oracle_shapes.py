@@ -7,11 +7,12 @@ import pytest
 import scipy.sparse.linalg as spla
 
 from oracle import mesh as M, post as P, shapes as SH, solve as SV, system as S
+from paper_2512_12232_gb300 import workloads as W
 
 
 def test_inside_polygon_matches_a_brute_force_winding_number():
     rng = np.random.default_rng(0)
-    v = SH.ellipse(1.3, 0.6, 37, cx=0.2, cy=-0.1, angle=0.4).vertices
+    v = W.ellipse_body(1.3, 0.6, 37, cx=0.2, cy=-0.1, angle=0.4).vertices
     px, py = rng.uniform(-1.5, 1.5, 2000), rng.uniform(-1.2, 1.2, 2000)
     ins = SH.inside_polygon(px, py, v)
     for x, y, got in zip(px[:400], py[:400], ins[:400]):
@@ -33,7 +34,7 @@ def test_many_sided_polygon_meshes_like_the_circle():
     grid = (-4.0, 4.0, -2.0, 2.0, 96, 48)
     r = 0.77
     t = 2.0 * np.pi * (np.arange(4096) + 0.5) / 4096
-    poly = SH.Polygon(np.stack([0.1 + r * np.cos(t), 0.05 + r * np.sin(t)], axis=1), ref=(0.1, 0.05))
+    poly = W.PolygonBody(np.stack([0.1 + r * np.cos(t), 0.05 + r * np.sin(t)], axis=1), ref=(0.1, 0.05))
     mc = M.build_mesh(grid, np.array([[0.1, 0.05, r]]), 20)
     mp = M.build_mesh(grid, np.zeros((0, 3)), 20, polygons=[poly])
     dist = np.hypot(mc.xg - 0.1, mc.yg - 0.05)
@@ -55,7 +56,7 @@ def test_ellipse_flow_converges_to_the_exact_solution():
     a, b, alpha = 0.8, 0.4, np.radians(10.0)
     errs = []
     for nx in (96, 192):
-        ell = SH.ellipse(a, b, 720, angle=-alpha)
+        ell = W.ellipse_body(a, b, 720, angle=-alpha)
         grid = (-4.0, 4.0, -2.0, 2.0, nx, nx // 2)
         m = M.build_mesh(grid, np.zeros((0, 3)), nx // 4, polygons=[ell])
         g = SH.ellipse_psi(m.x.ravel(), m.y.ravel(), a, b, 1.0, alpha)
@@ -68,7 +69,7 @@ def test_ellipse_flow_converges_to_the_exact_solution():
 
 
 def _airfoil_case(nx, alpha_deg, kutta=True, ny=None):
-    af = SH.joukowski_airfoil(0.5, 0.08, 400, alpha=np.radians(alpha_deg))
+    af = W.joukowski_airfoil(0.5, 0.08, 400, alpha=np.radians(alpha_deg))
     if not kutta:
         af.kutta = -1
     grid = (-3.0, 3.0, -1.5, 1.5, nx, ny or nx // 2)
