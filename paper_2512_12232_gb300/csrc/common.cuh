@@ -118,11 +118,15 @@ struct Sched {                 // persistent tile schedule
 // its vertices (polygons: xy[2 off[k]] .. xy[2 off[k+1]], counter-clockwise), its
 // bounding box (xmin, xmax, ymin, ymax) and the trailing-edge vertex with the Kutta
 // condition (-1: none).  Circles use the pf_body table only.
+struct DBox {                  // axis-aligned box [x0, x1] x [y0, y1]
+  double x0, x1, y0, y1;
+};
+
 struct ShapeDev {
   const int* kind;
   const int* off;            // [B + 1]
   const double* xy;
-  const double4* box;
+  const DBox* box;
   const int* kutta;
 };
 
@@ -136,6 +140,21 @@ struct MeshDev {
   const float* K32;            // [6][Vtot]
   long long Vtot;
 };
+
+// x * 2^-k (0 <= k <= 4), bit for bit the correctly rounded FP64 product x * 2^-k.  For
+// +-0 and for normal x whose exponent field exceeds k + 1, the product is exact and is x
+// with the exponent field lowered by k: one integer subtraction instead of an FP64
+// multiply, which matters where the FP64 pipe is the bound (GB300 runs FP64 at a small
+// fraction of its FP32 rate).  Every other x (tiny or subnormal, Inf, NaN) takes the
+// FP64 multiply.
+static __device__ __noinline__ double pow2_scale_rare(double x, int k) { return __dmul_rn(x, ldexp(1.0, -k)); }
+static __device__ __forceinline__ double pow2_scale(double x, int k) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned e = (unsigned)(b >> 52) & 0x7ffu;
+  if (e > (unsigned)k + 1u && e < 2047u) return __longlong_as_double((long long)(b - ((unsigned long long)k << 52)));
+  if ((b << 1) == 0ull) return x;
+  return pow2_scale_rare(x, k);
+}
 
 // ---------------------------------------------------------------- reductions
 // Compensated two-float accumulation (Knuth TwoSum + exact FMA products, the Dot2

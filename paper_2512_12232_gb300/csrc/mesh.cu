@@ -47,8 +47,8 @@ __device__ __forceinline__ TileCtx tile_ctx(const DevVariant* var, const int* ti
 // Crossing-number test of (x, y) against polygon gb: an edge (a, b) is crossed when
 // (a_y > y) != (b_y > y) and x < a_x + ((y - a_y)(b_x - a_x)) / (b_y - a_y); odd = inside.
 __device__ bool inside_polygon(const ShapeDev& S, int gb, double x, double y) {
-  const double4 bx = S.box[gb];
-  if (x < bx.x || x > bx.y || y < bx.z || y > bx.w) return false;   // the count is even there
+  const DBox bx = S.box[gb];
+  if (x < bx.x0 || x > bx.x1 || y < bx.y0 || y > bx.y1) return false;   // the count is even there
   const int v0 = S.off[gb], n = S.off[gb + 1] - v0;
   const double* p = S.xy + 2 * v0;
   bool in = false;
@@ -248,6 +248,11 @@ __global__ void __launch_bounds__(256) k_kutta(const DevVariant* var, const int*
 //    zero farther than s + 1 cells from every body node, so a tile farther than the
 //    reach of the launch's last sweep from every body's node box is all zeros in both
 //    ping-pong buffers and is skipped.
+// x / 4, correctly rounded (bit for bit the oracle's division; see pow2_scale): the
+// smoothing is bound by the FP64 pipe, which then runs three additions per component
+// instead of three additions and a multiply.
+__device__ __forceinline__ double quarter(double x) { return pow2_scale(x, 2); }
+
 constexpr int JK = 4;
 constexpr int JRW = CTX + 2 * JK, JRH = CTY + 2 * JK;      // window 72 x 24
 constexpr int JACOBI_SMEM = 2 * JRW * JRH * (int)sizeof(double2) + JRW * JRH;
@@ -302,10 +307,7 @@ __global__ void __launch_bounds__(NT) k_jacobi(const DevVariant* var, const int*
         const double2 w = a[q - 1], e = a[q + 1], s = a[q - JRW], nn = a[q + JRW];
         const double sx = __dadd_rn(__dadd_rn(__dadd_rn(w.x, e.x), s.x), nn.x);
         const double sy = __dadd_rn(__dadd_rn(__dadd_rn(w.y, e.y), s.y), nn.y);
-        // the sum divided by 4: a power of two, so x / 4 and x * 0.25 are the correctly
-        // rounded values of the same real number and agree bit for bit (subnormals
-        // included); the product costs one FP64 multiply instead of a division
-        out = make_double2(__dmul_rn(sx, 0.25), __dmul_rn(sy, 0.25));
+        out = make_double2(quarter(sx), quarter(sy));
       }
       b[q] = out;
     }
@@ -671,21 +673,21 @@ void build_batch(Batch& b, const pf_grid* grids, const int* body_offsets, const 
   }
   b.has_polygons = std::find(b.shape_kind.begin(), b.shape_kind.end(), (int)PF_SHAPE_POLYGON) != b.shape_kind.end();
   b.has_kutta = false;
-  std::vector<double4> pbox(std::max(1, b.B), make_double4(0, 0, 0, 0));
+  std::vector<DBox> pbox(std::max(1, b.B), DBox{0, 0, 0, 0});
   for (int k = 0; k < b.B; ++k) {
     if (b.shape_kind[k] == PF_SHAPE_POLYGON) {
       const int v0 = b.poly_off[k], n = b.poly_off[k + 1] - v0;
       if (n < 3) throw Error{PF_EINVAL, "body " + std::to_string(k) + ": a polygon needs at least 3 vertices"};
       const double* p = b.poly_xy.data() + 2 * v0;
       double area2 = 0.0;
-      double4 bx = make_double4(p[0], p[0], p[1], p[1]);
+      DBox bx{p[0], p[0], p[1], p[1]};
       for (int e = 0; e < n; ++e) {
         const int f = (e + 1) % n;
         area2 += p[2 * e] * p[2 * f + 1] - p[2 * f] * p[2 * e + 1];
-        bx.x = std::min(bx.x, p[2 * e]);
-        bx.y = std::max(bx.y, p[2 * e]);
-        bx.z = std::min(bx.z, p[2 * e + 1]);
-        bx.w = std::max(bx.w, p[2 * e + 1]);
+        bx.x0 = std::min(bx.x0, p[2 * e]);
+        bx.x1 = std::max(bx.x1, p[2 * e]);
+        bx.y0 = std::min(bx.y0, p[2 * e + 1]);
+        bx.y1 = std::max(bx.y1, p[2 * e + 1]);
       }
       if (!(area2 > 0)) throw Error{PF_EINVAL, "body " + std::to_string(k) + ": polygon vertices must run counter-clockwise"};
       if (b.kutta[k] >= n) throw Error{PF_EINVAL, "body " + std::to_string(k) + ": Kutta vertex out of range"};
@@ -693,7 +695,7 @@ void build_batch(Batch& b, const pf_grid* grids, const int* body_offsets, const 
       pbox[k] = bx;
     } else {
       const pf_body& B = b.bodies[k];
-      pbox[k] = make_double4(B.cx - B.r, B.cx + B.r, B.cy - B.r, B.cy + B.r);
+      pbox[k] = DBox{B.cx - B.r, B.cx + B.r, B.cy - B.r, B.cy + B.r};
     }
   }
 
@@ -747,15 +749,15 @@ void build_batch(Batch& b, const pf_grid* grids, const int* body_offsets, const 
       const bool poly = b.shape_kind[gk] == PF_SHAPE_POLYGON;
       if (!poly && !(B.r > 0))
         throw Error{PF_EINVAL, "variant " + std::to_string(v) + ": body radius must be positive"};
-      const double4 bx = pbox[gk];
-      if (bx.x < g.x0 + 2 * H.hx || bx.y > g.x1 - 2 * H.hx || bx.z < g.y0 + 2 * H.hy || bx.w > g.y1 - 2 * H.hy)
+      const DBox bx = pbox[gk];
+      if (bx.x0 < g.x0 + 2 * H.hx || bx.x1 > g.x1 - 2 * H.hx || bx.y0 < g.y0 + 2 * H.hy || bx.y1 > g.y1 - 2 * H.hy)
         throw Error{PF_EINVAL, "variant " + std::to_string(v) + ": body within 2h of the outer boundary"};
       for (int k2 = 0; k2 < k; ++k2) {
         const int gk2 = H.body0 + k2;
         const pf_body& C = b.bodies[gk2];
         if (poly || b.shape_kind[gk2] == PF_SHAPE_POLYGON) {
-          const double4 cb = pbox[gk2];   // conservative: bounding boxes of polygons may not overlap
-          if (!(bx.y < cb.x || cb.y < bx.x || bx.w < cb.z || cb.w < bx.z))
+          const DBox cb = pbox[gk2];   // conservative: bounding boxes of polygons may not overlap
+          if (!(bx.x1 < cb.x0 || cb.x1 < bx.x0 || bx.y1 < cb.y0 || cb.y1 < bx.y0))
             throw Error{PF_EINVAL, "variant " + std::to_string(v) + ": body bounding boxes overlap"};
           continue;
         }
@@ -766,10 +768,10 @@ void build_batch(Batch& b, const pf_grid* grids, const int* body_offsets, const 
       // node box of the body (polygons: 3 more cells, a Kutta wake node lies near the box)
       const int pad = poly ? 4 : 1;
       int4 bb;
-      bb.x = std::max(0, (int)std::floor((bx.x - g.x0) / H.hx) - pad);
-      bb.y = std::min(g.nx, (int)std::ceil((bx.y - g.x0) / H.hx) + pad);
-      bb.z = std::max(0, (int)std::floor((bx.z - g.y0) / H.hy) - pad);
-      bb.w = std::min(g.ny, (int)std::ceil((bx.w - g.y0) / H.hy) + pad);
+      bb.x = std::max(0, (int)std::floor((bx.x0 - g.x0) / H.hx) - pad);
+      bb.y = std::min(g.nx, (int)std::ceil((bx.x1 - g.x0) / H.hx) + pad);
+      bb.z = std::max(0, (int)std::floor((bx.y0 - g.y0) / H.hy) - pad);
+      bb.w = std::min(g.ny, (int)std::ceil((bx.y1 - g.y0) / H.hy) + pad);
       bbox[H.body0 + k] = bb;
       body_var[H.body0 + k] = v;
     }

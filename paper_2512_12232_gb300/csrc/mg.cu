@@ -176,14 +176,18 @@ __global__ void k_mg_rap(LvArgs c, double* A64c, float* A32c, float* dinvc, Mesh
   };
   if (c.act[q.k]) {
     const int fx = fine_of(q.i, df.x), fy = fine_of(q.j, df.y);
+    // every interpolation weight is 1 or 1/2, so each product weight x stencil entry is
+    // the entry scaled by a power of two: exact, formed by pow2_scale with the number of
+    // halves (the same value as the FP64 product, without the FP64 multiplies)
     for (int ay = fy - 1; ay <= fy + 1; ++ay) {
       if (ay < 0 || ay > df.y) continue;
       const double wy = pw(ay, df.y, q.j);
       if (wy == 0.0) continue;
       for (int ax = fx - 1; ax <= fx + 1; ++ax) {
         if (ax < 0 || ax > df.x) continue;
-        const double wa = pw(ax, df.x, q.i) * wy;
-        if (wa == 0.0 || !factive(ax, ay)) continue;
+        const double wxa = pw(ax, df.x, q.i);
+        const int ha = (wxa == 0.5) + (wy == 0.5);       // halves of wa = wxa * wy
+        if (wxa == 0.0 || !factive(ax, ay)) continue;
         double st[9];
         const long long na = fidx(ax, ay);
         if (fine0) fine_stencil(m, V, na, ax, ay, st);
@@ -202,7 +206,7 @@ __global__ void k_mg_rap(LvArgs c, double* A64c, float* A32c, float* dinvc, Mesh
                 const int ddx = Ix[t] - q.i, ddy = Iy[u] - q.j;
                 if (ddx < -1 || ddx > 1 || ddy < -1 || ddy > 1) continue;
                 if (!c.act[q.k + (long long)ddy * (q.nx + 1) + ddx]) continue;
-                acc[(ddy + 1) * 3 + ddx + 1] += wa * sv * wx[t] * wyb[u];
+                acc[(ddy + 1) * 3 + ddx + 1] += pow2_scale(sv, ha + (wx[t] == 0.5) + (wyb[u] == 0.5));
               }
           }
       }
