@@ -271,9 +271,9 @@ pf_status pf_apply(pf_batch* b, int precision, const double* dev_p, double* dev_
    exit.  A handle with more than PF_NOALLOC_MAX_BODIES bodies in total is rejected with
    PF_EINVAL.  The handle is only read, never modified.  The first call on a device looks
    up that array's device address (once per device) and keeps it for the life of the
-   process, so the library is not to be used across a cudaDeviceReset; make that first
-   call before any stream capture.  The call waits for `stream` to finish its work before
-   returning.  Every call on a device shares the array and it keeps the last call's
+   process, so the library is not to be used across a cudaDeviceReset.  The call waits
+   for `stream` to finish its work before returning, so it cannot be captured: on a
+   capturing stream it returns PF_EINVAL before launching anything.  Every call on a device shares the array and it keeps the last call's
    contents; each call overwrites what it reads back.  Calls that overlap on the GPU
    (e.g. on two streams at once) race on it. */
 pf_status pf_apply_noalloc(const pf_batch* b, int precision, const double* dev_p, double* dev_y,

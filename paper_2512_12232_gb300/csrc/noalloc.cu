@@ -175,6 +175,10 @@ extern "C" pf_status pf_apply_noalloc(const pf_batch* h, int precision, const do
     if (dev != b->device) throw Error{PF_EINVAL, "call made with another device current than the handle's"};
     if (!dev_p || !dev_y) throw Error{PF_EINVAL, "NULL vector"};
     if (precision != PF_FP64 && precision != PF_MIXED) throw Error{PF_EINVAL, "invalid precision"};
+    // the call ends by synchronising its stream, which a capturing stream does not allow
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    PF_CUDA(cudaStreamIsCapturing((cudaStream_t)stream, &cap));
+    if (cap != cudaStreamCaptureStatusNone) throw Error{PF_EINVAL, "the stream is capturing"};
     apply_operator_noalloc(*b, precision, dev_p, dev_y, body_sums, (cudaStream_t)stream);
     return PF_OK;
   } catch (const Error& e) {

@@ -92,3 +92,27 @@ def test_noalloc_apply_rejects_a_call_on_another_device():
             code = lib.pf_apply_noalloc(g.handle, api.PF_FP64, C.c_void_p(p.data_ptr()), C.c_void_p(p.data_ptr()),
                                         None, None)
         assert code == L.PF_EINVAL
+
+
+def test_noalloc_apply_refuses_a_capturing_stream():
+    """The call ends by synchronising its stream, so on a stream that is being captured it
+    returns PF_EINVAL before launching anything; the capture itself stays valid."""
+    from paper_2512_12232_gb300 import _lib as L, api
+    lib = L.load()
+    c = W.single_cylinder()
+    with api.mesh_build(c.grid, c.bodies, c.sweeps, c.bc) as g:
+        p = torch.from_numpy(W.random_vector(c.n_nodes, 9)).cuda()
+        y = torch.zeros_like(p)
+        x = torch.zeros(16, device="cuda")
+        s = torch.cuda.Stream()
+        graph = torch.cuda.CUDAGraph()
+        torch.cuda.synchronize()
+        with torch.cuda.graph(graph, stream=s):
+            x.add_(1.0)
+            code = lib.pf_apply_noalloc(g.handle, api.PF_FP64, C.c_void_p(p.data_ptr()), C.c_void_p(y.data_ptr()),
+                                        None, C.c_void_p(s.cuda_stream))
+        assert code == L.PF_EINVAL
+        assert b"capturing" in lib.pf_last_error()
+        graph.replay()
+        torch.cuda.synchronize()
+        assert torch.count_nonzero(y).item() == 0 and x[0].item() == 1.0
