@@ -55,8 +55,7 @@ struct MgLevel {
   int2* d_dims = nullptr;
   int* d_blkvar = nullptr;           // [nblk] variant of each block
   uint8_t* act = nullptr;            // coarse node carries an unknown
-  double* A64 = nullptr;             // [9][n] Galerkin stencil (setup precision)
-  float* A32 = nullptr;              // [9][n] the same in FP32 (the cycle)
+  float* A32 = nullptr;              // [9][n] Galerkin stencil (FP32: set-up and cycle)
   float* dinv = nullptr;             // omega / diagonal at active nodes, else 0
   float *r = nullptr, *za = nullptr, *zb = nullptr, *res = nullptr;
 };

@@ -11,7 +11,7 @@
 //     line copies its coarse node).  A coarse node carries an unknown only if the fine node
 //     under it does (constraints are injected), and P has no entries for constrained
 //     nodes.  Coarse operators are Galerkin products A_{l+1} = P^T A_l P (9-point
-//     stencils, formed once in FP64).  Smoother: damped Jacobi (omega = 0.85), two sweeps
+//     stencils, formed once in FP32, the precision the cycle applies them in).  Smoother: damped Jacobi (omega = 0.85), two sweeps
 //     before and two after the coarse correction; the coarsest level (at most 17 x 17
 //     nodes) takes 100 Jacobi sweeps from zero.  Jacobi with a fixed sweep
 //     count is a fixed symmetric operator, so the cycle is a valid CG preconditioner.
@@ -107,6 +107,39 @@ __device__ void fine_stencil(const MeshDev& m, const DevVariant& V, long long n,
   st[4] = -s;
 }
 
+// The same row from the FP32 coefficients, summed in FP32 (the multigrid set-up: the
+// preconditioner's operators are FP32, and FP64 arithmetic runs at a small fraction of
+// the FP32 rate on this GPU).
+__device__ void fine_stencil32(const MeshDev& m, const DevVariant& V, long long n, int i, int j, float st[9]) {
+  for (int k = 0; k < 9; ++k) st[k] = 0.0f;
+  const long long plane = m.Vtot;
+  const long long P = V.P;
+  auto coef = [&](long long c, int mm, bool gen) { return gen ? m.K32[mm * plane + c] : V.kr32[mm]; };
+  if (i < V.nx && j < V.ny && (m.tag[n] & CELL_ACTIVE)) {
+    const bool g = m.tag[n] & CELL_GENERAL;
+    st[5] += coef(n, 0, g); st[8] += coef(n, 1, g); st[7] += coef(n, 2, g);
+  }
+  if (i > 0 && j < V.ny && (m.tag[n - 1] & CELL_ACTIVE)) {
+    const long long c = n - 1;
+    const bool g = m.tag[c] & CELL_GENERAL;
+    st[3] += coef(c, 0, g); st[7] += coef(c, 3, g); st[6] += coef(c, 4, g);
+  }
+  if (i > 0 && j > 0 && (m.tag[n - P - 1] & CELL_ACTIVE)) {
+    const long long c = n - P - 1;
+    const bool g = m.tag[c] & CELL_GENERAL;
+    st[0] += coef(c, 1, g); st[1] += coef(c, 3, g); st[3] += coef(c, 5, g);
+  }
+  if (j > 0 && i < V.nx && (m.tag[n - P] & CELL_ACTIVE)) {
+    const long long c = n - P;
+    const bool g = m.tag[c] & CELL_GENERAL;
+    st[1] += coef(c, 2, g); st[2] += coef(c, 4, g); st[5] += coef(c, 5, g);
+  }
+  float s = 0.0f;
+  for (int k = 0; k < 9; ++k)
+    if (k != 4) s += st[k];
+  st[4] = -s;
+}
+
 // Node of a packed coarse level handled by this thread: variant, (i, j) and the index,
 // or false for padding / variants without the level.
 struct LvNode {
@@ -156,13 +189,13 @@ __global__ void k_mg_act(LvArgs c, const uint8_t* act_f, const long long* off_f,
 }
 
 // Galerkin stencil of coarse node I = sum_{a, b} P(a, I) A_f(a, b) P(b, J) over active
-// fine nodes a, b, in FP64, with its FP32 copy and the Jacobi factor.
-__global__ void k_mg_rap(LvArgs c, double* A64c, float* A32c, float* dinvc, MeshDev m, const uint8_t* act_f,
-                         const double* A64f, const long long* off_f, const int2* dims_f, long long nf) {
+// fine nodes a, b, in FP32 (the precision the cycle applies it in), and the Jacobi factor.
+__global__ void k_mg_rap(LvArgs c, float* A32c, float* dinvc, MeshDev m, const uint8_t* act_f, const float* A32f,
+                         const long long* off_f, const int2* dims_f, long long nf) {
   LvNode q;
   if (!lv_node(c.off, c.dims, c.blkvar, q)) return;
-  double acc[9];
-  for (int k = 0; k < 9; ++k) acc[k] = 0.0;
+  float acc[9];
+  for (int k = 0; k < 9; ++k) acc[k] = 0.0f;
   const DevVariant& V = m.var[q.v];
   const bool fine0 = off_f == nullptr;
   const int2 df = fine0 ? make_int2(V.nx, V.ny) : dims_f[q.v];
@@ -177,8 +210,7 @@ __global__ void k_mg_rap(LvArgs c, double* A64c, float* A32c, float* dinvc, Mesh
   if (c.act[q.k]) {
     const int fx = fine_of(q.i, df.x), fy = fine_of(q.j, df.y);
     // every interpolation weight is 1 or 1/2, so each product weight x stencil entry is
-    // the entry scaled by a power of two: exact, formed by pow2_scale with the number of
-    // halves (the same value as the FP64 product, without the FP64 multiplies)
+    // the entry scaled by 2^-h (h halves): exact, one FP32 multiply by that power of two
     for (int ay = fy - 1; ay <= fy + 1; ++ay) {
       if (ay < 0 || ay > df.y) continue;
       const double wy = pw(ay, df.y, q.j);
@@ -188,16 +220,16 @@ __global__ void k_mg_rap(LvArgs c, double* A64c, float* A32c, float* dinvc, Mesh
         const double wxa = pw(ax, df.x, q.i);
         const int ha = (wxa == 0.5) + (wy == 0.5);       // halves of wa = wxa * wy
         if (wxa == 0.0 || !factive(ax, ay)) continue;
-        double st[9];
+        float st[9];
         const long long na = fidx(ax, ay);
-        if (fine0) fine_stencil(m, V, na, ax, ay, st);
+        if (fine0) fine_stencil32(m, V, na, ax, ay, st);
         else
-          for (int k = 0; k < 9; ++k) st[k] = A64f[k * nf + na];
+          for (int k = 0; k < 9; ++k) st[k] = A32f[k * nf + na];
         for (int dy = -1; dy <= 1; ++dy)
           for (int dx = -1; dx <= 1; ++dx) {
-            const double sv = st[(dy + 1) * 3 + dx + 1];
+            const float sv = st[(dy + 1) * 3 + dx + 1];
             const int bx = ax + dx, by = ay + dy;
-            if (sv == 0.0 || bx < 0 || by < 0 || bx > df.x || by > df.y || !factive(bx, by)) continue;
+            if (sv == 0.0f || bx < 0 || by < 0 || bx > df.x || by > df.y || !factive(bx, by)) continue;
             int Ix[2], Iy[2];
             double wx[2], wyb[2];
             const int nxp = parents(bx, df.x, Ix, wx), nyp = parents(by, df.y, Iy, wyb);
@@ -206,17 +238,15 @@ __global__ void k_mg_rap(LvArgs c, double* A64c, float* A32c, float* dinvc, Mesh
                 const int ddx = Ix[t] - q.i, ddy = Iy[u] - q.j;
                 if (ddx < -1 || ddx > 1 || ddy < -1 || ddy > 1) continue;
                 if (!c.act[q.k + (long long)ddy * (q.nx + 1) + ddx]) continue;
-                acc[(ddy + 1) * 3 + ddx + 1] += pow2_scale(sv, ha + (wx[t] == 0.5) + (wyb[u] == 0.5));
+                const int h = ha + (wx[t] == 0.5) + (wyb[u] == 0.5);
+                acc[(ddy + 1) * 3 + ddx + 1] += sv * __int_as_float((127 - h) << 23);   // sv * 2^-h
               }
           }
       }
     }
   }
-  for (int k = 0; k < 9; ++k) {
-    A64c[k * c.n + q.k] = acc[k];
-    A32c[k * c.n + q.k] = (float)acc[k];
-  }
-  dinvc[q.k] = (c.act[q.k] && acc[4] > 0.0) ? (float)(MG_OMEGA / acc[4]) : 0.0f;
+  for (int k = 0; k < 9; ++k) A32c[k * c.n + q.k] = acc[k];
+  dinvc[q.k] = (c.act[q.k] && acc[4] > 0.0f) ? (float)MG_OMEGA / acc[4] : 0.0f;
 }
 
 // Jacobi factor of the fine level: omega / diagonal at FREE nodes.
@@ -228,9 +258,9 @@ __global__ void k_mg_dinv0(MeshDev m, const int* tile_var, const int2* tile_ij, 
   const long long n = V.base + (long long)j * V.P + i;
   float d = 0.0f;
   if ((m.tag[n] & KIND_MASK) == K_FREE) {
-    double st[9];
-    fine_stencil(m, V, n, i, j, st);
-    d = st[4] > 0.0 ? (float)(MG_OMEGA / st[4]) : 0.0f;
+    float st[9];
+    fine_stencil32(m, V, n, i, j, st);
+    d = st[4] > 0.0f ? (float)MG_OMEGA / st[4] : 0.0f;
   }
   dinv0[n] = d;
 }
@@ -843,9 +873,8 @@ void mg_setup(Batch& b) {
     MgLevel& F = b.mg[l - 1];
     k_mg_act<<<(unsigned)M.nblk, 256, 0, s>>>(c, f0 ? nullptr : F.act, f0 ? nullptr : F.d_off,
                                                f0 ? nullptr : F.d_dims, b.d_var, b.tag, M.act);
-    k_mg_rap<<<(unsigned)M.nblk, 256, 0, s>>>(c, M.A64, M.A32, M.dinv, m, f0 ? nullptr : F.act,
-                                               f0 ? nullptr : F.A64, f0 ? nullptr : F.d_off,
-                                               f0 ? nullptr : F.d_dims, f0 ? 0 : F.n);
+    k_mg_rap<<<(unsigned)M.nblk, 256, 0, s>>>(c, M.A32, M.dinv, m, f0 ? nullptr : F.act, f0 ? nullptr : F.A32,
+                                               f0 ? nullptr : F.d_off, f0 ? nullptr : F.d_dims, f0 ? 0 : F.n);
   }
   PF_CUDA(cudaGetLastError());
   b.launches += 1 + (b.B > 0 ? 1 : 0) + 2 * (L - 1);
@@ -901,7 +930,6 @@ static void mg_layout(Batch& b) {
     PF_CUDA(cudaMemcpyAsync(M.d_blkvar, blkvar.data(), blkvar.size() * sizeof(int), cudaMemcpyHostToDevice,
                             b.stream));
     M.act = (uint8_t*)dev_alloc(b, M.n);
-    M.A64 = (double*)dev_alloc(b, 9 * M.n * sizeof(double));
     M.A32 = (float*)dev_alloc(b, 9 * M.n * sizeof(float));
     M.dinv = (float*)dev_alloc(b, M.n * sizeof(float));
     M.r = (float*)dev_alloc(b, M.n * sizeof(float));
@@ -910,7 +938,6 @@ static void mg_layout(Batch& b) {
     M.res = (float*)dev_alloc(b, M.n * sizeof(float));
     PF_CUDA(cudaMemsetAsync(M.act, 0, M.n, b.stream));
     for (float* f : {M.r, M.za, M.zb, M.res, M.dinv}) PF_CUDA(cudaMemsetAsync(f, 0, M.n * sizeof(float), b.stream));
-    PF_CUDA(cudaMemsetAsync(M.A64, 0, 9 * M.n * sizeof(double), b.stream));
     PF_CUDA(cudaMemsetAsync(M.A32, 0, 9 * M.n * sizeof(float), b.stream));
   }
 }
