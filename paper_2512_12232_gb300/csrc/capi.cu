@@ -125,6 +125,7 @@ pf_status pf_batch_build(const pf_grid* grids, const int* body_offsets, const pf
 
 pf_status pf_batch_build_shapes(const pf_grid* grids, const int* body_offsets, const pf_shape* shapes,
                                 int n_variants, int sweeps, const int bc[4], void* stream, pf_batch** out) {
+  if (out) *out = nullptr;
   if (!out || !body_offsets || n_variants < 1) {
     g_err = "invalid arguments";
     return PF_EINVAL;
@@ -134,26 +135,32 @@ pf_status pf_batch_build_shapes(const pf_grid* grids, const int* body_offsets, c
     g_err = "shapes is NULL";
     return PF_EINVAL;
   }
-  std::vector<pf_body> bodies(std::max(1, B));
+  std::vector<pf_body> bodies;
   ShapeInput si;
-  si.off.push_back(0);
-  for (int k = 0; k < B; ++k) {
-    const pf_shape& sh = shapes[k];
-    if (sh.kind != PF_SHAPE_CIRCLE && sh.kind != PF_SHAPE_POLYGON) {
-      g_err = "invalid shape kind";
-      return PF_EINVAL;
-    }
-    bodies[k] = pf_body{sh.cx, sh.cy, sh.kind == PF_SHAPE_CIRCLE ? sh.r : 0.0};
-    si.kind.push_back(sh.kind);
-    si.kutta.push_back(sh.kind == PF_SHAPE_POLYGON ? sh.kutta_vertex : -1);
-    if (sh.kind == PF_SHAPE_POLYGON) {
-      if (sh.n_vertices < 3 || !sh.vertex_xy) {
-        g_err = "a polygon needs at least 3 vertices";
+  try {
+    bodies.resize(std::max(1, B));
+    si.off.push_back(0);
+    for (int k = 0; k < B; ++k) {
+      const pf_shape& sh = shapes[k];
+      if (sh.kind != PF_SHAPE_CIRCLE && sh.kind != PF_SHAPE_POLYGON) {
+        g_err = "invalid shape kind";
         return PF_EINVAL;
       }
-      si.xy.insert(si.xy.end(), sh.vertex_xy, sh.vertex_xy + 2 * (size_t)sh.n_vertices);
+      bodies[k] = pf_body{sh.cx, sh.cy, sh.kind == PF_SHAPE_CIRCLE ? sh.r : 0.0};
+      si.kind.push_back(sh.kind);
+      si.kutta.push_back(sh.kind == PF_SHAPE_POLYGON ? sh.kutta_vertex : -1);
+      if (sh.kind == PF_SHAPE_POLYGON) {
+        if (sh.n_vertices < 3 || !sh.vertex_xy) {
+          g_err = "a polygon needs at least 3 vertices";
+          return PF_EINVAL;
+        }
+        si.xy.insert(si.xy.end(), sh.vertex_xy, sh.vertex_xy + 2 * (size_t)sh.n_vertices);
+      }
+      si.off.push_back((int)(si.xy.size() / 2));
     }
-    si.off.push_back((int)(si.xy.size() / 2));
+  } catch (const std::exception& e) {
+    g_err = std::string("host allocation failed: ") + e.what();
+    return PF_ENOMEM;
   }
   return build_handle(grids, body_offsets, bodies.data(), n_variants, sweeps, bc, stream, out, &si);
 }
