@@ -48,6 +48,7 @@ void destroy_phi_view(Batch& b) {
   Batch* p = b.phi;
   for (int k = 0; k < 2; ++k)
     if (p->graph[k]) cudaGraphExecDestroy(p->graph[k]);
+  if (p->graph_pcg) cudaGraphExecDestroy(p->graph_pcg);
   for (int k = 0; k < Batch::N_EV; ++k)
     if (p->ev[k]) cudaEventDestroy(p->ev[k]);
   if (p->h_poll) cudaFreeHost(p->h_poll);
