@@ -203,8 +203,10 @@ typedef struct pf_shape {
      leaves T along w and the circulation follows (pf_psi_solve then runs the Schur form, the
      only form that allows that non-symmetric equation: the small body system is eliminated
      with partial pivoting, info[v].iters sums the fixed-body solves' iterations and
-     info[v].rel_true_residual is the largest of their residuals; pf_phi_solve and pf_grad
-     refuse such a handle).
+     info[v].rel_true_residual is the largest of their residuals; pf_phi_solve refuses such
+     a handle).
+   - pf_grad and pf_coords_vjp refuse any handle with a polygon (the shape derivative is
+     written for circles).
    - Polygons need >= 3 vertices in counter-clockwise order; their bounding boxes must stay
      2h inside the box and may not overlap any other body's bounding box.
    Otherwise as pf_batch_build (body_offsets index `shapes`). */
