@@ -107,9 +107,10 @@ enum { PF_TOL_REL_TRUE = 0,     /* ||b - A u||_2 / ||b||_2 <= tol, the FP64 true
    whose Appendix A CG is unpreconditioned and needs a number of iterations that grows with the
    grid).  PF_PRECOND_MG: each CG iteration applies one V(2,2)-cycle of geometric multigrid on
    the logical node grid of every variant to the free unknowns (Galerkin coarse operators,
-   bilinear interpolation, constraints injected on coarse nodes, damped Jacobi smoothing) and
-   the inverse diagonal of the collapsed body row to each body unknown.  The preconditioner is
-   a fixed symmetric positive-definite operator, so the iterates converge to the same solution;
+   bilinear interpolation, constraints injected on coarse nodes, damped Jacobi smoothing),
+   coupled to the body unknowns by a symmetric block Gauss-Seidel sweep (body, free, body;
+   each body by the diagonal of its collapsed row).  The preconditioner is a fixed symmetric
+   positive-definite operator, so the iterates converge to the same solution;
    convergence is decided by the same FP64 true residual and refinement.  The hierarchy is
    built on the first such solve of a handle (and again after pf_mesh_set_coords). */
 enum { PF_PRECOND_NONE = 0, PF_PRECOND_MG = 1 };

@@ -180,6 +180,12 @@ struct Batch {
   float *mg_p[2] = {nullptr, nullptr}, *mg_q = nullptr, *mg_dinv0 = nullptr;
   double* mg_part = nullptr;         // [T] per-tile partial sums of one dot product
   double* mg_Abb = nullptr;          // [B] diagonal of the collapsed body rows
+  float* mg_yb = nullptr;            // [B] body values of the forward body step of the cycle
+  // free nodes next to each body (CSR over global bodies, row-major in the body's box) and
+  // their coupling c = sum of A(n, m) over the body's nodes m: A_fb and A_bf of the cycle
+  int* mg_adj_ptr = nullptr;
+  long long* mg_adj_node = nullptr;
+  float* mg_adj_c = nullptr;
   cudaGraphExec_t graph_pcg = nullptr;
   int graph_pcg_chunk = 0;
   bool dirichlet_x = false;          // Dirichlet data U x (the velocity potential) instead of U y

@@ -157,6 +157,7 @@ static __device__ __forceinline__ double pow2_scale(double x, int k) {
 }
 
 // ---------------------------------------------------------------- reductions
+
 // Compensated two-float accumulation (Knuth TwoSum + exact FMA products, the Dot2
 // scheme of Ogita, Rump and Oishi): every FP32 product x*y is split exactly into
 // p + e with e = fma(x, y, -p), p is added to the high word with TwoSum and the two
@@ -253,6 +254,30 @@ template <> struct Acc<float> {
 };
 
 __device__ __forceinline__ int linear_tid() { return threadIdx.y * TX + threadIdx.x; }
+
+// Block-wide exclusive scan of one int per thread (256 threads, 1-D linear id).
+static __device__ __forceinline__ int block_exscan(int x, int* total, int* sh /* >= NT/32 + 1 */) {
+  const int tid = linear_tid(), lane = tid & 31, w = tid >> 5;
+  int incl = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  __syncthreads();
+  if (lane == 31) sh[w] = incl;
+  __syncthreads();
+  if (tid == 0) {
+    int s = 0;
+    for (int k = 0; k < NT / 32; ++k) { int t = sh[k]; sh[k] = s; s += t; }
+    sh[NT / 32] = s;
+  }
+  __syncthreads();
+  const int r = sh[w] + incl - x;
+  *total = sh[NT / 32];
+  __syncthreads();
+  return r;
+}
 
 // Atomic add with acquire-release semantics at GPU scope; returns the old value.  Used
 // as the arrival of a CTA at a per-variant counter: it publishes the CTA's stores

@@ -427,8 +427,6 @@ __global__ void k_stiffness(const DevVariant* var, const int* tile_var, const in
   if (tid == 0 && dmin < 1e300) atomic_min_double(&detmin[c.v], dmin);
 }
 
-__device__ int block_exscan(int x, int* total, int* sh /* >= 9 */);
-
 // 5b. per fused-CG tile: does any cell used by the tile (cells i0-1 .. i0+CTX-1,
 //     j0-1 .. j0+CTY-1 of its variant) carry stored coefficients (bit 0: FP64 operator,
 //     bit 1: FP32 operator); is the tile "plain" for that operator (bit 2: FP64, bit 3:
@@ -473,30 +471,6 @@ __global__ void k_tile_general(const DevVariant* var, const int* tile_var, const
                        (allfree && !g32 ? TILE_PLAIN32 : 0));
     act[t] = tot;
   }
-}
-
-// Block-wide exclusive scan of one int per thread (256 threads, 1-D linear id).
-__device__ int block_exscan(int x, int* total, int* sh /* >= 9 */) {
-  const int tid = linear_tid(), lane = tid & 31, w = tid >> 5;
-  int incl = x;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    int y = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += y;
-  }
-  __syncthreads();
-  if (lane == 31) sh[w] = incl;
-  __syncthreads();
-  if (tid == 0) {
-    int s = 0;
-    for (int k = 0; k < NT / 32; ++k) { int t = sh[k]; sh[k] = s; s += t; }
-    sh[NT / 32] = s;
-  }
-  __syncthreads();
-  const int r = sh[w] + incl - x;
-  *total = sh[NT / 32];
-  __syncthreads();
-  return r;
 }
 
 // 6. per-body node lists (row-major inside the body's node box).  pass 0 counts,
