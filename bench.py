@@ -651,7 +651,7 @@ def run_ours(args, rank, world, local):
                    if args.precision == "mixed" else "FP64",
                    "inner_tol": args.inner_tol, "parallelism": f"replicas x{world}",
                    "preconditioner": "none (the paper's CG)" if args.precond == "none"
-                   else "geometric multigrid V(2,2) (PF_PRECOND_MG)",
+                   else "geometric multigrid V(1,1) (PF_PRECOND_MG)",
                    "l2": "inputs larger than L2: each step builds fresh meshes (working set "
                          f"{int(nodes) * 48 / 1e6:.0f} MB of CG state and coefficients, L2 is 126 MB)"},
         "solves_per_s": vals[2] / vals[1], "all_converged": ok,

@@ -105,7 +105,7 @@ enum { PF_TOL_REL_TRUE = 0,     /* ||b - A u||_2 / ||b||_2 <= tol, the FP64 true
 
 /* Preconditioners of a solve (pf_solve_opts.preconditioner; an extension beyond the paper,
    whose Appendix A CG is unpreconditioned and needs a number of iterations that grows with the
-   grid).  PF_PRECOND_MG: each CG iteration applies one V(2,2)-cycle of geometric multigrid on
+   grid).  PF_PRECOND_MG: each CG iteration applies one V(1,1)-cycle of geometric multigrid on
    the logical node grid of every variant to the free unknowns (Galerkin coarse operators,
    bilinear interpolation, constraints injected on coarse nodes, damped Jacobi smoothing),
    coupled to the body unknowns by a symmetric block Gauss-Seidel sweep (body, free, body;

@@ -3,7 +3,7 @@
 // count grows with the grid, about 2,100 iterations on a 1024x512 grid).
 //
 // Preconditioner M^-1 (symmetric positive definite, the same every iteration):
-//   * free unknowns: one V(2,2)-cycle of geometric multigrid on the logical node grid of
+//   * free unknowns: one V(1,1)-cycle of geometric multigrid on the logical node grid of
 //     each variant.  Level 0 is the mesh itself with its Q4 element matrices (the FP32
 //     operator of the CG); level l+1 has ceil(n_l / 2) cells per direction, coarse node I
 //     sitting on fine node min(2I, n_l).  Interpolation P is bilinear along the index
@@ -11,9 +11,10 @@
 //     line copies its coarse node).  A coarse node carries an unknown only if the fine node
 //     under it does (constraints are injected), and P has no entries for constrained
 //     nodes.  Coarse operators are Galerkin products A_{l+1} = P^T A_l P (9-point
-//     stencils, formed once in FP32, the precision the cycle applies them in).  Smoother: damped Jacobi (omega = 0.85), two sweeps
-//     before and two after the coarse correction; the coarsest level (at most 17 x 17
-//     nodes) takes 100 Jacobi sweeps from zero.  Jacobi with a fixed sweep
+//     stencils, formed once in FP32, the precision the cycle applies them in).  Smoother: damped Jacobi (omega = 0.85), one sweep
+//     before (from zero) and one after the coarse correction on every level (two each way
+//     took more time per solve: fewer iterations did not pay for the extra passes); the
+//     coarsest level (at most 17 x 17 nodes) takes 100 Jacobi sweeps from zero.  Jacobi with a fixed sweep
 //     count is a fixed symmetric operator, so the cycle is a valid CG preconditioner.
 //   * body unknowns (one per body, the multi-point constraint) and their coupling to the
 //     free unknowns: a symmetric block Gauss-Seidel sweep body, free, body.  Forward:
@@ -687,7 +688,8 @@ __global__ void __launch_bounds__(256) k_mg_sweep(LvArgs c, int l, const int* Lv
   zo[q.k] = MODE == 1 ? rr : zi[q.k] + c.dinv[q.k] * rr;
 }
 
-// zb_f += P zb_c on a packed fine level (l >= 1).
+// za_f += P zb_c on a packed fine level (l >= 1): the pre-sweep value plus the coarse
+// correction, which the post-sweep then smooths into zb_f.
 __global__ void __launch_bounds__(256) k_mg_prolong(LvArgs f, LvArgs c, int l, const int* Lv, const VarState* st) {
   LvNode q;
   if (!lv_node(f.off, f.dims, f.blkvar, q)) return;
@@ -701,7 +703,7 @@ __global__ void __launch_bounds__(256) k_mg_prolong(LvArgs f, LvArgs c, int l, c
   float e = 0.0f;     // coarse values are zero at inactive coarse nodes
   for (int u = 0; u < nyp; ++u)
     for (int t = 0; t < nxp; ++t) e += wx[t] * wy[u] * c.zb[oc + (long long)Iy[u] * (dc.x + 1) + Ix[t]];
-  if (act) f.zb[q.k] = f.zb[q.k] + e;
+  if (act) f.za[q.k] = f.za[q.k] + e;
 }
 
 // Coarsest level of every variant (its own level Lv - 1): a fixed number of Jacobi
@@ -1126,11 +1128,10 @@ void launch_pcg_chunk(Batch& b, int iters, cudaStream_t s) {
   for (int it = 0; it < iters; ++it) {
     k_mg0_update<<<T, blk, 0, s>>>(a);
     k_mg_finA<<<nv, blk, 0, s>>>(f);
-    // descent: the forward body step's term of the first sweep, level 0 second sweep
-    // (z -> t), residual, restriction to level 1
+    // descent: the forward body step's term of the pre-sweep (z), the residual r - A z,
+    // restriction to level 1 (which also runs the level's pre-sweep from zero)
     if (b.B > 0) k_mg_fwd<<<nv, blk, 0, s>>>(a, b.mg_adj_ptr, b.mg_adj_node, b.mg_adj_c);
-    k_mg0_sweep<0, false><<<T, blk, 0, s>>>(a, b.mg_z, b.mg_t);
-    k_mg0_sweep<1, false><<<T, blk, 0, s>>>(a, b.mg_t, b.mg_res);
+    k_mg0_sweep<1, false><<<T, blk, 0, s>>>(a, b.mg_z, b.mg_res);
     for (int l = 1; l < L; ++l) {
       MgLevel& M = b.mg[l];
       if (M.nblk == 0) continue;
@@ -1141,10 +1142,9 @@ void launch_pcg_chunk(Batch& b, int iters, cudaStream_t s) {
         MgLevel& F = b.mg[l - 1];
         k_mg_restrict<<<(unsigned)M.nblk, 256, 0, s>>>(c, l, b.d_mg_Lv, b.state, b.d_var, F.res, F.d_off, F.d_dims);
       }
-      // pre-smoothing of the level (variants whose coarsest level this is skip: the coarse
-      // solve below takes their restricted residual)
-      k_mg_sweep<0><<<(unsigned)M.nblk, 256, 0, s>>>(c, l, b.d_mg_Lv, b.state, M.za, M.zb);
-      k_mg_sweep<1><<<(unsigned)M.nblk, 256, 0, s>>>(c, l, b.d_mg_Lv, b.state, M.zb, M.res);
+      // the level's residual after its pre-sweep (variants whose coarsest level this is
+      // skip: the coarse solve below takes their restricted residual)
+      k_mg_sweep<1><<<(unsigned)M.nblk, 256, 0, s>>>(c, l, b.d_mg_Lv, b.state, M.za, M.res);
     }
     k_mg_coarse<<<nv, 256, 0, s>>>(ct, b.d_mg_Lv, b.state);
     // ascent
@@ -1153,12 +1153,10 @@ void launch_pcg_chunk(Batch& b, int iters, cudaStream_t s) {
       if (M.nblk == 0) continue;
       const LvArgs c = lv_args(M);
       k_mg_prolong<<<(unsigned)M.nblk, 256, 0, s>>>(c, lv_args(b.mg[l + 1]), l, b.d_mg_Lv, b.state);
-      k_mg_sweep<0><<<(unsigned)M.nblk, 256, 0, s>>>(c, l, b.d_mg_Lv, b.state, M.zb, M.za);
       k_mg_sweep<0><<<(unsigned)M.nblk, 256, 0, s>>>(c, l, b.d_mg_Lv, b.state, M.za, M.zb);
     }
-    // post-smoothing of level 0, the first sweep on t + P e (the correction from level 1)
-    k_mg0_sweep<0, true><<<T, blk, 0, s>>>(a, b.mg_t, b.mg_z);
-    k_mg0_sweep<2, false><<<T, blk, 0, s>>>(a, b.mg_z, b.mg_t);
+    // post-smoothing of level 0: one sweep on z + P e (the correction from level 1), r.t
+    k_mg0_sweep<2, true><<<T, blk, 0, s>>>(a, b.mg_z, b.mg_t);
     k_mg_finB<<<nv, blk, 0, s>>>(f);
     k_mg0_apply<<<T, blk, 0, s>>>(a);
     k_mg_finC<<<nv, blk, 0, s>>>(f);

@@ -1826,9 +1826,9 @@ static cudaGraphExec_t get_graph(Batch& b, int precision, int chunk) {
 constexpr int PCG_CHUNK = 4;
 
 static int pcg_launches_per_iter(const Batch& b) {
-  int n = 10 + (b.B > 0 ? 1 : 0);                // fine level, finalisers, the forward body step
+  int n = 8 + (b.B > 0 ? 1 : 0);                // fine level, finalisers, the forward body step
   for (int l = 1; l < b.mg_L; ++l)
-    if (b.mg[l].nblk > 0) n += 3 + (l <= b.mg_L - 2 ? 3 : 0);
+    if (b.mg[l].nblk > 0) n += 2 + (l <= b.mg_L - 2 ? 2 : 0);
   return n;
 }
 
