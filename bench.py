@@ -483,13 +483,16 @@ def run_ours(args, rank, world, local):
         t_mesh = time.perf_counter() - t_mesh
         res = api.psi_solve(g, U=1.0, tol=args.tol, precision=p, inner_tol=args.inner_tol,
                             tune_schedule=args.tune and pre == "none", preconditioner=pre)
+        tm = g.timing()                          # the forward solve's timers
         if args.config == "c5":
+            # the adjoint solve (same preconditioner) replaces the handle's solve timers
             api.grad(g, api.PF_OBJ_COPFI, 3, 4, 1.0, args.tol, want_dX=False)
+            tm["adjoint_solve_ms"] = g.timing()["solve_ms"]
         # CoPFI of the gap between the two stacked bodies (the single-cylinder case has none)
         cps = [] if args.config == "c1" else [api.copfi(g, v, 3, 4, 1.0) for v in range(len(cs))]
         if host_out is not None:
             host_out.copy_(res.psi, non_blocking=True)
-        tm = g.timing()
+        tm["kernel_launches"] = g.timing()["kernel_launches"]   # the whole step's, gradient included
         tm["mesh_build_ms"] = 1e3 * t_mesh
         st = [g.stats(v) for v in range(len(cs))]
         if keep:
@@ -543,9 +546,10 @@ def run_ours(args, rank, world, local):
     # whole solve (device events, tuning launches included), its fused-CG and refinement
     # kernels, and the rest of the step (outputs, gradient, copies, teardown)
     n_rec = max(1, len(records))
-    breakdown = {k: sum(tm[src] for _, _, tm, _ in records) / n_rec
-                 for k, src in (("mesh_build", "mesh_build_ms"), ("solve", "solve_ms"), ("cg_kernels", "cg_kernel_ms"),
-                                ("refinement_kernels", "residual_kernel_ms"))}
+    parts = (("mesh_build", "mesh_build_ms"), ("solve", "solve_ms"), ("cg_kernels", "cg_kernel_ms"),
+             ("refinement_kernels", "residual_kernel_ms")) + ((("adjoint_solve", "adjoint_solve_ms"),)
+                                                             if args.config == "c5" else ())
+    breakdown = {k: sum(tm[src] for _, _, tm, _ in records) / n_rec for k, src in parts}
 
     # e2e: the public API with host buffers (geometry in, psi field and body values out)
     e2e = None
@@ -601,7 +605,8 @@ def run_ours(args, rank, world, local):
                                    for res, _, _, _ in recm for i in res.info),
               "iters_per_variant": itm if len(itm) <= 8 else {"min": min(itm), "max": max(itm)},
               "breakdown_ms": {k: sum(tm[src] for _, _, tm, _ in recm) / len(recm)
-                               for k, src in (("mesh_build", "mesh_build_ms"), ("solve", "solve_ms"))},
+                               for k, src in (("mesh_build", "mesh_build_ms"), ("solve", "solve_ms"))
+                               + ((("adjoint_solve", "adjoint_solve_ms"),) if args.config == "c5" else ())},
               "clocks": clkm,
               "mg_over_cg_solves_per_s": (len(cs) * len(recm) / elm) / (vals[2] / vals[1])}
 
@@ -661,7 +666,8 @@ def run_ours(args, rank, world, local):
         "iters_per_variant": iters if len(iters) <= 8 else {"min": min(iters), "max": max(iters)},
         "copfi": [cp for cp, _ in records[-1][1]] if len(cs) <= 8 else None,
         "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": int(launches),
-        "breakdown_ms": {**breakdown, "rest": 1e3 * vals[1] / args.steps - breakdown["mesh_build"] - breakdown["solve"]},
+        "breakdown_ms": {**breakdown, "rest": 1e3 * vals[1] / args.steps - breakdown["mesh_build"] - breakdown["solve"]
+                         - breakdown.get("adjoint_solve", 0.0)},
         **({"apply_sweep": apply_sweep} if apply_sweep else {}),
         "plain_fp64": fp64, "mg_pcg": mg, "parity": parity,
         "e2e": ({"value": e2e[0] / e2e[1], "unit": UNIT, "h2d_bytes_per_step": e2e[2],

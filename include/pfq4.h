@@ -373,7 +373,9 @@ pf_status pf_copfi(const pf_batch* b, int variant, int body_lo, int body_hi, dou
    with respect to the final node coordinates (topology held fixed); dJdc: optional host
    output [total bodies][2], with respect to the body centres through the projection and the
    S smoothing sweeps; J: optional host output [n_variants].  The adjoint system is solved
-   in FP64 to `tol`. */
+   to a relative FP64 true residual of `tol` (FP32 inner CG with FP64 refinement, as
+   PF_MIXED), with the preconditioner of the handle's last pf_psi_solve (PF_PRECOND_MG
+   after a multigrid-preconditioned solve, else none). */
 pf_status pf_grad(pf_batch* b, int objective, int body_lo, int body_hi, double U, double tol,
                   double* dev_dJdX, double* dJdc, double* J, void* stream);
 

@@ -170,6 +170,7 @@ struct Batch {
   void** d_vecs = nullptr;           // device list of the vectors k_init clears
   // multigrid-preconditioned CG (mg.cu): hierarchy made on the first such solve
   bool pcg_active = false;           // the current solve runs the preconditioned CG
+  int last_precond = PF_PRECOND_NONE; // preconditioner of the last forward solve (the adjoint reuses it)
   bool mg_ready = false;
   int mg_L = 0;                      // levels of the deepest variant
   std::vector<int> mg_Lv;            // [nv] levels per variant (>= 2)

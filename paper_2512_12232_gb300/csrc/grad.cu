@@ -346,6 +346,7 @@ pf_status shape_gradient(Batch& b, int obj, int lo, int hi, double U, double tol
   o.k_max = 100000000;
   o.precision = PF_MIXED;
   o.inner_tol = PF_DEFAULT_INNER_TOL;
+  o.preconditioner = b.last_precond;   // the forward solve's choice (both run in PF_MIXED)
   b.rhs_active = true;
   pf_status st = PF_OK;
   try {

@@ -1878,6 +1878,7 @@ pf_status solve_core(Batch& b, double U, const pf_solve_opts& o, double* dev_psi
     throw Error{PF_EINVAL, "invalid preconditioner"};
   const bool pcg = o.preconditioner == PF_PRECOND_MG;
   if (pcg && prec != PF_MIXED) throw Error{PF_EINVAL, "the multigrid-preconditioned CG runs in PF_MIXED precision"};
+  if (!b.rhs_active) b.last_precond = o.preconditioner;
   ensure_solver_memory(b, prec);
   // the preconditioned path is active for this solve only (also when it throws)
   struct PcgScope {

@@ -81,6 +81,25 @@ def test_batched_gradient_equals_single(api):
                                    atol=1e-7 * np.abs(dX1.cpu().numpy()).max())
 
 
+def test_multigrid_adjoint_gives_the_same_gradient(api):
+    """pf_grad solves the adjoint with the preconditioner of the last forward solve: after a
+    multigrid-preconditioned solve the adjoint is multigrid-preconditioned too (far fewer
+    iterations, counted by the solve timers) and the gradient is the paper's CG's."""
+    cases = W.gradient_study(3, seed=1, nx=256)
+    out = {}
+    for pre in ("none", "mg"):
+        with api.batch_build(cases) as g:
+            api.psi_solve(g, U=1.0, tol=1e-12, precision=api.PF_MIXED, preconditioner=pre)
+            dX, dc, J = api.grad(g, 0, 3, 4, 1.0, 1e-12)
+            out[pre] = (dX.cpu().numpy(), dc, J, g.timing()["cg_launches"])
+    dX0, dc0, J0, it0 = out["none"]
+    dX1, dc1, J1, it1 = out["mg"]
+    assert 4 * it1 < it0, (it0, it1)
+    np.testing.assert_allclose(J1, J0, rtol=0, atol=1e-9)
+    np.testing.assert_allclose(dc1, dc0, rtol=0, atol=1e-7 * np.abs(dc0).max())
+    np.testing.assert_allclose(dX1, dX0, rtol=0, atol=1e-7 * np.abs(dX0).max())
+
+
 def test_autograd_function(api):
     from paper_2512_12232_gb300 import autograd as AG
     c = torch.tensor(CASE.bodies[:, :2], dtype=torch.float64, requires_grad=True)
