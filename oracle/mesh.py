@@ -58,6 +58,7 @@ class Mesh:
     polygons: tuple = ()          # polygon bodies (after the circles)
     wake: np.ndarray = None       # (ny+1, nx+1) bool: Kutta wake nodes (held at their body's value)
     wake_node: tuple = ()         # per polygon: flat index of its wake node, or -1
+    cut_points: np.ndarray = None  # mixed-cell mesh (`oracle.cutmesh`): (4, ny+1, nx+1, 2) surface points
 
     @property
     def n_nodes(self):

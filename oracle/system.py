@@ -63,7 +63,11 @@ def dirichlet_values(mesh: Mesh, U):
 
 
 def element_matrices(mesh: Mesh):
-    """K_e and the corner node indices of every active cell."""
+    """K_e and the corner node indices of every active cell (the cut-cell matrices of
+    `oracle.cutmesh` on a mixed-cell mesh)."""
+    if mesh.cut_points is not None:
+        from .cutmesh import element_matrices as cut_element_matrices
+        return cut_element_matrices(mesh)
     xy = cell_coords(mesh)[mesh.active]
     cells = cell_nodes(mesh.nx, mesh.ny)[mesh.active]
     Ke, detmin = q4_stiffness(xy)
