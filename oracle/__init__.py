@@ -24,6 +24,10 @@ follows:
               Appendix A (Algorithm, element-by-element), and the body Schur form.
 * `post`    - surface tangential velocity (section "Velocity Field and Surface
               Tangential Velocity") and Q / CoPFI (section "Effect of Gap Ratio").
+* `cutmesh` - the mixed-cell variant of the grid generation: surface points where grid
+              edges cross the circle, node splitting, triangle / pentagon cells
+              (pentagon = triangle + quadrilateral), boundary-point redistribution,
+              and the cut-cell element matrices and outputs.
 * `grad`    - adjoint shape gradient of CoPFI / gap flow (beyond the paper; its
               conclusions name sensitivity analysis and shape optimisation).
 
@@ -33,6 +37,8 @@ nullspace, rigid-motion and scale invariance), brute-force loop versions of the
 mesh rules on tiny grids, the linear patch test, the closed-form cylinder
 psi = U y (1 - a^2/r^2) with second-order convergence, symmetry invariants of the
 paper's Table 1 layout, flux balance, dense-vs-sparse-vs-CG agreement, Schur vs
-MPC, and central finite differences of the gradient.  The paper's Table 1 numbers
+MPC, central finite differences of the gradient, and for the mixed-cell mesh hand-built
+split layouts, the right-triangle stiffness, the tiling-area identity, the piece-wise
+patch test and closed-form cylinder convergence.  The paper's Table 1 numbers
 themselves are "parity unpinned": its cylinder x-positions are only in figures.
 """
