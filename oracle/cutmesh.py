@@ -247,13 +247,14 @@ def point_cells(i, j, d):
     return (i - 1, j - 1), (i, j - 1)
 
 
-def redistribute(mesh: Mesh, sigma):
-    """One pass of the minimum-spacing rule on mesh.cut_points (returns the new array)."""
+def redistribute(mesh: Mesh, sigma, hx, hy):
+    """One pass of the minimum-spacing rule on mesh.cut_points (returns the new array);
+    hx = (x1 - x0) / nx and hy = (y1 - y0) / ny are the grid spacings."""
     P0 = mesh.cut_points
     P1 = P0.copy()
     if sigma <= 0:
         return P1
-    smin = sigma * min(mesh.xg[0, 1] - mesh.xg[0, 0], mesh.yg[1, 0] - mesh.yg[0, 0])
+    smin = sigma * min(hx, hy)
     push = {}                                        # (cell i, cell j) -> {point id: (mx, my)}
     for (j, i) in cut_cells(mesh):
         (A, _, ida), (B, _, idb) = chord(mesh, j, i, P0)
@@ -313,7 +314,8 @@ def build_cut_mesh(grid, bodies, sweeps, bc=(0, 0, 0, 0), sigma=0.0) -> Mesh:
              zero.copy(), (), np.zeros(xg.shape, dtype=bool), (), P)
     for (j, i) in cut_cells(m):                     # refuse saddles and two-body cells early
         cut_polygon(m, j, i)
-    m.cut_points = redistribute(m, sigma)
+    x0, x1, y0, y1, nx, ny = grid
+    m.cut_points = redistribute(m, sigma, (x1 - x0) / nx, (y1 - y0) / ny)
     return m
 
 

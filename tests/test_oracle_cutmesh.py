@@ -237,9 +237,12 @@ def test_redistribution_identity_circle_and_spacing():
 
 
 def test_saddle_and_two_body_cells_are_refused():
-    # two circles one cell apart on the diagonal: a cell has inside corners of both
-    with pytest.raises(M.MeshError):
+    # two circles one cell apart on the diagonal: a cell with two diagonal inside corners
+    with pytest.raises(M.MeshError, match="diagonal"):
         CM.build_cut_mesh((0.0, 12.0, 0.0, 12.0, 12, 12), np.array([[5.0, 5.0, 0.3], [6.0, 6.0, 0.3]]), 0)
+    # side by side: a cell with inside corners of both
+    with pytest.raises(M.MeshError, match="two bodies"):
+        CM.build_cut_mesh((0.0, 12.0, 0.0, 12.0, 12, 12), np.array([[5.0, 5.0, 0.3], [6.0, 5.0, 0.3]]), 0)
 
 
 def test_free_node_coordinates_follow_the_directional_smoothing_by_hand():
