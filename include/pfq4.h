@@ -214,6 +214,38 @@ typedef struct pf_shape {
 pf_status pf_batch_build_shapes(const pf_grid* grids, const int* body_offsets, const pf_shape* shapes,
                                 int n_variants, int sweeps, const int bc[4], void* stream, pf_batch** out);
 
+/* pf_batch_build with the mixed-cell mesh of section "Body-Conforming Grid Generation":
+   node splitting, triangle and pentagon cells, boundary-point redistribution.  Circular
+   bodies only (body rows as in pf_batch_build).
+   - Node kinds as in pf_batch_build.  A BODY node keeps its background position; for each
+     outside 4-neighbour it has a surface point where their grid edge crosses the circle
+     (on a row (cx +- sqrt(r^2 - (y - cy)^2), y), on a column (x, cy +- sqrt(r^2 - (x - cx)^2)),
+     explicitly rounded FP64).  A node with two or more outside neighbours is split into that
+     many points, all carrying the body's single value C_k.
+   - The S Jacobi sweeps average the four neighbours as in pf_batch_build, a BODY neighbour
+     contributing the displacement of its surface point on the common edge.
+   - A cut cell (an active cell with an inside corner) is the polygon of its outside corners
+     and surface points, walked counter-clockwise from corner 0: a triangle (linear element),
+     a quadrilateral (Q4), or a pentagon split into the triangle (P+, c_{m+1}, c_{m+2}) and the
+     quadrilateral (P+, c_{m+2}, c_{m+3}, P-) around its inside corner m, P+ the point on edge m.
+     Its pieces' element matrices, scattered onto the cell's corners, are stored as the cell's
+     coefficients, so every operator, solve and preconditioner of the library runs unchanged.
+   - min_spacing in [0, 1]: after the smoothing, the chord of every cut cell shorter than
+     s_min = min_spacing * min(hx, hy) (and not of zero length) pushes its two points apart
+     along it by (s_min - L)/2 each; a point adds the pushes of its two cells and is projected
+     radially back onto the circle.  0 leaves the points in place.
+   - PF_EINVAL also for a cell with two diagonal inside corners or with inside corners of two
+     bodies, and for min_spacing outside [0, 1].  min_detJ covers every piece (twice the area
+     for a triangle).
+   - pf_surface_velocity lists one chord per cut cell (u_t from the mean of the polygon's
+     vertex values and the distance of its vertex centroid from the chord); pf_velocity_field
+     gives a cut cell the area-weighted mean of its pieces' gradients.  pf_grad,
+     pf_coords_vjp, pf_mesh_set_coords and pf_phi_solve refuse the handle (PF_EINVAL).
+   pf_mesh_coords reports BODY nodes at their background position; pf_mesh_cut_points gives
+   the surface points. */
+pf_status pf_batch_build_cut(const pf_grid* grids, const int* body_offsets, const pf_body* bodies, int n_variants,
+                             int sweeps, const int bc[4], double min_spacing, void* stream, pf_batch** out);
+
 /* Single-variant convenience form of pf_batch_build. */
 pf_status pf_mesh_build(const pf_grid* grid, const pf_body* bodies, int n_bodies, int sweeps,
                         const int bc[4], void* stream, pf_batch** out);
@@ -249,6 +281,12 @@ pf_status pf_coords_vjp(pf_batch* b, const double* dev_gX, double* gc, void* str
 /* Node classification of variant v: dev_kind[n] = PF_NODE_*, dev_body[n] = body index
    (local to the variant) for BODY nodes, else -1.  Either pointer may be NULL. */
 pf_status pf_mesh_tags(const pf_batch* b, int variant, int8_t* dev_kind, int32_t* dev_body, void* stream);
+
+/* Surface points of variant v of a pf_batch_build_cut handle: dev_pts is a caller-owned
+   device array [4][nodes][2] of doubles, direction d (0 E, 1 N, 2 W, 3 S) then node
+   m = j*(nx+1) + i then (x, y); NaN where node m has no surface point in direction d.
+   PF_EINVAL for another handle, a variant out of range or a NULL output. */
+pf_status pf_mesh_cut_points(const pf_batch* b, int variant, double* dev_pts, void* stream);
 
 /* Matrix-free operator of the reduced system on nodal vectors (Appendix A, "Compute Ap"):
    y_n = sum over active cells e containing n of (K_e p_e)_n for FREE and BODY nodes,

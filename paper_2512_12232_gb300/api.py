@@ -89,10 +89,12 @@ class SolveResult:
 class Mesh:
     """A pf_batch handle: one or more body-conforming mesh variants on the GPU."""
 
-    def __init__(self, grids, body_lists, sweeps, bc=(0, 0, 0, 0), polygon_lists=None):
+    def __init__(self, grids, body_lists, sweeps, bc=(0, 0, 0, 0), polygon_lists=None, cut_spacing=None):
         """polygon_lists (optional): per variant, polygon bodies (objects with `vertices`
         ((n, 2), counter-clockwise), `ref` (reference point of the polar angle) and `kutta`
-        (trailing-edge vertex or -1)); a variant's bodies are its circles, then its polygons."""
+        (trailing-edge vertex or -1)); a variant's bodies are its circles, then its polygons.
+        cut_spacing (optional, circles only): build the mixed-cell mesh (pf_batch_build_cut)
+        with this minimum surface-point spacing, a fraction of min(hx, hy)."""
         lib = L.load()
         nv = len(grids)
         g = (L.pf_grid * nv)()
@@ -113,7 +115,13 @@ class Mesh:
         bcs = (C.c_int * 4)(*[int(s) for s in bc])
         h = C.c_void_p()
         self._h = None
-        if any(polygon_lists):
+        if cut_spacing is not None:
+            if any(polygon_lists):
+                raise ValueError("the mixed-cell mesh takes circular bodies only")
+            bodies = (L.pf_body * max(1, len(flat)))(*[L.pf_body(*row) for _, row in flat])
+            code = lib.pf_batch_build_cut(g, off, bodies, nv, int(sweeps), bcs, float(cut_spacing), _stream(),
+                                          C.byref(h))
+        elif any(polygon_lists):
             shapes = (L.pf_shape * max(1, len(flat)))()
             self._vertex_bufs = []
             for k, (kind, b) in enumerate(flat):
@@ -145,6 +153,7 @@ class Mesh:
         self.node_offsets = np.concatenate([[0], np.cumsum(self.n_nodes)]).astype(np.int64)
         self.sweeps = sweeps
         self.bc = tuple(bc)
+        self.cut = cut_spacing is not None
         _LIVE.add(self)
 
     # ------------------------------------------------------------------ handle
@@ -204,6 +213,12 @@ class Mesh:
         check(L.load().pf_coords_vjp(self.handle, _ptr(gX), gc, _stream()))
         return np.array(gc[:2 * nb]).reshape(nb, 2)
 
+    def cut_points(self, v=0):
+        """(4, nodes, 2) surface points of a mixed-cell mesh (E, N, W, S; NaN where none)."""
+        out = torch.empty((4, self.n_nodes[v], 2), dtype=torch.float64, device="cuda")
+        check(L.load().pf_mesh_cut_points(self.handle, v, _ptr(out), _stream()))
+        return out
+
     def tags(self, v=0):
         kind = torch.empty(self.n_nodes[v], dtype=torch.int8, device="cuda")
         body = torch.empty(self.n_nodes[v], dtype=torch.int32, device="cuda")
@@ -232,12 +247,18 @@ def mesh_build(grid, bodies, sweeps, bc=(0, 0, 0, 0), polygons=None) -> Mesh:
     return Mesh([grid], [bodies], sweeps, bc, None if polygons is None else [polygons])
 
 
-def batch_build(cases, sweeps=None, bc=None, polygons=None) -> Mesh:
+def batch_build(cases, sweeps=None, bc=None, polygons=None, cut_spacing=None) -> Mesh:
     """Many variants (objects with .grid, .bodies, .sweeps, .bc) in one handle; polygons:
-    optional per-variant lists of polygon bodies."""
+    optional per-variant lists of polygon bodies; cut_spacing: the mixed-cell mesh with this
+    minimum surface-point spacing (a fraction of min(hx, hy), 0 for none)."""
     sweeps = cases[0].sweeps if sweeps is None else sweeps
     bc = cases[0].bc if bc is None else bc
-    return Mesh([c.grid for c in cases], [c.bodies for c in cases], sweeps, bc, polygons)
+    return Mesh([c.grid for c in cases], [c.bodies for c in cases], sweeps, bc, polygons, cut_spacing)
+
+
+def cut_mesh_build(grid, bodies, sweeps, bc=(0, 0, 0, 0), cut_spacing=0.0) -> Mesh:
+    """One variant of the mixed-cell mesh (node splitting, triangle / pentagon cells)."""
+    return Mesh([grid], [bodies], sweeps, bc, None, cut_spacing)
 
 
 def apply(mesh: Mesh, p: torch.Tensor, precision=PF_FP64):

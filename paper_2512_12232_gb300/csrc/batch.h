@@ -80,6 +80,9 @@ struct Batch {
   std::vector<double> poly_xy;       // [vertices][2]
   std::vector<int> kutta;            // [B] trailing-edge vertex or -1
   bool has_polygons = false, has_kutta = false;
+  bool cut = false;                  // mixed-cell mesh: surface points per edge, cut cells (circles only)
+  double cut_sigma = 0.0;            // its minimum surface-point spacing, a fraction of min(hx, hy)
+  double2* pcut = nullptr;           // [4][Vtot] surface points of BODY nodes by direction (E, N, W, S), NaN elsewhere
   ShapeDev shp{};                    // device copies (null when there are no polygons)
   std::vector<long long> h_wake;     // [B] padded index of each Kutta body's wake node, or -1
   std::vector<int> h_body_ptr;       // [B+1]
@@ -238,6 +241,7 @@ void export_coords(Batch& b, int v, double* dev_xy);
 void set_coords(Batch& b, int v, const double* dev_xy);
 void tile_flags(Batch& b);
 void export_tags(Batch& b, int v, int8_t* kind, int32_t* body);
+void export_cut_points(Batch& b, int v, double* pts);
 
 // solver.cu
 void make_schedule(Batch& b);

@@ -116,7 +116,7 @@ pf_status pf_set_allocator(pf_alloc_fn alloc, pf_free_fn free_fn, void* ctx) {
 
 static pf_status build_handle(const pf_grid* grids, const int* body_offsets, const pf_body* bodies,
                               int n_variants, int sweeps, const int bc[4], void* stream, pf_batch** out,
-                              const ShapeInput* shapes);
+                              const ShapeInput* shapes, bool cut = false, double cut_sigma = 0.0);
 
 pf_status pf_batch_build(const pf_grid* grids, const int* body_offsets, const pf_body* bodies, int n_variants,
                          int sweeps, const int bc[4], void* stream, pf_batch** out) {
@@ -165,9 +165,14 @@ pf_status pf_batch_build_shapes(const pf_grid* grids, const int* body_offsets, c
   return build_handle(grids, body_offsets, bodies.data(), n_variants, sweeps, bc, stream, out, &si);
 }
 
+pf_status pf_batch_build_cut(const pf_grid* grids, const int* body_offsets, const pf_body* bodies, int n_variants,
+                             int sweeps, const int bc[4], double min_spacing, void* stream, pf_batch** out) {
+  return build_handle(grids, body_offsets, bodies, n_variants, sweeps, bc, stream, out, nullptr, true, min_spacing);
+}
+
 static pf_status build_handle(const pf_grid* grids, const int* body_offsets, const pf_body* bodies,
                               int n_variants, int sweeps, const int bc[4], void* stream, pf_batch** out,
-                              const ShapeInput* shapes) {
+                              const ShapeInput* shapes, bool cut, double cut_sigma) {
   if (!out) {
     g_err = "out is NULL";
     return PF_EINVAL;
@@ -184,6 +189,8 @@ static pf_status build_handle(const pf_grid* grids, const int* body_offsets, con
     b->alloc_fn = g_alloc;
     b->free_fn = g_free;
     b->alloc_ctx = g_ctx;
+    b->cut = cut;
+    b->cut_sigma = cut_sigma;
     build_batch(*b, grids, body_offsets, bodies, n_variants, sweeps, bc, shapes);
     if (!b->valid) throw Error{PF_EMESH_INVALID, "mesh has det J <= 0 at a Gauss point of an active cell"};
     return PF_OK;
@@ -274,6 +281,19 @@ pf_status pf_coords_vjp(pf_batch* h, const double* dev_gX, double* gc, void* str
     bind(b, stream);
     if (!dev_gX || (!gc && b->B > 0)) throw Error{PF_EINVAL, "NULL argument"};
     coords_vjp(*b, dev_gX, gc);
+    return PF_OK;
+  });
+}
+
+pf_status pf_mesh_cut_points(const pf_batch* h, int variant, double* dev_pts, void* stream) {
+  return guarded([&]() -> pf_status {
+    Batch* b = (Batch*)h;
+    bind(b, stream);
+    check_variant(b, variant);
+    if (!b->cut) throw Error{PF_EINVAL, "pf_mesh_cut_points: not a mixed-cell mesh"};
+    if (!dev_pts) throw Error{PF_EINVAL, "dev_pts is NULL"};
+    export_cut_points(*b, variant, dev_pts);
+    PF_CUDA(cudaStreamSynchronize(b->stream));
     return PF_OK;
   });
 }

@@ -297,6 +297,7 @@ static void centre_chain(Batch& b, double* gc) {
 }
 
 void coords_vjp(Batch& b, const double* dev_gX, double* gc) {
+  if (b.cut) throw Error{PF_EINVAL, "pf_coords_vjp: the mesh generator's Jacobian is that of the Q4 mesh"};
   if (b.has_polygons)
     throw Error{PF_EINVAL, "pf_coords_vjp: the projection Jacobian is that of circular bodies"};
   ensure_grad_memory(b);
@@ -310,6 +311,7 @@ void coords_vjp(Batch& b, const double* dev_gX, double* gc) {
 pf_status shape_gradient(Batch& b, int obj, int lo, int hi, double U, double tol, double* dev_dJdX, double* dJdc,
                          double* J) {
   if (!b.solved) throw Error{PF_EINVAL, "pf_grad needs a solve on this handle first"};
+  if (b.cut) throw Error{PF_EINVAL, "pf_grad: the shape derivative is written for the Q4 mesh"};
   if (b.has_polygons)
     throw Error{PF_EINVAL, "pf_grad: the centre chain rule is that of circular bodies (radial projection)"};
   if (U != b.lastU) throw Error{PF_EINVAL, "pf_grad must use the U of the last solve"};

@@ -13,6 +13,7 @@
 #include <cstring>
 
 #include "batch.h"
+#include "cut.cuh"
 
 namespace pfq4 {
 
@@ -122,7 +123,7 @@ __global__ void k_classify(const DevVariant* var, const int* tile_var, const int
 // 2. node kinds, cell activity, ring flag, projection displacement d0.
 __global__ void k_kinds(const DevVariant* var, const int* tile_var, const int2* tile_ij,
                         const pf_body* bodies, ShapeDev shp, const int* bid, uint8_t* tag, double2* d0,
-                        int bc0, int bc1, int bc2, int bc3, int* err) {
+                        int bc0, int bc1, int bc2, int bc3, int cut, int* err) {
   TileCtx c = tile_ctx(var, tile_var, tile_ij);
   const DevVariant& V = var[c.v];
   if (!c.in) return;
@@ -146,7 +147,9 @@ __global__ void k_kinds(const DevVariant* var, const int* tile_var, const int2* 
   } else {
     const bool touch = cell_active(i - 1, j - 1) || cell_active(i, j - 1) || cell_active(i - 1, j) ||
                        cell_active(i, j);
-    if (touch) {
+    if (touch && cut) {
+      t |= K_BODY;                     // mixed-cell mesh: the node stays, its surface points are per edge
+    } else if (touch) {
       t |= K_BODY;
       const int gb = V.body0 + ib;
       const double xg = grid_x(V, i), yg = grid_y(V, j);
@@ -168,6 +171,42 @@ __global__ void k_kinds(const DevVariant* var, const int* tile_var, const int2* 
   }
   tag[n] = t;
   d0[n] = d;
+}
+
+// 2a. mixed-cell mesh: the surface points of every BODY node (circles), where the grid
+//     edge towards an outside neighbour crosses the circle: on a row
+//     (cx +- sqrt(r^2 - (y - cy)^2), y), on a column (x, cy +- sqrt(r^2 - (x - cx)^2)), the
+//     sign that of the step; NaN for the other directions and for every other node.
+__global__ void k_cut_points(const DevVariant* var, const int* tile_var, const int2* tile_ij,
+                             const pf_body* bodies, const int* bid, const uint8_t* tag, double2* pcut,
+                             long long Vtot) {
+  TileCtx c = tile_ctx(var, tile_var, tile_ij);
+  const DevVariant& V = var[c.v];
+  if (!c.in) return;
+  const double nan = __longlong_as_double(0x7ff8000000000000LL);
+  double2 out[4];
+  for (int d = 0; d < 4; ++d) out[d] = make_double2(nan, nan);
+  if ((tag[c.n] & KIND_MASK) == K_BODY) {
+    const pf_body B = bodies[V.body0 + bid[c.n]];
+    const double xg = grid_x(V, c.i), yg = grid_y(V, c.j);
+    const double rr = __dmul_rn(B.r, B.r);
+    const int di[4] = {1, 0, -1, 0}, dj[4] = {0, 1, 0, -1};
+    for (int d = 0; d < 4; ++d) {
+      const int ni = c.i + di[d], nj = c.j + dj[d];
+      if (ni < 0 || nj < 0 || ni > V.nx || nj > V.ny) continue;
+      if (bid[V.base + (long long)nj * V.P + ni] >= 0) continue;
+      if (d == 0 || d == 2) {
+        const double e = __dsub_rn(yg, B.cy);
+        const double sq = __dsqrt_rn(__dsub_rn(rr, __dmul_rn(e, e)));
+        out[d] = make_double2(d == 0 ? __dadd_rn(B.cx, sq) : __dsub_rn(B.cx, sq), yg);
+      } else {
+        const double e = __dsub_rn(xg, B.cx);
+        const double sq = __dsqrt_rn(__dsub_rn(rr, __dmul_rn(e, e)));
+        out[d] = make_double2(xg, d == 1 ? __dadd_rn(B.cy, sq) : __dsub_rn(B.cy, sq));
+      }
+    }
+  }
+  for (int d = 0; d < 4; ++d) pcut[d * Vtot + c.n] = out[d];
 }
 
 // 2b. Kutta condition of polygon gb (one CTA per global body; others return): the wake
@@ -257,9 +296,17 @@ constexpr int JK = 4;
 constexpr int JRW = CTX + 2 * JK, JRH = CTY + 2 * JK;      // window 72 x 24
 constexpr int JACOBI_SMEM = 2 * JRW * JRH * (int)sizeof(double2) + JRW * JRH;
 
+// CUT: the mixed-cell mesh, where a BODY neighbour contributes the displacement of its
+// surface point on the common edge (P - x_grid of the neighbour) instead of its own.
+__device__ __forceinline__ double2 cut_disp(const DevVariant& V, double2 p, int i, int j) {
+  return make_double2(__dsub_rn(p.x, grid_x(V, i)), __dsub_rn(p.y, grid_y(V, j)));
+}
+
+template <bool CUT>
 __global__ void __launch_bounds__(NT) k_jacobi(const DevVariant* var, const int* tile_var, const int2* tile_ij,
                                                const int* bid, const uint8_t* tag, const int4* bbox, int sweep0,
-                                               int nsw, const double2* __restrict__ src, double2* __restrict__ dst) {
+                                               int nsw, const double2* __restrict__ src, double2* __restrict__ dst,
+                                               const double2* __restrict__ pcut, long long Vtot) {
   extern __shared__ __align__(16) unsigned char jsm[];
   double2* w0 = reinterpret_cast<double2*>(jsm);
   double2* w1 = w0 + JRW * JRH;
@@ -286,6 +333,7 @@ __global__ void __launch_bounds__(NT) k_jacobi(const DevVariant* var, const int*
       const long long n = V.base + (long long)j * V.P + i;
       v = src[n];
       u = bid[n] < 0 && !(tag[n] & (RING | WAKE));
+      if (CUT && (tag[n] & KIND_MASK) == K_BODY) u |= 2;
     }
     w0[q] = v;
     upd[q] = u;
@@ -303,8 +351,18 @@ __global__ void __launch_bounds__(NT) k_jacobi(const DevVariant* var, const int*
       const int q = rj * JRW + ri;
       double2 out = a[q];
       // an updatable node is off the ring, so its four neighbours lie in the grid
-      if (upd[q]) {
-        const double2 w = a[q - 1], e = a[q + 1], s = a[q - JRW], nn = a[q + JRW];
+      if (upd[q] & 1) {
+        double2 w = a[q - 1], e = a[q + 1], s = a[q - JRW], nn = a[q + JRW];
+        if (CUT) {
+          // the neighbours' surface points towards this node: W's E point, E's W point,
+          // S's N point, N's S point
+          const int gi = ij.x - JK + ri, gj = ij.y - JK + rj;
+          const long long gn = V.base + (long long)gj * V.P + gi;
+          if (upd[q - 1] & 2) w = cut_disp(V, pcut[gn - 1], gi - 1, gj);
+          if (upd[q + 1] & 2) e = cut_disp(V, pcut[2 * Vtot + gn + 1], gi + 1, gj);
+          if (upd[q - JRW] & 2) s = cut_disp(V, pcut[Vtot + gn - V.P], gi, gj - 1);
+          if (upd[q + JRW] & 2) nn = cut_disp(V, pcut[3 * Vtot + gn + V.P], gi, gj + 1);
+        }
         const double sx = __dadd_rn(__dadd_rn(__dadd_rn(w.x, e.x), s.x), nn.x);
         const double sy = __dadd_rn(__dadd_rn(__dadd_rn(w.y, e.y), s.y), nn.y);
         out = make_double2(quarter(sx), quarter(sy));
@@ -344,12 +402,86 @@ __device__ void atomic_min_double(double* addr, double val) {
   }
 }
 
-// 5. Q4 element matrices (2x2 Gauss), FP64 and FP32 copies, of the active cells with a
-//    displaced corner (every reader uses the closed-form constants for the others),
-//    CELL_GENERAL / CELL_GEN32 flags, per-variant counts and min det J.
+// 4b. mixed-cell mesh, boundary-point redistribution (one pass, after the smoothing): the
+//     chord (A, B) of every cut cell with 0 < L = |B - A| < s_min pushes its ends apart
+//     along it, A by -f (B - A) and B by +f (B - A) with f = ((s_min - L) * 0.5) / L; a
+//     point adds the pushes of the two cells beside its edge (the cell below, or left of,
+//     it first) and, if pushed, is projected radially back onto its circle.
+//     s_min = sigma * min(hx, hy).  The push of one cell on point (corner a_here, d):
+__device__ inline bool cut_push(const DevVariant& V, const int* bid, const double* X, long long Vtot,
+                                const double2* pin, int ci, int cj, int a_here, int d, double smin, double& mx,
+                                double& my) {
+  mx = 0.0;
+  my = 0.0;
+  CutPoly p;
+  if (cut_polygon(V, bid, X, Vtot, pin, V.base + (long long)cj * V.P + ci, p) != CUT_OK || p.n == 0) return false;
+  int ka, kb;
+  cut_chord(p, ka, kb);
+  const double ex = __dsub_rn(p.x[kb], p.x[ka]), ey = __dsub_rn(p.y[kb], p.y[ka]);
+  const double L = __dsqrt_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)));
+  if (!(L > 0.0 && L < smin)) return false;
+  const double f = __ddiv_rn(__dmul_rn(__dsub_rn(smin, L), 0.5), L);
+  const int id = (a_here << 2) | d;
+  if (p.pt[ka] == id) {
+    mx = -__dmul_rn(f, ex);
+    my = -__dmul_rn(f, ey);
+    return true;
+  }
+  if (p.pt[kb] == id) {
+    mx = __dmul_rn(f, ex);
+    my = __dmul_rn(f, ey);
+    return true;
+  }
+  return false;
+}
+
+__global__ void k_redistribute(const DevVariant* var, const int* tile_var, const int2* tile_ij,
+                               const pf_body* bodies, const int* bid, const uint8_t* tag, const double* X,
+                               long long Vtot, double sigma, const double2* pin, double2* pout) {
+  TileCtx c = tile_ctx(var, tile_var, tile_ij);
+  const DevVariant& V = var[c.v];
+  if (!c.in) return;
+  const bool body = (tag[c.n] & KIND_MASK) == K_BODY;
+  const double smin = __dmul_rn(sigma, fmin(V.hx, V.hy));
+  for (int d = 0; d < 4; ++d) {
+    double2 q = pin[d * Vtot + c.n];
+    if (body && !isnan(q.x)) {
+      // the cells beside the edge: below then above (E, W), left then right (N, S)
+      int ci[2], cj[2];
+      if (d == 0) { ci[0] = c.i; cj[0] = c.j - 1; ci[1] = c.i; cj[1] = c.j; }
+      else if (d == 2) { ci[0] = c.i - 1; cj[0] = c.j - 1; ci[1] = c.i - 1; cj[1] = c.j; }
+      else if (d == 1) { ci[0] = c.i - 1; cj[0] = c.j; ci[1] = c.i; cj[1] = c.j; }
+      else { ci[0] = c.i - 1; cj[0] = c.j - 1; ci[1] = c.i; cj[1] = c.j - 1; }
+      bool moved = false;
+      double qx = q.x, qy = q.y;
+      for (int k = 0; k < 2; ++k) {
+        const int di = c.i - ci[k], dj = c.j - cj[k];
+        double mx, my;
+        moved |= cut_push(V, bid, X, Vtot, pin, ci[k], cj[k], di + 3 * dj - 2 * di * dj, d, smin, mx, my);
+        qx = __dadd_rn(qx, mx);
+        qy = __dadd_rn(qy, my);
+      }
+      if (moved) {
+        const pf_body B = bodies[V.body0 + bid[c.n]];
+        const double ux = __dsub_rn(qx, B.cx), uy = __dsub_rn(qy, B.cy);
+        const double rho = __dsqrt_rn(__dadd_rn(__dmul_rn(ux, ux), __dmul_rn(uy, uy)));
+        q = make_double2(__dadd_rn(B.cx, __ddiv_rn(__dmul_rn(B.r, ux), rho)),
+                         __dadd_rn(B.cy, __ddiv_rn(__dmul_rn(B.r, uy), rho)));
+      }
+    }
+    pout[d * Vtot + c.n] = q;
+  }
+}
+
+// 5. element matrices, FP64 and FP32 copies, of the active cells that need stored
+//    coefficients: Q4 (2x2 Gauss) of the cells with a displaced corner, and on the
+//    mixed-cell mesh (pcut != NULL) the cut-cell matrices (every reader uses the
+//    closed-form constants for the other cells); CELL_GENERAL / CELL_GEN32 flags,
+//    per-variant counts and min det J.  err bit 4: a cut cell with two diagonal inside
+//    corners; bit 8: inside corners of two bodies.
 __global__ void k_stiffness(const DevVariant* var, const int* tile_var, const int2* tile_ij,
                             uint8_t* tag, const double* X, long long Vtot, double* K64, float* K32, float* K32i,
-                            long long* stats_i, double* detmin) {
+                            long long* stats_i, double* detmin, const int* bid, const double2* pcut, int* err) {
   TileCtx c = tile_ctx(var, tile_var, tile_ij);
   const DevVariant& V = var[c.v];
   __shared__ long long cnt[6];
@@ -368,46 +500,35 @@ __global__ void k_stiffness(const DevVariant* var, const int* tile_var, const in
     if (t & CELL_ACTIVE) {
       atomicAdd((unsigned long long*)&cnt[3], 1ull);
       const long long idx[4] = {n, n + 1, n + 1 + V.P, n + V.P};
+      CutPoly cp;
+      cp.n = 0;
+      int cst = CUT_OK;
+      if (pcut) {
+        cst = cut_polygon(V, bid, X, Vtot, pcut, n, cp);
+        if (cst != CUT_OK) atomicOr(err, cst == CUT_SADDLE ? 4 : 8);
+      }
       bool disp = false;
       for (int a = 0; a < 4; ++a) disp |= (tag[idx[a]] & DISPLACED) != 0;
-      if (!disp) {
+      if (cst != CUT_OK) {
+        atomic_min_double(&dmin, -1.0);              // refused cell: the mesh is invalid
+      } else if (cp.n == 0 && !disp) {
         // an undisplaced hx-by-hy rectangle: every reader of stored K_e uses the
         // closed-form constants for it, and det J = (hx/2)(hy/2) at every Gauss point
         atomic_min_double(&dmin, 0.25 * V.hx * V.hy);
       } else {
-        double x[4], y[4];
-        for (int a = 0; a < 4; ++a) {
-          x[a] = X[idx[a]];
-          y[a] = X[Vtot + idx[a]];
+        double k6[6], dm;
+        if (cp.n > 0) {
+          dm = cut_cell_matrix(cp, k6);
+        } else {
+          double x[4], y[4], K[4][4];
+          for (int a = 0; a < 4; ++a) {
+            x[a] = X[idx[a]];
+            y[a] = X[Vtot + idx[a]];
+          }
+          dm = q4_element(x, y, K);
+          k6[0] = K[0][1]; k6[1] = K[0][2]; k6[2] = K[0][3];
+          k6[3] = K[1][2]; k6[4] = K[1][3]; k6[5] = K[2][3];
         }
-        const double g = 0.57735026918962576451;   // 1/sqrt(3)
-        const double xi_a[4] = {-1, 1, 1, -1}, eta_a[4] = {-1, -1, 1, 1};
-        const double gx[4] = {-g, g, g, -g}, gy[4] = {-g, -g, g, g};
-        double K[4][4] = {};
-        double dm = 1e300;
-        for (int q = 0; q < 4; ++q) {
-          double dxi[4], deta[4];
-          for (int a = 0; a < 4; ++a) {
-            dxi[a] = 0.25 * xi_a[a] * (1.0 + eta_a[a] * gy[q]);
-            deta[a] = 0.25 * eta_a[a] * (1.0 + xi_a[a] * gx[q]);
-          }
-          double j00 = 0, j01 = 0, j10 = 0, j11 = 0;
-          for (int a = 0; a < 4; ++a) {
-            j00 += dxi[a] * x[a]; j01 += dxi[a] * y[a];
-            j10 += deta[a] * x[a]; j11 += deta[a] * y[a];
-          }
-          const double det = j00 * j11 - j01 * j10;
-          dm = fmin(dm, det);
-          const double inv = 1.0 / det;
-          double bx[4], by[4];
-          for (int a = 0; a < 4; ++a) {
-            bx[a] = (j11 * dxi[a] - j01 * deta[a]) * inv;
-            by[a] = (-j10 * dxi[a] + j00 * deta[a]) * inv;
-          }
-          for (int a = 0; a < 4; ++a)
-            for (int b2 = a + 1; b2 < 4; ++b2) K[a][b2] += det * (bx[a] * bx[b2] + by[a] * by[b2]);
-        }
-        const double k6[6] = {K[0][1], K[0][2], K[0][3], K[1][2], K[1][3], K[2][3]};
         for (int m = 0; m < 6; ++m) {
           K64[m * Vtot + n] = k6[m];
           K32[m * Vtot + n] = (float)k6[m];
@@ -505,11 +626,13 @@ __global__ void k_body_nodes(const DevVariant* var, const int* body_var, const i
 }
 
 // 7. per-body boundary edges: edges (corner a -> a+1) of active cells whose two end
-//    nodes are BODY nodes of this body at distinct positions.  Cells row-major in the
-//    body's box, edges by first corner.  pass 0 counts, pass 1 writes.
+//    nodes are BODY nodes of this body at distinct positions; on the mixed-cell mesh
+//    (pcut != NULL) the chord of every cut cell of this body whose two surface points
+//    differ, recorded with a = 0.  Cells row-major in the body's box, edges by first
+//    corner.  pass 0 counts, pass 1 writes.
 __global__ void k_body_edges(const DevVariant* var, const int* body_var, const int4* bbox,
                              const uint8_t* tag, const int* bid, const double* X, long long Vtot,
-                             int* count, const int* ptr, long long* out, int pass) {
+                             int* count, const int* ptr, long long* out, int pass, const double2* pcut) {
   __shared__ int sh[NT / 32 + 1];
   const int gb = blockIdx.x;
   const int v = body_var[gb];
@@ -528,7 +651,19 @@ __global__ void k_body_edges(const DevVariant* var, const int* body_var, const i
     if (q < total) {
       const int i = ci0 + (int)(q % w), j = cj0 + (int)(q / w);
       n = V.base + (long long)j * V.P + i;
-      if (tag[n] & CELL_ACTIVE) {
+      if ((tag[n] & CELL_ACTIVE) && pcut) {
+        CutPoly p;
+        if (cut_polygon(V, bid, X, Vtot, pcut, n, p) == CUT_OK && p.n > 0) {
+          int ka, kb;
+          cut_chord(p, ka, kb);
+          const int g = p.pt[ka] >> 2;                       // the inside corner behind the chord
+          const long long gn = n + cut_ci(g) + (long long)cut_cj(g) * V.P;
+          if (bid[gn] == k && (p.x[ka] != p.x[kb] || p.y[ka] != p.y[kb])) {
+            mask = 1u;
+            cnt = 1;
+          }
+        }
+      } else if (tag[n] & CELL_ACTIVE) {
         const long long idx[4] = {n, n + 1, n + 1 + V.P, n + V.P};
         bool isb[4];
         for (int a = 0; a < 4; ++a) isb[a] = ((tag[idx[a]] & KIND_MASK) == K_BODY) && bid[idx[a]] == k;
@@ -552,6 +687,21 @@ __global__ void k_body_edges(const DevVariant* var, const int* body_var, const i
     run += tot;
   }
   if (pass == 0 && linear_tid() == 0) count[gb] = run;
+}
+
+// Surface points of variant v in logical order: out[(d * N + m) * 2 + c], m = j*(nx+1) + i.
+__global__ void k_export_cut(const DevVariant* var, int v, const double2* pcut, long long Vtot, double* out) {
+  const DevVariant& V = var[v];
+  const long long N = (long long)(V.nx + 1) * (V.ny + 1);
+  const long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (m >= N) return;
+  const int i = (int)(m % (V.nx + 1)), j = (int)(m / (V.nx + 1));
+  const long long n = V.base + (long long)j * V.P + i;
+  for (int d = 0; d < 4; ++d) {
+    const double2 q = pcut[d * Vtot + n];
+    out[(d * N + m) * 2] = q.x;
+    out[(d * N + m) * 2 + 1] = q.y;
+  }
 }
 
 // Caller-given node coordinates of variant v (logical order, [n][2]): X and the
@@ -647,6 +797,9 @@ void build_batch(Batch& b, const pf_grid* grids, const int* body_offsets, const 
   }
   b.has_polygons = std::find(b.shape_kind.begin(), b.shape_kind.end(), (int)PF_SHAPE_POLYGON) != b.shape_kind.end();
   b.has_kutta = false;
+  if (b.cut && b.has_polygons) throw Error{PF_EINVAL, "the mixed-cell mesh takes circular bodies only"};
+  if (b.cut && !(b.cut_sigma >= 0.0 && b.cut_sigma <= 1.0))
+    throw Error{PF_EINVAL, "the minimum spacing of the mixed-cell mesh must lie in [0, 1] (times min(hx, hy))"};
   std::vector<DBox> pbox(std::max(1, b.B), DBox{0, 0, 0, 0});
   for (int k = 0; k < b.B; ++k) {
     if (b.shape_kind[k] == PF_SHAPE_POLYGON) {
@@ -793,6 +946,7 @@ void build_batch(Batch& b, const pf_grid* grids, const int* body_offsets, const 
   b.K64 = (double*)dev_alloc(b, 6 * Vt * sizeof(double));
   b.K32 = (float*)dev_alloc(b, 6 * Vt * sizeof(float));
   b.K32i = (float*)dev_alloc(b, 6 * Vt * sizeof(float));
+  if (b.cut) b.pcut = (double2*)dev_alloc(b, 4 * Vt * sizeof(double2));
   double2* dA = (double2*)dev_alloc(b, Vt * sizeof(double2));
   double2* dB = (double2*)dev_alloc(b, Vt * sizeof(double2));
   int* err = (int*)dev_alloc(b, sizeof(int));
@@ -818,23 +972,44 @@ void build_batch(Batch& b, const pf_grid* grids, const int* body_offsets, const 
   const unsigned grid = (unsigned)b.T;
   k_classify<<<grid, blk, 0, s>>>(b.d_var, b.tile_var, b.tile_ij, b.d_bodies, b.shp, b.bid, err);
   k_kinds<<<grid, blk, 0, s>>>(b.d_var, b.tile_var, b.tile_ij, b.d_bodies, b.shp, b.bid, b.tag, dA, bc[0], bc[1],
-                               bc[2], bc[3], err);
+                               bc[2], bc[3], b.cut ? 1 : 0, err);
+  if (b.cut) {
+    k_cut_points<<<grid, blk, 0, s>>>(b.d_var, b.tile_var, b.tile_ij, b.d_bodies, b.bid, b.tag, b.pcut, Vt);
+    b.launches += 1;
+  }
   if (b.has_kutta) {
     k_kutta<<<b.B, 256, 0, s>>>(b.d_var, b.d_body_var, b.shp, b.tag, dA, d_wake);
     PF_CUDA(cudaMemcpyAsync(b.h_wake.data(), d_wake, b.B * sizeof(long long), cudaMemcpyDeviceToHost, s));
     b.launches += 1;
   }
   PF_CUDA(cudaMemcpyAsync(dB, dA, Vt * sizeof(double2), cudaMemcpyDeviceToDevice, s));
-  if (sweeps > 0) PF_CUDA(cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, JACOBI_SMEM));
+  if (sweeps > 0) {
+    PF_CUDA(cudaFuncSetAttribute(k_jacobi<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, JACOBI_SMEM));
+    PF_CUDA(cudaFuncSetAttribute(k_jacobi<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, JACOBI_SMEM));
+  }
   for (int it = 0; it < sweeps; it += JK) {
     const int nsw = std::min(JK, sweeps - it);
-    k_jacobi<<<(unsigned)b.Tcg, NT, JACOBI_SMEM, s>>>(b.d_var, b.tile_cg_var, b.tile_cg_ij, b.bid, b.tag, b.d_bbox, it,
-                                                      nsw, dA, dB);
+    if (b.cut)
+      k_jacobi<true><<<(unsigned)b.Tcg, NT, JACOBI_SMEM, s>>>(b.d_var, b.tile_cg_var, b.tile_cg_ij, b.bid, b.tag,
+                                                              b.d_bbox, it, nsw, dA, dB, b.pcut, Vt);
+    else
+      k_jacobi<false><<<(unsigned)b.Tcg, NT, JACOBI_SMEM, s>>>(b.d_var, b.tile_cg_var, b.tile_cg_ij, b.bid, b.tag,
+                                                               b.d_bbox, it, nsw, dA, dB, nullptr, Vt);
     std::swap(dA, dB);
   }
   k_finalize<<<grid, blk, 0, s>>>(b.d_var, b.tile_var, b.tile_ij, dA, b.tag, b.X, Vt);
+  if (b.cut && b.cut_sigma > 0.0) {
+    double2* pn = (double2*)dev_alloc(b, 4 * Vt * sizeof(double2));
+    k_redistribute<<<grid, blk, 0, s>>>(b.d_var, b.tile_var, b.tile_ij, b.d_bodies, b.bid, b.tag, b.X, Vt,
+                                        b.cut_sigma, b.pcut, pn);
+    PF_CUDA(cudaGetLastError());
+    std::swap(b.pcut, pn);
+    PF_CUDA(cudaStreamSynchronize(s));
+    dev_free(b, pn);
+    b.launches += 1;
+  }
   k_stiffness<<<grid, blk, 0, s>>>(b.d_var, b.tile_var, b.tile_ij, b.tag, b.X, Vt, b.K64, b.K32, b.K32i, b.d_stats_i,
-                                   b.d_detmin);
+                                   b.d_detmin, b.bid, b.cut ? b.pcut : nullptr, err);
   k_tile_general<<<(unsigned)b.Tcg, blk, 0, s>>>(b.d_var, b.tile_cg_var, b.tile_cg_ij, b.tag, b.tile_cg_gen,
                                                  b.tile_cg_act);
   PF_CUDA(cudaGetLastError());
@@ -847,7 +1022,7 @@ void build_batch(Batch& b, const pf_grid* grids, const int* body_offsets, const 
   if (b.B > 0) {
     k_body_nodes<<<b.B, blk, 0, s>>>(b.d_var, b.d_body_var, b.d_bbox, b.tag, b.bid, cnt, nullptr, nullptr, 0);
     k_body_edges<<<b.B, blk, 0, s>>>(b.d_var, b.d_body_var, b.d_bbox, b.tag, b.bid, b.X, Vt, cnt + b.B, nullptr,
-                                     nullptr, 0);
+                                     nullptr, 0, b.cut ? b.pcut : nullptr);
     PF_CUDA(cudaMemcpyAsync(hcnt.data(), cnt, 2 * b.B * sizeof(int), cudaMemcpyDeviceToHost, s));
   }
   int herr = 0;
@@ -855,6 +1030,8 @@ void build_batch(Batch& b, const pf_grid* grids, const int* body_offsets, const 
   PF_CUDA(cudaStreamSynchronize(s));
   if (herr & 1) throw Error{PF_EINVAL, "a grid node lies inside two bodies"};
   if (herr & 2) throw Error{PF_EINVAL, "a grid node lies at a body centre"};
+  if (herr & 4) throw Error{PF_EINVAL, "mixed-cell mesh: a cell has two diagonal inside corners"};
+  if (herr & 8) throw Error{PF_EINVAL, "mixed-cell mesh: a cell has inside corners of two bodies"};
   b.h_body_ptr.assign(b.B + 1, 0);
   b.h_edge_ptr.assign(b.B + 1, 0);
   for (int k = 0; k < b.B; ++k) {
@@ -870,7 +1047,7 @@ void build_batch(Batch& b, const pf_grid* grids, const int* body_offsets, const 
     k_body_nodes<<<b.B, blk, 0, s>>>(b.d_var, b.d_body_var, b.d_bbox, b.tag, b.bid, nullptr, b.body_ptr,
                                      b.body_nodes, 1);
     k_body_edges<<<b.B, blk, 0, s>>>(b.d_var, b.d_body_var, b.d_bbox, b.tag, b.bid, b.X, Vt, nullptr, b.edge_ptr,
-                                     b.edge_rec, 1);
+                                     b.edge_rec, 1, b.cut ? b.pcut : nullptr);
   }
   PF_CUDA(cudaGetLastError());
 
@@ -918,6 +1095,7 @@ void tile_flags(Batch& b) {
 // matrices of cells with a displaced corner, the cell and tile flags, the per-variant
 // counts and min det J.
 void set_coords(Batch& b, int v, const double* dev_xy) {
+  if (b.cut) throw Error{PF_EINVAL, "pf_mesh_set_coords: a mixed-cell mesh places its surface points itself"};
   HostVariant& H = b.hv[v];
   const long long N = (long long)(H.g.nx + 1) * (H.g.ny + 1);
   cudaStream_t s = b.stream;
@@ -929,7 +1107,7 @@ void set_coords(Batch& b, int v, const double* dev_xy) {
   const dim3 blk(TX, TY);
   const unsigned nt = (unsigned)((long long)H.tiles_x * H.tiles_y);
   k_stiffness<<<nt, blk, 0, s>>>(b.d_var, b.tile_var + H.tile0, b.tile_ij + H.tile0, b.tag, b.X, Vt, b.K64, b.K32,
-                                 b.K32i, b.d_stats_i, b.d_detmin);
+                                 b.K32i, b.d_stats_i, b.d_detmin, b.bid, nullptr, nullptr);
   // the variant's fused-CG tiles follow those of the variants before it
   long long t0 = 0;
   for (int u = 0; u < v; ++u)
@@ -954,6 +1132,13 @@ void set_coords(Batch& b, int v, const double* dev_xy) {
   destroy_phi_view(b);       // its tile flags were made from the old coordinates
   destroy_mg(b);             // and the multigrid operators from the old element matrices
   b.solved = false;          // any earlier solution belongs to the old coordinates
+}
+
+void export_cut_points(Batch& b, int v, double* pts) {
+  const long long N = (long long)(b.hv[v].g.nx + 1) * (b.hv[v].g.ny + 1);
+  k_export_cut<<<(unsigned)((N + 255) / 256), 256, 0, b.stream>>>(b.d_var, v, b.pcut, b.Vtot, pts);
+  PF_CUDA(cudaGetLastError());
+  b.launches += 1;
 }
 
 void export_coords(Batch& b, int v, double* dev_xy) {

@@ -139,6 +139,8 @@ pf_status phi_solve(Batch& b, double U, const pf_solve_opts& o, double* dev_phi,
   if (!b.valid) throw Error{PF_EMESH_INVALID, "mesh has det J <= 0 at a Gauss point; solve refused"};
   if (b.has_kutta)
     throw Error{PF_EINVAL, "pf_phi_solve: a Kutta circulation makes phi multivalued (it needs a cut)"};
+  if (b.cut)
+    throw Error{PF_EINVAL, "pf_phi_solve: phi differs between the split copies of a node, one unknown per node cannot hold it"};
   if (o.k_max < 1) throw Error{PF_EINVAL, "k_max must be >= 1"};
   Batch& p = phi_view(b);
   p.rhs_active = false;

@@ -53,6 +53,10 @@ def test_error_path_without_gpu(lib_path):
     assert lib.pf_velocity_field(None, 0, None, None, None) == _lib.PF_EINVAL
     assert lib.pf_mesh_set_coords(None, 0, None, None) == _lib.PF_EINVAL
     assert lib.pf_coords_vjp(None, None, None, None) == _lib.PF_EINVAL
+    # the mixed-cell mesh: refused before any device work without an output, and its
+    # surface-point export without a handle
+    assert lib.pf_batch_build_cut(None, None, None, 1, 0, None, 0.0, None, None) == _lib.PF_EINVAL
+    assert lib.pf_mesh_cut_points(None, 0, None, None) == _lib.PF_EINVAL
     # general shapes: refused on the host before any device work
     assert lib.pf_batch_build_shapes(None, None, None, 1, 0, None, None, None) == _lib.PF_EINVAL
     g = (_lib.pf_grid * 1)(_lib.pf_grid(-1.0, 1.0, -1.0, 1.0, 16, 16))
