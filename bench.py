@@ -86,6 +86,11 @@ def parse(argv=None):
     ap.add_argument("--apply-sweep", action="store_true", help="time only the stand-alone operator")
     ap.add_argument("--apply-reps", type=int, default=100)
     ap.add_argument("--config", choices=["c1", "c2", "c3", "c4", "c5"], default="c4")
+    ap.add_argument("--mesh", choices=["q4", "cut"], default="q4",
+                    help="q4: the body-conforming Q4 mesh; cut: the mixed-cell mesh with node splitting, "
+                         "triangle / pentagon cells and boundary-point redistribution (circles, no gradient)")
+    ap.add_argument("--cut-spacing", type=float, default=0.25,
+                    help="mixed-cell mesh: minimum surface-point spacing, a fraction of min(hx, hy)")
     ap.add_argument("--tune", dest="tune", action="store_true", default=True,
                     help="re-balance the persistent CG schedule from timed launches (default)")
     ap.add_argument("--no-tune", dest="tune", action="store_false")
@@ -108,7 +113,8 @@ def cases(args):
 
 
 def workload_name(args, n_cases):
-    if args.config == "c4" and n_cases == 256 and args.precision == "mixed" and args.tol == 1e-8:
+    if args.config == "c4" and n_cases == 256 and args.precision == "mixed" and args.tol == 1e-8 \
+            and args.mesh == "q4":
         return WORKLOAD
     names = {"c1": "single_cylinder_128x64_S50", "c3": "five_cylinders_8192x4096_S200_delta0.25",
              "c4": f"parametric_sweep_{n_cases}_variants_nx256-1024_S200_seed0",
@@ -117,7 +123,8 @@ def workload_name(args, n_cases):
         base = "five_cylinders_2048x1024_S200_delta{0.1,0.25,0.5,1,2}_batched"
     else:
         base = names.get(args.config, f"five_cylinders_{args.nx}x{args.nx // 2}_x{n_cases}")
-    return f"{base}_{args.precision}_{args.tol:g}"
+    mesh = f"_cutmesh{args.cut_spacing:g}" if args.mesh == "cut" else ""
+    return f"{base}{mesh}_{args.precision}_{args.tol:g}"
 
 
 def peaks():
@@ -248,6 +255,11 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
+def cut_of(args):
+    """The mixed-cell mesh's minimum spacing, or None for the Q4 mesh."""
+    return args.cut_spacing if args.mesh == "cut" else None
+
+
 # ------------------------------------------------------------------ CPU oracle sample
 def oracle_cases(args):
     """The variants the CPU oracle is timed on: the workload's own for c1, c2, c4 and c5;
@@ -260,14 +272,23 @@ def oracle_cases(args):
     return cases(args)
 
 
-def _oracle_proc(case, units, conn, barrier):
+def _oracle_mesh(case, cut_spacing):
+    """The oracle's mesh of one variant: Q4, or the mixed-cell mesh when cut_spacing is set."""
+    if cut_spacing is None:
+        from oracle import mesh as OM
+        return OM.build_mesh(case.grid, case.bodies, case.sweeps, case.bc)
+    from oracle import cutmesh as CM
+    return CM.build_cut_mesh(case.grid, case.bodies, case.sweeps, case.bc, sigma=cut_spacing)
+
+
+def _oracle_proc(case, units, conn, barrier, cut_spacing=None):
     """One host process of the CPU sample: builds its variant's mesh and element matrices
     (untimed), then on every request runs the oracle's element-by-element CG (Appendix A)
     for a fixed number of iterations between two wall-clock stamps."""
     import numpy as np  # noqa: F401  (imported here: the process starts from scratch)
 
-    from oracle import mesh as OM, solve as OS, system as OSY
-    m = OM.build_mesh(case.grid, case.bodies, case.sweeps, case.bc)
+    from oracle import solve as OS, system as OSY
+    m = _oracle_mesh(case, cut_spacing)
     s = OSY.assemble(m, 1.0)
     kind, body = m.kind.ravel(), m.body.ravel()
     iters = max(2, int(round(units / s.n_dof)))
@@ -285,7 +306,7 @@ class OracleSample:
     barrier.  A step's rate is the DOF-iterations of all processes divided by the wall
     time from the first start to the last end."""
 
-    def __init__(self, case_list, procs=0, units=5e7):
+    def __init__(self, case_list, procs=0, units=5e7, cut_spacing=None):
         import multiprocessing as mp
         n = procs if procs > 0 else (os.cpu_count() or 1)
         n = max(1, min(n, 64))
@@ -298,7 +319,8 @@ class OracleSample:
             self.conns, self.procs = [], []
             for w in range(n):
                 a, b = ctx.Pipe()
-                p = ctx.Process(target=_oracle_proc, args=(case_list[w % len(case_list)], units, b, self.barrier),
+                p = ctx.Process(target=_oracle_proc,
+                                args=(case_list[w % len(case_list)], units, b, self.barrier, cut_spacing),
                                 daemon=True)
                 p.start()
                 self.conns.append(a)
@@ -344,7 +366,7 @@ class OracleSample:
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
-    smp = OracleSample(oracle_cases(args), args.cpu_procs, args.cpu_units)
+    smp = OracleSample(oracle_cases(args), args.cpu_procs, args.cpu_units, cut_of(args))
     try:
         for _ in range(args.warmup):
             smp.step()
@@ -369,10 +391,12 @@ def run_reference(args, rank, world):
 
 
 # ------------------------------------------------------------------ parity against the oracle
-def _oracle_direct(case):
-    """The oracle's direct solution of one variant (runs in a spawned process)."""
-    from oracle import mesh as OM, solve as OS, system as OSY
-    m = OM.build_mesh(case.grid, case.bodies, case.sweeps, case.bc)
+def _oracle_direct(job):
+    """The oracle's direct solution of one variant (runs in a spawned process); job =
+    (case, cut_spacing or None)."""
+    from oracle import solve as OS, system as OSY
+    case, cut_spacing = job
+    m = _oracle_mesh(case, cut_spacing)
     s = OSY.assemble(m, 1.0)
     u, psi = OS.solve_direct(s)
     return {"psi": psi, "C": u[s.n_free:], "A": s.A.tocsr(), "b": s.b, "dof": s.dof}
@@ -436,11 +460,11 @@ def aggregate(vals, e2e, dist, device):
 
 
 # ------------------------------------------------------------------ GPU arm
-def _apply_sweep(api, cs, reps, hbm):
+def _apply_sweep(api, cs, reps, hbm, cut=None):
     """Bandwidth of the stand-alone Q4 operator (no conversions, no body sums), FP32 and
     FP64: timings of `reps` back-to-back applications each (ten for FP32, three for the
     FP64 operator, which is bound by FP64 arithmetic), best and median."""
-    g = api.batch_build(cs)
+    g = api.batch_build(cs, cut_spacing=cut)
     out = {}
     for name, pr, n_t, r in (("fp32", api.PF_MIXED, 10, reps), ("fp64", api.PF_FP64, 3, max(1, reps // 5))):
         ts = []
@@ -467,11 +491,12 @@ def run_ours(args, rank, world, local):
     from paper_2512_12232_gb300 import api
     api.use_torch_allocator()
     cs = cases(args)
+    cut = cut_of(args)
     prec = api.PF_MIXED if args.precision == "mixed" else api.PF_FP64
     hbm = peaks().get("hbm_gbs")
     if args.apply_sweep:
         if rank == 0:
-            sw = _apply_sweep(api, cs, args.apply_reps, hbm or 6800.0)
+            sw = _apply_sweep(api, cs, args.apply_reps, hbm or 6800.0, cut)
             print(json.dumps({"workload": workload_name(args, len(cs)), "apply_sweep": sw}), flush=True)
         if dist:
             dist.destroy_process_group()
@@ -479,7 +504,7 @@ def run_ours(args, rank, world, local):
 
     def step(p=prec, host_out=None, keep=False, pre=args.precond):
         t_mesh = time.perf_counter()
-        g = api.batch_build(cs)                  # returns after the device mesh is complete
+        g = api.batch_build(cs, cut_spacing=cut)  # returns after the device mesh is complete
         t_mesh = time.perf_counter() - t_mesh
         res = api.psi_solve(g, U=1.0, tol=args.tol, precision=p, inner_tol=args.inner_tol,
                             tune_schedule=args.tune and pre == "none", preconditioner=pre)
@@ -616,7 +641,7 @@ def run_ours(args, rank, world, local):
         import multiprocessing as mp
         picks = parity_variants(cs) if len(cs) > 1 else [0]
         with mp.get_context("spawn").Pool(len(picks)) as pool:
-            refs = pool.map(_oracle_direct, [cs[v] for v in picks])
+            refs = pool.map(_oracle_direct, [(cs[v], cut) for v in picks])
         res, cps, _, _, g = step(prec, keep=True)
         parity = parity_block(api, cs, res, g.node_offsets, g.body_offsets, [c for c, _ in cps] if cps else [],
                               picks, refs, args.tol)
@@ -626,7 +651,8 @@ def run_ours(args, rank, world, local):
                              "tests/test_gpu_full_size.py holds the 2048x1024 batch against the oracle"}
 
     achieved = cg_bytes / (cg_ms / 1e3) / 1e9 if cg_ms > 0 else None
-    traffic = ncu_traffic(args.config, node_launches / cg_launches) if cg_launches else None
+    # the committed ncu traffic summaries are of the Q4 meshes
+    traffic = ncu_traffic(args.config, node_launches / cg_launches) if cg_launches and cut is None else None
     roofline = {"bound": "hbm", "kernel": "k_cg<float> (fused CG iteration: r, x, p updates + Q4 apply + 4 dots)",
                 "achieved": achieved, "peak": hbm if hbm else 6800.0,
                 "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if hbm else "fallback 6.8 TB/s",
@@ -637,7 +663,7 @@ def run_ours(args, rank, world, local):
                 "avg_nodes_per_launch": node_launches / cg_launches if cg_launches else None}
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        smp = OracleSample(oracle_cases(args), args.cpu_procs, args.cpu_units)
+        smp = OracleSample(oracle_cases(args), args.cpu_procs, args.cpu_units, cut_of(args))
         try:
             u, w = smp.step()
         finally:
@@ -657,6 +683,8 @@ def run_ours(args, rank, world, local):
                    "inner_tol": args.inner_tol, "parallelism": f"replicas x{world}",
                    "preconditioner": "none (the paper's CG)" if args.precond == "none"
                    else "geometric multigrid V(1,1) (PF_PRECOND_MG)",
+                   "mesh": "body-conforming Q4 (radial projection)" if cut is None else
+                   f"mixed-cell: node splitting, triangle / pentagon cells, minimum spacing {cut:g} h",
                    "l2": "inputs larger than L2: each step builds fresh meshes (working set "
                          f"{int(nodes) * 48 / 1e6:.0f} MB of CG state and coefficients, L2 is 126 MB)"},
         "solves_per_s": vals[2] / vals[1], "all_converged": ok,
@@ -684,6 +712,8 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.mesh == "cut" and args.config == "c5":
+        sys.exit("bench.py: the gradient workload needs the Q4 mesh (pf_grad refuses a mixed-cell mesh)")
     if args.impl == "reference":
         return run_reference(args, rank, world)
     return run_ours(args, rank, world, local)
