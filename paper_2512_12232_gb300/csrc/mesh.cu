@@ -315,12 +315,16 @@ __global__ void __launch_bounds__(NT) k_jacobi(const DevVariant* var, const int*
   const DevVariant& V = var[tile_var[t]];
   const int2 ij = tile_ij[t];
   {
+    // a sweep moves a nonzero displacement one node in L1 distance: after `reach` sweeps
+    // every node whose L1 distance from all bodies' node boxes (which hold every source:
+    // BODY nodes, a Kutta wake node) exceeds reach is still +0, here and in dst
     const int reach = sweep0 + nsw;
     bool near = false;
     for (int k = 0; k < V.nb && !near; ++k) {
       const int4 bx = bbox[V.body0 + k];
-      near = ij.x <= bx.y + reach && ij.x + CTX - 1 >= bx.x - reach && ij.y <= bx.w + reach &&
-             ij.y + CTY - 1 >= bx.z - reach;
+      const int gx = max(0, max(bx.x - (ij.x + CTX - 1), ij.x - bx.y));
+      const int gy = max(0, max(bx.z - (ij.y + CTY - 1), ij.y - bx.w));
+      near = gx + gy <= reach;
     }
     if (!near) return;
   }
@@ -363,9 +367,19 @@ __global__ void __launch_bounds__(NT) k_jacobi(const DevVariant* var, const int*
           if (upd[q - JRW] & 2) s = cut_disp(V, pcut[Vtot + gn - V.P], gi, gj - 1);
           if (upd[q + JRW] & 2) nn = cut_disp(V, pcut[3 * Vtot + gn + V.P], gi, gj + 1);
         }
-        const double sx = __dadd_rn(__dadd_rn(__dadd_rn(w.x, e.x), s.x), nn.x);
-        const double sy = __dadd_rn(__dadd_rn(__dadd_rn(w.y, e.y), s.y), nn.y);
-        out = make_double2(quarter(sx), quarter(sy));
+        // four neighbours all +0 (bit for bit) give +0 without the eight FP64 operations:
+        // the front of the displacement runs diagonally through the tiles it reaches
+        const unsigned long long z =
+            __double_as_longlong(w.x) | __double_as_longlong(w.y) | __double_as_longlong(e.x) |
+            __double_as_longlong(e.y) | __double_as_longlong(s.x) | __double_as_longlong(s.y) |
+            __double_as_longlong(nn.x) | __double_as_longlong(nn.y);
+        if (z == 0ull) {
+          out = make_double2(0.0, 0.0);
+        } else {
+          const double sx = __dadd_rn(__dadd_rn(__dadd_rn(w.x, e.x), s.x), nn.x);
+          const double sy = __dadd_rn(__dadd_rn(__dadd_rn(w.y, e.y), s.y), nn.y);
+          out = make_double2(quarter(sx), quarter(sy));
+        }
       }
       b[q] = out;
     }
