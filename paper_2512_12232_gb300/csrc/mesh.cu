@@ -95,7 +95,7 @@ __device__ void nearest_on_polygon(const ShapeDev& S, int gb, double x, double y
 // 1. inside test: bid[n] = body k (local) if (x-cx)^2 + (y-cy)^2 <= r^2 (circles) or the
 //    crossing-number test counts odd (polygons), else -1.
 __global__ void k_classify(const DevVariant* var, const int* tile_var, const int2* tile_ij,
-                           const pf_body* bodies, ShapeDev shp, int* bid, int* err) {
+                           const pf_body* bodies, ShapeDev shp, const int4* bbox, int* bid, int* err) {
   TileCtx c = tile_ctx(var, tile_var, tile_ij);
   const DevVariant& V = var[c.v];
   if (!c.in) return;
@@ -103,6 +103,9 @@ __global__ void k_classify(const DevVariant* var, const int* tile_var, const int
   int ib = -1;
   for (int k = 0; k < V.nb; ++k) {
     const int gb = V.body0 + k;
+    // the body's node box (padded by a node or more) holds every node the test can find inside
+    const int4 bx = bbox[gb];
+    if (c.i < bx.x || c.i > bx.y || c.j < bx.z || c.j > bx.w) continue;
     bool in;
     if (shp.kind && shp.kind[gb] == PF_SHAPE_POLYGON) {
       in = inside_polygon(shp, gb, x, y);
@@ -984,7 +987,7 @@ void build_batch(Batch& b, const pf_grid* grids, const int* body_offsets, const 
 
   const dim3 blk(TX, TY);
   const unsigned grid = (unsigned)b.T;
-  k_classify<<<grid, blk, 0, s>>>(b.d_var, b.tile_var, b.tile_ij, b.d_bodies, b.shp, b.bid, err);
+  k_classify<<<grid, blk, 0, s>>>(b.d_var, b.tile_var, b.tile_ij, b.d_bodies, b.shp, b.d_bbox, b.bid, err);
   k_kinds<<<grid, blk, 0, s>>>(b.d_var, b.tile_var, b.tile_ij, b.d_bodies, b.shp, b.bid, b.tag, dA, bc[0], bc[1],
                                bc[2], bc[3], b.cut ? 1 : 0, err);
   if (b.cut) {
