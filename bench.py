@@ -651,8 +651,9 @@ def run_ours(args, rank, world, local):
                              "tests/test_gpu_full_size.py holds the 2048x1024 batch against the oracle"}
 
     achieved = cg_bytes / (cg_ms / 1e3) / 1e9 if cg_ms > 0 else None
-    # the committed ncu traffic summaries are of the Q4 meshes
-    traffic = ncu_traffic(args.config, node_launches / cg_launches) if cg_launches and cut is None else None
+    # the committed ncu traffic summaries are of k_cg<float> on the Q4 meshes
+    traffic = (ncu_traffic(args.config, node_launches / cg_launches)
+               if cg_launches and cut is None and args.precision == "mixed" else None)
     roofline = {"bound": "hbm", "kernel": "k_cg<float> (fused CG iteration: r, x, p updates + Q4 apply + 4 dots)",
                 "achieved": achieved, "peak": hbm if hbm else 6800.0,
                 "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if hbm else "fallback 6.8 TB/s",
