@@ -10,8 +10,9 @@ Readings taken where the paper is silent:
   * "immediately inside" = an inside node that is a corner of at least one active
     cell, where a cell is active iff at least one corner lies outside every body;
     a node is inside body k iff (x-cx)^2 + (y-cy)^2 <= r^2 (ties count as inside);
-  * the surface point is the radial projection c + r (x - c)/|x - c|; node
-    splitting and the triangle/pentagon repair are not performed (Q4 only);
+  * the surface point is the radial projection c + r (x - c)/|x - c| and every cell
+    stays a quadrilateral (the node splitting and the triangle / pentagon cells are the
+    mixed-cell mesh of `oracle.cutmesh`);
   * the Laplace problem for d is approximated by a fixed number S of Jacobi sweeps
     on the logical grid, d_n <- (d_W + d_E + d_S + d_N) / 4 summed in that order,
     over nodes that are outside every body and not on the outer ring.

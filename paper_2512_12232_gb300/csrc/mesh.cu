@@ -3,6 +3,10 @@
 // inside each body, S Jacobi sweeps of the displacement, x = x_grid + d; then the
 // Q4 element matrices (section "Weak formulation", 2x2 Gauss) and the per-body node
 // and boundary-edge lists used by the constraint collapse and the post-processing.
+// The mixed-cell variant (pf_batch_build_cut) keeps the nodes just inside a body in
+// place and gives them one surface point per grid edge to an outside neighbour (node
+// splitting), smooths with those points' displacements, redistributes the points and
+// forms the cut cells' triangle / quadrilateral pieces (cut.cuh).
 //
 // The mesh rules are evaluated with explicitly rounded FP64 intrinsics
 // (__dadd_rn, __dmul_rn, __ddiv_rn, __dsqrt_rn), never contracted into FMAs, so the
