@@ -47,6 +47,19 @@ steps on a figure only, so every rule below is a reading:
     its vertices to the chord line, theta the polar angle of the chord midpoint; chords of
     zero length are not listed.
 
+Polygonal bodies (`oracle.shapes`, after the circles) take the same steps, with these
+readings for their surface points and the Kutta condition:
+  * on a row the crossings of the polygon's edges are those of the inside test,
+    x = a_x + ((y - a_y)(b_x - a_x)) / (b_y - a_y) for an edge with (a_y > y) != (b_y > y),
+    and the surface point is the one nearest the inside node with x_g < x <= x_k (towards
+    +x) or x_k < x <= x_g (towards -x); the inside test counts an odd number of them there;
+  * on a column the same with x and y exchanged; should rounding near a vertex leave no
+    crossing in that range, the crossing nearest the range (the first edge on ties) is
+    clipped onto it, and without any crossing on the line the edge's midpoint is taken;
+  * a redistributed point of a polygon moves to the nearest point of its boundary
+    (`oracle.shapes.nearest_on_polygon`) instead of the radial projection;
+  * the Kutta wake node moves onto its point as on the Q4 mesh and keeps that position.
+
 Every mesh expression is a sequence of individually rounded IEEE float64 operations, so
 the surface points and the node coordinates are reproducible bit for bit.
 """
@@ -54,9 +67,10 @@ from __future__ import annotations
 
 import numpy as np
 
+from . import shapes as SH
 from .element import q4_stiffness, shape_derivatives
 from .mesh import (BODY, FREE, Mesh, MeshError, background_grid, cell_coords, cell_nodes, classify,
-                   node_kinds, smoothing_mask, validate_inputs)
+                   kutta_nodes, node_kinds, smoothing_mask, validate_inputs)
 
 DIRS = ((1, 0), (0, 1), (-1, 0), (0, -1))       # E, N, W, S as (di, dj)
 CI = (0, 1, 1, 0)                               # corner a of cell (i, j) is node (i + CI[a], j + CJ[a])
@@ -108,13 +122,56 @@ def neighbour_outside(outside, d):
     return m
 
 
-def surface_points(xg, yg, kind, body, bodies):
+def polygon_crossing(v, xg, yg, xk, yk, d):
+    """Surface point of a polygon on the grid edge from the inside node (xg, yg) to its
+    outside neighbour (xk, yk) in direction d (readings in the module header)."""
+    row = d in (0, 2)
+    c = yg if row else xg                     # the grid line
+    g, k = (xg, xk) if row else (yg, yk)      # positions along it
+    up = k > g
+    lo, hi = (g, k) if up else (k, g)
+    n = len(v)
+    best, fb, fbd, anyx = None, 0.0, np.inf, False
+    for e in range(n):
+        ax, ay = v[e]
+        bx, by = v[(e + 1) % n]
+        if row:
+            if (ay > c) == (by > c):
+                continue
+            t = ax + ((c - ay) * (bx - ax)) / (by - ay)
+        else:
+            if (ax > c) == (bx > c):
+                continue
+            t = ay + ((c - ax) * (by - ay)) / (bx - ax)
+        anyx = True
+        if (g < t <= k) if up else (k < t <= g):
+            best = t if best is None else (min(best, t) if up else max(best, t))
+        else:
+            dist = lo - t if t < lo else t - hi
+            if dist < fbd:
+                fbd, fb = dist, t
+    if best is not None:
+        s = best
+    elif anyx:
+        s = min(max(fb, lo), hi)
+    else:
+        s = (g + k) * 0.5
+    return (s, yg) if row else (xg, s)
+
+
+def surface_points(xg, yg, kind, body, bodies, polygons=()):
     """P[d, j, i] = (x, y) of the surface point of BODY node (i, j) on its edge towards the
     outside neighbour in direction d (E, N, W, S); NaN where there is none."""
     P = np.full((4,) + xg.shape + (2,), np.nan)
     outside = body < 0
     for d in range(4):
         m = (kind == BODY) & neighbour_outside(outside, d)
+        di, dj = DIRS[d]
+        for q, poly in enumerate(polygons):
+            js, is_ = np.nonzero(m & (body == len(bodies) + q))
+            for j, i in zip(js.tolist(), is_.tolist()):
+                P[d, j, i] = polygon_crossing(poly.vertices, xg[j, i], yg[j, i], xg[j + dj, i + di],
+                                              yg[j + dj, i + di], d)
         for k, (cx, cy, r) in enumerate(bodies):
             mk = m & (body == k)
             if d in (0, 2):
@@ -285,6 +342,12 @@ def redistribute(mesh: Mesh, sigma, hx, hy):
                 qy = qy + my
             if moved:
                 k = mesh.body[j, i]
+                nc = len(mesh.bodies) - len(mesh.polygons)
+                if k >= nc:
+                    px, py = SH.nearest_on_polygon(np.array([qx]), np.array([qy]), mesh.polygons[k - nc].vertices)
+                    P1[d, j, i, 0] = px[0]
+                    P1[d, j, i, 1] = py[0]
+                    continue
                 cx, cy, r = mesh.bodies[k]
                 ux = qx - cx
                 uy = qy - cy
@@ -295,23 +358,27 @@ def redistribute(mesh: Mesh, sigma, hx, hy):
 
 
 # ---------------------------------------------------------------- the mesh
-def build_cut_mesh(grid, bodies, sweeps, bc=(0, 0, 0, 0), sigma=0.0) -> Mesh:
-    """Background grid -> classify -> surface points (node splitting) -> S smoothing sweeps
-    with the points' displacements as data -> x = x_grid + d -> redistribution.  Circles
-    only.  BODY nodes keep their background coordinates; their surface points are
-    mesh.cut_points[d, j, i]."""
-    bodies = validate_inputs(grid, bodies, ())
+def build_cut_mesh(grid, bodies, sweeps, bc=(0, 0, 0, 0), sigma=0.0, polygons=()) -> Mesh:
+    """Background grid -> classify -> surface points (node splitting) and Kutta wake points
+    -> S smoothing sweeps with the points' displacements as data -> x = x_grid + d ->
+    redistribution.  Circles, then polygons.  BODY nodes keep their background
+    coordinates; their surface points are mesh.cut_points[d, j, i]."""
+    polygons = tuple(polygons)
+    bodies = validate_inputs(grid, bodies, polygons)
     xg, yg = background_grid(grid)
-    body = classify(xg, yg, bodies)
+    body = classify(xg, yg, bodies, polygons)
     kind, active = node_kinds(body, bc)
-    P = surface_points(xg, yg, kind, body, bodies)
-    mask = smoothing_mask(kind, body)
+    P = surface_points(xg, yg, kind, body, bodies, polygons)
+    dx0 = np.zeros_like(xg)
+    dy0 = np.zeros_like(yg)
+    wake, wake_node = kutta_nodes(xg, yg, body, kind, dx0, dy0, bodies, polygons, (grid[1] - grid[0]) / grid[4])
+    mask = smoothing_mask(kind, body, wake)
     isbody = kind == BODY
-    zero = np.zeros_like(xg)
-    dx = jacobi_sweeps_cut(zero, P[..., 0], xg, isbody, mask, sweeps)
-    dy = jacobi_sweeps_cut(zero, P[..., 1], yg, isbody, mask, sweeps)
-    m = Mesh(grid[4], grid[5], xg + dx, yg + dy, xg, yg, kind, body, active, bodies, tuple(bc), zero.copy(),
-             zero.copy(), (), np.zeros(xg.shape, dtype=bool), (), P)
+    dx = jacobi_sweeps_cut(dx0, P[..., 0], xg, isbody, mask, sweeps)
+    dy = jacobi_sweeps_cut(dy0, P[..., 1], yg, isbody, mask, sweeps)
+    rows = np.concatenate([bodies, np.array([[p.ref[0], p.ref[1], 0.0] for p in polygons]).reshape(-1, 3)])
+    m = Mesh(grid[4], grid[5], xg + dx, yg + dy, xg, yg, kind, body, active, rows, tuple(bc), dx0, dy0,
+             polygons, wake, wake_node, P)
     for (j, i) in cut_cells(m):                     # refuse saddles and two-body cells early
         cut_polygon(m, j, i)
     x0, x1, y0, y1, nx, ny = grid
