@@ -214,14 +214,18 @@ typedef struct pf_shape {
 pf_status pf_batch_build_shapes(const pf_grid* grids, const int* body_offsets, const pf_shape* shapes,
                                 int n_variants, int sweeps, const int bc[4], void* stream, pf_batch** out);
 
-/* pf_batch_build with the mixed-cell mesh of section "Body-Conforming Grid Generation":
-   node splitting, triangle and pentagon cells, boundary-point redistribution.  Circular
-   bodies only (body rows as in pf_batch_build).
+/* pf_batch_build_shapes with the mixed-cell mesh of section "Body-Conforming Grid
+   Generation": node splitting, triangle and pentagon cells, boundary-point redistribution.
+   Bodies as in pf_batch_build_shapes (circles and polygons, Kutta vertices allowed).
    - Node kinds as in pf_batch_build.  A BODY node keeps its background position; for each
-     outside 4-neighbour it has a surface point where their grid edge crosses the circle
-     (on a row (cx +- sqrt(r^2 - (y - cy)^2), y), on a column (x, cy +- sqrt(r^2 - (x - cx)^2)),
-     explicitly rounded FP64).  A node with two or more outside neighbours is split into that
-     many points, all carrying the body's single value C_k.
+     outside 4-neighbour it has a surface point where their grid edge crosses the body's
+     boundary, explicitly rounded FP64: for a circle on a row (cx +- sqrt(r^2 - (y - cy)^2), y),
+     on a column (x, cy +- sqrt(r^2 - (x - cx)^2)); for a polygon the crossing of the inside
+     test's formula on a row (x = a_x + ((y - a_y)(b_x - a_x)) / (b_y - a_y)), or its
+     transpose on a column, nearest the node within the edge (g < x <= k or k < x <= g;
+     without one, the nearest crossing clipped onto the edge, or the edge's midpoint).  A
+     node with two or more outside neighbours is split into that many points, all carrying
+     the body's single value C_k.  A Kutta wake node is placed as in pf_batch_build_shapes.
    - The S Jacobi sweeps average the four neighbours as in pf_batch_build, a BODY neighbour
      contributing the displacement of its surface point on the common edge.
    - A cut cell (an active cell with an inside corner) is the polygon of its outside corners
@@ -233,7 +237,8 @@ pf_status pf_batch_build_shapes(const pf_grid* grids, const int* body_offsets, c
    - min_spacing in [0, 1]: after the smoothing, the chord of every cut cell shorter than
      s_min = min_spacing * min(hx, hy) (and not of zero length) pushes its two points apart
      along it by (s_min - L)/2 each; a point adds the pushes of its two cells and is projected
-     radially back onto the circle.  0 leaves the points in place.
+     back onto its body (radially for a circle, to the nearest boundary point for a polygon).
+     0 leaves the points in place.
    - PF_EINVAL also for a cell with two diagonal inside corners or with inside corners of two
      bodies, and for min_spacing outside [0, 1].  min_detJ covers every piece (twice the area
      for a triangle).
@@ -243,7 +248,7 @@ pf_status pf_batch_build_shapes(const pf_grid* grids, const int* body_offsets, c
      pf_coords_vjp, pf_mesh_set_coords and pf_phi_solve refuse the handle (PF_EINVAL).
    pf_mesh_coords reports BODY nodes at their background position; pf_mesh_cut_points gives
    the surface points. */
-pf_status pf_batch_build_cut(const pf_grid* grids, const int* body_offsets, const pf_body* bodies, int n_variants,
+pf_status pf_batch_build_cut(const pf_grid* grids, const int* body_offsets, const pf_shape* shapes, int n_variants,
                              int sweeps, const int bc[4], double min_spacing, void* stream, pf_batch** out);
 
 /* Single-variant convenience form of pf_batch_build. */

@@ -73,7 +73,7 @@ _SIGS = {
     "pf_mesh_stats_get": (C.c_int, [P, C.c_int, C.POINTER(pf_mesh_stats)]),
     "pf_mesh_coords": (C.c_int, [P, C.c_int, P, P]),
     "pf_mesh_tags": (C.c_int, [P, C.c_int, P, P, P]),
-    "pf_batch_build_cut": (C.c_int, [C.POINTER(pf_grid), C.POINTER(C.c_int), C.POINTER(pf_body), C.c_int, C.c_int,
+    "pf_batch_build_cut": (C.c_int, [C.POINTER(pf_grid), C.POINTER(C.c_int), C.POINTER(pf_shape), C.c_int, C.c_int,
                                      C.POINTER(C.c_int), C.c_double, P, C.POINTER(P)]),
     "pf_mesh_cut_points": (C.c_int, [P, C.c_int, P, P]),
     "pf_mesh_set_coords": (C.c_int, [P, C.c_int, P, P]),

@@ -115,13 +115,7 @@ class Mesh:
         bcs = (C.c_int * 4)(*[int(s) for s in bc])
         h = C.c_void_p()
         self._h = None
-        if cut_spacing is not None:
-            if any(polygon_lists):
-                raise ValueError("the mixed-cell mesh takes circular bodies only")
-            bodies = (L.pf_body * max(1, len(flat)))(*[L.pf_body(*row) for _, row in flat])
-            code = lib.pf_batch_build_cut(g, off, bodies, nv, int(sweeps), bcs, float(cut_spacing), _stream(),
-                                          C.byref(h))
-        elif any(polygon_lists):
+        if any(polygon_lists) or cut_spacing is not None:
             shapes = (L.pf_shape * max(1, len(flat)))()
             self._vertex_bufs = []
             for k, (kind, b) in enumerate(flat):
@@ -133,7 +127,11 @@ class Mesh:
                     self._vertex_bufs.append(buf)
                     shapes[k] = L.pf_shape(L.PF_SHAPE_POLYGON, float(b.ref[0]), float(b.ref[1]), 0.0, len(vx),
                                            C.cast(buf, C.POINTER(C.c_double)), int(b.kutta))
-            code = lib.pf_batch_build_shapes(g, off, shapes, nv, int(sweeps), bcs, _stream(), C.byref(h))
+            if cut_spacing is not None:
+                code = lib.pf_batch_build_cut(g, off, shapes, nv, int(sweeps), bcs, float(cut_spacing), _stream(),
+                                              C.byref(h))
+            else:
+                code = lib.pf_batch_build_shapes(g, off, shapes, nv, int(sweeps), bcs, _stream(), C.byref(h))
         else:
             bodies = (L.pf_body * max(1, len(flat)))(*[L.pf_body(*row) for _, row in flat])
             code = lib.pf_batch_build(g, off, bodies, nv, int(sweeps), bcs, _stream(), C.byref(h))
@@ -256,9 +254,10 @@ def batch_build(cases, sweeps=None, bc=None, polygons=None, cut_spacing=None) ->
     return Mesh([c.grid for c in cases], [c.bodies for c in cases], sweeps, bc, polygons, cut_spacing)
 
 
-def cut_mesh_build(grid, bodies, sweeps, bc=(0, 0, 0, 0), cut_spacing=0.0) -> Mesh:
-    """One variant of the mixed-cell mesh (node splitting, triangle / pentagon cells)."""
-    return Mesh([grid], [bodies], sweeps, bc, None, cut_spacing)
+def cut_mesh_build(grid, bodies, sweeps, bc=(0, 0, 0, 0), cut_spacing=0.0, polygons=None) -> Mesh:
+    """One variant of the mixed-cell mesh (node splitting, triangle / pentagon cells);
+    polygons: optional polygon bodies after the circles."""
+    return Mesh([grid], [bodies], sweeps, bc, None if polygons is None else [polygons], cut_spacing)
 
 
 def apply(mesh: Mesh, p: torch.Tensor, precision=PF_FP64):

@@ -123,10 +123,11 @@ pf_status pf_batch_build(const pf_grid* grids, const int* body_offsets, const pf
   return build_handle(grids, body_offsets, bodies, n_variants, sweeps, bc, stream, out, nullptr);
 }
 
-pf_status pf_batch_build_shapes(const pf_grid* grids, const int* body_offsets, const pf_shape* shapes,
-                                int n_variants, int sweeps, const int bc[4], void* stream, pf_batch** out) {
-  if (out) *out = nullptr;
-  if (!out || !body_offsets || n_variants < 1) {
+// Host copies of the bodies of a pf_shape list: circles as pf_body rows (polygons keep
+// their reference point there) and the polygons' kinds, vertices and Kutta vertices.
+static pf_status parse_shapes(const int* body_offsets, const pf_shape* shapes, int n_variants,
+                              std::vector<pf_body>& bodies, ShapeInput& si) {
+  if (!body_offsets || n_variants < 1) {
     g_err = "invalid arguments";
     return PF_EINVAL;
   }
@@ -135,8 +136,6 @@ pf_status pf_batch_build_shapes(const pf_grid* grids, const int* body_offsets, c
     g_err = "shapes is NULL";
     return PF_EINVAL;
   }
-  std::vector<pf_body> bodies;
-  ShapeInput si;
   try {
     bodies.resize(std::max(1, B));
     si.off.push_back(0);
@@ -162,12 +161,36 @@ pf_status pf_batch_build_shapes(const pf_grid* grids, const int* body_offsets, c
     g_err = std::string("host allocation failed: ") + e.what();
     return PF_ENOMEM;
   }
+  return PF_OK;
+}
+
+pf_status pf_batch_build_shapes(const pf_grid* grids, const int* body_offsets, const pf_shape* shapes,
+                                int n_variants, int sweeps, const int bc[4], void* stream, pf_batch** out) {
+  if (out) *out = nullptr;
+  if (!out) {
+    g_err = "invalid arguments";
+    return PF_EINVAL;
+  }
+  std::vector<pf_body> bodies;
+  ShapeInput si;
+  const pf_status st = parse_shapes(body_offsets, shapes, n_variants, bodies, si);
+  if (st != PF_OK) return st;
   return build_handle(grids, body_offsets, bodies.data(), n_variants, sweeps, bc, stream, out, &si);
 }
 
-pf_status pf_batch_build_cut(const pf_grid* grids, const int* body_offsets, const pf_body* bodies, int n_variants,
+pf_status pf_batch_build_cut(const pf_grid* grids, const int* body_offsets, const pf_shape* shapes, int n_variants,
                              int sweeps, const int bc[4], double min_spacing, void* stream, pf_batch** out) {
-  return build_handle(grids, body_offsets, bodies, n_variants, sweeps, bc, stream, out, nullptr, true, min_spacing);
+  if (out) *out = nullptr;
+  if (!out) {
+    g_err = "invalid arguments";
+    return PF_EINVAL;
+  }
+  std::vector<pf_body> bodies;
+  ShapeInput si;
+  const pf_status st = parse_shapes(body_offsets, shapes, n_variants, bodies, si);
+  if (st != PF_OK) return st;
+  return build_handle(grids, body_offsets, bodies.data(), n_variants, sweeps, bc, stream, out, &si, true,
+                      min_spacing);
 }
 
 static pf_status build_handle(const pf_grid* grids, const int* body_offsets, const pf_body* bodies,

@@ -180,13 +180,60 @@ __global__ void k_kinds(const DevVariant* var, const int* tile_var, const int2* 
   d0[n] = d;
 }
 
-// 2a. mixed-cell mesh: the surface points of every BODY node (circles), where the grid
-//     edge towards an outside neighbour crosses the circle: on a row
+// Surface point of polygon gb on the grid edge from the inside node (xg, yg) to its
+// outside neighbour (xk, yk) in direction d.  On a row the crossings are those of the
+// inside test, x = a_x + ((y - a_y)(b_x - a_x)) / (b_y - a_y) for an edge with
+// (a_y > y) != (b_y > y), of which the inside test counts an odd number in the half-open
+// range from the inside node (g < x <= k towards +x, k < x <= g towards -x); the one
+// nearest the inside node is taken.  On a column the same with x and y exchanged; without
+// a crossing in range the crossing nearest the range (the first edge on ties) is clipped
+// onto it, and without any crossing on the line the edge's midpoint is taken.
+__device__ double2 polygon_crossing(const ShapeDev& S, int gb, double xg, double yg, double xk, double yk, int d) {
+  const int v0 = S.off[gb], n = S.off[gb + 1] - v0;
+  const double* p = S.xy + 2 * v0;
+  const bool row = d == 0 || d == 2;
+  const double c = row ? yg : xg;
+  const double g = row ? xg : yg, k = row ? xk : yk;
+  const bool up = k > g;
+  const double lo = up ? g : k, hi = up ? k : g;
+  double best = 0.0, fb = 0.0, fbd = 1.0 / 0.0;
+  bool found = false, anyx = false;
+  for (int e = 0; e < n; ++e) {
+    const int f = e + 1 == n ? 0 : e + 1;
+    const double ax = p[2 * e], ay = p[2 * e + 1], bx = p[2 * f], by = p[2 * f + 1];
+    double t;
+    if (row) {
+      if ((ay > c) == (by > c)) continue;
+      t = __dadd_rn(ax, __ddiv_rn(__dmul_rn(__dsub_rn(c, ay), __dsub_rn(bx, ax)), __dsub_rn(by, ay)));
+    } else {
+      if ((ax > c) == (bx > c)) continue;
+      t = __dadd_rn(ay, __ddiv_rn(__dmul_rn(__dsub_rn(c, ax), __dsub_rn(by, ay)), __dsub_rn(bx, ax)));
+    }
+    anyx = true;
+    const bool in = up ? (g < t && t <= k) : (k < t && t <= g);
+    if (in) {
+      best = !found ? t : (up ? fmin(best, t) : fmax(best, t));
+      found = true;
+    } else {
+      const double dist = t < lo ? __dsub_rn(lo, t) : __dsub_rn(t, hi);
+      if (dist < fbd) {
+        fbd = dist;
+        fb = t;
+      }
+    }
+  }
+  const double sv = found ? best : (anyx ? fmin(fmax(fb, lo), hi) : __dmul_rn(__dadd_rn(g, k), 0.5));
+  return row ? make_double2(sv, yg) : make_double2(xg, sv);
+}
+
+// 2a. mixed-cell mesh: the surface points of every BODY node, where the grid edge
+//     towards an outside neighbour crosses the body's boundary: for a circle on a row
 //     (cx +- sqrt(r^2 - (y - cy)^2), y), on a column (x, cy +- sqrt(r^2 - (x - cx)^2)), the
-//     sign that of the step; NaN for the other directions and for every other node.
+//     sign that of the step; for a polygon polygon_crossing; NaN for the other directions
+//     and for every other node.
 __global__ void k_cut_points(const DevVariant* var, const int* tile_var, const int2* tile_ij,
-                             const pf_body* bodies, const int* bid, const uint8_t* tag, double2* pcut,
-                             long long Vtot) {
+                             const pf_body* bodies, ShapeDev shp, const int* bid, const uint8_t* tag,
+                             double2* pcut, long long Vtot) {
   TileCtx c = tile_ctx(var, tile_var, tile_ij);
   const DevVariant& V = var[c.v];
   if (!c.in) return;
@@ -194,7 +241,9 @@ __global__ void k_cut_points(const DevVariant* var, const int* tile_var, const i
   double2 out[4];
   for (int d = 0; d < 4; ++d) out[d] = make_double2(nan, nan);
   if ((tag[c.n] & KIND_MASK) == K_BODY) {
-    const pf_body B = bodies[V.body0 + bid[c.n]];
+    const int gb = V.body0 + bid[c.n];
+    const pf_body B = bodies[gb];
+    const bool poly = shp.kind && shp.kind[gb] == PF_SHAPE_POLYGON;
     const double xg = grid_x(V, c.i), yg = grid_y(V, c.j);
     const double rr = __dmul_rn(B.r, B.r);
     const int di[4] = {1, 0, -1, 0}, dj[4] = {0, 1, 0, -1};
@@ -202,7 +251,9 @@ __global__ void k_cut_points(const DevVariant* var, const int* tile_var, const i
       const int ni = c.i + di[d], nj = c.j + dj[d];
       if (ni < 0 || nj < 0 || ni > V.nx || nj > V.ny) continue;
       if (bid[V.base + (long long)nj * V.P + ni] >= 0) continue;
-      if (d == 0 || d == 2) {
+      if (poly) {
+        out[d] = polygon_crossing(shp, gb, xg, yg, grid_x(V, ni), grid_y(V, nj), d);
+      } else if (d == 0 || d == 2) {
         const double e = __dsub_rn(yg, B.cy);
         const double sq = __dsqrt_rn(__dsub_rn(rr, __dmul_rn(e, e)));
         out[d] = make_double2(d == 0 ? __dadd_rn(B.cx, sq) : __dsub_rn(B.cx, sq), yg);
@@ -427,7 +478,8 @@ __device__ void atomic_min_double(double* addr, double val) {
 //     chord (A, B) of every cut cell with 0 < L = |B - A| < s_min pushes its ends apart
 //     along it, A by -f (B - A) and B by +f (B - A) with f = ((s_min - L) * 0.5) / L; a
 //     point adds the pushes of the two cells beside its edge (the cell below, or left of,
-//     it first) and, if pushed, is projected radially back onto its circle.
+//     it first) and, if pushed, is projected back onto its body: radially for a circle,
+//     to the nearest boundary point for a polygon.
 //     s_min = sigma * min(hx, hy).  The push of one cell on point (corner a_here, d):
 __device__ inline bool cut_push(const DevVariant& V, const int* bid, const double* X, long long Vtot,
                                 const double2* pin, int ci, int cj, int a_here, int d, double smin, double& mx,
@@ -457,8 +509,8 @@ __device__ inline bool cut_push(const DevVariant& V, const int* bid, const doubl
 }
 
 __global__ void k_redistribute(const DevVariant* var, const int* tile_var, const int2* tile_ij,
-                               const pf_body* bodies, const int* bid, const uint8_t* tag, const double* X,
-                               long long Vtot, double sigma, const double2* pin, double2* pout) {
+                               const pf_body* bodies, ShapeDev shp, const int* bid, const uint8_t* tag,
+                               const double* X, long long Vtot, double sigma, const double2* pin, double2* pout) {
   TileCtx c = tile_ctx(var, tile_var, tile_ij);
   const DevVariant& V = var[c.v];
   if (!c.in) return;
@@ -482,8 +534,13 @@ __global__ void k_redistribute(const DevVariant* var, const int* tile_var, const
         qx = __dadd_rn(qx, mx);
         qy = __dadd_rn(qy, my);
       }
-      if (moved) {
-        const pf_body B = bodies[V.body0 + bid[c.n]];
+      const int gb = V.body0 + bid[c.n];
+      if (moved && shp.kind && shp.kind[gb] == PF_SHAPE_POLYGON) {
+        double px, py;
+        nearest_on_polygon(shp, gb, qx, qy, px, py);
+        q = make_double2(px, py);
+      } else if (moved) {
+        const pf_body B = bodies[gb];
         const double ux = __dsub_rn(qx, B.cx), uy = __dsub_rn(qy, B.cy);
         const double rho = __dsqrt_rn(__dadd_rn(__dmul_rn(ux, ux), __dmul_rn(uy, uy)));
         q = make_double2(__dadd_rn(B.cx, __ddiv_rn(__dmul_rn(B.r, ux), rho)),
@@ -818,7 +875,6 @@ void build_batch(Batch& b, const pf_grid* grids, const int* body_offsets, const 
   }
   b.has_polygons = std::find(b.shape_kind.begin(), b.shape_kind.end(), (int)PF_SHAPE_POLYGON) != b.shape_kind.end();
   b.has_kutta = false;
-  if (b.cut && b.has_polygons) throw Error{PF_EINVAL, "the mixed-cell mesh takes circular bodies only"};
   if (b.cut && !(b.cut_sigma >= 0.0 && b.cut_sigma <= 1.0))
     throw Error{PF_EINVAL, "the minimum spacing of the mixed-cell mesh must lie in [0, 1] (times min(hx, hy))"};
   std::vector<DBox> pbox(std::max(1, b.B), DBox{0, 0, 0, 0});
@@ -995,7 +1051,7 @@ void build_batch(Batch& b, const pf_grid* grids, const int* body_offsets, const 
   k_kinds<<<grid, blk, 0, s>>>(b.d_var, b.tile_var, b.tile_ij, b.d_bodies, b.shp, b.bid, b.tag, dA, bc[0], bc[1],
                                bc[2], bc[3], b.cut ? 1 : 0, err);
   if (b.cut) {
-    k_cut_points<<<grid, blk, 0, s>>>(b.d_var, b.tile_var, b.tile_ij, b.d_bodies, b.bid, b.tag, b.pcut, Vt);
+    k_cut_points<<<grid, blk, 0, s>>>(b.d_var, b.tile_var, b.tile_ij, b.d_bodies, b.shp, b.bid, b.tag, b.pcut, Vt);
     b.launches += 1;
   }
   if (b.has_kutta) {
@@ -1021,7 +1077,7 @@ void build_batch(Batch& b, const pf_grid* grids, const int* body_offsets, const 
   k_finalize<<<grid, blk, 0, s>>>(b.d_var, b.tile_var, b.tile_ij, dA, b.tag, b.X, Vt);
   if (b.cut && b.cut_sigma > 0.0) {
     double2* pn = (double2*)dev_alloc(b, 4 * Vt * sizeof(double2));
-    k_redistribute<<<grid, blk, 0, s>>>(b.d_var, b.tile_var, b.tile_ij, b.d_bodies, b.bid, b.tag, b.X, Vt,
+    k_redistribute<<<grid, blk, 0, s>>>(b.d_var, b.tile_var, b.tile_ij, b.d_bodies, b.shp, b.bid, b.tag, b.X, Vt,
                                         b.cut_sigma, b.pcut, pn);
     PF_CUDA(cudaGetLastError());
     std::swap(b.pcut, pn);

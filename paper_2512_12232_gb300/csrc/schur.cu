@@ -160,6 +160,8 @@ pf_status schur_solve(Batch& b, double U, const pf_solve_opts& o, double* dev_ps
   S.alloc_fn = b.alloc_fn;
   S.free_fn = b.free_fn;
   S.alloc_ctx = b.alloc_ctx;
+  S.cut = b.cut;                        // the copies are meshed as the handle was
+  S.cut_sigma = b.cut_sigma;
   build_batch(S, grids.data(), offs.data(), bodies.data(), (int)grids.size(), b.sweeps, b.bc,
               b.has_polygons ? &shp : nullptr);
   if (!S.valid) throw Error{PF_EMESH_INVALID, "Schur sub-problem mesh invalid"};

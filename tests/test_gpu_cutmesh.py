@@ -102,7 +102,7 @@ def test_cut_operator_matches_oracle(api, case, sigma):
 
 
 @pytest.mark.parametrize("case,sigma", [CASES[2], CASES[4]], ids=[IDS[2], IDS[4]])
-@pytest.mark.parametrize("mode", ["fp64", "mixed", "mg", "schur"])
+@pytest.mark.parametrize("mode", ["fp64", "mixed", "mg", "schur", "schur64"])
 def test_cut_solve_matches_oracle(api, case, sigma, mode):
     m = oracle_mesh(case, sigma)
     s = OSY.assemble(m, 1.0)
@@ -111,13 +111,14 @@ def test_cut_solve_matches_oracle(api, case, sigma, mode):
     kw = {"fp64": dict(precision=api.PF_FP64, tol=1e-12),
           "mixed": dict(precision=api.PF_MIXED, tol=1e-11),
           "mg": dict(precision=api.PF_MIXED, tol=1e-11, preconditioner="mg"),
-          "schur": dict(precision=api.PF_MIXED, tol=1e-11, method="schur")}[mode]
+          "schur": dict(precision=api.PF_MIXED, tol=1e-11, method="schur"),
+          "schur64": dict(precision=api.PF_FP64, tol=1e-12, method="schur")}[mode]
     with api.cut_mesh_build(case.grid, case.bodies, case.sweeps, case.bc, sigma) as g:
         res = api.psi_solve(g, U=1.0, **kw)
         psi = res.psi.cpu().numpy()
     assert res.status == 0
     live = m.kind.ravel() != OM.INACTIVE
-    assert rel_l2(psi[live], psi_ref[live]) <= (1e-9 if mode == "fp64" else 1e-8)
+    assert rel_l2(psi[live], psi_ref[live]) <= (1e-9 if mode in ("fp64", "schur64") else 1e-8)
     np.testing.assert_allclose(res.body_psi, C_ref, rtol=0, atol=1e-8 * max(1.0, np.abs(psi_ref).max()))
 
 
@@ -195,3 +196,72 @@ def test_full_size_cut_mesh_and_mixed_solve(api):
     uvec[s.n_free:] = res.body_psi
     r = s.b - s.A @ uvec
     assert np.linalg.norm(r) <= 2e-8 * np.linalg.norm(s.b)
+
+
+# ---------------------------------------------------------------- polygon bodies
+def polygon_case(kind, nx):
+    if kind == "ellipse":
+        body = W.ellipse_body(0.8, 0.4, 720, angle=-np.radians(10.0))
+        return (-4.0, 4.0, -2.0, 2.0, nx, nx // 2), body
+    if kind == "airfoil":
+        body = W.joukowski_airfoil(0.5, 0.08, 400, alpha=np.radians(6.0))
+        return (-3.0, 3.0, -1.5, 1.5, nx, nx // 2), body
+    sq = W.PolygonBody([(2.5, 2.5), (5.5, 2.5), (5.5, 5.5), (2.5, 5.5)], ref=(4.0, 4.0))
+    return (0.0, 10.0, 0.0, 10.0, 10, 10), sq
+
+
+@pytest.mark.parametrize("kind,nx,sweeps,sigma", [("square", 10, 2, 0.3), ("ellipse", 192, 48, 0.25),
+                                                  ("airfoil", 256, 64, 0.25), ("airfoil", 200, 30, 0.0)])
+def test_polygon_cut_mesh_is_bit_exact(api, kind, nx, sweeps, sigma):
+    grid, body = polygon_case(kind, nx)
+    m = CM.build_cut_mesh(grid, np.zeros((0, 3)), sweeps, polygons=[body], sigma=sigma)
+    with api.cut_mesh_build(grid, np.zeros((0, 3)), sweeps, (0, 0, 0, 0), sigma, polygons=[body]) as g:
+        xy = g.coords().cpu().numpy()
+        kind_g, body_g = (t.cpu().numpy() for t in g.tags())
+        pts = g.cut_points().cpu().numpy()
+        st = g.stats()
+    assert np.array_equal(kind_g, m.kind.ravel()) and np.array_equal(body_g, m.body.ravel())
+    assert np.array_equal(bits(xy[:, 0]), bits(m.x.ravel()))
+    assert np.array_equal(bits(xy[:, 1]), bits(m.y.ravel()))
+    ref = m.cut_points.reshape(4, -1, 2)
+    assert np.array_equal(np.isnan(pts), np.isnan(ref))
+    assert np.array_equal(bits(pts[~np.isnan(pts)]), bits(ref[~np.isnan(ref)]))
+    assert st["min_detJ"] == pytest.approx(OSY.assemble(m, 1.0).detmin.min(), rel=1e-12)
+
+
+def test_mixed_circle_and_polygon_cut_batch(api):
+    """Circles and a polygon in one variant, a second variant with an airfoil: each variant
+    as the oracle builds it."""
+    c = W.five_cylinder_case(0.5, 320, 160, 30)
+    ell = W.ellipse_body(0.3, 0.15, 240, cx=-6.0, cy=3.0, angle=0.3)
+    grid2, af = polygon_case("airfoil", 192)
+    with api.Mesh([c.grid, grid2], [c.bodies, np.zeros((0, 3))], 30, (0, 0, 0, 0), [[ell], [af]], 0.25) as g:
+        for v, (grid, circ, polys) in enumerate([(c.grid, c.bodies, [ell]), (grid2, np.zeros((0, 3)), [af])]):
+            m = CM.build_cut_mesh(grid, circ, 30, polygons=polys, sigma=0.25)
+            xy = g.coords(v).cpu().numpy()
+            pts = g.cut_points(v).cpu().numpy()
+            assert np.array_equal(g.tags(v)[0].cpu().numpy(), m.kind.ravel())
+            assert np.array_equal(bits(xy[:, 0]), bits(m.x.ravel()))
+            assert np.array_equal(bits(xy[:, 1]), bits(m.y.ravel()))
+            ref = m.cut_points.reshape(4, -1, 2)
+            assert np.array_equal(bits(pts[~np.isnan(pts)]), bits(ref[~np.isnan(ref)]))
+
+
+@pytest.mark.parametrize("mode", ["fp64", "mixed", "mg"])
+def test_polygon_cut_solves_match_oracle(api, mode):
+    """The ellipse (MPC form) and the Kutta airfoil (Schur form with the wake row) on the
+    mixed-cell mesh against the oracle's direct solves."""
+    kw = {"fp64": dict(precision=api.PF_FP64, tol=1e-12), "mixed": dict(precision=api.PF_MIXED, tol=1e-11),
+          "mg": dict(precision=api.PF_MIXED, tol=1e-11, preconditioner="mg")}[mode]
+    for kind in ("ellipse", "airfoil"):
+        grid, body = polygon_case(kind, 192)
+        m = CM.build_cut_mesh(grid, np.zeros((0, 3)), 48, polygons=[body], sigma=0.25)
+        s = OSY.assemble(m, 1.0)
+        u, psi_ref = OSV.solve_kutta(s, m) if kind == "airfoil" else OSV.solve_direct(s)
+        with api.cut_mesh_build(grid, np.zeros((0, 3)), 48, (0, 0, 0, 0), 0.25, polygons=[body]) as g:
+            res = api.psi_solve(g, U=1.0, **kw)
+            psi = res.psi.cpu().numpy()
+        assert res.status == 0
+        live = m.kind.ravel() != OM.INACTIVE
+        assert rel_l2(psi[live], psi_ref[live]) <= (1e-9 if mode == "fp64" else 1e-6), kind
+        np.testing.assert_allclose(res.body_psi, u[s.n_free:], rtol=0, atol=1e-8)
