@@ -88,7 +88,7 @@ def parse(argv=None):
     ap.add_argument("--config", choices=["c1", "c2", "c3", "c4", "c5"], default="c4")
     ap.add_argument("--mesh", choices=["q4", "cut"], default="q4",
                     help="q4: the body-conforming Q4 mesh; cut: the mixed-cell mesh with node splitting, "
-                         "triangle / pentagon cells and boundary-point redistribution (circles, no gradient)")
+                         "triangle / pentagon cells and boundary-point redistribution (no gradient)")
     ap.add_argument("--cut-spacing", type=float, default=0.25,
                     help="mixed-cell mesh: minimum surface-point spacing, a fraction of min(hx, hy)")
     ap.add_argument("--tune", dest="tune", action="store_true", default=True,

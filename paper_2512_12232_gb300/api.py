@@ -93,7 +93,7 @@ class Mesh:
         """polygon_lists (optional): per variant, polygon bodies (objects with `vertices`
         ((n, 2), counter-clockwise), `ref` (reference point of the polar angle) and `kutta`
         (trailing-edge vertex or -1)); a variant's bodies are its circles, then its polygons.
-        cut_spacing (optional, circles only): build the mixed-cell mesh (pf_batch_build_cut)
+        cut_spacing (optional): build the mixed-cell mesh (pf_batch_build_cut)
         with this minimum surface-point spacing, a fraction of min(hx, hy)."""
         lib = L.load()
         nv = len(grids)
