@@ -8,13 +8,14 @@ import sys
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def run(extra_env=None):
+def run(extra_env=None, extra_args=()):
     env = dict(os.environ)
     for k in ("RANK", "WORLD_SIZE", "LOCAL_RANK"):
         env.pop(k, None)
     env.update(extra_env or {})
     return subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--config", "c1", "--steps", "2",
-                           "--warmup", "1", "--cpu-units", "2e6", "--cpu-procs", "2"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=300)
+                           "--warmup", "1", "--cpu-units", "2e6", "--cpu-procs", "2", *extra_args], cwd=ROOT, env=env,
+                          capture_output=True, text=True, timeout=300)
 
 
 def test_reference_arm_prints_one_contract_line():
@@ -37,3 +38,17 @@ def test_reference_arm_other_ranks_exit_quietly():
     r = run({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
     assert r.returncode == 0, r.stderr[-2000:]
     assert not [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+
+
+def test_reference_arm_on_the_mixed_cell_mesh():
+    """--mesh cut times the oracle on its mixed-cell mesh and names it in the workload."""
+    r = run(extra_args=("--mesh", "cut", "--cut-spacing", "0.3"))
+    assert r.returncode == 0, r.stderr[-2000:]
+    d = json.loads([ln for ln in r.stdout.splitlines() if ln.startswith("{")][0])
+    assert d["value"] > 0 and "cutmesh0.3" in d["config"]["workload"]
+
+
+def test_gradient_workload_refuses_the_mixed_cell_mesh():
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--config", "c5", "--mesh", "cut"],
+                       cwd=ROOT, capture_output=True, text=True, timeout=120)
+    assert r.returncode != 0 and "pf_grad refuses" in r.stderr
