@@ -1886,6 +1886,7 @@ pf_status solve_core(Batch& b, double U, const pf_solve_opts& o, double* dev_psi
     ~PcgScope() { b.pcg_active = false; }
   } pcg_scope{b};
   b.pcg_active = pcg;
+  PF_CUDA(cudaEventRecord(b.ev[3], b.stream));   // the solve's device time starts here, set-up included
   if (pcg) {
     mg_setup(b);
     for (float* f : {b.mg_x, b.mg_p[0], b.mg_p[1], b.mg_q, b.mg_r})
@@ -1938,7 +1939,6 @@ pf_status solve_core(Batch& b, double U, const pf_solve_opts& o, double* dev_psi
                                                 b.X + (b.dirichlet_x ? 0 : b.Vtot), U,
                                                 b.Uv_active ? b.d_Uv : nullptr, warm, b.x64, b.w64);
   PF_CUDA(cudaGetLastError());
-  PF_CUDA(cudaEventRecord(b.ev[3], s));
   launch_resid_only(b, prec, s);
   int chunk = o.chunk > 0 ? o.chunk : 0;
   if (pcg && chunk == 0) chunk = PCG_CHUNK;
