@@ -336,3 +336,35 @@ def test_kutta_circulation_on_the_polygon_cut_mesh():
         u, _ = SV.solve_kutta(s, m)
         errs.append(abs(u[s.n_free] - psi_b))
     assert errs[2] < 0.6 * errs[1] < 0.36 * errs[0] and errs[2] < 1e-3, errs
+
+
+def exact_cylinder_velocity(x, y, a, U=1.0):
+    """(u, v) = (dpsi/dy, -dpsi/dx) of psi = U y (1 - a^2 / rho^2)."""
+    r2 = x * x + y * y
+    u = U * (1.0 - a * a * (x * x - y * y) / (r2 * r2))
+    v = -U * 2.0 * a * a * x * y / (r2 * r2)
+    return u, v
+
+
+def test_cut_cell_velocity_approaches_the_exact_flow():
+    """Element velocity of the cut cells (area-weighted mean of the pieces' gradients) on the
+    exact-data cylinder: the error against the exact velocity at the cell's vertex centroid
+    falls under refinement (first order at the boundary), and a mix-up of the pieces'
+    gradients (say the triangle's b and c exchanged) would not converge."""
+    errs = []
+    for nx in (128, 256):
+        m = CM.build_cut_mesh((-4.0, 4.0, -2.0, 2.0, nx, nx // 2), np.array([[0.0, 0.0, 0.5]]), 3 * nx // 8,
+                              sigma=0.25)
+        g = exact_cylinder_psi(m.x, m.y, 0.5).ravel()
+        sysm = S.assemble(m, g=g)
+        _, psi = SV.solve_direct(sysm)
+        uu, vv = CM.velocity_field(m, psi)
+        pos = -np.ones((m.ny, m.nx), dtype=np.int64)
+        pos[m.active] = np.arange(int(m.active.sum()))
+        e = []
+        for (j, i) in CM.cut_cells(m):
+            V = np.array([p[0] for p in CM.cut_polygon(m, j, i)])
+            ue, ve = exact_cylinder_velocity(V[:, 0].mean(), V[:, 1].mean(), 0.5)
+            e.append(np.hypot(uu[pos[j, i]] - ue, vv[pos[j, i]] - ve))
+        errs.append(np.mean(e))
+    assert errs[1] < 0.75 * errs[0] and errs[1] < 0.2, errs
