@@ -154,49 +154,88 @@ __global__ void k_shape_nodes(const DevVariant* var, const int* tile_var, const 
   dX[Vtot + n] = gy;
 }
 
-// One transposed Jacobi sweep: out_m = [m fixed] in_m + sum over updated neighbours n of in_n / 4.
-// Only the body nodes' values are read after the last sweep, and a sweep moves a value
-// one node, so after this sweep only nodes within `reach` (the sweeps still to come) of a
-// body node matter.  A tile farther than that from every body's node box (Chebyshev
-// distance, a lower bound of the number of hops) is skipped: its stale values are only
-// ever read by nodes that are themselves too far to matter.
-__global__ void k_jacobi_T(const DevVariant* var, const int* tile_var, const int2* tile_ij, const uint8_t* tag,
-                           const int* bid, const int4* bbox, int reach, long long Vtot, const double* in,
-                           double* out) {
-  const long long t = blockIdx.x;
-  const int v = tile_var[t];
-  const DevVariant& V = var[v];
+// Transposed Jacobi sweeps, JKT per launch: out_m = [m fixed] in_m + sum over the updated
+// neighbours n of in_n / 4 (W, E, S, N), on a fused-CG tile's window with a JKT-node halo
+// swept in shared memory (sweep s of the launch covers the nodes at distance >= s + 1 from
+// the window edge, the only ones read again), the tile written back.  Only the body nodes'
+// values are read after the last sweep, and a sweep moves a value one node, so after this
+// launch only nodes within `reach` (the sweeps still to come) of a body node matter.  A
+// tile whose L1 distance from every body's node box exceeds that is skipped: its stale
+// values are only ever read by nodes that are themselves too far to matter.
+constexpr int JKT = 4;
+constexpr int JTW = CTX + 2 * JKT, JTH = CTY + 2 * JKT;    // window 72 x 24
+constexpr int JT_SMEM = 2 * JTW * JTH * (int)sizeof(double2) + JTW * JTH;
+
+__global__ void __launch_bounds__(NT) k_jacobi_T(const DevVariant* var, const int* tile_var, const int2* tile_ij,
+                                                 const uint8_t* tag, const int* bid, const int4* bbox, int reach,
+                                                 int nsw, long long Vtot, const double* in, double* out) {
+  extern __shared__ __align__(16) unsigned char jts[];
+  double2* w0 = reinterpret_cast<double2*>(jts);
+  double2* w1 = w0 + JTW * JTH;
+  uint8_t* upd = reinterpret_cast<uint8_t*>(w1 + JTW * JTH);
+  const int t = blockIdx.x;
+  const DevVariant& V = var[tile_var[t]];
   const int2 ij = tile_ij[t];
   {
     bool near = false;
     for (int k = 0; k < V.nb && !near; ++k) {
       const int4 bx = bbox[V.body0 + k];
-      near = ij.x <= bx.y + reach && ij.x + TX - 1 >= bx.x - reach && ij.y <= bx.w + reach &&
-             ij.y + TY - 1 >= bx.z - reach;
+      const int gx = max(0, max(bx.x - (ij.x + CTX - 1), ij.x - bx.y));
+      const int gy = max(0, max(bx.z - (ij.y + CTY - 1), ij.y - bx.w));
+      near = gx + gy <= reach;
     }
     if (!near) return;
   }
-  const int i = ij.x + threadIdx.x, j = ij.y + threadIdx.y;
-  if (i > V.nx || j > V.ny) return;
-  const long long n = V.base + (long long)j * V.P + i;
-  auto updated = [&](long long m) -> bool { return bid[m] < 0 && !(tag[m] & (RING | WAKE)); };
-  double ox = 0.0, oy = 0.0;
-  if (!updated(n)) {
-    ox = in[n];
-    oy = in[Vtot + n];
+  const int tid = linear_tid();
+  for (int q = tid; q < JTW * JTH; q += NT) {
+    const int i = ij.x - JKT + q % JTW, j = ij.y - JKT + q / JTW;
+    double2 v = make_double2(0.0, 0.0);
+    uint8_t u = 0;
+    if (i >= 0 && j >= 0 && i <= V.nx && j <= V.ny) {
+      const long long n = V.base + (long long)j * V.P + i;
+      v = make_double2(in[n], in[Vtot + n]);
+      u = bid[n] < 0 && !(tag[n] & (RING | WAKE));
+    }
+    w0[q] = v;
+    upd[q] = u;
   }
-  const int ni[4] = {i - 1, i + 1, i, i};
-  const int nj[4] = {j, j, j - 1, j + 1};
-  for (int k = 0; k < 4; ++k) {
-    if (ni[k] < 0 || nj[k] < 0 || ni[k] > V.nx || nj[k] > V.ny) continue;
-    const long long m = V.base + (long long)nj[k] * V.P + ni[k];
-    if (updated(m)) {
-      ox += 0.25 * in[m];
-      oy += 0.25 * in[Vtot + m];
+  __syncthreads();
+  double2* a = w0;
+  double2* b = w1;
+  for (int sw = 0; sw < nsw; ++sw) {
+    const int rw = JTW - 2 * (sw + 1), rh = JTH - 2 * (sw + 1);
+    for (int k = tid; k < rw * rh; k += NT) {
+      const int ri = sw + 1 + k % rw, rj = sw + 1 + k / rw;
+      const int q = rj * JTW + ri;
+      double ox = 0.0, oy = 0.0;
+      if (!upd[q]) {
+        ox = a[q].x;
+        oy = a[q].y;
+      }
+      // neighbours outside the grid carry upd = 0 and add nothing
+      const int nq[4] = {q - 1, q + 1, q - JTW, q + JTW};
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        if (upd[nq[e]]) {
+          ox += 0.25 * a[nq[e]].x;
+          oy += 0.25 * a[nq[e]].y;
+        }
+      b[q] = make_double2(ox, oy);
+    }
+    __syncthreads();
+    double2* tmp = a;
+    a = b;
+    b = tmp;
+  }
+  for (int q = tid; q < CTX * CTY; q += NT) {
+    const int i = ij.x + q % CTX, j = ij.y + q / CTX;
+    if (i <= V.nx && j <= V.ny) {
+      const long long n = V.base + (long long)j * V.P + i;
+      const double2 r = a[(JKT + q / CTX) * JTW + JKT + q % CTX];
+      out[n] = r.x;
+      out[Vtot + n] = r.y;
     }
   }
-  out[n] = ox;
-  out[Vtot + n] = oy;
 }
 
 // dJ/dc_k = sum over the body's nodes of Jp^T (dJ/dd0)_n, Jp = I - (r/rho)(I - u u^T) at
@@ -280,9 +319,12 @@ static void centre_chain(Batch& b, double* gc) {
   double* a = b.gradX;
   double* c = b.gradT;
   PF_CUDA(cudaMemsetAsync(c, 0, 2 * Vt * sizeof(double), s));
-  for (int k = 0; k < b.sweeps; ++k) {
-    k_jacobi_T<<<(unsigned)b.T, blk, 0, s>>>(b.d_var, b.tile_var, b.tile_ij, b.tag, b.bid, b.d_bbox,
-                                             b.sweeps - 1 - k, Vt, a, c);
+  if (b.sweeps > 0) PF_CUDA(cudaFuncSetAttribute(k_jacobi_T, cudaFuncAttributeMaxDynamicSharedMemorySize, JT_SMEM));
+  int launches = 0;
+  for (int k = 0; k < b.sweeps; k += JKT, ++launches) {
+    const int nsw = std::min(JKT, b.sweeps - k);
+    k_jacobi_T<<<(unsigned)b.Tcg, NT, JT_SMEM, s>>>(b.d_var, b.tile_cg_var, b.tile_cg_ij, b.tag, b.bid, b.d_bbox,
+                                                    b.sweeps - k - nsw, nsw, Vt, a, c);
     std::swap(a, c);
   }
   PF_CUDA(cudaGetLastError());
@@ -293,7 +335,7 @@ static void centre_chain(Batch& b, double* gc) {
     PF_CUDA(cudaMemcpyAsync(gc, out, 2 * b.B * sizeof(double), cudaMemcpyDeviceToHost, s));
   }
   PF_CUDA(cudaStreamSynchronize(s));
-  b.launches += b.sweeps + (b.B > 0 ? 1 : 0);
+  b.launches += launches + (b.B > 0 ? 1 : 0);
 }
 
 void coords_vjp(Batch& b, const double* dev_gX, double* gc) {
