@@ -315,13 +315,17 @@ __device__ __forceinline__ void halo_pos(int h, int& li, int& lj) {
 // position (li, lj): y = sum over the four cells around the node of
 // sum_{b != a} K_e[a,b] (p_b - p_a), which equals (K_e p_e)_a because every row of
 // K_e sums to zero.  Inactive cells contribute nothing.  Cell coefficients come
-// from the stored planes for displaced cells and from `kr` (closed-form rectangle)
-// otherwise.  n: padded node index, P: pitch, K: [6][plane]; W: the shared tiles' row
-// width (tile width + 2).
+// from the stored planes where they differ from `kr` (the closed-form rectangle) in this
+// precision (CELL_GENERAL for FP64, CELL_GEN32 for FP32) and from `kr` otherwise.
+// n: padded node index, P: pitch, K: [6][plane]; W: the shared tiles' row width (tile
+// width + 2).
 template <typename T, int W = SW>
 __device__ __forceinline__ T q4_row(const T (*ps)[W], const uint8_t (*ts)[W], int li, int lj,
                                     long long n, int P, const T* __restrict__ K, long long plane,
                                     const T* kr) {
+  // stored coefficients where they differ from the rectangle constants of this precision
+  // (an FP32 row reads them only for CELL_GEN32 cells: the others round to kr exactly)
+  constexpr uint8_t GEN = sizeof(T) == 4 ? CELL_GEN32 : CELL_GENERAL;
   const T pc = ps[lj][li];
   const T dE = ps[lj][li + 1] - pc, dW = ps[lj][li - 1] - pc;
   const T dN = ps[lj + 1][li] - pc, dS = ps[lj - 1][li] - pc;
@@ -337,18 +341,18 @@ __device__ __forceinline__ T q4_row(const T (*ps)[W], const uint8_t (*ts)[W], in
   T b0 = kr[0], b1 = kr[3], b2 = kr[4];         // K01 K12 K13 of cell (i-1, j)
   T e0 = kr[1], e1 = kr[3], e2 = kr[5];         // K02 K12 K23 of cell (i-1, j-1)
   T f0 = kr[2], f1 = kr[4], f2 = kr[5];         // K03 K13 K23 of cell (i, j-1)
-  if ((t0 & (CELL_ACTIVE | CELL_GENERAL)) == (CELL_ACTIVE | CELL_GENERAL)) {
+  if ((t0 & (CELL_ACTIVE | GEN)) == (CELL_ACTIVE | GEN)) {
     a0 = __ldg(K + n); a1 = __ldg(K + plane + n); a2 = __ldg(K + 2 * plane + n);
   }
-  if ((t1 & (CELL_ACTIVE | CELL_GENERAL)) == (CELL_ACTIVE | CELL_GENERAL)) {
+  if ((t1 & (CELL_ACTIVE | GEN)) == (CELL_ACTIVE | GEN)) {
     const long long c = n - 1;
     b0 = __ldg(K + c); b1 = __ldg(K + 3 * plane + c); b2 = __ldg(K + 4 * plane + c);
   }
-  if ((t2 & (CELL_ACTIVE | CELL_GENERAL)) == (CELL_ACTIVE | CELL_GENERAL)) {
+  if ((t2 & (CELL_ACTIVE | GEN)) == (CELL_ACTIVE | GEN)) {
     const long long c = n - P - 1;
     e0 = __ldg(K + plane + c); e1 = __ldg(K + 3 * plane + c); e2 = __ldg(K + 5 * plane + c);
   }
-  if ((t3 & (CELL_ACTIVE | CELL_GENERAL)) == (CELL_ACTIVE | CELL_GENERAL)) {
+  if ((t3 & (CELL_ACTIVE | GEN)) == (CELL_ACTIVE | GEN)) {
     const long long c = n - P;
     f0 = __ldg(K + 2 * plane + c); f1 = __ldg(K + 4 * plane + c); f2 = __ldg(K + 5 * plane + c);
   }
