@@ -117,29 +117,30 @@ __device__ void fine_stencil(const MeshDev& m, const DevVariant& V, long long n,
 
 // The same row from the FP32 coefficients, summed in FP32 (the multigrid set-up: the
 // preconditioner's operators are FP32, and FP64 arithmetic runs at a small fraction of
-// the FP32 rate on this GPU).
+// the FP32 rate on this GPU).  Stored coefficients are read only where their FP32 values
+// differ from the rectangle's (CELL_GEN32); elsewhere they equal kr32 exactly.
 __device__ void fine_stencil32(const MeshDev& m, const DevVariant& V, long long n, int i, int j, float st[9]) {
   for (int k = 0; k < 9; ++k) st[k] = 0.0f;
   const long long plane = m.Vtot;
   const long long P = V.P;
   auto coef = [&](long long c, int mm, bool gen) { return gen ? m.K32[mm * plane + c] : V.kr32[mm]; };
   if (i < V.nx && j < V.ny && (m.tag[n] & CELL_ACTIVE)) {
-    const bool g = m.tag[n] & CELL_GENERAL;
+    const bool g = m.tag[n] & CELL_GEN32;
     st[5] += coef(n, 0, g); st[8] += coef(n, 1, g); st[7] += coef(n, 2, g);
   }
   if (i > 0 && j < V.ny && (m.tag[n - 1] & CELL_ACTIVE)) {
     const long long c = n - 1;
-    const bool g = m.tag[c] & CELL_GENERAL;
+    const bool g = m.tag[c] & CELL_GEN32;
     st[3] += coef(c, 0, g); st[7] += coef(c, 3, g); st[6] += coef(c, 4, g);
   }
   if (i > 0 && j > 0 && (m.tag[n - P - 1] & CELL_ACTIVE)) {
     const long long c = n - P - 1;
-    const bool g = m.tag[c] & CELL_GENERAL;
+    const bool g = m.tag[c] & CELL_GEN32;
     st[0] += coef(c, 1, g); st[1] += coef(c, 3, g); st[3] += coef(c, 5, g);
   }
   if (j > 0 && i < V.nx && (m.tag[n - P] & CELL_ACTIVE)) {
     const long long c = n - P;
-    const bool g = m.tag[c] & CELL_GENERAL;
+    const bool g = m.tag[c] & CELL_GEN32;
     st[1] += coef(c, 2, g); st[2] += coef(c, 4, g); st[5] += coef(c, 5, g);
   }
   float s = 0.0f;
