@@ -81,3 +81,18 @@ def test_product_path_fails_loudly_without_library(tmp_path):
             _lib.load(str(tmp_path / "nope.so"))
     finally:
         _lib._lib = saved
+
+
+def test_header_compiles_as_c99_and_cxx(tmp_path):
+    """include/pfq4.h is a C header: it compiles alone as pedantic C99 and as C++17."""
+    import shutil
+    src = tmp_path / "use.c"
+    src.write_text('#include "pfq4.h"\nint main(void) { pf_shape s = {0}; pf_batch* b = 0; (void)s; (void)b; return 0; }\n')
+    inc = os.path.join(ROOT, "include")
+    for cc, args in (("gcc", ["-std=c99", "-pedantic", "-Wall", "-Wextra", "-Werror"]),
+                     ("g++", ["-std=c++17", "-Wall", "-Werror", "-x", "c++"])):
+        if shutil.which(cc) is None:
+            pytest.skip(f"{cc} not installed")
+        r = subprocess.run([cc, *args, "-I", inc, "-c", str(src), "-o", str(tmp_path / "use.o")],
+                           capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
