@@ -25,7 +25,8 @@ follows:
 * `post`    - surface tangential velocity (section "Velocity Field and Surface
               Tangential Velocity") and Q / CoPFI (section "Effect of Gap Ratio").
 * `cutmesh` - the mixed-cell variant of the grid generation: surface points where grid
-              edges cross the circle, node splitting, triangle / pentagon cells
+              edges cross the body boundary (circles and polygons), node splitting,
+              triangle / pentagon cells
               (pentagon = triangle + quadrilateral), boundary-point redistribution,
               and the cut-cell element matrices and outputs.
 * `grad`    - adjoint shape gradient of CoPFI / gap flow (beyond the paper; its
