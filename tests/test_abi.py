@@ -96,3 +96,30 @@ def test_header_compiles_as_c99_and_cxx(tmp_path):
         r = subprocess.run([cc, *args, "-I", inc, "-c", str(src), "-o", str(tmp_path / "use.o")],
                            capture_output=True, text=True)
         assert r.returncode == 0, r.stderr
+
+
+def declared_arities():
+    """Number of parameters of every function declared in include/pfq4.h."""
+    src = open(os.path.join(ROOT, "include", "pfq4.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    out = {}
+    for m in re.finditer(r"\b(pf_[a-z_]+)\s*\(([^;{]*?)\)\s*;", src):
+        name, args = m.group(1), m.group(2).strip()
+        if name in ("pf_alloc_fn", "pf_free_fn"):
+            continue
+        depth, n = 0, (0 if args in ("", "void") else 1)
+        for ch in args:
+            depth += ch == "("
+            depth -= ch == ")"
+            n += ch == "," and depth == 0
+        out[name] = n
+    return out
+
+
+def test_ctypes_signatures_match_the_header_arities():
+    """Every ctypes declaration passes as many arguments as the C prototype takes."""
+    from paper_2512_12232_gb300 import _lib
+    ar = declared_arities()
+    assert ar, "no prototypes parsed"
+    bad = {k: (n, len(_lib._SIGS[k][1])) for k, n in ar.items() if k in _lib._SIGS and len(_lib._SIGS[k][1]) != n}
+    assert not bad, bad
