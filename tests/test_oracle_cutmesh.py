@@ -368,3 +368,22 @@ def test_cut_cell_velocity_approaches_the_exact_flow():
             e.append(np.hypot(uu[pos[j, i]] - ue, vv[pos[j, i]] - ve))
         errs.append(np.mean(e))
     assert errs[1] < 0.75 * errs[0] and errs[1] < 0.2, errs
+
+
+def test_three_solution_routes_agree_on_a_small_cut_mesh():
+    """Dense Cholesky (which needs the cut-cell system to be symmetric positive definite),
+    sparse LU and the element-by-element CG of Appendix A agree on a small mixed-cell mesh
+    with two bodies, one of them a polygon."""
+    sq = W.PolygonBody([(1.0, -0.6), (1.9, -0.6), (1.9, 0.5), (1.0, 0.5)], ref=(1.45, 0.0))
+    m = CM.build_cut_mesh((-3.0, 3.0, -2.0, 2.0, 36, 24), np.array([[-1.0, 0.2, 0.7]]), 9, polygons=[sq],
+                          sigma=0.3)
+    sysm = S.assemble(m, 1.3)
+    A = sysm.A.toarray()
+    assert np.abs(A - A.T).max() <= 1e-12 * np.abs(A).max()
+    u1, psi1 = SV.solve_direct(sysm, dense=True)
+    u2, psi2 = SV.solve_direct(sysm)
+    np.testing.assert_allclose(psi1, psi2, rtol=0, atol=1e-12)
+    x, psik, it, _ = SV.cg_paper(sysm, m.kind.ravel(), m.body.ravel(), tol=1e-14, criterion="relative")
+    assert it > 10
+    np.testing.assert_allclose(x, psi2, rtol=0, atol=1e-10)
+    np.testing.assert_allclose(psik, u2[sysm.n_free:], rtol=0, atol=1e-10)
